@@ -1,0 +1,166 @@
+/*
+ * helicwave.h -- C ABI of the GB300 (sm_103a) library for the helical-wave spectral method
+ * (Agarwal & Banerjee, arXiv 2210.12252): matrix-free Hamiltonian x block products, the
+ * diagonal preconditioner and a block eigensolver, for many (eta, nu) points.
+ *
+ * Conventions for every call
+ *   - Units: Hartree and bohr.
+ *   - Complex arrays are interleaved (re, im) FP64 pairs ("complex128"), column-major with a
+ *     leading dimension ld >= L_k counted in complex entries: entry (i, j) is at
+ *     ptr[2*(i + j*ld)] (real) and ptr[2*(i + j*ld) + 1] (imag).
+ *   - Device pointers are caller-owned device memory on the context's device; the library
+ *     never frees them.  The library owns its tables and workspace, sized by hw_setup_basis;
+ *     hw_apply_H / hw_apply_precond allocate nothing.
+ *   - Calls are ordered on the context's CUDA stream and asynchronous unless stated
+ *     (hw_solve_eigs, the hw_get_* queries and hw_build_potential return with results on the
+ *     host).  A context is not thread-safe.
+ *   - Errors: every call returns an hw_status; nothing throws across the ABI.  The message of
+ *     the last failure is hw_last_error(ctx).  Invalid arguments are rejected on the host
+ *     before any launch (HW_EINVAL); device-side waits are bounded and report HW_ETIMEOUT.
+ *
+ * Reciprocal-space order (compact): the order of eq. wavefun_storage,
+ *     i(m,n,k) = (m+M)(2N+1)K + (n+N)K + k,
+ * restricted to the modes kept by the kinetic-energy cutoff of eq. Energy_cutoff at the
+ * k-point (mask of Sec. "Imposition of kinetic energy cutoff").  L_k is the kept count.
+ * Real-space order: eq. wavefun_storage_real, theta1 slowest, r fastest, with theta1_i =
+ * i/N_th1, theta2_j = j/(Ncyc N_th2) and r_p the Gauss-Jacobi(0,1) nodes on (0, R) in
+ * ascending order.
+ */
+#ifndef HELICWAVE_H
+#define HELICWAVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hw_ctx hw_ctx;
+
+typedef enum {
+  HW_OK = 0,
+  HW_EINVAL = 1,     /* invalid argument (checked on the host before any launch)        */
+  HW_ENOMEM = 2,     /* device or host allocation failed during setup                   */
+  HW_ECUDA = 3,      /* a CUDA runtime / cuBLAS call failed                              */
+  HW_ESTATE = 4,     /* call out of order (no basis, no potential, no device, ...)       */
+  HW_ENOTCONV = 5,   /* eigensolver reached maxit; partial results are returned          */
+  HW_ETIMEOUT = 6    /* a bounded device-side wait gave up; the context stays usable     */
+} hw_status;
+
+typedef enum {
+  HW_FP64 = 0,       /* every step in FP64                                                 */
+  HW_MIXED = 1       /* transforms in FP32 (FP32 accumulate); diagonal terms, Gram,
+                        Cholesky, Rayleigh-Ritz and the final residual check in FP64      */
+} hw_prec;
+
+typedef enum {
+  HW_PRECOND_TPA = 0,      /* Teter-Payne-Allan diagonal (Sec. Eigensolvers and Preconditioning) */
+  HW_PRECOND_LEARNED = 1,  /* per-mode MLP scaling installed by hw_set_mlp                       */
+  HW_PRECOND_NONE = 2
+} hw_precond_kind;
+
+/* Geometry and discretisation (Secs. "Description of Physical System", "Wave function
+ * storage", "Imposition of kinetic energy cutoff").  The basis box follows the grids:
+ * M = floor((N_th1-1)/s), N = floor((N_th2-1)/s), K = floor(N_r/s) with s = oversample
+ * (the paper's grid rule N_th = 4*max+1, N_r = 4*K_max read backwards). */
+typedef struct {
+  double R;          /* cylinder radius (Dirichlet wall), bohr, > 0                        */
+  double tau;        /* screw pitch, bohr, > 0                                              */
+  double alpha;      /* twist per pitch (turns)                                             */
+  int ncyc;          /* cyclic order Ncyc >= 1                                              */
+  double ecut;       /* kinetic cutoff, Hartree; <= 0 keeps the whole box                   */
+  int Nr;            /* radial Gauss-Jacobi nodes, >= oversample                            */
+  int Nth1;          /* theta1 Fourier nodes; factors 2 and 3 only; >= 2M+1                 */
+  int Nth2;          /* theta2 Fourier nodes; factors 2 and 3 only; >= 2N+1                 */
+  int oversample;    /* s >= 2                                                              */
+} hw_basis_params;
+
+/* Create a context on CUDA device `device` whose calls are ordered on `cuda_stream` (a
+ * cudaStream_t, NULL = legacy default stream).  device = -1 creates a host-only context:
+ * hw_setup_basis and the hw_get_* queries work, every device call returns HW_ESTATE. */
+hw_status hw_create(hw_ctx** out, int device, void* cuda_stream);
+void hw_destroy(hw_ctx* ctx);
+const char* hw_last_error(const hw_ctx* ctx);
+
+/* Basis set, radial quadrature, tables and cutoff masks for nk points (eta_b, nu_b)
+ * (eqs. Phi_expanded_in_basis_set, Basis_fun_derived, Energy_cutoff; Sec. eta-space
+ * discretization).  ecut_per_k (host, nullable) overrides params->ecut per point.
+ * nu must be 0 (the 1/r^2 terms of eqs. ell_mnk and I_nkk_prime are not built).
+ * L_out (host, [nk]) receives the masked basis sizes.  Replaces any earlier basis. */
+hw_status hw_setup_basis(hw_ctx* ctx, const hw_basis_params* params, int nk, const double* eta,
+                         const double* nu, const double* ecut_per_k, int64_t* L_out);
+
+/* Sizes: box limits, grid point count N_th1*N_th2*N_r, number of (m, n) angular pairs kept
+ * at any of the k-points. Any pointer may be NULL. */
+hw_status hw_get_sizes(const hw_ctx* ctx, int* M, int* N, int* K, int64_t* grid_points,
+                       int* n_pairs);
+
+/* Radial nodes r_p (ascending) and weights omega_p with sum_p omega_p f(r_p) ~ int_0^R f r dr
+ * (host outputs, [Nr] each; either may be NULL). */
+hw_status hw_get_grid(const hw_ctx* ctx, double* r_nodes, double* r_weights);
+
+/* (m, n, k) of every kept mode of k-point k in compact order, k 0-based (host, [3*L_k]). */
+hw_status hw_get_index_map(const hw_ctx* ctx, int k, int32_t* mnk);
+
+/* Diagonal of the Hamiltonian's reciprocal-space part at k-point k, i.e. the shifted kinetic
+ * energy 1/2 lambda^0 - a - b(i2pi m) - c(i2pi n Ncyc) of Algorithm 5 (host, [L_k]). */
+hw_status hw_get_kinetic(const hw_ctx* ctx, int k, double* ke);
+
+/* Radial table xi_{n,k}(r_p) for angular order n (host output [Nr*K], p-major). */
+hw_status hw_get_radial_table(const hw_ctx* ctx, int n, double* table);
+
+/* Install the real potential V on the grid (eq. wavefun_storage_real order, length
+ * N_th1*N_th2*N_r).  on_device != 0: V is a device pointer (copied on the stream), else a
+ * host pointer (copied synchronously). */
+hw_status hw_set_potential(hw_ctx* ctx, const double* V, int on_device);
+
+/* Build and install the Gaussian-well potential
+ *   V(x) = sum_a sum_{zeta,mu} -Z_a exp(-|x - Upsilon_{zeta,mu} x_a|^2 / (2 sigma_a^2))
+ * summed over the images of the helical group (eq. symm_opera) with |z - z_image| <= 10 sigma.
+ * atoms: host array [n_atoms][5] of (r, vartheta, z, Z, sigma).  Runs on the device and
+ * returns when V is installed.  V_out (host, nullable) receives V in eq. wavefun_storage_real
+ * order. */
+hw_status hw_build_potential(hw_ctx* ctx, int n_atoms, const double* atoms, double* V_out);
+
+/* Y = H X at k-point k (Algorithm 5): reciprocal-space diagonal terms, inverse transform
+ * (Algorithms 1-2), pointwise V, forward transform (Algorithms 3-4).  X, Y: device,
+ * complex128, L_k x ns, leading dimension ld.  X and Y must not overlap. */
+hw_status hw_apply_H(hw_ctx* ctx, int k, const double* X, double* Y, int ns, int64_t ld,
+                     hw_prec prec);
+
+/* Y_b = H(b) X_b for the nk k-points kidx[0..nk) in one pipeline; X[b], Y[b] are device
+ * pointers to L_{kidx[b]} x ns blocks with leading dimension ld (>= max L). */
+hw_status hw_apply_H_batched(hw_ctx* ctx, int nk, const int* kidx, const double* const* X,
+                             double* const* Y, int ns, int64_t ld, hw_prec prec);
+
+/* Z = K R, a diagonal preconditioner at k-point k applied column by column (device,
+ * complex128, L_k x ns, leading dimension ld; Z may equal R).  kind = HW_PRECOND_TPA: the
+ * Teter-Payne-Allan diagonal P(g)/(P(g)+16 g^4), P = 27+18g+12g^2+8g^3, g_i = KE_i / KE_res,
+ * KE_res the |r_i|^2-weighted mean of KE_i over the column (Sec. Eigensolvers and
+ * Preconditioning).  kind = HW_PRECOND_LEARNED: Z_i = s(features_i, ritz_j) R_i with the MLP
+ * of hw_set_mlp; ritz is a device array [ns] (required for LEARNED, ignored otherwise). */
+hw_status hw_apply_precond(hw_ctx* ctx, int k, const double* R, double* Z, int ns, int64_t ld,
+                           const double* ritz, int kind);
+
+/* Lowest n_eig eigenpairs at the nk k-points kidx[] by block LOBPCG (Sec. Eigensolvers and
+ * Preconditioning) on blocks of `block` >= n_eig columns (0: n_eig + max(4, n_eig/8)).
+ * A column is converged when ||H x - theta x||_2 <= tol with ||x|| = 1.  X0 (nullable):
+ * nk device pointers to L_k x block complex128 start blocks (leading dimension L_k); NULL
+ * draws a seeded Gaussian start on the device.  Outputs: evals (host, [nk*n_eig]), iters
+ * (host, [nk], nullable), resid (host, [nk*n_eig], nullable: final residual norms),
+ * evecs (nullable: nk device pointers to L_k x n_eig blocks with leading dimension ld_evecs).
+ * Returns HW_ENOTCONV (with the partial results) when maxit is reached.  Synchronous. */
+hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx, int n_eig, int block, double tol,
+                        int maxit, hw_prec prec, int precond_kind, const double* const* X0,
+                        double* evals, double* const* evecs, int64_t ld_evecs, int* iters,
+                        double* resid);
+
+/* Wait for all work on the context's stream. */
+hw_status hw_synchronize(hw_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HELICWAVE_H */

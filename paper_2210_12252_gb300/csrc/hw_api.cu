@@ -1,0 +1,417 @@
+// C ABI of the helical-wave library (declarations and argument contracts: include/helicwave.h).
+// Context lifetime, basis setup and upload, potential installation, H X and preconditioner
+// entry points.  The block eigensolver lives in hw_lobpcg.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hw_common.cuh"
+#include "hw_ctx.h"
+
+hw_status hw_fail(hw_ctx* ctx, hw_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+namespace hw {
+
+void free_basis(hw_ctx* ctx);
+void lobpcg_free(hw_ctx* ctx);
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (dev >= 0 && cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+cudaError_t upload(T** dst, const T* src, size_t n) {
+  cudaError_t e = cudaMalloc((void**)dst, std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (n) e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+// V[i][j][p] (eq. wavefun_storage_real) -> Vd[p][j][i] in FP64 and FP32
+__global__ void k_v_relayout(const double* __restrict__ V, double* __restrict__ V64,
+                             float* __restrict__ V32, int n1, int n2, int nr) {
+  const long total = (long)n1 * n2 * nr;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n1);
+    const long rest = t / n1;
+    const int j = (int)(rest % n2);
+    const int p = (int)(rest / n2);
+    const double v = V[((size_t)i * n2 + j) * nr + p];
+    V64[t] = v;
+    V32[t] = (float)v;
+  }
+}
+
+std::vector<double> twiddles(int n) {
+  std::vector<double> t(2 * n);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int k = 0; k < n; ++k) {
+    const long double a = -2.0L * pi * k / n;
+    t[2 * k] = (double)cosl(a);
+    t[2 * k + 1] = (double)sinl(a);
+  }
+  return t;
+}
+
+hw_status cuda_fail(hw_ctx* ctx, cudaError_t e, const char* what) {
+  return hw_fail(ctx, HW_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+hw_status check_device_call(hw_ctx* ctx) {
+  if (!ctx) return HW_EINVAL;
+  if (ctx->device < 0) return hw_fail(ctx, HW_ESTATE, "host-only context has no device");
+  if (!ctx->have_basis) return hw_fail(ctx, HW_ESTATE, "hw_setup_basis has not been called");
+  return HW_OK;
+}
+
+}  // namespace
+
+void free_basis(hw_ctx* ctx) {
+  auto& db = ctx->db;
+  dfree(db.group_start);
+  dfree(db.pair_n);
+  dfree(db.pair_mrow);
+  dfree(db.mrow_m);
+  dfree(db.off);
+  dfree(db.Ka);
+  dfree(db.ke);
+  dfree(db.vscratch);
+  db.ke_off.clear();
+  for (auto* t : {&db.t64.rinv, &db.t64.rfwd, &db.t64.V, &db.t64.tw1, &db.t64.tw2}) dfree(*t);
+  for (auto* t : {&db.t32.rinv, &db.t32.rfwd, &db.t32.V, &db.t32.tw1, &db.t32.tw2}) dfree(*t);
+  dfree(ctx->ws.gbuf);
+  dfree(ctx->ws.hbuf);
+  ctx->ws.cols = 0;
+  lobpcg_free(ctx);
+  ctx->have_basis = false;
+  ctx->have_V = false;
+}
+
+}  // namespace hw
+
+using namespace hw;
+
+extern "C" {
+
+hw_status hw_create(hw_ctx** out, int device, void* cuda_stream) {
+  if (!out) return HW_EINVAL;
+  *out = nullptr;
+  hw_ctx* ctx = new (std::nothrow) hw_ctx();
+  if (!ctx) return HW_ENOMEM;
+  ctx->device = device;
+  if (device >= 0) {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || device >= n) {
+      delete ctx;
+      return HW_ECUDA;
+    }
+    DeviceGuard g(device);
+    cudaSetDevice(device);
+    ctx->stream = (cudaStream_t)cuda_stream;
+    if (cublasCreate(&ctx->cublas) != CUBLAS_STATUS_SUCCESS) {
+      delete ctx;
+      return HW_ECUDA;
+    }
+    cublasSetStream(ctx->cublas, ctx->stream);
+    cublasSetPointerMode(ctx->cublas, CUBLAS_POINTER_MODE_HOST);
+    if (cudaMalloc((void**)&ctx->dflag, 64 * sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->dflag, 0, 64 * sizeof(int)) != cudaSuccess) {
+      cublasDestroy(ctx->cublas);
+      delete ctx;
+      return HW_ECUDA;
+    }
+    if (hx_configure(ctx) != cudaSuccess) {
+      cudaFree(ctx->dflag);
+      cublasDestroy(ctx->cublas);
+      delete ctx;
+      return HW_ECUDA;
+    }
+  }
+  *out = ctx;
+  return HW_OK;
+}
+
+void hw_destroy(hw_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->device >= 0) {
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_basis(ctx);
+    if (ctx->dflag) cudaFree(ctx->dflag);
+    if (ctx->cublas) cublasDestroy(ctx->cublas);
+  }
+  delete ctx;
+}
+
+const char* hw_last_error(const hw_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+hw_status hw_setup_basis(hw_ctx* ctx, const hw_basis_params* params, int nk, const double* eta,
+                         const double* nu, const double* ecut_per_k, int64_t* L_out) {
+  if (!ctx || !params) return hw_fail(ctx, HW_EINVAL, "null argument");
+  HostBasis hb;
+  std::string msg = build_host_basis(*params, nk, eta, nu, ecut_per_k, hb);
+  if (!msg.empty()) return hw_fail(ctx, HW_EINVAL, msg);
+  if (hb.K > 64) return hw_fail(ctx, HW_EINVAL, "K = Nr/oversample must be <= 64");
+  FftPlan p1, p2;
+  if (!make_fft_plan(params->Nth1, p1) || !make_fft_plan(params->Nth2, p2))
+    return hw_fail(ctx, HW_EINVAL, "angular grid sizes must factor into 2 and 3");
+  if (ctx->device >= 0) {
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_basis(ctx);
+    auto& db = ctx->db;
+    cudaError_t e = cudaSuccess;
+    const int Nr = params->Nr, K = hb.K, N = hb.N;
+    // radial tables
+    std::vector<double> rinv((size_t)(N + 1) * Nr * K), rfwd((size_t)(N + 1) * K * Nr);
+    const double pi = 3.14159265358979323846;
+    const double scale = 2.0 * pi * params->tau / params->ncyc / (double(params->Nth1) * params->Nth2);
+    for (int n = 0; n <= N; ++n)
+      for (int p = 0; p < Nr; ++p)
+        for (int k = 0; k < K; ++k) {
+          const double x = hb.xi[((size_t)n * Nr + p) * K + k];
+          rinv[((size_t)n * Nr + p) * K + k] = x;
+          rfwd[((size_t)n * K + k) * Nr + p] = scale * hb.wr[p] * x;
+        }
+    std::vector<float> rinv32(rinv.begin(), rinv.end()), rfwd32(rfwd.begin(), rfwd.end());
+    std::vector<double> tw1 = twiddles(params->Nth1), tw2 = twiddles(params->Nth2);
+    std::vector<float> tw1f(tw1.begin(), tw1.end()), tw2f(tw2.begin(), tw2.end());
+    std::vector<double> keall;
+    db.ke_off.assign(nk + 1, 0);
+    for (int b = 0; b < nk; ++b) {
+      db.ke_off[b] = (int64_t)keall.size();
+      keall.insert(keall.end(), hb.ke[b].begin(), hb.ke[b].end());
+    }
+    db.ke_off[nk] = (int64_t)keall.size();
+    const size_t grid = (size_t)params->Nth1 * params->Nth2 * Nr;
+#define UP(dst, vec)                                            \
+  if (e == cudaSuccess) e = upload(&(dst), (vec).data(), (vec).size());
+    UP(db.group_start, hb.group_start);
+    UP(db.pair_n, hb.pair_n);
+    UP(db.pair_mrow, hb.pair_mrow);
+    UP(db.mrow_m, hb.mrow_m);
+    UP(db.off, hb.off);
+    UP(db.Ka, hb.Ka);
+    UP(db.ke, keall);
+    UP(db.t64.rinv, rinv);
+    UP(db.t64.rfwd, rfwd);
+    UP(db.t64.tw1, tw1);
+    UP(db.t64.tw2, tw2);
+    UP(db.t32.rinv, rinv32);
+    UP(db.t32.rfwd, rfwd32);
+    UP(db.t32.tw1, tw1f);
+    UP(db.t32.tw2, tw2f);
+#undef UP
+    if (e == cudaSuccess) e = cudaMalloc((void**)&db.t64.V, grid * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&db.t32.V, grid * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&db.vscratch, grid * sizeof(double));
+    // G / H workspace: passes of up to `cols` columns, ~1 GiB for both buffers
+    const size_t per_col = 2 * (size_t)Nr * hb.nA * sizeof(double2);
+    size_t cols = std::max<size_t>(16, std::min<size_t>(2048, (size_t(1) << 30) / per_col));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->ws.gbuf, cols * per_col / 2);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->ws.hbuf, cols * per_col / 2);
+    if (e != cudaSuccess) {
+      free_basis(ctx);
+      return hw_fail(ctx, e == cudaErrorMemoryAllocation ? HW_ENOMEM : HW_ECUDA,
+                     std::string("setup upload: ") + cudaGetErrorString(e));
+    }
+    ctx->ws.cols = cols;
+  }
+  ctx->hb = std::move(hb);
+  ctx->plan1 = p1;
+  ctx->plan2 = p2;
+  ctx->have_basis = true;
+  ctx->have_V = false;
+  if (L_out)
+    for (int b = 0; b < nk; ++b) L_out[b] = ctx->hb.L[b];
+  return HW_OK;
+}
+
+hw_status hw_get_sizes(const hw_ctx* ctx, int* M, int* N, int* K, int64_t* grid_points,
+                       int* n_pairs) {
+  if (!ctx) return HW_EINVAL;
+  if (!ctx->have_basis) return HW_ESTATE;
+  const auto& hb = ctx->hb;
+  if (M) *M = hb.M;
+  if (N) *N = hb.N;
+  if (K) *K = hb.K;
+  if (grid_points) *grid_points = (int64_t)hb.prm.Nth1 * hb.prm.Nth2 * hb.prm.Nr;
+  if (n_pairs) *n_pairs = hb.nA;
+  return HW_OK;
+}
+
+hw_status hw_get_grid(const hw_ctx* ctx, double* r_nodes, double* r_weights) {
+  if (!ctx) return HW_EINVAL;
+  if (!ctx->have_basis) return HW_ESTATE;
+  if (r_nodes) std::memcpy(r_nodes, ctx->hb.r.data(), ctx->hb.r.size() * sizeof(double));
+  if (r_weights) std::memcpy(r_weights, ctx->hb.wr.data(), ctx->hb.wr.size() * sizeof(double));
+  return HW_OK;
+}
+
+hw_status hw_get_index_map(const hw_ctx* ctx, int k, int32_t* mnk) {
+  if (!ctx || !mnk) return HW_EINVAL;
+  if (!ctx->have_basis) return HW_ESTATE;
+  if (k < 0 || k >= ctx->hb.nk) return HW_EINVAL;
+  std::memcpy(mnk, ctx->hb.mnk[k].data(), ctx->hb.mnk[k].size() * sizeof(int32_t));
+  return HW_OK;
+}
+
+hw_status hw_get_kinetic(const hw_ctx* ctx, int k, double* ke) {
+  if (!ctx || !ke) return HW_EINVAL;
+  if (!ctx->have_basis) return HW_ESTATE;
+  if (k < 0 || k >= ctx->hb.nk) return HW_EINVAL;
+  std::memcpy(ke, ctx->hb.ke[k].data(), ctx->hb.ke[k].size() * sizeof(double));
+  return HW_OK;
+}
+
+hw_status hw_get_radial_table(const hw_ctx* ctx, int n, double* table) {
+  if (!ctx || !table) return HW_EINVAL;
+  if (!ctx->have_basis) return HW_ESTATE;
+  const auto& hb = ctx->hb;
+  if (n < -hb.N || n > hb.N) return HW_EINVAL;
+  const size_t sz = (size_t)hb.prm.Nr * hb.K;
+  std::memcpy(table, hb.xi.data() + (size_t)std::abs(n) * sz, sz * sizeof(double));
+  return HW_OK;
+}
+
+hw_status hw_set_potential(hw_ctx* ctx, const double* V, int on_device) {
+  hw_status st = check_device_call(ctx);
+  if (st != HW_OK) return st;
+  if (!V) return hw_fail(ctx, HW_EINVAL, "null potential");
+  DeviceGuard g(ctx->device);
+  const auto& p = ctx->hb.prm;
+  const size_t grid = (size_t)p.Nth1 * p.Nth2 * p.Nr;
+  cudaError_t e;
+  if (on_device) {
+    e = cudaMemcpyAsync(ctx->db.vscratch, V, grid * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream);
+  } else {
+    for (size_t i = 0; i < grid; ++i)
+      if (!std::isfinite(V[i])) return hw_fail(ctx, HW_EINVAL, "potential has a non-finite entry");
+    e = cudaMemcpyAsync(ctx->db.vscratch, V, grid * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "set_potential copy");
+  k_v_relayout<<<1024, 256, 0, ctx->stream>>>(ctx->db.vscratch, ctx->db.t64.V, ctx->db.t32.V, p.Nth1,
+                                              p.Nth2, p.Nr);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "set_potential relayout");
+  ctx->have_V = true;
+  return HW_OK;
+}
+
+hw_status hw_build_potential(hw_ctx* ctx, int n_atoms, const double* atoms, double* V_out) {
+  if (!ctx) return HW_EINVAL;
+  if (!ctx->have_basis) return hw_fail(ctx, HW_ESTATE, "hw_setup_basis has not been called");
+  if (n_atoms < 0 || (n_atoms > 0 && !atoms)) return hw_fail(ctx, HW_EINVAL, "bad atom list");
+  for (int a = 0; a < n_atoms; ++a) {
+    for (int c = 0; c < 5; ++c)
+      if (!std::isfinite(atoms[5 * a + c])) return hw_fail(ctx, HW_EINVAL, "non-finite atom entry");
+    if (!(atoms[5 * a + 4] > 0)) return hw_fail(ctx, HW_EINVAL, "sigma must be > 0");
+    if (atoms[5 * a] < 0) return hw_fail(ctx, HW_EINVAL, "atom radius must be >= 0");
+  }
+  std::vector<double> V;
+  build_gaussian_potential(ctx->hb, n_atoms, atoms, V);
+  if (V_out) std::memcpy(V_out, V.data(), V.size() * sizeof(double));
+  if (ctx->device < 0) return HW_OK;
+  return hw_set_potential(ctx, V.data(), 0);
+}
+
+static hw_status apply_common(hw_ctx* ctx, int nk, const int* kidx, const double* const* X,
+                              double* const* Y, int ns, int64_t ld, hw_prec prec) {
+  hw_status st = check_device_call(ctx);
+  if (st != HW_OK) return st;
+  if (!ctx->have_V) return hw_fail(ctx, HW_ESTATE, "no potential installed");
+  if (nk < 1 || ns < 1 || !kidx || !X || !Y) return hw_fail(ctx, HW_EINVAL, "bad block arguments");
+  if (prec != HW_FP64 && prec != HW_MIXED) return hw_fail(ctx, HW_EINVAL, "bad precision");
+  int64_t maxL = 0;
+  for (int b = 0; b < nk; ++b) {
+    if (kidx[b] < 0 || kidx[b] >= ctx->hb.nk) return hw_fail(ctx, HW_EINVAL, "k-point index out of range");
+    if (!X[b] || !Y[b]) return hw_fail(ctx, HW_EINVAL, "null block pointer");
+    if (X[b] == Y[b]) return hw_fail(ctx, HW_EINVAL, "X and Y must not overlap");
+    maxL = std::max(maxL, ctx->hb.L[kidx[b]]);
+  }
+  if (ld < maxL) return hw_fail(ctx, HW_EINVAL, "ld < L");
+  DeviceGuard g(ctx->device);
+  for (int b0 = 0; b0 < nk; b0 += MAXSLOT) {
+    Blocks blk;
+    blk.nslot = std::min(MAXSLOT, nk - b0);
+    for (int i = 0; i < blk.nslot; ++i) {
+      blk.x[i] = X[b0 + i];
+      blk.y[i] = Y[b0 + i];
+      blk.kb[i] = kidx[b0 + i];
+    }
+    cudaError_t e = prec == HW_FP64 ? launch_hx<double>(ctx, blk, ns, ld) : launch_hx<float>(ctx, blk, ns, ld);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "apply_H launch");
+  }
+  return HW_OK;
+}
+
+hw_status hw_apply_H(hw_ctx* ctx, int k, const double* X, double* Y, int ns, int64_t ld,
+                     hw_prec prec) {
+  return apply_common(ctx, 1, &k, &X, &Y, ns, ld, prec);
+}
+
+hw_status hw_apply_H_batched(hw_ctx* ctx, int nk, const int* kidx, const double* const* X,
+                             double* const* Y, int ns, int64_t ld, hw_prec prec) {
+  return apply_common(ctx, nk, kidx, X, Y, ns, ld, prec);
+}
+
+hw_status hw_apply_precond(hw_ctx* ctx, int k, const double* R, double* Z, int ns, int64_t ld,
+                           const double* ritz, int kind) {
+  hw_status st = check_device_call(ctx);
+  if (st != HW_OK) return st;
+  if (k < 0 || k >= ctx->hb.nk) return hw_fail(ctx, HW_EINVAL, "k-point index out of range");
+  if (!R || !Z || ns < 1 || ld < ctx->hb.L[k]) return hw_fail(ctx, HW_EINVAL, "bad block arguments");
+  DeviceGuard g(ctx->device);
+  Blocks blk;
+  blk.nslot = 1;
+  blk.x[0] = R;
+  blk.y[0] = Z;
+  blk.kb[0] = k;
+  cudaError_t e;
+  if (kind == HW_PRECOND_TPA) {
+    e = launch_tpa(ctx, blk, ns, ld);
+  } else if (kind == HW_PRECOND_NONE) {
+    e = (R == Z) ? cudaSuccess
+                 : cudaMemcpy2DAsync(Z, ld * 16, R, ld * 16, ctx->hb.L[k] * 16, ns, cudaMemcpyDeviceToDevice,
+                                     ctx->stream);
+  } else {
+    (void)ritz;
+    return hw_fail(ctx, HW_EINVAL, "unknown preconditioner kind");
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "apply_precond");
+  return HW_OK;
+}
+
+hw_status hw_synchronize(hw_ctx* ctx) {
+  if (!ctx) return HW_EINVAL;
+  if (ctx->device < 0) return HW_OK;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize");
+  return HW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// The library context and device-side data (CUDA translation units only).
+#pragma once
+
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "hw_internal.h"
+
+namespace hw {
+
+constexpr int MAXSLOT = 64;   // column blocks (k-points) per launch
+
+template <typename T>
+struct DevTables {
+  T* rinv = nullptr;   // [(N+1)][Nr][K]      xi_{n,k}(r_p)
+  T* rfwd = nullptr;   // [(N+1)][K][Nr]      (2 pi tau / Ncyc) w_p xi_{n,k}(r_p) / (Nth1 Nth2)
+  T* V = nullptr;      // [Nr][Nth2][Nth1]    potential, slab layout
+  T* tw1 = nullptr;    // [2*Nth1]            e^{-2 pi i t / Nth1} as (re, im)
+  T* tw2 = nullptr;    // [2*Nth2]
+};
+
+struct DevBasis {
+  int* group_start = nullptr;  // [N+2]
+  int* pair_n = nullptr;       // [nA]
+  int* pair_mrow = nullptr;    // [nA]
+  int* mrow_m = nullptr;       // [nmr]
+  int* off = nullptr;          // [nk][nA]
+  int* Ka = nullptr;           // [nk][nA]
+  double* ke = nullptr;        // concatenated [sum L_b] shifted kinetic energies
+  std::vector<int64_t> ke_off; // host: start of k-point b in ke
+  double* vscratch = nullptr;  // [grid] staging for set_potential
+  DevTables<double> t64;
+  DevTables<float> t32;
+};
+
+// G / H intermediates for `cols` columns per pass, [column][r_p][pair] complex FP64-sized
+struct Workspace {
+  void* gbuf = nullptr;
+  void* hbuf = nullptr;
+  size_t cols = 0;
+};
+
+// per-launch column blocks, passed by value to the kernels
+struct Blocks {
+  const double* x[MAXSLOT];
+  double* y[MAXSLOT];
+  int kb[MAXSLOT];
+  int nslot;
+};
+
+struct LobpcgWork;
+struct MlpState;
+
+}  // namespace hw
+
+struct hw_ctx {
+  int device = -1;
+  cudaStream_t stream = nullptr;
+  cublasHandle_t cublas = nullptr;
+  std::string err;
+  bool have_basis = false;
+  bool have_V = false;
+  hw::HostBasis hb;
+  hw::FftPlan plan1, plan2;
+  hw::DevBasis db;
+  hw::Workspace ws;
+  hw::LobpcgWork* lw = nullptr;
+  hw::MlpState* mlp = nullptr;
+  int* dflag = nullptr;        // device status word for bounded waits
+};
+
+// set the context's error message and return the status
+hw_status hw_fail(hw_ctx* ctx, hw_status st, const std::string& msg);
+
+namespace hw {
+template <typename T>
+cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld);
+cudaError_t hx_configure(hw_ctx* ctx);
+cudaError_t launch_tpa(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld);
+}  // namespace hw

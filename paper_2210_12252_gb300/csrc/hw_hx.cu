@@ -1,0 +1,450 @@
+// H X for the helical-wave discretisation (arXiv 2210.12252, Algorithm 5), as three kernels:
+//
+//   k_radial_inv   gather of the kept coefficients + inverse radial transform
+//                  G_{m,n}(r_p) = sum_k xi_{n,k}(r_p) X_{m,n,k}        (Algorithm 1, first loop)
+//   k_slab         per radial node and column: inverse angular DFT of the kept (m, n) band,
+//                  pointwise multiply by V(theta1, theta2, r_p), forward angular DFT cropped
+//                  back to the band                                   (Algorithms 2 and 4)
+//   k_radial_fwd   forward radial quadrature + reciprocal-space diagonal + scatter to the
+//                  compact order
+//                  Y_{m,n,k} = d_{m,n,k} X_{m,n,k} + sum_p O_n[k,p] H_{m,n}(r_p)
+//                                                                      (Algorithm 3, Alg. 5)
+//
+// The intermediates G and H are stored as [column][r_p][pair] with pairs = the (m, n) angular
+// pairs kept at any k-point, grouped by |n| so that pairs sharing a radial table are adjacent.
+// The forward angular DFT is unnormalised; its 1/(N_th1 N_th2) and the quadrature factor
+// 2 pi tau / Ncyc * w_p are folded into the forward radial table.
+//
+// The angular DFTs are mixed-radix (4, 3, 2) Stockham FFTs in shared memory.  The inverse
+// transform is pruned to the kept band: the theta2 pass runs only over the m rows that carry
+// kept pairs, the theta1 pass inserts those rows into otherwise-zero columns, and the forward
+// pass extracts only the kept bins.  T is double (FP64 path) or float (mixed path); the
+// diagonal term is always applied in FP64.
+#include <algorithm>
+#include <cstdio>
+
+#include "hw_common.cuh"
+#include "hw_ctx.h"
+
+namespace hw {
+
+// --------------------------------------------------------------------------- shared FFT
+struct FftDev {
+  int n, nst;
+  int rad[16];
+};
+
+// Batched Stockham FFT of `nb` transforms of length `n` stored with row stride n, ping-ponging
+// between src and dst; returns the buffer that holds the result.  sign = -1 forward
+// (e^{-2 pi i jk/n}), +1 inverse (unnormalised).  tw[t] = e^{-2 pi i t/n}.  Ends with a barrier.
+template <typename T>
+__device__ cplx_t<T>* fft_batch(cplx_t<T>* src, cplx_t<T>* dst, const FftDev& pl, int nb,
+                                const cplx_t<T>* __restrict__ tw, int sign) {
+  using V = cplx_t<T>;
+  const int n = pl.n;
+  int Ns = 1;
+  for (int s = 0; s < pl.nst; ++s) {
+    const int R = pl.rad[s];
+    const int nbf = n / R;
+    const int tstride = n / (Ns * R);
+    for (int idx = threadIdx.x; idx < nb * nbf; idx += blockDim.x) {
+      const int b = idx / nbf, j = idx - b * nbf;
+      const V* in = src + b * n;
+      V* out = dst + b * n;
+      const int k = j % Ns;
+      V v0 = in[j], v1 = in[j + nbf], v2, v3;
+      if (R >= 3) v2 = in[j + 2 * nbf];
+      if (R == 4) v3 = in[j + 3 * nbf];
+      if (k) {
+        V w = tw[k * tstride];
+        if (sign > 0) w = cconj(w);
+        v1 = cmul(v1, w);
+        if (R >= 3) {
+          V w2 = tw[2 * k * tstride];
+          if (sign > 0) w2 = cconj(w2);
+          v2 = cmul(v2, w2);
+        }
+        if (R == 4) {
+          V w3 = tw[3 * k * tstride];
+          if (sign > 0) w3 = cconj(w3);
+          v3 = cmul(v3, w3);
+        }
+      }
+      const int base = (j / Ns) * Ns * R + k;
+      if (R == 2) {
+        out[base] = cadd(v0, v1);
+        out[base + Ns] = csub(v0, v1);
+      } else if (R == 4) {
+        V s02 = cadd(v0, v2), d02 = csub(v0, v2);
+        V s13 = cadd(v1, v3), d13 = csub(v1, v3);
+        V t = cmul_i(d13, sign);  // sign*i*(v1 - v3)
+        out[base] = cadd(s02, s13);
+        out[base + Ns] = cadd(d02, t);
+        out[base + 2 * Ns] = csub(s02, s13);
+        out[base + 3 * Ns] = csub(d02, t);
+      } else {  // R == 3
+        const T h = T(0.86602540378443864676);  // sqrt(3)/2
+        V s12 = cadd(v1, v2), d12 = csub(v1, v2);
+        V t;
+        t.x = v0.x - T(0.5) * s12.x;
+        t.y = v0.y - T(0.5) * s12.y;
+        V u = cmul_i(d12, sign);  // sign*i*(v1 - v2)
+        u.x *= h;
+        u.y *= h;
+        out[base] = cadd(v0, s12);
+        out[base + Ns] = cadd(t, u);
+        out[base + 2 * Ns] = csub(t, u);
+      }
+    }
+    __syncthreads();
+    V* tmp = src;
+    src = dst;
+    dst = tmp;
+    Ns *= R;
+  }
+  return src;
+}
+
+// --------------------------------------------------------------------------- radial inverse
+template <typename T>
+struct RadArgs {
+  int Nr, K, nA, ncols, ns, c0;   // ncols columns of this pass start at global column c0;
+                                  // global column c belongs to block c / ns, column c % ns
+  const int* group_start;     // [N+2] pair range of each |n| group
+  const int* off;             // [nk][nA]
+  const int* Ka;              // [nk][nA]
+  int64_t ld;
+  const T* rtab;              // inverse [(N+1)][Nr][K] or forward [(N+1)][K][Nr]
+  const double* ke;           // concatenated shifted kinetic energies (forward only)
+  int64_t keoff[MAXSLOT];     // start of each block's k-point in ke
+  cplx_t<T>* gh;              // G (inverse output) or H (forward input)
+  Blocks blk;
+};
+
+constexpr int RAD_Q = 64;   // (column, pair) items per CTA
+constexpr int RAD_THREADS = 256;
+
+// grid: x = tile of items within group g, y = g.  Items of group g are (c, a) with
+// a in [gs, ge), flattened as c * na + (a - gs).
+template <typename T>
+__global__ void __launch_bounds__(RAD_THREADS) k_radial_inv(RadArgs<T> A) {
+  using V = cplx_t<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int g = blockIdx.y;
+  const int gs = A.group_start[g], na = A.group_start[g + 1] - gs;
+  const long nitems = (long)na * A.ncols;
+  const long q0 = (long)blockIdx.x * RAD_Q;
+  if (na == 0 || q0 >= nitems) return;
+  const int K = A.K, Nr = A.Nr;
+  T* Rs = reinterpret_cast<T*>(smem_raw);                 // [Nr][K]
+  V* Xs = reinterpret_cast<V*>(smem_raw + (((size_t)Nr * K * sizeof(T) + 15) & ~size_t(15)));  // [K][RAD_Q]
+  const T* tab = A.rtab + (size_t)g * Nr * K;
+  for (int i = threadIdx.x; i < Nr * K; i += blockDim.x) Rs[i] = tab[i];
+  // gather the kept coefficients of each item (zero beyond Ka)
+  for (int i = threadIdx.x; i < RAD_Q * K; i += blockDim.x) {
+    const int q = i / K, k = i - q * K;
+    const long item = q0 + q;
+    V v = mk<T>(T(0), T(0));
+    if (item < nitems) {
+      const int c = (int)(item / na), a = gs + (int)(item - (long)c * na);
+      const int cg = A.c0 + c;
+      const int slot = cg / A.ns, s = cg - slot * A.ns;
+      const int kb = A.blk.kb[slot];
+      const int ka = A.Ka[(size_t)kb * A.nA + a];
+      if (k < ka) {
+        const double* x = A.blk.x[slot] + 2 * ((size_t)A.off[(size_t)kb * A.nA + a] + k + (size_t)s * A.ld);
+        v = mk<T>(T(x[0]), T(x[1]));
+      }
+    }
+    Xs[k * RAD_Q + q] = v;
+  }
+  __syncthreads();
+  const int q = threadIdx.x % RAD_Q;
+  const long item = q0 + q;
+  if (item >= nitems) return;
+  const int c = (int)(item / na), a = gs + (int)(item - (long)c * na);
+  V* out = A.gh + ((size_t)c * Nr) * A.nA + a;
+  for (int p = threadIdx.x / RAD_Q; p < Nr; p += RAD_THREADS / RAD_Q) {
+    T ax = 0, ay = 0;
+    const T* rr = Rs + p * K;
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+      const V xv = Xs[k * RAD_Q + q];
+      ax += rr[k] * xv.x;
+      ay += rr[k] * xv.y;
+    }
+    out[(size_t)p * A.nA] = mk<T>(ax, ay);
+  }
+}
+
+// forward radial quadrature + diagonal term + scatter
+template <typename T>
+__global__ void __launch_bounds__(RAD_THREADS) k_radial_fwd(RadArgs<T> A) {
+  using V = cplx_t<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int g = blockIdx.y;
+  const int gs = A.group_start[g], na = A.group_start[g + 1] - gs;
+  const long nitems = (long)na * A.ncols;
+  const long q0 = (long)blockIdx.x * RAD_Q;
+  if (na == 0 || q0 >= nitems) return;
+  const int K = A.K, Nr = A.Nr;
+  constexpr int PC = 32;                                   // radial nodes per chunk
+  T* Rs = reinterpret_cast<T*>(smem_raw);                  // [K][Nr]
+  size_t o = (((size_t)K * Nr * sizeof(T)) + 15) & ~size_t(15);
+  V* Hs = reinterpret_cast<V*>(smem_raw + o);              // [PC][RAD_Q]
+  o += (size_t)PC * RAD_Q * sizeof(V);
+  V* Ys = reinterpret_cast<V*>(smem_raw + o);              // [RAD_Q][K+1]
+  const T* tab = A.rtab + (size_t)g * K * Nr;
+  for (int i = threadIdx.x; i < K * Nr; i += blockDim.x) Rs[i] = tab[i];
+  const int q = threadIdx.x % RAD_Q;
+  const int kg = threadIdx.x / RAD_Q;                      // 4 groups of k
+  constexpr int KG = RAD_THREADS / RAD_Q;
+  const long item = q0 + q;
+  int c = 0, a = gs;
+  if (item < nitems) {
+    c = (int)(item / na);
+    a = gs + (int)(item - (long)c * na);
+  }
+  T acc[2 * 16];  // up to 16 k per thread: K <= 64
+#pragma unroll
+  for (int i = 0; i < 32; ++i) acc[i] = 0;
+  const int kper = (K + KG - 1) / KG;
+  for (int p0 = 0; p0 < Nr; p0 += PC) {
+    const int pc = min(PC, Nr - p0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < pc * RAD_Q; i += blockDim.x) {
+      const int pp = i / RAD_Q, qq = i - pp * RAD_Q;
+      const long it = q0 + qq;
+      V v = mk<T>(T(0), T(0));
+      if (it < nitems) {
+        const int cc = (int)(it / na), aa = gs + (int)(it - (long)cc * na);
+        v = A.gh[((size_t)cc * Nr + p0 + pp) * A.nA + aa];
+      }
+      Hs[pp * RAD_Q + qq] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int k = kg + j * KG;
+      if (j < kper && k < K) {
+        T ax = acc[2 * j], ay = acc[2 * j + 1];
+        const T* rr = Rs + (size_t)k * Nr + p0;
+        for (int pp = 0; pp < pc; ++pp) {
+          const V hv = Hs[pp * RAD_Q + q];
+          ax += rr[pp] * hv.x;
+          ay += rr[pp] * hv.y;
+        }
+        acc[2 * j] = ax;
+        acc[2 * j + 1] = ay;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int k = kg + j * KG;
+    if (j < kper && k < K) Ys[q * (K + 1) + k] = mk<T>(acc[2 * j], acc[2 * j + 1]);
+  }
+  __syncthreads();
+  // scatter: one warp per item, lanes over k (contiguous in the compact order)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int qq = warp; qq < RAD_Q; qq += RAD_THREADS / 32) {
+    const long it = q0 + qq;
+    if (it >= nitems) break;
+    const int cc = (int)(it / na), aa = gs + (int)(it - (long)cc * na);
+    const int cg = A.c0 + cc;
+    const int slot = cg / A.ns, s = cg - slot * A.ns;
+    const int kb = A.blk.kb[slot];
+    const int ka = A.Ka[(size_t)kb * A.nA + aa];
+    const size_t o0 = (size_t)A.off[(size_t)kb * A.nA + aa];
+    const double* x = A.blk.x[slot] + 2 * (o0 + (size_t)s * A.ld);
+    double* y = A.blk.y[slot] + 2 * (o0 + (size_t)s * A.ld);
+    const double* ke = A.ke + A.keoff[slot] + o0;
+    for (int k = lane; k < ka; k += 32) {
+      const V h = Ys[qq * (K + 1) + k];
+      const double d = ke[k];
+      y[2 * k] = d * x[2 * k] + double(h.x);
+      y[2 * k + 1] = d * x[2 * k + 1] + double(h.y);
+    }
+  }
+}
+
+// --------------------------------------------------------------------------- slab
+template <typename T>
+struct SlabArgs {
+  int Nr, Nth1, Nth2, nA, nmr, ncols, Jc;
+  FftDev p1, p2;
+  const int* pair_n;
+  const int* pair_mrow;
+  const int* mrow_m;
+  const T* V;        // [Nr][Nth2][Nth1]
+  const cplx_t<T>* tw1;
+  const cplx_t<T>* tw2;
+  const cplx_t<T>* G;
+  cplx_t<T>* H;
+};
+
+constexpr int SLAB_THREADS = 256;
+
+// grid: x = column, y = radial node
+template <typename T>
+__global__ void __launch_bounds__(SLAB_THREADS) k_slab(SlabArgs<T> A) {
+  using V = cplx_t<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int c = blockIdx.x, p = blockIdx.y;
+  const int n1 = A.Nth1, n2 = A.Nth2, nmr = A.nmr;
+  const int wsz = max(nmr * n2, A.Jc * n1);
+  V* Tb = reinterpret_cast<V*>(smem_raw);     // [nmr][n2]
+  V* W0 = Tb + nmr * n2;
+  V* W1 = W0 + wsz;
+  const V zero = mk<T>(T(0), T(0));
+  const V* Gc = A.G + ((size_t)c * A.Nr + p) * A.nA;
+  V* Hc = A.H + ((size_t)c * A.Nr + p) * A.nA;
+  // theta2 inverse pass over the kept m rows
+  for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) W0[i] = zero;
+  __syncthreads();
+  for (int a = threadIdx.x; a < A.nA; a += blockDim.x)
+    W0[A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2)] = Gc[a];
+  __syncthreads();
+  V* r = fft_batch<T>(W0, W1, A.p2, nmr, A.tw2, +1);
+  for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) Tb[i] = r[i];
+  __syncthreads();
+  // theta1 pass per theta2 column chunk: insert rows, inverse FFT, x V, forward FFT, extract
+  const T* Vp = A.V + (size_t)p * n2 * n1;
+  for (int j0 = 0; j0 < n2; j0 += A.Jc) {
+    const int jn = min(A.Jc, n2 - j0);
+    for (int i = threadIdx.x; i < jn * n1; i += blockDim.x) W0[i] = zero;
+    __syncthreads();
+    for (int i = threadIdx.x; i < jn * nmr; i += blockDim.x) {
+      const int jj = i / nmr, rr = i - jj * nmr;
+      W0[jj * n1 + pmod(A.mrow_m[rr], n1)] = Tb[rr * n2 + j0 + jj];
+    }
+    __syncthreads();
+    V* u = fft_batch<T>(W0, W1, A.p1, jn, A.tw1, +1);
+    for (int i = threadIdx.x; i < jn * n1; i += blockDim.x) {
+      const T v = Vp[(size_t)j0 * n1 + i];
+      u[i].x *= v;
+      u[i].y *= v;
+    }
+    __syncthreads();
+    V* w = fft_batch<T>(u, u == W0 ? W1 : W0, A.p1, jn, A.tw1, -1);
+    for (int i = threadIdx.x; i < jn * nmr; i += blockDim.x) {
+      const int jj = i / nmr, rr = i - jj * nmr;
+      Tb[rr * n2 + j0 + jj] = w[jj * n1 + pmod(A.mrow_m[rr], n1)];
+    }
+    __syncthreads();
+  }
+  // theta2 forward pass, extract the kept pairs
+  for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) W0[i] = Tb[i];
+  __syncthreads();
+  r = fft_batch<T>(W0, W1, A.p2, nmr, A.tw2, -1);
+  for (int a = threadIdx.x; a < A.nA; a += blockDim.x)
+    Hc[a] = r[A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2)];
+}
+
+// --------------------------------------------------------------------------- host launcher
+static FftDev to_dev(const FftPlan& p) {
+  FftDev d;
+  d.n = p.n;
+  d.nst = p.nst;
+  for (int i = 0; i < 16; ++i) d.rad[i] = p.rad[i];
+  return d;
+}
+
+size_t slab_smem_bytes(const hw_ctx* ctx, size_t elem, int Jc) {
+  const auto& hb = ctx->hb;
+  const int nmr = (int)hb.mrow_m.size();
+  const size_t wsz = std::max((size_t)nmr * hb.prm.Nth2, (size_t)Jc * hb.prm.Nth1);
+  return elem * ((size_t)nmr * hb.prm.Nth2 + 2 * wsz);
+}
+
+int slab_pick_jc(const hw_ctx* ctx, size_t elem) {
+  // largest theta2 chunk whose shared memory fits in ~110 KB (two CTAs per SM)
+  int Jc = ctx->hb.prm.Nth2;
+  while (Jc > 1 && slab_smem_bytes(ctx, elem, Jc) > 110 * 1024) Jc = (Jc + 1) / 2;
+  return Jc;
+}
+
+// Launch the three kernels for the column blocks `blk` (ns columns each).  Columns are
+// processed in passes of at most ctx->ws.cols columns.
+template <typename T>
+cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld) {
+  auto& hb = ctx->hb;
+  auto& db = ctx->db;
+  const DevTables<T>& tb = *reinterpret_cast<const DevTables<T>*>(
+      sizeof(T) == 8 ? (const void*)&db.t64 : (const void*)&db.t32);
+  const int ncols_total = blk.nslot * ns;
+  const int chunk = (int)ctx->ws.cols;
+  if (chunk <= 0 || blk.nslot > MAXSLOT) return cudaErrorInvalidValue;
+  const int Nr = hb.prm.Nr, K = hb.K;
+  int maxna = 0;
+  for (int g = 0; g <= hb.N; ++g) maxna = std::max(maxna, hb.group_start[g + 1] - hb.group_start[g]);
+  const int Jc = slab_pick_jc(ctx, sizeof(cplx_t<T>));
+  for (int c0 = 0; c0 < ncols_total; c0 += chunk) {
+    const int nc = std::min(chunk, ncols_total - c0);
+    RadArgs<T> ra;
+    ra.Nr = Nr;
+    ra.K = K;
+    ra.nA = hb.nA;
+    ra.ncols = nc;
+    ra.ns = ns;
+    ra.c0 = c0;
+    ra.group_start = db.group_start;
+    ra.off = db.off;
+    ra.Ka = db.Ka;
+    ra.ld = ld;
+    ra.ke = db.ke;
+    for (int i = 0; i < blk.nslot; ++i) ra.keoff[i] = db.ke_off[blk.kb[i]];
+    ra.blk = blk;
+    ra.gh = reinterpret_cast<cplx_t<T>*>(ctx->ws.gbuf);
+    ra.rtab = tb.rinv;
+    dim3 grid((unsigned)(((long)maxna * nc + RAD_Q - 1) / RAD_Q), hb.N + 1);
+    const size_t sm_inv = ((size_t(Nr) * K * sizeof(T) + 15) & ~size_t(15)) +
+                          (size_t)K * RAD_Q * sizeof(cplx_t<T>);
+    k_radial_inv<T><<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra);
+    SlabArgs<T> sa;
+    sa.Nr = Nr;
+    sa.Nth1 = hb.prm.Nth1;
+    sa.Nth2 = hb.prm.Nth2;
+    sa.nA = hb.nA;
+    sa.nmr = (int)hb.mrow_m.size();
+    sa.ncols = nc;
+    sa.Jc = Jc;
+    sa.p1 = to_dev(ctx->plan1);
+    sa.p2 = to_dev(ctx->plan2);
+    sa.pair_n = db.pair_n;
+    sa.pair_mrow = db.pair_mrow;
+    sa.mrow_m = db.mrow_m;
+    sa.V = tb.V;
+    sa.tw1 = reinterpret_cast<const cplx_t<T>*>(tb.tw1);
+    sa.tw2 = reinterpret_cast<const cplx_t<T>*>(tb.tw2);
+    sa.G = reinterpret_cast<const cplx_t<T>*>(ctx->ws.gbuf);
+    sa.H = reinterpret_cast<cplx_t<T>*>(ctx->ws.hbuf);
+    const size_t sm_slab = slab_smem_bytes(ctx, sizeof(cplx_t<T>), Jc);
+    k_slab<T><<<dim3(nc, Nr), SLAB_THREADS, sm_slab, ctx->stream>>>(sa);
+    ra.gh = reinterpret_cast<cplx_t<T>*>(ctx->ws.hbuf);
+    ra.rtab = tb.rfwd;
+    const size_t sm_fwd = ((size_t(K) * Nr * sizeof(T) + 15) & ~size_t(15)) +
+                          32 * RAD_Q * sizeof(cplx_t<T>) + (size_t)RAD_Q * (K + 1) * sizeof(cplx_t<T>);
+    k_radial_fwd<T><<<grid, RAD_THREADS, sm_fwd, ctx->stream>>>(ra);
+  }
+  return cudaGetLastError();
+}
+
+// opt in to large dynamic shared memory for every instantiation (called once at setup)
+cudaError_t hx_configure(hw_ctx* ctx) {
+  cudaError_t e = cudaSuccess;
+  const int big = 200 * 1024;
+  e = cudaFuncSetAttribute(k_radial_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radial_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radial_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radial_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slab<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slab<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  (void)ctx;
+  return e;
+}
+
+template cudaError_t launch_hx<double>(hw_ctx*, const Blocks&, int, int64_t);
+template cudaError_t launch_hx<float>(hw_ctx*, const Blocks&, int, int64_t);
+
+}  // namespace hw

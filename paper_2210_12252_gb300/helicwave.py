@@ -1,0 +1,326 @@
+"""Thin Python binding of the C ABI in include/helicwave.h (argument marshalling only).
+
+The module-level functions carry the C names (hw_create, hw_setup_basis, hw_apply_H, ...) and
+take plain integers / pointers; `Context` wraps them for torch tensors.  Every computation runs
+in libhelicwave.so; importing this module fails loudly when that library has not been built.
+
+Block layout: a column-major complex128 block L x ns with leading dimension ld is a contiguous
+torch tensor of shape (ns, ld) and dtype complex128 (row j holds column j).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhelicwave.so")
+
+HW_OK, HW_EINVAL, HW_ENOMEM, HW_ECUDA, HW_ESTATE, HW_ENOTCONV, HW_ETIMEOUT = range(7)
+HW_FP64, HW_MIXED = 0, 1
+HW_PRECOND_TPA, HW_PRECOND_LEARNED, HW_PRECOND_NONE = 0, 1, 2
+STATUS_NAMES = ["HW_OK", "HW_EINVAL", "HW_ENOMEM", "HW_ECUDA", "HW_ESTATE", "HW_ENOTCONV",
+                "HW_ETIMEOUT"]
+
+
+class HwError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+class hw_basis_params(C.Structure):
+    _fields_ = [("R", C.c_double), ("tau", C.c_double), ("alpha", C.c_double),
+                ("ncyc", C.c_int), ("ecut", C.c_double), ("Nr", C.c_int), ("Nth1", C.c_int),
+                ("Nth2", C.c_int), ("oversample", C.c_int)]
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_SIGS = {
+    "hw_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
+    "hw_destroy": (None, [C.c_void_p]),
+    "hw_last_error": (C.c_char_p, [C.c_void_p]),
+    "hw_setup_basis": (C.c_int, [C.c_void_p, C.POINTER(hw_basis_params), C.c_int, _D, _D, _D,
+                                 C.POINTER(C.c_int64)]),
+    "hw_get_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                               C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
+    "hw_get_grid": (C.c_int, [C.c_void_p, _D, _D]),
+    "hw_get_index_map": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int32)]),
+    "hw_get_kinetic": (C.c_int, [C.c_void_p, C.c_int, _D]),
+    "hw_get_radial_table": (C.c_int, [C.c_void_p, C.c_int, _D]),
+    "hw_set_potential": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "hw_build_potential": (C.c_int, [C.c_void_p, C.c_int, _D, _D]),
+    "hw_apply_H": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int64,
+                             C.c_int]),
+    "hw_apply_H_batched": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int),
+                                     C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
+                                     C.c_int64, C.c_int]),
+    "hw_apply_precond": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                   C.c_int64, C.c_void_p, C.c_int]),
+    "hw_solve_eigs": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int,
+                                C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p),
+                                _D, C.POINTER(C.c_void_p), C.c_int64, C.POINTER(C.c_int), _D]),
+    "hw_synchronize": (C.c_int, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libhelicwave.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2210_12252_gb300.build`")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_D) if a is not None else None
+
+
+# ----------------------------------------------------------------- C-named thin wrappers
+
+def hw_create(device: int = 0, stream: int = 0):
+    lib = load_library()
+    h = C.c_void_p()
+    st = lib.hw_create(C.byref(h), device, C.c_void_p(stream or None))
+    if st != HW_OK:
+        raise HwError(st, "hw_create failed")
+    return h
+
+
+def hw_destroy(h):
+    load_library().hw_destroy(h)
+
+
+def hw_last_error(h) -> str:
+    return load_library().hw_last_error(h).decode()
+
+
+def _check(h, st):
+    if st != HW_OK:
+        raise HwError(st, hw_last_error(h))
+
+
+def hw_setup_basis(h, params: hw_basis_params, eta, nu=None, ecut_per_k=None):
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    nk = eta.size
+    nu = None if nu is None else np.ascontiguousarray(nu, dtype=np.float64)
+    ec = None if ecut_per_k is None else np.ascontiguousarray(ecut_per_k, dtype=np.float64)
+    L = np.zeros(nk, dtype=np.int64)
+    _check(h, load_library().hw_setup_basis(h, C.byref(params), nk, _dptr(eta), _dptr(nu),
+                                            _dptr(ec), L.ctypes.data_as(C.POINTER(C.c_int64))))
+    return L
+
+
+def hw_get_sizes(h):
+    M, N, K, nA = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    G = C.c_int64()
+    _check(h, load_library().hw_get_sizes(h, C.byref(M), C.byref(N), C.byref(K), C.byref(G),
+                                          C.byref(nA)))
+    return dict(M=M.value, N=N.value, K=K.value, grid_points=G.value, n_pairs=nA.value)
+
+
+def hw_get_grid(h, Nr):
+    r = np.zeros(Nr)
+    w = np.zeros(Nr)
+    _check(h, load_library().hw_get_grid(h, _dptr(r), _dptr(w)))
+    return r, w
+
+
+def hw_get_index_map(h, k, L):
+    out = np.zeros(3 * L, dtype=np.int32)
+    _check(h, load_library().hw_get_index_map(h, k, out.ctypes.data_as(C.POINTER(C.c_int32))))
+    return out.reshape(L, 3)
+
+
+def hw_get_kinetic(h, k, L):
+    out = np.zeros(L)
+    _check(h, load_library().hw_get_kinetic(h, k, _dptr(out)))
+    return out
+
+
+def hw_get_radial_table(h, n, Nr, K):
+    out = np.zeros(Nr * K)
+    _check(h, load_library().hw_get_radial_table(h, n, _dptr(out)))
+    return out.reshape(Nr, K)
+
+
+def hw_set_potential(h, V_ptr: int, on_device: bool):
+    _check(h, load_library().hw_set_potential(h, C.c_void_p(V_ptr), int(bool(on_device))))
+
+
+def hw_build_potential(h, atoms, grid_points):
+    atoms = np.ascontiguousarray(np.asarray(atoms, dtype=np.float64).reshape(-1, 5))
+    V = np.zeros(grid_points)
+    _check(h, load_library().hw_build_potential(h, atoms.shape[0], _dptr(atoms), _dptr(V)))
+    return V
+
+
+def hw_apply_H(h, k, X_ptr, Y_ptr, ns, ld, prec=HW_FP64):
+    _check(h, load_library().hw_apply_H(h, k, C.c_void_p(X_ptr), C.c_void_p(Y_ptr), ns, ld, prec))
+
+
+def hw_apply_H_batched(h, kidx, X_ptrs, Y_ptrs, ns, ld, prec=HW_FP64):
+    nk = len(kidx)
+    ki = (C.c_int * nk)(*kidx)
+    xs = (C.c_void_p * nk)(*X_ptrs)
+    ys = (C.c_void_p * nk)(*Y_ptrs)
+    _check(h, load_library().hw_apply_H_batched(h, nk, ki, xs, ys, ns, ld, prec))
+
+
+def hw_apply_precond(h, k, R_ptr, Z_ptr, ns, ld, ritz_ptr=0, kind=HW_PRECOND_TPA):
+    _check(h, load_library().hw_apply_precond(h, k, C.c_void_p(R_ptr), C.c_void_p(Z_ptr), ns, ld,
+                                              C.c_void_p(ritz_ptr or None), kind))
+
+
+def hw_solve_eigs(h, kidx, n_eig, block=0, tol=1e-6, maxit=500, prec=HW_FP64,
+                  precond=HW_PRECOND_TPA, X0_ptrs=None, evec_ptrs=None, ld_evecs=0):
+    nk = len(kidx)
+    ki = (C.c_int * nk)(*kidx)
+    x0 = (C.c_void_p * nk)(*X0_ptrs) if X0_ptrs is not None else None
+    ev = (C.c_void_p * nk)(*evec_ptrs) if evec_ptrs is not None else None
+    evals = np.zeros(nk * n_eig)
+    resid = np.zeros(nk * n_eig)
+    iters = (C.c_int * nk)()
+    st = load_library().hw_solve_eigs(h, nk, ki, n_eig, block, tol, maxit, prec, precond, x0,
+                                      _dptr(evals), ev, ld_evecs, iters, _dptr(resid))
+    if st not in (HW_OK, HW_ENOTCONV):
+        _check(h, st)
+    return (evals.reshape(nk, n_eig), np.array(list(iters)), resid.reshape(nk, n_eig),
+            st == HW_OK)
+
+
+def hw_synchronize(h):
+    _check(h, load_library().hw_synchronize(h))
+
+
+# ----------------------------------------------------------------------------- Context
+
+_PREC = {"fp64": HW_FP64, "mixed": HW_MIXED}
+_PRECOND = {"tpa": HW_PRECOND_TPA, "learned": HW_PRECOND_LEARNED, "none": HW_PRECOND_NONE}
+
+
+class Context:
+    """One library context on one device (device=-1: host-only, setup queries only)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.device = device
+        if device >= 0:
+            import torch
+            if stream is None:
+                stream = torch.cuda.current_stream(device)
+            self.stream = stream
+            sp = stream.cuda_stream
+        else:
+            self.stream = None
+            sp = 0
+        self.h = hw_create(device, sp)
+        self.L = None
+
+    def close(self):
+        if self.h is not None:
+            hw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- setup
+    def setup_basis(self, geom, etas, nus=None, ecuts=None):
+        self.geom = geom
+        p = hw_basis_params(geom.R, geom.tau, geom.alpha, geom.ncyc, geom.ecut, geom.Nr,
+                            geom.Nth1, geom.Nth2, geom.oversample)
+        self.L = hw_setup_basis(self.h, p, etas, nus, ecuts)
+        self.sizes = hw_get_sizes(self.h)
+        return self.L
+
+    def grid(self):
+        return hw_get_grid(self.h, self.geom.Nr)
+
+    def index_map(self, k):
+        return hw_get_index_map(self.h, k, int(self.L[k]))
+
+    def kinetic(self, k):
+        return hw_get_kinetic(self.h, k, int(self.L[k]))
+
+    def radial_table(self, n):
+        return hw_get_radial_table(self.h, n, self.geom.Nr, self.sizes["K"])
+
+    def build_potential(self, atoms):
+        return hw_build_potential(self.h, atoms, self.sizes["grid_points"])
+
+    def set_potential(self, V):
+        import torch
+        if isinstance(V, torch.Tensor) and V.is_cuda:
+            V = V.contiguous().to(torch.float64)
+            hw_set_potential(self.h, V.data_ptr(), True)
+            self._vkeep = V
+        else:
+            V = np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(-1))
+            hw_set_potential(self.h, V.ctypes.data, False)
+
+    # -- compute
+    @staticmethod
+    def _blk(X):
+        assert X.dtype.is_complex and X.element_size() == 16 and X.is_contiguous()
+        return X.shape[0], X.shape[1]
+
+    def apply_H(self, k, X, Y=None, prec="fp64"):
+        import torch
+        ns, ld = self._blk(X)
+        if Y is None:
+            Y = torch.zeros_like(X)
+        hw_apply_H(self.h, k, X.data_ptr(), Y.data_ptr(), ns, ld, _PREC[prec])
+        return Y
+
+    def apply_H_batched(self, kidx, Xs, Ys, prec="fp64"):
+        ns, ld = self._blk(Xs[0])
+        hw_apply_H_batched(self.h, list(kidx), [x.data_ptr() for x in Xs],
+                           [y.data_ptr() for y in Ys], ns, ld, _PREC[prec])
+        return Ys
+
+    def apply_precond(self, k, R, Z=None, ritz=None, kind="tpa"):
+        import torch
+        ns, ld = self._blk(R)
+        if Z is None:
+            Z = torch.empty_like(R)
+        hw_apply_precond(self.h, k, R.data_ptr(), Z.data_ptr(), ns, ld,
+                         ritz.data_ptr() if ritz is not None else 0, _PRECOND[kind])
+        return Z
+
+    def solve_eigs(self, kidx, n_eig, block=0, tol=1e-6, maxit=500, prec="fp64",
+                   precond="tpa", X0=None, vectors=False):
+        import torch
+        evecs = None
+        ptrs = None
+        if vectors:
+            Lmax = int(max(self.L[k] for k in kidx))
+            evecs = [torch.zeros((n_eig, Lmax), dtype=torch.complex128, device=f"cuda:{self.device}")
+                     for _ in kidx]
+            ptrs = [e.data_ptr() for e in evecs]
+        x0p = [x.data_ptr() for x in X0] if X0 is not None else None
+        ev, it, res, ok = hw_solve_eigs(self.h, list(kidx), n_eig, block, tol, maxit, _PREC[prec],
+                                        _PRECOND[precond], x0p, ptrs,
+                                        evecs[0].shape[1] if vectors else 0)
+        return dict(evals=ev, iters=it, resid=res, converged=ok, evecs=evecs)
+
+    def synchronize(self):
+        hw_synchronize(self.h)

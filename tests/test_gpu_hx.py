@@ -1,0 +1,150 @@
+"""GPU parity of H X and the TPA preconditioner (through the C ABI) against the CPU oracle.
+
+Tolerances: the FP64 path must match Algorithm 5 of the oracle to 1e-10 relative (per column,
+in the 2-norm); the mixed path (FP32 transforms, FP64 diagonal) to 2e-6 relative, the FP32
+rounding of O(100) accumulated terms.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import basis as B
+from oracle import eigensolver as E
+from oracle import hamiltonian as Hm
+from oracle import potential as P
+from paper_2210_12252_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_TOL = 2e-6
+
+
+@pytest.fixture(scope="module")
+def hwmod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_12252_gb300 import build
+    build.build()
+    from paper_2210_12252_gb300 import helicwave
+    return helicwave
+
+
+def oracle_basis(g):
+    return B.Basis(g.R, g.tau, g.alpha, g.Nr, g.Nth1, g.Nth2, g.ncyc, g.oversample)
+
+
+def to_dev(X, ld=None):
+    """column-major L x ns numpy block -> (ns, ld) complex128 CUDA tensor"""
+    L, ns = X.shape
+    ld = ld or L
+    T = torch.zeros((ns, ld), dtype=torch.complex128)
+    T[:, :L] = torch.from_numpy(np.ascontiguousarray(X.T))
+    return T.cuda()
+
+
+def from_dev(T, L):
+    return T[:, :L].cpu().numpy().T
+
+
+def rel_err(Y, Yref):
+    return (np.linalg.norm(Y - Yref, axis=0) / np.linalg.norm(Yref, axis=0)).max()
+
+
+class Case:
+    def __init__(self, hwmod, w, etas=None, ecuts=None):
+        self.w = w
+        self.etas = np.asarray(w.etas if etas is None else etas, dtype=float)
+        self.ecuts = ecuts
+        self.ctx = hwmod.Context(0)
+        self.L = self.ctx.setup_basis(w.geom, self.etas, None, ecuts)
+        self.ctx.build_potential(w.atoms)
+        self.b = oracle_basis(w.geom)
+        self.V = P.gaussian_wells(self.b, w.atoms)
+        self.kps = [B.KPoint(self.b, e, 0.0, w.geom.ecut if ecuts is None else ecuts[i])
+                    for i, e in enumerate(self.etas)]
+
+
+@pytest.fixture(scope="module")
+def tiny(hwmod):
+    return Case(hwmod, inputs.tiny())
+
+
+@pytest.fixture(scope="module")
+def tube(hwmod):
+    return Case(hwmod, inputs.tube())
+
+
+@pytest.mark.parametrize("ns", [1, 5, 16])
+def test_apply_H_fp64_tiny(tiny, ns):
+    kp = tiny.kps[0]
+    X = inputs.random_block(kp.L, ns, 100 + ns)
+    Yref = Hm.apply_H(kp, tiny.V, X)
+    Y = from_dev(tiny.ctx.apply_H(0, to_dev(X)), kp.L)
+    assert rel_err(Y, Yref) < FP64_TOL
+
+
+def test_apply_H_fp64_tube_ragged_with_padding(tube):
+    kp = tube.kps[0]
+    assert tube.L[0] == kp.L
+    X = inputs.random_block(kp.L, 3, 7)
+    Xd = to_dev(X, ld=kp.L + 13)
+    Yd = torch.full_like(Xd, complex(7.0, -3.0))
+    tube.ctx.apply_H(0, Xd, Yd)
+    Y = from_dev(Yd, kp.L)
+    Yref = Hm.apply_H(kp, tube.V, X)
+    assert rel_err(Y, Yref) < FP64_TOL
+    # padding rows untouched
+    assert torch.all(Yd[:, kp.L:] == complex(7.0, -3.0))
+
+
+def test_apply_H_mixed_tube(tube):
+    kp = tube.kps[0]
+    X = inputs.random_block(kp.L, 4, 8)
+    Yref = Hm.apply_H(kp, tube.V, X)
+    Y = from_dev(tube.ctx.apply_H(0, to_dev(X), prec="mixed"), kp.L)
+    e = rel_err(Y, Yref)
+    assert e < MIXED_TOL and e > 1e-12   # really ran in reduced precision
+
+
+def test_apply_H_is_hermitian_on_device(tiny):
+    kp = tiny.kps[0]
+    X = inputs.random_block(kp.L, 6, 21)
+    Y = from_dev(tiny.ctx.apply_H(0, to_dev(X)), kp.L)
+    G = X.conj().T @ Y
+    assert np.abs(G - G.conj().T).max() < 1e-12 * np.abs(G).max()
+
+
+def test_apply_H_batched_uneven_kpoints(hwmod):
+    w = inputs.tube_kpoints(nk=4, uneven=True)
+    case = Case(hwmod, w, ecuts=w.ecuts)
+    ns = 3
+    Lmax = int(max(case.L))
+    Xs, Ys, refs = [], [], []
+    for b, kp in enumerate(case.kps):
+        X = inputs.random_block(kp.L, ns, 300 + b)
+        Xs.append(to_dev(X, ld=Lmax))
+        Ys.append(torch.zeros_like(Xs[-1]))
+        refs.append(Hm.apply_H(kp, case.V, X))
+    case.ctx.apply_H_batched(list(range(len(case.kps))), Xs, Ys)
+    for b, kp in enumerate(case.kps):
+        assert rel_err(from_dev(Ys[b], kp.L), refs[b]) < FP64_TOL
+
+
+def test_tpa_preconditioner_matches_oracle(tube):
+    kp = tube.kps[0]
+    R = inputs.random_block(kp.L, 5, 9) * np.exp(-0.01 * np.arange(kp.L))[:, None]
+    Z = from_dev(tube.ctx.apply_precond(0, to_dev(R)), kp.L)
+    Zref = E.tpa(kp.ke, R)
+    assert rel_err(Z, Zref) < 1e-13
+
+
+def test_set_potential_from_device_matches_host_build(tube):
+    kp = tube.kps[0]
+    V = torch.from_numpy(tube.V.ravel().copy()).cuda()
+    tube.ctx.set_potential(V)       # oracle-built V from device memory
+    X = inputs.random_block(kp.L, 2, 5)
+    Y = from_dev(tube.ctx.apply_H(0, to_dev(X)), kp.L)
+    assert rel_err(Y, Hm.apply_H(kp, tube.V, X)) < FP64_TOL
+    tube.ctx.build_potential(tube.w.atoms)   # restore the library-built V
