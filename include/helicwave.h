@@ -118,9 +118,10 @@ hw_status hw_set_potential(hw_ctx* ctx, const double* V, int on_device);
 /* Build and install the Gaussian-well potential
  *   V(x) = sum_a sum_{zeta,mu} -Z_a exp(-|x - Upsilon_{zeta,mu} x_a|^2 / (2 sigma_a^2))
  * summed over the images of the helical group (eq. symm_opera) with |z - z_image| <= 10 sigma.
- * atoms: host array [n_atoms][5] of (r, vartheta, z, Z, sigma).  Runs on the device and
- * returns when V is installed.  V_out (host, nullable) receives V in eq. wavefun_storage_real
- * order. */
+ * atoms: host array [n_atoms][5] of (r, vartheta, z, Z, sigma).  Evaluated once per potential
+ * in FP64 on the host's cores (std::thread), then installed as by hw_set_potential; returns when
+ * V is installed (host-only contexts only evaluate it).  V_out (host, nullable) receives V in
+ * eq. wavefun_storage_real order. */
 hw_status hw_build_potential(hw_ctx* ctx, int n_atoms, const double* atoms, double* V_out);
 
 /* Y = H X at k-point k (Algorithm 5): reciprocal-space diagonal terms, inverse transform
@@ -158,6 +159,33 @@ hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx, int n_eig, int blo
 
 /* Wait for all work on the context's stream. */
 hw_status hw_synchronize(hw_ctx* ctx);
+
+/* Phases timed by the profiler (CUDA events recorded on the context's stream around each
+ * launch of the phase; device time, not host time). */
+typedef enum {
+  HW_PH_RADIAL_INV = 0,   /* gather + inverse radial transform (Algorithm 1, first loop)   */
+  HW_PH_SLAB = 1,         /* angular FFTs with the potential multiply (Algorithms 2, 4)     */
+  HW_PH_RADIAL_FWD = 2,   /* forward radial quadrature + diagonal + scatter (Algorithm 3)   */
+  HW_PH_PRECOND = 3,      /* diagonal preconditioner                                        */
+  HW_PH_GEMM = 4,         /* tall-skinny FP64 products of the eigensolver (cuBLAS ZGEMM)    */
+  HW_PH_CHOL = 5,         /* Cholesky factorisations + triangular inverses                  */
+  HW_PH_EIG = 6,          /* dense Hermitian eigensolver of the Rayleigh-Ritz step          */
+  HW_PH_OTHER = 7,        /* residuals, gathers, padding                                     */
+  HW_PH_MLP = 8,          /* preconditioner network (inference and training)                 */
+  HW_NPHASE = 9
+} hw_phase;
+
+/* Turn per-phase profiling on (enable != 0) or off; either resets the accumulators.  While on,
+ * every phase launch is bracketed by CUDA events (small overhead). */
+hw_status hw_profile(hw_ctx* ctx, int enable);
+
+/* Synchronize the stream and read the accumulated device milliseconds and launch counts per
+ * phase (host arrays of HW_NPHASE entries; either may be NULL). */
+hw_status hw_profile_read(hw_ctx* ctx, double* ms, int64_t* count);
+
+/* Number of this library's own kernels launched on the context's stream since creation
+ * (cuBLAS kernels are not counted). */
+int64_t hw_launch_count(const hw_ctx* ctx);
 
 #ifdef __cplusplus
 }

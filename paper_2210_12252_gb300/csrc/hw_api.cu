@@ -415,3 +415,84 @@ hw_status hw_synchronize(hw_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------ profiling
+namespace hw {
+
+ProfScope::ProfScope(hw_ctx* ctx, int ph) : ctx_(ctx), ph_(ph) {
+  if (!ctx_ || !ctx_->prof.on) return;
+  auto& p = ctx_->prof;
+  if (p.pool.empty()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    p.pool.push_back(e);
+  }
+  a_ = p.pool.back();
+  p.pool.pop_back();
+  cudaEventRecord(a_, ctx_->stream);
+}
+
+ProfScope::~ProfScope() {
+  if (!a_) return;
+  auto& p = ctx_->prof;
+  cudaEvent_t b;
+  if (p.pool.empty()) {
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      p.pool.push_back(a_);
+      return;
+    }
+  } else {
+    b = p.pool.back();
+    p.pool.pop_back();
+  }
+  cudaEventRecord(b, ctx_->stream);
+  p.pending.push_back({ph_, a_, b});
+}
+
+static void prof_collect(hw_ctx* ctx) {
+  auto& p = ctx->prof;
+  for (auto& r : p.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      p.ms[r.ph] += ms;
+      p.cnt[r.ph] += 1;
+    }
+    p.pool.push_back(r.a);
+    p.pool.push_back(r.b);
+  }
+  p.pending.clear();
+}
+
+}  // namespace hw
+
+extern "C" {
+
+hw_status hw_profile(hw_ctx* ctx, int enable) {
+  if (!ctx) return HW_EINVAL;
+  if (ctx->device < 0) return hw_fail(ctx, HW_ESTATE, "host-only context has no device");
+  cudaStreamSynchronize(ctx->stream);
+  hw::prof_collect(ctx);
+  for (int i = 0; i < HW_NPHASE; ++i) {
+    ctx->prof.ms[i] = 0.0;
+    ctx->prof.cnt[i] = 0;
+  }
+  ctx->prof.on = enable != 0;
+  return HW_OK;
+}
+
+hw_status hw_profile_read(hw_ctx* ctx, double* ms, int64_t* count) {
+  if (!ctx) return HW_EINVAL;
+  if (ctx->device < 0) return hw_fail(ctx, HW_ESTATE, "host-only context has no device");
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, cudaGetErrorString(e));
+  hw::prof_collect(ctx);
+  for (int i = 0; i < HW_NPHASE; ++i) {
+    if (ms) ms[i] = ctx->prof.ms[i];
+    if (count) count[i] = ctx->prof.cnt[i];
+  }
+  return HW_OK;
+}
+
+int64_t hw_launch_count(const hw_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "hw_internal.h"
 
@@ -53,6 +54,19 @@ struct Blocks {
 struct LobpcgWork;
 struct MlpState;
 
+// Per-phase timing with CUDA events on the context's stream (enabled by hw_profile).
+struct Prof {
+  bool on = false;
+  struct Rec {
+    int ph;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Rec> pending;
+  double ms[HW_NPHASE] = {0};
+  int64_t cnt[HW_NPHASE] = {0};
+};
+
 }  // namespace hw
 
 struct hw_ctx {
@@ -69,10 +83,25 @@ struct hw_ctx {
   hw::LobpcgWork* lw = nullptr;
   hw::MlpState* mlp = nullptr;
   int* dflag = nullptr;        // device status word for bounded waits
+  int64_t launches = 0;        // kernels of this library launched on the stream
+  hw::Prof prof;
 };
 
 // set the context's error message and return the status
 hw_status hw_fail(hw_ctx* ctx, hw_status st, const std::string& msg);
+
+namespace hw {
+// Records [start, end) events of one phase on the context's stream when profiling is on.
+class ProfScope {
+ public:
+  ProfScope(hw_ctx* ctx, int ph);
+  ~ProfScope();
+ private:
+  hw_ctx* ctx_;
+  int ph_;
+  cudaEvent_t a_ = nullptr;
+};
+}  // namespace hw
 
 namespace hw {
 template <typename T>

@@ -1,0 +1,466 @@
+// Small dense FP64 linear algebra for the block eigensolver, batched over k-points:
+//
+//   k_chol        in-place Cholesky G = L L^H of a Hermitian positive definite n x n matrix
+//                 (Cholesky-QR of the search directions); one CTA per problem, the matrix
+//                 staged in shared memory.  A non-positive pivot sets the problem's fail flag.
+//   k_trinv       L^{-1} of a lower-triangular matrix, written as the upper-triangular U^{-1}
+//                 with U = L^H, so that W U^{-1} is a plain GEMM.
+//   k_jacobi      all eigenpairs of nprob Hermitian n x n matrices by the parallel cyclic
+//                 two-sided Jacobi method (round-robin pairing, n/2 disjoint rotations per
+//                 step, one grid barrier per step); cooperative launch, bounded barrier waits.
+//   k_eig_sort    ascending eigenvalues with eigenvector columns permuted accordingly.
+//
+// Problems carry a "valid size" nv <= n: entries beyond it are padding.  Gram matrices get an
+// identity there (so Cholesky passes through), Rayleigh-Ritz matrices a huge diagonal (so the
+// padding sorts last).
+#include <cooperative_groups.h>
+
+#include <cmath>
+
+#include "hw_common.cuh"
+#include "hw_ctx.h"
+
+namespace hw {
+
+// ---------------------------------------------------------------------- padding helpers
+// G[b] (n x n, column-major, stride sG): zero rows/cols >= nv[b], diagonal = diagval (+ index)
+__global__ void k_pad_square(double2* G, int n, int64_t sG, const int* nv, double diagval, int ramp) {
+  const int b = blockIdx.y;
+  double2* g = G + (size_t)b * sG;
+  const int v = nv[b];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * n; t += gridDim.x * blockDim.x) {
+    const int i = t % n, j = t / n;
+    if (i >= v || j >= v) {
+      double2 z;
+      z.x = (i == j) ? diagval + (ramp ? double(i) : 0.0) : 0.0;
+      z.y = 0.0;
+      g[t] = z;
+    }
+  }
+}
+
+// A = (A + A^H) / 2 in place
+__global__ void k_hermitize(double2* A, int n, int64_t sA) {
+  const int b = blockIdx.y;
+  double2* a = A + (size_t)b * sA;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * n; t += gridDim.x * blockDim.x) {
+    const int i = t % n, j = t / n;
+    if (i > j) continue;
+    const double2 x = a[i + (size_t)j * n], y = a[j + (size_t)i * n];
+    double2 m;
+    m.x = 0.5 * (x.x + y.x);
+    m.y = 0.5 * (x.y - y.y);
+    if (i == j) m.y = 0.0;
+    a[i + (size_t)j * n] = m;
+    double2 mc = m;
+    mc.y = -m.y;
+    a[j + (size_t)i * n] = mc;
+  }
+}
+
+// ---------------------------------------------------------------------- Cholesky
+constexpr int CHOL_THREADS = 256;
+
+// lower Cholesky in place (upper triangle zeroed); fail[b] = 1 + column of a bad pivot
+__global__ void __launch_bounds__(CHOL_THREADS) k_chol(double2* G, int n, int64_t sG, int* fail,
+                                                       int use_smem) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.x;
+  double2* g = G + (size_t)b * sG;
+  double2* a = use_smem ? reinterpret_cast<double2*>(smem_raw) : g;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  if (use_smem)
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) a[t] = g[t];
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const double d = a[j + (size_t)j * n].x;
+    if (!(d > 0.0) || !isfinite(d)) {
+      if (threadIdx.x == 0) bad = j + 1;
+      __syncthreads();
+      break;
+    }
+    const double s = sqrt(d), inv = 1.0 / s;
+    __syncthreads();
+    for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
+      double2 v = a[i + (size_t)j * n];
+      if (i == j) {
+        v.x = s;
+        v.y = 0.0;
+      } else {
+        v.x *= inv;
+        v.y *= inv;
+      }
+      a[i + (size_t)j * n] = v;
+    }
+    __syncthreads();
+    // trailing update: a[i][k] -= l[i][j] conj(l[k][j]) for j < k <= i
+    const int m = n - j - 1;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      const int i = j + 1 + t % m, k = j + 1 + t / m;
+      if (k > i) continue;
+      const double2 li = a[i + (size_t)j * n], lk = a[k + (size_t)j * n];
+      double2 v = a[i + (size_t)k * n];
+      v.x -= li.x * lk.x + li.y * lk.y;
+      v.y -= li.y * lk.x - li.x * lk.y;
+      a[i + (size_t)k * n] = v;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  // zero the strict upper triangle
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int i = t % n, k = t / n;
+    if (k > i) a[t] = make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  if (use_smem)
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) g[t] = a[t];
+  if (threadIdx.x == 0) fail[b] = bad;
+}
+
+// Given lower L (n x n), write Uinv = (L^H)^{-1} (upper triangular) into Ui.  Column j of
+// L^{-1} by forward substitution (one thread per column); Uinv = (L^{-1})^H.
+__global__ void k_trinv(const double2* L, int64_t sL, double2* Ui, int64_t sU, int n) {
+  const int b = blockIdx.y;
+  const double2* l = L + (size_t)b * sL;
+  double2* u = Ui + (size_t)b * sU;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  // x = L^{-1} e_j: x[i] = 0 for i < j; then store conj(x[i]) at u[j][i] (row j, column i)
+  for (int i = 0; i < n; ++i) u[j + (size_t)i * n] = make_double2(0.0, 0.0);
+  for (int i = j; i < n; ++i) {
+    double sr = (i == j) ? 1.0 : 0.0, si = 0.0;
+    for (int k = j; k < i; ++k) {
+      const double2 lik = l[i + (size_t)k * n];
+      const double2 xk = u[j + (size_t)k * n];   // conj(x[k]) stored
+      // s -= l[i][k] * x[k]  with x[k] = conj(xk)
+      sr -= lik.x * xk.x + lik.y * xk.y;
+      si -= lik.y * xk.x - lik.x * xk.y;
+    }
+    const double2 lii = l[i + (size_t)i * n];      // real positive
+    const double inv = 1.0 / lii.x;
+    u[j + (size_t)i * n] = make_double2(sr * inv, -si * inv);
+  }
+}
+
+// ---------------------------------------------------------------------- grid barrier
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+  int abort;
+  int pad;
+};
+
+// returns false when the barrier gave up (error flag set; the caller leaves the kernel)
+__device__ bool grid_sync(GridBar* bar, int* status) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned int* vgen = &bar->gen;
+    volatile int* vab = &bar->abort;
+    const unsigned int g = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&bar->count, 1u);
+    if (arrived == gridDim.x - 1) {
+      bar->count = 0;
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      long spins = 0;
+      while (*vgen == g) {
+        if (*vab) { ok = 0; break; }
+        if (++spins > (1L << 24)) {   // ~2 s with the sleeps below
+          atomicExch(&bar->abort, 1);
+          atomicExch(status, HW_ETIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// ---------------------------------------------------------------------- Jacobi
+struct JacArgs {
+  int nprob, n, maxsweep;
+  double tol;           // stop when off(A)_F <= tol * ||A||_F for every problem
+  double2* A0;          // [nprob][n*n] input (destroyed)
+  double2* A1;          // [nprob][n*n] scratch
+  double2* V;           // [nprob][n*n] eigenvectors (columns)
+  double* off;          // [maxsweep+1][nprob] off-norm accumulators (zeroed by the host)
+  double* fro;          // [nprob] ||A||_F^2 (zeroed by the host)
+  GridBar* bar;
+  int* status;
+  int* sweeps_done;
+};
+
+__device__ __forceinline__ int rr_index(int pos, int t, int n) {
+  return pos == 0 ? 0 : 1 + (pos - 1 + t) % (n - 1);
+}
+
+struct Rot {
+  double cs, sn;
+  double er, ei;   // e = c / |c|
+};
+
+__device__ __forceinline__ Rot make_rot(const double2* a, int n, int p, int q) {
+  Rot r;
+  const double app = a[p + (size_t)p * n].x, aqq = a[q + (size_t)q * n].x;
+  const double2 c = a[p + (size_t)q * n];
+  const double ac = hypot(c.x, c.y);
+  if (!(ac > 1e-300)) {
+    r.cs = 1.0; r.sn = 0.0; r.er = 1.0; r.ei = 0.0;
+    return r;
+  }
+  const double zeta = (aqq - app) / (2.0 * ac);
+  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  r.cs = 1.0 / sqrt(1.0 + t * t);
+  r.sn = t * r.cs;
+  r.er = c.x / ac;
+  r.ei = c.y / ac;
+  return r;
+}
+
+// grid-stride over (problem, block I, block J) and (problem, row, block I)
+__global__ void __launch_bounds__(256) k_jacobi(JacArgs J) {
+  const int n = J.n, h = n / 2;
+  const long nA = (long)J.nprob * h * h;
+  const long nV = (long)J.nprob * n * h;
+  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const long nth = (long)gridDim.x * blockDim.x;
+  // Frobenius norms
+  for (long t = tid; t < (long)J.nprob * n * n; t += nth) {
+    const int b = (int)(t / ((long)n * n));
+    const double2 v = J.A0[t];
+    const double m2 = v.x * v.x + v.y * v.y;
+    if (m2 < 1e18) atomicAdd(&J.fro[b], m2);   // padding entries (>= 1e9) do not count
+  }
+  if (!grid_sync(J.bar, J.status)) return;
+  double2* Acur = J.A0;
+  double2* Anext = J.A1;
+  int sweep = 0;
+  for (; sweep < J.maxsweep; ++sweep) {
+    double* offacc = J.off + (size_t)sweep * J.nprob;
+    for (int step = 0; step < n - 1; ++step) {
+      const bool last = (step == n - 2);
+      for (long t = tid; t < nA + nV; t += nth) {
+        if (t < nA) {
+          const int b = (int)(t / ((long)h * h));
+          const int rem = (int)(t - (long)b * h * h);
+          const int I = rem % h, Jb = rem / h;
+          const double2* a = Acur + (size_t)b * n * n;
+          double2* an = Anext + (size_t)b * n * n;
+          const int pI = rr_index(I, step, n), qI = rr_index(n - 1 - I, step, n);
+          const int pJ = rr_index(Jb, step, n), qJ = rr_index(n - 1 - Jb, step, n);
+          const int p1 = min(pI, qI), q1 = max(pI, qI);
+          const int p2 = min(pJ, qJ), q2 = max(pJ, qJ);
+          const Rot r1 = make_rot(a, n, p1, q1);
+          if (I == Jb) {
+            const double app = a[p1 + (size_t)p1 * n].x, aqq = a[q1 + (size_t)q1 * n].x;
+            const double2 c = a[p1 + (size_t)q1 * n];
+            const double ac = hypot(c.x, c.y);
+            const double t1 = r1.cs != 0.0 ? r1.sn / r1.cs : 0.0;
+            an[p1 + (size_t)p1 * n] = make_double2(app - t1 * ac, 0.0);
+            an[q1 + (size_t)q1 * n] = make_double2(aqq + t1 * ac, 0.0);
+            an[p1 + (size_t)q1 * n] = make_double2(0.0, 0.0);
+            an[q1 + (size_t)p1 * n] = make_double2(0.0, 0.0);
+            continue;
+          }
+          const Rot r2 = make_rot(a, n, p2, q2);
+          // M = J1^H A_blk:  row p1' = cs A[p1,:] - sn e1 A[q1,:];  row q1' = sn A[p1,:] + cs e1 A[q1,:]
+          double2 A_pp = a[p1 + (size_t)p2 * n], A_pq = a[p1 + (size_t)q2 * n];
+          double2 A_qp = a[q1 + (size_t)p2 * n], A_qq = a[q1 + (size_t)q2 * n];
+          auto e_mul = [](double er, double ei, double2 z) { return make_double2(er * z.x - ei * z.y, er * z.y + ei * z.x); };
+          const double2 eq_p = e_mul(r1.er, r1.ei, A_qp), eq_q = e_mul(r1.er, r1.ei, A_qq);
+          double2 M_pp = make_double2(r1.cs * A_pp.x - r1.sn * eq_p.x, r1.cs * A_pp.y - r1.sn * eq_p.y);
+          double2 M_pq = make_double2(r1.cs * A_pq.x - r1.sn * eq_q.x, r1.cs * A_pq.y - r1.sn * eq_q.y);
+          double2 M_qp = make_double2(r1.sn * A_pp.x + r1.cs * eq_p.x, r1.sn * A_pp.y + r1.cs * eq_p.y);
+          double2 M_qq = make_double2(r1.sn * A_pq.x + r1.cs * eq_q.x, r1.sn * A_pq.y + r1.cs * eq_q.y);
+          // M J2: col p2' = cs M[:,p2] - sn conj(e2) M[:,q2];  col q2' = sn M[:,p2] + cs conj(e2) M[:,q2]
+          const double2 cq_p = e_mul(r2.er, -r2.ei, M_pq), cq_q = e_mul(r2.er, -r2.ei, M_qq);
+          const double2 o_pp = make_double2(r2.cs * M_pp.x - r2.sn * cq_p.x, r2.cs * M_pp.y - r2.sn * cq_p.y);
+          const double2 o_qp = make_double2(r2.cs * M_qp.x - r2.sn * cq_q.x, r2.cs * M_qp.y - r2.sn * cq_q.y);
+          const double2 o_pq = make_double2(r2.sn * M_pp.x + r2.cs * cq_p.x, r2.sn * M_pp.y + r2.cs * cq_p.y);
+          const double2 o_qq = make_double2(r2.sn * M_qp.x + r2.cs * cq_q.x, r2.sn * M_qp.y + r2.cs * cq_q.y);
+          an[p1 + (size_t)p2 * n] = o_pp;
+          an[p1 + (size_t)q2 * n] = o_pq;
+          an[q1 + (size_t)p2 * n] = o_qp;
+          an[q1 + (size_t)q2 * n] = o_qq;
+          if (last) {
+            const double s = o_pp.x * o_pp.x + o_pp.y * o_pp.y + o_pq.x * o_pq.x + o_pq.y * o_pq.y +
+                             o_qp.x * o_qp.x + o_qp.y * o_qp.y + o_qq.x * o_qq.x + o_qq.y * o_qq.y;
+            atomicAdd(&offacc[b], s);
+          }
+        } else {
+          const long u = t - nA;
+          const int b = (int)(u / ((long)n * h));
+          const int rem = (int)(u - (long)b * n * h);
+          const int row = rem % n, I = rem / n;
+          const double2* a = Acur + (size_t)b * n * n;
+          double2* v = J.V + (size_t)b * n * n;
+          const int pI = rr_index(I, step, n), qI = rr_index(n - 1 - I, step, n);
+          const int p1 = min(pI, qI), q1 = max(pI, qI);
+          const Rot r = make_rot(a, n, p1, q1);
+          const double2 vp = v[row + (size_t)p1 * n], vq = v[row + (size_t)q1 * n];
+          // V' col p = cs vp - sn conj(e) vq;  col q = sn vp + cs conj(e) vq
+          const double2 cv = make_double2(r.er * vq.x + r.ei * vq.y, r.er * vq.y - r.ei * vq.x);
+          v[row + (size_t)p1 * n] = make_double2(r.cs * vp.x - r.sn * cv.x, r.cs * vp.y - r.sn * cv.y);
+          v[row + (size_t)q1 * n] = make_double2(r.sn * vp.x + r.cs * cv.x, r.sn * vp.y + r.cs * cv.y);
+        }
+      }
+      if (!grid_sync(J.bar, J.status)) return;
+      double2* tmp = Acur;
+      Acur = Anext;
+      Anext = tmp;
+    }
+    // every problem converged?
+    bool done = true;
+    for (int b = 0; b < J.nprob; ++b)
+      if (offacc[b] > J.tol * J.tol * J.fro[b]) done = false;
+    if (done) {
+      ++sweep;
+      break;
+    }
+  }
+  // make sure the result sits in A0
+  if (Acur != J.A0) {
+    for (long t = tid; t < (long)J.nprob * n * n; t += nth) J.A0[t] = Acur[t];
+  }
+  if (tid == 0) *J.sweeps_done = sweep;
+}
+
+// eigenvalues ascending: w[b][i], vectors Z[b] columns permuted (Z may not alias V)
+__global__ void k_eig_sort(const double2* A, const double2* V, int n, double* w, double2* Z) {
+  const int b = blockIdx.x;
+  const double2* a = A + (size_t)b * n * n;
+  const double2* v = V + (size_t)b * n * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double di = a[i + (size_t)i * n].x;
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double dj = a[j + (size_t)j * n].x;
+      rank += (dj < di) || (dj == di && j < i);
+    }
+    w[(size_t)b * n + rank] = di;
+    for (int r = 0; r < n; ++r) Z[(size_t)b * n * n + r + (size_t)rank * n] = v[r + (size_t)i * n];
+  }
+}
+
+__global__ void k_identity(double2* V, int n, int nprob) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < (long)nprob * n * n;
+       t += (long)gridDim.x * blockDim.x) {
+    const int r = (int)(t % n), c = (int)((t / n) % n);
+    V[t] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+  }
+}
+
+// ---------------------------------------------------------------------- host wrappers
+struct DenseWork {
+  double2* A1 = nullptr;
+  double2* V = nullptr;
+  double* off = nullptr;
+  double* fro = nullptr;
+  GridBar* bar = nullptr;
+  int* sweeps = nullptr;
+  size_t cap = 0;       // elements of A1 / V
+  int maxsweep = 40;
+  int coop_blocks = 0;
+};
+
+
+cudaError_t dense_alloc(DenseWork*& dw, size_t cap_elems, int maxnprob) {
+  if (!dw) dw = new DenseWork();
+  if (dw->cap >= cap_elems && dw->A1) return cudaSuccess;
+  if (dw->A1) cudaFree(dw->A1);
+  if (dw->V) cudaFree(dw->V);
+  if (dw->off) cudaFree(dw->off);
+  if (dw->fro) cudaFree(dw->fro);
+  if (dw->bar) cudaFree(dw->bar);
+  if (dw->sweeps) cudaFree(dw->sweeps);
+  cudaError_t e = cudaMalloc((void**)&dw->A1, cap_elems * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dw->V, cap_elems * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dw->off, (size_t)(dw->maxsweep + 1) * maxnprob * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dw->fro, (size_t)maxnprob * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dw->bar, sizeof(GridBar));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dw->sweeps, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(dw->bar, 0, sizeof(GridBar));
+  dw->cap = cap_elems;
+  if (e == cudaSuccess) {
+    int dev = 0, nsm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi, 256, 0);
+    dw->coop_blocks = nsm * std::max(1, std::min(occ, 2));
+  }
+  return e;
+}
+
+void dense_free(DenseWork*& dw) {
+  if (!dw) return;
+  for (void* p : {(void*)dw->A1, (void*)dw->V, (void*)dw->off, (void*)dw->fro, (void*)dw->bar,
+                  (void*)dw->sweeps})
+    if (p) cudaFree(p);
+  delete dw;
+  dw = nullptr;
+}
+
+// Eigen-decomposition of nprob Hermitian n x n matrices A (contiguous, n*n each; destroyed):
+// w [nprob][n] ascending, Z [nprob][n*n] eigenvector columns.  status: device int (HW_*).
+cudaError_t dense_heev(DenseWork* dw, cudaStream_t st, double2* A, int n, int nprob, double* w,
+                       double2* Z, int* status, double tol) {
+  const size_t elems = (size_t)nprob * n * n;
+  if (elems > dw->cap || (n & 1)) return cudaErrorInvalidValue;
+  k_identity<<<256, 256, 0, st>>>(dw->V, n, nprob);
+  cudaMemsetAsync(dw->off, 0, (size_t)(dw->maxsweep + 1) * nprob * sizeof(double), st);
+  cudaMemsetAsync(dw->fro, 0, (size_t)nprob * sizeof(double), st);
+  cudaMemsetAsync(dw->bar, 0, sizeof(GridBar), st);
+  JacArgs ja;
+  ja.nprob = nprob;
+  ja.n = n;
+  ja.maxsweep = dw->maxsweep;
+  ja.tol = tol;
+  ja.A0 = A;
+  ja.A1 = dw->A1;
+  ja.V = dw->V;
+  ja.off = dw->off;
+  ja.fro = dw->fro;
+  ja.bar = dw->bar;
+  ja.status = status;
+  ja.sweeps_done = dw->sweeps;
+  void* args[] = {&ja};
+  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(dw->coop_blocks), dim3(256), args, 0, st);
+  if (e != cudaSuccess) return e;
+  k_eig_sort<<<nprob, 256, 0, st>>>(A, dw->V, n, w, Z);
+  return cudaGetLastError();
+}
+
+cudaError_t dense_chol(cudaStream_t st, double2* G, int n, int nprob, int* fail) {
+  const size_t bytes = (size_t)n * n * sizeof(double2);
+  const int use_smem = bytes <= 200 * 1024;
+  if (use_smem) cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  k_chol<<<nprob, CHOL_THREADS, use_smem ? bytes : 0, st>>>(G, n, (int64_t)n * n, fail, use_smem);
+  return cudaGetLastError();
+}
+
+cudaError_t dense_trinv(cudaStream_t st, const double2* L, double2* Ui, int n, int nprob) {
+  k_trinv<<<dim3((n + 63) / 64, nprob), 64, 0, st>>>(L, (int64_t)n * n, Ui, (int64_t)n * n, n);
+  return cudaGetLastError();
+}
+
+cudaError_t dense_pad(cudaStream_t st, double2* G, int n, int nprob, const int* nv, double diag, int ramp) {
+  k_pad_square<<<dim3(32, nprob), 256, 0, st>>>(G, n, (int64_t)n * n, nv, diag, ramp);
+  return cudaGetLastError();
+}
+
+cudaError_t dense_hermitize(cudaStream_t st, double2* A, int n, int nprob) {
+  k_hermitize<<<dim3(32, nprob), 256, 0, st>>>(A, n, (int64_t)n * n);
+  return cudaGetLastError();
+}
+
+}  // namespace hw

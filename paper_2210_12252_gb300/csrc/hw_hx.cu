@@ -400,7 +400,11 @@ cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld) {
     dim3 grid((unsigned)(((long)maxna * nc + RAD_Q - 1) / RAD_Q), hb.N + 1);
     const size_t sm_inv = ((size_t(Nr) * K * sizeof(T) + 15) & ~size_t(15)) +
                           (size_t)K * RAD_Q * sizeof(cplx_t<T>);
-    k_radial_inv<T><<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra);
+    {
+      ProfScope ps(ctx, HW_PH_RADIAL_INV);
+      k_radial_inv<T><<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra);
+      ctx->launches++;
+    }
     SlabArgs<T> sa;
     sa.Nr = Nr;
     sa.Nth1 = hb.prm.Nth1;
@@ -420,12 +424,20 @@ cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld) {
     sa.G = reinterpret_cast<const cplx_t<T>*>(ctx->ws.gbuf);
     sa.H = reinterpret_cast<cplx_t<T>*>(ctx->ws.hbuf);
     const size_t sm_slab = slab_smem_bytes(ctx, sizeof(cplx_t<T>), Jc);
-    k_slab<T><<<dim3(nc, Nr), SLAB_THREADS, sm_slab, ctx->stream>>>(sa);
+    {
+      ProfScope ps(ctx, HW_PH_SLAB);
+      k_slab<T><<<dim3(nc, Nr), SLAB_THREADS, sm_slab, ctx->stream>>>(sa);
+      ctx->launches++;
+    }
     ra.gh = reinterpret_cast<cplx_t<T>*>(ctx->ws.hbuf);
     ra.rtab = tb.rfwd;
     const size_t sm_fwd = ((size_t(K) * Nr * sizeof(T) + 15) & ~size_t(15)) +
                           32 * RAD_Q * sizeof(cplx_t<T>) + (size_t)RAD_Q * (K + 1) * sizeof(cplx_t<T>);
-    k_radial_fwd<T><<<grid, RAD_THREADS, sm_fwd, ctx->stream>>>(ra);
+    {
+      ProfScope ps(ctx, HW_PH_RADIAL_FWD);
+      k_radial_fwd<T><<<grid, RAD_THREADS, sm_fwd, ctx->stream>>>(ra);
+      ctx->launches++;
+    }
   }
   return cudaGetLastError();
 }

@@ -1,15 +1,684 @@
-// Block LOBPCG (placeholder until the solver lands).
+// Block LOBPCG for the helical-wave Hamiltonian (arXiv 2210.12252, Sec. "Eigensolvers and
+// Preconditioning": LOBPCG with the Teter-Payne-Allan preconditioner), batched over k-points
+// that iterate in lockstep.
+//
+// Per iteration and k-point (X: nb Ritz vectors, P: previous search directions, W: new ones):
+//   R = H X - X Theta, residual norms (FP64); columns with ||r|| <= tol are soft-locked
+//   W = K R[:, active]                      preconditioner (TPA or learned)
+//   W -= [X P]([X P]^H W), twice            projection (classical Gram-Schmidt, repeated)
+//   W = W U^{-1}, W^H W = U^H U, twice      Cholesky-QR
+//   HW = H W                                the matrix-free product of Algorithm 5
+//   A = S^H (H S), S = [X P W] orthonormal  Rayleigh-Ritz projection, FP64
+//   A = Z diag(lambda) Z^H                  dense Hermitian eigensolver (Jacobi)
+//   X = S Z[:, :nb], HX = HS Z[:, :nb]
+//   P = S Y, HP = HS Y with Y = the W/P part of Z[:, active], orthogonalised against Z[:, :nb]
+//        and orthonormalised in the small space (so [X P] stays orthonormal)
+// Padding: k-points share the block layout; columns beyond a k-point's valid counts are zero
+// and their Gram / Rayleigh-Ritz rows are padded (identity / huge diagonal).
+//
+// Precision: HW_FP64 runs every product in FP64.  HW_MIXED applies H in FP32 (the transforms)
+// while Gram, Cholesky, Rayleigh-Ritz and the residuals stay FP64; HX is refreshed with an FP64
+// product when the residuals first fall below 1e-3, and every convergence claim is verified by
+// an FP64 recomputation of HX before it is accepted.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "hw_common.cuh"
 #include "hw_ctx.h"
 
 namespace hw {
-struct LobpcgWork {};
+
+struct DenseWork;
+cudaError_t dense_alloc(DenseWork*& dw, size_t cap_elems, int maxnprob);
+void dense_free(DenseWork*& dw);
+cudaError_t dense_heev(DenseWork* dw, cudaStream_t st, double2* A, int n, int nprob, double* w,
+                       double2* Z, int* status, double tol);
+cudaError_t dense_chol(cudaStream_t st, double2* G, int n, int nprob, int* fail);
+cudaError_t dense_trinv(cudaStream_t st, const double2* L, double2* Ui, int n, int nprob);
+cudaError_t dense_hermitize(cudaStream_t st, double2* A, int n, int nprob);
+cudaError_t launch_precond_learned(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld,
+                                   const double* const* ritz);
+
+struct LobpcgWork {
+  int nk = 0, nb = 0, ne = 0;   // ne: even Rayleigh-Ritz size bound >= 3 nb
+  int64_t Lpad = 0;
+  double2* SB[2] = {nullptr, nullptr};
+  double2* HSB[2] = {nullptr, nullptr};
+  double2* R = nullptr;
+  double2* A = nullptr;     // [nk][ne*ne]
+  double2* Z = nullptr;     // [nk][ne*ne]
+  double* w = nullptr;      // [nk][ne]
+  double2* G = nullptr;     // [nk][nb*nb] Gram / Cholesky factor
+  double2* Ui = nullptr;    // [nk][nb*nb]
+  double2* C = nullptr;     // [nk][2nb*nb] projection coefficients
+  double2* Y = nullptr;     // [nk][ne*nb]
+  double2* Y2 = nullptr;    // [nk][ne*nb]
+  double* res = nullptr;    // [nk][nb]
+  double* theta = nullptr;  // [nk][nb]
+  int* iact = nullptr;      // [nk][nb] active column indices (-1 = padding)
+  int* fail = nullptr;      // [nk]
+  int* status = nullptr;
+  DenseWork* dw = nullptr;
+};
+
 void lobpcg_free(hw_ctx* ctx) {
-  delete ctx->lw;
+  LobpcgWork* w = ctx->lw;
+  if (!w) return;
+  for (void* p : {(void*)w->SB[0], (void*)w->SB[1], (void*)w->HSB[0], (void*)w->HSB[1], (void*)w->R,
+                  (void*)w->A, (void*)w->Z, (void*)w->w, (void*)w->G, (void*)w->Ui, (void*)w->C,
+                  (void*)w->Y, (void*)w->Y2, (void*)w->res, (void*)w->theta, (void*)w->iact,
+                  (void*)w->fail, (void*)w->status})
+    if (p) cudaFree(p);
+  dense_free(w->dw);
+  delete w;
   ctx->lw = nullptr;
 }
+
+namespace {
+
+// ------------------------------------------------------------------------ small kernels
+// R = HX - X theta and ||r_j||_2 (FP64); grid (nb, nk)
+__global__ void k_residual(const double2* S, const double2* HS, int64_t Lpad, int64_t sK,
+                           const double* theta, int nb, double2* R, double* res) {
+  __shared__ double red[8];
+  const int j = blockIdx.x, b = blockIdx.y;
+  const double2* x = S + (size_t)b * sK + (size_t)j * Lpad;
+  const double2* hx = HS + (size_t)b * sK + (size_t)j * Lpad;
+  double2* r = R + (size_t)b * Lpad * nb + (size_t)j * Lpad;
+  const double th = theta[(size_t)b * nb + j];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < Lpad; i += blockDim.x) {
+    const double2 a = hx[i], v = x[i];
+    double2 q;
+    q.x = a.x - th * v.x;
+    q.y = a.y - th * v.y;
+    r[i] = q;
+    s += q.x * q.x + q.y * q.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    res[(size_t)b * nb + j] = sqrt(t);
+  }
+}
+
+// W[:, i] = R[:, iact[b][i]] (zero for -1); W lives in S at column offset woff; grid (na, nk)
+__global__ void k_gather_w(const double2* R, int nb, int64_t Lpad, const int* iact, int na, double2* S,
+                           int64_t sK, int woff) {
+  const int i = blockIdx.x, b = blockIdx.y;
+  const int src = iact[(size_t)b * nb + i];
+  double2* w = S + (size_t)b * sK + (size_t)(woff + i) * Lpad;
+  const double2* r = R + (size_t)b * Lpad * nb + (size_t)(src < 0 ? 0 : src) * Lpad;
+  for (int64_t t = threadIdx.x; t < Lpad; t += blockDim.x) w[t] = src < 0 ? make_double2(0.0, 0.0) : r[t];
+}
+
+// pad an n x n Gram matrix: rows/cols i >= nv[b] become identity
+__global__ void k_pad_gram(double2* G, int n, const int* nv) {
+  const int b = blockIdx.y;
+  double2* g = G + (size_t)b * n * n;
+  const int v = nv[b];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * n; t += gridDim.x * blockDim.x) {
+    const int i = t % n, j = t / n;
+    if (i >= v || j >= v) g[t] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+}
+
+// pad the Rayleigh-Ritz matrix: index j of S = [X(nb) P(np) W(na)] is valid iff j < nb, or
+// j in the P block below npv[b], or j in the W block below nav[b]; invalid rows/cols get a
+// huge distinct diagonal so they sort last.  n may exceed nb+np+na by one (even size).
+__global__ void k_pad_rr(double2* A, int n, int nb, int np, int na, const int* npv, const int* nav) {
+  const int b = blockIdx.y;
+  double2* a = A + (size_t)b * n * n;
+  auto valid = [&](int j) {
+    if (j < nb) return true;
+    if (j < nb + np) return j - nb < npv[b];
+    if (j < nb + np + na) return j - nb - np < nav[b];
+    return false;
+  };
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * n; t += gridDim.x * blockDim.x) {
+    const int i = t % n, j = t / n;
+    if (!valid(i) || !valid(j)) a[t] = make_double2(i == j ? 1e10 * (1.0 + 1e-3 * i) : 0.0, 0.0);
+  }
+}
+
+// Y[:, i] = Z[:, iact[b][i]] with the X rows (< nb) zeroed; zero column for padding; grid (na, nk)
+__global__ void k_build_y(const double2* Z, int ne, int nb, const int* iact, int na, double2* Y) {
+  const int i = blockIdx.x, b = blockIdx.y;
+  const int src = iact[(size_t)b * nb + i];
+  double2* y = Y + (size_t)b * ne * na + (size_t)i * ne;
+  const double2* z = Z + (size_t)b * ne * ne + (size_t)(src < 0 ? 0 : src) * ne;
+  for (int r = threadIdx.x; r < ne; r += blockDim.x)
+    y[r] = (src < 0 || r < nb) ? make_double2(0.0, 0.0) : z[r];
+}
+
+// Gaussian start block from a counter-based generator (splitmix64 + Box-Muller); grid (nb, nk)
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+__global__ void k_random_start(double2* S, int64_t Lpad, int64_t sK, const int64_t* L, int nb, uint64_t seed) {
+  const int j = blockIdx.x, b = blockIdx.y;
+  double2* x = S + (size_t)b * sK + (size_t)j * Lpad;
+  for (int64_t i = threadIdx.x; i < Lpad; i += blockDim.x) {
+    double2 v = make_double2(0.0, 0.0);
+    if (i < L[b]) {
+      const uint64_t c = ((uint64_t)b << 48) ^ ((uint64_t)j << 32) ^ (uint64_t)i;
+      const uint64_t u1 = splitmix64(seed ^ (2 * c)), u2 = splitmix64(seed ^ (2 * c + 1));
+      const double a = ((u1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+      const double t = ((u2 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+      const double rr = sqrt(-log(a));   // complex Gaussian with E|z|^2 = 1
+      v.x = rr * cos(6.283185307179586 * t);
+      v.y = rr * sin(6.283185307179586 * t);
+    }
+    x[i] = v;
+  }
+}
+
+// copy the user's start block (L_b x nb, ld L_b) into S; grid (nb, nk)
+struct PtrArr {
+  const double* p[MAXSLOT];
+};
+__global__ void k_copy_start(PtrArr src, double2* S, int64_t Lpad, int64_t sK, const int64_t* L) {
+  const int j = blockIdx.x, b = blockIdx.y;
+  const double2* s = reinterpret_cast<const double2*>(src.p[b]) + (size_t)j * L[b];
+  double2* x = S + (size_t)b * sK + (size_t)j * Lpad;
+  for (int64_t i = threadIdx.x; i < Lpad; i += blockDim.x) x[i] = i < L[b] ? s[i] : make_double2(0.0, 0.0);
+}
+
+// ------------------------------------------------------------------------ cuBLAS helper
+struct Gemm {
+  hw_ctx* ctx;
+  cublasStatus_t st = CUBLAS_STATUS_SUCCESS;
+  void operator()(cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, double alpha,
+                  const double2* A, int64_t lda, int64_t sA, const double2* B, int64_t ldb, int64_t sB,
+                  double beta, double2* C, int64_t ldc, int64_t sC, int batch) {
+    if (st != CUBLAS_STATUS_SUCCESS || m <= 0 || n <= 0) return;
+    if (k <= 0) {  // C = beta C
+      if (beta == 1.0) return;
+    }
+    const cuDoubleComplex al = make_cuDoubleComplex(alpha, 0.0), be = make_cuDoubleComplex(beta, 0.0);
+    ProfScope ps(ctx, HW_PH_GEMM);
+    st = cublasZgemmStridedBatched(ctx->cublas, ta, tb, m, n, std::max(k, 1), &al,
+                                   reinterpret_cast<const cuDoubleComplex*>(A), (int)lda, sA,
+                                   reinterpret_cast<const cuDoubleComplex*>(B), (int)ldb, sB, &be,
+                                   reinterpret_cast<cuDoubleComplex*>(C), (int)ldc, sC, batch);
+  }
+};
+
+}  // namespace
+
+// Orthonormalise `ncol` columns of S at column offset c0 for every k-point by Cholesky-QR
+// (Gram, Cholesky, triangular inverse, GEMM), `passes` times.  nv[b]: valid columns of k-point
+// b (device).  On a failed factorisation the k-point's fail flag is set.
+static hw_status cholqr(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, double2* S, int c0, int ncol,
+                        const int* d_nv, int passes, std::vector<int>& failed) {
+  const int nk = w->nk;
+  const int64_t Lpad = w->Lpad, sK = Lpad * 3 * w->nb;
+  double2* Wb = S + (size_t)c0 * Lpad;
+  failed.assign(nk, 0);
+  for (int pass = 0; pass < passes; ++pass) {
+    gemm(CUBLAS_OP_C, CUBLAS_OP_N, ncol, ncol, (int)Lpad, 1.0, Wb, Lpad, sK, Wb, Lpad, sK, 0.0, w->G, ncol,
+         (int64_t)ncol * ncol, nk);
+    {
+      ProfScope ps_(ctx, HW_PH_OTHER);
+      k_pad_gram<<<dim3(8, nk), 256, 0, ctx->stream>>>(w->G, ncol, d_nv);
+      ctx->launches++;
+    }
+    {
+      ProfScope ps_(ctx, HW_PH_CHOL);
+      dense_hermitize(ctx->stream, w->G, ncol, nk);
+      dense_chol(ctx->stream, w->G, ncol, nk, w->fail);
+      dense_trinv(ctx->stream, w->G, w->Ui, ncol, nk);
+      ctx->launches += 3;
+    }
+    // R-buffer as temporary: T = W Ui, then copy back
+    gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, ncol, ncol, 1.0, Wb, Lpad, sK, w->Ui, ncol, (int64_t)ncol * ncol,
+         0.0, w->R, Lpad, Lpad * w->nb, nk);
+    for (int b = 0; b < nk; ++b)
+      cudaMemcpyAsync(Wb + (size_t)b * sK, w->R + (size_t)b * Lpad * w->nb, (size_t)Lpad * ncol * sizeof(double2),
+                      cudaMemcpyDeviceToDevice, ctx->stream);
+    std::vector<int> f(nk);
+    cudaMemcpyAsync(f.data(), w->fail, nk * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("cholqr: ") + cudaGetErrorString(e));
+    for (int b = 0; b < nk; ++b)
+      if (f[b]) failed[b] = 1;
+  }
+  return gemm.st == CUBLAS_STATUS_SUCCESS ? HW_OK : hw_fail(ctx, HW_ECUDA, "cuBLAS failure in Cholesky-QR");
+}
+
+// apply H to `ncol` columns of S at column offset c0, result at the same offset of HS
+static hw_status apply_block(hw_ctx* ctx, LobpcgWork* w, const std::vector<int>& kidx, double2* S, double2* HS,
+                             int c0, int ncol, bool fp64, const std::vector<int>* only = nullptr) {
+  if (ncol <= 0) return HW_OK;
+  const int64_t sK = w->Lpad * 3 * w->nb;
+  Blocks blk;
+  blk.nslot = 0;
+  for (int b = 0; b < w->nk; ++b) {
+    if (only && !(*only)[b]) continue;
+    blk.x[blk.nslot] = reinterpret_cast<const double*>(S + (size_t)b * sK + (size_t)c0 * w->Lpad);
+    blk.y[blk.nslot] = reinterpret_cast<double*>(HS + (size_t)b * sK + (size_t)c0 * w->Lpad);
+    blk.kb[blk.nslot] = kidx[b];
+    ++blk.nslot;
+  }
+  if (blk.nslot == 0) return HW_OK;
+  cudaError_t e = fp64 ? launch_hx<double>(ctx, blk, ncol, w->Lpad) : launch_hx<float>(ctx, blk, ncol, w->Lpad);
+  if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("apply_H: ") + cudaGetErrorString(e));
+  return HW_OK;
+}
+
+static hw_status ensure_work(hw_ctx* ctx, int nk, int nb, int64_t Lpad) {
+  LobpcgWork* w = ctx->lw;
+  if (w && w->nk == nk && w->nb == nb && w->Lpad == Lpad) return HW_OK;
+  lobpcg_free(ctx);
+  w = new LobpcgWork();
+  ctx->lw = w;
+  w->nk = nk;
+  w->nb = nb;
+  w->Lpad = Lpad;
+  w->ne = 3 * nb + ((3 * nb) & 1);
+  const size_t sK = (size_t)Lpad * 3 * nb;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess) e = cudaMemset(*p, 0, std::max<size_t>(bytes, 16));
+  };
+  for (int i = 0; i < 2; ++i) {
+    A((void**)&w->SB[i], nk * sK * sizeof(double2));
+    A((void**)&w->HSB[i], nk * sK * sizeof(double2));
+  }
+  A((void**)&w->R, (size_t)nk * Lpad * nb * sizeof(double2));
+  const size_t ne2 = (size_t)w->ne * w->ne;
+  A((void**)&w->A, nk * ne2 * sizeof(double2));
+  A((void**)&w->Z, nk * ne2 * sizeof(double2));
+  A((void**)&w->w, (size_t)nk * w->ne * sizeof(double));
+  A((void**)&w->G, (size_t)nk * nb * nb * sizeof(double2));
+  A((void**)&w->Ui, (size_t)nk * nb * nb * sizeof(double2));
+  A((void**)&w->C, (size_t)nk * 2 * nb * nb * sizeof(double2));
+  A((void**)&w->Y, (size_t)nk * w->ne * nb * sizeof(double2));
+  A((void**)&w->Y2, (size_t)nk * w->ne * nb * sizeof(double2));
+  A((void**)&w->res, (size_t)nk * nb * sizeof(double));
+  A((void**)&w->theta, (size_t)nk * nb * sizeof(double));
+  A((void**)&w->iact, (size_t)nk * nb * sizeof(int));
+  A((void**)&w->fail, (size_t)nk * sizeof(int));
+  A((void**)&w->status, sizeof(int));
+  if (e == cudaSuccess) e = dense_alloc(w->dw, nk * ne2, nk);
+  if (e != cudaSuccess) {
+    lobpcg_free(ctx);
+    return hw_fail(ctx, HW_ENOMEM, std::string("eigensolver workspace: ") + cudaGetErrorString(e));
+  }
+  return HW_OK;
+}
+
 }  // namespace hw
 
-extern "C" hw_status hw_solve_eigs(hw_ctx* ctx, int, const int*, int, int, double, int, hw_prec, int,
-                                   const double* const*, double*, double* const*, int64_t, int*, double*) {
-  return hw_fail(ctx, HW_ESTATE, "solver not built yet");
+using namespace hw;
+
+extern "C" hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, int block,
+                                   double tol, int maxit, hw_prec prec, int precond_kind,
+                                   const double* const* X0, double* evals, double* const* evecs,
+                                   int64_t ld_evecs, int* iters, double* resid) {
+  if (!ctx) return HW_EINVAL;
+  if (ctx->device < 0) return hw_fail(ctx, HW_ESTATE, "host-only context has no device");
+  if (!ctx->have_basis) return hw_fail(ctx, HW_ESTATE, "hw_setup_basis has not been called");
+  if (!ctx->have_V) return hw_fail(ctx, HW_ESTATE, "no potential installed");
+  if (nk < 1 || nk > MAXSLOT || !kidx_in || !evals) return hw_fail(ctx, HW_EINVAL, "bad k-point list");
+  if (n_eig < 1 || !(tol > 0) || maxit < 1) return hw_fail(ctx, HW_EINVAL, "bad n_eig / tol / maxit");
+  if (prec != HW_FP64 && prec != HW_MIXED) return hw_fail(ctx, HW_EINVAL, "bad precision");
+  if (precond_kind != HW_PRECOND_TPA && precond_kind != HW_PRECOND_NONE &&
+      !(precond_kind == HW_PRECOND_LEARNED && ctx->mlp))
+    return hw_fail(ctx, HW_EINVAL, "bad preconditioner kind (learned needs hw_set_mlp)");
+  std::vector<int> kidx(kidx_in, kidx_in + nk);
+  int64_t Lmax = 0, Lmin = INT64_MAX;
+  for (int b = 0; b < nk; ++b) {
+    if (kidx[b] < 0 || kidx[b] >= ctx->hb.nk) return hw_fail(ctx, HW_EINVAL, "k-point index out of range");
+    Lmax = std::max(Lmax, ctx->hb.L[kidx[b]]);
+    Lmin = std::min(Lmin, ctx->hb.L[kidx[b]]);
+  }
+  int nb = block > 0 ? block : n_eig + std::max(4, n_eig / 8);
+  if (nb < n_eig) return hw_fail(ctx, HW_EINVAL, "block < n_eig");
+  if (3 * (int64_t)nb > Lmin) return hw_fail(ctx, HW_EINVAL, "block too large for the basis (3*block > L)");
+  if (evecs && ld_evecs < Lmax) return hw_fail(ctx, HW_EINVAL, "ld_evecs < L");
+  const int64_t Lpad = (Lmax + 7) / 8 * 8;
+  cudaSetDevice(ctx->device);
+  hw_status hs = ensure_work(ctx, nk, nb, Lpad);
+  if (hs != HW_OK) return hs;
+  LobpcgWork* w = ctx->lw;
+  cudaStream_t st = ctx->stream;
+  Gemm gemm{ctx};
+  const int64_t sK = Lpad * 3 * nb;
+  const int ne = w->ne;
+  std::vector<int64_t> Lb(nk);
+  for (int b = 0; b < nk; ++b) Lb[b] = ctx->hb.L[kidx[b]];
+  int64_t* dL = nullptr;
+  int* dnv = nullptr;   // [3][nk]: valid counts for CholQR / P / W
+  cudaMalloc((void**)&dL, nk * sizeof(int64_t));
+  cudaMalloc((void**)&dnv, 3 * nk * sizeof(int));
+  cudaMemcpy(dL, Lb.data(), nk * sizeof(int64_t), cudaMemcpyHostToDevice);
+  struct Cleanup {
+    void* a;
+    void* b;
+    ~Cleanup() {
+      cudaFree(a);
+      cudaFree(b);
+    }
+  } cleanup{dL, dnv};
+  cudaMemsetAsync(w->status, 0, sizeof(int), st);
+  std::vector<int> failed;
+  int cur = 0;
+  // ---- start block
+  if (X0) {
+    PtrArr pa;
+    for (int b = 0; b < nk; ++b) {
+      if (!X0[b]) return hw_fail(ctx, HW_EINVAL, "null start block");
+      pa.p[b] = X0[b];
+    }
+    {
+      ProfScope ps_(ctx, HW_PH_OTHER);
+      k_copy_start<<<dim3(nb, nk), 256, 0, st>>>(pa, w->SB[0], Lpad, sK, dL);
+      ctx->launches++;
+    }
+  } else {
+    {
+      ProfScope ps_(ctx, HW_PH_OTHER);
+      k_random_start<<<dim3(nb, nk), 256, 0, st>>>(w->SB[0], Lpad, sK, dL, nb, 0x5eed1234abcdULL);
+      ctx->launches++;
+    }
+  }
+  std::vector<int> nvh(3 * nk, nb);
+  cudaMemcpy(dnv, nvh.data(), 3 * nk * sizeof(int), cudaMemcpyHostToDevice);
+  hs = cholqr(ctx, w, gemm, w->SB[0], 0, nb, dnv, 2, failed);
+  if (hs != HW_OK) return hs;
+  for (int b = 0; b < nk; ++b)
+    if (failed[b]) return hw_fail(ctx, HW_EINVAL, "start block is rank deficient");
+  const bool mixed = prec == HW_MIXED;
+  bool fp64_products = !mixed;
+  hs = apply_block(ctx, w, kidx, w->SB[0], w->HSB[0], 0, nb, fp64_products);
+  if (hs != HW_OK) return hs;
+  // Rayleigh-Ritz on X alone
+  {
+    const int n = nb + (nb & 1);
+    gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, (int)Lpad, 1.0, w->SB[0], Lpad, sK, w->HSB[0], Lpad, sK, 0.0, w->A, n,
+         (int64_t)n * n, nk);
+    std::vector<int> z(nk, 0);
+    cudaMemcpyAsync(dnv + nk, z.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dnv + 2 * nk, z.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
+    {
+      ProfScope ps_(ctx, HW_PH_OTHER);
+      k_pad_rr<<<dim3(8, nk), 256, 0, st>>>(w->A, n, nb, 0, 0, dnv + nk, dnv + 2 * nk);
+      ctx->launches++;
+    }
+    cudaError_t e;
+    {
+      ProfScope ps_(ctx, HW_PH_EIG);
+      dense_hermitize(st, w->A, n, nk);
+      e = dense_heev(w->dw, st, w->A, n, nk, w->w, w->Z, w->status, 1e-13);
+      ctx->launches += 4;
+    }
+    if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
+    gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nb, 1.0, w->SB[0], Lpad, sK, w->Z, n, (int64_t)n * n, 0.0,
+         w->SB[1], Lpad, sK, nk);
+    gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nb, 1.0, w->HSB[0], Lpad, sK, w->Z, n, (int64_t)n * n, 0.0,
+         w->HSB[1], Lpad, sK, nk);
+    for (int b = 0; b < nk; ++b)
+      cudaMemcpyAsync(w->theta + (size_t)b * nb, w->w + (size_t)b * n, nb * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    cur = 1;
+  }
+  int np = 0;                                  // P block width (uniform)
+  std::vector<int> npv(nk, 0);                 // valid P columns per k-point
+  std::vector<char> done(nk, 0);
+  std::vector<int> it_done(nk, maxit);
+  std::vector<double> resh((size_t)nk * nb), thh((size_t)nk * nb);
+  bool refreshed = !mixed;
+  int it = 0;
+  hw_status final_status = HW_ENOTCONV;
+  for (it = 0; it <= maxit; ++it) {
+    double2* S = w->SB[cur];
+    double2* HS = w->HSB[cur];
+    {
+      ProfScope ps_(ctx, HW_PH_OTHER);
+      k_residual<<<dim3(nb, nk), 256, 0, st>>>(S, HS, Lpad, sK, w->theta, nb, w->R, w->res);
+      ctx->launches++;
+    }
+    cudaMemcpyAsync(resh.data(), w->res, resh.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(thh.data(), w->theta, thh.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    int dstat = 0;
+    cudaMemcpyAsync(&dstat, w->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
+    if (dstat == HW_ETIMEOUT) return hw_fail(ctx, HW_ETIMEOUT, "dense eigensolver barrier timed out");
+    if (gemm.st != CUBLAS_STATUS_SUCCESS) return hw_fail(ctx, HW_ECUDA, "cuBLAS failure");
+    // mixed: refresh HX in FP64 once the residuals are small, and before accepting convergence
+    double maxres = 0.0;
+    std::vector<int> claim(nk, 0);
+    int nclaim = 0;
+    for (int b = 0; b < nk; ++b) {
+      if (done[b]) continue;
+      double mr = 0.0;
+      for (int j = 0; j < n_eig; ++j) mr = std::max(mr, resh[(size_t)b * nb + j]);
+      maxres = std::max(maxres, mr);
+      if (mr <= tol) {
+        claim[b] = 1;
+        ++nclaim;
+      }
+    }
+    if (mixed && ((!refreshed && maxres < 1e-3) || nclaim > 0)) {
+      std::vector<int> which(nk, 0);
+      for (int b = 0; b < nk; ++b) which[b] = !done[b] && (!refreshed || claim[b]);
+      hs = apply_block(ctx, w, kidx, S, HS, 0, nb, true, &which);
+      if (hs != HW_OK) return hs;
+      refreshed = true;
+      {
+        ProfScope ps_(ctx, HW_PH_OTHER);
+        k_residual<<<dim3(nb, nk), 256, 0, st>>>(S, HS, Lpad, sK, w->theta, nb, w->R, w->res);
+        ctx->launches++;
+      }
+      cudaMemcpyAsync(resh.data(), w->res, resh.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+      e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
+      for (int b = 0; b < nk; ++b) {
+        claim[b] = 0;
+        if (done[b]) continue;
+        double mr = 0.0;
+        for (int j = 0; j < n_eig; ++j) mr = std::max(mr, resh[(size_t)b * nb + j]);
+        claim[b] = mr <= tol;
+      }
+    } else if (!mixed) {
+      // FP64 products: residuals are already exact
+    }
+    for (int b = 0; b < nk; ++b) {
+      if (done[b] || !claim[b]) continue;
+      done[b] = 1;
+      it_done[b] = it;
+      for (int j = 0; j < n_eig; ++j) {
+        evals[(size_t)b * n_eig + j] = thh[(size_t)b * nb + j];
+        if (resid) resid[(size_t)b * n_eig + j] = resh[(size_t)b * nb + j];
+      }
+      if (evecs && evecs[b])
+        cudaMemcpy2DAsync(evecs[b], ld_evecs * 16, S + (size_t)b * sK, Lpad * 16, Lb[b] * 16, n_eig,
+                          cudaMemcpyDeviceToDevice, st);
+    }
+    bool all = true;
+    for (int b = 0; b < nk; ++b) all = all && done[b];
+    if (all) {
+      final_status = HW_OK;
+      break;
+    }
+    if (it == maxit) break;
+    // ---- active sets (soft locking)
+    std::vector<int> act((size_t)nk * nb, -1);
+    std::vector<int> nav(nk, 0);
+    int na = 0;
+    for (int b = 0; b < nk; ++b) {
+      if (done[b]) continue;
+      for (int j = 0; j < nb; ++j)
+        if (resh[(size_t)b * nb + j] > tol) act[(size_t)b * nb + nav[b]++] = j;
+      na = std::max(na, nav[b]);
+    }
+    if (na == 0) na = 1;  // converged residuals but claim not verified yet: keep one direction
+    cudaMemcpyAsync(w->iact, act.data(), act.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    std::vector<int> nvall(3 * nk);
+    for (int b = 0; b < nk; ++b) {
+      nvall[b] = nav[b];
+      nvall[nk + b] = npv[b];
+      nvall[2 * nk + b] = nav[b];
+    }
+    cudaMemcpyAsync(dnv, nvall.data(), 3 * nk * sizeof(int), cudaMemcpyHostToDevice, st);
+    const int woff = nb + np;
+    // ---- W = K R[:, act]
+    {
+      ProfScope ps_(ctx, HW_PH_OTHER);
+      k_gather_w<<<dim3(na, nk), 256, 0, st>>>(w->R, nb, Lpad, w->iact, na, S, sK, woff);
+      ctx->launches++;
+    }
+    {
+      Blocks blk;
+      blk.nslot = nk;
+      for (int b = 0; b < nk; ++b) {
+        blk.x[b] = reinterpret_cast<const double*>(S + (size_t)b * sK + (size_t)woff * Lpad);
+        blk.y[b] = reinterpret_cast<double*>(S + (size_t)b * sK + (size_t)woff * Lpad);
+        blk.kb[b] = kidx[b];
+      }
+      if (precond_kind == HW_PRECOND_TPA) {
+        e = launch_tpa(ctx, blk, na, Lpad);
+      } else if (precond_kind == HW_PRECOND_LEARNED) {
+        // Ritz value of each W column: theta of its source column
+        std::vector<double> rz((size_t)nk * na, 0.0);
+        for (int b = 0; b < nk; ++b)
+          for (int i = 0; i < nav[b]; ++i) rz[(size_t)b * na + i] = thh[(size_t)b * nb + act[(size_t)b * nb + i]];
+        cudaMemcpyAsync(w->C, rz.data(), rz.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+        std::vector<const double*> rp(nk);
+        for (int b = 0; b < nk; ++b) rp[b] = reinterpret_cast<const double*>(w->C) + (size_t)b * na;
+        e = launch_precond_learned(ctx, blk, na, Lpad, rp.data());
+        cudaStreamSynchronize(st);
+      } else {
+        e = cudaSuccess;
+      }
+      if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("precond: ") + cudaGetErrorString(e));
+    }
+    // ---- project out [X P], twice
+    for (int pass = 0; pass < 2; ++pass) {
+      gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb + np, na, (int)Lpad, 1.0, S, Lpad, sK, S + (size_t)woff * Lpad, Lpad, sK,
+           0.0, w->C, nb + np, (int64_t)2 * nb * nb, nk);
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, na, nb + np, -1.0, S, Lpad, sK, w->C, nb + np,
+           (int64_t)2 * nb * nb, 1.0, S + (size_t)woff * Lpad, Lpad, sK, nk);
+    }
+    // ---- Cholesky-QR of W (twice)
+    hs = cholqr(ctx, w, gemm, S, woff, na, dnv, 2, failed);
+    if (hs != HW_OK) return hs;
+    bool anyfail = false;
+    for (int b = 0; b < nk; ++b)
+      if (failed[b] && nav[b] > 0) {
+        anyfail = true;
+        nav[b] = 0;   // drop this k-point's search directions for this iteration
+      }
+    if (anyfail) {
+      for (int b = 0; b < nk; ++b) nvall[2 * nk + b] = nav[b];
+      for (int b = 0; b < nk; ++b)
+        if (nav[b] == 0)
+          cudaMemsetAsync(S + (size_t)b * sK + (size_t)woff * Lpad, 0, (size_t)Lpad * na * sizeof(double2), st);
+      cudaMemcpyAsync(dnv, nvall.data(), 3 * nk * sizeof(int), cudaMemcpyHostToDevice, st);
+    }
+    // ---- HW
+    hs = apply_block(ctx, w, kidx, S, HS, woff, na, fp64_products);
+    if (hs != HW_OK) return hs;
+    // ---- Rayleigh-Ritz on S = [X P W]
+    const int nS = nb + np + na;
+    const int n = nS + (nS & 1);
+    gemm(CUBLAS_OP_C, CUBLAS_OP_N, nS, nS, (int)Lpad, 1.0, S, Lpad, sK, HS, Lpad, sK, 0.0, w->A, n, (int64_t)n * n, nk);
+    {
+      ProfScope ps_(ctx, HW_PH_OTHER);
+      k_pad_rr<<<dim3(8, nk), 256, 0, st>>>(w->A, n, nb, np, na, dnv + nk, dnv + 2 * nk);
+      ctx->launches++;
+    }
+    {
+      ProfScope ps_(ctx, HW_PH_EIG);
+      dense_hermitize(st, w->A, n, nk);
+      e = dense_heev(w->dw, st, w->A, n, nk, w->w, w->Z, w->status, 1e-13);
+      ctx->launches += 4;
+    }
+    if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
+    const int nxt = 1 - cur;
+    double2* S2 = w->SB[nxt];
+    double2* HS2 = w->HSB[nxt];
+    gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nS, 1.0, S, Lpad, sK, w->Z, n, (int64_t)n * n, 0.0, S2, Lpad, sK, nk);
+    gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nS, 1.0, HS, Lpad, sK, w->Z, n, (int64_t)n * n, 0.0, HS2, Lpad, sK, nk);
+    for (int b = 0; b < nk; ++b)
+      cudaMemcpyAsync(w->theta + (size_t)b * nb, w->w + (size_t)b * n, nb * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    // ---- P = S Y (active columns), Y orthogonal to Z[:, :nb] and orthonormal
+    {
+      ProfScope ps_(ctx, HW_PH_OTHER);
+      k_build_y<<<dim3(na, nk), 128, 0, st>>>(w->Z, n, nb, w->iact, na, w->Y);
+      ctx->launches++;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, na, n, 1.0, w->Z, n, (int64_t)n * n, w->Y, n, (int64_t)n * na, 0.0, w->C, nb,
+           (int64_t)2 * nb * nb, nk);
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, na, nb, -1.0, w->Z, n, (int64_t)n * n, w->C, nb, (int64_t)2 * nb * nb, 1.0,
+           w->Y, n, (int64_t)n * na, nk);
+    }
+    // small-space Cholesky-QR of Y
+    bool pfail = false;
+    for (int pass = 0; pass < 2; ++pass) {
+      gemm(CUBLAS_OP_C, CUBLAS_OP_N, na, na, n, 1.0, w->Y, n, (int64_t)n * na, w->Y, n, (int64_t)n * na, 0.0, w->G, na,
+           (int64_t)na * na, nk);
+      {
+        ProfScope ps_(ctx, HW_PH_OTHER);
+        k_pad_gram<<<dim3(8, nk), 256, 0, st>>>(w->G, na, dnv + 2 * nk);
+        ctx->launches++;
+      }
+      {
+        ProfScope ps_(ctx, HW_PH_CHOL);
+        dense_hermitize(st, w->G, na, nk);
+        dense_chol(st, w->G, na, nk, w->fail);
+        dense_trinv(st, w->G, w->Ui, na, nk);
+        ctx->launches += 3;
+      }
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, na, na, 1.0, w->Y, n, (int64_t)n * na, w->Ui, na, (int64_t)na * na, 0.0, w->Y2,
+           n, (int64_t)n * na, nk);
+      std::swap(w->Y, w->Y2);
+      std::vector<int> f(nk);
+      cudaMemcpyAsync(f.data(), w->fail, nk * sizeof(int), cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+      for (int b = 0; b < nk; ++b)
+        if (f[b] && nav[b] > 0) pfail = true;
+    }
+    if (pfail) {
+      np = 0;   // restart the conjugate directions everywhere
+      std::fill(npv.begin(), npv.end(), 0);
+    } else {
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, na, nS, 1.0, S, Lpad, sK, w->Y, n, (int64_t)n * na, 0.0,
+           S2 + (size_t)nb * Lpad, Lpad, sK, nk);
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, na, nS, 1.0, HS, Lpad, sK, w->Y, n, (int64_t)n * na, 0.0,
+           HS2 + (size_t)nb * Lpad, Lpad, sK, nk);
+      np = na;
+      npv = nav;
+    }
+    cur = nxt;
+  }
+  // k-points that never converged: report the last Ritz values
+  for (int b = 0; b < nk; ++b) {
+    if (!done[b]) {
+      for (int j = 0; j < n_eig; ++j) {
+        evals[(size_t)b * n_eig + j] = thh[(size_t)b * nb + j];
+        if (resid) resid[(size_t)b * n_eig + j] = resh[(size_t)b * nb + j];
+      }
+      if (evecs && evecs[b])
+        cudaMemcpy2DAsync(evecs[b], ld_evecs * 16, w->SB[cur] + (size_t)b * sK, Lpad * 16, Lb[b] * 16, n_eig,
+                          cudaMemcpyDeviceToDevice, st);
+    }
+    if (iters) iters[b] = it_done[b];
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
+  if (final_status != HW_OK) return hw_fail(ctx, HW_ENOTCONV, "maxit reached before convergence");
+  return HW_OK;
 }

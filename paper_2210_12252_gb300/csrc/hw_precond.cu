@@ -74,7 +74,9 @@ cudaError_t launch_tpa(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld) {
     a.L[i] = ctx->hb.L[blk.kb[i]];
   }
   a.blk = blk;
+  ProfScope ps(ctx, HW_PH_PRECOND);
   k_tpa<<<dim3(ns, blk.nslot), TPA_THREADS, 0, ctx->stream>>>(a);
+  ctx->launches++;
   return cudaGetLastError();
 }
 

@@ -1,0 +1,108 @@
+"""GPU block eigensolver (hw_solve_eigs) against the oracle's direct diagonalisation.
+
+Bars: FP64 path within 1e-8 Ha of the dense oracle eigenvalues; mixed path (FP32 transforms,
+FP64 Gram / Rayleigh-Ritz / residual check) within 1e-6 Ha; every reported residual below the
+requested tolerance.  Stored eigenvalues under tests/golden/ were written by
+tests/golden/make_golden.py from the oracle alone.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import basis as B
+from oracle import hamiltonian as Hm
+from oracle import potential as P
+from paper_2210_12252_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden(name):
+    return np.loadtxt(os.path.join(GOLD, name))
+
+
+@pytest.fixture(scope="module")
+def hwmod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_12252_gb300 import build
+    build.build()
+    from paper_2210_12252_gb300 import helicwave
+    return helicwave
+
+
+def make_ctx(hwmod, w, etas=None, ecuts=None):
+    ctx = hwmod.Context(0)
+    L = ctx.setup_basis(w.geom, w.etas if etas is None else etas, None, ecuts)
+    ctx.build_potential(w.atoms)
+    return ctx, L
+
+
+def test_tiny_fp64_matches_dense_oracle(hwmod):
+    w = inputs.tiny()
+    ctx, L = make_ctx(hwmod, w)
+    r = ctx.solve_eigs([0], w.n_eig, tol=1e-6, maxit=400, vectors=True)
+    assert r["converged"]
+    ref = golden("tiny_eigs.txt")[: w.n_eig]
+    assert np.abs(r["evals"][0] - ref).max() < 1e-8
+    assert r["resid"].max() <= 1e-6
+    # returned vectors: orthonormal and eigenvectors of the device H
+    X = r["evecs"][0]
+    G = (X.conj() @ X.T).cpu().numpy()
+    assert np.abs(G - np.eye(w.n_eig)).max() < 1e-10
+    HX = ctx.apply_H(0, X.contiguous())
+    res = torch.linalg.norm(HX - torch.from_numpy(r["evals"][0]).cuda()[:, None] * X, dim=1)
+    assert res.max().item() <= 1.01e-6
+
+
+def test_tiny_zero_potential_gives_closed_form(hwmod):
+    w = inputs.tiny(zero_potential=True)
+    ctx, L = make_ctx(hwmod, w)
+    r = ctx.solve_eigs([0], w.n_eig, tol=1e-8, maxit=400)
+    g = w.geom
+    b = B.Basis(g.R, g.tau, g.alpha, g.Nr, g.Nth1, g.Nth2)
+    kp = B.KPoint(b, 0.0, 0.0, 0.0)
+    closed = np.sort(kp.ke)[: w.n_eig]
+    assert np.abs(r["evals"][0] - closed).max() < 1e-10
+
+
+@pytest.mark.parametrize("prec,bar", [("fp64", 1e-8), ("mixed", 1e-6)])
+def test_tube_64_eigenpairs(hwmod, prec, bar):
+    w = inputs.tube()
+    ctx, L = make_ctx(hwmod, w)
+    assert L[0] == 5066
+    r = ctx.solve_eigs([0], w.n_eig, tol=1e-6, maxit=500, prec=prec)
+    assert r["converged"], r["iters"]
+    ref = golden("tube_eigs.txt")[: w.n_eig]
+    err = np.abs(r["evals"][0] - ref).max()
+    assert err < bar, err
+    assert r["resid"].max() <= 1e-6
+
+
+def test_batched_kpoints_time_reversal_and_consistency(hwmod):
+    """lambda(eta) = lambda(1 - eta): the spectrum at -eta (time reversal) equals that at
+    1 - eta when the cutoff set stays inside the box; solved in one lockstep batch."""
+    w = inputs.tube()
+    etas = np.array([0.0, 0.23, 0.77, 0.5])
+    ctx, L = make_ctx(hwmod, w, etas=etas)
+    ne = 16
+    r = ctx.solve_eigs([0, 1, 2, 3], ne, tol=1e-6, maxit=500)
+    assert r["converged"]
+    ev = r["evals"]
+    assert np.abs(ev[0] - golden("tube_eigs.txt")[:ne]).max() < 1e-8
+    assert np.abs(ev[1] - ev[2]).max() < 1e-8
+    # the batch equals single-point solves
+    r1 = ctx.solve_eigs([3], ne, tol=1e-6, maxit=500)
+    assert np.abs(r1["evals"][0] - ev[3]).max() < 1e-8
+
+
+def test_not_converged_status_returns_partial_results(hwmod):
+    w = inputs.tiny()
+    ctx, L = make_ctx(hwmod, w)
+    r = ctx.solve_eigs([0], w.n_eig, tol=1e-12, maxit=2)
+    assert not r["converged"]
+    assert np.all(np.isfinite(r["evals"]))
