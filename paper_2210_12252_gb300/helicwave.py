@@ -63,7 +63,12 @@ _SIGS = {
                                 C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p),
                                 _D, C.POINTER(C.c_void_p), C.c_int64, C.POINTER(C.c_int), _D]),
     "hw_synchronize": (C.c_int, [C.c_void_p]),
+    "hw_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "hw_profile_read": (C.c_int, [C.c_void_p, _D, C.POINTER(C.c_int64)]),
+    "hw_launch_count": (C.c_int64, [C.c_void_p]),
 }
+
+PHASES = ["radial_inv", "slab", "radial_fwd", "precond", "gemm", "chol", "eig", "other", "mlp"]
 
 _lib = None
 
@@ -209,6 +214,21 @@ def hw_synchronize(h):
     _check(h, load_library().hw_synchronize(h))
 
 
+def hw_profile(h, enable: bool):
+    _check(h, load_library().hw_profile(h, int(bool(enable))))
+
+
+def hw_profile_read(h):
+    ms = np.zeros(len(PHASES))
+    cnt = np.zeros(len(PHASES), dtype=np.int64)
+    _check(h, load_library().hw_profile_read(h, _dptr(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64))))
+    return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
+
+
+def hw_launch_count(h) -> int:
+    return int(load_library().hw_launch_count(h))
+
+
 # ----------------------------------------------------------------------------- Context
 
 _PREC = {"fp64": HW_FP64, "mixed": HW_MIXED}
@@ -324,3 +344,12 @@ class Context:
 
     def synchronize(self):
         hw_synchronize(self.h)
+
+    def profile(self, enable=True):
+        hw_profile(self.h, enable)
+
+    def profile_read(self):
+        return hw_profile_read(self.h)
+
+    def launch_count(self):
+        return hw_launch_count(self.h)
