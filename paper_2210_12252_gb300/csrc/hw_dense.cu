@@ -15,6 +15,7 @@
 // padding sorts last).
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "hw_common.cuh"
@@ -189,11 +190,11 @@ __device__ bool grid_sync(GridBar* bar, int* status) {
 // ---------------------------------------------------------------------- Jacobi
 struct JacArgs {
   int nprob, n, maxsweep;
-  double tol;           // stop when off(A)_F <= tol * ||A||_F for every problem
+  double tol;           // rotation threshold relative to ||A||_F
   double2* A0;          // [nprob][n*n] input (destroyed)
   double2* A1;          // [nprob][n*n] scratch
   double2* V;           // [nprob][n*n] eigenvectors (columns)
-  double* off;          // [maxsweep+1][nprob] off-norm accumulators (zeroed by the host)
+  int* rotated;         // [maxsweep+1] rotations applied per sweep (zeroed by the host)
   double* fro;          // [nprob] ||A||_F^2 (zeroed by the host)
   GridBar* bar;
   int* status;
@@ -204,17 +205,24 @@ __device__ __forceinline__ int rr_index(int pos, int t, int n) {
   return pos == 0 ? 0 : 1 + (pos - 1 + t) % (n - 1);
 }
 
+// one rotation of the current step: pair (p < q), cos/sin, phase e = c/|c|, and the new
+// diagonal entries of the pair
 struct Rot {
-  double cs, sn;
-  double er, ei;   // e = c / |c|
+  int p, q;
+  double cs, sn, er, ei;
+  double app, aqq;
 };
 
-__device__ __forceinline__ Rot make_rot(const double2* a, int n, int p, int q) {
+__device__ __forceinline__ Rot make_rot(const double2* a, int n, int p, int q, double thr) {
   Rot r;
+  r.p = p;
+  r.q = q;
   const double app = a[p + (size_t)p * n].x, aqq = a[q + (size_t)q * n].x;
   const double2 c = a[p + (size_t)q * n];
   const double ac = hypot(c.x, c.y);
-  if (!(ac > 1e-300)) {
+  r.app = app;
+  r.aqq = aqq;
+  if (!(ac > thr)) {   // negligible coupling: no rotation (keeps padding exactly decoupled)
     r.cs = 1.0; r.sn = 0.0; r.er = 1.0; r.ei = 0.0;
     return r;
   }
@@ -224,17 +232,24 @@ __device__ __forceinline__ Rot make_rot(const double2* a, int n, int p, int q) {
   r.sn = t * r.cs;
   r.er = c.x / ac;
   r.ei = c.y / ac;
+  r.app = app - t * ac;
+  r.aqq = aqq + t * ac;
   return r;
 }
 
-// grid-stride over (problem, block I, block J) and (problem, row, block I)
+// Grid-stride over (problem, block I, block J) and (problem, row, block I).  Every CTA first
+// computes the step's rotations of all problems into shared memory (cheap, one per thread),
+// then applies them; one grid barrier per step.  A sweep without any rotation above the
+// threshold ends the iteration.
 __global__ void __launch_bounds__(256) k_jacobi(JacArgs J) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Rot* rot = reinterpret_cast<Rot*>(smem_raw);   // [nprob][n/2]
+  __shared__ double thr_s[64];
   const int n = J.n, h = n / 2;
   const long nA = (long)J.nprob * h * h;
   const long nV = (long)J.nprob * n * h;
   const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const long nth = (long)gridDim.x * blockDim.x;
-  // Frobenius norms
   for (long t = tid; t < (long)J.nprob * n * n; t += nth) {
     const int b = (int)(t / ((long)n * n));
     const double2 v = J.A0[t];
@@ -242,13 +257,24 @@ __global__ void __launch_bounds__(256) k_jacobi(JacArgs J) {
     if (m2 < 1e18) atomicAdd(&J.fro[b], m2);   // padding entries (>= 1e9) do not count
   }
   if (!grid_sync(J.bar, J.status)) return;
+  for (int b = threadIdx.x; b < J.nprob && b < 64; b += blockDim.x)
+    thr_s[b] = J.tol * sqrt(J.fro[b]) + 1e-300;
+  __syncthreads();
   double2* Acur = J.A0;
   double2* Anext = J.A1;
   int sweep = 0;
   for (; sweep < J.maxsweep; ++sweep) {
-    double* offacc = J.off + (size_t)sweep * J.nprob;
+    int nrot = 0;
     for (int step = 0; step < n - 1; ++step) {
-      const bool last = (step == n - 2);
+      // rotations of this step (identical in every CTA)
+      for (int i = threadIdx.x; i < J.nprob * h; i += blockDim.x) {
+        const int b = i / h, I = i - b * h;
+        const int pI = rr_index(I, step, n), qI = rr_index(n - 1 - I, step, n);
+        const Rot r = make_rot(Acur + (size_t)b * n * n, n, min(pI, qI), max(pI, qI), thr_s[b < 64 ? b : 63]);
+        rot[i] = r;
+        if (blockIdx.x == 0 && r.sn != 0.0) nrot = 1;
+      }
+      __syncthreads();
       for (long t = tid; t < nA + nV; t += nth) {
         if (t < nA) {
           const int b = (int)(t / ((long)h * h));
@@ -256,62 +282,51 @@ __global__ void __launch_bounds__(256) k_jacobi(JacArgs J) {
           const int I = rem % h, Jb = rem / h;
           const double2* a = Acur + (size_t)b * n * n;
           double2* an = Anext + (size_t)b * n * n;
-          const int pI = rr_index(I, step, n), qI = rr_index(n - 1 - I, step, n);
-          const int pJ = rr_index(Jb, step, n), qJ = rr_index(n - 1 - Jb, step, n);
-          const int p1 = min(pI, qI), q1 = max(pI, qI);
-          const int p2 = min(pJ, qJ), q2 = max(pJ, qJ);
-          const Rot r1 = make_rot(a, n, p1, q1);
+          const Rot r1 = rot[b * h + I];
+          const int p1 = r1.p, q1 = r1.q;
           if (I == Jb) {
-            const double app = a[p1 + (size_t)p1 * n].x, aqq = a[q1 + (size_t)q1 * n].x;
-            const double2 c = a[p1 + (size_t)q1 * n];
-            const double ac = hypot(c.x, c.y);
-            const double t1 = r1.cs != 0.0 ? r1.sn / r1.cs : 0.0;
-            an[p1 + (size_t)p1 * n] = make_double2(app - t1 * ac, 0.0);
-            an[q1 + (size_t)q1 * n] = make_double2(aqq + t1 * ac, 0.0);
-            an[p1 + (size_t)q1 * n] = make_double2(0.0, 0.0);
-            an[q1 + (size_t)p1 * n] = make_double2(0.0, 0.0);
+            an[p1 + (size_t)p1 * n] = make_double2(r1.app, 0.0);
+            an[q1 + (size_t)q1 * n] = make_double2(r1.aqq, 0.0);
+            if (r1.sn != 0.0) {
+              an[p1 + (size_t)q1 * n] = make_double2(0.0, 0.0);
+              an[q1 + (size_t)p1 * n] = make_double2(0.0, 0.0);
+            } else {
+              an[p1 + (size_t)q1 * n] = a[p1 + (size_t)q1 * n];
+              an[q1 + (size_t)p1 * n] = a[q1 + (size_t)p1 * n];
+            }
             continue;
           }
-          const Rot r2 = make_rot(a, n, p2, q2);
-          // M = J1^H A_blk:  row p1' = cs A[p1,:] - sn e1 A[q1,:];  row q1' = sn A[p1,:] + cs e1 A[q1,:]
-          double2 A_pp = a[p1 + (size_t)p2 * n], A_pq = a[p1 + (size_t)q2 * n];
-          double2 A_qp = a[q1 + (size_t)p2 * n], A_qq = a[q1 + (size_t)q2 * n];
-          auto e_mul = [](double er, double ei, double2 z) { return make_double2(er * z.x - ei * z.y, er * z.y + ei * z.x); };
-          const double2 eq_p = e_mul(r1.er, r1.ei, A_qp), eq_q = e_mul(r1.er, r1.ei, A_qq);
-          double2 M_pp = make_double2(r1.cs * A_pp.x - r1.sn * eq_p.x, r1.cs * A_pp.y - r1.sn * eq_p.y);
-          double2 M_pq = make_double2(r1.cs * A_pq.x - r1.sn * eq_q.x, r1.cs * A_pq.y - r1.sn * eq_q.y);
-          double2 M_qp = make_double2(r1.sn * A_pp.x + r1.cs * eq_p.x, r1.sn * A_pp.y + r1.cs * eq_p.y);
-          double2 M_qq = make_double2(r1.sn * A_pq.x + r1.cs * eq_q.x, r1.sn * A_pq.y + r1.cs * eq_q.y);
-          // M J2: col p2' = cs M[:,p2] - sn conj(e2) M[:,q2];  col q2' = sn M[:,p2] + cs conj(e2) M[:,q2]
-          const double2 cq_p = e_mul(r2.er, -r2.ei, M_pq), cq_q = e_mul(r2.er, -r2.ei, M_qq);
-          const double2 o_pp = make_double2(r2.cs * M_pp.x - r2.sn * cq_p.x, r2.cs * M_pp.y - r2.sn * cq_p.y);
-          const double2 o_qp = make_double2(r2.cs * M_qp.x - r2.sn * cq_q.x, r2.cs * M_qp.y - r2.sn * cq_q.y);
-          const double2 o_pq = make_double2(r2.sn * M_pp.x + r2.cs * cq_p.x, r2.sn * M_pp.y + r2.cs * cq_p.y);
-          const double2 o_qq = make_double2(r2.sn * M_qp.x + r2.cs * cq_q.x, r2.sn * M_qp.y + r2.cs * cq_q.y);
-          an[p1 + (size_t)p2 * n] = o_pp;
-          an[p1 + (size_t)q2 * n] = o_pq;
-          an[q1 + (size_t)p2 * n] = o_qp;
-          an[q1 + (size_t)q2 * n] = o_qq;
-          if (last) {
-            const double s = o_pp.x * o_pp.x + o_pp.y * o_pp.y + o_pq.x * o_pq.x + o_pq.y * o_pq.y +
-                             o_qp.x * o_qp.x + o_qp.y * o_qp.y + o_qq.x * o_qq.x + o_qq.y * o_qq.y;
-            atomicAdd(&offacc[b], s);
-          }
+          const Rot r2 = rot[b * h + Jb];
+          const int p2 = r2.p, q2 = r2.q;
+          const double2 A_pp = a[p1 + (size_t)p2 * n], A_pq = a[p1 + (size_t)q2 * n];
+          const double2 A_qp = a[q1 + (size_t)p2 * n], A_qq = a[q1 + (size_t)q2 * n];
+          // M = J1^H A_blk: row p = cs A[p,:] - sn e1 A[q,:];  row q = sn A[p,:] + cs e1 A[q,:]
+          const double2 eq_p = make_double2(r1.er * A_qp.x - r1.ei * A_qp.y, r1.er * A_qp.y + r1.ei * A_qp.x);
+          const double2 eq_q = make_double2(r1.er * A_qq.x - r1.ei * A_qq.y, r1.er * A_qq.y + r1.ei * A_qq.x);
+          const double2 M_pp = make_double2(r1.cs * A_pp.x - r1.sn * eq_p.x, r1.cs * A_pp.y - r1.sn * eq_p.y);
+          const double2 M_pq = make_double2(r1.cs * A_pq.x - r1.sn * eq_q.x, r1.cs * A_pq.y - r1.sn * eq_q.y);
+          const double2 M_qp = make_double2(r1.sn * A_pp.x + r1.cs * eq_p.x, r1.sn * A_pp.y + r1.cs * eq_p.y);
+          const double2 M_qq = make_double2(r1.sn * A_pq.x + r1.cs * eq_q.x, r1.sn * A_pq.y + r1.cs * eq_q.y);
+          // M J2: col p = cs M[:,p] - sn conj(e2) M[:,q];  col q = sn M[:,p] + cs conj(e2) M[:,q]
+          const double2 cq_p = make_double2(r2.er * M_pq.x + r2.ei * M_pq.y, r2.er * M_pq.y - r2.ei * M_pq.x);
+          const double2 cq_q = make_double2(r2.er * M_qq.x + r2.ei * M_qq.y, r2.er * M_qq.y - r2.ei * M_qq.x);
+          an[p1 + (size_t)p2 * n] = make_double2(r2.cs * M_pp.x - r2.sn * cq_p.x, r2.cs * M_pp.y - r2.sn * cq_p.y);
+          an[q1 + (size_t)p2 * n] = make_double2(r2.cs * M_qp.x - r2.sn * cq_q.x, r2.cs * M_qp.y - r2.sn * cq_q.y);
+          an[p1 + (size_t)q2 * n] = make_double2(r2.sn * M_pp.x + r2.cs * cq_p.x, r2.sn * M_pp.y + r2.cs * cq_p.y);
+          an[q1 + (size_t)q2 * n] = make_double2(r2.sn * M_qp.x + r2.cs * cq_q.x, r2.sn * M_qp.y + r2.cs * cq_q.y);
         } else {
           const long u = t - nA;
           const int b = (int)(u / ((long)n * h));
           const int rem = (int)(u - (long)b * n * h);
           const int row = rem % n, I = rem / n;
-          const double2* a = Acur + (size_t)b * n * n;
+          const Rot r = rot[b * h + I];
+          if (r.sn == 0.0) continue;
           double2* v = J.V + (size_t)b * n * n;
-          const int pI = rr_index(I, step, n), qI = rr_index(n - 1 - I, step, n);
-          const int p1 = min(pI, qI), q1 = max(pI, qI);
-          const Rot r = make_rot(a, n, p1, q1);
-          const double2 vp = v[row + (size_t)p1 * n], vq = v[row + (size_t)q1 * n];
+          const double2 vp = v[row + (size_t)r.p * n], vq = v[row + (size_t)r.q * n];
           // V' col p = cs vp - sn conj(e) vq;  col q = sn vp + cs conj(e) vq
           const double2 cv = make_double2(r.er * vq.x + r.ei * vq.y, r.er * vq.y - r.ei * vq.x);
-          v[row + (size_t)p1 * n] = make_double2(r.cs * vp.x - r.sn * cv.x, r.cs * vp.y - r.sn * cv.y);
-          v[row + (size_t)q1 * n] = make_double2(r.sn * vp.x + r.cs * cv.x, r.sn * vp.y + r.cs * cv.y);
+          v[row + (size_t)r.p * n] = make_double2(r.cs * vp.x - r.sn * cv.x, r.cs * vp.y - r.sn * cv.y);
+          v[row + (size_t)r.q * n] = make_double2(r.sn * vp.x + r.cs * cv.x, r.sn * vp.y + r.cs * cv.y);
         }
       }
       if (!grid_sync(J.bar, J.status)) return;
@@ -319,11 +334,13 @@ __global__ void __launch_bounds__(256) k_jacobi(JacArgs J) {
       Acur = Anext;
       Anext = tmp;
     }
-    // every problem converged?
-    bool done = true;
-    for (int b = 0; b < J.nprob; ++b)
-      if (offacc[b] > J.tol * J.tol * J.fro[b]) done = false;
-    if (done) {
+    // CTA 0 reports whether this sweep rotated anything (visible after the next barrier)
+    if (blockIdx.x == 0) {
+      nrot = __syncthreads_or(nrot);
+      if (threadIdx.x == 0) J.rotated[sweep] = nrot;
+    }
+    if (!grid_sync(J.bar, J.status)) return;
+    if (*((volatile int*)&J.rotated[sweep]) == 0) {
       ++sweep;
       break;
     }
@@ -364,7 +381,7 @@ __global__ void k_identity(double2* V, int n, int nprob) {
 struct DenseWork {
   double2* A1 = nullptr;
   double2* V = nullptr;
-  double* off = nullptr;
+  int* rotated = nullptr;
   double* fro = nullptr;
   GridBar* bar = nullptr;
   int* sweeps = nullptr;
@@ -379,13 +396,13 @@ cudaError_t dense_alloc(DenseWork*& dw, size_t cap_elems, int maxnprob) {
   if (dw->cap >= cap_elems && dw->A1) return cudaSuccess;
   if (dw->A1) cudaFree(dw->A1);
   if (dw->V) cudaFree(dw->V);
-  if (dw->off) cudaFree(dw->off);
+  if (dw->rotated) cudaFree(dw->rotated);
   if (dw->fro) cudaFree(dw->fro);
   if (dw->bar) cudaFree(dw->bar);
   if (dw->sweeps) cudaFree(dw->sweeps);
   cudaError_t e = cudaMalloc((void**)&dw->A1, cap_elems * sizeof(double2));
   if (e == cudaSuccess) e = cudaMalloc((void**)&dw->V, cap_elems * sizeof(double2));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&dw->off, (size_t)(dw->maxsweep + 1) * maxnprob * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dw->rotated, (size_t)(dw->maxsweep + 1) * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&dw->fro, (size_t)maxnprob * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&dw->bar, sizeof(GridBar));
   if (e == cudaSuccess) e = cudaMalloc((void**)&dw->sweeps, sizeof(int));
@@ -395,15 +412,16 @@ cudaError_t dense_alloc(DenseWork*& dw, size_t cap_elems, int maxnprob) {
     int dev = 0, nsm = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi, 256, 0);
-    dw->coop_blocks = nsm * std::max(1, std::min(occ, 2));
+    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi, 256, 200 * 1024);
+    dw->coop_blocks = nsm * std::max(1, std::min(occ, 1));
   }
   return e;
 }
 
 void dense_free(DenseWork*& dw) {
   if (!dw) return;
-  for (void* p : {(void*)dw->A1, (void*)dw->V, (void*)dw->off, (void*)dw->fro, (void*)dw->bar,
+  for (void* p : {(void*)dw->A1, (void*)dw->V, (void*)dw->rotated, (void*)dw->fro, (void*)dw->bar,
                   (void*)dw->sweeps})
     if (p) cudaFree(p);
   delete dw;
@@ -417,7 +435,7 @@ cudaError_t dense_heev(DenseWork* dw, cudaStream_t st, double2* A, int n, int np
   const size_t elems = (size_t)nprob * n * n;
   if (elems > dw->cap || (n & 1)) return cudaErrorInvalidValue;
   k_identity<<<256, 256, 0, st>>>(dw->V, n, nprob);
-  cudaMemsetAsync(dw->off, 0, (size_t)(dw->maxsweep + 1) * nprob * sizeof(double), st);
+  cudaMemsetAsync(dw->rotated, 0, (size_t)(dw->maxsweep + 1) * sizeof(int), st);
   cudaMemsetAsync(dw->fro, 0, (size_t)nprob * sizeof(double), st);
   cudaMemsetAsync(dw->bar, 0, sizeof(GridBar), st);
   JacArgs ja;
@@ -428,13 +446,19 @@ cudaError_t dense_heev(DenseWork* dw, cudaStream_t st, double2* A, int n, int np
   ja.A0 = A;
   ja.A1 = dw->A1;
   ja.V = dw->V;
-  ja.off = dw->off;
+  ja.rotated = dw->rotated;
   ja.fro = dw->fro;
   ja.bar = dw->bar;
   ja.status = status;
   ja.sweeps_done = dw->sweeps;
   void* args[] = {&ja};
-  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(dw->coop_blocks), dim3(256), args, 0, st);
+  const size_t smem = (size_t)nprob * (n / 2) * sizeof(Rot);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  // grid: enough CTAs for ~2 items per thread, at most the co-resident count
+  const long items = (long)nprob * (n / 2) * (n / 2) + (long)nprob * n * (n / 2);
+  int blocks = (int)std::min<long>(dw->coop_blocks, std::max<long>(8, (items + 511) / 512));
+  cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaError_t e = cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(blocks), dim3(256), args, smem, st);
   if (e != cudaSuccess) return e;
   k_eig_sort<<<nprob, 256, 0, st>>>(A, dw->V, n, w, Z);
   return cudaGetLastError();

@@ -355,7 +355,6 @@ extern "C" hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx_in, int 
   cudaStream_t st = ctx->stream;
   Gemm gemm{ctx};
   const int64_t sK = Lpad * 3 * nb;
-  const int ne = w->ne;
   std::vector<int64_t> Lb(nk);
   for (int b = 0; b < nk; ++b) Lb[b] = ctx->hb.L[kidx[b]];
   int64_t* dL = nullptr;
@@ -420,7 +419,7 @@ extern "C" hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx_in, int 
     {
       ProfScope ps_(ctx, HW_PH_EIG);
       dense_hermitize(st, w->A, n, nk);
-      e = dense_heev(w->dw, st, w->A, n, nk, w->w, w->Z, w->status, 1e-13);
+      e = dense_heev(w->dw, st, w->A, n, nk, w->w, w->Z, w->status, 1e-14);
       ctx->launches += 4;
     }
     if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
@@ -602,7 +601,7 @@ extern "C" hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx_in, int 
     {
       ProfScope ps_(ctx, HW_PH_EIG);
       dense_hermitize(st, w->A, n, nk);
-      e = dense_heev(w->dw, st, w->A, n, nk, w->w, w->Z, w->status, 1e-13);
+      e = dense_heev(w->dw, st, w->A, n, nk, w->w, w->Z, w->status, 1e-14);
       ctx->launches += 4;
     }
     if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
