@@ -157,6 +157,50 @@ hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx, int n_eig, int blo
                         double* evals, double* const* evecs, int64_t ld_evecs, int* iters,
                         double* resid);
 
+/* ---- learned per-mode preconditioner (an extension refining the TPA diagonal) ----------
+ * Network: x_i = [KE_i/10, (m-eta)/M, (n Ncyc-nu)/N, k/K, theta/10, Vd_i/10] (Hartree),
+ * o_i = w3 . silu(W2 silu(W1 x_i + b1) + b2) + b3, scaling s_i = tpa_i exp(o_i) with tpa_i the
+ * TPA factor of the column; Vd_i is the potential's diagonal in mode i (angular mean of V on
+ * each radial node integrated against xi_{n,k}^2).  Parameters: 4673 FP32 values laid out as
+ * W1[64][6] | b1[64] | W2[64][64] | b2[64] | w3[64] | b3; inference and training use their
+ * BF16 roundings with FP32 accumulation; the FP32 values are the Adam master copy. */
+
+/* Install (host FP32 array of n = 4673 values) and reset the optimiser state. */
+hw_status hw_set_mlp(hw_ctx* ctx, const float* params, int64_t n);
+
+/* Copy the current FP32 parameters to the host (n = 4673). */
+hw_status hw_get_mlp(hw_ctx* ctx, float* params, int64_t n);
+
+/* Vd_i of every kept mode of k-point k (host [L_k]); needs a network and a potential. */
+hw_status hw_get_potential_diagonal(hw_ctx* ctx, int k, double* vd);
+
+/* Training loss of a batch of ns columns at k-point k: mean over columns of
+ * 1 - |<s.R, E>|^2 / (|s.R|^2 |E|^2).  R (residuals) and E (target corrections): device
+ * complex128 L_k x ns blocks, leading dimension ld; ritz: host [ns] Ritz values; vdiag: device
+ * [L_k] potential diagonal of the batch's potential (NULL: the installed potential's).
+ * loss: host scalar; grad (nullable): host [4673] gradient w.r.t. the parameters. */
+hw_status hw_mlp_loss_grad(hw_ctx* ctx, int k, const double* R, const double* E,
+                           const double* ritz, int ns, int64_t ld, const double* vdiag,
+                           double* loss, float* grad);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step size lr) on the same batch loss;
+ * loss (host, nullable) receives the loss before the step. */
+hw_status hw_mlp_train_step(hw_ctx* ctx, int k, const double* R, const double* E,
+                            const double* ritz, int ns, int64_t ld, const double* vdiag,
+                            float lr, double* loss);
+
+/* hw_solve_eigs at one k-point that also records training data: at the iterations rec_iters
+ * [n_rec] it stores the residual block R (device rec_R, [n_rec][block][ld] complex128), the
+ * Ritz values and residual norms (host rec_theta / rec_res, [n_rec][block]); after
+ * convergence it stores in rec_E the target correction of every recorded column,
+ * e_j = (I - X X^H) X* X*^H x_j, with X the recorded block and X* the converged n_eig
+ * eigenvectors.  Entries of iterations never reached are left untouched. */
+hw_status hw_solve_eigs_traced(hw_ctx* ctx, int k, int n_eig, int block, double tol, int maxit,
+                               hw_prec prec, int precond_kind, const double* X0, int n_rec,
+                               const int* rec_iters, double* rec_R, double* rec_E,
+                               double* rec_theta, double* rec_res, int64_t ld, double* evals,
+                               int* iters);
+
 /* Wait for all work on the context's stream. */
 hw_status hw_synchronize(hw_ctx* ctx);
 

@@ -104,6 +104,7 @@ void free_basis(hw_ctx* ctx) {
   dfree(ctx->ws.hbuf);
   ctx->ws.cols = 0;
   lobpcg_free(ctx);
+  mlp_free_basis(ctx);
   ctx->have_basis = false;
   ctx->have_V = false;
 }
@@ -159,6 +160,7 @@ void hw_destroy(hw_ctx* ctx) {
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     free_basis(ctx);
+    mlp_free(ctx);
     if (ctx->dflag) cudaFree(ctx->dflag);
     if (ctx->cublas) cublasDestroy(ctx->cublas);
   }
@@ -317,7 +319,12 @@ hw_status hw_set_potential(hw_ctx* ctx, const double* V, int on_device) {
                                               p.Nth2, p.Nr);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "set_potential relayout");
+  ctx->launches++;
   ctx->have_V = true;
+  if (ctx->mlp) {
+    e = mlp_refresh_potential(ctx);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "potential diagonal");
+  }
   return HW_OK;
 }
 
@@ -397,8 +404,13 @@ hw_status hw_apply_precond(hw_ctx* ctx, int k, const double* R, double* Z, int n
     e = (R == Z) ? cudaSuccess
                  : cudaMemcpy2DAsync(Z, ld * 16, R, ld * 16, ctx->hb.L[k] * 16, ns, cudaMemcpyDeviceToDevice,
                                      ctx->stream);
+  } else if (kind == HW_PRECOND_LEARNED) {
+    if (!ctx->mlp) return hw_fail(ctx, HW_ESTATE, "no network installed (hw_set_mlp)");
+    if (!ctx->have_V) return hw_fail(ctx, HW_ESTATE, "no potential installed");
+    if (!ritz) return hw_fail(ctx, HW_EINVAL, "the learned preconditioner needs the Ritz values");
+    e = launch_precond_learned(ctx, blk, ns, ld, &ritz);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   } else {
-    (void)ritz;
     return hw_fail(ctx, HW_EINVAL, "unknown preconditioner kind");
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "apply_precond");

@@ -108,4 +108,9 @@ template <typename T>
 cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld);
 cudaError_t hx_configure(hw_ctx* ctx);
 cudaError_t launch_tpa(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld);
+cudaError_t launch_precond_learned(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld,
+                                   const double* const* ritz);
+cudaError_t mlp_refresh_potential(hw_ctx* ctx);
+void mlp_free_basis(hw_ctx* ctx);
+void mlp_free(hw_ctx* ctx);
 }  // namespace hw

@@ -213,27 +213,41 @@ struct Rot {
   double app, aqq;
 };
 
+// The rotation angle is computed in FP32 (no FP64 division or square root, which are slow
+// on this GPU); the cosine/sine pair and the phase are then renormalised in FP64 by one
+// Newton step for 1/sqrt(x) about 1, so the applied rotation is unitary to FP64 rounding.
+// An inexact angle only leaves a residual coupling ~1e-7 |c| that later sweeps remove.
+__device__ __forceinline__ double renorm(double x2) {   // ~1/sqrt(x2) for x2 = 1 + O(1e-7)
+  const double d = x2 - 1.0;
+  return 1.0 - 0.5 * d + 0.375 * d * d;
+}
+
 __device__ __forceinline__ Rot make_rot(const double2* a, int n, int p, int q, double thr) {
   Rot r;
   r.p = p;
   r.q = q;
   const double app = a[p + (size_t)p * n].x, aqq = a[q + (size_t)q * n].x;
   const double2 c = a[p + (size_t)q * n];
-  const double ac = hypot(c.x, c.y);
+  const double c2 = c.x * c.x + c.y * c.y;
   r.app = app;
   r.aqq = aqq;
-  if (!(ac > thr)) {   // negligible coupling: no rotation (keeps padding exactly decoupled)
+  if (!(c2 > thr * thr)) {   // negligible coupling: no rotation (keeps padding exactly decoupled)
     r.cs = 1.0; r.sn = 0.0; r.er = 1.0; r.ei = 0.0;
     return r;
   }
-  const double zeta = (aqq - app) / (2.0 * ac);
-  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  r.cs = 1.0 / sqrt(1.0 + t * t);
-  r.sn = t * r.cs;
-  r.er = c.x / ac;
-  r.ei = c.y / ac;
-  r.app = app - t * ac;
-  r.aqq = aqq + t * ac;
+  const float acf = sqrtf((float)c2);
+  const float zeta = (float)(aqq - app) / (2.0f * acf);
+  const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+  const float csf = rsqrtf(1.0f + t * t);
+  double cs = csf, sn = (double)(t * csf);
+  double sc = renorm(cs * cs + sn * sn);
+  r.cs = cs * sc;
+  r.sn = sn * sc;
+  const float inv = 1.0f / acf;
+  double er = (double)((float)c.x * inv), ei = (double)((float)c.y * inv);
+  sc = renorm(er * er + ei * ei);
+  r.er = er * sc;
+  r.ei = ei * sc;
   return r;
 }
 
@@ -246,7 +260,8 @@ __global__ void __launch_bounds__(256) k_jacobi(JacArgs J) {
   Rot* rot = reinterpret_cast<Rot*>(smem_raw);   // [nprob][n/2]
   __shared__ double thr_s[64];
   const int n = J.n, h = n / 2;
-  const long nA = (long)J.nprob * h * h;
+  const long nAh = (long)h * (h + 1) / 2;   // lower-triangle blocks per problem
+  const long nA = (long)J.nprob * nAh;
   const long nV = (long)J.nprob * n * h;
   const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const long nth = (long)gridDim.x * blockDim.x;
@@ -277,27 +292,18 @@ __global__ void __launch_bounds__(256) k_jacobi(JacArgs J) {
       __syncthreads();
       for (long t = tid; t < nA + nV; t += nth) {
         if (t < nA) {
-          const int b = (int)(t / ((long)h * h));
-          const int rem = (int)(t - (long)b * h * h);
-          const int I = rem % h, Jb = rem / h;
+          const int b = (int)(t / nAh);
+          const int rem = (int)(t - (long)b * nAh);
+          // rem -> (I, Jb) with I >= Jb (row-major lower triangle of the h x h block grid)
+          int I = (int)((sqrtf(8.0f * rem + 1.0f) - 1.0f) * 0.5f);
+          while ((I + 1) * (I + 2) / 2 <= rem) ++I;
+          while (I * (I + 1) / 2 > rem) --I;
+          const int Jb = rem - I * (I + 1) / 2;
           const double2* a = Acur + (size_t)b * n * n;
           double2* an = Anext + (size_t)b * n * n;
           const Rot r1 = rot[b * h + I];
-          const int p1 = r1.p, q1 = r1.q;
-          if (I == Jb) {
-            an[p1 + (size_t)p1 * n] = make_double2(r1.app, 0.0);
-            an[q1 + (size_t)q1 * n] = make_double2(r1.aqq, 0.0);
-            if (r1.sn != 0.0) {
-              an[p1 + (size_t)q1 * n] = make_double2(0.0, 0.0);
-              an[q1 + (size_t)p1 * n] = make_double2(0.0, 0.0);
-            } else {
-              an[p1 + (size_t)q1 * n] = a[p1 + (size_t)q1 * n];
-              an[q1 + (size_t)p1 * n] = a[q1 + (size_t)p1 * n];
-            }
-            continue;
-          }
           const Rot r2 = rot[b * h + Jb];
-          const int p2 = r2.p, q2 = r2.q;
+          const int p1 = r1.p, q1 = r1.q, p2 = r2.p, q2 = r2.q;
           const double2 A_pp = a[p1 + (size_t)p2 * n], A_pq = a[p1 + (size_t)q2 * n];
           const double2 A_qp = a[q1 + (size_t)p2 * n], A_qq = a[q1 + (size_t)q2 * n];
           // M = J1^H A_blk: row p = cs A[p,:] - sn e1 A[q,:];  row q = sn A[p,:] + cs e1 A[q,:]
@@ -310,10 +316,27 @@ __global__ void __launch_bounds__(256) k_jacobi(JacArgs J) {
           // M J2: col p = cs M[:,p] - sn conj(e2) M[:,q];  col q = sn M[:,p] + cs conj(e2) M[:,q]
           const double2 cq_p = make_double2(r2.er * M_pq.x + r2.ei * M_pq.y, r2.er * M_pq.y - r2.ei * M_pq.x);
           const double2 cq_q = make_double2(r2.er * M_qq.x + r2.ei * M_qq.y, r2.er * M_qq.y - r2.ei * M_qq.x);
-          an[p1 + (size_t)p2 * n] = make_double2(r2.cs * M_pp.x - r2.sn * cq_p.x, r2.cs * M_pp.y - r2.sn * cq_p.y);
-          an[q1 + (size_t)p2 * n] = make_double2(r2.cs * M_qp.x - r2.sn * cq_q.x, r2.cs * M_qp.y - r2.sn * cq_q.y);
-          an[p1 + (size_t)q2 * n] = make_double2(r2.sn * M_pp.x + r2.cs * cq_p.x, r2.sn * M_pp.y + r2.cs * cq_p.y);
-          an[q1 + (size_t)q2 * n] = make_double2(r2.sn * M_qp.x + r2.cs * cq_q.x, r2.sn * M_qp.y + r2.cs * cq_q.y);
+          const double2 o_pp = make_double2(r2.cs * M_pp.x - r2.sn * cq_p.x, r2.cs * M_pp.y - r2.sn * cq_p.y);
+          const double2 o_qp = make_double2(r2.cs * M_qp.x - r2.sn * cq_q.x, r2.cs * M_qp.y - r2.sn * cq_q.y);
+          const double2 o_pq = make_double2(r2.sn * M_pp.x + r2.cs * cq_p.x, r2.sn * M_pp.y + r2.cs * cq_p.y);
+          const double2 o_qq = make_double2(r2.sn * M_qp.x + r2.cs * cq_q.x, r2.sn * M_qp.y + r2.cs * cq_q.y);
+          if (I == Jb) {   // diagonal block: Hermitian by construction, keep it exactly so
+            an[p1 + (size_t)p1 * n] = make_double2(o_pp.x, 0.0);
+            an[q1 + (size_t)q1 * n] = make_double2(o_qq.x, 0.0);
+            const double2 m = make_double2(0.5 * (o_pq.x + o_qp.x), 0.5 * (o_pq.y - o_qp.y));
+            an[p1 + (size_t)q1 * n] = m;
+            an[q1 + (size_t)p1 * n] = make_double2(m.x, -m.y);
+            continue;
+          }
+          an[p1 + (size_t)p2 * n] = o_pp;
+          an[q1 + (size_t)p2 * n] = o_qp;
+          an[p1 + (size_t)q2 * n] = o_pq;
+          an[q1 + (size_t)q2 * n] = o_qq;
+          // mirrored block (J, I) = conjugate transpose
+          an[p2 + (size_t)p1 * n] = make_double2(o_pp.x, -o_pp.y);
+          an[p2 + (size_t)q1 * n] = make_double2(o_qp.x, -o_qp.y);
+          an[q2 + (size_t)p1 * n] = make_double2(o_pq.x, -o_pq.y);
+          an[q2 + (size_t)q1 * n] = make_double2(o_qq.x, -o_qq.y);
         } else {
           const long u = t - nA;
           const int b = (int)(u / ((long)n * h));
@@ -455,7 +478,7 @@ cudaError_t dense_heev(DenseWork* dw, cudaStream_t st, double2* A, int n, int np
   const size_t smem = (size_t)nprob * (n / 2) * sizeof(Rot);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   // grid: enough CTAs for ~2 items per thread, at most the co-resident count
-  const long items = (long)nprob * (n / 2) * (n / 2) + (long)nprob * n * (n / 2);
+  const long items = (long)nprob * (n / 2) * (n / 2 + 1) / 2 + (long)nprob * n * (n / 2);
   int blocks = (int)std::min<long>(dw->coop_blocks, std::max<long>(8, (items + 511) / 512));
   cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaError_t e = cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(blocks), dim3(256), args, smem, st);

@@ -322,10 +322,24 @@ static hw_status ensure_work(hw_ctx* ctx, int nk, int nb, int64_t Lpad) {
 
 using namespace hw;
 
-extern "C" hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, int block,
-                                   double tol, int maxit, hw_prec prec, int precond_kind,
-                                   const double* const* X0, double* evals, double* const* evecs,
-                                   int64_t ld_evecs, int* iters, double* resid) {
+namespace {
+// Training-data recorder of hw_solve_eigs_traced (single k-point).
+struct Trace {
+  int n_rec;
+  const int* rec_iters;
+  double* rec_R;       // device [n_rec][nb][ld]
+  double* rec_E;       // device [n_rec][nb][ld]: the recorded X block until the end, then E
+  double* rec_theta;   // host [n_rec][nb]
+  double* rec_res;     // host [n_rec][nb]
+  int64_t ld;
+  std::vector<char> got;
+};
+}  // namespace
+
+static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, int block,
+                            double tol, int maxit, hw_prec prec, int precond_kind,
+                            const double* const* X0, double* evals, double* const* evecs,
+                            int64_t ld_evecs, int* iters, double* resid, Trace* trace) {
   if (!ctx) return HW_EINVAL;
   if (ctx->device < 0) return hw_fail(ctx, HW_ESTATE, "host-only context has no device");
   if (!ctx->have_basis) return hw_fail(ctx, HW_ESTATE, "hw_setup_basis has not been called");
@@ -455,6 +469,21 @@ extern "C" hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx_in, int 
     if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
     if (dstat == HW_ETIMEOUT) return hw_fail(ctx, HW_ETIMEOUT, "dense eigensolver barrier timed out");
     if (gemm.st != CUBLAS_STATUS_SUCCESS) return hw_fail(ctx, HW_ECUDA, "cuBLAS failure");
+    if (trace) {
+      for (int r = 0; r < trace->n_rec; ++r) {
+        if (trace->rec_iters[r] != it || trace->got[r]) continue;
+        trace->got[r] = 1;
+        const size_t nbytes = (size_t)Lb[0] * 16;
+        cudaMemcpy2DAsync(trace->rec_R + 2 * (size_t)r * nb * trace->ld, trace->ld * 16, w->R, Lpad * 16, nbytes,
+                          nb, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpy2DAsync(trace->rec_E + 2 * (size_t)r * nb * trace->ld, trace->ld * 16, S, Lpad * 16, nbytes, nb,
+                          cudaMemcpyDeviceToDevice, st);
+        for (int j = 0; j < nb; ++j) {
+          trace->rec_theta[(size_t)r * nb + j] = thh[j];
+          trace->rec_res[(size_t)r * nb + j] = resh[j];
+        }
+      }
+    }
     // mixed: refresh HX in FP64 once the residuals are small, and before accepting convergence
     double maxres = 0.0;
     std::vector<int> claim(nk, 0);
@@ -676,8 +705,47 @@ extern "C" hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx_in, int 
     }
     if (iters) iters[b] = it_done[b];
   }
+  if (trace && final_status == HW_OK) {
+    // e_j = (I - X X^H) X* X*^H x_j with X* the converged n_eig vectors (first columns of S)
+    const double2* Xs = w->SB[cur];
+    const int64_t ld = trace->ld;
+    for (int r = 0; r < trace->n_rec; ++r) {
+      if (!trace->got[r]) continue;
+      double2* Xr = reinterpret_cast<double2*>(trace->rec_E) + (size_t)r * nb * ld;
+      gemm(CUBLAS_OP_C, CUBLAS_OP_N, n_eig, nb, (int)Lb[0], 1.0, Xs, Lpad, sK, Xr, ld, 0, 0.0, w->C, n_eig, 0, 1);
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lb[0], nb, n_eig, 1.0, Xs, Lpad, sK, w->C, n_eig, 0, 0.0, w->R, Lpad, 0, 1);
+      gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, (int)Lb[0], 1.0, Xr, ld, 0, w->R, Lpad, 0, 0.0, w->C, nb, 0, 1);
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lb[0], nb, nb, -1.0, Xr, ld, 0, w->C, nb, 0, 1.0, w->R, Lpad, 0, 1);
+      cudaMemcpy2DAsync(Xr, ld * 16, w->R, Lpad * 16, (size_t)Lb[0] * 16, nb, cudaMemcpyDeviceToDevice, st);
+    }
+  }
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
+  if (gemm.st != CUBLAS_STATUS_SUCCESS) return hw_fail(ctx, HW_ECUDA, "cuBLAS failure");
   if (final_status != HW_OK) return hw_fail(ctx, HW_ENOTCONV, "maxit reached before convergence");
   return HW_OK;
+}
+
+extern "C" hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx, int n_eig, int block, double tol,
+                                   int maxit, hw_prec prec, int precond_kind, const double* const* X0,
+                                   double* evals, double* const* evecs, int64_t ld_evecs, int* iters,
+                                   double* resid) {
+  return solve_impl(ctx, nk, kidx, n_eig, block, tol, maxit, prec, precond_kind, X0, evals, evecs, ld_evecs,
+                    iters, resid, nullptr);
+}
+
+extern "C" hw_status hw_solve_eigs_traced(hw_ctx* ctx, int k, int n_eig, int block, double tol, int maxit,
+                                          hw_prec prec, int precond_kind, const double* X0, int n_rec,
+                                          const int* rec_iters, double* rec_R, double* rec_E,
+                                          double* rec_theta, double* rec_res, int64_t ld, double* evals,
+                                          int* iters) {
+  if (!ctx) return HW_EINVAL;
+  if (n_rec < 0 || (n_rec > 0 && (!rec_iters || !rec_R || !rec_E || !rec_theta || !rec_res)))
+    return hw_fail(ctx, HW_EINVAL, "bad trace buffers");
+  if (ctx->have_basis && (k < 0 || k >= ctx->hb.nk || ld < ctx->hb.L[k]))
+    return hw_fail(ctx, HW_EINVAL, "bad k-point or ld");
+  Trace tr{n_rec, rec_iters, rec_R, rec_E, rec_theta, rec_res, ld, std::vector<char>(std::max(n_rec, 0), 0)};
+  const double* x0[1] = {X0};
+  return solve_impl(ctx, 1, &k, n_eig, block, tol, maxit, prec, precond_kind, X0 ? x0 : nullptr, evals, nullptr,
+                    0, iters, nullptr, &tr);
 }

@@ -66,7 +66,20 @@ _SIGS = {
     "hw_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "hw_profile_read": (C.c_int, [C.c_void_p, _D, C.POINTER(C.c_int64)]),
     "hw_launch_count": (C.c_int64, [C.c_void_p]),
+    "hw_set_mlp": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int64]),
+    "hw_get_mlp": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int64]),
+    "hw_get_potential_diagonal": (C.c_int, [C.c_void_p, C.c_int, _D]),
+    "hw_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, _D, C.c_int,
+                                   C.c_int64, C.c_void_p, _D, C.POINTER(C.c_float)]),
+    "hw_mlp_train_step": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, _D, C.c_int,
+                                    C.c_int64, C.c_void_p, C.c_float, _D]),
+    "hw_solve_eigs_traced": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
+                                       C.c_int, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int),
+                                       C.c_void_p, C.c_void_p, _D, _D, C.c_int64, _D,
+                                       C.POINTER(C.c_int)]),
 }
+
+MLP_NPARAM = 4673
 
 PHASES = ["radial_inv", "slab", "radial_fwd", "precond", "gemm", "chol", "eig", "other", "mlp"]
 
@@ -229,6 +242,63 @@ def hw_launch_count(h) -> int:
     return int(load_library().hw_launch_count(h))
 
 
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def hw_set_mlp(h, params):
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+    _check(h, load_library().hw_set_mlp(h, _fptr(p), p.size))
+
+
+def hw_get_mlp(h):
+    p = np.zeros(MLP_NPARAM, dtype=np.float32)
+    _check(h, load_library().hw_get_mlp(h, _fptr(p), p.size))
+    return p
+
+
+def hw_get_potential_diagonal(h, k, L):
+    out = np.zeros(L)
+    _check(h, load_library().hw_get_potential_diagonal(h, k, _dptr(out)))
+    return out
+
+
+def hw_mlp_loss_grad(h, k, R_ptr, E_ptr, ritz, ns, ld, vdiag_ptr=0, want_grad=True):
+    ritz = np.ascontiguousarray(ritz, dtype=np.float64)
+    loss = np.zeros(1)
+    g = np.zeros(MLP_NPARAM, dtype=np.float32) if want_grad else None
+    _check(h, load_library().hw_mlp_loss_grad(h, k, C.c_void_p(R_ptr), C.c_void_p(E_ptr), _dptr(ritz),
+                                              ns, ld, C.c_void_p(vdiag_ptr or None), _dptr(loss),
+                                              _fptr(g) if g is not None else None))
+    return float(loss[0]), g
+
+
+def hw_mlp_train_step(h, k, R_ptr, E_ptr, ritz, ns, ld, lr, vdiag_ptr=0):
+    ritz = np.ascontiguousarray(ritz, dtype=np.float64)
+    loss = np.zeros(1)
+    _check(h, load_library().hw_mlp_train_step(h, k, C.c_void_p(R_ptr), C.c_void_p(E_ptr), _dptr(ritz),
+                                               ns, ld, C.c_void_p(vdiag_ptr or None), C.c_float(lr),
+                                               _dptr(loss)))
+    return float(loss[0])
+
+
+def hw_solve_eigs_traced(h, k, n_eig, block, tol, maxit, prec, precond, X0_ptr, rec_iters,
+                         rec_R_ptr, rec_E_ptr, ld):
+    n_rec = len(rec_iters)
+    ri = (C.c_int * max(n_rec, 1))(*rec_iters)
+    th = np.zeros(n_rec * block)
+    rs = np.zeros(n_rec * block)
+    ev = np.zeros(n_eig)
+    it = (C.c_int * 1)()
+    st = load_library().hw_solve_eigs_traced(h, k, n_eig, block, tol, maxit, prec, precond,
+                                             C.c_void_p(X0_ptr or None), n_rec, ri,
+                                             C.c_void_p(rec_R_ptr), C.c_void_p(rec_E_ptr),
+                                             _dptr(th), _dptr(rs), ld, _dptr(ev), it)
+    if st not in (HW_OK, HW_ENOTCONV):
+        _check(h, st)
+    return ev, int(it[0]), th.reshape(n_rec, block), rs.reshape(n_rec, block), st == HW_OK
+
+
 # ----------------------------------------------------------------------------- Context
 
 _PREC = {"fp64": HW_FP64, "mixed": HW_MIXED}
@@ -353,3 +423,38 @@ class Context:
 
     def launch_count(self):
         return hw_launch_count(self.h)
+
+    # -- learned preconditioner
+    def set_mlp(self, params):
+        hw_set_mlp(self.h, params)
+
+    def get_mlp(self):
+        return hw_get_mlp(self.h)
+
+    def potential_diagonal(self, k):
+        return hw_get_potential_diagonal(self.h, k, int(self.L[k]))
+
+    def mlp_loss_grad(self, k, R, E, ritz, vdiag=None, want_grad=True):
+        ns, ld = self._blk(R)
+        return hw_mlp_loss_grad(self.h, k, R.data_ptr(), E.data_ptr(), ritz, ns, ld,
+                                vdiag.data_ptr() if vdiag is not None else 0, want_grad)
+
+    def mlp_train_step(self, k, R, E, ritz, lr, vdiag=None):
+        ns, ld = self._blk(R)
+        return hw_mlp_train_step(self.h, k, R.data_ptr(), E.data_ptr(), ritz, ns, ld, lr,
+                                 vdiag.data_ptr() if vdiag is not None else 0)
+
+    def solve_traced(self, k, n_eig, block, rec_iters, tol=1e-6, maxit=500, prec="fp64",
+                     precond="tpa", X0=None):
+        """Solve at k-point k recording (R, E, theta, |r|) at the given iterations; returns
+        evals, iterations, recorded R and E as (n_rec, block, L) tensors, theta, res, ok."""
+        import torch
+        L = int(self.L[k])
+        n_rec = len(rec_iters)
+        dev = f"cuda:{self.device}"
+        R = torch.zeros((n_rec, block, L), dtype=torch.complex128, device=dev)
+        E = torch.zeros_like(R)
+        ev, it, th, rs, ok = hw_solve_eigs_traced(self.h, k, n_eig, block, tol, maxit, _PREC[prec],
+                                                  _PRECOND[precond], X0.data_ptr() if X0 is not None else 0,
+                                                  list(rec_iters), R.data_ptr(), E.data_ptr(), L)
+        return dict(evals=ev, iters=it, R=R, E=E, theta=th, res=rs, converged=ok)
