@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="per-phase device times to stderr")
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--kernel-case", default=None, choices=["hx_fp64", "hx_mixed", "solve_mixed"],
+                    help="run one small case for a profiler capture and exit (prints nothing)")
     return ap.parse_args()
 
 
@@ -409,6 +411,29 @@ def cpu_baseline(w, iters_full, iters_sample=2):
                        f"GPU solve needs")}
 
 
+def kernel_case(args):
+    """A few launches of one code path on the tube workload, for ncu captures: 3 H X calls of
+    64 columns (FP64 or mixed), or one mixed-precision solve."""
+    import torch
+    from paper_2210_12252_gb300 import build, helicwave as hw, inputs
+    build.build()
+    w = inputs.tube()
+    ctx = hw.Context(0)
+    L = int(ctx.setup_basis(w.geom, w.etas)[0])
+    ctx.build_potential(w.atoms)
+    if args.kernel_case.startswith("hx"):
+        prec = args.kernel_case.split("_")[1]
+        X = torch.from_numpy(np.ascontiguousarray(inputs.random_block(L, 64, 77).T)).cuda()
+        Y = torch.empty_like(X)
+        for _ in range(3):
+            ctx.apply_H(0, X, Y, prec=prec)
+    else:
+        nb = w.n_eig + max(4, w.n_eig // 8)
+        X0 = torch.from_numpy(np.ascontiguousarray(inputs.random_block(L, nb, 1234).T)).cuda()
+        ctx.solve_eigs([0], w.n_eig, block=nb, tol=TOL, maxit=600, prec="mixed", X0=[X0])
+    torch.cuda.synchronize()
+
+
 def reference_main(args):
     """The oracle as it stands, on the host cores, for the same metric and workload: each step
     is a bounded sample (start block + 1 LOBPCG iteration) scaled to a full solve with the
@@ -444,7 +469,9 @@ def reference_main(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.kernel_case:
+        kernel_case(a)
+    elif a.impl == "reference":
         reference_main(a)
     else:
         ours_main(a)

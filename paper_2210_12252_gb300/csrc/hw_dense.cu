@@ -511,3 +511,267 @@ cudaError_t dense_hermitize(cudaStream_t st, double2* A, int n, int nprob) {
 }
 
 }  // namespace hw
+
+// ===================================================================== FP32 Jacobi, one CTA
+// Used while the eigensolver's residuals are large: the Rayleigh-Ritz matrix (shifted by the
+// mean of its valid diagonal) is packed as a lower triangle in shared memory (n(n+1)/2
+// complex FP32 values) and diagonalised by the same round-robin Jacobi as above without any
+// grid barrier.  Rotations are logged to global memory; k_jac32_vectors replays the log on
+// rows of the identity to form the eigenvectors.  Accuracy ~1e-7 relative; the caller
+// re-orthonormalises the wanted vectors in FP64.
+namespace hw {
+
+struct Rot32 {
+  float cs, sn, er, ei;
+};
+
+__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }   // i >= j
+
+__device__ __forceinline__ float2 tget(const float2* A, int r, int c) {
+  if (r >= c) return A[tri(r, c)];
+  const float2 v = A[tri(c, r)];
+  return make_float2(v.x, -v.y);
+}
+__device__ __forceinline__ void tput(float2* A, int r, int c, float2 v) {
+  if (r >= c) A[tri(r, c)] = v;
+  else A[tri(c, r)] = make_float2(v.x, -v.y);
+}
+
+constexpr int J32_THREADS = 1024;
+
+// grid: one CTA per problem.  A: [nprob][n*n] FP64 (read only).  shift: [nprob] output.
+// log: [nprob][maxsweep][n-1][n/2] rotations.  w: [nprob][n] eigenvalues (unsorted, FP64).
+__global__ void __launch_bounds__(J32_THREADS) k_jac32(const double2* A, int n, int maxsweep, double* shift,
+                                                      Rot32* log, double* w, int* sweeps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int h = n / 2;
+  float2* S = reinterpret_cast<float2*>(smem_raw);
+  Rot32* rot = reinterpret_cast<Rot32*>(smem_raw + (((size_t)n * (n + 1) / 2 * sizeof(float2) + 15) & ~size_t(15)));
+  __shared__ double red[32];
+  __shared__ float thr_s;
+  __shared__ int any_s;
+  const int b = blockIdx.x;
+  const double2* a = A + (size_t)b * n * n;
+  // shift = mean of the valid diagonal (padding entries are >= 1e9)
+  double sd = 0.0, cnt = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double d = a[i + (size_t)i * n].x;
+    if (fabs(d) < 1e9) { sd += d; cnt += 1.0; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sd += __shfl_xor_sync(0xffffffffu, sd, o);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = sd; }
+  __syncthreads();
+  __shared__ double mu_s;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    mu_s = t;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    mu_s = t > 0.0 ? mu_s / t : 0.0;
+    shift[b] = mu_s;
+  }
+  __syncthreads();
+  const double mu = mu_s;
+  float dmax = 0.f;
+  for (int t = threadIdx.x; t < n * (n + 1) / 2; t += blockDim.x) {
+    int i = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= t) ++i;
+    while (i * (i + 1) / 2 > t) --i;
+    const int j = t - i * (i + 1) / 2;
+    double2 v = a[i + (size_t)j * n];
+    if (i == j) {
+      v.x = fabs(v.x) < 1e9 ? v.x - mu : v.x;
+      v.y = 0.0;
+      if (fabs(v.x) < 1e9) dmax = fmaxf(dmax, fabsf((float)v.x));
+    }
+    S[t] = make_float2((float)v.x, (float)v.y);
+  }
+  for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, (float)red[i]);
+    thr_s = 2e-6f * fmaxf(m, 1e-30f);
+  }
+  __syncthreads();
+  const float thr = thr_s;
+  const int nblk = h * (h + 1) / 2;
+  int sweep = 0;
+  for (; sweep < maxsweep; ++sweep) {
+    if (threadIdx.x == 0) any_s = 0;
+    __syncthreads();
+    for (int step = 0; step < n - 1; ++step) {
+      for (int I = threadIdx.x; I < h; I += blockDim.x) {
+        int p = rr_index(I, step, n), q = rr_index(n - 1 - I, step, n);
+        if (p > q) { const int tt = p; p = q; q = tt; }
+        const float app = S[tri(p, p)].x, aqq = S[tri(q, q)].x;
+        const float2 c = tget(S, p, q);
+        const float ac = sqrtf(c.x * c.x + c.y * c.y);
+        Rot32 r;
+        if (!(ac > thr)) {
+          r.cs = 1.f; r.sn = 0.f; r.er = 1.f; r.ei = 0.f;
+        } else {
+          const float zeta = (aqq - app) / (2.0f * ac);
+          const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+          r.cs = rsqrtf(1.0f + t * t);
+          r.sn = t * r.cs;
+          r.er = c.x / ac;
+          r.ei = c.y / ac;
+          any_s = 1;
+        }
+        rot[I] = r;
+        log[(((size_t)b * maxsweep + sweep) * (n - 1) + step) * h + I] = r;
+      }
+      __syncthreads();
+      for (int it = threadIdx.x; it < nblk; it += blockDim.x) {
+        int I = (int)((sqrtf(8.0f * it + 1.0f) - 1.0f) * 0.5f);
+        while ((I + 1) * (I + 2) / 2 <= it) ++I;
+        while (I * (I + 1) / 2 > it) --I;
+        const int Jb = it - I * (I + 1) / 2;
+        const Rot32 r1 = rot[I], r2 = rot[Jb];
+        if (r1.sn == 0.f && r2.sn == 0.f) continue;
+        int p1 = rr_index(I, step, n), q1 = rr_index(n - 1 - I, step, n);
+        if (p1 > q1) { const int tt = p1; p1 = q1; q1 = tt; }
+        int p2 = rr_index(Jb, step, n), q2 = rr_index(n - 1 - Jb, step, n);
+        if (p2 > q2) { const int tt = p2; p2 = q2; q2 = tt; }
+        const float2 A_pp = tget(S, p1, p2), A_pq = tget(S, p1, q2), A_qp = tget(S, q1, p2), A_qq = tget(S, q1, q2);
+        const float2 eq_p = make_float2(r1.er * A_qp.x - r1.ei * A_qp.y, r1.er * A_qp.y + r1.ei * A_qp.x);
+        const float2 eq_q = make_float2(r1.er * A_qq.x - r1.ei * A_qq.y, r1.er * A_qq.y + r1.ei * A_qq.x);
+        const float2 M_pp = make_float2(r1.cs * A_pp.x - r1.sn * eq_p.x, r1.cs * A_pp.y - r1.sn * eq_p.y);
+        const float2 M_pq = make_float2(r1.cs * A_pq.x - r1.sn * eq_q.x, r1.cs * A_pq.y - r1.sn * eq_q.y);
+        const float2 M_qp = make_float2(r1.sn * A_pp.x + r1.cs * eq_p.x, r1.sn * A_pp.y + r1.cs * eq_p.y);
+        const float2 M_qq = make_float2(r1.sn * A_pq.x + r1.cs * eq_q.x, r1.sn * A_pq.y + r1.cs * eq_q.y);
+        const float2 cq_p = make_float2(r2.er * M_pq.x + r2.ei * M_pq.y, r2.er * M_pq.y - r2.ei * M_pq.x);
+        const float2 cq_q = make_float2(r2.er * M_qq.x + r2.ei * M_qq.y, r2.er * M_qq.y - r2.ei * M_qq.x);
+        const float2 o_pp = make_float2(r2.cs * M_pp.x - r2.sn * cq_p.x, r2.cs * M_pp.y - r2.sn * cq_p.y);
+        const float2 o_qp = make_float2(r2.cs * M_qp.x - r2.sn * cq_q.x, r2.cs * M_qp.y - r2.sn * cq_q.y);
+        const float2 o_pq = make_float2(r2.sn * M_pp.x + r2.cs * cq_p.x, r2.sn * M_pp.y + r2.cs * cq_p.y);
+        const float2 o_qq = make_float2(r2.sn * M_qp.x + r2.cs * cq_q.x, r2.sn * M_qp.y + r2.cs * cq_q.y);
+        if (I == Jb) {
+          S[tri(p1, p1)] = make_float2(o_pp.x, 0.f);
+          S[tri(q1, q1)] = make_float2(o_qq.x, 0.f);
+          S[tri(q1, p1)] = make_float2(0.5f * (o_qp.x + o_pq.x), 0.5f * (o_qp.y - o_pq.y));
+        } else {
+          tput(S, p1, p2, o_pp);
+          tput(S, p1, q2, o_pq);
+          tput(S, q1, p2, o_qp);
+          tput(S, q1, q2, o_qq);
+        }
+      }
+      __syncthreads();
+    }
+    const int any = any_s;
+    __syncthreads();
+    if (!any) {
+      ++sweep;
+      break;
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float d = S[tri(i, i)].x;
+    w[(size_t)b * n + i] = fabsf(d) < 1e9f ? (double)d + mu : (double)d;
+  }
+  if (threadIdx.x == 0) sweeps[b] = sweep;
+}
+
+// replay the rotation log on rows [r0, r0 + RB) of the identity; Z[b] gets the eigenvectors
+// in the column order of the log (unsorted), FP64.  grid (row blocks, nprob)
+constexpr int JV_ROWS = 8;
+__global__ void __launch_bounds__(256) k_jac32_vectors(const Rot32* log, int n, int maxsweep, const int* sweeps,
+                                                       double2* Z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* V = reinterpret_cast<float2*>(smem_raw);   // [JV_ROWS][n]
+  const int b = blockIdx.y, r0 = blockIdx.x * JV_ROWS;
+  const int h = n / 2;
+  const int nr = min(JV_ROWS, n - r0);
+  for (int t = threadIdx.x; t < JV_ROWS * n; t += blockDim.x) {
+    const int rr = t / n, c = t - rr * n;
+    V[t] = make_float2((r0 + rr) == c ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  const int ns = sweeps[b];
+  for (int sw = 0; sw < ns; ++sw)
+    for (int step = 0; step < n - 1; ++step) {
+      const Rot32* rs = log + (((size_t)b * maxsweep + sw) * (n - 1) + step) * h;
+      for (int t = threadIdx.x; t < nr * h; t += blockDim.x) {
+        const int rr = t / h, I = t - rr * h;
+        const Rot32 r = rs[I];
+        if (r.sn == 0.f) continue;
+        int p = rr_index(I, step, n), q = rr_index(n - 1 - I, step, n);
+        if (p > q) { const int tt = p; p = q; q = tt; }
+        float2* v = V + rr * n;
+        const float2 vp = v[p], vq = v[q];
+        const float2 cv = make_float2(r.er * vq.x + r.ei * vq.y, r.er * vq.y - r.ei * vq.x);
+        v[p] = make_float2(r.cs * vp.x - r.sn * cv.x, r.cs * vp.y - r.sn * cv.y);
+        v[q] = make_float2(r.sn * vp.x + r.cs * cv.x, r.sn * vp.y + r.cs * cv.y);
+      }
+      __syncthreads();
+    }
+  for (int t = threadIdx.x; t < nr * n; t += blockDim.x) {
+    const int rr = t / n, c = t - rr * n;
+    Z[(size_t)b * n * n + (r0 + rr) + (size_t)c * n] = make_double2(V[t].x, V[t].y);
+  }
+}
+
+// sort eigenvalues ascending and permute the eigenvector columns; grid nprob
+__global__ void k_sort_pairs(const double* w_in, const double2* Zin, int n, double* w_out, double2* Zout) {
+  const int b = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double di = w_in[(size_t)b * n + i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double dj = w_in[(size_t)b * n + j];
+      rank += (dj < di) || (dj == di && j < i);
+    }
+    w_out[(size_t)b * n + rank] = di;
+    for (int r = 0; r < n; ++r) Zout[(size_t)b * n * n + r + (size_t)rank * n] = Zin[(size_t)b * n * n + r + (size_t)i * n];
+  }
+}
+
+size_t jac32_smem(int n) {
+  return (((size_t)n * (n + 1) / 2 * sizeof(float2) + 15) & ~size_t(15)) + (size_t)(n / 2) * sizeof(Rot32);
+}
+
+// FP32 eigen-decomposition of nprob Hermitian n x n FP64 matrices (A read only): w ascending,
+// Z eigenvector columns (FP64 storage, FP32 accuracy).  scratch: log and unsorted copies.
+cudaError_t dense_heev32(cudaStream_t st, const double2* A, int n, int nprob, double* w, double2* Z,
+                         void* scratch, size_t scratch_bytes, int maxsweep) {
+  const size_t smem = jac32_smem(n);
+  if (smem > 226 * 1024 || (n & 1)) return cudaErrorInvalidValue;
+  const size_t logb = (size_t)nprob * maxsweep * (n - 1) * (n / 2) * sizeof(Rot32);
+  const size_t need = logb + (size_t)nprob * (n * 2 + 8) * sizeof(double) + (size_t)nprob * n * n * sizeof(double2) + 1024;
+  if (need > scratch_bytes) return cudaErrorInvalidValue;
+  unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
+  Rot32* log = reinterpret_cast<Rot32*>(p);
+  p += (logb + 255) & ~size_t(255);
+  double* wu = reinterpret_cast<double*>(p);
+  p += (((size_t)nprob * n * sizeof(double)) + 255) & ~size_t(255);
+  double* shift = reinterpret_cast<double*>(p);
+  p += (((size_t)nprob * sizeof(double)) + 255) & ~size_t(255);
+  int* sweeps = reinterpret_cast<int*>(p);
+  p += (((size_t)nprob * sizeof(int)) + 255) & ~size_t(255);
+  double2* Zu = reinterpret_cast<double2*>(p);
+  cudaFuncSetAttribute(k_jac32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_jac32<<<nprob, J32_THREADS, smem, st>>>(A, n, maxsweep, shift, log, wu, sweeps);
+  k_jac32_vectors<<<dim3((n + JV_ROWS - 1) / JV_ROWS, nprob), 256, JV_ROWS * n * sizeof(float2), st>>>(
+      log, n, maxsweep, sweeps, Zu);
+  k_sort_pairs<<<nprob, 256, 0, st>>>(wu, Zu, n, w, Z);
+  return cudaGetLastError();
+}
+
+size_t heev32_scratch_bytes(int n, int nprob, int maxsweep) {
+  return (size_t)nprob * maxsweep * (n - 1) * (n / 2) * sizeof(Rot32) + (size_t)nprob * (n * 2 + 8) * sizeof(double) +
+         (size_t)nprob * n * n * sizeof(double2) + 4096;
+}
+
+}  // namespace hw

@@ -39,6 +39,12 @@ cudaError_t dense_heev(DenseWork* dw, cudaStream_t st, double2* A, int n, int np
 cudaError_t dense_chol(cudaStream_t st, double2* G, int n, int nprob, int* fail);
 cudaError_t dense_trinv(cudaStream_t st, const double2* L, double2* Ui, int n, int nprob);
 cudaError_t dense_hermitize(cudaStream_t st, double2* A, int n, int nprob);
+cudaError_t dense_heev32(cudaStream_t st, const double2* A, int n, int nprob, double* w, double2* Z,
+                         void* scratch, size_t scratch_bytes, int maxsweep);
+size_t heev32_scratch_bytes(int n, int nprob, int maxsweep);
+size_t jac32_smem(int n);
+constexpr int J32_SWEEPS = 12;
+constexpr double FP32_RR_ABOVE = 1e-4;   // Rayleigh-Ritz in FP32 while residuals exceed this
 cudaError_t launch_precond_learned(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld,
                                    const double* const* ritz);
 
@@ -62,6 +68,8 @@ struct LobpcgWork {
   int* fail = nullptr;      // [nk]
   int* status = nullptr;
   DenseWork* dw = nullptr;
+  void* j32 = nullptr;      // FP32 Jacobi scratch (rotation log, unsorted pairs)
+  size_t j32_bytes = 0;
 };
 
 void lobpcg_free(hw_ctx* ctx) {
@@ -70,7 +78,7 @@ void lobpcg_free(hw_ctx* ctx) {
   for (void* p : {(void*)w->SB[0], (void*)w->SB[1], (void*)w->HSB[0], (void*)w->HSB[1], (void*)w->R,
                   (void*)w->A, (void*)w->Z, (void*)w->w, (void*)w->G, (void*)w->Ui, (void*)w->C,
                   (void*)w->Y, (void*)w->Y2, (void*)w->res, (void*)w->theta, (void*)w->iact,
-                  (void*)w->fail, (void*)w->status})
+                  (void*)w->fail, (void*)w->status, w->j32})
     if (p) cudaFree(p);
   dense_free(w->dw);
   delete w;
@@ -155,6 +163,34 @@ __global__ void k_build_y(const double2* Z, int ne, int nb, const int* iact, int
   const double2* z = Z + (size_t)b * ne * ne + (size_t)(src < 0 ? 0 : src) * ne;
   for (int r = threadIdx.x; r < ne; r += blockDim.x)
     y[r] = (src < 0 || r < nb) ? make_double2(0.0, 0.0) : z[r];
+}
+
+// C = 1.5 I - 0.5 G (one Newton-Schulz step towards orthonormal columns); grid (8, nk)
+__global__ void k_ns_coef(const double2* G, int m, double2* C) {
+  const int b = blockIdx.y;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m * m; t += gridDim.x * blockDim.x) {
+    const int i = t % m, j = t / m;
+    const double2 g = G[(size_t)b * m * m + t];
+    C[(size_t)b * m * m + t] = make_double2((i == j ? 1.5 : 0.0) - 0.5 * g.x, -0.5 * g.y);
+  }
+}
+
+// w[b][j] = Re(z_j^H t_j) for the first m columns (Z and T with leading dimension n); grid (m, nk)
+__global__ void k_rq_diag(const double2* Z, const double2* T, int n, int64_t sZ, int64_t sT, double* w, int64_t sw) {
+  __shared__ double red[8];
+  const int j = blockIdx.x, b = blockIdx.y;
+  const double2* z = Z + (size_t)b * sZ + (size_t)j * n;
+  const double2* t = T + (size_t)b * sT + (size_t)j * n;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += z[i].x * t[i].x + z[i].y * t[i].y;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += red[i];
+    w[(size_t)b * sw + j] = a;
+  }
 }
 
 // Gaussian start block from a counter-based generator (splitmix64 + Box-Muller); grid (nb, nk)
@@ -255,6 +291,53 @@ static hw_status cholqr(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, double2* S, int 
   return gemm.st == CUBLAS_STATUS_SUCCESS ? HW_OK : hw_fail(ctx, HW_ECUDA, "cuBLAS failure in Cholesky-QR");
 }
 
+// Rayleigh-Ritz eigenpairs of the nk matrices w->A (n x n, padded, Hermitian): w->w ascending,
+// w->Z eigenvector columns.  fp32: FP32 Jacobi, then the first nb vectors are made orthonormal
+// in FP64 (two Newton-Schulz steps) and their Rayleigh quotients recomputed in FP64; else the
+// FP64 Jacobi.
+static cudaError_t rr_eig(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int nb, bool fp32) {
+  cudaStream_t st = ctx->stream;
+  const int nk = w->nk;
+  cudaError_t e;
+  if (fp32 && w->j32 && jac32_smem(n) <= 226 * 1024) {
+    {
+      ProfScope ps_(ctx, HW_PH_EIG);
+      dense_hermitize(st, w->A, n, nk);
+      e = dense_heev32(st, w->A, n, nk, w->w, w->Z, w->j32, w->j32_bytes, J32_SWEEPS);
+      ctx->launches += 4;
+    }
+    if (e != cudaSuccess) return e;
+    const int64_t sZ = (int64_t)n * n;
+    for (int pass = 0; pass < 2; ++pass) {
+      gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, n, 1.0, w->Z, n, sZ, w->Z, n, sZ, 0.0, w->G, nb, (int64_t)nb * nb, nk);
+      {
+        ProfScope ps_(ctx, HW_PH_OTHER);
+        k_ns_coef<<<dim3(8, nk), 256, 0, st>>>(w->G, nb, w->Ui);
+        ctx->launches++;
+      }
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, nb, 1.0, w->Z, n, sZ, w->Ui, nb, (int64_t)nb * nb, 0.0, w->Y2, n,
+           (int64_t)n * nb, nk);
+      // each k-point's n x nb block back into the first nb columns of its n x n Z
+      cudaMemcpy2DAsync(w->Z, (size_t)n * n * 16, w->Y2, (size_t)n * nb * 16, (size_t)n * nb * 16, nk,
+                        cudaMemcpyDeviceToDevice, st);
+    }
+    gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, n, 1.0, w->A, n, sZ, w->Z, n, sZ, 0.0, w->Y2, n, (int64_t)n * nb, nk);
+    {
+      ProfScope ps_(ctx, HW_PH_OTHER);
+      k_rq_diag<<<dim3(nb, nk), 256, 0, st>>>(w->Z, w->Y2, n, sZ, (int64_t)n * nb, w->w, n);
+      ctx->launches++;
+    }
+    return cudaGetLastError();
+  }
+  {
+    ProfScope ps_(ctx, HW_PH_EIG);
+    dense_hermitize(st, w->A, n, nk);
+    e = dense_heev(w->dw, st, w->A, n, nk, w->w, w->Z, w->status, 1e-14);
+    ctx->launches += 4;
+  }
+  return e;
+}
+
 // apply H to `ncol` columns of S at column offset c0, result at the same offset of HS
 static hw_status apply_block(hw_ctx* ctx, LobpcgWork* w, const std::vector<int>& kidx, double2* S, double2* HS,
                              int c0, int ncol, bool fp64, const std::vector<int>* only = nullptr) {
@@ -311,6 +394,10 @@ static hw_status ensure_work(hw_ctx* ctx, int nk, int nb, int64_t Lpad) {
   A((void**)&w->fail, (size_t)nk * sizeof(int));
   A((void**)&w->status, sizeof(int));
   if (e == cudaSuccess) e = dense_alloc(w->dw, nk * ne2, nk);
+  if (e == cudaSuccess && jac32_smem(w->ne) <= 226 * 1024) {
+    w->j32_bytes = heev32_scratch_bytes(w->ne, nk, J32_SWEEPS);
+    e = cudaMalloc(&w->j32, w->j32_bytes);
+  }
   if (e != cudaSuccess) {
     lobpcg_free(ctx);
     return hw_fail(ctx, HW_ENOMEM, std::string("eigensolver workspace: ") + cudaGetErrorString(e));
@@ -429,13 +516,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       k_pad_rr<<<dim3(8, nk), 256, 0, st>>>(w->A, n, nb, 0, 0, dnv + nk, dnv + 2 * nk);
       ctx->launches++;
     }
-    cudaError_t e;
-    {
-      ProfScope ps_(ctx, HW_PH_EIG);
-      dense_hermitize(st, w->A, n, nk);
-      e = dense_heev(w->dw, st, w->A, n, nk, w->w, w->Z, w->status, 1e-14);
-      ctx->launches += 4;
-    }
+    cudaError_t e = rr_eig(ctx, w, gemm, n, nb, true);
     if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
     gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nb, 1.0, w->SB[0], Lpad, sK, w->Z, n, (int64_t)n * n, 0.0,
          w->SB[1], Lpad, sK, nk);
@@ -627,12 +708,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       k_pad_rr<<<dim3(8, nk), 256, 0, st>>>(w->A, n, nb, np, na, dnv + nk, dnv + 2 * nk);
       ctx->launches++;
     }
-    {
-      ProfScope ps_(ctx, HW_PH_EIG);
-      dense_hermitize(st, w->A, n, nk);
-      e = dense_heev(w->dw, st, w->A, n, nk, w->w, w->Z, w->status, 1e-14);
-      ctx->launches += 4;
-    }
+    e = rr_eig(ctx, w, gemm, n, nb, maxres > FP32_RR_ABOVE);
     if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
     const int nxt = 1 - cur;
     double2* S2 = w->SB[nxt];
