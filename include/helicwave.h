@@ -130,6 +130,18 @@ hw_status hw_build_potential(hw_ctx* ctx, int n_atoms, const double* atoms, doub
 hw_status hw_apply_H(hw_ctx* ctx, int k, const double* X, double* Y, int ns, int64_t ld,
                      hw_prec prec);
 
+/* The same product as hw_apply_H for callers that cannot allocate device memory (a budget
+ * fixed at start-up, or places where cudaMalloc is not allowed or would synchronise).  No
+ * counterpart in the paper.  The call allocates nothing: its intermediates live in one
+ * file-scope device array of 64 MiB that every GPU loading this library holds until exit,
+ * resolved with cudaGetSymbolAddress on the first call on each device (make that first call
+ * before any stream capture).  Columns are processed in passes that fit the array; a basis
+ * whose single column does not fit (2 * N_r * n_pairs complex values) is rejected with
+ * HW_EINVAL.  Calls share the array: calls that overlap on the GPU race and must be ordered
+ * by the caller.  Arguments as for hw_apply_H. */
+hw_status hw_apply_H_noalloc(hw_ctx* ctx, int k, const double* X, double* Y, int ns, int64_t ld,
+                             hw_prec prec);
+
 /* Y_b = H(b) X_b for the nk k-points kidx[0..nk) in one pipeline; X[b], Y[b] are device
  * pointers to L_{kidx[b]} x ns blocks with leading dimension ld (>= max L). */
 hw_status hw_apply_H_batched(hw_ctx* ctx, int nk, const int* kidx, const double* const* X,

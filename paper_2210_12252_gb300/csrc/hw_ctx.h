@@ -107,6 +107,8 @@ namespace hw {
 template <typename T>
 cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld);
 cudaError_t hx_configure(hw_ctx* ctx);
+template <typename T>
+cudaError_t launch_hx_into(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, void* gbuf, void* hbuf, int cols);
 cudaError_t launch_tpa(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld);
 cudaError_t launch_precond_learned(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld,
                                    const double* const* ritz);

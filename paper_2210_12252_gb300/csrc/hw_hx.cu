@@ -442,6 +442,74 @@ cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld) {
   return cudaGetLastError();
 }
 
+// The same three kernels with caller-chosen G / H buffers holding `cols` columns per pass
+// (used by the entry point that allocates nothing).
+template <typename T>
+cudaError_t launch_hx_into(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, void* gbuf, void* hbuf, int cols) {
+  auto& hb = ctx->hb;
+  auto& db = ctx->db;
+  const DevTables<T>& tb = *reinterpret_cast<const DevTables<T>*>(
+      sizeof(T) == 8 ? (const void*)&db.t64 : (const void*)&db.t32);
+  const int ncols_total = blk.nslot * ns;
+  if (cols <= 0 || blk.nslot > MAXSLOT) return cudaErrorInvalidValue;
+  const int Nr = hb.prm.Nr, K = hb.K;
+  int maxna = 0;
+  for (int g = 0; g <= hb.N; ++g) maxna = std::max(maxna, hb.group_start[g + 1] - hb.group_start[g]);
+  const int Jc = slab_pick_jc(ctx, sizeof(cplx_t<T>));
+  for (int c0 = 0; c0 < ncols_total; c0 += cols) {
+    const int nc = std::min(cols, ncols_total - c0);
+    RadArgs<T> ra;
+    ra.Nr = Nr;
+    ra.K = K;
+    ra.nA = hb.nA;
+    ra.ncols = nc;
+    ra.ns = ns;
+    ra.c0 = c0;
+    ra.group_start = db.group_start;
+    ra.off = db.off;
+    ra.Ka = db.Ka;
+    ra.ld = ld;
+    ra.ke = db.ke;
+    for (int i = 0; i < blk.nslot; ++i) ra.keoff[i] = db.ke_off[blk.kb[i]];
+    ra.blk = blk;
+    ra.gh = reinterpret_cast<cplx_t<T>*>(gbuf);
+    ra.rtab = tb.rinv;
+    dim3 grid((unsigned)(((long)maxna * nc + RAD_Q - 1) / RAD_Q), hb.N + 1);
+    const size_t sm_inv = ((size_t(Nr) * K * sizeof(T) + 15) & ~size_t(15)) +
+                          (size_t)K * RAD_Q * sizeof(cplx_t<T>);
+    k_radial_inv<T><<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra);
+    SlabArgs<T> sa;
+    sa.Nr = Nr;
+    sa.Nth1 = hb.prm.Nth1;
+    sa.Nth2 = hb.prm.Nth2;
+    sa.nA = hb.nA;
+    sa.nmr = (int)hb.mrow_m.size();
+    sa.ncols = nc;
+    sa.Jc = Jc;
+    sa.p1 = to_dev(ctx->plan1);
+    sa.p2 = to_dev(ctx->plan2);
+    sa.pair_n = db.pair_n;
+    sa.pair_mrow = db.pair_mrow;
+    sa.mrow_m = db.mrow_m;
+    sa.V = tb.V;
+    sa.tw1 = reinterpret_cast<const cplx_t<T>*>(tb.tw1);
+    sa.tw2 = reinterpret_cast<const cplx_t<T>*>(tb.tw2);
+    sa.G = reinterpret_cast<const cplx_t<T>*>(gbuf);
+    sa.H = reinterpret_cast<cplx_t<T>*>(hbuf);
+    k_slab<T><<<dim3(nc, Nr), SLAB_THREADS, slab_smem_bytes(ctx, sizeof(cplx_t<T>), Jc), ctx->stream>>>(sa);
+    ra.gh = reinterpret_cast<cplx_t<T>*>(hbuf);
+    ra.rtab = tb.rfwd;
+    const size_t sm_fwd = ((size_t(K) * Nr * sizeof(T) + 15) & ~size_t(15)) +
+                          32 * RAD_Q * sizeof(cplx_t<T>) + (size_t)RAD_Q * (K + 1) * sizeof(cplx_t<T>);
+    k_radial_fwd<T><<<grid, RAD_THREADS, sm_fwd, ctx->stream>>>(ra);
+    ctx->launches += 3;
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_hx_into<double>(hw_ctx*, const Blocks&, int, int64_t, void*, void*, int);
+template cudaError_t launch_hx_into<float>(hw_ctx*, const Blocks&, int, int64_t, void*, void*, int);
+
 // opt in to large dynamic shared memory for every instantiation (called once at setup)
 cudaError_t hx_configure(hw_ctx* ctx) {
   cudaError_t e = cudaSuccess;

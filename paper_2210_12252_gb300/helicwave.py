@@ -54,6 +54,8 @@ _SIGS = {
     "hw_build_potential": (C.c_int, [C.c_void_p, C.c_int, _D, _D]),
     "hw_apply_H": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int64,
                              C.c_int]),
+    "hw_apply_H_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int64,
+                                     C.c_int]),
     "hw_apply_H_batched": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int),
                                      C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int,
                                      C.c_int64, C.c_int]),
@@ -191,6 +193,12 @@ def hw_build_potential(h, atoms, grid_points):
 
 def hw_apply_H(h, k, X_ptr, Y_ptr, ns, ld, prec=HW_FP64):
     _check(h, load_library().hw_apply_H(h, k, C.c_void_p(X_ptr), C.c_void_p(Y_ptr), ns, ld, prec))
+
+
+def hw_apply_H_noalloc(h, k, X_ptr, Y_ptr, ns, ld, prec=HW_FP64):
+    """H X through the entry point that allocates nothing (fixed 64 MiB device scratch)."""
+    _check(h, load_library().hw_apply_H_noalloc(h, k, C.c_void_p(X_ptr), C.c_void_p(Y_ptr), ns, ld,
+                                                prec))
 
 
 def hw_apply_H_batched(h, kidx, X_ptrs, Y_ptrs, ns, ld, prec=HW_FP64):
