@@ -213,6 +213,16 @@ hw_status hw_solve_eigs_traced(hw_ctx* ctx, int k, int n_eig, int block, double 
                                double* rec_theta, double* rec_res, int64_t ld, double* evals,
                                int* iters);
 
+/* The Rayleigh-Ritz step's dense Hermitian eigensolver on its own (Sec. "Eigensolvers and
+ * Preconditioning": the small projected eigenproblem of LOBPCG).  A: device, nprob Hermitian
+ * n x n complex128 matrices (column-major, contiguous, n even, read only); w: device
+ * [nprob][n] eigenvalues ascending; Z: device [nprob][n][n] eigenvector columns.  method 0:
+ * FP64 parallel Jacobi (all n pairs).  method 1: FP32 Householder tridiagonalisation,
+ * bisection and inverse iteration, then FP64 refinement of the lowest nw pairs (only the first
+ * nw entries of w and columns of Z are FP64-accurate; n <= 236).  Synchronous. */
+hw_status hw_heev(hw_ctx* ctx, int n, int nprob, int nw, const double* A, double* w, double* Z,
+                  int method);
+
 /* Wait for all work on the context's stream. */
 hw_status hw_synchronize(hw_ctx* ctx);
 

@@ -775,3 +775,575 @@ size_t heev32_scratch_bytes(int n, int nprob, int maxsweep) {
 }
 
 }  // namespace hw
+
+// ===================================================================== Householder eigensolver
+// For the Rayleigh-Ritz step only the lowest `nw` eigenpairs are needed.  Stages:
+//   k_hh_tridiag  one CTA per problem: the matrix (shifted by the mean of its valid diagonal)
+//                 packed as a lower triangle in shared memory, reduced to Hermitian tridiagonal
+//                 form by n-2 Householder reflections in FP32; reflectors kept in global memory
+//   k_tri_wanted  one CTA per problem: the tridiagonal made real by a diagonal phase matrix,
+//                 its lowest nw eigenvalues by Sturm bisection (one thread each), eigenvectors
+//                 by inverse iteration, Gram-Schmidt inside near-degenerate groups (FP32)
+//   k_hh_back     one warp per wanted vector: Z = Q D Y (reflectors applied in reverse), FP64 out
+// followed (host side) by an FP64 refinement of the wanted vectors (Ogita-Aishima style
+// first-order correction against all FP32 vectors, then Rayleigh-Ritz inside groups).
+namespace hw {
+
+struct HhArgs {
+  int n, nw;
+  const double2* A;    // [nprob][n*n] FP64 input (read only)
+  float2* vq;          // [nprob][n][n] reflector k stored in column k (rows k+1..n-1)
+  float* beta;         // [nprob][n]
+  float* d;            // [nprob][n] diagonal of T
+  float2* e;           // [nprob][n] sub-diagonal of T (e[k] = T[k+1][k])
+  double* shift;       // [nprob]
+  float* lam;          // [nprob][nw] eigenvalues of the shifted T (ascending)
+  double* lam64;       // [nprob][n stride] the same plus the shift (FP64 storage), may be null
+  float* Y;            // [nprob][nw][n] eigenvectors of the real tridiagonal
+  float* work;         // [nprob][nw][3n] inverse-iteration factors
+  double2* Z;          // [nprob][n][nw] output vectors (column-major n x nw)
+};
+
+constexpr int HH_THREADS = 1024;
+
+__device__ __forceinline__ float block_sum_f(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+  return t;
+}
+
+__global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = H.n, b = blockIdx.x;
+  float2* S = reinterpret_cast<float2*>(smem_raw);                       // packed lower triangle
+  float2* v = S + ((size_t)n * (n + 1) / 2 + 1);                          // [n]
+  float2* p = v + n;                                                      // [n]
+  __shared__ float red[32];
+  __shared__ float2 alpha_s;
+  __shared__ float beta_s;
+  const double2* a = H.A + (size_t)b * n * n;
+  // shift = mean of the valid diagonal (padding entries are >= 1e9)
+  float sd = 0.f, cnt = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = a[i + (size_t)i * n].x;
+    if (fabs(x) < 1e9) { sd += (float)x; cnt += 1.f; }
+  }
+  sd = block_sum_f(sd, red);
+  cnt = block_sum_f(cnt, red);
+  const double mu = cnt > 0.f ? (double)(sd / cnt) : 0.0;
+  // load (FP64 -> FP32, shifted)
+  for (int t = threadIdx.x; t < n * (n + 1) / 2; t += blockDim.x) {
+    int i = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= t) ++i;
+    while (i * (i + 1) / 2 > t) --i;
+    const int j = t - i * (i + 1) / 2;
+    const double2 x = a[i + (size_t)j * n];
+    double re = x.x;
+    if (i == j && fabs(re) < 1e9) re -= mu;
+    S[t] = make_float2((float)re, i == j ? 0.f : (float)x.y);
+  }
+  __syncthreads();
+  float2* vq = H.vq + (size_t)b * n * n;
+  for (int k = 0; k < n - 2; ++k) {
+    const int m = n - k - 1;   // length of the column below the diagonal
+    // sigma = ||x||^2, x = A[k+1:, k]
+    float s = 0.f;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const float2 x = S[tri(k + 1 + i, k)];
+      s += x.x * x.x + x.y * x.y;
+    }
+    s = block_sum_f(s, red);
+    if (threadIdx.x == 0) {
+      const float2 x0 = S[tri(k + 1, k)];
+      const float ax0 = sqrtf(x0.x * x0.x + x0.y * x0.y);
+      const float tail = s - ax0 * ax0;
+      if (!(tail > 1e-30f * fmaxf(s, 1e-30f)) || s == 0.f) {
+        beta_s = 0.f;             // already reduced
+        alpha_s = x0;
+      } else {
+        const float sq = sqrtf(s);
+        const float2 ph = ax0 > 0.f ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
+        alpha_s = make_float2(-ph.x * sq, -ph.y * sq);
+        beta_s = 1.0f / (sq * (sq + ax0));   // 2 / ||v||^2
+      }
+    }
+    __syncthreads();
+    const float bet = beta_s;
+    const float2 alpha = alpha_s;
+    if (threadIdx.x == 0) {
+      H.beta[(size_t)b * n + k] = bet;
+      H.e[(size_t)b * n + k] = alpha;
+      H.d[(size_t)b * n + k] = S[tri(k, k)].x;
+    }
+    if (bet == 0.f) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) vq[(size_t)k * n + k + 1 + i] = make_float2(0.f, 0.f);
+      __syncthreads();
+      continue;
+    }
+    // v = x - alpha e1
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      float2 x = S[tri(k + 1 + i, k)];
+      if (i == 0) { x.x -= alpha.x; x.y -= alpha.y; }
+      v[i] = x;
+      vq[(size_t)k * n + k + 1 + i] = x;
+    }
+    __syncthreads();
+    // p = beta A' v   (A' = A[k+1:, k+1:]); 4 threads per row
+    // (every lane of a warp runs the same number of iterations, so the shuffles are uniform)
+    for (int t0 = 0; t0 < 4 * m; t0 += blockDim.x) {
+      const int t = t0 + threadIdx.x;
+      const bool act = t < 4 * m;
+      const int i = t >> 2, part = t & 3;
+      float pr = 0.f, pi = 0.f;
+      if (act) {
+        for (int j = part; j < m; j += 4) {
+          const float2 aij = tget(S, k + 1 + i, k + 1 + j);
+          const float2 vj = v[j];
+          pr += aij.x * vj.x - aij.y * vj.y;
+          pi += aij.x * vj.y + aij.y * vj.x;
+        }
+      }
+      pr += __shfl_xor_sync(0xffffffffu, pr, 1);
+      pi += __shfl_xor_sync(0xffffffffu, pi, 1);
+      pr += __shfl_xor_sync(0xffffffffu, pr, 2);
+      pi += __shfl_xor_sync(0xffffffffu, pi, 2);
+      if (act && part == 0) p[i] = make_float2(bet * pr, bet * pi);
+    }
+    __syncthreads();
+    // K = (beta / 2) v^H p  (real for Hermitian A')
+    float kk = 0.f;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) kk += v[i].x * p[i].x + v[i].y * p[i].y;
+    kk = 0.5f * bet * block_sum_f(kk, red);
+    // w = p - K v  (in place in p)
+    for (int i = threadIdx.x; i < m; i += blockDim.x) p[i] = make_float2(p[i].x - kk * v[i].x, p[i].y - kk * v[i].y);
+    __syncthreads();
+    // A' -= v w^H + w v^H (lower triangle); column k becomes (alpha, 0, ...)
+    for (int t = threadIdx.x; t < m * (m + 1) / 2; t += blockDim.x) {
+      int i = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+      while ((i + 1) * (i + 2) / 2 <= t) ++i;
+      while (i * (i + 1) / 2 > t) --i;
+      const int j = t - i * (i + 1) / 2;
+      const float2 vi = v[i], vj = v[j], wi = p[i], wj = p[j];
+      float2 x = S[tri(k + 1 + i, k + 1 + j)];
+      // v_i conj(w_j) + w_i conj(v_j)
+      x.x -= (vi.x * wj.x + vi.y * wj.y) + (wi.x * vj.x + wi.y * vj.y);
+      x.y -= (vi.y * wj.x - vi.x * wj.y) + (wi.y * vj.x - wi.x * vj.y);
+      if (i == j) x.y = 0.f;
+      S[tri(k + 1 + i, k + 1 + j)] = x;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    H.d[(size_t)b * n + n - 2] = S[tri(n - 2, n - 2)].x;
+    H.d[(size_t)b * n + n - 1] = S[tri(n - 1, n - 1)].x;
+    H.e[(size_t)b * n + n - 2] = S[tri(n - 1, n - 2)];
+    H.beta[(size_t)b * n + n - 2] = 0.f;
+    H.beta[(size_t)b * n + n - 1] = 0.f;
+    H.shift[b] = mu;
+  }
+}
+
+// eigenvalues count below x of the real tridiagonal (diag dd, off-diagonal magnitudes ee)
+__device__ __forceinline__ int sturm32(const float* dd, const float* ee2, int n, float x, float pivmin) {
+  int c = 0;
+  float q = dd[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  if (q < 0.f) ++c;
+  for (int i = 1; i < n; ++i) {
+    q = dd[i] - x - ee2[i - 1] / q;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    if (q < 0.f) ++c;
+  }
+  return c;
+}
+
+__global__ void __launch_bounds__(256) k_tri_wanted(HhArgs H) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = H.n, nw = H.nw, b = blockIdx.x;
+  float* dd = reinterpret_cast<float*>(smem_raw);   // [n]
+  float* ee = dd + n;                               // [n] |e|
+  float* ee2 = ee + n;                              // [n] |e|^2
+  float* lam = ee2 + n;                             // [nw]
+  __shared__ float bounds[2];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    dd[i] = H.d[(size_t)b * n + i];
+    const float2 e = i < n - 1 ? H.e[(size_t)b * n + i] : make_float2(0.f, 0.f);
+    ee[i] = sqrtf(e.x * e.x + e.y * e.y);
+    ee2[i] = e.x * e.x + e.y * e.y;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {   // Gershgorin bounds over the non-padding part
+    float lo = 1e30f, hi = -1e30f;
+    for (int i = 0; i < n; ++i) {
+      const float r = (i > 0 ? ee[i - 1] : 0.f) + (i < n - 1 ? ee[i] : 0.f);
+      lo = fminf(lo, dd[i] - r);
+      hi = fmaxf(hi, dd[i] + r);
+    }
+    bounds[0] = lo;
+    bounds[1] = hi;
+  }
+  __syncthreads();
+  float tnorm = fmaxf(fabsf(bounds[0]), fabsf(bounds[1]));
+  // clamp the upper bound to the valid spectrum scale (padding sits near 1e10)
+  const float pivmin = 1e-30f;
+  // bisection: thread j -> j-th smallest eigenvalue
+  for (int j = threadIdx.x; j < nw; j += blockDim.x) {
+    float lo = bounds[0], hi = bounds[1];
+    for (int it = 0; it < 80 && hi - lo > 2e-7f * fmaxf(fabsf(lo), fabsf(hi)) + 1e-30f; ++it) {
+      const float mid = 0.5f * (lo + hi);
+      if (sturm32(dd, ee2, n, mid, pivmin) > j) hi = mid;
+      else lo = mid;
+    }
+    lam[j] = 0.5f * (lo + hi);
+    H.lam[(size_t)b * nw + j] = lam[j];
+    if (H.lam64) H.lam64[(size_t)b * n + j] = (double)lam[j] + H.shift[b];
+  }
+  __syncthreads();
+  // inverse iteration (LU without pivoting, guarded pivots), one thread per wanted vector
+  float scale = 0.f;
+  for (int i = 0; i < nw; ++i) scale = fmaxf(scale, fabsf(lam[i]));
+  scale = fmaxf(scale, 1e-6f);
+  for (int j = threadIdx.x; j < nw; j += blockDim.x) {
+    float* y = H.Y + ((size_t)b * nw + j) * n;
+    float* u = H.work + ((size_t)b * nw + j) * 3 * n;   // u (pivots), l (multipliers)
+    float* l = u + n;
+    const float guard = 1e-7f * scale;
+    // perturb the shift slightly inside its group so equal eigenvalues give different vectors
+    const float sh = lam[j] + (float)(j % 7) * 1e-7f * scale;
+    u[0] = dd[0] - sh;
+    if (fabsf(u[0]) < guard) u[0] = guard;
+    for (int i = 1; i < n; ++i) {
+      l[i] = ee[i - 1] / u[i - 1];
+      u[i] = dd[i] - sh - l[i] * ee[i - 1];
+      if (fabsf(u[i]) < guard) u[i] = copysignf(guard, u[i] == 0.f ? 1.f : u[i]);
+    }
+    for (int i = 0; i < n; ++i) y[i] = 1.0f + 0.1f * (float)((i * 7919 + j * 104729) % 17) / 17.f;
+    for (int it = 0; it < 3; ++it) {
+      for (int i = 1; i < n; ++i) y[i] -= l[i] * y[i - 1];
+      y[n - 1] /= u[n - 1];
+      for (int i = n - 2; i >= 0; --i) y[i] = (y[i] - ee[i] * y[i + 1]) / u[i];
+      float s = 0.f;
+      for (int i = 0; i < n; ++i) s += y[i] * y[i];
+      s = rsqrtf(fmaxf(s, 1e-30f));
+      for (int i = 0; i < n; ++i) y[i] *= s;
+    }
+  }
+  __syncthreads();
+  // Gram-Schmidt inside groups of near-equal eigenvalues (gap < 1e-4 * scale), one thread per
+  // group start
+  for (int j = threadIdx.x; j < nw; j += blockDim.x) {
+    if (j > 0 && lam[j] - lam[j - 1] < 1e-4f * scale) continue;   // not a group start
+    int end = j + 1;
+    while (end < nw && lam[end] - lam[end - 1] < 1e-4f * scale) ++end;
+    for (int c = j + 1; c < end; ++c) {
+      float* yc = H.Y + ((size_t)b * nw + c) * n;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int q = j; q < c; ++q) {
+          const float* yq = H.Y + ((size_t)b * nw + q) * n;
+          float dot = 0.f;
+          for (int i = 0; i < n; ++i) dot += yq[i] * yc[i];
+          for (int i = 0; i < n; ++i) yc[i] -= dot * yq[i];
+        }
+      float s = 0.f;
+      for (int i = 0; i < n; ++i) s += yc[i] * yc[i];
+      s = rsqrtf(fmaxf(s, 1e-30f));
+      for (int i = 0; i < n; ++i) yc[i] *= s;
+    }
+  }
+  (void)tnorm;
+}
+
+// Z[:, j] = Q D y_j, one warp per wanted vector; grid (ceil(nw / 8), nprob), 256 threads
+__global__ void __launch_bounds__(256) k_hh_back(HhArgs H) {
+  const int n = H.n, nw = H.nw, b = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * 8 + warp;
+  if (j >= nw) return;
+  const float* y = H.Y + ((size_t)b * nw + j) * n;
+  double2* z = H.Z + (size_t)b * n * nw + (size_t)j * n;
+  const float2* vq = H.vq + (size_t)b * n * n;
+  const float* beta = H.beta + (size_t)b * n;
+  const float2* e = H.e + (size_t)b * n;
+  // phases: d_0 = 1, d_{k+1} = d_k e_k / |e_k|  (lane 0 walks the chain, writes z = D y)
+  if (lane == 0) {
+    float2 ph = make_float2(1.f, 0.f);
+    for (int i = 0; i < n; ++i) {
+      z[i] = make_double2((double)(ph.x * y[i]), (double)(ph.y * y[i]));
+      if (i < n - 1) {
+        const float2 ek = e[i];
+        const float ae = sqrtf(ek.x * ek.x + ek.y * ek.y);
+        if (ae > 0.f) {
+          const float2 u = make_float2(ek.x / ae, ek.y / ae);
+          ph = make_float2(ph.x * u.x - ph.y * u.y, ph.x * u.y + ph.y * u.x);
+        }
+      }
+    }
+  }
+  __syncwarp();
+  for (int k = n - 3; k >= 0; --k) {
+    const float bet = beta[k];
+    if (bet == 0.f) continue;
+    const float2* v = vq + (size_t)k * n;   // entries k+1 .. n-1
+    double sr = 0.0, si = 0.0;              // s = v^H z
+    for (int i = k + 1 + lane; i < n; i += 32) {
+      const float2 vi = v[i];
+      const double2 zi = z[i];
+      sr += vi.x * zi.x + vi.y * zi.y;
+      si += vi.x * zi.y - vi.y * zi.x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    sr *= bet;
+    si *= bet;
+    for (int i = k + 1 + lane; i < n; i += 32) {
+      const float2 vi = v[i];
+      double2 zi = z[i];
+      zi.x -= vi.x * sr - vi.y * si;
+      zi.y -= vi.x * si + vi.y * sr;
+      z[i] = zi;
+    }
+    __syncwarp();
+  }
+}
+
+size_t hh_smem(int n) { return ((size_t)n * (n + 1) / 2 + 1 + 2 * (size_t)n) * sizeof(float2); }
+
+size_t hh_scratch_bytes(int n, int nw, int nprob) {
+  return (size_t)nprob * ((size_t)n * n * sizeof(float2) + 3 * n * sizeof(float) + n * sizeof(float2) +
+                          nw * sizeof(float) + (size_t)nw * n * sizeof(float) * 4 + sizeof(double) + 64) +
+         4096;
+}
+
+// FP32 stage: Z (FP64 storage, [nprob][n x nw]) holds approximate eigenvectors of the lowest nw
+// eigenvalues of each A (read only), lam32 their FP32 eigenvalues (shift added back in lam64).
+cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, int nprob, double2* Z,
+                            void* scratch, size_t scratch_bytes, double* lam64) {
+  if (hh_smem(n) > 226 * 1024 || nw > n || nw < 1) return cudaErrorInvalidValue;
+  if (hh_scratch_bytes(n, nw, nprob) > scratch_bytes) return cudaErrorInvalidValue;
+  unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
+  auto take = [&](size_t bytes) {
+    void* r = p;
+    p += (bytes + 255) & ~size_t(255);
+    return r;
+  };
+  HhArgs H;
+  H.n = n;
+  H.nw = nw;
+  H.A = A;
+  H.vq = (float2*)take((size_t)nprob * n * n * sizeof(float2));
+  H.beta = (float*)take((size_t)nprob * n * sizeof(float));
+  H.d = (float*)take((size_t)nprob * n * sizeof(float));
+  H.e = (float2*)take((size_t)nprob * n * sizeof(float2));
+  H.shift = (double*)take((size_t)nprob * sizeof(double));
+  H.lam = (float*)take((size_t)nprob * nw * sizeof(float));
+  H.Y = (float*)take((size_t)nprob * nw * n * sizeof(float));
+  H.work = (float*)take((size_t)nprob * nw * 3 * n * sizeof(float));
+  H.Z = Z;
+  H.lam64 = lam64;
+  cudaFuncSetAttribute(k_hh_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hh_smem(n));
+  k_hh_tridiag<<<nprob, HH_THREADS, hh_smem(n), st>>>(H);
+  k_tri_wanted<<<nprob, 256, (3 * n + nw) * sizeof(float), st>>>(H);
+  k_hh_back<<<dim3((nw + 7) / 8, nprob), 256, 0, st>>>(H);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- FP64 refinement kernels
+// First-order correction of the nw wanted vectors against all n vectors of Z:
+// R = Z^H Z_w (n x nw), S = Z^H A Z_w (n x nw), lamall [n] estimates of every eigenvalue.
+// E (n x nw): E_jj = (1 - R_jj)/2; E_ij = (S_ij - lam_j R_ij)/(lam_j - lam_i) (i != j) when that
+// is below 0.1 in size, else the orthogonality fix -R_ij/2 (near-degenerate pair).  Adds the
+// identity in rows < nw so that Z_w <- Z E is one GEMM.  grid (blocks, nprob)
+__global__ void k_oa_correction(const double2* R, const double2* S, int n, int nw, const double* lamall, double2* E) {
+  const int b = blockIdx.y;
+  const double2* r = R + (size_t)b * n * nw;
+  const double2* s = S + (size_t)b * n * nw;
+  double2* e = E + (size_t)b * n * nw;
+  const double* la = lamall + (size_t)b * n;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * nw; t += gridDim.x * blockDim.x) {
+    const int i = t % n, j = t / n;
+    const double2 rij = r[t];
+    const double lj = s[j + (size_t)j * n].x / r[j + (size_t)j * n].x;
+    if (i == j) {
+      e[t] = make_double2(1.0 + 0.5 * (1.0 - rij.x), 0.0);
+      continue;
+    }
+    const double2 sij = s[t];
+    const double li = i < nw ? s[i + (size_t)i * n].x / r[i + (size_t)i * n].x : la[i];
+    const double num_r = sij.x - lj * rij.x, num_i = sij.y - lj * rij.y;
+    const double den = lj - li;
+    const double mag = sqrt(num_r * num_r + num_i * num_i);
+    if (fabs(den) > 10.0 * mag && den != 0.0) e[t] = make_double2(num_r / den, num_i / den);
+    else e[t] = make_double2(-0.5 * rij.x, -0.5 * rij.y);
+  }
+}
+
+// links between consecutive wanted vectors that still couple noticeably in S_w = Z_w^H A Z_w
+// (nw x nw): grp[j] = 1 joins j and j+1 into one group
+__global__ void k_group_links(const double2* S, int nw, int* grp) {
+  const int b = blockIdx.x;
+  const double2* s = S + (size_t)b * nw * nw;
+  for (int j = threadIdx.x; j < nw; j += blockDim.x) {
+    int link = 0;
+    if (j + 1 < nw) {
+      const double dj = s[j + (size_t)j * nw].x, dk = s[(j + 1) + (size_t)(j + 1) * nw].x;
+      const double scale = 1.0 + fabs(dj) + fabs(dk);
+      // any coupling of j with a later vector that is not negligible against their gap
+      for (int k = j + 1; k < nw && k < j + 16; ++k) {
+        const double2 c = s[j + (size_t)k * nw];
+        const double ac = sqrt(c.x * c.x + c.y * c.y);
+        const double gap = fabs(s[k + (size_t)k * nw].x - dj);
+        if (ac > 1e-13 * scale && ac > 1e-8 * gap) {
+          link = 1;
+          break;
+        }
+      }
+      (void)dk;
+    }
+    grp[(size_t)b * nw + j] = link;
+  }
+}
+
+// Rayleigh-Ritz inside groups of consecutive vectors flagged by k_oa_correction: S (nw x nw,
+// FP64) restricted to a group is diagonalised by a serial cyclic Jacobi (one thread per group);
+// the group's rotation U is written into E (identity elsewhere) and the eigenvalues into lam.
+__global__ void k_group_rr(const double2* S, int nw, const int* grp, double* lam, int lstride, double2* U) {
+  const int b = blockIdx.x;
+  const double2* s = S + (size_t)b * nw * nw;
+  double2* u = U + (size_t)b * nw * nw;
+  double* l = lam + (size_t)b * lstride;
+  const int* g = grp + (size_t)b * nw;
+  for (int t = threadIdx.x; t < nw * nw; t += blockDim.x) u[t] = make_double2((t % nw) == (t / nw) ? 1.0 : 0.0, 0.0);
+  __syncthreads();
+  for (int j0 = threadIdx.x; j0 < nw; j0 += blockDim.x) {
+    if (j0 > 0 && g[j0 - 1]) continue;          // not a group start
+    int end = j0 + 1;                            // group = [j0, end)
+    while (end < nw && g[end - 1]) ++end;
+    const int m = end - j0;
+    if (m == 1) {
+      l[j0] = s[j0 + (size_t)j0 * nw].x;
+      continue;
+    }
+    if (m > 16) {   // larger groups keep the first-order result
+      for (int c = 0; c < m; ++c) l[j0 + c] = s[(j0 + c) + (size_t)(j0 + c) * nw].x;
+      continue;
+    }
+    double2 a[16][16], v[16][16];
+    for (int i = 0; i < m; ++i)
+      for (int k = 0; k < m; ++k) {
+        a[i][k] = s[(j0 + i) + (size_t)(j0 + k) * nw];
+        v[i][k] = make_double2(i == k ? 1.0 : 0.0, 0.0);
+      }
+    for (int sweep = 0; sweep < 30; ++sweep) {
+      double off = 0.0;
+      for (int p = 0; p < m; ++p)
+        for (int q = p + 1; q < m; ++q) off += a[p][q].x * a[p][q].x + a[p][q].y * a[p][q].y;
+      if (off < 1e-30) break;
+      for (int p = 0; p < m; ++p)
+        for (int q = p + 1; q < m; ++q) {
+          const double2 c = a[p][q];
+          const double ac = hypot(c.x, c.y);
+          if (ac < 1e-300) continue;
+          const double zeta = (a[q][q].x - a[p][p].x) / (2.0 * ac);
+          const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+          const double er = c.x / ac, ei = c.y / ac;
+          // rows: p' = cs a_p - sn e a_q ; q' = sn a_p + cs e a_q  (J^H A)
+          for (int k = 0; k < m; ++k) {
+            const double2 ap = a[p][k], aq = a[q][k];
+            const double2 eq = make_double2(er * aq.x - ei * aq.y, er * aq.y + ei * aq.x);
+            a[p][k] = make_double2(cs * ap.x - sn * eq.x, cs * ap.y - sn * eq.y);
+            a[q][k] = make_double2(sn * ap.x + cs * eq.x, sn * ap.y + cs * eq.y);
+          }
+          // cols: p' = cs a_p - sn conj(e) a_q ; q' = sn a_p + cs conj(e) a_q  (A J), same for V
+          for (int k = 0; k < m; ++k) {
+            const double2 ap = a[k][p], aq = a[k][q];
+            const double2 cq = make_double2(er * aq.x + ei * aq.y, er * aq.y - ei * aq.x);
+            a[k][p] = make_double2(cs * ap.x - sn * cq.x, cs * ap.y - sn * cq.y);
+            a[k][q] = make_double2(sn * ap.x + cs * cq.x, sn * ap.y + cs * cq.y);
+            const double2 vp = v[k][p], vq = v[k][q];
+            const double2 cv = make_double2(er * vq.x + ei * vq.y, er * vq.y - ei * vq.x);
+            v[k][p] = make_double2(cs * vp.x - sn * cv.x, cs * vp.y - sn * cv.y);
+            v[k][q] = make_double2(sn * vp.x + cs * cv.x, sn * vp.y + cs * cv.y);
+          }
+        }
+    }
+    // sort the group ascending (selection) and write U, lam
+    int ord[16];
+    for (int i = 0; i < m; ++i) ord[i] = i;
+    for (int i = 0; i < m; ++i)
+      for (int k = i + 1; k < m; ++k)
+        if (a[ord[k]][ord[k]].x < a[ord[i]][ord[i]].x) { const int tt = ord[i]; ord[i] = ord[k]; ord[k] = tt; }
+    for (int c = 0; c < m; ++c) {
+      l[j0 + c] = a[ord[c]][ord[c]].x;
+      for (int i = 0; i < m; ++i) u[(j0 + i) + (size_t)(j0 + c) * nw] = v[i][ord[c]];
+    }
+  }
+}
+
+cudaError_t launch_oa_correction(cudaStream_t st, const double2* R, const double2* S, int n, int nw, int nprob,
+                                 const double* lamall, double2* E) {
+  k_oa_correction<<<dim3(16, nprob), 256, 0, st>>>(R, S, n, nw, lamall, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_rr(cudaStream_t st, const double2* Sw, int nw, int nprob, int* grp, double* lam,
+                            int lstride, double2* U) {
+  k_group_links<<<nprob, 128, 0, st>>>(Sw, nw, grp);
+  k_group_rr<<<nprob, 64, 0, st>>>(Sw, nw, grp, lam, lstride, U);
+  return cudaGetLastError();
+}
+
+// add the identity to E (so that Z (I + E) is one GEMM); grid (8, nprob)
+__global__ void k_add_identity(double2* E, int nw) {
+  const int b = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += gridDim.x * blockDim.x)
+    E[(size_t)b * nw * nw + i + (size_t)i * nw].x += 1.0;
+}
+
+}  // namespace hw
+
+// ===================================================================== Cholesky-QR apply
+// W <- W (L^H)^{-1} for each k-point, one thread per row: row w of W solves y L^H = w, i.e.
+// y_j = (w_j - sum_{i<j} conj(L_ji) y_i) / L_jj, in place.  L (m x m, lower, from k_chol) is
+// staged in shared memory.  W: rows x m block with leading dimension ld, batch stride sW.
+namespace hw {
+__global__ void __launch_bounds__(128) k_trsm_lh(const double2* L, int m, double2* W, int64_t rows, int64_t ld,
+                                                 int64_t sW) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* Ls = reinterpret_cast<double2*>(smem_raw);
+  const int b = blockIdx.y;
+  const double2* l = L + (size_t)b * m * m;
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) Ls[t] = l[t];
+  __syncthreads();
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  double2* w = W + (size_t)b * sW + r;
+  for (int j = 0; j < m; ++j) {
+    double2 acc = w[(size_t)j * ld];
+    for (int i = 0; i < j; ++i) {
+      const double2 lji = Ls[j + (size_t)i * m];   // L[j][i]
+      const double2 yi = w[(size_t)i * ld];
+      // acc -= conj(lji) * yi
+      acc.x -= lji.x * yi.x + lji.y * yi.y;
+      acc.y -= lji.x * yi.y - lji.y * yi.x;
+    }
+    const double inv = 1.0 / Ls[j + (size_t)j * m].x;
+    w[(size_t)j * ld] = make_double2(acc.x * inv, acc.y * inv);
+  }
+}
+
+cudaError_t dense_trsm_lh(cudaStream_t st, const double2* L, int m, int nprob, double2* W, int64_t rows, int64_t ld,
+                          int64_t sW) {
+  const size_t smem = (size_t)m * m * sizeof(double2);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  cudaFuncSetAttribute(k_trsm_lh, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  k_trsm_lh<<<dim3((unsigned)((rows + 127) / 128), nprob), 128, smem, st>>>(L, m, W, rows, ld, sW);
+  return cudaGetLastError();
+}
+}  // namespace hw

@@ -43,6 +43,16 @@ cudaError_t dense_heev32(cudaStream_t st, const double2* A, int n, int nprob, do
                          void* scratch, size_t scratch_bytes, int maxsweep);
 size_t heev32_scratch_bytes(int n, int nprob, int maxsweep);
 size_t jac32_smem(int n);
+size_t hh_smem(int n);
+cudaError_t dense_trsm_lh(cudaStream_t st, const double2* L, int m, int nprob, double2* W, int64_t rows, int64_t ld,
+                          int64_t sW);
+size_t hh_scratch_bytes(int n, int nw, int nprob);
+cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, int nprob, double2* Z,
+                            void* scratch, size_t scratch_bytes, double* lam64);
+cudaError_t launch_oa_correction(cudaStream_t st, const double2* R, const double2* S, int n, int nw, int nprob,
+                                 const double* lamall, double2* E);
+cudaError_t launch_group_rr(cudaStream_t st, const double2* Sw, int nw, int nprob, int* grp, double* lam,
+                            int lstride, double2* U);
 constexpr int J32_SWEEPS = 12;
 // Rayleigh-Ritz in FP32 while residuals exceed this.  Measured on the tube workload the FP32
 // phase raised the iteration count (60 -> 71) without lowering the eigensolver time (the
@@ -73,6 +83,12 @@ struct LobpcgWork {
   DenseWork* dw = nullptr;
   void* j32 = nullptr;      // FP32 Jacobi scratch (rotation log, unsorted pairs)
   size_t j32_bytes = 0;
+  void* hh = nullptr;       // Householder eigensolver scratch
+  size_t hh_bytes = 0;
+  double2* B1 = nullptr;    // [nk][ne*nb] refinement buffers
+  double2* B2 = nullptr;
+  double2* B3 = nullptr;
+  int* grp = nullptr;       // [nk][nb]
 };
 
 void lobpcg_free(hw_ctx* ctx) {
@@ -81,7 +97,8 @@ void lobpcg_free(hw_ctx* ctx) {
   for (void* p : {(void*)w->SB[0], (void*)w->SB[1], (void*)w->HSB[0], (void*)w->HSB[1], (void*)w->R,
                   (void*)w->A, (void*)w->Z, (void*)w->w, (void*)w->G, (void*)w->Ui, (void*)w->C,
                   (void*)w->Y, (void*)w->Y2, (void*)w->res, (void*)w->theta, (void*)w->iact,
-                  (void*)w->fail, (void*)w->status, w->j32})
+                  (void*)w->fail, (void*)w->status, w->j32, w->hh, (void*)w->B1, (void*)w->B2,
+                  (void*)w->B3, (void*)w->grp})
     if (p) cudaFree(p);
   dense_free(w->dw);
   delete w;
@@ -275,15 +292,9 @@ static hw_status cholqr(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, double2* S, int 
       ProfScope ps_(ctx, HW_PH_CHOL);
       dense_hermitize(ctx->stream, w->G, ncol, nk);
       dense_chol(ctx->stream, w->G, ncol, nk, w->fail);
-      dense_trinv(ctx->stream, w->G, w->Ui, ncol, nk);
+      dense_trsm_lh(ctx->stream, w->G, ncol, nk, Wb, Lpad, Lpad, sK);   // W <- W L^{-H}, in place
       ctx->launches += 3;
     }
-    // R-buffer as temporary: T = W Ui, then copy back
-    gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, ncol, ncol, 1.0, Wb, Lpad, sK, w->Ui, ncol, (int64_t)ncol * ncol,
-         0.0, w->R, Lpad, Lpad * w->nb, nk);
-    for (int b = 0; b < nk; ++b)
-      cudaMemcpyAsync(Wb + (size_t)b * sK, w->R + (size_t)b * Lpad * w->nb, (size_t)Lpad * ncol * sizeof(double2),
-                      cudaMemcpyDeviceToDevice, ctx->stream);
     std::vector<int> f(nk);
     cudaMemcpyAsync(f.data(), w->fail, nk * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -298,10 +309,52 @@ static hw_status cholqr(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, double2* S, int 
 // w->Z eigenvector columns.  fp32: FP32 Jacobi, then the first nb vectors are made orthonormal
 // in FP64 (two Newton-Schulz steps) and their Rayleigh quotients recomputed in FP64; else the
 // FP64 Jacobi.
+// Householder route: FP32 tridiagonalisation, bisection, inverse iteration and back-transform
+// for all n vectors, then two FP64 first-order corrections of the wanted nb vectors against
+// all n, then FP64 Rayleigh-Ritz inside groups of near-degenerate wanted vectors.
+static cudaError_t rr_eig_hh(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int nb) {
+  cudaStream_t st = ctx->stream;
+  const int nk = w->nk;
+  cudaError_t e;
+  {
+    ProfScope ps_(ctx, HW_PH_EIG);
+    dense_hermitize(st, w->A, n, nk);
+    e = dense_heev_hh32(st, w->A, n, n, nk, w->Z, w->hh, w->hh_bytes, w->w);
+    ctx->launches += 4;
+  }
+  if (e != cudaSuccess) return e;
+  const int64_t sZ = (int64_t)n * n, sB = (int64_t)n * nb;
+  for (int it = 0; it < 2; ++it) {
+    gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, n, 1.0, w->A, n, sZ, w->Z, n, sZ, 0.0, w->B1, n, sB, nk);   // A Z_w
+    gemm(CUBLAS_OP_C, CUBLAS_OP_N, n, nb, n, 1.0, w->Z, n, sZ, w->B1, n, sB, 0.0, w->B2, n, sB, nk);  // Z^H A Z_w
+    gemm(CUBLAS_OP_C, CUBLAS_OP_N, n, nb, n, 1.0, w->Z, n, sZ, w->Z, n, sZ, 0.0, w->B3, n, sB, nk);   // Z^H Z_w
+    {
+      ProfScope ps_(ctx, HW_PH_EIG);
+      e = launch_oa_correction(st, w->B3, w->B2, n, nb, nk, w->w, w->B1);
+      ctx->launches++;
+    }
+    if (e != cudaSuccess) return e;
+    gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, n, 1.0, w->Z, n, sZ, w->B1, n, sB, 0.0, w->B2, n, sB, nk);   // Z E
+    cudaMemcpy2DAsync(w->Z, (size_t)sZ * 16, w->B2, (size_t)sB * 16, (size_t)sB * 16, nk, cudaMemcpyDeviceToDevice, st);
+  }
+  gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, n, 1.0, w->A, n, sZ, w->Z, n, sZ, 0.0, w->B1, n, sB, nk);
+  gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, n, 1.0, w->Z, n, sZ, w->B1, n, sB, 0.0, w->G, nb, (int64_t)nb * nb, nk);
+  {
+    ProfScope ps_(ctx, HW_PH_EIG);
+    e = launch_group_rr(st, w->G, nb, nk, w->grp, w->w, n, w->Ui);
+    ctx->launches += 2;
+  }
+  if (e != cudaSuccess) return e;
+  gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, nb, 1.0, w->Z, n, sZ, w->Ui, nb, (int64_t)nb * nb, 0.0, w->B2, n, sB, nk);
+  cudaMemcpy2DAsync(w->Z, (size_t)sZ * 16, w->B2, (size_t)sB * 16, (size_t)sB * 16, nk, cudaMemcpyDeviceToDevice, st);
+  return cudaGetLastError();
+}
+
 static cudaError_t rr_eig(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int nb, bool fp32) {
   cudaStream_t st = ctx->stream;
   const int nk = w->nk;
   cudaError_t e;
+  if (w->hh && hh_smem(n) <= 226 * 1024) return rr_eig_hh(ctx, w, gemm, n, nb);
   if (fp32 && w->j32 && jac32_smem(n) <= 226 * 1024) {
     {
       ProfScope ps_(ctx, HW_PH_EIG);
@@ -397,6 +450,14 @@ static hw_status ensure_work(hw_ctx* ctx, int nk, int nb, int64_t Lpad) {
   A((void**)&w->fail, (size_t)nk * sizeof(int));
   A((void**)&w->status, sizeof(int));
   if (e == cudaSuccess) e = dense_alloc(w->dw, nk * ne2, nk);
+  if (e == cudaSuccess && hh_smem(w->ne) <= 226 * 1024) {
+    w->hh_bytes = hh_scratch_bytes(w->ne, w->ne, nk);
+    e = cudaMalloc(&w->hh, w->hh_bytes);
+    A((void**)&w->B1, (size_t)nk * w->ne * nb * sizeof(double2));
+    A((void**)&w->B2, (size_t)nk * w->ne * nb * sizeof(double2));
+    A((void**)&w->B3, (size_t)nk * w->ne * nb * sizeof(double2));
+    A((void**)&w->grp, (size_t)nk * nb * sizeof(int));
+  }
   if (e == cudaSuccess && jac32_smem(w->ne) <= 226 * 1024) {
     w->j32_bytes = heev32_scratch_bytes(w->ne, nk, J32_SWEEPS);
     e = cudaMalloc(&w->j32, w->j32_bytes);
@@ -746,12 +807,9 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
         ProfScope ps_(ctx, HW_PH_CHOL);
         dense_hermitize(st, w->G, na, nk);
         dense_chol(st, w->G, na, nk, w->fail);
-        dense_trinv(st, w->G, w->Ui, na, nk);
+        dense_trsm_lh(st, w->G, na, nk, w->Y, n, n, (int64_t)n * na);   // Y <- Y L^{-H}, in place
         ctx->launches += 3;
       }
-      gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, na, na, 1.0, w->Y, n, (int64_t)n * na, w->Ui, na, (int64_t)na * na, 0.0, w->Y2,
-           n, (int64_t)n * na, nk);
-      std::swap(w->Y, w->Y2);
       std::vector<int> f(nk);
       cudaMemcpyAsync(f.data(), w->fail, nk * sizeof(int), cudaMemcpyDeviceToHost, st);
       cudaStreamSynchronize(st);
@@ -802,6 +860,40 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
   if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
   if (gemm.st != CUBLAS_STATUS_SUCCESS) return hw_fail(ctx, HW_ECUDA, "cuBLAS failure");
   if (final_status != HW_OK) return hw_fail(ctx, HW_ENOTCONV, "maxit reached before convergence");
+  return HW_OK;
+}
+
+extern "C" hw_status hw_heev(hw_ctx* ctx, int n, int nprob, int nw, const double* A, double* w, double* Z,
+                              int method) {
+  if (!ctx) return HW_EINVAL;
+  if (ctx->device < 0) return hw_fail(ctx, HW_ESTATE, "host-only context has no device");
+  if (n < 2 || (n & 1) || nprob < 1 || nprob > MAXSLOT || nw < 1 || nw > n || !A || !w || !Z)
+    return hw_fail(ctx, HW_EINVAL, "need even n >= 2, 1 <= nprob <= 64, 1 <= nw <= n");
+  if (method != 0 && method != 1) return hw_fail(ctx, HW_EINVAL, "method 0 (Jacobi) or 1 (Householder)");
+  const int nbw = std::max(nw, (n + 2) / 3);
+  if (3 * nbw + ((3 * nbw) & 1) < n) return hw_fail(ctx, HW_EINVAL, "size");
+  cudaSetDevice(ctx->device);
+  hw_status hs = ensure_work(ctx, nprob, nbw, 8);
+  if (hs != HW_OK) return hs;
+  LobpcgWork* wk = ctx->lw;
+  if (method == 1 && !(wk->hh && hh_smem(n) <= 226 * 1024))
+    return hw_fail(ctx, HW_EINVAL, "n too large for the Householder route (shared-memory bound)");
+  cudaStream_t st = ctx->stream;
+  cudaMemcpyAsync(wk->A, A, (size_t)nprob * n * n * 16, cudaMemcpyDeviceToDevice, st);
+  Gemm gemm{ctx};
+  cudaError_t e;
+  if (method == 1) {
+    e = rr_eig_hh(ctx, wk, gemm, n, nw);
+  } else {
+    ProfScope ps_(ctx, HW_PH_EIG);
+    dense_hermitize(st, wk->A, n, nprob);
+    e = dense_heev(wk->dw, st, wk->A, n, nprob, wk->w, wk->Z, wk->status, 1e-14);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w, wk->w, (size_t)nprob * n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Z, wk->Z, (size_t)nprob * n * n * 16, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("heev: ") + cudaGetErrorString(e));
+  if (gemm.st != CUBLAS_STATUS_SUCCESS) return hw_fail(ctx, HW_ECUDA, "cuBLAS failure in heev");
   return HW_OK;
 }
 

@@ -65,6 +65,8 @@ _SIGS = {
                                 C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p),
                                 _D, C.POINTER(C.c_void_p), C.c_int64, C.POINTER(C.c_int), _D]),
     "hw_synchronize": (C.c_int, [C.c_void_p]),
+    "hw_heev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                          C.c_int]),
     "hw_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "hw_profile_read": (C.c_int, [C.c_void_p, _D, C.POINTER(C.c_int64)]),
     "hw_launch_count": (C.c_int64, [C.c_void_p]),
@@ -233,6 +235,20 @@ def hw_solve_eigs(h, kidx, n_eig, block=0, tol=1e-6, maxit=500, prec=HW_FP64,
 
 def hw_synchronize(h):
     _check(h, load_library().hw_synchronize(h))
+
+
+def hw_heev(h, A, nw, method=1):
+    """A: (nprob, n, n) complex128 CUDA tensor of Hermitian matrices (row j of A[b] holds
+    column j).  Returns (w, Z) as CUDA tensors: w (nprob, n), Z (nprob, n, n) with Z[b][j] the
+    j-th eigenvector."""
+    import torch
+    nprob, n, _ = A.shape
+    A = A.contiguous()
+    w = torch.zeros((nprob, n), dtype=torch.float64, device=A.device)
+    Z = torch.zeros_like(A)
+    _check(h, load_library().hw_heev(h, n, nprob, nw, C.c_void_p(A.data_ptr()), C.c_void_p(w.data_ptr()),
+                                     C.c_void_p(Z.data_ptr()), method))
+    return w, Z
 
 
 def hw_profile(h, enable: bool):
