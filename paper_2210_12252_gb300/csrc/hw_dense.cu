@@ -1004,8 +1004,12 @@ __global__ void __launch_bounds__(256) k_tri_wanted(HhArgs H) {
   }
   __syncthreads();
   // inverse iteration (LU without pivoting, guarded pivots), one thread per wanted vector
+  // scale of the valid spectrum (padding eigenvalues sit near 1e10 and must not set it)
   float scale = 0.f;
-  for (int i = 0; i < nw; ++i) scale = fmaxf(scale, fabsf(lam[i]));
+  for (int i = 0; i < nw; ++i)
+    if (fabsf(lam[i]) < 1e9f) scale = fmaxf(scale, fabsf(lam[i]));
+  for (int i = 0; i < n - 1; ++i)
+    if (ee[i] < 1e9f) scale = fmaxf(scale, ee[i]);
   scale = fmaxf(scale, 1e-6f);
   for (int j = threadIdx.x; j < nw; j += blockDim.x) {
     float* y = H.Y + ((size_t)b * nw + j) * n;
@@ -1038,7 +1042,7 @@ __global__ void __launch_bounds__(256) k_tri_wanted(HhArgs H) {
   for (int j = threadIdx.x; j < nw; j += blockDim.x) {
     if (j > 0 && lam[j] - lam[j - 1] < 1e-4f * scale) continue;   // not a group start
     int end = j + 1;
-    while (end < nw && lam[end] - lam[end - 1] < 1e-4f * scale) ++end;
+    while (end < nw && lam[end] - lam[end - 1] < 1e-4f * scale && end - j < 32) ++end;
     for (int c = j + 1; c < end; ++c) {
       float* yc = H.Y + ((size_t)b * nw + c) * n;
       for (int pass = 0; pass < 2; ++pass)
