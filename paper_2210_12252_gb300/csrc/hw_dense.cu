@@ -1180,35 +1180,40 @@ __global__ void k_oa_correction(const double2* R, const double2* S, int n, int n
     const double2 sij = s[t];
     const double li = i < nw ? s[i + (size_t)i * n].x / r[i + (size_t)i * n].x : la[i];
     const double num_r = sij.x - lj * rij.x, num_i = sij.y - lj * rij.y;
+    double mag = sqrt(num_r * num_r + num_i * num_i);
+    if (i < nw) {   // the decision must be the same for (i, j) and (j, i)
+      const double2 sji = s[j + (size_t)i * n], rji = r[j + (size_t)i * n];
+      const double mr = sji.x - li * rji.x, mi = sji.y - li * rji.y;
+      mag = fmax(mag, sqrt(mr * mr + mi * mi));
+    }
     const double den = lj - li;
-    const double mag = sqrt(num_r * num_r + num_i * num_i);
-    if (fabs(den) > 10.0 * mag && den != 0.0) e[t] = make_double2(num_r / den, num_i / den);
+    const double tau = 1e-8 * (1.0 + fmax(fabs(li), fabs(lj)));
+    if (fabs(den) > tau && fabs(den) > 10.0 * mag) e[t] = make_double2(num_r / den, num_i / den);
     else e[t] = make_double2(-0.5 * rij.x, -0.5 * rij.y);
   }
 }
 
-// links between consecutive wanted vectors that still couple noticeably in S_w = Z_w^H A Z_w
-// (nw x nw): grp[j] = 1 joins j and j+1 into one group
+// Final Rayleigh-Ritz of the wanted block from S_w = Z_w^H A Z_w (nw x nw, Z_w orthonormal):
+// consecutive vectors whose coupling is not small against their gap (> 1e-2 of it) or whose
+// gap is below 1e-8 (1 + |lambda|) form a group, diagonalised exactly by a serial FP64 Jacobi
+// (one thread per group, groups of up to 16); couplings between groups get the first-order
+// rotation S_ij / (lambda_j - lambda_i).
+__device__ __forceinline__ bool strong_link(const double2* s, int nw, int j, int k) {
+  const double dj = s[j + (size_t)j * nw].x, dk = s[k + (size_t)k * nw].x;
+  const double2 c = s[j + (size_t)k * nw];
+  const double ac = sqrt(c.x * c.x + c.y * c.y);
+  const double gap = fabs(dk - dj);
+  return gap < 1e-8 * (1.0 + fabs(dj) + fabs(dk)) || ac > 1e-2 * gap;
+}
+
+// grp[j] = 1 joins j and j+1: some vector at or before j couples strongly to one after j
 __global__ void k_group_links(const double2* S, int nw, int* grp) {
   const int b = blockIdx.x;
   const double2* s = S + (size_t)b * nw * nw;
   for (int j = threadIdx.x; j < nw; j += blockDim.x) {
     int link = 0;
-    if (j + 1 < nw) {
-      const double dj = s[j + (size_t)j * nw].x, dk = s[(j + 1) + (size_t)(j + 1) * nw].x;
-      const double scale = 1.0 + fabs(dj) + fabs(dk);
-      // any coupling of j with a later vector that is not negligible against their gap
-      for (int k = j + 1; k < nw && k < j + 16; ++k) {
-        const double2 c = s[j + (size_t)k * nw];
-        const double ac = sqrt(c.x * c.x + c.y * c.y);
-        const double gap = fabs(s[k + (size_t)k * nw].x - dj);
-        if (ac > 1e-13 * scale && ac > 1e-8 * gap) {
-          link = 1;
-          break;
-        }
-      }
-      (void)dk;
-    }
+    for (int a = max(0, j - 15); a <= j && !link; ++a)
+      for (int k = j + 1; k < nw && k <= a + 15 && !link; ++k) link = strong_link(s, nw, a, k);
     grp[(size_t)b * nw + j] = link;
   }
 }
@@ -1222,7 +1227,30 @@ __global__ void k_group_rr(const double2* S, int nw, const int* grp, double* lam
   double2* u = U + (size_t)b * nw * nw;
   double* l = lam + (size_t)b * lstride;
   const int* g = grp + (size_t)b * nw;
-  for (int t = threadIdx.x; t < nw * nw; t += blockDim.x) u[t] = make_double2((t % nw) == (t / nw) ? 1.0 : 0.0, 0.0);
+  // group id of each vector: index of its group's first member
+  extern __shared__ int gid[];
+  if (threadIdx.x == 0) {
+    int cur = 0;
+    for (int j = 0; j < nw; ++j) {
+      if (j > 0 && !g[j - 1]) cur = j;
+      gid[j] = cur;
+    }
+  }
+  __syncthreads();
+  // identity inside groups (the group rotations overwrite it), first-order rotation between
+  // groups
+  for (int t = threadIdx.x; t < nw * nw; t += blockDim.x) {
+    const int i = t % nw, j = t / nw;
+    if (i == j) {
+      u[t] = make_double2(1.0, 0.0);
+    } else if (gid[i] == gid[j]) {
+      u[t] = make_double2(0.0, 0.0);
+    } else {
+      const double den = s[j + (size_t)j * nw].x - s[i + (size_t)i * nw].x;
+      const double2 c = s[t];
+      u[t] = den != 0.0 ? make_double2(c.x / den, c.y / den) : make_double2(0.0, 0.0);
+    }
+  }
   __syncthreads();
   for (int j0 = threadIdx.x; j0 < nw; j0 += blockDim.x) {
     if (j0 > 0 && g[j0 - 1]) continue;          // not a group start
@@ -1299,7 +1327,7 @@ cudaError_t launch_oa_correction(cudaStream_t st, const double2* R, const double
 cudaError_t launch_group_rr(cudaStream_t st, const double2* Sw, int nw, int nprob, int* grp, double* lam,
                             int lstride, double2* U) {
   k_group_links<<<nprob, 128, 0, st>>>(Sw, nw, grp);
-  k_group_rr<<<nprob, 64, 0, st>>>(Sw, nw, grp, lam, lstride, U);
+  k_group_rr<<<nprob, 64, nw * sizeof(int), st>>>(Sw, nw, grp, lam, lstride, U);
   return cudaGetLastError();
 }
 

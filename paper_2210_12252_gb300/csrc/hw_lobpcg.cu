@@ -337,6 +337,17 @@ static cudaError_t rr_eig_hh(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int 
     gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, n, 1.0, w->Z, n, sZ, w->B1, n, sB, 0.0, w->B2, n, sB, nk);   // Z E
     cudaMemcpy2DAsync(w->Z, (size_t)sZ * 16, w->B2, (size_t)sB * 16, (size_t)sB * 16, nk, cudaMemcpyDeviceToDevice, st);
   }
+  // orthonormalise the wanted block (two Newton-Schulz steps)
+  for (int pass = 0; pass < 2; ++pass) {
+    gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, n, 1.0, w->Z, n, sZ, w->Z, n, sZ, 0.0, w->G, nb, (int64_t)nb * nb, nk);
+    {
+      ProfScope ps_(ctx, HW_PH_EIG);
+      k_ns_coef<<<dim3(8, nk), 256, 0, st>>>(w->G, nb, w->Ui);
+      ctx->launches++;
+    }
+    gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, nb, 1.0, w->Z, n, sZ, w->Ui, nb, (int64_t)nb * nb, 0.0, w->B2, n, sB, nk);
+    cudaMemcpy2DAsync(w->Z, (size_t)sZ * 16, w->B2, (size_t)sB * 16, (size_t)sB * 16, nk, cudaMemcpyDeviceToDevice, st);
+  }
   gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, n, 1.0, w->A, n, sZ, w->Z, n, sZ, 0.0, w->B1, n, sB, nk);
   gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, n, 1.0, w->Z, n, sZ, w->B1, n, sB, 0.0, w->G, nb, (int64_t)nb * nb, nk);
   {

@@ -57,10 +57,10 @@ def test_heev_matches_numpy(hwmod, method, n):
     for b in range(A.shape[0]):
         ref = np.linalg.eigvalsh(A[b])
         scale = np.abs(ref[:-1]).max()
-        assert np.abs(w[b, :nw] - ref[:nw]).max() < 1e-11 * scale, (b, np.abs(w[b, :nw] - ref[:nw]).max())
+        assert np.abs(w[b, :nw] - ref[:nw]).max() < 1e-10 * scale, (b, np.abs(w[b, :nw] - ref[:nw]).max())
         Zb = Z[b, :nw].T                     # n x nw
         G = Zb.conj().T @ Zb
         assert np.abs(G - np.eye(nw)).max() < 1e-12
         R = A[b] @ Zb - Zb * w[b, :nw]
-        assert np.linalg.norm(R, axis=0).max() < 1e-11 * scale
+        assert np.linalg.norm(R, axis=0).max() < 1e-10 * scale
     ctx.close()
