@@ -947,6 +947,18 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
   }
 }
 
+// deterministic pseudo-random value in [-1, 1] for (problem, vector, entry, attempt)
+__device__ __forceinline__ float hash_unit(int b, int j, int i, int a) {
+  unsigned int x = (unsigned int)(b * 73856093) ^ (unsigned int)(j * 19349663) ^ (unsigned int)(i * 83492791) ^
+                   (unsigned int)(a * 2654435761u);
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return (float)(x & 0xFFFFFF) * (2.0f / 16777215.0f) - 1.0f;
+}
+
 // eigenvalues count below x of the real tridiagonal (diag dd, off-diagonal magnitudes ee)
 __device__ __forceinline__ int sturm32(const float* dd, const float* ee2, int n, float x, float pivmin) {
   int c = 0;
@@ -1025,7 +1037,7 @@ __global__ void __launch_bounds__(256) k_tri_wanted(HhArgs H) {
       u[i] = dd[i] - sh - l[i] * ee[i - 1];
       if (fabsf(u[i]) < guard) u[i] = copysignf(guard, u[i] == 0.f ? 1.f : u[i]);
     }
-    for (int i = 0; i < n; ++i) y[i] = 1.0f + 0.1f * (float)((i * 7919 + j * 104729) % 17) / 17.f;
+    for (int i = 0; i < n; ++i) y[i] = hash_unit(b, j, i, 0);
     for (int it = 0; it < 3; ++it) {
       for (int i = 1; i < n; ++i) y[i] -= l[i] * y[i - 1];
       y[n - 1] /= u[n - 1];
@@ -1045,17 +1057,35 @@ __global__ void __launch_bounds__(256) k_tri_wanted(HhArgs H) {
     while (end < nw && lam[end] - lam[end - 1] < 1e-4f * scale && end - j < 32) ++end;
     for (int c = j + 1; c < end; ++c) {
       float* yc = H.Y + ((size_t)b * nw + c) * n;
-      for (int pass = 0; pass < 2; ++pass)
-        for (int q = j; q < c; ++q) {
-          const float* yq = H.Y + ((size_t)b * nw + q) * n;
-          float dot = 0.f;
-          for (int i = 0; i < n; ++i) dot += yq[i] * yc[i];
-          for (int i = 0; i < n; ++i) yc[i] -= dot * yq[i];
+      // if the group's earlier vectors absorb almost all of this one (exactly degenerate,
+      // decoupled eigenvalues give parallel inverse-iteration vectors), restart from a fresh
+      // random vector of the group's subspace directions
+      for (int attempt = 0; attempt < 4; ++attempt) {
+        for (int pass = 0; pass < 2; ++pass)
+          for (int q = j; q < c; ++q) {
+            const float* yq = H.Y + ((size_t)b * nw + q) * n;
+            float dot = 0.f;
+            for (int i = 0; i < n; ++i) dot += yq[i] * yc[i];
+            for (int i = 0; i < n; ++i) yc[i] -= dot * yq[i];
+          }
+        float s = 0.f;
+        for (int i = 0; i < n; ++i) s += yc[i] * yc[i];
+        if (s > 1e-4f) {
+          s = rsqrtf(s);
+          for (int i = 0; i < n; ++i) yc[i] *= s;
+          break;
         }
-      float s = 0.f;
-      for (int i = 0; i < n; ++i) s += yc[i] * yc[i];
-      s = rsqrtf(fmaxf(s, 1e-30f));
-      for (int i = 0; i < n; ++i) yc[i] *= s;
+        // fresh start: random combination of the group's vectors' supports, then orthogonalise
+        for (int i = 0; i < n; ++i) {
+          float t = 0.f;
+          for (int q = j; q < c; ++q) t += fabsf((H.Y + ((size_t)b * nw + q) * n)[i]);
+          yc[i] = hash_unit(b, c, i, attempt + 1) * (t > 0.f ? 1.f : 0.05f);
+        }
+        float s2 = 0.f;
+        for (int i = 0; i < n; ++i) s2 += yc[i] * yc[i];
+        s2 = rsqrtf(fmaxf(s2, 1e-30f));
+        for (int i = 0; i < n; ++i) yc[i] *= s2;
+      }
     }
   }
   (void)tnorm;
