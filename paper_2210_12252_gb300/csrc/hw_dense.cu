@@ -1354,10 +1354,26 @@ cudaError_t launch_oa_correction(cudaStream_t st, const double2* R, const double
   return cudaGetLastError();
 }
 
+// order the wanted pairs by eigenvalue: column rank(j) of Uout = column j of U
+__global__ void k_sort_wanted(const double* lam_in, int lstride, const double2* U, int nw, double* lam_out,
+                              double2* Uout) {
+  const int b = blockIdx.x;
+  const double* l = lam_in + (size_t)b * lstride;
+  for (int j = threadIdx.x; j < nw; j += blockDim.x) {
+    const double dj = l[j];
+    int rank = 0;
+    for (int i = 0; i < nw; ++i) rank += (l[i] < dj) || (l[i] == dj && i < j);
+    lam_out[(size_t)b * lstride + rank] = dj;
+    for (int r = 0; r < nw; ++r) Uout[(size_t)b * nw * nw + r + (size_t)rank * nw] = U[(size_t)b * nw * nw + r + (size_t)j * nw];
+  }
+}
+
+// groups and first-order couplings (U, lam unsorted into tmp buffers), then sorted into U / lam
 cudaError_t launch_group_rr(cudaStream_t st, const double2* Sw, int nw, int nprob, int* grp, double* lam,
-                            int lstride, double2* U) {
+                            int lstride, double2* U, double* lam_tmp, double2* U_tmp) {
   k_group_links<<<nprob, 128, 0, st>>>(Sw, nw, grp);
-  k_group_rr<<<nprob, 64, nw * sizeof(int), st>>>(Sw, nw, grp, lam, lstride, U);
+  k_group_rr<<<nprob, 64, nw * sizeof(int), st>>>(Sw, nw, grp, lam_tmp, lstride, U_tmp);
+  k_sort_wanted<<<nprob, 128, 0, st>>>(lam_tmp, lstride, U_tmp, nw, lam, U);
   return cudaGetLastError();
 }
 

@@ -52,7 +52,7 @@ cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, in
 cudaError_t launch_oa_correction(cudaStream_t st, const double2* R, const double2* S, int n, int nw, int nprob,
                                  const double* lamall, double2* E);
 cudaError_t launch_group_rr(cudaStream_t st, const double2* Sw, int nw, int nprob, int* grp, double* lam,
-                            int lstride, double2* U);
+                            int lstride, double2* U, double* lam_tmp, double2* U_tmp);
 constexpr int J32_SWEEPS = 12;
 // Rayleigh-Ritz in FP32 while residuals exceed this.  Measured on the tube workload the FP32
 // phase raised the iteration count (60 -> 71) without lowering the eigensolver time (the
@@ -352,8 +352,9 @@ static cudaError_t rr_eig_hh(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int 
   gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, n, 1.0, w->Z, n, sZ, w->B1, n, sB, 0.0, w->G, nb, (int64_t)nb * nb, nk);
   {
     ProfScope ps_(ctx, HW_PH_EIG);
-    e = launch_group_rr(st, w->G, nb, nk, w->grp, w->w, n, w->Ui);
-    ctx->launches += 2;
+    // unsorted results go to B3 (as an nb x nb block) and to the tail of B2 (as eigenvalues)
+    e = launch_group_rr(st, w->G, nb, nk, w->grp, w->w, n, w->Ui, reinterpret_cast<double*>(w->B2), w->B3);
+    ctx->launches += 3;
   }
   if (e != cudaSuccess) return e;
   gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, nb, 1.0, w->Z, n, sZ, w->Ui, nb, (int64_t)nb * nb, 0.0, w->B2, n, sB, nk);
