@@ -223,6 +223,15 @@ hw_status hw_solve_eigs_traced(hw_ctx* ctx, int k, int n_eig, int block, double 
 hw_status hw_heev(hw_ctx* ctx, int n, int nprob, int nw, const double* A, double* w, double* Z,
                   int method);
 
+/* Autotune the H X kernels' tile shapes for blocks of ns columns at k-point k: the slab
+ * kernel's theta2 chunk and the number of columns per pass are timed (CUDA events, best of
+ * 2 after a warm-up) for every candidate in FP64 and FP32 and the fastest are kept for later
+ * calls.  results (host, nullable): up to max_results rows of 4 floats (precision 0/1, chunk,
+ * pass columns, milliseconds); n_results receives the row count.  Allocates two temporary
+ * blocks; synchronous. */
+hw_status hw_autotune(hw_ctx* ctx, int k, int ns, float* results, int max_results,
+                      int* n_results);
+
 /* Wait for all work on the context's stream. */
 hw_status hw_synchronize(hw_ctx* ctx);
 

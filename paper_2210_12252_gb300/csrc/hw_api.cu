@@ -417,6 +417,23 @@ hw_status hw_apply_precond(hw_ctx* ctx, int k, const double* R, double* Z, int n
   return HW_OK;
 }
 
+hw_status hw_autotune(hw_ctx* ctx, int k, int ns, float* results, int max_results, int* n_results) {
+  hw_status st = check_device_call(ctx);
+  if (st != HW_OK) return st;
+  if (!ctx->have_V) return hw_fail(ctx, HW_ESTATE, "no potential installed");
+  if (k < 0 || k >= ctx->hb.nk || ns < 1) return hw_fail(ctx, HW_EINVAL, "bad k-point or column count");
+  DeviceGuard g(ctx->device);
+  std::vector<float> log;
+  cudaError_t e = hx_autotune(ctx, k, ns, log);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+  const int nr = (int)(log.size() / 4);
+  if (results)
+    for (int i = 0; i < std::min(nr, max_results); ++i)
+      for (int c = 0; c < 4; ++c) results[4 * i + c] = log[4 * i + c];
+  if (n_results) *n_results = nr;
+  return HW_OK;
+}
+
 hw_status hw_synchronize(hw_ctx* ctx) {
   if (!ctx) return HW_EINVAL;
   if (ctx->device < 0) return HW_OK;

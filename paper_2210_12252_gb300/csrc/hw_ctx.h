@@ -40,7 +40,9 @@ struct DevBasis {
 struct Workspace {
   void* gbuf = nullptr;
   void* hbuf = nullptr;
-  size_t cols = 0;
+  size_t cols = 0;        // capacity of gbuf / hbuf in FP64 columns
+  int pass_cols[2] = {0, 0};   // autotuned columns per pass (FP64, FP32); 0 = capacity
+  int jc[2] = {0, 0};          // autotuned slab theta2 chunk (FP64, FP32); 0 = heuristic
 };
 
 // per-launch column blocks, passed by value to the kernels
@@ -107,6 +109,7 @@ namespace hw {
 template <typename T>
 cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld);
 cudaError_t hx_configure(hw_ctx* ctx);
+cudaError_t hx_autotune(hw_ctx* ctx, int k, int ns, std::vector<float>& log);
 template <typename T>
 cudaError_t launch_hx_into(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, void* gbuf, void* hbuf, int cols);
 cudaError_t launch_tpa(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld);

@@ -22,6 +22,7 @@
 // diagonal term is always applied in FP64.
 #include <algorithm>
 #include <cstdio>
+#include <vector>
 
 #include "hw_common.cuh"
 #include "hw_ctx.h"
@@ -373,12 +374,14 @@ cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld) {
   const DevTables<T>& tb = *reinterpret_cast<const DevTables<T>*>(
       sizeof(T) == 8 ? (const void*)&db.t64 : (const void*)&db.t32);
   const int ncols_total = blk.nslot * ns;
-  const int chunk = (int)ctx->ws.cols;
+  const int ti = sizeof(T) == 8 ? 0 : 1;
+  int chunk = (int)ctx->ws.cols;
+  if (ctx->ws.pass_cols[ti] > 0) chunk = std::min(chunk, ctx->ws.pass_cols[ti]);
   if (chunk <= 0 || blk.nslot > MAXSLOT) return cudaErrorInvalidValue;
   const int Nr = hb.prm.Nr, K = hb.K;
   int maxna = 0;
   for (int g = 0; g <= hb.N; ++g) maxna = std::max(maxna, hb.group_start[g + 1] - hb.group_start[g]);
-  const int Jc = slab_pick_jc(ctx, sizeof(cplx_t<T>));
+  const int Jc = ctx->ws.jc[ti] > 0 ? ctx->ws.jc[ti] : slab_pick_jc(ctx, sizeof(cplx_t<T>));
   for (int c0 = 0; c0 < ncols_total; c0 += chunk) {
     const int nc = std::min(chunk, ncols_total - c0);
     RadArgs<T> ra;
@@ -521,6 +524,87 @@ cudaError_t hx_configure(hw_ctx* ctx) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slab<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slab<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   (void)ctx;
+  return e;
+}
+
+// ---------------------------------------------------------------------------- autotuner
+// Times the H X pipeline on `ns` random-free columns (zeros are enough: the kernels' work does
+// not depend on the values) for candidate slab theta2 chunks and column-pass widths and keeps
+// the fastest per precision.
+template <typename T>
+static float time_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, cudaEvent_t e0, cudaEvent_t e1) {
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, ctx->stream);
+    if (launch_hx<T>(ctx, blk, ns, ld) != cudaSuccess) return 1e30f;
+    cudaEventRecord(e1, ctx->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) best = std::min(best, ms);
+  }
+  return best;
+}
+
+template <typename T>
+static void tune_one(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, cudaEvent_t e0, cudaEvent_t e1,
+                     std::vector<float>& log) {
+  const int ti = sizeof(T) == 8 ? 0 : 1;
+  const auto& hb = ctx->hb;
+  std::vector<int> jcs;
+  for (int j = hb.prm.Nth2; j >= 1; j = (j > 1 ? (j + 1) / 2 : 0)) {
+    if (slab_smem_bytes(ctx, sizeof(cplx_t<T>), j) <= 200 * 1024) jcs.push_back(j);
+    if (j == 1) break;
+  }
+  float best = 1e30f;
+  int bj = 0, bc = 0;
+  const int cap = (int)ctx->ws.cols;
+  const int passes[4] = {cap, std::min(cap, 512), std::min(cap, 128), std::min(cap, 32)};
+  for (int jc : jcs) {
+    if (jcs.size() > 4 && jc < 4) continue;
+    for (int pc : passes) {
+      ctx->ws.jc[ti] = jc;
+      ctx->ws.pass_cols[ti] = pc;
+      const float t = time_hx<T>(ctx, blk, ns, ld, e0, e1);
+      log.push_back((float)ti);
+      log.push_back((float)jc);
+      log.push_back((float)pc);
+      log.push_back(t);
+      if (t < best) {
+        best = t;
+        bj = jc;
+        bc = pc;
+      }
+    }
+  }
+  ctx->ws.jc[ti] = bj;
+  ctx->ws.pass_cols[ti] = bc;
+}
+
+cudaError_t hx_autotune(hw_ctx* ctx, int k, int ns, std::vector<float>& log) {
+  const int64_t L = ctx->hb.L[k];
+  double2* X = nullptr;
+  double2* Y = nullptr;
+  cudaError_t e = cudaMalloc((void**)&X, (size_t)L * ns * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&Y, (size_t)L * ns * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMemsetAsync(X, 0, (size_t)L * ns * sizeof(double2), ctx->stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) {
+    Blocks blk;
+    blk.nslot = 1;
+    blk.x[0] = reinterpret_cast<const double*>(X);
+    blk.y[0] = reinterpret_cast<double*>(Y);
+    blk.kb[0] = k;
+    tune_one<double>(ctx, blk, ns, L, e0, e1, log);
+    tune_one<float>(ctx, blk, ns, L, e0, e1, log);
+    e = cudaStreamSynchronize(ctx->stream);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (X) cudaFree(X);
+  if (Y) cudaFree(Y);
   return e;
 }
 

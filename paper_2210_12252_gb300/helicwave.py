@@ -65,6 +65,8 @@ _SIGS = {
                                 C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p),
                                 _D, C.POINTER(C.c_void_p), C.c_int64, C.POINTER(C.c_int), _D]),
     "hw_synchronize": (C.c_int, [C.c_void_p]),
+    "hw_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_float), C.c_int,
+                              C.POINTER(C.c_int)]),
     "hw_heev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                           C.c_int]),
     "hw_profile": (C.c_int, [C.c_void_p, C.c_int]),
@@ -235,6 +237,15 @@ def hw_solve_eigs(h, kidx, n_eig, block=0, tol=1e-6, maxit=500, prec=HW_FP64,
 
 def hw_synchronize(h):
     _check(h, load_library().hw_synchronize(h))
+
+
+def hw_autotune(h, k, ns):
+    """Tune the H X tile shapes; returns rows (precision, theta2 chunk, pass columns, ms)."""
+    buf = np.zeros(4 * 256, dtype=np.float32)
+    nr = C.c_int()
+    _check(h, load_library().hw_autotune(h, k, ns, buf.ctypes.data_as(C.POINTER(C.c_float)), 256,
+                                         C.byref(nr)))
+    return buf[: 4 * min(nr.value, 256)].reshape(-1, 4)
 
 
 def hw_heev(h, A, nw, method=1):
@@ -438,6 +449,9 @@ class Context:
 
     def synchronize(self):
         hw_synchronize(self.h)
+
+    def autotune(self, k=0, ns=64):
+        return hw_autotune(self.h, k, ns)
 
     def profile(self, enable=True):
         hw_profile(self.h, enable)
