@@ -1257,29 +1257,10 @@ __global__ void k_group_rr(const double2* S, int nw, const int* grp, double* lam
   double2* u = U + (size_t)b * nw * nw;
   double* l = lam + (size_t)b * lstride;
   const int* g = grp + (size_t)b * nw;
-  // group id of each vector: index of its group's first member
-  extern __shared__ int gid[];
-  if (threadIdx.x == 0) {
-    int cur = 0;
-    for (int j = 0; j < nw; ++j) {
-      if (j > 0 && !g[j - 1]) cur = j;
-      gid[j] = cur;
-    }
-  }
-  __syncthreads();
-  // identity inside groups (the group rotations overwrite it), first-order rotation between
-  // groups
+  // identity (the group rotations overwrite their blocks)
   for (int t = threadIdx.x; t < nw * nw; t += blockDim.x) {
     const int i = t % nw, j = t / nw;
-    if (i == j) {
-      u[t] = make_double2(1.0, 0.0);
-    } else if (gid[i] == gid[j]) {
-      u[t] = make_double2(0.0, 0.0);
-    } else {
-      const double den = s[j + (size_t)j * nw].x - s[i + (size_t)i * nw].x;
-      const double2 c = s[t];
-      u[t] = den != 0.0 ? make_double2(c.x / den, c.y / den) : make_double2(0.0, 0.0);
-    }
+    u[t] = make_double2(i == j ? 1.0 : 0.0, 0.0);
   }
   __syncthreads();
   for (int j0 = threadIdx.x; j0 < nw; j0 += blockDim.x) {
@@ -1354,6 +1335,41 @@ cudaError_t launch_oa_correction(cudaStream_t st, const double2* R, const double
   return cudaGetLastError();
 }
 
+// F = I + first-order rotation between groups, from S' = V_g^H S_w V_g (already rotated inside
+// groups, so only between-group entries remain): F_ij = S'_ij / (lambda_j - lambda_i)
+__global__ void k_first_order(const double2* Sp, int nw, const int* grp, double2* F) {
+  const int b = blockIdx.x;
+  const double2* s = Sp + (size_t)b * nw * nw;
+  double2* f = F + (size_t)b * nw * nw;
+  const int* g = grp + (size_t)b * nw;
+  extern __shared__ int gid[];
+  if (threadIdx.x == 0) {
+    int cur = 0;
+    for (int j = 0; j < nw; ++j) {
+      if (j > 0 && !g[j - 1]) cur = j;
+      gid[j] = cur;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nw * nw; t += blockDim.x) {
+    const int i = t % nw, j = t / nw;
+    if (i == j) {
+      f[t] = make_double2(1.0, 0.0);
+    } else if (gid[i] == gid[j]) {
+      f[t] = make_double2(0.0, 0.0);
+    } else {
+      const double den = s[j + (size_t)j * nw].x - s[i + (size_t)i * nw].x;
+      const double2 c = s[t];
+      f[t] = den != 0.0 ? make_double2(c.x / den, c.y / den) : make_double2(0.0, 0.0);
+    }
+  }
+}
+
+cudaError_t launch_first_order(cudaStream_t st, const double2* Sp, int nw, int nprob, const int* grp, double2* F) {
+  k_first_order<<<nprob, 128, nw * sizeof(int), st>>>(Sp, nw, grp, F);
+  return cudaGetLastError();
+}
+
 // order the wanted pairs by eigenvalue: column rank(j) of Uout = column j of U
 __global__ void k_sort_wanted(const double* lam_in, int lstride, const double2* U, int nw, double* lam_out,
                               double2* Uout) {
@@ -1368,12 +1384,17 @@ __global__ void k_sort_wanted(const double* lam_in, int lstride, const double2* 
   }
 }
 
-// groups and first-order couplings (U, lam unsorted into tmp buffers), then sorted into U / lam
+// group links and exact group rotations: Ug (identity outside groups), lam (unsorted)
 cudaError_t launch_group_rr(cudaStream_t st, const double2* Sw, int nw, int nprob, int* grp, double* lam,
-                            int lstride, double2* U, double* lam_tmp, double2* U_tmp) {
+                            int lstride, double2* Ug) {
   k_group_links<<<nprob, 128, 0, st>>>(Sw, nw, grp);
-  k_group_rr<<<nprob, 64, nw * sizeof(int), st>>>(Sw, nw, grp, lam_tmp, lstride, U_tmp);
-  k_sort_wanted<<<nprob, 128, 0, st>>>(lam_tmp, lstride, U_tmp, nw, lam, U);
+  k_group_rr<<<nprob, 64, 0, st>>>(Sw, nw, grp, lam, lstride, Ug);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort_wanted(cudaStream_t st, const double* lam_in, int lstride, const double2* U, int nw, int nprob,
+                               double* lam_out, double2* Uout) {
+  k_sort_wanted<<<nprob, 128, 0, st>>>(lam_in, lstride, U, nw, lam_out, Uout);
   return cudaGetLastError();
 }
 

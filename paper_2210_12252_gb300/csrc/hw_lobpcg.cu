@@ -52,7 +52,10 @@ cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, in
 cudaError_t launch_oa_correction(cudaStream_t st, const double2* R, const double2* S, int n, int nw, int nprob,
                                  const double* lamall, double2* E);
 cudaError_t launch_group_rr(cudaStream_t st, const double2* Sw, int nw, int nprob, int* grp, double* lam,
-                            int lstride, double2* U, double* lam_tmp, double2* U_tmp);
+                            int lstride, double2* Ug);
+cudaError_t launch_first_order(cudaStream_t st, const double2* Sp, int nw, int nprob, const int* grp, double2* F);
+cudaError_t launch_sort_wanted(cudaStream_t st, const double* lam_in, int lstride, const double2* U, int nw, int nprob,
+                               double* lam_out, double2* Uout);
 constexpr int J32_SWEEPS = 12;
 // Rayleigh-Ritz in FP32 while residuals exceed this.  Measured on the tube workload the FP32
 // phase raised the iteration count (60 -> 71) without lowering the eigensolver time (the
@@ -352,9 +355,27 @@ static cudaError_t rr_eig_hh(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int 
   gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, n, 1.0, w->Z, n, sZ, w->B1, n, sB, 0.0, w->G, nb, (int64_t)nb * nb, nk);
   {
     ProfScope ps_(ctx, HW_PH_EIG);
-    // unsorted results go to B3 (as an nb x nb block) and to the tail of B2 (as eigenvalues)
-    e = launch_group_rr(st, w->G, nb, nk, w->grp, w->w, n, w->Ui, reinterpret_cast<double*>(w->B2), w->B3);
-    ctx->launches += 3;
+    // exact rotations inside groups of near-degenerate vectors: Ug in B3, eigenvalues (unsorted)
+    // in B2 viewed as doubles
+    e = launch_group_rr(st, w->G, nb, nk, w->grp, reinterpret_cast<double*>(w->B2), n, w->B3);
+    ctx->launches += 2;
+  }
+  if (e != cudaSuccess) return e;
+  // S' = Ug^H S_w Ug, then U = Ug (I + F) with F the first-order rotation between groups
+  const int64_t s2 = (int64_t)nb * nb;
+  gemm(CUBLAS_OP_N, CUBLAS_OP_N, nb, nb, nb, 1.0, w->G, nb, s2, w->B3, nb, s2, 0.0, w->C, nb, (int64_t)2 * nb * nb, nk);
+  gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, nb, 1.0, w->B3, nb, s2, w->C, nb, (int64_t)2 * nb * nb, 0.0, w->G, nb, s2, nk);
+  {
+    ProfScope ps_(ctx, HW_PH_EIG);
+    e = launch_first_order(st, w->G, nb, nk, w->grp, w->Ui);
+    ctx->launches++;
+  }
+  if (e != cudaSuccess) return e;
+  gemm(CUBLAS_OP_N, CUBLAS_OP_N, nb, nb, nb, 1.0, w->B3, nb, s2, w->Ui, nb, s2, 0.0, w->C, nb, s2, nk);   // contiguous
+  {
+    ProfScope ps_(ctx, HW_PH_EIG);
+    e = launch_sort_wanted(st, reinterpret_cast<double*>(w->B2), n, w->C, nb, nk, w->w, w->Ui);
+    ctx->launches++;
   }
   if (e != cudaSuccess) return e;
   gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, nb, 1.0, w->Z, n, sZ, w->Ui, nb, (int64_t)nb * nb, 0.0, w->B2, n, sB, nk);
