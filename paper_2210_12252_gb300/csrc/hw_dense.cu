@@ -1224,16 +1224,16 @@ __global__ void k_oa_correction(const double2* R, const double2* S, int n, int n
 }
 
 // Final Rayleigh-Ritz of the wanted block from S_w = Z_w^H A Z_w (nw x nw, Z_w orthonormal):
-// consecutive vectors whose coupling is not small against their gap (> 1e-6 of it) or whose
+// consecutive vectors whose coupling is not small against their gap (> 1e-7 of it) or whose
 // gap is below 1e-8 (1 + |lambda|) form a group, diagonalised exactly by a serial FP64 Jacobi
 // (one thread per group, groups of up to 16); couplings between groups get the first-order
-// rotation S_ij / (lambda_j - lambda_i), unitary to O(1e-12).
+// rotation S_ij / (lambda_j - lambda_i), unitary to O(1e-14).
 __device__ __forceinline__ bool strong_link(const double2* s, int nw, int j, int k) {
   const double dj = s[j + (size_t)j * nw].x, dk = s[k + (size_t)k * nw].x;
   const double2 c = s[j + (size_t)k * nw];
   const double ac = sqrt(c.x * c.x + c.y * c.y);
   const double gap = fabs(dk - dj);
-  return gap < 1e-8 * (1.0 + fabs(dj) + fabs(dk)) || ac > 1e-6 * gap;
+  return gap < 1e-8 * (1.0 + fabs(dj) + fabs(dk)) || ac > 1e-7 * gap;
 }
 
 // grp[j] = 1 joins j and j+1: some vector at or before j couples strongly to one after j
