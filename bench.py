@@ -512,9 +512,14 @@ def kernel_case(args):
         for _ in range(3):
             ctx.apply_H(0, X, Y, prec=prec)
     else:
+        from paper_2210_12252_gb300 import train_precond
+        pc = "tpa"
+        if os.path.exists(train_precond.WEIGHTS):
+            ctx.set_mlp(train_precond.load_weights())
+            pc = "learned"
         nb = w.n_eig + max(4, w.n_eig // 8)
         X0 = torch.from_numpy(np.ascontiguousarray(inputs.random_block(L, nb, 1234).T)).cuda()
-        ctx.solve_eigs([0], w.n_eig, block=nb, tol=TOL, maxit=600, prec="mixed", X0=[X0])
+        ctx.solve_eigs([0], w.n_eig, block=nb, tol=TOL, maxit=600, prec="mixed", precond=pc, X0=[X0])
     torch.cuda.synchronize()
 
 

@@ -232,6 +232,18 @@ hw_status hw_heev(hw_ctx* ctx, int n, int nprob, int nw, const double* A, double
 hw_status hw_autotune(hw_ctx* ctx, int k, int ns, float* results, int max_results,
                       int* n_results);
 
+/* Options of a context. */
+typedef enum {
+  HW_OPT_RR_METHOD = 0,     /* Rayleigh-Ritz eigensolver: 0 auto (Householder FP32 + FP64
+                               refinement when n <= 236, checked, with the FP64 Jacobi as the
+                               retry), 1 FP64 Jacobi always.  Default 0. */
+  HW_OPT_RR_FALLBACKS = 1   /* read only: Householder results rejected by the check so far */
+} hw_option;
+/* Set an option (HW_EINVAL for an unknown option, a read-only one or a bad value). */
+hw_status hw_set_option(hw_ctx* ctx, int option, int value);
+/* Read an option or counter into *value. */
+hw_status hw_get_option(hw_ctx* ctx, int option, long long* value);
+
 /* Wait for all work on the context's stream. */
 hw_status hw_synchronize(hw_ctx* ctx);
 

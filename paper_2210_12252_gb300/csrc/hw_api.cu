@@ -434,6 +434,23 @@ hw_status hw_autotune(hw_ctx* ctx, int k, int ns, float* results, int max_result
   return HW_OK;
 }
 
+hw_status hw_set_option(hw_ctx* ctx, int option, int value) {
+  if (!ctx) return HW_EINVAL;
+  if (option == HW_OPT_RR_METHOD) {
+    if (value != 0 && value != 1) return hw_fail(ctx, HW_EINVAL, "RR method 0 (auto) or 1 (Jacobi)");
+    ctx->rr_method = value;
+    return HW_OK;
+  }
+  return hw_fail(ctx, HW_EINVAL, "unknown or read-only option");
+}
+
+hw_status hw_get_option(hw_ctx* ctx, int option, long long* value) {
+  if (!ctx || !value) return HW_EINVAL;
+  if (option == HW_OPT_RR_METHOD) { *value = ctx->rr_method; return HW_OK; }
+  if (option == HW_OPT_RR_FALLBACKS) { *value = ctx->rr_fallbacks; return HW_OK; }
+  return hw_fail(ctx, HW_EINVAL, "unknown option");
+}
+
 hw_status hw_synchronize(hw_ctx* ctx) {
   if (!ctx) return HW_EINVAL;
   if (ctx->device < 0) return HW_OK;

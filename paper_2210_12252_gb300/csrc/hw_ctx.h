@@ -86,6 +86,8 @@ struct hw_ctx {
   hw::MlpState* mlp = nullptr;
   int* dflag = nullptr;        // device status word for bounded waits
   int64_t launches = 0;        // kernels of this library launched on the stream
+  int rr_method = 0;           // HW_OPT_RR_METHOD
+  int64_t rr_fallbacks = 0;    // Householder results rejected by the check (Jacobi used)
   hw::Prof prof;
 };
 

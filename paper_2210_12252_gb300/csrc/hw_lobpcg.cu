@@ -92,6 +92,7 @@ struct LobpcgWork {
   double2* B2 = nullptr;
   double2* B3 = nullptr;
   int* grp = nullptr;       // [nk][nb]
+  double2* Abak = nullptr;  // [nk][ne*ne] copy of the Rayleigh-Ritz matrix (Jacobi retry)
 };
 
 void lobpcg_free(hw_ctx* ctx) {
@@ -101,7 +102,7 @@ void lobpcg_free(hw_ctx* ctx) {
                   (void*)w->A, (void*)w->Z, (void*)w->w, (void*)w->G, (void*)w->Ui, (void*)w->C,
                   (void*)w->Y, (void*)w->Y2, (void*)w->res, (void*)w->theta, (void*)w->iact,
                   (void*)w->fail, (void*)w->status, w->j32, w->hh, (void*)w->B1, (void*)w->B2,
-                  (void*)w->B3, (void*)w->grp})
+                  (void*)w->B3, (void*)w->grp, (void*)w->Abak})
     if (p) cudaFree(p);
   dense_free(w->dw);
   delete w;
@@ -214,6 +215,27 @@ __global__ void k_rq_diag(const double2* Z, const double2* T, int n, int64_t sZ,
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += red[i];
     w[(size_t)b * sw + j] = a;
   }
+}
+
+// check of the Householder route's wanted block: fail[b] = 1 when an entry of Z_w^H Z_w - I
+// (G, m x m) exceeds 1e-9 in modulus or an eigenvalue is not finite; grid nk
+__global__ void k_check_gram(const double2* G, int m, const double* w, int wstride, int* fail) {
+  __shared__ int bad;
+  const int b = blockIdx.x;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    const int i = t % m, j = t / m;
+    const double2 g = G[(size_t)b * m * m + t];
+    const double dx = g.x - (i == j ? 1.0 : 0.0);
+    if (!(dx * dx + g.y * g.y < 1e-18)) mine = 1;
+  }
+  for (int j = threadIdx.x; j < m; j += blockDim.x)
+    if (!isfinite(w[(size_t)b * wstride + j])) mine = 1;
+  if (mine) bad = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) fail[b] = bad;
 }
 
 // Gaussian start block from a counter-based generator (splitmix64 + Box-Muller); grid (nb, nk)
@@ -387,7 +409,29 @@ static cudaError_t rr_eig(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int nb,
   cudaStream_t st = ctx->stream;
   const int nk = w->nk;
   cudaError_t e;
-  if (w->hh && hh_smem(n) <= 226 * 1024) return rr_eig_hh(ctx, w, gemm, n, nb);
+  if (ctx->rr_method == 0 && w->hh && hh_smem(n) <= 226 * 1024) {
+    // the Householder route is checked (orthonormal wanted block, finite eigenvalues); a
+    // problem that fails the check is solved again by the FP64 Jacobi from a saved copy
+    cudaMemcpyAsync(w->Abak, w->A, (size_t)nk * n * n * 16, cudaMemcpyDeviceToDevice, st);
+    e = rr_eig_hh(ctx, w, gemm, n, nb);
+    if (e != cudaSuccess) return e;
+    gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, n, 1.0, w->Z, n, (int64_t)n * n, w->Z, n, (int64_t)n * n, 0.0, w->G, nb,
+         (int64_t)nb * nb, nk);
+    {
+      ProfScope ps_(ctx, HW_PH_EIG);
+      k_check_gram<<<nk, 256, 0, st>>>(w->G, nb, w->w, n, w->fail);
+      ctx->launches++;
+    }
+    std::vector<int> f(nk);
+    cudaMemcpyAsync(f.data(), w->fail, nk * sizeof(int), cudaMemcpyDeviceToHost, st);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    bool any = false;
+    for (int b = 0; b < nk; ++b) any = any || f[b];
+    if (!any) return cudaSuccess;
+    ctx->rr_fallbacks++;
+    cudaMemcpyAsync(w->A, w->Abak, (size_t)nk * n * n * 16, cudaMemcpyDeviceToDevice, st);
+  }
   if (fp32 && w->j32 && jac32_smem(n) <= 226 * 1024) {
     {
       ProfScope ps_(ctx, HW_PH_EIG);
@@ -490,6 +534,7 @@ static hw_status ensure_work(hw_ctx* ctx, int nk, int nb, int64_t Lpad) {
     A((void**)&w->B2, (size_t)nk * w->ne * nb * sizeof(double2));
     A((void**)&w->B3, (size_t)nk * w->ne * nb * sizeof(double2));
     A((void**)&w->grp, (size_t)nk * nb * sizeof(int));
+    A((void**)&w->Abak, nk * ne2 * sizeof(double2));
   }
   if (e == cudaSuccess && jac32_smem(w->ne) <= 226 * 1024) {
     w->j32_bytes = heev32_scratch_bytes(w->ne, nk, J32_SWEEPS);

@@ -65,6 +65,8 @@ _SIGS = {
                                 C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p),
                                 _D, C.POINTER(C.c_void_p), C.c_int64, C.POINTER(C.c_int), _D]),
     "hw_synchronize": (C.c_int, [C.c_void_p]),
+    "hw_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "hw_get_option": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_longlong)]),
     "hw_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_float), C.c_int,
                               C.POINTER(C.c_int)]),
     "hw_heev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -237,6 +239,20 @@ def hw_solve_eigs(h, kidx, n_eig, block=0, tol=1e-6, maxit=500, prec=HW_FP64,
 
 def hw_synchronize(h):
     _check(h, load_library().hw_synchronize(h))
+
+
+HW_OPT_RR_METHOD = 0
+HW_OPT_RR_FALLBACKS = 1
+
+
+def hw_set_option(h, option, value):
+    _check(h, load_library().hw_set_option(h, option, value))
+
+
+def hw_get_option(h, option):
+    v = C.c_longlong(0)
+    _check(h, load_library().hw_get_option(h, option, C.byref(v)))
+    return int(v.value)
 
 
 def hw_autotune(h, k, ns):
@@ -449,6 +465,12 @@ class Context:
 
     def synchronize(self):
         hw_synchronize(self.h)
+
+    def set_option(self, option, value):
+        hw_set_option(self.h, option, value)
+
+    def get_option(self, option):
+        return hw_get_option(self.h, option)
 
     def autotune(self, k=0, ns=64):
         return hw_autotune(self.h, k, ns)

@@ -70,6 +70,23 @@ def test_tiny_zero_potential_gives_closed_form(hwmod):
     assert np.abs(r["evals"][0] - closed).max() < 1e-10
 
 
+def test_rr_methods_agree(hwmod):
+    """Householder route (checked, Jacobi retry) and the FP64 Jacobi give the same tiny-case
+    spectrum; the Jacobi-only run never counts a retry."""
+    w = inputs.tiny()
+    out = []
+    for method in (0, 1):
+        ctx, L = make_ctx(hwmod, w)
+        ctx.set_option(hwmod.HW_OPT_RR_METHOD, method)
+        r = ctx.solve_eigs([0], w.n_eig, tol=1e-8, maxit=400)
+        assert r["converged"]
+        out.append(r["evals"][0])
+        if method == 1:
+            assert ctx.get_option(hwmod.HW_OPT_RR_FALLBACKS) == 0
+        ctx.close()
+    assert np.abs(out[0] - out[1]).max() < 1e-9
+
+
 @pytest.mark.parametrize("prec,bar", [("fp64", 1e-8), ("mixed", 1e-6)])
 def test_tube_64_eigenpairs(hwmod, prec, bar):
     w = inputs.tube()

@@ -114,3 +114,18 @@ def test_device_calls_on_host_context_are_rejected(lib):
     with pytest.raises(hw.HwError) as e:
         hw.hw_apply_H(ctx.h, 0, 0, 0, 1, int(L[0]))
     assert e.value.status == hw.HW_ESTATE
+
+
+def test_options_set_get_and_reject(lib):
+    ctx = hw.Context(device=-1)
+    assert ctx.get_option(hw.HW_OPT_RR_METHOD) == 0
+    assert ctx.get_option(hw.HW_OPT_RR_FALLBACKS) == 0
+    ctx.set_option(hw.HW_OPT_RR_METHOD, 1)
+    assert ctx.get_option(hw.HW_OPT_RR_METHOD) == 1
+    for opt, val in ((hw.HW_OPT_RR_METHOD, 2), (hw.HW_OPT_RR_FALLBACKS, 0), (99, 0)):
+        with pytest.raises(hw.HwError) as e:
+            ctx.set_option(opt, val)
+        assert e.value.status == hw.HW_EINVAL
+    with pytest.raises(hw.HwError):
+        ctx.get_option(99)
+    ctx.close()
