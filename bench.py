@@ -212,7 +212,8 @@ def ours_main(args):
                    "tol": TOL, "form": f"mixed FP32 transforms + FP64 Gram/RR, {precond} preconditioner",
                    "l2": "flushed (512 MB write) before every step"},
         "chosen_form": {"iters": iters_mixed, "converged": conv,
-                        "max_abs_err_vs_oracle_Ha": err_mixed},
+                        "max_abs_err_vs_oracle_Ha": err_mixed,
+                        "rr_jacobi_retries": ctx.get_option(hw.HW_OPT_RR_FALLBACKS)},
         "clocks": clk, "gpu_launches": int(launches),
     }
     if rank != 0:
@@ -317,7 +318,9 @@ def batched_kpoints(hw, inputs, local, stream, flush, precond):
         return e0.elapsed_time(e1) / 1e3, r
 
     run(list(range(nk)))                      # warm-up (workspace for the batch)
+    fb0 = ctx.get_option(hw.HW_OPT_RR_FALLBACKS)
     tb, rb = run(list(range(nk)))
+    fb_batched = ctx.get_option(hw.HW_OPT_RR_FALLBACKS) - fb0
     ts = 0.0
     iters_seq = []
     for k in range(nk):
@@ -331,6 +334,7 @@ def batched_kpoints(hw, inputs, local, stream, flush, precond):
            "sequential_value": round(nk * ne / ts, 3), "sequential_seconds": round(ts, 3),
            "speedup_vs_sequential": round(ts / tb, 3),
            "iters_batched_max": int(rb["iters"].max()), "iters_sequential_mean": float(np.mean(iters_seq)),
+           "rr_jacobi_retries_batched": int(fb_batched),
            "form": f"mixed, {precond} preconditioner, all k-points in lockstep"}
     ctx.close()
     return out

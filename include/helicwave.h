@@ -157,7 +157,8 @@ hw_status hw_apply_precond(hw_ctx* ctx, int k, const double* R, double* Z, int n
                            const double* ritz, int kind);
 
 /* Lowest n_eig eigenpairs at the nk k-points kidx[] by block LOBPCG (Sec. Eigensolvers and
- * Preconditioning) on blocks of `block` >= n_eig columns (0: n_eig + max(4, n_eig/8)).
+ * Preconditioning) on blocks of `block` >= n_eig columns (0: n_eig + max(4, n_eig/8)),
+ * at most 112 columns (HW_EINVAL above: the Cholesky-QR keeps its factor in shared memory).
  * A column is converged when ||H x - theta x||_2 <= tol with ||x|| = 1.  X0 (nullable):
  * nk device pointers to L_k x block complex128 start blocks (leading dimension L_k); NULL
  * draws a seeded Gaussian start on the device.  Outputs: evals (host, [nk*n_eig]), iters
@@ -237,7 +238,13 @@ typedef enum {
   HW_OPT_RR_METHOD = 0,     /* Rayleigh-Ritz eigensolver: 0 auto (Householder FP32 + FP64
                                refinement when n <= 236, checked, with the FP64 Jacobi as the
                                retry), 1 FP64 Jacobi always.  Default 0. */
-  HW_OPT_RR_FALLBACKS = 1   /* read only: Householder results rejected by the check so far */
+  HW_OPT_RR_FALLBACKS = 1,  /* read only: Householder results rejected by the check so far */
+  HW_OPT_LOWP_SWITCH = 2    /* mixed form only: the block products over the basis dimension
+                               (Gram matrices, projections, block updates) run in complex FP32
+                               until every wanted residual is below 10^-value (or the residuals
+                               stop falling: FP32 products stall near 1e-5), then in FP64 (X
+                               re-orthonormalised, H X recomputed in FP64, P restarted).
+                               0 disables (FP64 throughout); 1..12; default 4. */
 } hw_option;
 /* Set an option (HW_EINVAL for an unknown option, a read-only one or a bad value). */
 hw_status hw_set_option(hw_ctx* ctx, int option, int value);

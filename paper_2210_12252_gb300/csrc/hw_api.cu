@@ -441,6 +441,11 @@ hw_status hw_set_option(hw_ctx* ctx, int option, int value) {
     ctx->rr_method = value;
     return HW_OK;
   }
+  if (option == HW_OPT_LOWP_SWITCH) {
+    if (value < 0 || value > 12) return hw_fail(ctx, HW_EINVAL, "low-precision switch exponent 0..12");
+    ctx->lowp_exp = value;
+    return HW_OK;
+  }
   return hw_fail(ctx, HW_EINVAL, "unknown or read-only option");
 }
 
@@ -448,6 +453,7 @@ hw_status hw_get_option(hw_ctx* ctx, int option, long long* value) {
   if (!ctx || !value) return HW_EINVAL;
   if (option == HW_OPT_RR_METHOD) { *value = ctx->rr_method; return HW_OK; }
   if (option == HW_OPT_RR_FALLBACKS) { *value = ctx->rr_fallbacks; return HW_OK; }
+  if (option == HW_OPT_LOWP_SWITCH) { *value = ctx->lowp_exp; return HW_OK; }
   return hw_fail(ctx, HW_EINVAL, "unknown option");
 }
 

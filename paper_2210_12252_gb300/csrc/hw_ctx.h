@@ -87,6 +87,7 @@ struct hw_ctx {
   int* dflag = nullptr;        // device status word for bounded waits
   int64_t launches = 0;        // kernels of this library launched on the stream
   int rr_method = 0;           // HW_OPT_RR_METHOD
+  int lowp_exp = 4;            // HW_OPT_LOWP_SWITCH
   int64_t rr_fallbacks = 0;    // Householder results rejected by the check (Jacobi used)
   hw::Prof prof;
 };

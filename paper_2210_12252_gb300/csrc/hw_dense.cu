@@ -60,13 +60,16 @@ __global__ void k_hermitize(double2* A, int n, int64_t sA) {
 }
 
 // ---------------------------------------------------------------------- Cholesky
-constexpr int CHOL_THREADS = 256;
+constexpr int CHOL_THREADS = 1024;
 
-// lower Cholesky in place (upper triangle zeroed); fail[b] = 1 + column of a bad pivot
+// lower Cholesky in place (upper triangle zeroed); fail[b] = 1 + column of a bad pivot.
+// Right-looking; the trailing update gives each warp whole columns k (lanes over rows i >= k),
+// so only the lower triangle is touched and shared-memory reads are contiguous.
 __global__ void __launch_bounds__(CHOL_THREADS) k_chol(double2* G, int n, int64_t sG, int* fail,
                                                        int use_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   double2* g = G + (size_t)b * sG;
   double2* a = use_smem ? reinterpret_cast<double2*>(smem_raw) : g;
   __shared__ int bad;
@@ -96,15 +99,15 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol(double2* G, int n, int64_
     }
     __syncthreads();
     // trailing update: a[i][k] -= l[i][j] conj(l[k][j]) for j < k <= i
-    const int m = n - j - 1;
-    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-      const int i = j + 1 + t % m, k = j + 1 + t / m;
-      if (k > i) continue;
-      const double2 li = a[i + (size_t)j * n], lk = a[k + (size_t)j * n];
-      double2 v = a[i + (size_t)k * n];
-      v.x -= li.x * lk.x + li.y * lk.y;
-      v.y -= li.y * lk.x - li.x * lk.y;
-      a[i + (size_t)k * n] = v;
+    for (int k = j + 1 + warp; k < n; k += nwarp) {
+      const double2 lk = a[k + (size_t)j * n];
+      for (int i = k + lane; i < n; i += 32) {
+        const double2 li = a[i + (size_t)j * n];
+        double2 v = a[i + (size_t)k * n];
+        v.x -= li.x * lk.x + li.y * lk.y;
+        v.y -= li.y * lk.x - li.x * lk.y;
+        a[i + (size_t)k * n] = v;
+      }
     }
     __syncthreads();
   }
@@ -781,10 +784,12 @@ size_t heev32_scratch_bytes(int n, int nprob, int maxsweep) {
 //   k_hh_tridiag  one CTA per problem: the matrix (shifted by the mean of its valid diagonal)
 //                 packed as a lower triangle in shared memory, reduced to Hermitian tridiagonal
 //                 form by n-2 Householder reflections in FP32; reflectors kept in global memory
-//   k_tri_wanted  one CTA per problem: the tridiagonal made real by a diagonal phase matrix,
-//                 its lowest nw eigenvalues by Sturm bisection (one thread each), eigenvectors
-//                 by inverse iteration, Gram-Schmidt inside near-degenerate groups (FP32)
-//   k_hh_back     one warp per wanted vector: Z = Q D Y (reflectors applied in reverse), FP64 out
+//   k_tri_eig     one thread per wanted pair: the tridiagonal made real by a diagonal phase
+//                 matrix, its j-th eigenvalue by Sturm bisection and the vector by inverse
+//                 iteration (FP32)
+//   k_tri_gs      one CTA per problem: Gram-Schmidt inside near-degenerate groups, phases
+//   k_hh_back     one warp per wanted vector: Z = Q D Y (reflectors applied in reverse) in FP32
+//                 registers, FP64 out
 // followed (host side) by an FP64 refinement of the wanted vectors (Ogita-Aishima style
 // first-order correction against all FP32 vectors, then Rayleigh-Ritz inside groups).
 namespace hw {
@@ -792,16 +797,19 @@ namespace hw {
 struct HhArgs {
   int n, nw;
   const double2* A;    // [nprob][n*n] FP64 input (read only)
-  float2* vq;          // [nprob][n][n] reflector k stored in column k (rows k+1..n-1)
+  float2* vq;          // [nprob][n][n] reflector k stored in column k (compacted rows k+1..nv-1)
   float* beta;         // [nprob][n]
-  float* d;            // [nprob][n] diagonal of T
+  float* d;            // [nprob][n] diagonal of T (first nv entries)
   float2* e;           // [nprob][n] sub-diagonal of T (e[k] = T[k+1][k])
+  float2* ph;          // [nprob][n] phases D with T = D Tr D^H, Tr real
+  int* map;            // [nprob][n] compacted index -> original index (valid first, then padding)
+  int* nv;             // [nprob] number of valid indices
   double* shift;       // [nprob]
   float* lam;          // [nprob][nw] eigenvalues of the shifted T (ascending)
   double* lam64;       // [nprob][n stride] the same plus the shift (FP64 storage), may be null
-  float* Y;            // [nprob][nw][n] eigenvectors of the real tridiagonal
-  float* work;         // [nprob][nw][3n] inverse-iteration factors
-  double2* Z;          // [nprob][n][nw] output vectors (column-major n x nw)
+  float* Y;            // [nprob][nw][n] eigenvectors of Tr (compacted coordinates)
+  float* work;         // [nprob][nw][2n] inverse-iteration factors
+  double2* Z;          // [nprob][n][nw] output vectors (column-major n x nw), original coordinates
 };
 
 constexpr int HH_THREADS = 1024;
@@ -816,41 +824,60 @@ __device__ __forceinline__ float block_sum_f(float v, float* red) {
   return t;
 }
 
+// Padding rows (diagonal >= 1e9, zero off the diagonal) are decoupled: they are moved out of
+// the reduction (compacted index map) and come back as exact unit eigenvectors.
 __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = H.n, b = blockIdx.x;
   float2* S = reinterpret_cast<float2*>(smem_raw);                       // packed lower triangle
   float2* v = S + ((size_t)n * (n + 1) / 2 + 1);                          // [n]
   float2* p = v + n;                                                      // [n]
+  int* mp = reinterpret_cast<int*>(p + n);                                // [n]
   __shared__ float red[32];
   __shared__ float2 alpha_s;
   __shared__ float beta_s;
+  __shared__ int nv_s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const double2* a = H.A + (size_t)b * n * n;
-  // shift = mean of the valid diagonal (padding entries are >= 1e9)
-  float sd = 0.f, cnt = 0.f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double x = a[i + (size_t)i * n].x;
-    if (fabs(x) < 1e9) { sd += (float)x; cnt += 1.f; }
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int i = 0; i < n; ++i)
+      if (fabs(a[i + (size_t)i * n].x) < 1e9) mp[c++] = i;
+    const int nvalid = c;
+    for (int i = 0; i < n; ++i) {   // padding after, ascending by diagonal value
+      const double x = a[i + (size_t)i * n].x;
+      if (fabs(x) < 1e9) continue;
+      int q = c++;
+      while (q > nvalid && a[mp[q - 1] + (size_t)mp[q - 1] * n].x > x) {
+        mp[q] = mp[q - 1];
+        --q;
+      }
+      mp[q] = i;
+    }
+    nv_s = nvalid;
+    H.nv[b] = nvalid;
   }
+  __syncthreads();
+  const int nv = nv_s;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) H.map[(size_t)b * n + i] = mp[i];
+  // shift = mean of the valid diagonal
+  float sd = 0.f;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) sd += (float)a[mp[i] + (size_t)mp[i] * n].x;
   sd = block_sum_f(sd, red);
-  cnt = block_sum_f(cnt, red);
-  const double mu = cnt > 0.f ? (double)(sd / cnt) : 0.0;
-  // load (FP64 -> FP32, shifted)
-  for (int t = threadIdx.x; t < n * (n + 1) / 2; t += blockDim.x) {
-    int i = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
-    while ((i + 1) * (i + 2) / 2 <= t) ++i;
-    while (i * (i + 1) / 2 > t) --i;
-    const int j = t - i * (i + 1) / 2;
-    const double2 x = a[i + (size_t)j * n];
-    double re = x.x;
-    if (i == j && fabs(re) < 1e9) re -= mu;
-    S[t] = make_float2((float)re, i == j ? 0.f : (float)x.y);
+  const double mu = nv > 0 ? (double)(sd / (float)nv) : 0.0;
+  // load the valid lower triangle, FP64 -> FP32, shifted: row i of the lower triangle is the
+  // conjugate of column i above the diagonal (contiguous reads)
+  for (int i = warp; i < nv; i += nwarp) {
+    const double2* col = a + (size_t)mp[i] * n;
+    for (int j = lane; j <= i; j += 32) {
+      const double2 x = col[mp[j]];
+      S[tri(i, j)] = i == j ? make_float2((float)(x.x - mu), 0.f) : make_float2((float)x.x, (float)-x.y);
+    }
   }
   __syncthreads();
   float2* vq = H.vq + (size_t)b * n * n;
-  for (int k = 0; k < n - 2; ++k) {
-    const int m = n - k - 1;   // length of the column below the diagonal
-    // sigma = ||x||^2, x = A[k+1:, k]
+  for (int k = 0; k < nv - 2; ++k) {
+    const int m = nv - k - 1;   // length of the column below the diagonal
     float s = 0.f;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       const float2 x = S[tri(k + 1 + i, k)];
@@ -892,8 +919,7 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
       vq[(size_t)k * n + k + 1 + i] = x;
     }
     __syncthreads();
-    // p = beta A' v   (A' = A[k+1:, k+1:]); 4 threads per row
-    // (every lane of a warp runs the same number of iterations, so the shuffles are uniform)
+    // p = beta A' v   (A' = A[k+1:, k+1:]); 4 threads per row, uniform shuffles
     for (int t0 = 0; t0 < 4 * m; t0 += blockDim.x) {
       const int t = t0 + threadIdx.x;
       const bool act = t < 4 * m;
@@ -921,28 +947,32 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
     // w = p - K v  (in place in p)
     for (int i = threadIdx.x; i < m; i += blockDim.x) p[i] = make_float2(p[i].x - kk * v[i].x, p[i].y - kk * v[i].y);
     __syncthreads();
-    // A' -= v w^H + w v^H (lower triangle); column k becomes (alpha, 0, ...)
-    for (int t = threadIdx.x; t < m * (m + 1) / 2; t += blockDim.x) {
-      int i = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
-      while ((i + 1) * (i + 2) / 2 <= t) ++i;
-      while (i * (i + 1) / 2 > t) --i;
-      const int j = t - i * (i + 1) / 2;
-      const float2 vi = v[i], vj = v[j], wi = p[i], wj = p[j];
-      float2 x = S[tri(k + 1 + i, k + 1 + j)];
-      // v_i conj(w_j) + w_i conj(v_j)
-      x.x -= (vi.x * wj.x + vi.y * wj.y) + (wi.x * vj.x + wi.y * vj.y);
-      x.y -= (vi.y * wj.x - vi.x * wj.y) + (wi.y * vj.x - wi.x * vj.y);
-      if (i == j) x.y = 0.f;
-      S[tri(k + 1 + i, k + 1 + j)] = x;
+    // A' -= v w^H + w v^H on the lower triangle, one warp per row
+    for (int i = warp; i < m; i += nwarp) {
+      const float2 vi = v[i], wi = p[i];
+      float2* row = S + tri(k + 1 + i, k + 1);
+      for (int j = lane; j <= i; j += 32) {
+        const float2 vj = v[j], wj = p[j];
+        float2 x = row[j];
+        x.x -= (vi.x * wj.x + vi.y * wj.y) + (wi.x * vj.x + wi.y * vj.y);
+        x.y -= (vi.y * wj.x - vi.x * wj.y) + (wi.y * vj.x - wi.x * vj.y);
+        if (i == j) x.y = 0.f;
+        row[j] = x;
+      }
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    H.d[(size_t)b * n + n - 2] = S[tri(n - 2, n - 2)].x;
-    H.d[(size_t)b * n + n - 1] = S[tri(n - 1, n - 1)].x;
-    H.e[(size_t)b * n + n - 2] = S[tri(n - 1, n - 2)];
-    H.beta[(size_t)b * n + n - 2] = 0.f;
-    H.beta[(size_t)b * n + n - 1] = 0.f;
+    if (nv >= 2) {
+      H.d[(size_t)b * n + nv - 2] = S[tri(nv - 2, nv - 2)].x;
+      H.d[(size_t)b * n + nv - 1] = S[tri(nv - 1, nv - 1)].x;
+      H.e[(size_t)b * n + nv - 2] = S[tri(nv - 1, nv - 2)];
+      H.beta[(size_t)b * n + nv - 2] = 0.f;
+      H.beta[(size_t)b * n + nv - 1] = 0.f;
+    } else if (nv == 1) {
+      H.d[(size_t)b * n] = S[0].x;
+      H.beta[(size_t)b * n] = 0.f;
+    }
     H.shift[b] = mu;
   }
 }
@@ -973,142 +1003,98 @@ __device__ __forceinline__ int sturm32(const float* dd, const float* ee2, int n,
   return c;
 }
 
-__global__ void __launch_bounds__(256) k_tri_wanted(HhArgs H) {
+// spectrum scale of the valid tridiagonal (Gershgorin), shared by the eigenvalue and the
+// grouping kernels
+__device__ __forceinline__ void tri_bounds(const float* dd, const float* ee, int nv, float& lo, float& hi) {
+  lo = 1e30f;
+  hi = -1e30f;
+  for (int i = 0; i < nv; ++i) {
+    const float r = (i > 0 ? ee[i - 1] : 0.f) + (i < nv - 1 ? ee[i] : 0.f);
+    lo = fminf(lo, dd[i] - r);
+    hi = fmaxf(hi, dd[i] + r);
+  }
+  if (nv == 0) lo = hi = 0.f;
+}
+
+constexpr int TRI_THREADS = 32;
+
+// eigenvalue j by Sturm bisection and its vector by inverse iteration, one thread per j
+// (grid (ceil(nw / 32), nprob)); padding pairs (j >= nv) take their diagonal value
+__global__ void __launch_bounds__(TRI_THREADS) k_tri_eig(HhArgs H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = H.n, nw = H.nw, b = blockIdx.x;
+  const int n = H.n, nw = H.nw, b = blockIdx.y;
+  const int nv = H.nv[b];
   float* dd = reinterpret_cast<float*>(smem_raw);   // [n]
   float* ee = dd + n;                               // [n] |e|
   float* ee2 = ee + n;                              // [n] |e|^2
-  float* lam = ee2 + n;                             // [nw]
-  __shared__ float bounds[2];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
     dd[i] = H.d[(size_t)b * n + i];
-    const float2 e = i < n - 1 ? H.e[(size_t)b * n + i] : make_float2(0.f, 0.f);
+    const float2 e = i < nv - 1 ? H.e[(size_t)b * n + i] : make_float2(0.f, 0.f);
     ee[i] = sqrtf(e.x * e.x + e.y * e.y);
     ee2[i] = e.x * e.x + e.y * e.y;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {   // Gershgorin bounds over the non-padding part
-    float lo = 1e30f, hi = -1e30f;
-    for (int i = 0; i < n; ++i) {
-      const float r = (i > 0 ? ee[i - 1] : 0.f) + (i < n - 1 ? ee[i] : 0.f);
-      lo = fminf(lo, dd[i] - r);
-      hi = fmaxf(hi, dd[i] + r);
-    }
-    bounds[0] = lo;
-    bounds[1] = hi;
+  float lo, hi;
+  tri_bounds(dd, ee, nv, lo, hi);
+  const float scale = fmaxf(fmaxf(fabsf(lo), fabsf(hi)), 1e-6f);
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nw) return;
+  if (j >= nv) {
+    const int src = H.map[(size_t)b * n + j];
+    const double x = H.A[(size_t)b * n * n + src + (size_t)src * n].x;
+    H.lam[(size_t)b * nw + j] = (float)(x - H.shift[b]);
+    if (H.lam64) H.lam64[(size_t)b * n + j] = x;
+    return;
   }
-  __syncthreads();
-  float tnorm = fmaxf(fabsf(bounds[0]), fabsf(bounds[1]));
-  // clamp the upper bound to the valid spectrum scale (padding sits near 1e10)
-  const float pivmin = 1e-30f;
-  // bisection: thread j -> j-th smallest eigenvalue
-  for (int j = threadIdx.x; j < nw; j += blockDim.x) {
-    float lo = bounds[0], hi = bounds[1];
-    for (int it = 0; it < 80 && hi - lo > 2e-7f * fmaxf(fabsf(lo), fabsf(hi)) + 1e-30f; ++it) {
-      const float mid = 0.5f * (lo + hi);
-      if (sturm32(dd, ee2, n, mid, pivmin) > j) hi = mid;
-      else lo = mid;
-    }
-    lam[j] = 0.5f * (lo + hi);
-    H.lam[(size_t)b * nw + j] = lam[j];
-    if (H.lam64) H.lam64[(size_t)b * n + j] = (double)lam[j] + H.shift[b];
+  float a0 = lo, b0 = hi;
+  for (int it = 0; it < 64 && b0 - a0 > 2e-7f * scale; ++it) {
+    const float mid = 0.5f * (a0 + b0);
+    if (sturm32(dd, ee2, nv, mid, 1e-30f) > j) b0 = mid;
+    else a0 = mid;
   }
-  __syncthreads();
-  // inverse iteration (LU without pivoting, guarded pivots), one thread per wanted vector
-  // scale of the valid spectrum (padding eigenvalues sit near 1e10 and must not set it)
-  float scale = 0.f;
-  for (int i = 0; i < nw; ++i)
-    if (fabsf(lam[i]) < 1e9f) scale = fmaxf(scale, fabsf(lam[i]));
-  for (int i = 0; i < n - 1; ++i)
-    if (ee[i] < 1e9f) scale = fmaxf(scale, ee[i]);
-  scale = fmaxf(scale, 1e-6f);
-  for (int j = threadIdx.x; j < nw; j += blockDim.x) {
-    float* y = H.Y + ((size_t)b * nw + j) * n;
-    float* u = H.work + ((size_t)b * nw + j) * 3 * n;   // u (pivots), l (multipliers)
-    float* l = u + n;
-    const float guard = 1e-7f * scale;
-    // perturb the shift slightly inside its group so equal eigenvalues give different vectors
-    const float sh = lam[j] + (float)(j % 7) * 1e-7f * scale;
-    u[0] = dd[0] - sh;
-    if (fabsf(u[0]) < guard) u[0] = guard;
-    for (int i = 1; i < n; ++i) {
-      l[i] = ee[i - 1] / u[i - 1];
-      u[i] = dd[i] - sh - l[i] * ee[i - 1];
-      if (fabsf(u[i]) < guard) u[i] = copysignf(guard, u[i] == 0.f ? 1.f : u[i]);
-    }
-    for (int i = 0; i < n; ++i) y[i] = hash_unit(b, j, i, 0);
-    for (int it = 0; it < 3; ++it) {
-      for (int i = 1; i < n; ++i) y[i] -= l[i] * y[i - 1];
-      y[n - 1] /= u[n - 1];
-      for (int i = n - 2; i >= 0; --i) y[i] = (y[i] - ee[i] * y[i + 1]) / u[i];
-      float s = 0.f;
-      for (int i = 0; i < n; ++i) s += y[i] * y[i];
-      s = rsqrtf(fmaxf(s, 1e-30f));
-      for (int i = 0; i < n; ++i) y[i] *= s;
-    }
+  const float lamj = 0.5f * (a0 + b0);
+  H.lam[(size_t)b * nw + j] = lamj;
+  if (H.lam64) H.lam64[(size_t)b * n + j] = (double)lamj + H.shift[b];
+  // inverse iteration (LU without pivoting, guarded pivots)
+  float* y = H.Y + ((size_t)b * nw + j) * n;
+  float* u = H.work + ((size_t)b * nw + j) * 2 * n;   // u (pivots), l (multipliers)
+  float* l = u + n;
+  const float guard = 1e-7f * scale;
+  // perturb the shift slightly so equal eigenvalues give different vectors
+  const float sh = lamj + (float)(j % 7) * 1e-7f * scale;
+  u[0] = dd[0] - sh;
+  if (fabsf(u[0]) < guard) u[0] = guard;
+  for (int i = 1; i < nv; ++i) {
+    l[i] = ee[i - 1] / u[i - 1];
+    u[i] = dd[i] - sh - l[i] * ee[i - 1];
+    if (fabsf(u[i]) < guard) u[i] = copysignf(guard, u[i] == 0.f ? 1.f : u[i]);
   }
-  __syncthreads();
-  // Gram-Schmidt inside groups of near-equal eigenvalues (gap < 1e-4 * scale), one thread per
-  // group start
-  for (int j = threadIdx.x; j < nw; j += blockDim.x) {
-    if (j > 0 && lam[j] - lam[j - 1] < 1e-4f * scale) continue;   // not a group start
-    int end = j + 1;
-    while (end < nw && lam[end] - lam[end - 1] < 1e-4f * scale && end - j < 32) ++end;
-    for (int c = j + 1; c < end; ++c) {
-      float* yc = H.Y + ((size_t)b * nw + c) * n;
-      // if the group's earlier vectors absorb almost all of this one (exactly degenerate,
-      // decoupled eigenvalues give parallel inverse-iteration vectors), restart from a fresh
-      // random vector of the group's subspace directions
-      for (int attempt = 0; attempt < 4; ++attempt) {
-        for (int pass = 0; pass < 2; ++pass)
-          for (int q = j; q < c; ++q) {
-            const float* yq = H.Y + ((size_t)b * nw + q) * n;
-            float dot = 0.f;
-            for (int i = 0; i < n; ++i) dot += yq[i] * yc[i];
-            for (int i = 0; i < n; ++i) yc[i] -= dot * yq[i];
-          }
-        float s = 0.f;
-        for (int i = 0; i < n; ++i) s += yc[i] * yc[i];
-        if (s > 1e-4f) {
-          s = rsqrtf(s);
-          for (int i = 0; i < n; ++i) yc[i] *= s;
-          break;
-        }
-        // fresh start: random combination of the group's vectors' supports, then orthogonalise
-        for (int i = 0; i < n; ++i) {
-          float t = 0.f;
-          for (int q = j; q < c; ++q) t += fabsf((H.Y + ((size_t)b * nw + q) * n)[i]);
-          yc[i] = hash_unit(b, c, i, attempt + 1) * (t > 0.f ? 1.f : 0.05f);
-        }
-        float s2 = 0.f;
-        for (int i = 0; i < n; ++i) s2 += yc[i] * yc[i];
-        s2 = rsqrtf(fmaxf(s2, 1e-30f));
-        for (int i = 0; i < n; ++i) yc[i] *= s2;
-      }
-    }
+  for (int i = 0; i < nv; ++i) y[i] = hash_unit(b, j, i, 0);
+  for (int it = 0; it < 3; ++it) {
+    for (int i = 1; i < nv; ++i) y[i] -= l[i] * y[i - 1];
+    y[nv - 1] /= u[nv - 1];
+    for (int i = nv - 2; i >= 0; --i) y[i] = (y[i] - ee[i] * y[i + 1]) / u[i];
+    float s = 0.f;
+    for (int i = 0; i < nv; ++i) s += y[i] * y[i];
+    s = rsqrtf(fmaxf(s, 1e-30f));
+    for (int i = 0; i < nv; ++i) y[i] *= s;
   }
-  (void)tnorm;
 }
 
-// Z[:, j] = Q D y_j, one warp per wanted vector; grid (ceil(nw / 8), nprob), 256 threads
-__global__ void __launch_bounds__(256) k_hh_back(HhArgs H) {
-  const int n = H.n, nw = H.nw, b = blockIdx.y;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = blockIdx.x * 8 + warp;
-  if (j >= nw) return;
-  const float* y = H.Y + ((size_t)b * nw + j) * n;
-  double2* z = H.Z + (size_t)b * n * nw + (size_t)j * n;
-  const float2* vq = H.vq + (size_t)b * n * n;
-  const float* beta = H.beta + (size_t)b * n;
-  const float2* e = H.e + (size_t)b * n;
-  // phases: d_0 = 1, d_{k+1} = d_k e_k / |e_k|  (lane 0 walks the chain, writes z = D y)
-  if (lane == 0) {
+// Gram-Schmidt inside groups of near-equal eigenvalues (gap < 1e-4 * scale, at most 32), one
+// thread per group start; thread 0 first writes the phase chain d_0 = 1, d_{k+1} = d_k e_k/|e_k|.
+// grid nprob
+__global__ void __launch_bounds__(256) k_tri_gs(HhArgs H) {
+  const int n = H.n, nw = H.nw, b = blockIdx.x;
+  const int nv = H.nv[b];
+  const float* lam = H.lam + (size_t)b * nw;
+  if (threadIdx.x == 0) {
     float2 ph = make_float2(1.f, 0.f);
-    for (int i = 0; i < n; ++i) {
-      z[i] = make_double2((double)(ph.x * y[i]), (double)(ph.y * y[i]));
-      if (i < n - 1) {
-        const float2 ek = e[i];
+    float2* out = H.ph + (size_t)b * n;
+    for (int i = 0; i < nv; ++i) {
+      out[i] = ph;
+      if (i < nv - 1) {
+        const float2 ek = H.e[(size_t)b * n + i];
         const float ae = sqrtf(ek.x * ek.x + ek.y * ek.y);
         if (ae > 0.f) {
           const float2 u = make_float2(ek.x / ae, ek.y / ae);
@@ -1117,17 +1103,99 @@ __global__ void __launch_bounds__(256) k_hh_back(HhArgs H) {
       }
     }
   }
-  __syncwarp();
-  for (int k = n - 3; k >= 0; --k) {
+  // scale of the valid spectrum
+  float scale = 0.f;
+  const int nvw = nv < nw ? nv : nw;
+  for (int i = 0; i < nvw; ++i) scale = fmaxf(scale, fabsf(lam[i]));
+  for (int i = 0; i < nv - 1; ++i) {
+    const float2 ek = H.e[(size_t)b * n + i];
+    scale = fmaxf(scale, sqrtf(ek.x * ek.x + ek.y * ek.y));
+  }
+  scale = fmaxf(scale, 1e-6f);
+  for (int j = threadIdx.x; j < nvw; j += blockDim.x) {
+    if (j > 0 && lam[j] - lam[j - 1] < 1e-4f * scale) continue;   // not a group start
+    int end = j + 1;
+    while (end < nvw && lam[end] - lam[end - 1] < 1e-4f * scale && end - j < 32) ++end;
+    for (int c = j + 1; c < end; ++c) {
+      float* yc = H.Y + ((size_t)b * nw + c) * n;
+      // if the group's earlier vectors absorb almost all of this one (exactly degenerate,
+      // decoupled eigenvalues give parallel inverse-iteration vectors), restart from a fresh
+      // random vector on the group's support
+      for (int attempt = 0; attempt < 4; ++attempt) {
+        for (int pass = 0; pass < 2; ++pass)
+          for (int q = j; q < c; ++q) {
+            const float* yq = H.Y + ((size_t)b * nw + q) * n;
+            float dot = 0.f;
+            for (int i = 0; i < nv; ++i) dot += yq[i] * yc[i];
+            for (int i = 0; i < nv; ++i) yc[i] -= dot * yq[i];
+          }
+        float s = 0.f;
+        for (int i = 0; i < nv; ++i) s += yc[i] * yc[i];
+        if (s > 1e-4f) {
+          s = rsqrtf(s);
+          for (int i = 0; i < nv; ++i) yc[i] *= s;
+          break;
+        }
+        for (int i = 0; i < nv; ++i) {
+          float t = 0.f;
+          for (int q = j; q < c; ++q) t += fabsf((H.Y + ((size_t)b * nw + q) * n)[i]);
+          yc[i] = hash_unit(b, c, i, attempt + 1) * (t > 0.f ? 1.f : 0.05f);
+        }
+        float s2 = 0.f;
+        for (int i = 0; i < nv; ++i) s2 += yc[i] * yc[i];
+        s2 = rsqrtf(fmaxf(s2, 1e-30f));
+        for (int i = 0; i < nv; ++i) yc[i] *= s2;
+      }
+    }
+  }
+}
+
+constexpr int HB_PER = 8;   // n <= 256 entries per vector, 8 per lane
+
+// Z[:, j] = Q D y_j in FP32 registers, one warp per wanted vector, scattered back to the
+// original indices (padding pairs: unit vectors); grid (ceil(nw / 8), nprob), 256 threads
+__global__ void __launch_bounds__(256) k_hh_back(HhArgs H) {
+  const int n = H.n, nw = H.nw, b = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * 8 + warp;
+  if (j >= nw) return;
+  const int nv = H.nv[b];
+  const int* mp = H.map + (size_t)b * n;
+  double2* z = H.Z + (size_t)b * n * nw + (size_t)j * n;
+  if (j >= nv) {
+    const int src = mp[j];
+    for (int i = lane; i < n; i += 32) z[i] = make_double2(i == src ? 1.0 : 0.0, 0.0);
+    return;
+  }
+  const float* y = H.Y + ((size_t)b * nw + j) * n;
+  const float2* ph = H.ph + (size_t)b * n;
+  float2 zr[HB_PER];
+#pragma unroll
+  for (int c = 0; c < HB_PER; ++c) {
+    const int i = lane + 32 * c;
+    if (i < nv) {
+      const float yi = y[i];
+      const float2 d = ph[i];
+      zr[c] = make_float2(d.x * yi, d.y * yi);
+    } else {
+      zr[c] = make_float2(0.f, 0.f);
+    }
+  }
+  const float2* vq = H.vq + (size_t)b * n * n;
+  const float* beta = H.beta + (size_t)b * n;
+  for (int k = nv - 3; k >= 0; --k) {
     const float bet = beta[k];
     if (bet == 0.f) continue;
-    const float2* v = vq + (size_t)k * n;   // entries k+1 .. n-1
-    double sr = 0.0, si = 0.0;              // s = v^H z
-    for (int i = k + 1 + lane; i < n; i += 32) {
-      const float2 vi = v[i];
-      const double2 zi = z[i];
-      sr += vi.x * zi.x + vi.y * zi.y;
-      si += vi.x * zi.y - vi.y * zi.x;
+    const float2* v = vq + (size_t)k * n;   // entries k+1 .. nv-1
+    float sr = 0.f, si = 0.f;               // s = v^H z
+#pragma unroll
+    for (int c = 0; c < HB_PER; ++c) {
+      const int i = lane + 32 * c;
+      if (i > k && i < nv) {
+        const float2 vi = v[i];
+        sr += vi.x * zr[c].x + vi.y * zr[c].y;
+        si += vi.x * zr[c].y - vi.y * zr[c].x;
+      }
     }
     for (int o = 16; o > 0; o >>= 1) {
       sr += __shfl_xor_sync(0xffffffffu, sr, o);
@@ -1135,30 +1203,40 @@ __global__ void __launch_bounds__(256) k_hh_back(HhArgs H) {
     }
     sr *= bet;
     si *= bet;
-    for (int i = k + 1 + lane; i < n; i += 32) {
-      const float2 vi = v[i];
-      double2 zi = z[i];
-      zi.x -= vi.x * sr - vi.y * si;
-      zi.y -= vi.x * si + vi.y * sr;
-      z[i] = zi;
+#pragma unroll
+    for (int c = 0; c < HB_PER; ++c) {
+      const int i = lane + 32 * c;
+      if (i > k && i < nv) {
+        const float2 vi = v[i];
+        zr[c].x -= vi.x * sr - vi.y * si;
+        zr[c].y -= vi.x * si + vi.y * sr;
+      }
     }
-    __syncwarp();
   }
+#pragma unroll
+  for (int c = 0; c < HB_PER; ++c) {
+    const int i = lane + 32 * c;
+    if (i < nv) z[mp[i]] = make_double2((double)zr[c].x, (double)zr[c].y);
+  }
+  for (int t = nv + lane; t < n; t += 32) z[mp[t]] = make_double2(0.0, 0.0);
 }
 
-size_t hh_smem(int n) { return ((size_t)n * (n + 1) / 2 + 1 + 2 * (size_t)n) * sizeof(float2); }
+size_t hh_smem(int n) {
+  return ((size_t)n * (n + 1) / 2 + 1 + 2 * (size_t)n) * sizeof(float2) + (size_t)n * sizeof(int);
+}
 
 size_t hh_scratch_bytes(int n, int nw, int nprob) {
-  return (size_t)nprob * ((size_t)n * n * sizeof(float2) + 3 * n * sizeof(float) + n * sizeof(float2) +
-                          nw * sizeof(float) + (size_t)nw * n * sizeof(float) * 4 + sizeof(double) + 64) +
-         4096;
+  const size_t per = (size_t)n * n * sizeof(float2) + 2 * n * sizeof(float) + 2 * n * sizeof(float2) +
+                     n * sizeof(int) + sizeof(int) + sizeof(double) + nw * sizeof(float) +
+                     (size_t)nw * n * sizeof(float) * 3;
+  return (size_t)nprob * per + 16 * 256 + 4096;
 }
 
 // FP32 stage: Z (FP64 storage, [nprob][n x nw]) holds approximate eigenvectors of the lowest nw
-// eigenvalues of each A (read only), lam32 their FP32 eigenvalues (shift added back in lam64).
+// eigenvalues of each A (read only), lam64 their eigenvalues (shift added back).
 cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, int nprob, double2* Z,
                             void* scratch, size_t scratch_bytes, double* lam64) {
-  if (hh_smem(n) > 226 * 1024 || nw > n || nw < 1) return cudaErrorInvalidValue;
+  if (n > 32 * HB_PER || hh_smem(n) > 226 * 1024 || nw > n || nw < 1) return cudaErrorInvalidValue;
   if (hh_scratch_bytes(n, nw, nprob) > scratch_bytes) return cudaErrorInvalidValue;
   unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
   auto take = [&](size_t bytes) {
@@ -1174,15 +1252,19 @@ cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, in
   H.beta = (float*)take((size_t)nprob * n * sizeof(float));
   H.d = (float*)take((size_t)nprob * n * sizeof(float));
   H.e = (float2*)take((size_t)nprob * n * sizeof(float2));
+  H.ph = (float2*)take((size_t)nprob * n * sizeof(float2));
+  H.map = (int*)take((size_t)nprob * n * sizeof(int));
+  H.nv = (int*)take((size_t)nprob * sizeof(int));
   H.shift = (double*)take((size_t)nprob * sizeof(double));
   H.lam = (float*)take((size_t)nprob * nw * sizeof(float));
   H.Y = (float*)take((size_t)nprob * nw * n * sizeof(float));
-  H.work = (float*)take((size_t)nprob * nw * 3 * n * sizeof(float));
+  H.work = (float*)take((size_t)nprob * nw * 2 * n * sizeof(float));
   H.Z = Z;
   H.lam64 = lam64;
   cudaFuncSetAttribute(k_hh_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hh_smem(n));
   k_hh_tridiag<<<nprob, HH_THREADS, hh_smem(n), st>>>(H);
-  k_tri_wanted<<<nprob, 256, (3 * n + nw) * sizeof(float), st>>>(H);
+  k_tri_eig<<<dim3((nw + TRI_THREADS - 1) / TRI_THREADS, nprob), TRI_THREADS, 3 * n * sizeof(float), st>>>(H);
+  k_tri_gs<<<nprob, 256, 0, st>>>(H);
   k_hh_back<<<dim3((nw + 7) / 8, nprob), 256, 0, st>>>(H);
   return cudaGetLastError();
 }
@@ -1408,41 +1490,90 @@ __global__ void k_add_identity(double2* E, int nw) {
 }  // namespace hw
 
 // ===================================================================== Cholesky-QR apply
-// W <- W (L^H)^{-1} for each k-point, one thread per row: row w of W solves y L^H = w, i.e.
-// y_j = (w_j - sum_{i<j} conj(L_ji) y_i) / L_jj, in place.  L (m x m, lower, from k_chol) is
-// staged in shared memory.  W: rows x m block with leading dimension ld, batch stride sW.
+// W <- W (L^H)^{-1} for each k-point: row w of W solves y L^H = w, i.e.
+// y_j = (w_j - sum_{i<j} conj(L_ji) y_i) / L_jj, in place.  Eight lanes share one row: lane q
+// keeps the columns j = q (mod 8) in registers; at step j the owner finishes y_j and
+// broadcasts it, and every lane subtracts conj(L_kj) y_j from its columns k > j (right-looking
+// order, same arithmetic).  L (m x m, lower, from k_chol) is staged in shared memory with the
+// reciprocal diagonal.  W: rows x m block with leading dimension ld, batch stride sW.
 namespace hw {
-__global__ void __launch_bounds__(128) k_trsm_lh(const double2* L, int m, double2* W, int64_t rows, int64_t ld,
+template <int NPER>
+__global__ void __launch_bounds__(256) k_trsm_lh(const double2* L, int m, double2* W, int64_t rows, int64_t ld,
                                                  int64_t sW) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* Ls = reinterpret_cast<double2*>(smem_raw);
+  double* dinv = reinterpret_cast<double*>(Ls + (size_t)m * m);
   const int b = blockIdx.y;
   const double2* l = L + (size_t)b * m * m;
   for (int t = threadIdx.x; t < m * m; t += blockDim.x) Ls[t] = l[t];
   __syncthreads();
-  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= rows) return;
-  double2* w = W + (size_t)b * sW + r;
-  for (int j = 0; j < m; ++j) {
-    double2 acc = w[(size_t)j * ld];
-    for (int i = 0; i < j; ++i) {
-      const double2 lji = Ls[j + (size_t)i * m];   // L[j][i]
-      const double2 yi = w[(size_t)i * ld];
-      // acc -= conj(lji) * yi
-      acc.x -= lji.x * yi.x + lji.y * yi.y;
-      acc.y -= lji.x * yi.y - lji.y * yi.x;
-    }
-    const double inv = 1.0 / Ls[j + (size_t)j * m].x;
-    w[(size_t)j * ld] = make_double2(acc.x * inv, acc.y * inv);
+  for (int j = threadIdx.x; j < m; j += blockDim.x) dinv[j] = 1.0 / Ls[j + (size_t)j * m].x;
+  __syncthreads();
+  const int q = threadIdx.x & 7;
+  const int64_t r = (int64_t)blockIdx.x * 32 + (threadIdx.x >> 3);
+  const bool valid = r < rows;
+  double2* w = W + (size_t)b * sW + (valid ? r : 0);
+  double2 acc[NPER];
+#pragma unroll
+  for (int c = 0; c < NPER; ++c) {
+    const int j = q + 8 * c;
+    acc[c] = (valid && j < m) ? w[(size_t)j * ld] : make_double2(0.0, 0.0);
   }
+#pragma unroll
+  for (int cb = 0; cb < NPER; ++cb) {
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const int j = 8 * cb + o;
+      if (j < m) {
+        double yx = 0.0, yy = 0.0;
+        if (q == o) {
+          const double di = dinv[j];
+          yx = acc[cb].x * di;
+          yy = acc[cb].y * di;
+          acc[cb] = make_double2(yx, yy);
+        }
+        yx = __shfl_sync(0xffffffffu, yx, o, 8);
+        yy = __shfl_sync(0xffffffffu, yy, o, 8);
+#pragma unroll
+        for (int c = cb; c < NPER; ++c) {
+          const int k = q + 8 * c;
+          if (k > j && k < m) {
+            const double2 lkj = Ls[k + (size_t)j * m];   // L[k][j]; acc -= conj(lkj) y
+            acc[c].x -= lkj.x * yx + lkj.y * yy;
+            acc[c].y -= lkj.x * yy - lkj.y * yx;
+          }
+        }
+      }
+    }
+  }
+  if (valid) {
+#pragma unroll
+    for (int c = 0; c < NPER; ++c) {
+      const int j = q + 8 * c;
+      if (j < m) w[(size_t)j * ld] = acc[c];
+    }
+  }
+}
+
+template <int NPER>
+static cudaError_t trsm_launch(cudaStream_t st, const double2* L, int m, int nprob, double2* W, int64_t rows,
+                               int64_t ld, int64_t sW, size_t smem) {
+  cudaFuncSetAttribute(k_trsm_lh<NPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  k_trsm_lh<NPER><<<dim3((unsigned)((rows + 31) / 32), nprob), 256, smem, st>>>(L, m, W, rows, ld, sW);
+  return cudaGetLastError();
 }
 
 cudaError_t dense_trsm_lh(cudaStream_t st, const double2* L, int m, int nprob, double2* W, int64_t rows, int64_t ld,
                           int64_t sW) {
-  const size_t smem = (size_t)m * m * sizeof(double2);
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  cudaFuncSetAttribute(k_trsm_lh, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  k_trsm_lh<<<dim3((unsigned)((rows + 127) / 128), nprob), 128, smem, st>>>(L, m, W, rows, ld, sW);
-  return cudaGetLastError();
+  const size_t smem = (size_t)m * m * sizeof(double2) + (size_t)m * sizeof(double);
+  if (m > 120 || smem > 220 * 1024) return cudaErrorInvalidValue;
+  if (rows <= 0) return cudaSuccess;
+  const int nper = (m + 7) / 8;
+  if (nper <= 2) return trsm_launch<2>(st, L, m, nprob, W, rows, ld, sW, smem);
+  if (nper <= 4) return trsm_launch<4>(st, L, m, nprob, W, rows, ld, sW, smem);
+  if (nper <= 6) return trsm_launch<6>(st, L, m, nprob, W, rows, ld, sW, smem);
+  if (nper <= 9) return trsm_launch<9>(st, L, m, nprob, W, rows, ld, sW, smem);
+  if (nper <= 12) return trsm_launch<12>(st, L, m, nprob, W, rows, ld, sW, smem);
+  return trsm_launch<15>(st, L, m, nprob, W, rows, ld, sW, smem);
 }
 }  // namespace hw

@@ -93,6 +93,8 @@ struct LobpcgWork {
   double2* B3 = nullptr;
   int* grp = nullptr;       // [nk][nb]
   double2* Abak = nullptr;  // [nk][ne*ne] copy of the Rayleigh-Ritz matrix (Jacobi retry)
+  float2* F32[3] = {nullptr, nullptr, nullptr};   // FP32 operand copies for low-precision products
+  size_t f32_ab = 0, f32_c = 0;                   // their sizes (elements)
 };
 
 void lobpcg_free(hw_ctx* ctx) {
@@ -102,7 +104,8 @@ void lobpcg_free(hw_ctx* ctx) {
                   (void*)w->A, (void*)w->Z, (void*)w->w, (void*)w->G, (void*)w->Ui, (void*)w->C,
                   (void*)w->Y, (void*)w->Y2, (void*)w->res, (void*)w->theta, (void*)w->iact,
                   (void*)w->fail, (void*)w->status, w->j32, w->hh, (void*)w->B1, (void*)w->B2,
-                  (void*)w->B3, (void*)w->grp, (void*)w->Abak})
+                  (void*)w->B3, (void*)w->grp, (void*)w->Abak, (void*)w->F32[0], (void*)w->F32[1],
+                  (void*)w->F32[2]})
     if (p) cudaFree(p);
   dense_free(w->dw);
   delete w;
@@ -275,9 +278,47 @@ __global__ void k_copy_start(PtrArr src, double2* S, int64_t Lpad, int64_t sK, c
 }
 
 // ------------------------------------------------------------------------ cuBLAS helper
+// dst[b][c][r] = src[b][c*ld + r] (FP64 -> FP32 complex, packed columns); grid-stride
+__global__ void k_cvt_d2f(const double2* __restrict__ src, int64_t ld, int rows, int cols, int64_t sSrc,
+                          float2* __restrict__ dst, int batch) {
+  const int64_t per = (int64_t)rows * cols, tot = per * batch;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / per, q = t - b * per, c = q / rows, r = q - c * rows;
+    const double2 x = src[b * sSrc + c * ld + r];
+    dst[t] = make_float2((float)x.x, (float)x.y);
+  }
+}
+
+// dst[b][c*ld + r] = src[b][c][r] (FP32 -> FP64)
+__global__ void k_cvt_f2d(const float2* __restrict__ src, int rows, int cols, double2* __restrict__ dst, int64_t ld,
+                          int64_t sDst, int batch) {
+  const int64_t per = (int64_t)rows * cols, tot = per * batch;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / per, q = t - b * per, c = q / rows, r = q - c * rows;
+    const float2 x = src[t];
+    dst[b * sDst + c * ld + r] = make_double2((double)x.x, (double)x.y);
+  }
+}
+
+// Batched complex GEMM on the context's cuBLAS handle.  With `lowp` set, products that run
+// over the basis dimension (m or k equal to bigdim) are computed in complex FP32 on converted
+// copies of the operands (the early, large-residual iterations of the mixed form); the rest
+// stay FP64.
 struct Gemm {
   hw_ctx* ctx;
   cublasStatus_t st = CUBLAS_STATUS_SUCCESS;
+  bool lowp = false;
+  int64_t bigdim = -1;
+  float2* a32 = nullptr;
+  float2* b32 = nullptr;
+  float2* c32 = nullptr;
+  size_t cap_ab = 0, cap_c = 0;   // elements
+  void cvt_in(const double2* src, int64_t ld, int rows, int cols, int64_t s, float2* dst, int batch) {
+    const int64_t tot = (int64_t)rows * cols * batch;
+    const int grid = (int)std::min<int64_t>((tot + 255) / 256, 152 * 16);
+    k_cvt_d2f<<<grid, 256, 0, ctx->stream>>>(src, ld, rows, cols, s, dst, batch);
+    ctx->launches++;
+  }
   void operator()(cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, double alpha,
                   const double2* A, int64_t lda, int64_t sA, const double2* B, int64_t ldb, int64_t sB,
                   double beta, double2* C, int64_t ldc, int64_t sC, int batch) {
@@ -285,8 +326,27 @@ struct Gemm {
     if (k <= 0) {  // C = beta C
       if (beta == 1.0) return;
     }
-    const cuDoubleComplex al = make_cuDoubleComplex(alpha, 0.0), be = make_cuDoubleComplex(beta, 0.0);
     ProfScope ps(ctx, HW_PH_GEMM);
+    const int ra = ta == CUBLAS_OP_N ? m : k, ca = ta == CUBLAS_OP_N ? k : m;
+    const int rb = tb == CUBLAS_OP_N ? k : n, cb = tb == CUBLAS_OP_N ? n : k;
+    if (lowp && k > 0 && (m == bigdim || k == bigdim) && (size_t)ra * ca * batch <= cap_ab &&
+        (size_t)rb * cb * batch <= cap_ab && (size_t)m * n * batch <= cap_c) {
+      cvt_in(A, lda, ra, ca, sA, a32, batch);
+      const bool same = A == B && lda == ldb && sA == sB && ra == rb && ca == cb;
+      if (!same) cvt_in(B, ldb, rb, cb, sB, b32, batch);
+      if (beta != 0.0) cvt_in(C, ldc, m, n, sC, c32, batch);
+      const cuComplex al = make_cuComplex((float)alpha, 0.f), be = make_cuComplex((float)beta, 0.f);
+      st = cublasCgemmStridedBatched(ctx->cublas, ta, tb, m, n, k, &al, reinterpret_cast<const cuComplex*>(a32), ra,
+                                     (int64_t)ra * ca, reinterpret_cast<const cuComplex*>(same ? a32 : b32), rb,
+                                     (int64_t)rb * cb, &be, reinterpret_cast<cuComplex*>(c32), m, (int64_t)m * n,
+                                     batch);
+      const int64_t tot = (int64_t)m * n * batch;
+      const int grid = (int)std::min<int64_t>((tot + 255) / 256, 152 * 16);
+      k_cvt_f2d<<<grid, 256, 0, ctx->stream>>>(c32, m, n, C, ldc, sC, batch);
+      ctx->launches++;
+      return;
+    }
+    const cuDoubleComplex al = make_cuDoubleComplex(alpha, 0.0), be = make_cuDoubleComplex(beta, 0.0);
     st = cublasZgemmStridedBatched(ctx->cublas, ta, tb, m, n, std::max(k, 1), &al,
                                    reinterpret_cast<const cuDoubleComplex*>(A), (int)lda, sA,
                                    reinterpret_cast<const cuDoubleComplex*>(B), (int)ldb, sB, &be,
@@ -317,7 +377,8 @@ static hw_status cholqr(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, double2* S, int 
       ProfScope ps_(ctx, HW_PH_CHOL);
       dense_hermitize(ctx->stream, w->G, ncol, nk);
       dense_chol(ctx->stream, w->G, ncol, nk, w->fail);
-      dense_trsm_lh(ctx->stream, w->G, ncol, nk, Wb, Lpad, Lpad, sK);   // W <- W L^{-H}, in place
+      const cudaError_t te = dense_trsm_lh(ctx->stream, w->G, ncol, nk, Wb, Lpad, Lpad, sK);   // W <- W L^{-H}
+      if (te != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("cholqr: ") + cudaGetErrorString(te));
       ctx->launches += 3;
     }
     std::vector<int> f(nk);
@@ -588,6 +649,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
   }
   int nb = block > 0 ? block : n_eig + std::max(4, n_eig / 8);
   if (nb < n_eig) return hw_fail(ctx, HW_EINVAL, "block < n_eig");
+  if (nb > 112) return hw_fail(ctx, HW_EINVAL, "block > 112");
   if (3 * (int64_t)nb > Lmin) return hw_fail(ctx, HW_EINVAL, "block too large for the basis (3*block > L)");
   if (evecs && ld_evecs < Lmax) return hw_fail(ctx, HW_EINVAL, "ld_evecs < L");
   const int64_t Lpad = (Lmax + 7) / 8 * 8;
@@ -598,6 +660,39 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
   cudaStream_t st = ctx->stream;
   Gemm gemm{ctx};
   const int64_t sK = Lpad * 3 * nb;
+  // mixed form: products over the basis dimension in complex FP32 until the residuals fall
+  // below 10^-lowp_exp, then FP64 (X re-orthonormalised, H X recomputed, P restarted)
+  const double lowp_thr = (prec == HW_MIXED && ctx->lowp_exp > 0) ? std::pow(10.0, -ctx->lowp_exp) : 0.0;
+  if (lowp_thr > 0.0) {
+    const size_t ab = (size_t)nk * Lpad * 3 * nb;
+    const size_t cc = std::max((size_t)nk * Lpad * nb, (size_t)nk * w->ne * w->ne);
+    if (w->f32_ab < ab || w->f32_c < cc) {
+      for (auto& p : w->F32) {
+        if (p) cudaFree(p);
+        p = nullptr;
+      }
+      cudaError_t e0 = cudaMalloc((void**)&w->F32[0], ab * sizeof(float2));
+      if (e0 == cudaSuccess) e0 = cudaMalloc((void**)&w->F32[1], ab * sizeof(float2));
+      if (e0 == cudaSuccess) e0 = cudaMalloc((void**)&w->F32[2], cc * sizeof(float2));
+      if (e0 != cudaSuccess) {
+        for (auto& p : w->F32) {
+          if (p) cudaFree(p);
+          p = nullptr;
+        }
+        w->f32_ab = w->f32_c = 0;
+        return hw_fail(ctx, HW_ENOMEM, "FP32 product buffers");
+      }
+      w->f32_ab = ab;
+      w->f32_c = cc;
+    }
+    gemm.a32 = w->F32[0];
+    gemm.b32 = w->F32[1];
+    gemm.c32 = w->F32[2];
+    gemm.cap_ab = w->f32_ab;
+    gemm.cap_c = w->f32_c;
+    gemm.bigdim = Lpad;
+    gemm.lowp = true;
+  }
   std::vector<int64_t> Lb(nk);
   for (int b = 0; b < nk; ++b) Lb[b] = ctx->hb.L[kidx[b]];
   int64_t* dL = nullptr;
@@ -645,11 +740,11 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
   bool fp64_products = !mixed;
   hs = apply_block(ctx, w, kidx, w->SB[0], w->HSB[0], 0, nb, fp64_products);
   if (hs != HW_OK) return hs;
-  // Rayleigh-Ritz on X alone
-  {
+  // Rayleigh-Ritz on X alone: SB[from] -> SB[1 - from]
+  auto rr_on_x = [&](int from) -> hw_status {
     const int n = nb + (nb & 1);
-    gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, (int)Lpad, 1.0, w->SB[0], Lpad, sK, w->HSB[0], Lpad, sK, 0.0, w->A, n,
-         (int64_t)n * n, nk);
+    gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, (int)Lpad, 1.0, w->SB[from], Lpad, sK, w->HSB[from], Lpad, sK, 0.0, w->A,
+         n, (int64_t)n * n, nk);
     std::vector<int> z(nk, 0);
     cudaMemcpyAsync(dnv + nk, z.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(dnv + 2 * nk, z.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
@@ -660,20 +755,25 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     }
     cudaError_t e = rr_eig(ctx, w, gemm, n, nb, false);
     if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
-    gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nb, 1.0, w->SB[0], Lpad, sK, w->Z, n, (int64_t)n * n, 0.0,
-         w->SB[1], Lpad, sK, nk);
-    gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nb, 1.0, w->HSB[0], Lpad, sK, w->Z, n, (int64_t)n * n, 0.0,
-         w->HSB[1], Lpad, sK, nk);
+    gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nb, 1.0, w->SB[from], Lpad, sK, w->Z, n, (int64_t)n * n, 0.0,
+         w->SB[1 - from], Lpad, sK, nk);
+    gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nb, 1.0, w->HSB[from], Lpad, sK, w->Z, n, (int64_t)n * n, 0.0,
+         w->HSB[1 - from], Lpad, sK, nk);
     for (int b = 0; b < nk; ++b)
       cudaMemcpyAsync(w->theta + (size_t)b * nb, w->w + (size_t)b * n, nb * sizeof(double), cudaMemcpyDeviceToDevice, st);
-    cur = 1;
-  }
+    cur = 1 - from;
+    return HW_OK;
+  };
+  hs = rr_on_x(0);
+  if (hs != HW_OK) return hs;
   int np = 0;                                  // P block width (uniform)
   std::vector<int> npv(nk, 0);                 // valid P columns per k-point
   std::vector<char> done(nk, 0);
   std::vector<int> it_done(nk, maxit);
   std::vector<double> resh((size_t)nk * nb), thh((size_t)nk * nb);
   bool refreshed = !mixed;
+  double lowp_best = 1e300;
+  int lowp_best_it = 0;
   int it = 0;
   hw_status final_status = HW_ENOTCONV;
   for (it = 0; it <= maxit; ++it) {
@@ -720,6 +820,31 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
         claim[b] = 1;
         ++nclaim;
       }
+    }
+    // FP32 products stall near residual 1e-5: leave them also when the best residual has not
+    // dropped by 30% in 4 iterations
+    if (gemm.lowp) {
+      if (maxres < 0.7 * lowp_best) {
+        lowp_best = maxres;
+        lowp_best_it = it;
+      }
+    }
+    if (gemm.lowp && (maxres < lowp_thr || nclaim > 0 || it - lowp_best_it >= 4)) {
+      // leave the FP32 products: X re-orthonormalised and its H X recomputed in FP64, a
+      // Rayleigh-Ritz step on X alone, and the conjugate directions restarted
+      gemm.lowp = false;
+      std::vector<int> nbv(nk, nb);
+      cudaMemcpyAsync(dnv, nbv.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
+      hs = cholqr(ctx, w, gemm, S, 0, nb, dnv, 2, failed);
+      if (hs != HW_OK) return hs;
+      hs = apply_block(ctx, w, kidx, S, HS, 0, nb, true);
+      if (hs != HW_OK) return hs;
+      hs = rr_on_x(cur);
+      if (hs != HW_OK) return hs;
+      refreshed = true;
+      np = 0;
+      std::fill(npv.begin(), npv.end(), 0);
+      continue;
     }
     if (mixed && ((!refreshed && maxres < 1e-3) || nclaim > 0)) {
       std::vector<int> which(nk, 0);
@@ -885,7 +1010,8 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
         ProfScope ps_(ctx, HW_PH_CHOL);
         dense_hermitize(st, w->G, na, nk);
         dense_chol(st, w->G, na, nk, w->fail);
-        dense_trsm_lh(st, w->G, na, nk, w->Y, n, n, (int64_t)n * na);   // Y <- Y L^{-H}, in place
+        const cudaError_t te = dense_trsm_lh(st, w->G, na, nk, w->Y, n, n, (int64_t)n * na);   // Y <- Y L^{-H}
+        if (te != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("P basis: ") + cudaGetErrorString(te));
         ctx->launches += 3;
       }
       std::vector<int> f(nk);

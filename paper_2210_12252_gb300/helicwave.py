@@ -243,6 +243,7 @@ def hw_synchronize(h):
 
 HW_OPT_RR_METHOD = 0
 HW_OPT_RR_FALLBACKS = 1
+HW_OPT_LOWP_SWITCH = 2
 
 
 def hw_set_option(h, option, value):

@@ -1,8 +1,8 @@
 """GPU block eigensolver (hw_solve_eigs) against the oracle's direct diagonalisation.
 
 Bars: FP64 path within 1e-8 Ha of the dense oracle eigenvalues; mixed path (FP32 transforms,
-FP64 Gram / Rayleigh-Ritz / residual check) within 1e-6 Ha; every reported residual below the
-requested tolerance.  Stored eigenvalues under tests/golden/ were written by
+FP32 block products while the residuals are large, then FP64 Gram / Rayleigh-Ritz / residual
+check) within 1e-6 Ha; every reported residual below the requested tolerance.  Stored eigenvalues under tests/golden/ were written by
 tests/golden/make_golden.py from the oracle alone.
 """
 import os
@@ -85,6 +85,24 @@ def test_rr_methods_agree(hwmod):
             assert ctx.get_option(hwmod.HW_OPT_RR_FALLBACKS) == 0
         ctx.close()
     assert np.abs(out[0] - out[1]).max() < 1e-9
+
+
+@pytest.mark.parametrize("switch", [0, 2, 4, 12])
+def test_mixed_fp32_product_phase(hwmod, switch):
+    """The FP32 block-product phase ends at residual 10^-switch, or by the stagnation guard when
+    FP32 products cannot get there (12); every setting reaches the oracle's eigenvalues with
+    FP64-verified residuals and orthonormal vectors."""
+    w = inputs.tiny()
+    ctx, L = make_ctx(hwmod, w)
+    ctx.set_option(hwmod.HW_OPT_LOWP_SWITCH, switch)
+    r = ctx.solve_eigs([0], w.n_eig, tol=1e-7, maxit=400, prec="mixed", vectors=True)
+    assert r["converged"], r["iters"]
+    assert np.abs(r["evals"][0] - golden("tiny_eigs.txt")[: w.n_eig]).max() < 1e-6
+    assert r["resid"].max() <= 1e-7
+    X = r["evecs"][0]
+    G = (X.conj() @ X.T).cpu().numpy()
+    assert np.abs(G - np.eye(w.n_eig)).max() < 1e-9
+    ctx.close()
 
 
 @pytest.mark.parametrize("prec,bar", [("fp64", 1e-8), ("mixed", 1e-6)])

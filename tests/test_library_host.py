@@ -120,9 +120,12 @@ def test_options_set_get_and_reject(lib):
     ctx = hw.Context(device=-1)
     assert ctx.get_option(hw.HW_OPT_RR_METHOD) == 0
     assert ctx.get_option(hw.HW_OPT_RR_FALLBACKS) == 0
+    assert ctx.get_option(hw.HW_OPT_LOWP_SWITCH) == 4
+    ctx.set_option(hw.HW_OPT_LOWP_SWITCH, 0)
+    assert ctx.get_option(hw.HW_OPT_LOWP_SWITCH) == 0
     ctx.set_option(hw.HW_OPT_RR_METHOD, 1)
     assert ctx.get_option(hw.HW_OPT_RR_METHOD) == 1
-    for opt, val in ((hw.HW_OPT_RR_METHOD, 2), (hw.HW_OPT_RR_FALLBACKS, 0), (99, 0)):
+    for opt, val in ((hw.HW_OPT_RR_METHOD, 2), (hw.HW_OPT_RR_FALLBACKS, 0), (hw.HW_OPT_LOWP_SWITCH, 13), (99, 0)):
         with pytest.raises(hw.HwError) as e:
             ctx.set_option(opt, val)
         assert e.value.status == hw.HW_EINVAL
