@@ -62,35 +62,50 @@ __global__ void k_hermitize(double2* A, int n, int64_t sA) {
 // ---------------------------------------------------------------------- Cholesky
 constexpr int CHOL_THREADS = 1024;
 
+template <typename T> struct Cx;
+template <> struct Cx<double> { using t = double2; };
+template <> struct Cx<float> { using t = float2; };
+
 // lower Cholesky in place (upper triangle zeroed); fail[b] = 1 + column of a bad pivot.
 // Right-looking; the trailing update gives each warp whole columns k (lanes over rows i >= k),
-// so only the lower triangle is touched and shared-memory reads are contiguous.
-__global__ void __launch_bounds__(CHOL_THREADS) k_chol(double2* G, int n, int64_t sG, int* fail,
-                                                       int use_smem) {
+// so only the lower triangle is touched and shared-memory reads are contiguous.  T is the
+// arithmetic type (G stays FP64 in memory); the FP32 variant serves the FP32-product phase.
+template <typename T>
+__global__ void __launch_bounds__(CHOL_THREADS) k_chol(double2* G, int n, int64_t sG, int* fail, int use_smem) {
+  using C = typename Cx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   double2* g = G + (size_t)b * sG;
-  double2* a = use_smem ? reinterpret_cast<double2*>(smem_raw) : g;
+  C* a = use_smem ? reinterpret_cast<C*>(smem_raw) : reinterpret_cast<C*>(g);   // global only for T = double
   __shared__ int bad;
+  __shared__ T piv[2];   // sqrt of the pivot and its reciprocal (one thread computes them)
   if (threadIdx.x == 0) bad = 0;
   if (use_smem)
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) a[t] = g[t];
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+      const double2 x = g[t];
+      a[t].x = (T)x.x;
+      a[t].y = (T)x.y;
+    }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
-    const double d = a[j + (size_t)j * n].x;
-    if (!(d > 0.0) || !isfinite(d)) {
-      if (threadIdx.x == 0) bad = j + 1;
-      __syncthreads();
-      break;
+    if (threadIdx.x == 0) {
+      const T d = a[j + (size_t)j * n].x;
+      if (!(d > (T)0) || !isfinite(d)) {
+        bad = j + 1;
+      } else {
+        piv[0] = sqrt(d);
+        piv[1] = (T)1 / piv[0];
+      }
     }
-    const double s = sqrt(d), inv = 1.0 / s;
     __syncthreads();
+    if (bad) break;
+    const T s = piv[0], inv = piv[1];
     for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
-      double2 v = a[i + (size_t)j * n];
+      C v = a[i + (size_t)j * n];
       if (i == j) {
         v.x = s;
-        v.y = 0.0;
+        v.y = (T)0;
       } else {
         v.x *= inv;
         v.y *= inv;
@@ -100,10 +115,10 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol(double2* G, int n, int64_
     __syncthreads();
     // trailing update: a[i][k] -= l[i][j] conj(l[k][j]) for j < k <= i
     for (int k = j + 1 + warp; k < n; k += nwarp) {
-      const double2 lk = a[k + (size_t)j * n];
+      const C lk = a[k + (size_t)j * n];
       for (int i = k + lane; i < n; i += 32) {
-        const double2 li = a[i + (size_t)j * n];
-        double2 v = a[i + (size_t)k * n];
+        const C li = a[i + (size_t)j * n];
+        C v = a[i + (size_t)k * n];
         v.x -= li.x * lk.x + li.y * lk.y;
         v.y -= li.y * lk.x - li.x * lk.y;
         a[i + (size_t)k * n] = v;
@@ -115,11 +130,11 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol(double2* G, int n, int64_
   // zero the strict upper triangle
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const int i = t % n, k = t / n;
-    if (k > i) a[t] = make_double2(0.0, 0.0);
+    if (k > i) a[t].x = a[t].y = (T)0;
   }
   __syncthreads();
   if (use_smem)
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) g[t] = a[t];
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) g[t] = make_double2((double)a[t].x, (double)a[t].y);
   if (threadIdx.x == 0) fail[b] = bad;
 }
 
@@ -490,11 +505,18 @@ cudaError_t dense_heev(DenseWork* dw, cudaStream_t st, double2* A, int n, int np
   return cudaGetLastError();
 }
 
-cudaError_t dense_chol(cudaStream_t st, double2* G, int n, int nprob, int* fail) {
+cudaError_t dense_chol(cudaStream_t st, double2* G, int n, int nprob, int* fail, bool fp32) {
+  if (fp32) {
+    const size_t bytes = (size_t)n * n * sizeof(float2);
+    if (bytes > 200 * 1024) return cudaErrorInvalidValue;
+    cudaFuncSetAttribute(k_chol<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    k_chol<float><<<nprob, CHOL_THREADS, bytes, st>>>(G, n, (int64_t)n * n, fail, 1);
+    return cudaGetLastError();
+  }
   const size_t bytes = (size_t)n * n * sizeof(double2);
   const int use_smem = bytes <= 200 * 1024;
-  if (use_smem) cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  k_chol<<<nprob, CHOL_THREADS, use_smem ? bytes : 0, st>>>(G, n, (int64_t)n * n, fail, use_smem);
+  if (use_smem) cudaFuncSetAttribute(k_chol<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  k_chol<double><<<nprob, CHOL_THREADS, use_smem ? bytes : 0, st>>>(G, n, (int64_t)n * n, fail, use_smem);
   return cudaGetLastError();
 }
 
@@ -784,8 +806,8 @@ size_t heev32_scratch_bytes(int n, int nprob, int maxsweep) {
 //   k_hh_tridiag  one CTA per problem: the matrix (shifted by the mean of its valid diagonal)
 //                 packed as a lower triangle in shared memory, reduced to Hermitian tridiagonal
 //                 form by n-2 Householder reflections in FP32; reflectors kept in global memory
-//   k_tri_eig     one thread per wanted pair: the tridiagonal made real by a diagonal phase
-//                 matrix, its j-th eigenvalue by Sturm bisection and the vector by inverse
+//   k_tri_eig     one warp per wanted pair: the tridiagonal made real by a diagonal phase
+//                 matrix, its j-th eigenvalue by Sturm multisection and the vector by inverse
 //                 iteration (FP32)
 //   k_tri_gs      one CTA per problem: Gram-Schmidt inside near-degenerate groups, phases
 //   k_hh_back     one warp per wanted vector: Z = Q D Y (reflectors applied in reverse) in FP32
@@ -809,7 +831,8 @@ struct HhArgs {
   double* lam64;       // [nprob][n stride] the same plus the shift (FP64 storage), may be null
   float* Y;            // [nprob][nw][n] eigenvectors of Tr (compacted coordinates)
   float* work;         // [nprob][nw][2n] inverse-iteration factors
-  double2* Z;          // [nprob][n][nw] output vectors (column-major n x nw), original coordinates
+  double2* Z;          // output vectors, problem b at Z + b * zstride (column-major n x nw), original
+  int64_t zstride;     // coordinates
 };
 
 constexpr int HH_THREADS = 1024;
@@ -926,11 +949,26 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
       const int i = t >> 2, part = t & 3;
       float pr = 0.f, pi = 0.f;
       if (act) {
-        for (int j = part; j < m; j += 4) {
-          const float2 aij = tget(S, k + 1 + i, k + 1 + j);
+        const int r = k + 1 + i;
+        // j <= i: row r of the packed lower triangle (contiguous)
+        const float2* row = S + tri(r, k + 1);
+        int j = part;
+        for (; j <= i; j += 4) {
+          const float2 aij = row[j];
           const float2 vj = v[j];
           pr += aij.x * vj.x - aij.y * vj.y;
           pi += aij.x * vj.y + aij.y * vj.x;
+        }
+        // j > i: conj(A[c][r]) with c = k + 1 + j, packed index tri(c, r) advanced incrementally
+        int c = k + 1 + j;
+        int idx = tri(c, r);
+        for (; j < m; j += 4) {
+          const float2 a = S[idx];
+          const float2 vj = v[j];
+          pr += a.x * vj.x + a.y * vj.y;
+          pi += a.x * vj.y - a.y * vj.x;
+          idx += 4 * c + 10;
+          c += 4;
         }
       }
       pr += __shfl_xor_sync(0xffffffffu, pr, 1);
@@ -996,7 +1034,7 @@ __device__ __forceinline__ int sturm32(const float* dd, const float* ee2, int n,
   if (fabsf(q) < pivmin) q = -pivmin;
   if (q < 0.f) ++c;
   for (int i = 1; i < n; ++i) {
-    q = dd[i] - x - ee2[i - 1] / q;
+    q = dd[i] - x - __fdividef(ee2[i - 1], q);
     if (fabsf(q) < pivmin) q = -pivmin;
     if (q < 0.f) ++c;
   }
@@ -1016,17 +1054,20 @@ __device__ __forceinline__ void tri_bounds(const float* dd, const float* ee, int
   if (nv == 0) lo = hi = 0.f;
 }
 
-constexpr int TRI_THREADS = 32;
+constexpr int TRI_WARPS = 8;
 
-// eigenvalue j by Sturm bisection and its vector by inverse iteration, one thread per j
-// (grid (ceil(nw / 32), nprob)); padding pairs (j >= nv) take their diagonal value
-__global__ void __launch_bounds__(TRI_THREADS) k_tri_eig(HhArgs H) {
+// eigenvalue j by Sturm multisection (the 32 lanes of warp j test 32 interior points of the
+// bracket, which shrinks 33-fold per round) and its vector by inverse iteration (lane 0 runs
+// the recurrences with reciprocal pivots, the warp normalises); grid (ceil(nw / 8), nprob).
+// Padding pairs (j >= nv) take their diagonal value.
+__global__ void __launch_bounds__(32 * TRI_WARPS) k_tri_eig(HhArgs H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = H.n, nw = H.nw, b = blockIdx.y;
   const int nv = H.nv[b];
   float* dd = reinterpret_cast<float*>(smem_raw);   // [n]
   float* ee = dd + n;                               // [n] |e|
   float* ee2 = ee + n;                              // [n] |e|^2
+  __shared__ float bnd[2];
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
     dd[i] = H.d[(size_t)b * n + i];
     const float2 e = i < nv - 1 ? H.e[(size_t)b * n + i] : make_float2(0.f, 0.f);
@@ -1034,50 +1075,79 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tri_eig(HhArgs H) {
     ee2[i] = e.x * e.x + e.y * e.y;
   }
   __syncthreads();
-  float lo, hi;
-  tri_bounds(dd, ee, nv, lo, hi);
+  if (threadIdx.x == 0) tri_bounds(dd, ee, nv, bnd[0], bnd[1]);
+  __syncthreads();
+  const float lo = bnd[0], hi = bnd[1];
   const float scale = fmaxf(fmaxf(fabsf(lo), fabsf(hi)), 1e-6f);
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * TRI_WARPS + warp;
   if (j >= nw) return;
   if (j >= nv) {
-    const int src = H.map[(size_t)b * n + j];
-    const double x = H.A[(size_t)b * n * n + src + (size_t)src * n].x;
-    H.lam[(size_t)b * nw + j] = (float)(x - H.shift[b]);
-    if (H.lam64) H.lam64[(size_t)b * n + j] = x;
+    if (lane == 0) {
+      const int src = H.map[(size_t)b * n + j];
+      const double x = H.A[(size_t)b * n * n + src + (size_t)src * n].x;
+      H.lam[(size_t)b * nw + j] = (float)(x - H.shift[b]);
+      if (H.lam64) H.lam64[(size_t)b * n + j] = x;
+    }
     return;
   }
   float a0 = lo, b0 = hi;
-  for (int it = 0; it < 64 && b0 - a0 > 2e-7f * scale; ++it) {
-    const float mid = 0.5f * (a0 + b0);
-    if (sturm32(dd, ee2, nv, mid, 1e-30f) > j) b0 = mid;
-    else a0 = mid;
+  for (int round = 0; round < 12 && b0 - a0 > 2e-7f * scale; ++round) {
+    const float h = (b0 - a0) * (1.0f / 33.0f);
+    const int cnt = sturm32(dd, ee2, nv, a0 + h * (float)(lane + 1), 1e-30f);
+    const unsigned above = __ballot_sync(0xffffffffu, cnt > j);
+    const int first = above ? __ffs(above) - 1 : 32;   // first test point with more than j below it
+    const float na = first > 0 ? a0 + h * (float)first : a0;
+    const float nb = first < 32 ? a0 + h * (float)(first + 1) : b0;
+    a0 = na;
+    b0 = nb;
   }
   const float lamj = 0.5f * (a0 + b0);
-  H.lam[(size_t)b * nw + j] = lamj;
-  if (H.lam64) H.lam64[(size_t)b * n + j] = (double)lamj + H.shift[b];
-  // inverse iteration (LU without pivoting, guarded pivots)
-  float* y = H.Y + ((size_t)b * nw + j) * n;
-  float* u = H.work + ((size_t)b * nw + j) * 2 * n;   // u (pivots), l (multipliers)
-  float* l = u + n;
+  float* __restrict__ y = H.Y + ((size_t)b * nw + j) * n;
+  for (int i = lane; i < nv; i += 32) y[i] = hash_unit(b, j, i, 0);
+  if (lane == 0) {
+    H.lam[(size_t)b * nw + j] = lamj;
+    if (H.lam64) H.lam64[(size_t)b * n + j] = (double)lamj + H.shift[b];
+  }
+  float* __restrict__ ru = H.work + ((size_t)b * nw + j) * 2 * n;   // reciprocal pivots
+  float* __restrict__ l = ru + n;                                   // multipliers
   const float guard = 1e-7f * scale;
   // perturb the shift slightly so equal eigenvalues give different vectors
   const float sh = lamj + (float)(j % 7) * 1e-7f * scale;
-  u[0] = dd[0] - sh;
-  if (fabsf(u[0]) < guard) u[0] = guard;
-  for (int i = 1; i < nv; ++i) {
-    l[i] = ee[i - 1] / u[i - 1];
-    u[i] = dd[i] - sh - l[i] * ee[i - 1];
-    if (fabsf(u[i]) < guard) u[i] = copysignf(guard, u[i] == 0.f ? 1.f : u[i]);
+  if (lane == 0) {
+    float up = dd[0] - sh;
+    if (fabsf(up) < guard) up = guard;
+    ru[0] = 1.0f / up;
+    for (int i = 1; i < nv; ++i) {
+      const float li = ee[i - 1] * ru[i - 1];
+      l[i] = li;
+      up = dd[i] - sh - li * ee[i - 1];
+      if (fabsf(up) < guard) up = copysignf(guard, up == 0.f ? 1.f : up);
+      ru[i] = 1.0f / up;
+    }
   }
-  for (int i = 0; i < nv; ++i) y[i] = hash_unit(b, j, i, 0);
+  __syncwarp();
   for (int it = 0; it < 3; ++it) {
-    for (int i = 1; i < nv; ++i) y[i] -= l[i] * y[i - 1];
-    y[nv - 1] /= u[nv - 1];
-    for (int i = nv - 2; i >= 0; --i) y[i] = (y[i] - ee[i] * y[i + 1]) / u[i];
+    if (lane == 0) {
+      float prev = y[0];
+      for (int i = 1; i < nv; ++i) {
+        prev = y[i] - l[i] * prev;
+        y[i] = prev;
+      }
+      float nxt = y[nv - 1] * ru[nv - 1];
+      y[nv - 1] = nxt;
+      for (int i = nv - 2; i >= 0; --i) {
+        nxt = (y[i] - ee[i] * nxt) * ru[i];
+        y[i] = nxt;
+      }
+    }
+    __syncwarp();
     float s = 0.f;
-    for (int i = 0; i < nv; ++i) s += y[i] * y[i];
+    for (int i = lane; i < nv; i += 32) s += y[i] * y[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     s = rsqrtf(fmaxf(s, 1e-30f));
-    for (int i = 0; i < nv; ++i) y[i] *= s;
+    for (int i = lane; i < nv; i += 32) y[i] *= s;
+    __syncwarp();
   }
 }
 
@@ -1161,7 +1231,7 @@ __global__ void __launch_bounds__(256) k_hh_back(HhArgs H) {
   if (j >= nw) return;
   const int nv = H.nv[b];
   const int* mp = H.map + (size_t)b * n;
-  double2* z = H.Z + (size_t)b * n * nw + (size_t)j * n;
+  double2* z = H.Z + (size_t)b * H.zstride + (size_t)j * n;
   if (j >= nv) {
     const int src = mp[j];
     for (int i = lane; i < n; i += 32) z[i] = make_double2(i == src ? 1.0 : 0.0, 0.0);
@@ -1232,10 +1302,11 @@ size_t hh_scratch_bytes(int n, int nw, int nprob) {
   return (size_t)nprob * per + 16 * 256 + 4096;
 }
 
-// FP32 stage: Z (FP64 storage, [nprob][n x nw]) holds approximate eigenvectors of the lowest nw
-// eigenvalues of each A (read only), lam64 their eigenvalues (shift added back).
+// FP32 stage: Z (FP64 storage, problem b at Z + b * zstride, n x nw) holds approximate
+// eigenvectors of the lowest nw eigenvalues of each A (read only), lam64 their eigenvalues
+// (shift added back, stride n).
 cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, int nprob, double2* Z,
-                            void* scratch, size_t scratch_bytes, double* lam64) {
+                            int64_t zstride, void* scratch, size_t scratch_bytes, double* lam64) {
   if (n > 32 * HB_PER || hh_smem(n) > 226 * 1024 || nw > n || nw < 1) return cudaErrorInvalidValue;
   if (hh_scratch_bytes(n, nw, nprob) > scratch_bytes) return cudaErrorInvalidValue;
   unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
@@ -1260,10 +1331,11 @@ cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, in
   H.Y = (float*)take((size_t)nprob * nw * n * sizeof(float));
   H.work = (float*)take((size_t)nprob * nw * 2 * n * sizeof(float));
   H.Z = Z;
+  H.zstride = zstride;
   H.lam64 = lam64;
   cudaFuncSetAttribute(k_hh_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hh_smem(n));
   k_hh_tridiag<<<nprob, HH_THREADS, hh_smem(n), st>>>(H);
-  k_tri_eig<<<dim3((nw + TRI_THREADS - 1) / TRI_THREADS, nprob), TRI_THREADS, 3 * n * sizeof(float), st>>>(H);
+  k_tri_eig<<<dim3((nw + TRI_WARPS - 1) / TRI_WARPS, nprob), 32 * TRI_WARPS, 3 * n * sizeof(float), st>>>(H);
   k_tri_gs<<<nprob, 256, 0, st>>>(H);
   k_hh_back<<<dim3((nw + 7) / 8, nprob), 256, 0, st>>>(H);
   return cudaGetLastError();
@@ -1310,22 +1382,39 @@ __global__ void k_oa_correction(const double2* R, const double2* S, int n, int n
 // gap is below 1e-8 (1 + |lambda|) form a group, diagonalised exactly by a serial FP64 Jacobi
 // (one thread per group, groups of up to 16); couplings between groups get the first-order
 // rotation S_ij / (lambda_j - lambda_i), unitary to O(1e-14).
-__device__ __forceinline__ bool strong_link(const double2* s, int nw, int j, int k) {
-  const double dj = s[j + (size_t)j * nw].x, dk = s[k + (size_t)k * nw].x;
-  const double2 c = s[j + (size_t)k * nw];
-  const double ac = sqrt(c.x * c.x + c.y * c.y);
-  const double gap = fabs(dk - dj);
-  return gap < 1e-8 * (1.0 + fabs(dj) + fabs(dk)) || ac > 1e-7 * gap;
-}
 
 // grp[j] = 1 joins j and j+1: some vector at or before j couples strongly to one after j
+// (pairs at most 15 apart).  The strong-link bits of all such pairs are formed first, from
+// the diagonal in shared memory.  grid nprob, dynamic smem nw doubles + nw 16-bit masks
 __global__ void k_group_links(const double2* S, int nw, int* grp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* dg = reinterpret_cast<double*>(smem_raw);
+  unsigned short* lk = reinterpret_cast<unsigned short*>(dg + nw);   // bit d-1: a links to a+d
   const int b = blockIdx.x;
   const double2* s = S + (size_t)b * nw * nw;
   for (int j = threadIdx.x; j < nw; j += blockDim.x) {
+    dg[j] = s[j + (size_t)j * nw].x;
+    lk[j] = 0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nw * 15; t += blockDim.x) {
+    const int a = t / 15, d = t % 15 + 1, k = a + d;
+    if (k >= nw) continue;
+    const double dj = dg[a], dk = dg[k];
+    const double2 c = s[a + (size_t)k * nw];
+    const double gap = fabs(dk - dj);
+    if (gap < 1e-8 * (1.0 + fabs(dj) + fabs(dk)) || sqrt(c.x * c.x + c.y * c.y) > 1e-7 * gap)
+      atomicOr(reinterpret_cast<unsigned int*>(lk + (a & ~1)), 1u << (d - 1 + 16 * (a & 1)));
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nw; j += blockDim.x) {
     int link = 0;
-    for (int a = max(0, j - 15); a <= j && !link; ++a)
-      for (int k = j + 1; k < nw && k <= a + 15 && !link; ++k) link = strong_link(s, nw, a, k);
+    for (int a = max(0, j - 14); a <= j && !link; ++a) {
+      // a links to some k with j < k <= a + 15
+      const unsigned int bits = lk[a];
+      const int dmin = j + 1 - a;   // k = a + d > j
+      link = (bits >> (dmin - 1)) != 0;
+    }
     grp[(size_t)b * nw + j] = link;
   }
 }
@@ -1469,7 +1558,7 @@ __global__ void k_sort_wanted(const double* lam_in, int lstride, const double2* 
 // group links and exact group rotations: Ug (identity outside groups), lam (unsorted)
 cudaError_t launch_group_rr(cudaStream_t st, const double2* Sw, int nw, int nprob, int* grp, double* lam,
                             int lstride, double2* Ug) {
-  k_group_links<<<nprob, 128, 0, st>>>(Sw, nw, grp);
+  k_group_links<<<nprob, 256, nw * sizeof(double) + ((nw + 1) / 2) * 4 + 16, st>>>(Sw, nw, grp);
   k_group_rr<<<nprob, 64, 0, st>>>(Sw, nw, grp, lam, lstride, Ug);
   return cudaGetLastError();
 }
@@ -1490,34 +1579,38 @@ __global__ void k_add_identity(double2* E, int nw) {
 }  // namespace hw
 
 // ===================================================================== Cholesky-QR apply
-// W <- W (L^H)^{-1} for each k-point: row w of W solves y L^H = w, i.e.
+// W <- W (L^H)^{-1} for each k-point (skipped where skip[b] != 0): row w of W solves y L^H = w, i.e.
 // y_j = (w_j - sum_{i<j} conj(L_ji) y_i) / L_jj, in place.  Eight lanes share one row: lane q
 // keeps the columns j = q (mod 8) in registers; at step j the owner finishes y_j and
 // broadcasts it, and every lane subtracts conj(L_kj) y_j from its columns k > j (right-looking
-// order, same arithmetic).  L (m x m, lower, from k_chol) is staged in shared memory with the
-// reciprocal diagonal.  W: rows x m block with leading dimension ld, batch stride sW.
+// order, same arithmetic).  L (m x m, lower, from k_chol) is read through the L1 cache, the
+// reciprocal diagonal from shared memory.  W: rows x m block with leading dimension ld, batch
+// stride sW.
 namespace hw {
-template <int NPER>
-__global__ void __launch_bounds__(256) k_trsm_lh(const double2* L, int m, double2* W, int64_t rows, int64_t ld,
-                                                 int64_t sW) {
+constexpr int TRSM_THREADS = 32;   // 4 rows per block: many blocks per SM, even balance
+
+template <typename T, int NPER>
+__global__ void __launch_bounds__(TRSM_THREADS) k_trsm_lh(const double2* __restrict__ L, int m, double2* W,
+                                                          int64_t rows, int64_t ld, int64_t sW, const int* skip) {
+  using C = typename Cx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* Ls = reinterpret_cast<double2*>(smem_raw);
-  double* dinv = reinterpret_cast<double*>(Ls + (size_t)m * m);
+  T* dinv = reinterpret_cast<T*>(smem_raw);
   const int b = blockIdx.y;
+  if (skip && skip[b]) return;   // failed factorisation: W left as it was
   const double2* l = L + (size_t)b * m * m;
-  for (int t = threadIdx.x; t < m * m; t += blockDim.x) Ls[t] = l[t];
-  __syncthreads();
-  for (int j = threadIdx.x; j < m; j += blockDim.x) dinv[j] = 1.0 / Ls[j + (size_t)j * m].x;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) dinv[j] = (T)1 / (T)l[j + (size_t)j * m].x;
   __syncthreads();
   const int q = threadIdx.x & 7;
-  const int64_t r = (int64_t)blockIdx.x * 32 + (threadIdx.x >> 3);
+  const int64_t r = (int64_t)blockIdx.x * (TRSM_THREADS / 8) + (threadIdx.x >> 3);
   const bool valid = r < rows;
   double2* w = W + (size_t)b * sW + (valid ? r : 0);
-  double2 acc[NPER];
+  C acc[NPER];
 #pragma unroll
   for (int c = 0; c < NPER; ++c) {
     const int j = q + 8 * c;
-    acc[c] = (valid && j < m) ? w[(size_t)j * ld] : make_double2(0.0, 0.0);
+    const double2 x = (valid && j < m) ? w[(size_t)j * ld] : make_double2(0.0, 0.0);
+    acc[c].x = (T)x.x;
+    acc[c].y = (T)x.y;
   }
 #pragma unroll
   for (int cb = 0; cb < NPER; ++cb) {
@@ -1525,12 +1618,13 @@ __global__ void __launch_bounds__(256) k_trsm_lh(const double2* L, int m, double
     for (int o = 0; o < 8; ++o) {
       const int j = 8 * cb + o;
       if (j < m) {
-        double yx = 0.0, yy = 0.0;
+        T yx = (T)0, yy = (T)0;
         if (q == o) {
-          const double di = dinv[j];
+          const T di = dinv[j];
           yx = acc[cb].x * di;
           yy = acc[cb].y * di;
-          acc[cb] = make_double2(yx, yy);
+          acc[cb].x = yx;
+          acc[cb].y = yy;
         }
         yx = __shfl_sync(0xffffffffu, yx, o, 8);
         yy = __shfl_sync(0xffffffffu, yy, o, 8);
@@ -1538,9 +1632,10 @@ __global__ void __launch_bounds__(256) k_trsm_lh(const double2* L, int m, double
         for (int c = cb; c < NPER; ++c) {
           const int k = q + 8 * c;
           if (k > j && k < m) {
-            const double2 lkj = Ls[k + (size_t)j * m];   // L[k][j]; acc -= conj(lkj) y
-            acc[c].x -= lkj.x * yx + lkj.y * yy;
-            acc[c].y -= lkj.x * yy - lkj.y * yx;
+            const double2 lkj = __ldg(l + k + (size_t)j * m);   // L[k][j]; acc -= conj(lkj) y
+            const T lx = (T)lkj.x, ly = (T)lkj.y;
+            acc[c].x -= lx * yx + ly * yy;
+            acc[c].y -= lx * yy - ly * yx;
           }
         }
       }
@@ -1550,30 +1645,37 @@ __global__ void __launch_bounds__(256) k_trsm_lh(const double2* L, int m, double
 #pragma unroll
     for (int c = 0; c < NPER; ++c) {
       const int j = q + 8 * c;
-      if (j < m) w[(size_t)j * ld] = acc[c];
+      if (j < m) w[(size_t)j * ld] = make_double2((double)acc[c].x, (double)acc[c].y);
     }
   }
 }
 
-template <int NPER>
+template <typename T, int NPER>
 static cudaError_t trsm_launch(cudaStream_t st, const double2* L, int m, int nprob, double2* W, int64_t rows,
-                               int64_t ld, int64_t sW, size_t smem) {
-  cudaFuncSetAttribute(k_trsm_lh<NPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  k_trsm_lh<NPER><<<dim3((unsigned)((rows + 31) / 32), nprob), 256, smem, st>>>(L, m, W, rows, ld, sW);
+                               int64_t ld, int64_t sW, const int* skip) {
+  const int rpb = TRSM_THREADS / 8;
+  k_trsm_lh<T, NPER><<<dim3((unsigned)((rows + rpb - 1) / rpb), nprob), TRSM_THREADS, m * sizeof(T), st>>>(
+      L, m, W, rows, ld, sW, skip);
   return cudaGetLastError();
 }
 
-cudaError_t dense_trsm_lh(cudaStream_t st, const double2* L, int m, int nprob, double2* W, int64_t rows, int64_t ld,
-                          int64_t sW) {
-  const size_t smem = (size_t)m * m * sizeof(double2) + (size_t)m * sizeof(double);
-  if (m > 120 || smem > 220 * 1024) return cudaErrorInvalidValue;
-  if (rows <= 0) return cudaSuccess;
+template <typename T>
+static cudaError_t trsm_dispatch(cudaStream_t st, const double2* L, int m, int nprob, double2* W, int64_t rows,
+                                 int64_t ld, int64_t sW, const int* skip) {
   const int nper = (m + 7) / 8;
-  if (nper <= 2) return trsm_launch<2>(st, L, m, nprob, W, rows, ld, sW, smem);
-  if (nper <= 4) return trsm_launch<4>(st, L, m, nprob, W, rows, ld, sW, smem);
-  if (nper <= 6) return trsm_launch<6>(st, L, m, nprob, W, rows, ld, sW, smem);
-  if (nper <= 9) return trsm_launch<9>(st, L, m, nprob, W, rows, ld, sW, smem);
-  if (nper <= 12) return trsm_launch<12>(st, L, m, nprob, W, rows, ld, sW, smem);
-  return trsm_launch<15>(st, L, m, nprob, W, rows, ld, sW, smem);
+  if (nper <= 2) return trsm_launch<T, 2>(st, L, m, nprob, W, rows, ld, sW, skip);
+  if (nper <= 4) return trsm_launch<T, 4>(st, L, m, nprob, W, rows, ld, sW, skip);
+  if (nper <= 6) return trsm_launch<T, 6>(st, L, m, nprob, W, rows, ld, sW, skip);
+  if (nper <= 9) return trsm_launch<T, 9>(st, L, m, nprob, W, rows, ld, sW, skip);
+  if (nper <= 12) return trsm_launch<T, 12>(st, L, m, nprob, W, rows, ld, sW, skip);
+  return trsm_launch<T, 15>(st, L, m, nprob, W, rows, ld, sW, skip);
+}
+
+cudaError_t dense_trsm_lh(cudaStream_t st, const double2* L, int m, int nprob, double2* W, int64_t rows, int64_t ld,
+                          int64_t sW, bool fp32, const int* skip) {
+  if (m > 120) return cudaErrorInvalidValue;
+  if (rows <= 0) return cudaSuccess;
+  return fp32 ? trsm_dispatch<float>(st, L, m, nprob, W, rows, ld, sW, skip)
+              : trsm_dispatch<double>(st, L, m, nprob, W, rows, ld, sW, skip);
 }
 }  // namespace hw

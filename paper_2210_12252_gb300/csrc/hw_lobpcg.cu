@@ -36,7 +36,7 @@ cudaError_t dense_alloc(DenseWork*& dw, size_t cap_elems, int maxnprob);
 void dense_free(DenseWork*& dw);
 cudaError_t dense_heev(DenseWork* dw, cudaStream_t st, double2* A, int n, int nprob, double* w,
                        double2* Z, int* status, double tol);
-cudaError_t dense_chol(cudaStream_t st, double2* G, int n, int nprob, int* fail);
+cudaError_t dense_chol(cudaStream_t st, double2* G, int n, int nprob, int* fail, bool fp32 = false);
 cudaError_t dense_trinv(cudaStream_t st, const double2* L, double2* Ui, int n, int nprob);
 cudaError_t dense_hermitize(cudaStream_t st, double2* A, int n, int nprob);
 cudaError_t dense_heev32(cudaStream_t st, const double2* A, int n, int nprob, double* w, double2* Z,
@@ -45,9 +45,9 @@ size_t heev32_scratch_bytes(int n, int nprob, int maxsweep);
 size_t jac32_smem(int n);
 size_t hh_smem(int n);
 cudaError_t dense_trsm_lh(cudaStream_t st, const double2* L, int m, int nprob, double2* W, int64_t rows, int64_t ld,
-                          int64_t sW);
+                          int64_t sW, bool fp32 = false, const int* skip = nullptr);
 size_t hh_scratch_bytes(int n, int nw, int nprob);
-cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, int nprob, double2* Z,
+cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, int nprob, double2* Z, int64_t zstride,
                             void* scratch, size_t scratch_bytes, double* lam64);
 cudaError_t launch_oa_correction(cudaStream_t st, const double2* R, const double2* S, int n, int nw, int nprob,
                                  const double* lamall, double2* E);
@@ -221,8 +221,8 @@ __global__ void k_rq_diag(const double2* Z, const double2* T, int n, int64_t sZ,
 }
 
 // check of the Householder route's wanted block: fail[b] = 1 when an entry of Z_w^H Z_w - I
-// (G, m x m) exceeds 1e-9 in modulus or an eigenvalue is not finite; grid nk
-__global__ void k_check_gram(const double2* G, int m, const double* w, int wstride, int* fail) {
+// (G, m x m) exceeds tol in modulus or an eigenvalue is not finite; grid nk
+__global__ void k_check_gram(const double2* G, int m, const double* w, int wstride, double tol, int* fail) {
   __shared__ int bad;
   const int b = blockIdx.x;
   if (threadIdx.x == 0) bad = 0;
@@ -232,7 +232,7 @@ __global__ void k_check_gram(const double2* G, int m, const double* w, int wstri
     const int i = t % m, j = t / m;
     const double2 g = G[(size_t)b * m * m + t];
     const double dx = g.x - (i == j ? 1.0 : 0.0);
-    if (!(dx * dx + g.y * g.y < 1e-18)) mine = 1;
+    if (!(dx * dx + g.y * g.y < tol * tol)) mine = 1;
   }
   for (int j = threadIdx.x; j < m; j += blockDim.x)
     if (!isfinite(w[(size_t)b * wstride + j])) mine = 1;
@@ -300,15 +300,13 @@ __global__ void k_cvt_f2d(const float2* __restrict__ src, int rows, int cols, do
   }
 }
 
-// Batched complex GEMM on the context's cuBLAS handle.  With `lowp` set, products that run
-// over the basis dimension (m or k equal to bigdim) are computed in complex FP32 on converted
-// copies of the operands (the early, large-residual iterations of the mixed form); the rest
-// stay FP64.
+// Batched complex GEMM on the context's cuBLAS handle.  With `lowp` set (the early,
+// large-residual iterations of the mixed form) products are computed in complex FP32 on
+// converted copies of the operands; otherwise in FP64.
 struct Gemm {
   hw_ctx* ctx;
   cublasStatus_t st = CUBLAS_STATUS_SUCCESS;
   bool lowp = false;
-  int64_t bigdim = -1;
   float2* a32 = nullptr;
   float2* b32 = nullptr;
   float2* c32 = nullptr;
@@ -329,7 +327,7 @@ struct Gemm {
     ProfScope ps(ctx, HW_PH_GEMM);
     const int ra = ta == CUBLAS_OP_N ? m : k, ca = ta == CUBLAS_OP_N ? k : m;
     const int rb = tb == CUBLAS_OP_N ? k : n, cb = tb == CUBLAS_OP_N ? n : k;
-    if (lowp && k > 0 && (m == bigdim || k == bigdim) && (size_t)ra * ca * batch <= cap_ab &&
+    if (lowp && k >= 16 && (size_t)ra * ca * batch <= cap_ab &&
         (size_t)rb * cb * batch <= cap_ab && (size_t)m * n * batch <= cap_c) {
       cvt_in(A, lda, ra, ca, sA, a32, batch);
       const bool same = A == B && lda == ldb && sA == sB && ra == rb && ca == cb;
@@ -366,27 +364,39 @@ static hw_status cholqr(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, double2* S, int 
   double2* Wb = S + (size_t)c0 * Lpad;
   failed.assign(nk, 0);
   for (int pass = 0; pass < passes; ++pass) {
-    gemm(CUBLAS_OP_C, CUBLAS_OP_N, ncol, ncol, (int)Lpad, 1.0, Wb, Lpad, sK, Wb, Lpad, sK, 0.0, w->G, ncol,
-         (int64_t)ncol * ncol, nk);
-    {
-      ProfScope ps_(ctx, HW_PH_OTHER);
-      k_pad_gram<<<dim3(8, nk), 256, 0, ctx->stream>>>(w->G, ncol, d_nv);
-      ctx->launches++;
+    // FP32 factor in the FP32-product phase; a k-point whose FP32 factorisation fails keeps its
+    // block untouched and is factored again in FP64
+    for (int attempt = gemm.lowp ? 0 : 1; attempt < 2; ++attempt) {
+      const bool fp32 = attempt == 0;
+      const bool keep = gemm.lowp;
+      gemm.lowp = fp32;
+      gemm(CUBLAS_OP_C, CUBLAS_OP_N, ncol, ncol, (int)Lpad, 1.0, Wb, Lpad, sK, Wb, Lpad, sK, 0.0, w->G, ncol,
+           (int64_t)ncol * ncol, nk);
+      gemm.lowp = keep;
+      {
+        ProfScope ps_(ctx, HW_PH_OTHER);
+        k_pad_gram<<<dim3(8, nk), 256, 0, ctx->stream>>>(w->G, ncol, d_nv);
+        ctx->launches++;
+      }
+      {
+        ProfScope ps_(ctx, HW_PH_CHOL);
+        dense_hermitize(ctx->stream, w->G, ncol, nk);
+        dense_chol(ctx->stream, w->G, ncol, nk, w->fail, fp32);
+        const cudaError_t te = dense_trsm_lh(ctx->stream, w->G, ncol, nk, Wb, Lpad, Lpad, sK, fp32, w->fail);
+        if (te != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("cholqr: ") + cudaGetErrorString(te));
+        ctx->launches += 3;
+      }
+      std::vector<int> f(nk);
+      cudaMemcpyAsync(f.data(), w->fail, nk * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+      cudaError_t e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("cholqr: ") + cudaGetErrorString(e));
+      bool anyf = false;
+      for (int b = 0; b < nk; ++b) anyf = anyf || f[b];
+      if (!anyf) break;
+      if (!fp32)
+        for (int b = 0; b < nk; ++b)
+          if (f[b]) failed[b] = 1;
     }
-    {
-      ProfScope ps_(ctx, HW_PH_CHOL);
-      dense_hermitize(ctx->stream, w->G, ncol, nk);
-      dense_chol(ctx->stream, w->G, ncol, nk, w->fail);
-      const cudaError_t te = dense_trsm_lh(ctx->stream, w->G, ncol, nk, Wb, Lpad, Lpad, sK);   // W <- W L^{-H}
-      if (te != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("cholqr: ") + cudaGetErrorString(te));
-      ctx->launches += 3;
-    }
-    std::vector<int> f(nk);
-    cudaMemcpyAsync(f.data(), w->fail, nk * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("cholqr: ") + cudaGetErrorString(e));
-    for (int b = 0; b < nk; ++b)
-      if (f[b]) failed[b] = 1;
   }
   return gemm.st == CUBLAS_STATUS_SUCCESS ? HW_OK : hw_fail(ctx, HW_ECUDA, "cuBLAS failure in Cholesky-QR");
 }
@@ -398,18 +408,32 @@ static hw_status cholqr(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, double2* S, int 
 // Householder route: FP32 tridiagonalisation, bisection, inverse iteration and back-transform
 // for all n vectors, then two FP64 first-order corrections of the wanted nb vectors against
 // all n, then FP64 Rayleigh-Ritz inside groups of near-degenerate wanted vectors.
-static cudaError_t rr_eig_hh(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int nb) {
+static cudaError_t rr_eig_hh(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int nb, bool lite) {
   cudaStream_t st = ctx->stream;
   const int nk = w->nk;
   cudaError_t e;
   {
     ProfScope ps_(ctx, HW_PH_EIG);
     dense_hermitize(st, w->A, n, nk);
-    e = dense_heev_hh32(st, w->A, n, n, nk, w->Z, w->hh, w->hh_bytes, w->w);
-    ctx->launches += 4;
+    e = dense_heev_hh32(st, w->A, n, lite ? nb : n, nk, w->Z, (int64_t)n * n, w->hh, w->hh_bytes, w->w);
+    ctx->launches += 5;
   }
   if (e != cudaSuccess) return e;
   const int64_t sZ = (int64_t)n * n, sB = (int64_t)n * nb;
+  if (lite) {
+    // FP32-product phase: the FP32 pairs, made orthonormal by two Newton-Schulz steps
+    for (int pass = 0; pass < 2; ++pass) {
+      gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, n, 1.0, w->Z, n, sZ, w->Z, n, sZ, 0.0, w->G, nb, (int64_t)nb * nb, nk);
+      {
+        ProfScope ps_(ctx, HW_PH_EIG);
+        k_ns_coef<<<dim3(8, nk), 256, 0, st>>>(w->G, nb, w->Ui);
+        ctx->launches++;
+      }
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, nb, 1.0, w->Z, n, sZ, w->Ui, nb, (int64_t)nb * nb, 0.0, w->B2, n, sB, nk);
+      cudaMemcpy2DAsync(w->Z, (size_t)sZ * 16, w->B2, (size_t)sB * 16, (size_t)sB * 16, nk, cudaMemcpyDeviceToDevice, st);
+    }
+    return cudaGetLastError();
+  }
   for (int it = 0; it < 2; ++it) {
     gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, n, 1.0, w->A, n, sZ, w->Z, n, sZ, 0.0, w->B1, n, sB, nk);   // A Z_w
     gemm(CUBLAS_OP_C, CUBLAS_OP_N, n, nb, n, 1.0, w->Z, n, sZ, w->B1, n, sB, 0.0, w->B2, n, sB, nk);  // Z^H A Z_w
@@ -466,7 +490,7 @@ static cudaError_t rr_eig_hh(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int 
   return cudaGetLastError();
 }
 
-static cudaError_t rr_eig(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int nb, bool fp32) {
+static cudaError_t rr_eig(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int nb, bool fp32, bool lite = false) {
   cudaStream_t st = ctx->stream;
   const int nk = w->nk;
   cudaError_t e;
@@ -474,13 +498,14 @@ static cudaError_t rr_eig(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int nb,
     // the Householder route is checked (orthonormal wanted block, finite eigenvalues); a
     // problem that fails the check is solved again by the FP64 Jacobi from a saved copy
     cudaMemcpyAsync(w->Abak, w->A, (size_t)nk * n * n * 16, cudaMemcpyDeviceToDevice, st);
-    e = rr_eig_hh(ctx, w, gemm, n, nb);
+    e = rr_eig_hh(ctx, w, gemm, n, nb, lite);
     if (e != cudaSuccess) return e;
     gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, n, 1.0, w->Z, n, (int64_t)n * n, w->Z, n, (int64_t)n * n, 0.0, w->G, nb,
          (int64_t)nb * nb, nk);
     {
       ProfScope ps_(ctx, HW_PH_EIG);
-      k_check_gram<<<nk, 256, 0, st>>>(w->G, nb, w->w, n, w->fail);
+      // FP64 route: orthonormal to 1e-9; FP32-product phase: to 1e-5
+      k_check_gram<<<nk, 256, 0, st>>>(w->G, nb, w->w, n, lite ? 1e-5 : 1e-9, w->fail);
       ctx->launches++;
     }
     std::vector<int> f(nk);
@@ -690,7 +715,6 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     gemm.c32 = w->F32[2];
     gemm.cap_ab = w->f32_ab;
     gemm.cap_c = w->f32_c;
-    gemm.bigdim = Lpad;
     gemm.lowp = true;
   }
   std::vector<int64_t> Lb(nk);
@@ -753,7 +777,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       k_pad_rr<<<dim3(8, nk), 256, 0, st>>>(w->A, n, nb, 0, 0, dnv + nk, dnv + 2 * nk);
       ctx->launches++;
     }
-    cudaError_t e = rr_eig(ctx, w, gemm, n, nb, false);
+    cudaError_t e = rr_eig(ctx, w, gemm, n, nb, false, gemm.lowp);
     if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
     gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nb, 1.0, w->SB[from], Lpad, sK, w->Z, n, (int64_t)n * n, 0.0,
          w->SB[1 - from], Lpad, sK, nk);
@@ -975,7 +999,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       k_pad_rr<<<dim3(8, nk), 256, 0, st>>>(w->A, n, nb, np, na, dnv + nk, dnv + 2 * nk);
       ctx->launches++;
     }
-    e = rr_eig(ctx, w, gemm, n, nb, maxres > FP32_RR_ABOVE);
+    e = rr_eig(ctx, w, gemm, n, nb, maxres > FP32_RR_ABOVE, gemm.lowp);
     if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
     const int nxt = 1 - cur;
     double2* S2 = w->SB[nxt];
@@ -996,29 +1020,37 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, na, nb, -1.0, w->Z, n, (int64_t)n * n, w->C, nb, (int64_t)2 * nb * nb, 1.0,
            w->Y, n, (int64_t)n * na, nk);
     }
-    // small-space Cholesky-QR of Y
+    // small-space Cholesky-QR of Y (FP32 factor in the FP32-product phase, FP64 retry)
     bool pfail = false;
     for (int pass = 0; pass < 2; ++pass) {
-      gemm(CUBLAS_OP_C, CUBLAS_OP_N, na, na, n, 1.0, w->Y, n, (int64_t)n * na, w->Y, n, (int64_t)n * na, 0.0, w->G, na,
-           (int64_t)na * na, nk);
-      {
-        ProfScope ps_(ctx, HW_PH_OTHER);
-        k_pad_gram<<<dim3(8, nk), 256, 0, st>>>(w->G, na, dnv + 2 * nk);
-        ctx->launches++;
+      for (int attempt = gemm.lowp ? 0 : 1; attempt < 2; ++attempt) {
+        const bool fp32 = attempt == 0;
+        const bool keep = gemm.lowp;
+        gemm.lowp = fp32;
+        gemm(CUBLAS_OP_C, CUBLAS_OP_N, na, na, n, 1.0, w->Y, n, (int64_t)n * na, w->Y, n, (int64_t)n * na, 0.0, w->G,
+             na, (int64_t)na * na, nk);
+        gemm.lowp = keep;
+        {
+          ProfScope ps_(ctx, HW_PH_OTHER);
+          k_pad_gram<<<dim3(8, nk), 256, 0, st>>>(w->G, na, dnv + 2 * nk);
+          ctx->launches++;
+        }
+        {
+          ProfScope ps_(ctx, HW_PH_CHOL);
+          dense_hermitize(st, w->G, na, nk);
+          dense_chol(st, w->G, na, nk, w->fail, fp32);
+          const cudaError_t te = dense_trsm_lh(st, w->G, na, nk, w->Y, n, n, (int64_t)n * na, fp32, w->fail);
+          if (te != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("P basis: ") + cudaGetErrorString(te));
+          ctx->launches += 3;
+        }
+        std::vector<int> f(nk);
+        cudaMemcpyAsync(f.data(), w->fail, nk * sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        bool anyf = false;
+        for (int b = 0; b < nk; ++b) anyf = anyf || (f[b] && nav[b] > 0);
+        if (!anyf) break;
+        if (!fp32) pfail = true;
       }
-      {
-        ProfScope ps_(ctx, HW_PH_CHOL);
-        dense_hermitize(st, w->G, na, nk);
-        dense_chol(st, w->G, na, nk, w->fail);
-        const cudaError_t te = dense_trsm_lh(st, w->G, na, nk, w->Y, n, n, (int64_t)n * na);   // Y <- Y L^{-H}
-        if (te != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("P basis: ") + cudaGetErrorString(te));
-        ctx->launches += 3;
-      }
-      std::vector<int> f(nk);
-      cudaMemcpyAsync(f.data(), w->fail, nk * sizeof(int), cudaMemcpyDeviceToHost, st);
-      cudaStreamSynchronize(st);
-      for (int b = 0; b < nk; ++b)
-        if (f[b] && nav[b] > 0) pfail = true;
     }
     if (pfail) {
       np = 0;   // restart the conjugate directions everywhere
@@ -1087,7 +1119,7 @@ extern "C" hw_status hw_heev(hw_ctx* ctx, int n, int nprob, int nw, const double
   Gemm gemm{ctx};
   cudaError_t e;
   if (method == 1) {
-    e = rr_eig_hh(ctx, wk, gemm, n, nw);
+    e = rr_eig_hh(ctx, wk, gemm, n, nw, false);
   } else {
     ProfScope ps_(ctx, HW_PH_EIG);
     dense_hermitize(st, wk->A, n, nprob);
