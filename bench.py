@@ -228,8 +228,10 @@ def ours_main(args):
         flush.fill_(1.0)
         solve("mixed")
     prof = ctx.profile_read()
+    work = ctx.profile_work()
     ctx.profile(False)
     result["phases_ms"] = {k: round(v[0], 3) for k, v in prof.items() if v[1]}
+    result["phase_work"] = {k: v for k, v in work.items() if v > 0}
     result["phase_launches"] = {k: v[1] for k, v in prof.items() if v[1]}
     if args.profile:
         print(json.dumps({"profile_mixed": prof}), file=sys.stderr)
@@ -372,7 +374,9 @@ def hx_wire(hw, inputs, local, stream, flush):
 
 
 def roofline(result, w, ctx, L, nb):
-    """Roofline record of the library kernel with the largest device time in one step."""
+    """Roofline record of the library kernel (phase) with the largest device time in one
+    chosen-form step.  Algorithmic work: the library's own per-launch count for the dense
+    phases (tridiag, chol), the per-vector models below for the H X kernels."""
     peaks, src = load_peaks()
     phases = result["phases_ms"]
     mine = {k: v for k, v in phases.items() if k not in ("gemm",)}
@@ -383,16 +387,17 @@ def roofline(result, w, ctx, L, nb):
     launches = result["phase_launches"][dom]
     avg_ms = phases[dom] / launches
     rec = {"kernel": dom, "launches_per_step": launches, "avg_ms": round(avg_ms, 5),
-           "peak_source": src}
+           "share_of_step": round(phases[dom] / sum(phases.values()), 4), "peak_source": src}
+    work = result.get("phase_work", {})
+    fp32 = fp32_alu_peak_tflops(sm_mhz)
     if dom == "slab":
         # one slab launch processes (columns x N_r) slabs; mixed form runs in FP32
         hxm = result["hx"]["mixed"]["kernel_ms"]["slab"]
         cols = 64
         fl = slab_flops(w.geom, *nmr_nA) * cols * w.geom.Nr
         ach = fl / (hxm / 1e3) / 1e12
-        pk = fp32_alu_peak_tflops(sm_mhz)
-        rec.update({"bound": "alu", "achieved": round(ach, 3), "peak": round(pk, 2), "unit": "TFLOP/s",
-                    "frac": round(ach / pk, 4), "traffic": None,
+        rec.update({"bound": "alu", "achieved": round(ach, 3), "peak": round(fp32, 2), "unit": "TFLOP/s",
+                    "frac": round(ach / fp32, 4), "traffic": None,
                     "basis": "64-column H X launch, FP32 FMA peak 152x128x2 flop/clk at the sampled SM clock"})
     elif dom in ("radial_inv", "radial_fwd"):
         hxm = result["hx"]["mixed"]["kernel_ms"][dom]
@@ -401,19 +406,38 @@ def roofline(result, w, ctx, L, nb):
         pk = peaks["hbm_gbs"]
         rec.update({"bound": "hbm", "achieved": round(ach, 1), "peak": pk, "unit": "GB/s",
                     "frac": round(ach / pk, 4), "traffic": None})
-    elif dom == "eig":
-        # Jacobi: per sweep (n-1) steps x (n/2)^2 2x2-block updates (64 FP64 flop each) +
-        # n x n/2 eigenvector row updates (32 flop each)
-        n = 3 * nb
-        per_sweep = (n - 1) * ((n / 2) ** 2 * 64 + n * (n / 2) * 32)
-        rec.update({"bound": "alu", "unit": "TFLOP/s", "peak": 1.25, "traffic": None,
-                    "note": "FP64 pipe, nominal 1.25 TFLOP/s (recipe); flops per launch assume 8 sweeps at n=3*block",
-                    "achieved": round(per_sweep * 8 / (avg_ms / 1e3) / 1e12, 4)})
-        rec["frac"] = round(rec["achieved"] / rec["peak"], 4)
+    elif dom in work:
+        # dense phases: (16/3) n^3 real flop per Householder reduction, (8/3) n^3 + 4 rows n^2
+        # per Cholesky-QR factor + solve; FP32 FMA peak of the whole GPU (one CTA per k-point
+        # runs the reduction, so one k-point can use 1/152 of it)
+        ach = work[dom] / (phases[dom] / 1e3) / 1e12
+        rec.update({"bound": "alu", "achieved": round(ach, 4), "peak": round(fp32, 2), "unit": "TFLOP/s",
+                    "frac": round(ach / fp32, 6), "traffic": _traffic(dom),
+                    "flop_per_launch": round(work[dom] / launches),
+                    "basis": "FP32 FMA peak 152x128x2 flop/clk at the sampled SM clock"})
     else:
-        rec.update({"bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+        rec.update({"bound": "alu", "achieved": None, "peak": round(fp32, 2), "unit": "TFLOP/s",
                     "frac": None, "traffic": None})
     return rec
+
+
+def _traffic(phase):
+    """DRAM bytes per launch of a phase's kernel from the committed ncu summary, when the
+    summary was taken on the current kernel source (else None)."""
+    import hashlib
+    import re as _re
+    path = os.path.join(ROOT, "profiles", f"{phase}_tube_rr216.md")
+    src = os.path.join(ROOT, "paper_2210_12252_gb300", "csrc", "hw_dense.cu")
+    try:
+        txt = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        m = _re.search(r"source sha256\[:16\]: `([0-9a-f]+)`", txt)
+        t = _re.search(r"dram bytes per launch: ([0-9]+)", txt)
+        if m and t and m.group(1) == sha:
+            return int(t.group(1))
+    except OSError:
+        pass
+    return None
 
 
 def _slab_sizes(ctx):

@@ -261,12 +261,14 @@ typedef enum {
   HW_PH_SLAB = 1,         /* angular FFTs with the potential multiply (Algorithms 2, 4)     */
   HW_PH_RADIAL_FWD = 2,   /* forward radial quadrature + diagonal + scatter (Algorithm 3)   */
   HW_PH_PRECOND = 3,      /* diagonal preconditioner                                        */
-  HW_PH_GEMM = 4,         /* tall-skinny FP64 products of the eigensolver (cuBLAS ZGEMM)    */
-  HW_PH_CHOL = 5,         /* Cholesky factorisations + triangular inverses                  */
-  HW_PH_EIG = 6,          /* dense Hermitian eigensolver of the Rayleigh-Ritz step          */
+  HW_PH_GEMM = 4,         /* block products of the eigensolver (cuBLAS ZGEMM / CGEMM)       */
+  HW_PH_CHOL = 5,         /* Cholesky factorisations + triangular solves                    */
+  HW_PH_EIG = 6,          /* rest of the Rayleigh-Ritz eigensolver (eigenvalues, vectors,
+                             FP64 refinement)                                               */
   HW_PH_OTHER = 7,        /* residuals, gathers, padding                                     */
   HW_PH_MLP = 8,          /* preconditioner network (inference and training)                 */
-  HW_NPHASE = 9
+  HW_PH_TRIDIAG = 9,      /* Householder reduction of the Rayleigh-Ritz matrix (FP32)        */
+  HW_NPHASE = 10
 } hw_phase;
 
 /* Turn per-phase profiling on (enable != 0) or off; either resets the accumulators.  While on,
@@ -276,6 +278,12 @@ hw_status hw_profile(hw_ctx* ctx, int enable);
 /* Synchronize the stream and read the accumulated device milliseconds and launch counts per
  * phase (host arrays of HW_NPHASE entries; either may be NULL). */
 hw_status hw_profile_read(hw_ctx* ctx, double* ms, int64_t* count);
+
+/* Algorithmic work accumulated per phase since profiling was turned on (host array of
+ * HW_NPHASE entries): real floating-point operations of the method for HW_PH_TRIDIAG
+ * ((16/3) n^3 per n x n problem) and HW_PH_CHOL ((8/3) n^3 per factorisation plus 4 rows n^2
+ * per triangular solve of rows x n); zero for the other phases. */
+hw_status hw_profile_work(hw_ctx* ctx, double* work);
 
 /* Number of this library's own kernels launched on the context's stream since creation
  * (cuBLAS kernels are not counted). */

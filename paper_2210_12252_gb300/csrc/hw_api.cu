@@ -471,7 +471,7 @@ hw_status hw_synchronize(hw_ctx* ctx) {
 // ------------------------------------------------------------------------ profiling
 namespace hw {
 
-ProfScope::ProfScope(hw_ctx* ctx, int ph) : ctx_(ctx), ph_(ph) {
+ProfScope::ProfScope(hw_ctx* ctx, int ph, double work) : ctx_(ctx), ph_(ph), work_(work) {
   if (!ctx_ || !ctx_->prof.on) return;
   auto& p = ctx_->prof;
   if (p.pool.empty()) {
@@ -498,7 +498,7 @@ ProfScope::~ProfScope() {
     p.pool.pop_back();
   }
   cudaEventRecord(b, ctx_->stream);
-  p.pending.push_back({ph_, a_, b});
+  p.pending.push_back({ph_, a_, b, work_});
 }
 
 static void prof_collect(hw_ctx* ctx) {
@@ -508,6 +508,7 @@ static void prof_collect(hw_ctx* ctx) {
     if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
       p.ms[r.ph] += ms;
       p.cnt[r.ph] += 1;
+      p.work[r.ph] += r.work;
     }
     p.pool.push_back(r.a);
     p.pool.push_back(r.b);
@@ -527,6 +528,7 @@ hw_status hw_profile(hw_ctx* ctx, int enable) {
   for (int i = 0; i < HW_NPHASE; ++i) {
     ctx->prof.ms[i] = 0.0;
     ctx->prof.cnt[i] = 0;
+    ctx->prof.work[i] = 0.0;
   }
   ctx->prof.on = enable != 0;
   return HW_OK;
@@ -542,6 +544,16 @@ hw_status hw_profile_read(hw_ctx* ctx, double* ms, int64_t* count) {
     if (ms) ms[i] = ctx->prof.ms[i];
     if (count) count[i] = ctx->prof.cnt[i];
   }
+  return HW_OK;
+}
+
+hw_status hw_profile_work(hw_ctx* ctx, double* work) {
+  if (!ctx || !work) return HW_EINVAL;
+  if (ctx->device < 0) return hw_fail(ctx, HW_ESTATE, "host-only context has no device");
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, cudaGetErrorString(e));
+  hw::prof_collect(ctx);
+  for (int i = 0; i < HW_NPHASE; ++i) work[i] = ctx->prof.work[i];
   return HW_OK;
 }
 

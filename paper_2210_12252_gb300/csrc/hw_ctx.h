@@ -62,11 +62,13 @@ struct Prof {
   struct Rec {
     int ph;
     cudaEvent_t a, b;
+    double work;
   };
   std::vector<cudaEvent_t> pool;
   std::vector<Rec> pending;
   double ms[HW_NPHASE] = {0};
   int64_t cnt[HW_NPHASE] = {0};
+  double work[HW_NPHASE] = {0};
 };
 
 }  // namespace hw
@@ -99,11 +101,12 @@ namespace hw {
 // Records [start, end) events of one phase on the context's stream when profiling is on.
 class ProfScope {
  public:
-  ProfScope(hw_ctx* ctx, int ph);
+  ProfScope(hw_ctx* ctx, int ph, double work = 0.0);
   ~ProfScope();
  private:
   hw_ctx* ctx_;
   int ph_;
+  double work_;
   cudaEvent_t a_ = nullptr;
 };
 }  // namespace hw

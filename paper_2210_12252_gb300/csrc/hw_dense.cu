@@ -837,13 +837,15 @@ struct HhArgs {
 
 constexpr int HH_THREADS = 1024;
 
+// block-wide sum, returned to every thread (warp shuffles, one partial per warp in red)
 __device__ __forceinline__ float block_sum_f(float v, float* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  float t = 0.f;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+  const int lane = threadIdx.x & 31;
+  float t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f;
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
   return t;
 }
 
@@ -857,8 +859,6 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
   float2* p = v + n;                                                      // [n]
   int* mp = reinterpret_cast<int*>(p + n);                                // [n]
   __shared__ float red[32];
-  __shared__ float2 alpha_s;
-  __shared__ float beta_s;
   __shared__ int nv_s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const double2* a = H.A + (size_t)b * n * n;
@@ -907,23 +907,23 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
       s += x.x * x.x + x.y * x.y;
     }
     s = block_sum_f(s, red);
-    if (threadIdx.x == 0) {
+    // every thread forms the reflector scalars from the same values (no broadcast barrier)
+    float bet;
+    float2 alpha;
+    {
       const float2 x0 = S[tri(k + 1, k)];
       const float ax0 = sqrtf(x0.x * x0.x + x0.y * x0.y);
       const float tail = s - ax0 * ax0;
       if (!(tail > 1e-30f * fmaxf(s, 1e-30f)) || s == 0.f) {
-        beta_s = 0.f;             // already reduced
-        alpha_s = x0;
+        bet = 0.f;             // already reduced
+        alpha = x0;
       } else {
         const float sq = sqrtf(s);
         const float2 ph = ax0 > 0.f ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
-        alpha_s = make_float2(-ph.x * sq, -ph.y * sq);
-        beta_s = 1.0f / (sq * (sq + ax0));   // 2 / ||v||^2
+        alpha = make_float2(-ph.x * sq, -ph.y * sq);
+        bet = 1.0f / (sq * (sq + ax0));   // 2 / ||v||^2
       }
     }
-    __syncthreads();
-    const float bet = beta_s;
-    const float2 alpha = alpha_s;
     if (threadIdx.x == 0) {
       H.beta[(size_t)b * n + k] = bet;
       H.e[(size_t)b * n + k] = alpha;
@@ -1304,9 +1304,9 @@ size_t hh_scratch_bytes(int n, int nw, int nprob) {
 
 // FP32 stage: Z (FP64 storage, problem b at Z + b * zstride, n x nw) holds approximate
 // eigenvectors of the lowest nw eigenvalues of each A (read only), lam64 their eigenvalues
-// (shift added back, stride n).
+// (shift added back, stride n).  stage: 1 the reduction only, 2 the rest (same scratch), 3 both.
 cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, int nprob, double2* Z,
-                            int64_t zstride, void* scratch, size_t scratch_bytes, double* lam64) {
+                            int64_t zstride, void* scratch, size_t scratch_bytes, double* lam64, int stage) {
   if (n > 32 * HB_PER || hh_smem(n) > 226 * 1024 || nw > n || nw < 1) return cudaErrorInvalidValue;
   if (hh_scratch_bytes(n, nw, nprob) > scratch_bytes) return cudaErrorInvalidValue;
   unsigned char* p = reinterpret_cast<unsigned char*>(scratch);
@@ -1333,8 +1333,11 @@ cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, in
   H.Z = Z;
   H.zstride = zstride;
   H.lam64 = lam64;
-  cudaFuncSetAttribute(k_hh_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hh_smem(n));
-  k_hh_tridiag<<<nprob, HH_THREADS, hh_smem(n), st>>>(H);
+  if (stage & 1) {
+    cudaFuncSetAttribute(k_hh_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hh_smem(n));
+    k_hh_tridiag<<<nprob, HH_THREADS, hh_smem(n), st>>>(H);
+  }
+  if (!(stage & 2)) return cudaGetLastError();
   k_tri_eig<<<dim3((nw + TRI_WARPS - 1) / TRI_WARPS, nprob), 32 * TRI_WARPS, 3 * n * sizeof(float), st>>>(H);
   k_tri_gs<<<nprob, 256, 0, st>>>(H);
   k_hh_back<<<dim3((nw + 7) / 8, nprob), 256, 0, st>>>(H);

@@ -48,7 +48,7 @@ cudaError_t dense_trsm_lh(cudaStream_t st, const double2* L, int m, int nprob, d
                           int64_t sW, bool fp32 = false, const int* skip = nullptr);
 size_t hh_scratch_bytes(int n, int nw, int nprob);
 cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, int nprob, double2* Z, int64_t zstride,
-                            void* scratch, size_t scratch_bytes, double* lam64);
+                            void* scratch, size_t scratch_bytes, double* lam64, int stage = 3);
 cudaError_t launch_oa_correction(cudaStream_t st, const double2* R, const double2* S, int n, int nw, int nprob,
                                  const double* lamall, double2* E);
 cudaError_t launch_group_rr(cudaStream_t st, const double2* Sw, int nw, int nprob, int* grp, double* lam,
@@ -379,7 +379,8 @@ static hw_status cholqr(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, double2* S, int 
         ctx->launches++;
       }
       {
-        ProfScope ps_(ctx, HW_PH_CHOL);
+        ProfScope ps_(ctx, HW_PH_CHOL,
+                      nk * ((8.0 / 3.0) * ncol * (double)ncol * ncol + 4.0 * (double)Lpad * ncol * ncol));
         dense_hermitize(ctx->stream, w->G, ncol, nk);
         dense_chol(ctx->stream, w->G, ncol, nk, w->fail, fp32);
         const cudaError_t te = dense_trsm_lh(ctx->stream, w->G, ncol, nk, Wb, Lpad, Lpad, sK, fp32, w->fail);
@@ -415,8 +416,18 @@ static cudaError_t rr_eig_hh(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int 
   {
     ProfScope ps_(ctx, HW_PH_EIG);
     dense_hermitize(st, w->A, n, nk);
-    e = dense_heev_hh32(st, w->A, n, lite ? nb : n, nk, w->Z, (int64_t)n * n, w->hh, w->hh_bytes, w->w);
-    ctx->launches += 5;
+    ctx->launches++;
+  }
+  {
+    ProfScope ps_(ctx, HW_PH_TRIDIAG, (16.0 / 3.0) * n * (double)n * n * nk);
+    e = dense_heev_hh32(st, w->A, n, lite ? nb : n, nk, w->Z, (int64_t)n * n, w->hh, w->hh_bytes, w->w, 1);
+    ctx->launches++;
+  }
+  if (e != cudaSuccess) return e;
+  {
+    ProfScope ps_(ctx, HW_PH_EIG);
+    e = dense_heev_hh32(st, w->A, n, lite ? nb : n, nk, w->Z, (int64_t)n * n, w->hh, w->hh_bytes, w->w, 2);
+    ctx->launches += 3;
   }
   if (e != cudaSuccess) return e;
   const int64_t sZ = (int64_t)n * n, sB = (int64_t)n * nb;
@@ -1036,7 +1047,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
           ctx->launches++;
         }
         {
-          ProfScope ps_(ctx, HW_PH_CHOL);
+          ProfScope ps_(ctx, HW_PH_CHOL, nk * ((8.0 / 3.0) * na * (double)na * na + 4.0 * (double)n * na * na));
           dense_hermitize(st, w->G, na, nk);
           dense_chol(st, w->G, na, nk, w->fail, fp32);
           const cudaError_t te = dense_trsm_lh(st, w->G, na, nk, w->Y, n, n, (int64_t)n * na, fp32, w->fail);

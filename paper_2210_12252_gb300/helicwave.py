@@ -73,6 +73,7 @@ _SIGS = {
                           C.c_int]),
     "hw_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "hw_profile_read": (C.c_int, [C.c_void_p, _D, C.POINTER(C.c_int64)]),
+    "hw_profile_work": (C.c_int, [C.c_void_p, _D]),
     "hw_launch_count": (C.c_int64, [C.c_void_p]),
     "hw_set_mlp": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int64]),
     "hw_get_mlp": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int64]),
@@ -89,7 +90,7 @@ _SIGS = {
 
 MLP_NPARAM = 4673
 
-PHASES = ["radial_inv", "slab", "radial_fwd", "precond", "gemm", "chol", "eig", "other", "mlp"]
+PHASES = ["radial_inv", "slab", "radial_fwd", "precond", "gemm", "chol", "eig", "other", "mlp", "tridiag"]
 
 _lib = None
 
@@ -290,6 +291,12 @@ def hw_profile_read(h):
     return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
 
 
+def hw_profile_work(h):
+    work = np.zeros(len(PHASES))
+    _check(h, load_library().hw_profile_work(h, _dptr(work)))
+    return {p: float(work[i]) for i, p in enumerate(PHASES)}
+
+
 def hw_launch_count(h) -> int:
     return int(load_library().hw_launch_count(h))
 
@@ -481,6 +488,9 @@ class Context:
 
     def profile_read(self):
         return hw_profile_read(self.h)
+
+    def profile_work(self):
+        return hw_profile_work(self.h)
 
     def launch_count(self):
         return hw_launch_count(self.h)
