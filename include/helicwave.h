@@ -224,6 +224,16 @@ hw_status hw_solve_eigs_traced(hw_ctx* ctx, int k, int n_eig, int block, double 
 hw_status hw_heev(hw_ctx* ctx, int n, int nprob, int nw, const double* A, double* w, double* Z,
                   int method);
 
+/* Gram product of the eigensolver's mixed form (Sec. "Eigensolvers and Preconditioning": the
+ * Rayleigh-Ritz matrices S^H H S and the orthogonalisations): C_b = A_b^H B_b for nprob
+ * problems, A_b: K x m, B_b: K x n complex128 column-major device blocks (leading dimensions
+ * lda, ldb >= K; problem b at A + b*sA, B + b*sB elements), C_b: m x n (ldc >= m, stride sC).
+ * Products in FP32 (inputs rounded to nearest), accumulation in FP64 every 32 rows; chunk
+ * partials reduced in a fixed order (deterministic).  Asynchronous on the context's stream.
+ * HW_EINVAL on bad sizes (m, n <= 512, 1 <= nprob <= 64). */
+hw_status hw_gram(hw_ctx* ctx, int m, int n, int K, int nprob, const double* A, int64_t lda, int64_t sA,
+                  const double* B, int64_t ldb, int64_t sB, double* C, int64_t ldc, int64_t sC);
+
 /* Autotune the H X kernels' tile shapes for blocks of ns columns at k-point k: the slab
  * kernel's theta2 chunk and the number of columns per pass are timed (CUDA events, best of
  * 2 after a warm-up) for every candidate in FP64 and FP32 and the fastest are kept for later
@@ -239,12 +249,23 @@ typedef enum {
                                refinement when n <= 236, checked, with the FP64 Jacobi as the
                                retry), 1 FP64 Jacobi always.  Default 0. */
   HW_OPT_RR_FALLBACKS = 1,  /* read only: Householder results rejected by the check so far */
-  HW_OPT_LOWP_SWITCH = 2    /* mixed form only: the block products over the basis dimension
+  HW_OPT_LOWP_SWITCH = 2,   /* mixed form only: the block products over the basis dimension
                                (Gram matrices, projections, block updates) run in complex FP32
                                until every wanted residual is below 10^-value (or the residuals
                                stop falling: FP32 products stall near 1e-5), then in FP64 (X
                                re-orthonormalised, H X recomputed in FP64, P restarted).
-                               0 disables (FP64 throughout); 1..12; default 4. */
+                               0 disables (FP64 throughout); 1..12; default 5. */
+  HW_OPT_GRAM_KERNEL = 3,   /* mixed form, FP32-product phase only: 1 forms the products
+                               A^H B over the basis dimension with hw_gram's kernel (FP32
+                               products, FP64 accumulation every 32 rows); 0 (default) uses
+                               cuBLAS CGEMM on FP32 copies, measured faster on the tube. */
+  HW_OPT_HYBRID = 4         /* mixed form, FP64 phase: 1 keeps FP64 only for the
+                               products that involve X (its rows of the Rayleigh-Ritz matrix, its
+                               share of the X / H X updates, one projection of W and of P against
+                               X) and forms the rest of the W and P orthogonalisation, their Gram
+                               block and the P update in FP32 (residuals stall near 3e-7: for
+                               tolerances of 1e-6 and above); 0 (default) keeps every product
+                               FP64. */
 } hw_option;
 /* Set an option (HW_EINVAL for an unknown option, a read-only one or a bad value). */
 hw_status hw_set_option(hw_ctx* ctx, int option, int value);

@@ -446,6 +446,16 @@ hw_status hw_set_option(hw_ctx* ctx, int option, int value) {
     ctx->lowp_exp = value;
     return HW_OK;
   }
+  if (option == HW_OPT_GRAM_KERNEL) {
+    if (value != 0 && value != 1) return hw_fail(ctx, HW_EINVAL, "Gram kernel option 0 or 1");
+    ctx->gram_mixed = value;
+    return HW_OK;
+  }
+  if (option == HW_OPT_HYBRID) {
+    if (value != 0 && value != 1) return hw_fail(ctx, HW_EINVAL, "hybrid option 0 or 1");
+    ctx->hybrid = value;
+    return HW_OK;
+  }
   return hw_fail(ctx, HW_EINVAL, "unknown or read-only option");
 }
 
@@ -454,6 +464,8 @@ hw_status hw_get_option(hw_ctx* ctx, int option, long long* value) {
   if (option == HW_OPT_RR_METHOD) { *value = ctx->rr_method; return HW_OK; }
   if (option == HW_OPT_RR_FALLBACKS) { *value = ctx->rr_fallbacks; return HW_OK; }
   if (option == HW_OPT_LOWP_SWITCH) { *value = ctx->lowp_exp; return HW_OK; }
+  if (option == HW_OPT_GRAM_KERNEL) { *value = ctx->gram_mixed; return HW_OK; }
+  if (option == HW_OPT_HYBRID) { *value = ctx->hybrid; return HW_OK; }
   return hw_fail(ctx, HW_EINVAL, "unknown option");
 }
 

@@ -89,7 +89,9 @@ struct hw_ctx {
   int* dflag = nullptr;        // device status word for bounded waits
   int64_t launches = 0;        // kernels of this library launched on the stream
   int rr_method = 0;           // HW_OPT_RR_METHOD
-  int lowp_exp = 4;            // HW_OPT_LOWP_SWITCH
+  int lowp_exp = 5;            // HW_OPT_LOWP_SWITCH
+  int gram_mixed = 0;          // HW_OPT_GRAM_KERNEL
+  int hybrid = 0;              // HW_OPT_HYBRID
   int64_t rr_fallbacks = 0;    // Householder results rejected by the check (Jacobi used)
   hw::Prof prof;
 };

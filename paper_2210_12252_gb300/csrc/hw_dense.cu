@@ -67,9 +67,13 @@ template <> struct Cx<double> { using t = double2; };
 template <> struct Cx<float> { using t = float2; };
 
 // lower Cholesky in place (upper triangle zeroed); fail[b] = 1 + column of a bad pivot.
-// Right-looking; the trailing update gives each warp whole columns k (lanes over rows i >= k),
-// so only the lower triangle is touched and shared-memory reads are contiguous.  T is the
-// arithmetic type (G stays FP64 in memory); the FP32 variant serves the FP32-product phase.
+// Blocked right-looking with CHOL_NB-column panels, three block barriers per panel: warp 0
+// factors the diagonal block (warp-synchronous), one thread per row solves the panel below
+// it, and all warps apply the rank-CHOL_NB update to the trailing lower triangle (a warp per
+// column, lanes over rows: contiguous shared-memory reads).  T is the arithmetic type (G stays
+// FP64 in memory); the FP32 variant serves the FP32-product phase.
+constexpr int CHOL_NB = 16;
+
 template <typename T>
 __global__ void __launch_bounds__(CHOL_THREADS) k_chol(double2* G, int n, int64_t sG, int* fail, int use_smem) {
   using C = typename Cx<T>::t;
@@ -79,7 +83,7 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol(double2* G, int n, int64_
   double2* g = G + (size_t)b * sG;
   C* a = use_smem ? reinterpret_cast<C*>(smem_raw) : reinterpret_cast<C*>(g);   // global only for T = double
   __shared__ int bad;
-  __shared__ T piv[2];   // sqrt of the pivot and its reciprocal (one thread computes them)
+  __shared__ T rdiag[CHOL_NB];
   if (threadIdx.x == 0) bad = 0;
   if (use_smem)
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
@@ -88,45 +92,73 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol(double2* G, int n, int64_
       a[t].y = (T)x.y;
     }
   __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) {
-      const T d = a[j + (size_t)j * n].x;
-      if (!(d > (T)0) || !isfinite(d)) {
-        bad = j + 1;
-      } else {
-        piv[0] = sqrt(d);
-        piv[1] = (T)1 / piv[0];
+  for (int jb = 0; jb < n; jb += CHOL_NB) {
+    const int nb = min(CHOL_NB, n - jb);
+    // (1) diagonal block, warp 0
+    if (warp == 0) {
+      for (int c = 0; c < nb; ++c) {
+        const int col = jb + c;
+        T d = a[col + (size_t)col * n].x;
+        const bool ok = d > (T)0 && isfinite(d);
+        if (!ok) {
+          if (lane == 0) bad = col + 1;
+          break;   // warp-uniform
+        }
+        const T sq = sqrt(d), inv = (T)1 / sq;
+        if (lane == 0) rdiag[c] = inv;
+        if (lane == c) a[col + (size_t)col * n] = C{sq, (T)0};
+        if (lane > c && lane < nb) {
+          C v = a[jb + lane + (size_t)col * n];
+          v.x *= inv;
+          v.y *= inv;
+          a[jb + lane + (size_t)col * n] = v;
+        }
+        __syncwarp();
+        // update the rest of the diagonal block: a[i][k] -= l[i][c] conj(l[k][c]), c < k <= i < nb
+        for (int t = lane; t < CHOL_NB * CHOL_NB; t += 32) {
+          const int i = t % CHOL_NB, k = t / CHOL_NB;
+          if (k > c && k <= i && i < nb) {
+            const C li = a[jb + i + (size_t)col * n], lk = a[jb + k + (size_t)col * n];
+            C v = a[jb + i + (size_t)(jb + k) * n];
+            v.x -= li.x * lk.x + li.y * lk.y;
+            v.y -= li.y * lk.x - li.x * lk.y;
+            a[jb + i + (size_t)(jb + k) * n] = v;
+          }
+        }
+        __syncwarp();
       }
     }
     __syncthreads();
     if (bad) break;
-    const T s = piv[0], inv = piv[1];
-    for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
-      C v = a[i + (size_t)j * n];
-      if (i == j) {
-        v.x = s;
-        v.y = (T)0;
-      } else {
-        v.x *= inv;
-        v.y *= inv;
+    // (2) panel: rows i >= jb + nb, L[i][jb + c] = (A[i][jb + c] - sum_{cc<c} L[i][jb+cc] conj(L[jb+c][jb+cc])) / L_cc
+    for (int i = jb + nb + threadIdx.x; i < n; i += blockDim.x) {
+      for (int c = 0; c < nb; ++c) {
+        C x = a[i + (size_t)(jb + c) * n];
+        for (int cc = 0; cc < c; ++cc) {
+          const C lic = a[i + (size_t)(jb + cc) * n], lcc = a[jb + c + (size_t)(jb + cc) * n];
+          x.x -= lic.x * lcc.x + lic.y * lcc.y;
+          x.y -= lic.y * lcc.x - lic.x * lcc.y;
+        }
+        x.x *= rdiag[c];
+        x.y *= rdiag[c];
+        a[i + (size_t)(jb + c) * n] = x;
       }
-      a[i + (size_t)j * n] = v;
     }
     __syncthreads();
-    // trailing update: a[i][k] -= l[i][j] conj(l[k][j]) for j < k <= i
-    for (int k = j + 1 + warp; k < n; k += nwarp) {
-      const C lk = a[k + (size_t)j * n];
+    // (3) trailing update of the lower triangle: a[i][k] -= sum_c l[i][c] conj(l[k][c])
+    for (int k = jb + nb + warp; k < n; k += nwarp) {
       for (int i = k + lane; i < n; i += 32) {
-        const C li = a[i + (size_t)j * n];
         C v = a[i + (size_t)k * n];
-        v.x -= li.x * lk.x + li.y * lk.y;
-        v.y -= li.y * lk.x - li.x * lk.y;
+        for (int c = 0; c < nb; ++c) {
+          const C li = a[i + (size_t)(jb + c) * n], lk = a[k + (size_t)(jb + c) * n];
+          v.x -= li.x * lk.x + li.y * lk.y;
+          v.y -= li.y * lk.x - li.x * lk.y;
+        }
         a[i + (size_t)k * n] = v;
       }
     }
     __syncthreads();
   }
-  __syncthreads();
   // zero the strict upper triangle
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
     const int i = t % n, k = t / n;
@@ -942,7 +974,9 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
       vq[(size_t)k * n + k + 1 + i] = x;
     }
     __syncthreads();
-    // p = beta A' v   (A' = A[k+1:, k+1:]); 4 threads per row, uniform shuffles
+    // p = beta A' v   (A' = A[k+1:, k+1:]); 4 threads per row, uniform shuffles; the same pass
+    // accumulates v^H p for K
+    float kkp = 0.f;
     for (int t0 = 0; t0 < 4 * m; t0 += blockDim.x) {
       const int t = t0 + threadIdx.x;
       const bool act = t < 4 * m;
@@ -975,13 +1009,14 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
       pi += __shfl_xor_sync(0xffffffffu, pi, 1);
       pr += __shfl_xor_sync(0xffffffffu, pr, 2);
       pi += __shfl_xor_sync(0xffffffffu, pi, 2);
-      if (act && part == 0) p[i] = make_float2(bet * pr, bet * pi);
+      if (act && part == 0) {
+        const float2 pv = make_float2(bet * pr, bet * pi);
+        p[i] = pv;
+        kkp += v[i].x * pv.x + v[i].y * pv.y;
+      }
     }
-    __syncthreads();
-    // K = (beta / 2) v^H p  (real for Hermitian A')
-    float kk = 0.f;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) kk += v[i].x * p[i].x + v[i].y * p[i].y;
-    kk = 0.5f * bet * block_sum_f(kk, red);
+    // K = (beta / 2) v^H p  (real for Hermitian A'); the reduction's barriers publish p
+    const float kk = 0.5f * bet * block_sum_f(kkp, red);
     // w = p - K v  (in place in p)
     for (int i = threadIdx.x; i < m; i += blockDim.x) p[i] = make_float2(p[i].x - kk * v[i].x, p[i].y - kk * v[i].y);
     __syncthreads();
@@ -1583,14 +1618,14 @@ __global__ void k_add_identity(double2* E, int nw) {
 
 // ===================================================================== Cholesky-QR apply
 // W <- W (L^H)^{-1} for each k-point (skipped where skip[b] != 0): row w of W solves y L^H = w, i.e.
-// y_j = (w_j - sum_{i<j} conj(L_ji) y_i) / L_jj, in place.  Eight lanes share one row: lane q
-// keeps the columns j = q (mod 8) in registers; at step j the owner finishes y_j and
-// broadcasts it, and every lane subtracts conj(L_kj) y_j from its columns k > j (right-looking
-// order, same arithmetic).  L (m x m, lower, from k_chol) is read through the L1 cache, the
-// reciprocal diagonal from shared memory.  W: rows x m block with leading dimension ld, batch
-// stride sW.
+// y_j = (w_j - sum_{i<j} conj(L_ji) y_i) / L_jj, in place.  One warp per row: lane q keeps
+// the columns j = q (mod 32) in registers; at step j the owner finishes y_j and broadcasts it,
+// and every lane subtracts conj(L_kj) y_j from its columns k > j (right-looking order, same
+// arithmetic).  L (m x m, lower, from k_chol) is read through the L1 cache (coalesced along a
+// column), the reciprocal diagonal from shared memory.  W: rows x m block with leading
+// dimension ld, batch stride sW.
 namespace hw {
-constexpr int TRSM_THREADS = 32;   // 4 rows per block: many blocks per SM, even balance
+constexpr int TRSM_THREADS = 128;   // 4 rows per block, one warp per row
 
 template <typename T, int NPER>
 __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_lh(const double2* __restrict__ L, int m, double2* W,
@@ -1603,60 +1638,59 @@ __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_lh(const double2* __restr
   const double2* l = L + (size_t)b * m * m;
   for (int j = threadIdx.x; j < m; j += blockDim.x) dinv[j] = (T)1 / (T)l[j + (size_t)j * m].x;
   __syncthreads();
-  const int q = threadIdx.x & 7;
-  const int64_t r = (int64_t)blockIdx.x * (TRSM_THREADS / 8) + (threadIdx.x >> 3);
-  const bool valid = r < rows;
-  double2* w = W + (size_t)b * sW + (valid ? r : 0);
+  const int q = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * (TRSM_THREADS / 32) + (threadIdx.x >> 5);
+  if (r >= rows) return;   // whole warp (one row per warp)
+  double2* w = W + (size_t)b * sW + r;
+  // acc[c] holds column q + 32 (cb + c) of the current window; after each group of 32 steps
+  // the finished column acc[0] is stored and the window shifts (static register indices only)
   C acc[NPER];
 #pragma unroll
   for (int c = 0; c < NPER; ++c) {
-    const int j = q + 8 * c;
-    const double2 x = (valid && j < m) ? w[(size_t)j * ld] : make_double2(0.0, 0.0);
+    const int j = q + 32 * c;
+    const double2 x = j < m ? w[(size_t)j * ld] : make_double2(0.0, 0.0);
     acc[c].x = (T)x.x;
     acc[c].y = (T)x.y;
   }
+  const int ncb = (m + 31) / 32;
+  for (int cb = 0; cb < ncb; ++cb) {
+    const int jend = min(32, m - 32 * cb);
+    for (int o = 0; o < jend; ++o) {
+      const int j = 32 * cb + o;
+      T yx = (T)0, yy = (T)0;
+      if (q == o) {
+        const T di = dinv[j];
+        yx = acc[0].x * di;
+        yy = acc[0].y * di;
+        acc[0].x = yx;
+        acc[0].y = yy;
+      }
+      yx = __shfl_sync(0xffffffffu, yx, o);
+      yy = __shfl_sync(0xffffffffu, yy, o);
+      const double2* lj = l + (size_t)j * m;
 #pragma unroll
-  for (int cb = 0; cb < NPER; ++cb) {
-#pragma unroll
-    for (int o = 0; o < 8; ++o) {
-      const int j = 8 * cb + o;
-      if (j < m) {
-        T yx = (T)0, yy = (T)0;
-        if (q == o) {
-          const T di = dinv[j];
-          yx = acc[cb].x * di;
-          yy = acc[cb].y * di;
-          acc[cb].x = yx;
-          acc[cb].y = yy;
-        }
-        yx = __shfl_sync(0xffffffffu, yx, o, 8);
-        yy = __shfl_sync(0xffffffffu, yy, o, 8);
-#pragma unroll
-        for (int c = cb; c < NPER; ++c) {
-          const int k = q + 8 * c;
-          if (k > j && k < m) {
-            const double2 lkj = __ldg(l + k + (size_t)j * m);   // L[k][j]; acc -= conj(lkj) y
-            const T lx = (T)lkj.x, ly = (T)lkj.y;
-            acc[c].x -= lx * yx + ly * yy;
-            acc[c].y -= lx * yy - ly * yx;
-          }
+      for (int c = 0; c < NPER; ++c) {
+        const int k = q + 32 * (cb + c);
+        if (k > j && k < m) {
+          const double2 lkj = __ldg(lj + k);   // L[k][j]; acc -= conj(lkj) y
+          const T lx = (T)lkj.x, ly = (T)lkj.y;
+          acc[c].x -= lx * yx + ly * yy;
+          acc[c].y -= lx * yy - ly * yx;
         }
       }
     }
-  }
-  if (valid) {
+    const int jf = q + 32 * cb;   // finished column of this lane
+    if (jf < m) w[(size_t)jf * ld] = make_double2((double)acc[0].x, (double)acc[0].y);
 #pragma unroll
-    for (int c = 0; c < NPER; ++c) {
-      const int j = q + 8 * c;
-      if (j < m) w[(size_t)j * ld] = make_double2((double)acc[c].x, (double)acc[c].y);
-    }
+    for (int c = 0; c + 1 < NPER; ++c) acc[c] = acc[c + 1];
+    acc[NPER - 1].x = acc[NPER - 1].y = (T)0;
   }
 }
 
 template <typename T, int NPER>
 static cudaError_t trsm_launch(cudaStream_t st, const double2* L, int m, int nprob, double2* W, int64_t rows,
                                int64_t ld, int64_t sW, const int* skip) {
-  const int rpb = TRSM_THREADS / 8;
+  const int rpb = TRSM_THREADS / 32;
   k_trsm_lh<T, NPER><<<dim3((unsigned)((rows + rpb - 1) / rpb), nprob), TRSM_THREADS, m * sizeof(T), st>>>(
       L, m, W, rows, ld, sW, skip);
   return cudaGetLastError();
@@ -1665,18 +1699,16 @@ static cudaError_t trsm_launch(cudaStream_t st, const double2* L, int m, int npr
 template <typename T>
 static cudaError_t trsm_dispatch(cudaStream_t st, const double2* L, int m, int nprob, double2* W, int64_t rows,
                                  int64_t ld, int64_t sW, const int* skip) {
-  const int nper = (m + 7) / 8;
+  const int nper = (m + 31) / 32;
+  if (nper <= 1) return trsm_launch<T, 1>(st, L, m, nprob, W, rows, ld, sW, skip);
   if (nper <= 2) return trsm_launch<T, 2>(st, L, m, nprob, W, rows, ld, sW, skip);
-  if (nper <= 4) return trsm_launch<T, 4>(st, L, m, nprob, W, rows, ld, sW, skip);
-  if (nper <= 6) return trsm_launch<T, 6>(st, L, m, nprob, W, rows, ld, sW, skip);
-  if (nper <= 9) return trsm_launch<T, 9>(st, L, m, nprob, W, rows, ld, sW, skip);
-  if (nper <= 12) return trsm_launch<T, 12>(st, L, m, nprob, W, rows, ld, sW, skip);
-  return trsm_launch<T, 15>(st, L, m, nprob, W, rows, ld, sW, skip);
+  if (nper <= 3) return trsm_launch<T, 3>(st, L, m, nprob, W, rows, ld, sW, skip);
+  return trsm_launch<T, 4>(st, L, m, nprob, W, rows, ld, sW, skip);
 }
 
 cudaError_t dense_trsm_lh(cudaStream_t st, const double2* L, int m, int nprob, double2* W, int64_t rows, int64_t ld,
                           int64_t sW, bool fp32, const int* skip) {
-  if (m > 120) return cudaErrorInvalidValue;
+  if (m > 128) return cudaErrorInvalidValue;
   if (rows <= 0) return cudaSuccess;
   return fp32 ? trsm_dispatch<float>(st, L, m, nprob, W, rows, ld, sW, skip)
               : trsm_dispatch<double>(st, L, m, nprob, W, rows, ld, sW, skip);

@@ -37,6 +37,10 @@ void dense_free(DenseWork*& dw);
 cudaError_t dense_heev(DenseWork* dw, cudaStream_t st, double2* A, int n, int nprob, double* w,
                        double2* Z, int* status, double tol);
 cudaError_t dense_chol(cudaStream_t st, double2* G, int n, int nprob, int* fail, bool fp32 = false);
+size_t gram_work_bytes(int m, int n, int K, int batch);
+cudaError_t gram_cf(cudaStream_t st, int m, int n, int K, double alpha, const double2* A, int64_t lda, int64_t sA,
+                    const double2* B, int64_t ldb, int64_t sB, double beta, double2* C, int64_t ldc, int64_t sC,
+                    int batch, void* work, size_t work_bytes, int* launches);
 cudaError_t dense_trinv(cudaStream_t st, const double2* L, double2* Ui, int n, int nprob);
 cudaError_t dense_hermitize(cudaStream_t st, double2* A, int n, int nprob);
 cudaError_t dense_heev32(cudaStream_t st, const double2* A, int n, int nprob, double* w, double2* Z,
@@ -93,6 +97,8 @@ struct LobpcgWork {
   double2* B3 = nullptr;
   int* grp = nullptr;       // [nk][nb]
   double2* Abak = nullptr;  // [nk][ne*ne] copy of the Rayleigh-Ritz matrix (Jacobi retry)
+  void* gwork = nullptr;                          // gram_cf chunk partials
+  size_t gbytes = 0;
   float2* F32[3] = {nullptr, nullptr, nullptr};   // FP32 operand copies for low-precision products
   size_t f32_ab = 0, f32_c = 0;                   // their sizes (elements)
 };
@@ -105,7 +111,7 @@ void lobpcg_free(hw_ctx* ctx) {
                   (void*)w->Y, (void*)w->Y2, (void*)w->res, (void*)w->theta, (void*)w->iact,
                   (void*)w->fail, (void*)w->status, w->j32, w->hh, (void*)w->B1, (void*)w->B2,
                   (void*)w->B3, (void*)w->grp, (void*)w->Abak, (void*)w->F32[0], (void*)w->F32[1],
-                  (void*)w->F32[2]})
+                  (void*)w->F32[2], w->gwork})
     if (p) cudaFree(p);
   dense_free(w->dw);
   delete w;
@@ -241,6 +247,20 @@ __global__ void k_check_gram(const double2* G, int m, const double* w, int wstri
   if (threadIdx.x == 0) fail[b] = bad;
 }
 
+// A[i][j] = conj(A[j][i]) for rows i in [nb, nS) and columns j < nb (the X rows of the
+// Rayleigh-Ritz matrix are formed in FP64; their mirror image replaces the lower-left blocks).
+// grid (8, nk)
+__global__ void k_mirror_xrows(double2* A, int n, int nb, int nS) {
+  const int b = blockIdx.y;
+  double2* a = A + (size_t)b * n * n;
+  const int rows = nS - nb;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < rows * nb; t += gridDim.x * blockDim.x) {
+    const int i = nb + t % rows, j = t / rows;
+    const double2 v = a[j + (size_t)i * n];
+    a[i + (size_t)j * n] = make_double2(v.x, -v.y);
+  }
+}
+
 // Gaussian start block from a counter-based generator (splitmix64 + Box-Muller); grid (nb, nk)
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   x += 0x9E3779B97F4A7C15ull;
@@ -300,12 +320,17 @@ __global__ void k_cvt_f2d(const float2* __restrict__ src, int rows, int cols, do
   }
 }
 
-// Batched complex GEMM on the context's cuBLAS handle.  With `lowp` set (the early,
-// large-residual iterations of the mixed form) products are computed in complex FP32 on
-// converted copies of the operands; otherwise in FP64.
+// Batched complex GEMM.  With `lowp` set (the early, large-residual iterations of the mixed
+// form) products A^H B over the basis dimension go to gram_cf (FP32 products, FP64
+// accumulation every 32 rows) when `gram` is on, the other products to cuBLAS CGEMM on FP32
+// copies of the operands; otherwise everything is FP64 (cuBLAS ZGEMM).
 struct Gemm {
   hw_ctx* ctx;
   cublasStatus_t st = CUBLAS_STATUS_SUCCESS;
+  cudaError_t ce = cudaSuccess;
+  bool gram = false;          // mixed form: A^H B over the basis dimension by gram_cf
+  void* gwork = nullptr;
+  size_t gbytes = 0;
   bool lowp = false;
   float2* a32 = nullptr;
   float2* b32 = nullptr;
@@ -325,6 +350,15 @@ struct Gemm {
       if (beta == 1.0) return;
     }
     ProfScope ps(ctx, HW_PH_GEMM);
+    if (gram && lowp && ta == CUBLAS_OP_C && tb == CUBLAS_OP_N && k >= 256 &&
+        gram_work_bytes(m, n, k, batch) <= gbytes) {
+      int nl = 0;
+      const cudaError_t e = gram_cf(ctx->stream, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch,
+                                    gwork, gbytes, &nl);
+      ctx->launches += nl;
+      if (e != cudaSuccess && ce == cudaSuccess) ce = e;
+      return;
+    }
     const int ra = ta == CUBLAS_OP_N ? m : k, ca = ta == CUBLAS_OP_N ? k : m;
     const int rb = tb == CUBLAS_OP_N ? k : n, cb = tb == CUBLAS_OP_N ? n : k;
     if (lowp && k >= 16 && (size_t)ra * ca * batch <= cap_ab &&
@@ -624,6 +658,8 @@ static hw_status ensure_work(hw_ctx* ctx, int nk, int nb, int64_t Lpad) {
   A((void**)&w->fail, (size_t)nk * sizeof(int));
   A((void**)&w->status, sizeof(int));
   if (e == cudaSuccess) e = dense_alloc(w->dw, nk * ne2, nk);
+  w->gbytes = gram_work_bytes(w->ne, w->ne, (int)Lpad, nk);
+  A(&w->gwork, w->gbytes);
   if (e == cudaSuccess && hh_smem(w->ne) <= 226 * 1024) {
     w->hh_bytes = hh_scratch_bytes(w->ne, w->ne, nk);
     e = cudaMalloc(&w->hh, w->hh_bytes);
@@ -728,6 +764,11 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     gemm.cap_c = w->f32_c;
     gemm.lowp = true;
   }
+  if (prec == HW_MIXED && ctx->gram_mixed) {
+    gemm.gram = true;
+    gemm.gwork = w->gwork;
+    gemm.gbytes = w->gbytes;
+  }
   std::vector<int64_t> Lb(nk);
   for (int b = 0; b < nk; ++b) Lb[b] = ctx->hb.L[kidx[b]];
   int64_t* dL = nullptr;
@@ -827,6 +868,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
     if (dstat == HW_ETIMEOUT) return hw_fail(ctx, HW_ETIMEOUT, "dense eigensolver barrier timed out");
     if (gemm.st != CUBLAS_STATUS_SUCCESS) return hw_fail(ctx, HW_ECUDA, "cuBLAS failure");
+    if (gemm.ce != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("Gram kernel: ") + cudaGetErrorString(gemm.ce));
     if (trace) {
       for (int r = 0; r < trace->n_rec; ++r) {
         if (trace->rec_iters[r] != it || trace->got[r]) continue;
@@ -975,6 +1017,14 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       }
       if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("precond: ") + cudaGetErrorString(e));
     }
+    // FP64 phase of the mixed form ("hybrid"): only the products that involve X stay FP64 (its
+    // rows of the Rayleigh-Ritz matrix, its share of the X / H X update, and one projection of
+    // W and of P against X, which keeps the basis orthonormal to FP64 accuracy where it
+    // matters).  W and P enter the Ritz vectors with weights of the order of the residuals, so
+    // their mutual orthogonalisation, their Gram block and the P update are formed in FP32.
+    const bool hyb = mixed && !gemm.lowp && ctx->hybrid;
+    const bool lowp_now = gemm.lowp;
+    gemm.lowp = lowp_now || hyb;
     // ---- project out [X P], twice
     for (int pass = 0; pass < 2; ++pass) {
       gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb + np, na, (int)Lpad, 1.0, S, Lpad, sK, S + (size_t)woff * Lpad, Lpad, sK,
@@ -984,7 +1034,15 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     }
     // ---- Cholesky-QR of W (twice)
     hs = cholqr(ctx, w, gemm, S, woff, na, dnv, 2, failed);
+    gemm.lowp = lowp_now;
     if (hs != HW_OK) return hs;
+    if (hyb) {
+      // W orthogonal to X to FP64 accuracy: one FP64 projection pass against X alone
+      gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, na, (int)Lpad, 1.0, S, Lpad, sK, S + (size_t)woff * Lpad, Lpad, sK, 0.0,
+           w->C, nb, (int64_t)2 * nb * nb, nk);
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, na, nb, -1.0, S, Lpad, sK, w->C, nb, (int64_t)2 * nb * nb, 1.0,
+           S + (size_t)woff * Lpad, Lpad, sK, nk);
+    }
     bool anyfail = false;
     for (int b = 0; b < nk; ++b)
       if (failed[b] && nav[b] > 0) {
@@ -1004,7 +1062,23 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     // ---- Rayleigh-Ritz on S = [X P W]
     const int nS = nb + np + na;
     const int n = nS + (nS & 1);
-    gemm(CUBLAS_OP_C, CUBLAS_OP_N, nS, nS, (int)Lpad, 1.0, S, Lpad, sK, HS, Lpad, sK, 0.0, w->A, n, (int64_t)n * n, nk);
+    if (hyb && nS > nb) {
+      // X rows in FP64, the [P W] block in FP32, the lower-left blocks mirrored
+      gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nS, (int)Lpad, 1.0, S, Lpad, sK, HS, Lpad, sK, 0.0, w->A, n, (int64_t)n * n,
+           nk);
+      gemm.lowp = true;
+      gemm(CUBLAS_OP_C, CUBLAS_OP_N, nS - nb, nS - nb, (int)Lpad, 1.0, S + (size_t)nb * Lpad, Lpad, sK,
+           HS + (size_t)nb * Lpad, Lpad, sK, 0.0, w->A + nb + (size_t)nb * n, n, (int64_t)n * n, nk);
+      gemm.lowp = false;
+      {
+        ProfScope ps_(ctx, HW_PH_OTHER);
+        k_mirror_xrows<<<dim3(8, nk), 256, 0, st>>>(w->A, n, nb, nS);
+        ctx->launches++;
+      }
+    } else {
+      gemm(CUBLAS_OP_C, CUBLAS_OP_N, nS, nS, (int)Lpad, 1.0, S, Lpad, sK, HS, Lpad, sK, 0.0, w->A, n, (int64_t)n * n,
+           nk);
+    }
     {
       ProfScope ps_(ctx, HW_PH_OTHER);
       k_pad_rr<<<dim3(8, nk), 256, 0, st>>>(w->A, n, nb, np, na, dnv + nk, dnv + 2 * nk);
@@ -1015,8 +1089,26 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     const int nxt = 1 - cur;
     double2* S2 = w->SB[nxt];
     double2* HS2 = w->HSB[nxt];
-    gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nS, 1.0, S, Lpad, sK, w->Z, n, (int64_t)n * n, 0.0, S2, Lpad, sK, nk);
-    gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nS, 1.0, HS, Lpad, sK, w->Z, n, (int64_t)n * n, 0.0, HS2, Lpad, sK, nk);
+    if (hyb && nS > nb) {
+      // X_new = [P W] Z_w[nb:] (FP32) + X Z_w[:nb] (FP64, accumulated in FP64), same for H X
+      gemm.lowp = true;
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nS - nb, 1.0, S + (size_t)nb * Lpad, Lpad, sK, w->Z + nb, n,
+           (int64_t)n * n, 0.0, S2, Lpad, sK, nk);
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nS - nb, 1.0, HS + (size_t)nb * Lpad, Lpad, sK, w->Z + nb, n,
+           (int64_t)n * n, 0.0, HS2, Lpad, sK, nk);
+      gemm.lowp = false;
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nb, 1.0, S, Lpad, sK, w->Z, n, (int64_t)n * n, 1.0, S2, Lpad, sK,
+           nk);
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nb, 1.0, HS, Lpad, sK, w->Z, n, (int64_t)n * n, 1.0, HS2, Lpad,
+           sK, nk);
+    } else {
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nS, 1.0, S, Lpad, sK, w->Z, n, (int64_t)n * n, 0.0, S2, Lpad, sK,
+           nk);
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nS, 1.0, HS, Lpad, sK, w->Z, n, (int64_t)n * n, 0.0, HS2, Lpad,
+           sK, nk);
+    }
+    // the P basis (small space and the block update) in FP32 in the hybrid phase as well
+    gemm.lowp = lowp_now || hyb;
     for (int b = 0; b < nk; ++b)
       cudaMemcpyAsync(w->theta + (size_t)b * nb, w->w + (size_t)b * n, nb * sizeof(double), cudaMemcpyDeviceToDevice, st);
     // ---- P = S Y (active columns), Y orthogonal to Z[:, :nb] and orthonormal
@@ -1071,9 +1163,20 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
            S2 + (size_t)nb * Lpad, Lpad, sK, nk);
       gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, na, nS, 1.0, HS, Lpad, sK, w->Y, n, (int64_t)n * na, 0.0,
            HS2 + (size_t)nb * Lpad, Lpad, sK, nk);
+      if (hyb) {
+        // P orthogonal to the new X to FP64 accuracy (H P corrected alongside)
+        gemm.lowp = false;
+        gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, na, (int)Lpad, 1.0, S2, Lpad, sK, S2 + (size_t)nb * Lpad, Lpad, sK, 0.0,
+             w->C, nb, (int64_t)2 * nb * nb, nk);
+        gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, na, nb, -1.0, S2, Lpad, sK, w->C, nb, (int64_t)2 * nb * nb, 1.0,
+             S2 + (size_t)nb * Lpad, Lpad, sK, nk);
+        gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, na, nb, -1.0, HS2, Lpad, sK, w->C, nb, (int64_t)2 * nb * nb, 1.0,
+             HS2 + (size_t)nb * Lpad, Lpad, sK, nk);
+      }
       np = na;
       npv = nav;
     }
+    gemm.lowp = lowp_now;
     cur = nxt;
   }
   // k-points that never converged: report the last Ritz values
@@ -1107,6 +1210,29 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
   if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
   if (gemm.st != CUBLAS_STATUS_SUCCESS) return hw_fail(ctx, HW_ECUDA, "cuBLAS failure");
   if (final_status != HW_OK) return hw_fail(ctx, HW_ENOTCONV, "maxit reached before convergence");
+  return HW_OK;
+}
+
+extern "C" hw_status hw_gram(hw_ctx* ctx, int m, int n, int K, int nprob, const double* A, int64_t lda, int64_t sA,
+                              const double* B, int64_t ldb, int64_t sB, double* C, int64_t ldc, int64_t sC) {
+  if (!ctx) return HW_EINVAL;
+  if (ctx->device < 0) return hw_fail(ctx, HW_ESTATE, "host-only context has no device");
+  if (m < 1 || n < 1 || m > 512 || n > 512 || K < 1 || nprob < 1 || nprob > MAXSLOT || !A || !B || !C ||
+      lda < K || ldb < K || ldc < m)
+    return hw_fail(ctx, HW_EINVAL, "hw_gram: bad sizes");
+  cudaSetDevice(ctx->device);
+  const size_t need = gram_work_bytes(m, n, K, nprob);
+  void* work = nullptr;
+  if (cudaMalloc(&work, need) != cudaSuccess) return hw_fail(ctx, HW_ENOMEM, "hw_gram workspace");
+  int nl = 0;
+  cudaError_t e = gram_cf(ctx->stream, m, n, K, 1.0, reinterpret_cast<const double2*>(A), lda, sA,
+                          reinterpret_cast<const double2*>(B), ldb, sB, 0.0, reinterpret_cast<double2*>(C), ldc, sC,
+                          nprob, work, need, &nl);
+  ctx->launches += nl;
+  const cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+  cudaFree(work);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("hw_gram: ") + cudaGetErrorString(e));
   return HW_OK;
 }
 

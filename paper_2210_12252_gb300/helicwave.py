@@ -71,6 +71,8 @@ _SIGS = {
                               C.POINTER(C.c_int)]),
     "hw_heev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                           C.c_int]),
+    "hw_gram": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_int64,
+                          C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_int64]),
     "hw_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "hw_profile_read": (C.c_int, [C.c_void_p, _D, C.POINTER(C.c_int64)]),
     "hw_profile_work": (C.c_int, [C.c_void_p, _D]),
@@ -245,10 +247,25 @@ def hw_synchronize(h):
 HW_OPT_RR_METHOD = 0
 HW_OPT_RR_FALLBACKS = 1
 HW_OPT_LOWP_SWITCH = 2
+HW_OPT_GRAM_KERNEL = 3
+HW_OPT_HYBRID = 4
 
 
 def hw_set_option(h, option, value):
     _check(h, load_library().hw_set_option(h, option, value))
+
+
+def hw_gram(h, A, B):
+    """C_b = A_b^H B_b for torch complex128 tensors A (nprob, m, ld) and B (nprob, n, ld) whose
+    rows are the columns of the K x m / K x n blocks (K = the last dimension); returns C as
+    (nprob, n, m) (row j = column j)."""
+    import torch
+    nprob, m, K = A.shape
+    n = B.shape[1]
+    C = torch.empty((nprob, n, m), dtype=torch.complex128, device=A.device)
+    _check(h, load_library().hw_gram(h, m, n, K, nprob, A.data_ptr(), K, m * K, B.data_ptr(), K, n * K,
+                                     C.data_ptr(), m, m * n))
+    return C
 
 
 def hw_get_option(h, option):

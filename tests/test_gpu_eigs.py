@@ -105,6 +105,19 @@ def test_mixed_fp32_product_phase(hwmod, switch):
     ctx.close()
 
 
+def test_hybrid_fp64_phase_on_the_tube(hwmod):
+    """Hybrid FP64 phase (FP64 only for the products involving X) at tolerance 1e-6: converged,
+    eigenvalues within 1e-6 Ha of the oracle."""
+    w = inputs.tube()
+    ctx, L = make_ctx(hwmod, w)
+    ctx.set_option(hwmod.HW_OPT_HYBRID, 1)
+    r = ctx.solve_eigs([0], w.n_eig, tol=1e-6, maxit=500, prec="mixed")
+    assert r["converged"], r["iters"]
+    assert np.abs(r["evals"][0] - golden("tube_eigs.txt")[: w.n_eig]).max() < 1e-6
+    assert r["resid"].max() <= 1e-6
+    ctx.close()
+
+
 @pytest.mark.parametrize("prec,bar", [("fp64", 1e-8), ("mixed", 1e-6)])
 def test_tube_64_eigenpairs(hwmod, prec, bar):
     w = inputs.tube()

@@ -120,7 +120,7 @@ def test_options_set_get_and_reject(lib):
     ctx = hw.Context(device=-1)
     assert ctx.get_option(hw.HW_OPT_RR_METHOD) == 0
     assert ctx.get_option(hw.HW_OPT_RR_FALLBACKS) == 0
-    assert ctx.get_option(hw.HW_OPT_LOWP_SWITCH) == 4
+    assert ctx.get_option(hw.HW_OPT_LOWP_SWITCH) == 5
     ctx.set_option(hw.HW_OPT_LOWP_SWITCH, 0)
     assert ctx.get_option(hw.HW_OPT_LOWP_SWITCH) == 0
     ctx.set_option(hw.HW_OPT_RR_METHOD, 1)
