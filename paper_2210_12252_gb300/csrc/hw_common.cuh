@@ -41,6 +41,30 @@ __device__ __forceinline__ V cmul_i(V a, int s) {
   return r;
 }
 
+// FP64 <-> FP32 by integer bit operations.  This GPU executes the hardware conversions on its
+// FP64 pipe (1/64 of the FP32 rate), which otherwise bounds kernels that convert every operand.
+// d2f: round to nearest (ties away from zero), magnitudes below 2^-126 flush to zero, overflow
+// to infinity.  f2d: exact for normal numbers and zero (subnormal floats flush to zero).
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long v = u & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long r = ((v >> 28) + 1ull) >> 1;   // exponent | 23-bit mantissa, rounded
+  const unsigned long long lo = 897ull << 23, hi = 1151ull << 23;
+  unsigned int bits = r < lo ? 0u : (r >= hi ? 0x7F800000u : (unsigned int)(r - (896ull << 23)));
+  bits |= (unsigned int)(u >> 32) & 0x80000000u;
+  return __uint_as_float(bits);
+}
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned int u = __float_as_uint(x);
+  const unsigned int e = (u >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 0u) return __longlong_as_double((long long)sign);
+  const unsigned long long e64 = e == 255u ? 2047ull : (unsigned long long)e + 896ull;
+  return __longlong_as_double((long long)(sign | (e64 << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+__device__ __forceinline__ float2 d2f(double2 x) { return make_float2(d2f(x.x), d2f(x.y)); }
+__device__ __forceinline__ double2 f2d(float2 x) { return make_double2(f2d(x.x), f2d(x.y)); }
+
 __device__ __forceinline__ int pmod(int a, int n) {
   int r = a % n;
   return r < 0 ? r + n : r;

@@ -69,10 +69,16 @@ template <> struct Cx<float> { using t = float2; };
 // lower Cholesky in place (upper triangle zeroed); fail[b] = 1 + column of a bad pivot.
 // Blocked right-looking with CHOL_NB-column panels, three block barriers per panel: warp 0
 // factors the diagonal block (warp-synchronous), one thread per row solves the panel below
-// it, and all warps apply the rank-CHOL_NB update to the trailing lower triangle (a warp per
-// column, lanes over rows: contiguous shared-memory reads).  T is the arithmetic type (G stays
-// FP64 in memory); the FP32 variant serves the FP32-product phase.
+// it with the row held in registers, and all warps apply the rank-CHOL_NB update to the
+// trailing lower triangle (a warp per column, lanes over rows: contiguous shared-memory reads).
+// T is the arithmetic type.  T = double: the factor overwrites G (complex128).  T = float (the
+// FP32-product phase): G is read as complex128 and the factor is written as complex64 into
+// the first n*n*8 bytes of each problem's slot, which is what the FP32 triangular solve reads.
 constexpr int CHOL_NB = 16;
+
+template <typename T> __device__ __forceinline__ typename Cx<T>::t ld_c(const double2& x);
+template <> __device__ __forceinline__ double2 ld_c<double>(const double2& x) { return x; }
+template <> __device__ __forceinline__ float2 ld_c<float>(const double2& x) { return d2f(x); }
 
 template <typename T>
 __global__ void __launch_bounds__(CHOL_THREADS) k_chol(double2* G, int n, int64_t sG, int* fail, int use_smem) {
@@ -86,11 +92,7 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol(double2* G, int n, int64_
   __shared__ T rdiag[CHOL_NB];
   if (threadIdx.x == 0) bad = 0;
   if (use_smem)
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-      const double2 x = g[t];
-      a[t].x = (T)x.x;
-      a[t].y = (T)x.y;
-    }
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) a[t] = ld_c<T>(g[t]);
   __syncthreads();
   for (int jb = 0; jb < n; jb += CHOL_NB) {
     const int nb = min(CHOL_NB, n - jb);
@@ -130,19 +132,30 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol(double2* G, int n, int64_
     }
     __syncthreads();
     if (bad) break;
-    // (2) panel: rows i >= jb + nb, L[i][jb + c] = (A[i][jb + c] - sum_{cc<c} L[i][jb+cc] conj(L[jb+c][jb+cc])) / L_cc
+    // (2) panel: row i >= jb + nb solves x L_d^H = a (row in registers):
+    //     x_c = (a_c - sum_{cc<c} x_cc conj(L_d[c][cc])) / L_d[c][c]
     for (int i = jb + nb + threadIdx.x; i < n; i += blockDim.x) {
-      for (int c = 0; c < nb; ++c) {
-        C x = a[i + (size_t)(jb + c) * n];
-        for (int cc = 0; cc < c; ++cc) {
-          const C lic = a[i + (size_t)(jb + cc) * n], lcc = a[jb + c + (size_t)(jb + cc) * n];
-          x.x -= lic.x * lcc.x + lic.y * lcc.y;
-          x.y -= lic.y * lcc.x - lic.x * lcc.y;
+      C x[CHOL_NB];
+#pragma unroll
+      for (int c = 0; c < CHOL_NB; ++c) x[c] = c < nb ? a[i + (size_t)(jb + c) * n] : C{(T)0, (T)0};
+#pragma unroll
+      for (int c = 0; c < CHOL_NB; ++c) {
+        if (c < nb) {
+          C v = x[c];
+#pragma unroll
+          for (int cc = 0; cc < c; ++cc) {
+            const C l = a[jb + c + (size_t)(jb + cc) * n];
+            v.x -= x[cc].x * l.x + x[cc].y * l.y;
+            v.y -= x[cc].y * l.x - x[cc].x * l.y;
+          }
+          v.x *= rdiag[c];
+          v.y *= rdiag[c];
+          x[c] = v;
         }
-        x.x *= rdiag[c];
-        x.y *= rdiag[c];
-        a[i + (size_t)(jb + c) * n] = x;
       }
+#pragma unroll
+      for (int c = 0; c < CHOL_NB; ++c)
+        if (c < nb) a[i + (size_t)(jb + c) * n] = x[c];
     }
     __syncthreads();
     // (3) trailing update of the lower triangle: a[i][k] -= sum_c l[i][c] conj(l[k][c])
@@ -165,8 +178,14 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol(double2* G, int n, int64_
     if (k > i) a[t].x = a[t].y = (T)0;
   }
   __syncthreads();
-  if (use_smem)
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) g[t] = make_double2((double)a[t].x, (double)a[t].y);
+  if (use_smem) {
+    if (sizeof(T) == sizeof(float)) {
+      float2* gf = reinterpret_cast<float2*>(g);
+      for (int t = threadIdx.x; t < n * n; t += blockDim.x) gf[t] = make_float2((float)a[t].x, (float)a[t].y);
+    } else {
+      for (int t = threadIdx.x; t < n * n; t += blockDim.x) g[t] = make_double2((double)a[t].x, (double)a[t].y);
+    }
+  }
   if (threadIdx.x == 0) fail[b] = bad;
 }
 
@@ -926,7 +945,7 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
     const double2* col = a + (size_t)mp[i] * n;
     for (int j = lane; j <= i; j += 32) {
       const double2 x = col[mp[j]];
-      S[tri(i, j)] = i == j ? make_float2((float)(x.x - mu), 0.f) : make_float2((float)x.x, (float)-x.y);
+      S[tri(i, j)] = i == j ? make_float2(d2f(x.x - mu), 0.f) : make_float2(d2f(x.x), -d2f(x.y));
     }
   }
   __syncthreads();
@@ -1321,7 +1340,7 @@ __global__ void __launch_bounds__(256) k_hh_back(HhArgs H) {
 #pragma unroll
   for (int c = 0; c < HB_PER; ++c) {
     const int i = lane + 32 * c;
-    if (i < nv) z[mp[i]] = make_double2((double)zr[c].x, (double)zr[c].y);
+    if (i < nv) z[mp[i]] = f2d(zr[c]);
   }
   for (int t = nv + lane; t < n; t += 32) z[mp[t]] = make_double2(0.0, 0.0);
 }
@@ -1635,8 +1654,9 @@ __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_lh(const double2* __restr
   T* dinv = reinterpret_cast<T*>(smem_raw);
   const int b = blockIdx.y;
   if (skip && skip[b]) return;   // failed factorisation: W left as it was
-  const double2* l = L + (size_t)b * m * m;
-  for (int j = threadIdx.x; j < m; j += blockDim.x) dinv[j] = (T)1 / (T)l[j + (size_t)j * m].x;
+  // the factor: complex128 for T = double, complex64 (written by k_chol<float>) for T = float
+  const C* l = reinterpret_cast<const C*>(L + (size_t)b * m * m);
+  for (int j = threadIdx.x; j < m; j += blockDim.x) dinv[j] = (T)1 / l[j + (size_t)j * m].x;
   __syncthreads();
   const int q = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * (TRSM_THREADS / 32) + (threadIdx.x >> 5);
@@ -1648,9 +1668,7 @@ __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_lh(const double2* __restr
 #pragma unroll
   for (int c = 0; c < NPER; ++c) {
     const int j = q + 32 * c;
-    const double2 x = j < m ? w[(size_t)j * ld] : make_double2(0.0, 0.0);
-    acc[c].x = (T)x.x;
-    acc[c].y = (T)x.y;
+    acc[c] = ld_c<T>(j < m ? w[(size_t)j * ld] : make_double2(0.0, 0.0));
   }
   const int ncb = (m + 31) / 32;
   for (int cb = 0; cb < ncb; ++cb) {
@@ -1667,20 +1685,24 @@ __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_lh(const double2* __restr
       }
       yx = __shfl_sync(0xffffffffu, yx, o);
       yy = __shfl_sync(0xffffffffu, yy, o);
-      const double2* lj = l + (size_t)j * m;
+      const C* lj = l + (size_t)j * m;
 #pragma unroll
       for (int c = 0; c < NPER; ++c) {
         const int k = q + 32 * (cb + c);
         if (k > j && k < m) {
-          const double2 lkj = __ldg(lj + k);   // L[k][j]; acc -= conj(lkj) y
-          const T lx = (T)lkj.x, ly = (T)lkj.y;
-          acc[c].x -= lx * yx + ly * yy;
-          acc[c].y -= lx * yy - ly * yx;
+          const C lkj = lj[k];   // L[k][j]; acc -= conj(lkj) y
+          acc[c].x -= lkj.x * yx + lkj.y * yy;
+          acc[c].y -= lkj.x * yy - lkj.y * yx;
         }
       }
     }
     const int jf = q + 32 * cb;   // finished column of this lane
-    if (jf < m) w[(size_t)jf * ld] = make_double2((double)acc[0].x, (double)acc[0].y);
+    if (jf < m) {
+      if (sizeof(T) == sizeof(float))
+        w[(size_t)jf * ld] = f2d(make_float2((float)acc[0].x, (float)acc[0].y));
+      else
+        w[(size_t)jf * ld] = make_double2((double)acc[0].x, (double)acc[0].y);
+    }
 #pragma unroll
     for (int c = 0; c + 1 < NPER; ++c) acc[c] = acc[c + 1];
     acc[NPER - 1].x = acc[NPER - 1].y = (T)0;

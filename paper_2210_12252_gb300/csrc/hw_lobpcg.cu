@@ -304,8 +304,7 @@ __global__ void k_cvt_d2f(const double2* __restrict__ src, int64_t ld, int rows,
   const int64_t per = (int64_t)rows * cols, tot = per * batch;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = t / per, q = t - b * per, c = q / rows, r = q - c * rows;
-    const double2 x = src[b * sSrc + c * ld + r];
-    dst[t] = make_float2((float)x.x, (float)x.y);
+    dst[t] = d2f(src[b * sSrc + c * ld + r]);
   }
 }
 
@@ -315,8 +314,7 @@ __global__ void k_cvt_f2d(const float2* __restrict__ src, int rows, int cols, do
   const int64_t per = (int64_t)rows * cols, tot = per * batch;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = t / per, q = t - b * per, c = q / rows, r = q - c * rows;
-    const float2 x = src[t];
-    dst[b * sDst + c * ld + r] = make_double2((double)x.x, (double)x.y);
+    dst[b * sDst + c * ld + r] = f2d(src[t]);
   }
 }
 

@@ -178,21 +178,36 @@ __global__ void k_col_keres(MlpArgs A) {
   }
 }
 
-// inference: Z = s R; grid (row chunks, ns, nslot)
+// inference: Z = s R, all in FP32 (features, TPA factor, network, exp; FP64 <-> FP32 by bit
+// operations, since this GPU's FP64 pipe would otherwise cost as much as the network);
+// grid (row chunks, ns, nslot)
 __global__ void __launch_bounds__(128) k_mlp_apply(MlpArgs A) {
   extern __shared__ __align__(16) float Ps[];
   load_params_bf16(A.params, Ps);
   const int slot = blockIdx.z, s = blockIdx.y;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= A.L[slot]) return;
-  const double keres = A.colstat[5 * ((size_t)slot * A.ns + s)];
-  const double theta = A.ritz[(size_t)slot * A.ns + s];
+  const size_t col = (size_t)slot * A.ns + s;
+  const float rkeres = 1.0f / d2f(A.colstat[5 * col]);
+  const float theta = d2f(A.ritz[col]);
+  const int64_t o = A.off[slot] + i;
+  const int m = A.mnk[3 * o], n = A.mnk[3 * o + 1], k = A.mnk[3 * o + 2];
+  const float ke = d2f(A.ke[o]);
+  const float rE0 = (float)(1.0 / E0);
   float x[MIN_], a1[MH], h1[MH];
-  features(A, slot, i, theta, x);
-  const float o = net_forward(Ps, x, a1, h1);
-  const double f = tpa_of(A.ke[A.off[slot] + i] / keres) * exp((double)fminf(fmaxf(o, -30.f), 30.f));
-  const double2 r = reinterpret_cast<const double2*>(A.blk.x[slot])[(size_t)s * A.ld + i];
-  reinterpret_cast<double2*>(A.blk.y[slot])[(size_t)s * A.ld + i] = make_double2(f * r.x, f * r.y);
+  x[0] = ke * rE0;
+  x[1] = ((float)m - d2f(A.eta[slot])) / (float)max(A.M, 1);
+  x[2] = ((float)(n * A.ncyc) - d2f(A.nu[slot])) / (float)max(A.N, 1);
+  x[3] = (float)k / (float)max(A.K, 1);
+  x[4] = theta * rE0;
+  x[5] = d2f(A.vd[A.vdoff[slot] + i]) * rE0;
+  const float out = net_forward(Ps, x, a1, h1);
+  const float g = ke * rkeres;
+  const float P = 27.0f + g * (18.0f + g * (12.0f + g * 8.0f));
+  const float g2 = g * g;
+  const float f = P / (P + 16.0f * g2 * g2) * expf(fminf(fmaxf(out, -30.f), 30.f));
+  const float2 r = d2f(reinterpret_cast<const double2*>(A.blk.x[slot])[(size_t)s * A.ld + i]);
+  reinterpret_cast<double2*>(A.blk.y[slot])[(size_t)s * A.ld + i] = f2d(make_float2(f * r.x, f * r.y));
 }
 
 // training forward: s_i per row and column sums A = <z,e>, B = |z|^2, C = |e|^2
