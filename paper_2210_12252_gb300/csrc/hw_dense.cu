@@ -1275,68 +1275,91 @@ __global__ void __launch_bounds__(256) k_tri_gs(HhArgs H) {
 }
 
 constexpr int HB_PER = 8;   // n <= 256 entries per vector, 8 per lane
+constexpr int HB_RC = 16;   // reflectors staged in shared memory per round
 
 // Z[:, j] = Q D y_j in FP32 registers, one warp per wanted vector, scattered back to the
-// original indices (padding pairs: unit vectors); grid (ceil(nw / 8), nprob), 256 threads
+// original indices (padding pairs: unit vectors); the CTA stages HB_RC reflectors at a time in
+// shared memory (coalesced loads shared by its 8 vectors).  grid (ceil(nw / 8), nprob), 256
+// threads, dynamic smem HB_RC * n complex64
 __global__ void __launch_bounds__(256) k_hh_back(HhArgs H) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* vs = reinterpret_cast<float2*>(smem_raw);   // [HB_RC][n]
+  __shared__ float bs[HB_RC];
   const int n = H.n, nw = H.nw, b = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int j = blockIdx.x * 8 + warp;
-  if (j >= nw) return;
+  const bool has = j < nw;
   const int nv = H.nv[b];
   const int* mp = H.map + (size_t)b * n;
-  double2* z = H.Z + (size_t)b * H.zstride + (size_t)j * n;
-  if (j >= nv) {
+  double2* z = H.Z + (size_t)b * H.zstride + (size_t)(has ? j : 0) * n;
+  const bool pad = has && j >= nv;
+  if (pad) {
     const int src = mp[j];
     for (int i = lane; i < n; i += 32) z[i] = make_double2(i == src ? 1.0 : 0.0, 0.0);
-    return;
   }
-  const float* y = H.Y + ((size_t)b * nw + j) * n;
-  const float2* ph = H.ph + (size_t)b * n;
+  const bool work = has && !pad;   // warp-uniform
   float2 zr[HB_PER];
+  if (work) {
+    const float* y = H.Y + ((size_t)b * nw + j) * n;
+    const float2* ph = H.ph + (size_t)b * n;
 #pragma unroll
-  for (int c = 0; c < HB_PER; ++c) {
-    const int i = lane + 32 * c;
-    if (i < nv) {
-      const float yi = y[i];
-      const float2 d = ph[i];
-      zr[c] = make_float2(d.x * yi, d.y * yi);
-    } else {
-      zr[c] = make_float2(0.f, 0.f);
+    for (int c = 0; c < HB_PER; ++c) {
+      const int i = lane + 32 * c;
+      if (i < nv) {
+        const float yi = y[i];
+        const float2 d = ph[i];
+        zr[c] = make_float2(d.x * yi, d.y * yi);
+      } else {
+        zr[c] = make_float2(0.f, 0.f);
+      }
     }
   }
   const float2* vq = H.vq + (size_t)b * n * n;
   const float* beta = H.beta + (size_t)b * n;
-  for (int k = nv - 3; k >= 0; --k) {
-    const float bet = beta[k];
-    if (bet == 0.f) continue;
-    const float2* v = vq + (size_t)k * n;   // entries k+1 .. nv-1
-    float sr = 0.f, si = 0.f;               // s = v^H z
+  for (int khi = nv - 3; khi >= 0; khi -= HB_RC) {
+    const int klo = max(0, khi - HB_RC + 1);
+    const int cnt = khi - klo + 1;
+    __syncthreads();   // previous round's readers are done
+    for (int t = threadIdx.x; t < cnt * nv; t += blockDim.x) {
+      const int r = t / nv, i = t - r * nv;
+      const int k = khi - r;
+      vs[(size_t)r * n + i] = i > k ? vq[(size_t)k * n + i] : make_float2(0.f, 0.f);
+    }
+    if (threadIdx.x < cnt) bs[threadIdx.x] = beta[khi - threadIdx.x];
+    __syncthreads();
+    if (!work) continue;
+    for (int r = 0; r < cnt; ++r) {
+      const float bet = bs[r];
+      if (bet == 0.f) continue;
+      const float2* v = vs + (size_t)r * n;
+      float sr = 0.f, si = 0.f;   // s = v^H z
 #pragma unroll
-    for (int c = 0; c < HB_PER; ++c) {
-      const int i = lane + 32 * c;
-      if (i > k && i < nv) {
-        const float2 vi = v[i];
-        sr += vi.x * zr[c].x + vi.y * zr[c].y;
-        si += vi.x * zr[c].y - vi.y * zr[c].x;
+      for (int c = 0; c < HB_PER; ++c) {
+        const int i = lane + 32 * c;
+        if (i < nv) {
+          const float2 vi = v[i];
+          sr += vi.x * zr[c].x + vi.y * zr[c].y;
+          si += vi.x * zr[c].y - vi.y * zr[c].x;
+        }
       }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      sr += __shfl_xor_sync(0xffffffffu, sr, o);
-      si += __shfl_xor_sync(0xffffffffu, si, o);
-    }
-    sr *= bet;
-    si *= bet;
+      for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+      }
+      sr *= bet;
+      si *= bet;
 #pragma unroll
-    for (int c = 0; c < HB_PER; ++c) {
-      const int i = lane + 32 * c;
-      if (i > k && i < nv) {
-        const float2 vi = v[i];
-        zr[c].x -= vi.x * sr - vi.y * si;
-        zr[c].y -= vi.x * si + vi.y * sr;
+      for (int c = 0; c < HB_PER; ++c) {
+        const int i = lane + 32 * c;
+        if (i < nv) {
+          const float2 vi = v[i];
+          zr[c].x -= vi.x * sr - vi.y * si;
+          zr[c].y -= vi.x * si + vi.y * sr;
+        }
       }
     }
   }
+  if (!work) return;
 #pragma unroll
   for (int c = 0; c < HB_PER; ++c) {
     const int i = lane + 32 * c;
@@ -1394,7 +1417,7 @@ cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, in
   if (!(stage & 2)) return cudaGetLastError();
   k_tri_eig<<<dim3((nw + TRI_WARPS - 1) / TRI_WARPS, nprob), 32 * TRI_WARPS, 3 * n * sizeof(float), st>>>(H);
   k_tri_gs<<<nprob, 256, 0, st>>>(H);
-  k_hh_back<<<dim3((nw + 7) / 8, nprob), 256, 0, st>>>(H);
+  k_hh_back<<<dim3((nw + 7) / 8, nprob), 256, (size_t)HB_RC * n * sizeof(float2), st>>>(H);
   return cudaGetLastError();
 }
 
