@@ -259,13 +259,14 @@ typedef enum {
                                A^H B over the basis dimension with hw_gram's kernel (FP32
                                products, FP64 accumulation every 32 rows); 0 (default) uses
                                cuBLAS CGEMM on FP32 copies, measured faster on the tube. */
-  HW_OPT_HYBRID = 4         /* mixed form, FP64 phase: 1 keeps FP64 only for the
-                               products that involve X (its rows of the Rayleigh-Ritz matrix, its
-                               share of the X / H X updates, one projection of W and of P against
-                               X) and forms the rest of the W and P orthogonalisation, their Gram
-                               block and the P update in FP32 (residuals stall near 3e-7: for
-                               tolerances of 1e-6 and above); 0 (default) keeps every product
-                               FP64. */
+  HW_OPT_HYBRID = 4         /* mixed form, FP64 phase: 1 (default) first keeps FP64 only for
+                               the products that involve X (its rows of the Rayleigh-Ritz matrix,
+                               its share of the X / H X updates, one projection of W and of P
+                               against X) and forms the rest of the W and P orthogonalisation,
+                               their Gram block and the P update in FP32; such residuals stall
+                               near 3e-7, so when the best residual has not dropped by 30% in 4
+                               iterations every product becomes FP64.  0: FP64 throughout the
+                               phase. */
 } hw_option;
 /* Set an option (HW_EINVAL for an unknown option, a read-only one or a bad value). */
 hw_status hw_set_option(hw_ctx* ctx, int option, int value);

@@ -91,7 +91,7 @@ struct hw_ctx {
   int rr_method = 0;           // HW_OPT_RR_METHOD
   int lowp_exp = 5;            // HW_OPT_LOWP_SWITCH
   int gram_mixed = 0;          // HW_OPT_GRAM_KERNEL
-  int hybrid = 0;              // HW_OPT_HYBRID
+  int hybrid = 1;              // HW_OPT_HYBRID
   int64_t rr_fallbacks = 0;    // Householder results rejected by the check (Jacobi used)
   hw::Prof prof;
 };

@@ -735,7 +735,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
   const double lowp_thr = (prec == HW_MIXED && ctx->lowp_exp > 0) ? std::pow(10.0, -ctx->lowp_exp) : 0.0;
   if (lowp_thr > 0.0) {
     const size_t ab = (size_t)nk * Lpad * 3 * nb;
-    const size_t cc = std::max((size_t)nk * Lpad * nb, (size_t)nk * w->ne * w->ne);
+    const size_t cc = std::max((size_t)nk * Lpad * 2 * nb, (size_t)nk * w->ne * w->ne);
     if (w->f32_ab < ab || w->f32_c < cc) {
       for (auto& p : w->F32) {
         if (p) cudaFree(p);
@@ -848,6 +848,9 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
   bool refreshed = !mixed;
   double lowp_best = 1e300;
   int lowp_best_it = 0;
+  bool hyb_on = ctx->hybrid != 0;
+  double hyb_best = 1e300;
+  int hyb_best_it = 0;
   int it = 0;
   hw_status final_status = HW_ENOTCONV;
   for (it = 0; it <= maxit; ++it) {
@@ -904,10 +907,24 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
         lowp_best_it = it;
       }
     }
-    if (gemm.lowp && (maxres < lowp_thr || nclaim > 0 || it - lowp_best_it >= 4)) {
-      // leave the FP32 products: X re-orthonormalised and its H X recomputed in FP64, a
-      // Rayleigh-Ritz step on X alone, and the conjugate directions restarted
+    // the hybrid FP64 phase stalls near residual 3e-7: it hands over to all-FP64 products when
+    // the best residual has not dropped by 30% in 4 iterations
+    bool hyb_stall = false;
+    if (mixed && !gemm.lowp && hyb_on) {
+      if (maxres < 0.7 * hyb_best) {
+        hyb_best = maxres;
+        hyb_best_it = it;
+      } else if (it - hyb_best_it >= 4 && nclaim == 0) {
+        hyb_on = false;
+        hyb_stall = true;
+      }
+    }
+    if (hyb_stall || (gemm.lowp && (maxres < lowp_thr || nclaim > 0 || it - lowp_best_it >= 4))) {
+      // leave the FP32 (or hybrid) products: X re-orthonormalised and its H X recomputed in
+      // FP64, a Rayleigh-Ritz step on X alone, and the conjugate directions restarted
       gemm.lowp = false;
+      hyb_best = 1e300;
+      hyb_best_it = it;
       std::vector<int> nbv(nk, nb);
       cudaMemcpyAsync(dnv, nbv.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
       hs = cholqr(ctx, w, gemm, S, 0, nb, dnv, 2, failed);
@@ -1020,7 +1037,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     // W and of P against X, which keeps the basis orthonormal to FP64 accuracy where it
     // matters).  W and P enter the Ritz vectors with weights of the order of the residuals, so
     // their mutual orthogonalisation, their Gram block and the P update are formed in FP32.
-    const bool hyb = mixed && !gemm.lowp && ctx->hybrid;
+    const bool hyb = mixed && !gemm.lowp && hyb_on;
     const bool lowp_now = gemm.lowp;
     gemm.lowp = lowp_now || hyb;
     // ---- project out [X P], twice
@@ -1087,25 +1104,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     const int nxt = 1 - cur;
     double2* S2 = w->SB[nxt];
     double2* HS2 = w->HSB[nxt];
-    if (hyb && nS > nb) {
-      // X_new = [P W] Z_w[nb:] (FP32) + X Z_w[:nb] (FP64, accumulated in FP64), same for H X
-      gemm.lowp = true;
-      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nS - nb, 1.0, S + (size_t)nb * Lpad, Lpad, sK, w->Z + nb, n,
-           (int64_t)n * n, 0.0, S2, Lpad, sK, nk);
-      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nS - nb, 1.0, HS + (size_t)nb * Lpad, Lpad, sK, w->Z + nb, n,
-           (int64_t)n * n, 0.0, HS2, Lpad, sK, nk);
-      gemm.lowp = false;
-      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nb, 1.0, S, Lpad, sK, w->Z, n, (int64_t)n * n, 1.0, S2, Lpad, sK,
-           nk);
-      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nb, 1.0, HS, Lpad, sK, w->Z, n, (int64_t)n * n, 1.0, HS2, Lpad,
-           sK, nk);
-    } else {
-      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nS, 1.0, S, Lpad, sK, w->Z, n, (int64_t)n * n, 0.0, S2, Lpad, sK,
-           nk);
-      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nS, 1.0, HS, Lpad, sK, w->Z, n, (int64_t)n * n, 0.0, HS2, Lpad,
-           sK, nk);
-    }
-    // the P basis (small space and the block update) in FP32 in the hybrid phase as well
+    // the P basis in the small space: FP32 in the hybrid phase as well
     gemm.lowp = lowp_now || hyb;
     for (int b = 0; b < nk; ++b)
       cudaMemcpyAsync(w->theta + (size_t)b * nb, w->w + (size_t)b * n, nb * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -1157,13 +1156,29 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       np = 0;   // restart the conjugate directions everywhere
       std::fill(npv.begin(), npv.end(), 0);
     } else {
-      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, na, nS, 1.0, S, Lpad, sK, w->Y, n, (int64_t)n * na, 0.0,
-           S2 + (size_t)nb * Lpad, Lpad, sK, nk);
-      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, na, nS, 1.0, HS, Lpad, sK, w->Y, n, (int64_t)n * na, 0.0,
-           HS2 + (size_t)nb * Lpad, Lpad, sK, nk);
-      if (hyb) {
+      np = na;
+      npv = nav;
+    }
+    gemm.lowp = lowp_now;
+    // ---- block updates [X P]_new = S [Z_w Y], [HX HP]_new = HS [Z_w Y] (Y copied next to Z_w)
+    const int ncols = nb + (pfail ? 0 : na);
+    if (!pfail && na > 0)
+      cudaMemcpy2DAsync(w->Z + (size_t)nb * n, (size_t)n * n * 16, w->Y, (size_t)n * na * 16, (size_t)n * na * 16, nk,
+                        cudaMemcpyDeviceToDevice, st);
+    if (hyb && nS > nb) {
+      // [P W] rows of the coefficients in FP32, X rows in FP64 (accumulated in FP64)
+      gemm.lowp = true;
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, ncols, nS - nb, 1.0, S + (size_t)nb * Lpad, Lpad, sK, w->Z + nb, n,
+           (int64_t)n * n, 0.0, S2, Lpad, sK, nk);
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, ncols, nS - nb, 1.0, HS + (size_t)nb * Lpad, Lpad, sK, w->Z + nb,
+           n, (int64_t)n * n, 0.0, HS2, Lpad, sK, nk);
+      gemm.lowp = false;
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, ncols, nb, 1.0, S, Lpad, sK, w->Z, n, (int64_t)n * n, 1.0, S2, Lpad,
+           sK, nk);
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, ncols, nb, 1.0, HS, Lpad, sK, w->Z, n, (int64_t)n * n, 1.0, HS2,
+           Lpad, sK, nk);
+      if (!pfail && na > 0) {
         // P orthogonal to the new X to FP64 accuracy (H P corrected alongside)
-        gemm.lowp = false;
         gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, na, (int)Lpad, 1.0, S2, Lpad, sK, S2 + (size_t)nb * Lpad, Lpad, sK, 0.0,
              w->C, nb, (int64_t)2 * nb * nb, nk);
         gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, na, nb, -1.0, S2, Lpad, sK, w->C, nb, (int64_t)2 * nb * nb, 1.0,
@@ -1171,8 +1186,11 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
         gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, na, nb, -1.0, HS2, Lpad, sK, w->C, nb, (int64_t)2 * nb * nb, 1.0,
              HS2 + (size_t)nb * Lpad, Lpad, sK, nk);
       }
-      np = na;
-      npv = nav;
+    } else {
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, ncols, nS, 1.0, S, Lpad, sK, w->Z, n, (int64_t)n * n, 0.0, S2, Lpad,
+           sK, nk);
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, ncols, nS, 1.0, HS, Lpad, sK, w->Z, n, (int64_t)n * n, 0.0, HS2,
+           Lpad, sK, nk);
     }
     gemm.lowp = lowp_now;
     cur = nxt;
