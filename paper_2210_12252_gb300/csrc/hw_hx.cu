@@ -106,6 +106,87 @@ __device__ cplx_t<T>* fft_batch(cplx_t<T>* src, cplx_t<T>* dst, const FftDev& pl
   return src;
 }
 
+// The same Stockham passes with the length known at compile time (radix 4 while possible, then
+// 3, then 2): divisions, strides and twiddle indices fold to constants, which matters because
+// the slab kernel is bound by instruction issue.  Same arithmetic as fft_batch.
+template <typename T, int N, int Ns>
+__device__ __forceinline__ void fft_ct_stages(cplx_t<T>*& src, cplx_t<T>*& dst, int nb,
+                                              const cplx_t<T>* __restrict__ tw, int sign) {
+  using V = cplx_t<T>;
+  if constexpr (Ns < N) {
+    constexpr int Rem = N / Ns;
+    constexpr int R = (Rem % 4 == 0) ? 4 : ((Rem % 3 == 0) ? 3 : 2);
+    constexpr int nbf = N / R;
+    constexpr int tstride = N / (Ns * R);
+    for (int idx = threadIdx.x; idx < nb * nbf; idx += blockDim.x) {
+      const int b = idx / nbf, j = idx - b * nbf;
+      const V* in = src + b * N;
+      V* out = dst + b * N;
+      const int k = j % Ns;
+      V v0 = in[j], v1 = in[j + nbf], v2, v3;
+      if (R >= 3) v2 = in[j + 2 * nbf];
+      if (R == 4) v3 = in[j + 3 * nbf];
+      if (Ns > 1 && k) {
+        V w = tw[k * tstride];
+        if (sign > 0) w = cconj(w);
+        v1 = cmul(v1, w);
+        if (R >= 3) {
+          V w2 = tw[2 * k * tstride];
+          if (sign > 0) w2 = cconj(w2);
+          v2 = cmul(v2, w2);
+        }
+        if (R == 4) {
+          V w3 = tw[3 * k * tstride];
+          if (sign > 0) w3 = cconj(w3);
+          v3 = cmul(v3, w3);
+        }
+      }
+      const int base = (j / Ns) * Ns * R + k;
+      if (R == 2) {
+        out[base] = cadd(v0, v1);
+        out[base + Ns] = csub(v0, v1);
+      } else if (R == 4) {
+        V s02 = cadd(v0, v2), d02 = csub(v0, v2);
+        V s13 = cadd(v1, v3), d13 = csub(v1, v3);
+        V t = cmul_i(d13, sign);
+        out[base] = cadd(s02, s13);
+        out[base + Ns] = cadd(d02, t);
+        out[base + 2 * Ns] = csub(s02, s13);
+        out[base + 3 * Ns] = csub(d02, t);
+      } else {
+        const T h = T(0.86602540378443864676);
+        V s12 = cadd(v1, v2), d12 = csub(v1, v2);
+        V t;
+        t.x = v0.x - T(0.5) * s12.x;
+        t.y = v0.y - T(0.5) * s12.y;
+        V u = cmul_i(d12, sign);
+        u.x *= h;
+        u.y *= h;
+        out[base] = cadd(v0, s12);
+        out[base + Ns] = cadd(t, u);
+        out[base + 2 * Ns] = csub(t, u);
+      }
+    }
+    __syncthreads();
+    V* tmp = src;
+    src = dst;
+    dst = tmp;
+    fft_ct_stages<T, N, Ns * R>(src, dst, nb, tw, sign);
+  }
+}
+
+// length N at compile time when N > 0, else the runtime plan
+template <typename T, int N>
+__device__ __forceinline__ cplx_t<T>* fft_any(cplx_t<T>* src, cplx_t<T>* dst, const FftDev& pl, int nb,
+                                              const cplx_t<T>* __restrict__ tw, int sign) {
+  if constexpr (N > 0) {
+    fft_ct_stages<T, N, 1>(src, dst, nb, tw, sign);
+    return src;
+  } else {
+    return fft_batch<T>(src, dst, pl, nb, tw, sign);
+  }
+}
+
 // --------------------------------------------------------------------------- radial inverse
 template <typename T>
 struct RadArgs {
@@ -286,13 +367,14 @@ struct SlabArgs {
 
 constexpr int SLAB_THREADS = 256;
 
-// grid: x = column, y = radial node
-template <typename T>
+// grid: x = column, y = radial node.  N1, N2 > 0: grid sizes fixed at compile time (the
+// kernel is then specialised for them); 0: taken from A.
+template <typename T, int N1 = 0, int N2 = 0>
 __global__ void __launch_bounds__(SLAB_THREADS) k_slab(SlabArgs<T> A) {
   using V = cplx_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = blockIdx.x, p = blockIdx.y;
-  const int n1 = A.Nth1, n2 = A.Nth2, nmr = A.nmr;
+  const int n1 = N1 > 0 ? N1 : A.Nth1, n2 = N2 > 0 ? N2 : A.Nth2, nmr = A.nmr;
   const int wsz = max(nmr * n2, A.Jc * n1);
   V* Tb = reinterpret_cast<V*>(smem_raw);     // [nmr][n2]
   V* W0 = Tb + nmr * n2;
@@ -306,7 +388,7 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab(SlabArgs<T> A) {
   for (int a = threadIdx.x; a < A.nA; a += blockDim.x)
     W0[A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2)] = Gc[a];
   __syncthreads();
-  V* r = fft_batch<T>(W0, W1, A.p2, nmr, A.tw2, +1);
+  V* r = fft_any<T, N2>(W0, W1, A.p2, nmr, A.tw2, +1);
   for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) Tb[i] = r[i];
   __syncthreads();
   // theta1 pass per theta2 column chunk: insert rows, inverse FFT, x V, forward FFT, extract
@@ -320,14 +402,14 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab(SlabArgs<T> A) {
       W0[jj * n1 + pmod(A.mrow_m[rr], n1)] = Tb[rr * n2 + j0 + jj];
     }
     __syncthreads();
-    V* u = fft_batch<T>(W0, W1, A.p1, jn, A.tw1, +1);
+    V* u = fft_any<T, N1>(W0, W1, A.p1, jn, A.tw1, +1);
     for (int i = threadIdx.x; i < jn * n1; i += blockDim.x) {
       const T v = Vp[(size_t)j0 * n1 + i];
       u[i].x *= v;
       u[i].y *= v;
     }
     __syncthreads();
-    V* w = fft_batch<T>(u, u == W0 ? W1 : W0, A.p1, jn, A.tw1, -1);
+    V* w = fft_any<T, N1>(u, u == W0 ? W1 : W0, A.p1, jn, A.tw1, -1);
     for (int i = threadIdx.x; i < jn * nmr; i += blockDim.x) {
       const int jj = i / nmr, rr = i - jj * nmr;
       Tb[rr * n2 + j0 + jj] = w[jj * n1 + pmod(A.mrow_m[rr], n1)];
@@ -337,12 +419,28 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab(SlabArgs<T> A) {
   // theta2 forward pass, extract the kept pairs
   for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) W0[i] = Tb[i];
   __syncthreads();
-  r = fft_batch<T>(W0, W1, A.p2, nmr, A.tw2, -1);
+  r = fft_any<T, N2>(W0, W1, A.p2, nmr, A.tw2, -1);
   for (int a = threadIdx.x; a < A.nA; a += blockDim.x)
     Hc[a] = r[A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2)];
 }
 
 // --------------------------------------------------------------------------- host launcher
+// the slab kernel for this basis's angular grid: specialised for the grids in use, generic
+// otherwise
+template <typename T>
+static void* slab_kernel(int n1, int n2) {
+  if (n1 == 64 && n2 == 48) return (void*)k_slab<T, 64, 48>;
+  if (n1 == 192 && n2 == 96) return (void*)k_slab<T, 192, 96>;
+  return (void*)k_slab<T, 0, 0>;
+}
+
+template <typename T>
+static cudaError_t launch_slab(const hw_ctx* ctx, dim3 grid, size_t smem, const SlabArgs<T>& sa) {
+  void* f = slab_kernel<T>(sa.Nth1, sa.Nth2);
+  void* args[] = {(void*)&sa};
+  return cudaLaunchKernel(f, grid, dim3(SLAB_THREADS), args, smem, ctx->stream);
+}
+
 static FftDev to_dev(const FftPlan& p) {
   FftDev d;
   d.n = p.n;
@@ -429,7 +527,7 @@ cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld) {
     const size_t sm_slab = slab_smem_bytes(ctx, sizeof(cplx_t<T>), Jc);
     {
       ProfScope ps(ctx, HW_PH_SLAB);
-      k_slab<T><<<dim3(nc, Nr), SLAB_THREADS, sm_slab, ctx->stream>>>(sa);
+      launch_slab<T>(ctx, dim3(nc, Nr), sm_slab, sa);
       ctx->launches++;
     }
     ra.gh = reinterpret_cast<cplx_t<T>*>(ctx->ws.hbuf);
@@ -499,7 +597,7 @@ cudaError_t launch_hx_into(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, v
     sa.tw2 = reinterpret_cast<const cplx_t<T>*>(tb.tw2);
     sa.G = reinterpret_cast<const cplx_t<T>*>(gbuf);
     sa.H = reinterpret_cast<cplx_t<T>*>(hbuf);
-    k_slab<T><<<dim3(nc, Nr), SLAB_THREADS, slab_smem_bytes(ctx, sizeof(cplx_t<T>), Jc), ctx->stream>>>(sa);
+    launch_slab<T>(ctx, dim3(nc, Nr), slab_smem_bytes(ctx, sizeof(cplx_t<T>), Jc), sa);
     ra.gh = reinterpret_cast<cplx_t<T>*>(hbuf);
     ra.rtab = tb.rfwd;
     const size_t sm_fwd = ((size_t(K) * Nr * sizeof(T) + 15) & ~size_t(15)) +
@@ -521,8 +619,9 @@ cudaError_t hx_configure(hw_ctx* ctx) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radial_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radial_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radial_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slab<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slab<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  for (void* f : {(void*)k_slab<double, 0, 0>, (void*)k_slab<float, 0, 0>, (void*)k_slab<double, 64, 48>,
+                  (void*)k_slab<float, 64, 48>, (void*)k_slab<double, 192, 96>, (void*)k_slab<float, 192, 96>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   (void)ctx;
   return e;
 }
