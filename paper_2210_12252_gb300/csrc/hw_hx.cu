@@ -109,6 +109,11 @@ __device__ cplx_t<T>* fft_batch(cplx_t<T>* src, cplx_t<T>* dst, const FftDev& pl
 // The same Stockham passes with the length known at compile time (radix 4 while possible, then
 // 3, then 2): divisions, strides and twiddle indices fold to constants, which matters because
 // the slab kernel is bound by instruction issue.  Same arithmetic as fft_batch.
+// shared-memory index map of the specialised slab's FFT buffers: one pad element after every
+// 16, so the strided Stockham reads and writes spread over the banks
+__device__ __forceinline__ int pd(int i) { return i + (i >> 4); }
+__host__ __device__ inline int pd_size(int n) { return n + (n >> 4) + 1; }
+
 template <typename T, int N, int Ns>
 __device__ __forceinline__ void fft_ct_stages(cplx_t<T>*& src, cplx_t<T>*& dst, int nb,
                                               const cplx_t<T>* __restrict__ tw, int sign) {
@@ -120,12 +125,11 @@ __device__ __forceinline__ void fft_ct_stages(cplx_t<T>*& src, cplx_t<T>*& dst, 
     constexpr int tstride = N / (Ns * R);
     for (int idx = threadIdx.x; idx < nb * nbf; idx += blockDim.x) {
       const int b = idx / nbf, j = idx - b * nbf;
-      const V* in = src + b * N;
-      V* out = dst + b * N;
+      const int ib = b * N;
       const int k = j % Ns;
-      V v0 = in[j], v1 = in[j + nbf], v2, v3;
-      if (R >= 3) v2 = in[j + 2 * nbf];
-      if (R == 4) v3 = in[j + 3 * nbf];
+      V v0 = src[pd(ib + j)], v1 = src[pd(ib + j + nbf)], v2, v3;
+      if (R >= 3) v2 = src[pd(ib + j + 2 * nbf)];
+      if (R == 4) v3 = src[pd(ib + j + 3 * nbf)];
       if (Ns > 1 && k) {
         V w = tw[k * tstride];
         if (sign > 0) w = cconj(w);
@@ -141,18 +145,18 @@ __device__ __forceinline__ void fft_ct_stages(cplx_t<T>*& src, cplx_t<T>*& dst, 
           v3 = cmul(v3, w3);
         }
       }
-      const int base = (j / Ns) * Ns * R + k;
+      const int base = ib + (j / Ns) * Ns * R + k;
       if (R == 2) {
-        out[base] = cadd(v0, v1);
-        out[base + Ns] = csub(v0, v1);
+        dst[pd(base)] = cadd(v0, v1);
+        dst[pd(base + Ns)] = csub(v0, v1);
       } else if (R == 4) {
         V s02 = cadd(v0, v2), d02 = csub(v0, v2);
         V s13 = cadd(v1, v3), d13 = csub(v1, v3);
         V t = cmul_i(d13, sign);
-        out[base] = cadd(s02, s13);
-        out[base + Ns] = cadd(d02, t);
-        out[base + 2 * Ns] = csub(s02, s13);
-        out[base + 3 * Ns] = csub(d02, t);
+        dst[pd(base)] = cadd(s02, s13);
+        dst[pd(base + Ns)] = cadd(d02, t);
+        dst[pd(base + 2 * Ns)] = csub(s02, s13);
+        dst[pd(base + 3 * Ns)] = csub(d02, t);
       } else {
         const T h = T(0.86602540378443864676);
         V s12 = cadd(v1, v2), d12 = csub(v1, v2);
@@ -162,9 +166,9 @@ __device__ __forceinline__ void fft_ct_stages(cplx_t<T>*& src, cplx_t<T>*& dst, 
         V u = cmul_i(d12, sign);
         u.x *= h;
         u.y *= h;
-        out[base] = cadd(v0, s12);
-        out[base + Ns] = cadd(t, u);
-        out[base + 2 * Ns] = csub(t, u);
+        dst[pd(base)] = cadd(v0, s12);
+        dst[pd(base + Ns)] = cadd(t, u);
+        dst[pd(base + 2 * Ns)] = csub(t, u);
       }
     }
     __syncthreads();
@@ -372,56 +376,67 @@ constexpr int SLAB_THREADS = 256;
 template <typename T, int N1 = 0, int N2 = 0>
 __global__ void __launch_bounds__(SLAB_THREADS) k_slab(SlabArgs<T> A) {
   using V = cplx_t<T>;
+  constexpr bool PAD = N1 > 0;   // the specialised FFTs address their buffers through pd
+  auto ix = [](int i) { return PAD ? pd(i) : i; };
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = blockIdx.x, p = blockIdx.y;
   const int n1 = N1 > 0 ? N1 : A.Nth1, n2 = N2 > 0 ? N2 : A.Nth2, nmr = A.nmr;
-  const int wsz = max(nmr * n2, A.Jc * n1);
-  V* Tb = reinterpret_cast<V*>(smem_raw);     // [nmr][n2]
-  V* W0 = Tb + nmr * n2;
+  const int n2p = PAD ? n2 + 1 : n2;   // row stride of Tb
+  const int wsz = pd_size(max(nmr * n2, A.Jc * n1));
+  V* Tb = reinterpret_cast<V*>(smem_raw);     // [nmr][n2p]
+  V* W0 = Tb + nmr * (n2 + 1);
   V* W1 = W0 + wsz;
   const V zero = mk<T>(T(0), T(0));
   const V* Gc = A.G + ((size_t)c * A.Nr + p) * A.nA;
   V* Hc = A.H + ((size_t)c * A.Nr + p) * A.nA;
   // theta2 inverse pass over the kept m rows
-  for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) W0[i] = zero;
+  for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) W0[ix(i)] = zero;
   __syncthreads();
   for (int a = threadIdx.x; a < A.nA; a += blockDim.x)
-    W0[A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2)] = Gc[a];
+    W0[ix(A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2))] = Gc[a];
   __syncthreads();
   V* r = fft_any<T, N2>(W0, W1, A.p2, nmr, A.tw2, +1);
-  for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) Tb[i] = r[i];
+  for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) {
+    const int rr = i / n2, jj = i - rr * n2;
+    Tb[rr * n2p + jj] = r[ix(i)];
+  }
   __syncthreads();
   // theta1 pass per theta2 column chunk: insert rows, inverse FFT, x V, forward FFT, extract
   const T* Vp = A.V + (size_t)p * n2 * n1;
   for (int j0 = 0; j0 < n2; j0 += A.Jc) {
     const int jn = min(A.Jc, n2 - j0);
-    for (int i = threadIdx.x; i < jn * n1; i += blockDim.x) W0[i] = zero;
+    for (int i = threadIdx.x; i < jn * n1; i += blockDim.x) W0[ix(i)] = zero;
     __syncthreads();
     for (int i = threadIdx.x; i < jn * nmr; i += blockDim.x) {
       const int jj = i / nmr, rr = i - jj * nmr;
-      W0[jj * n1 + pmod(A.mrow_m[rr], n1)] = Tb[rr * n2 + j0 + jj];
+      W0[ix(jj * n1 + pmod(A.mrow_m[rr], n1))] = Tb[rr * n2p + j0 + jj];
     }
     __syncthreads();
     V* u = fft_any<T, N1>(W0, W1, A.p1, jn, A.tw1, +1);
     for (int i = threadIdx.x; i < jn * n1; i += blockDim.x) {
       const T v = Vp[(size_t)j0 * n1 + i];
-      u[i].x *= v;
-      u[i].y *= v;
+      V x = u[ix(i)];
+      x.x *= v;
+      x.y *= v;
+      u[ix(i)] = x;
     }
     __syncthreads();
     V* w = fft_any<T, N1>(u, u == W0 ? W1 : W0, A.p1, jn, A.tw1, -1);
     for (int i = threadIdx.x; i < jn * nmr; i += blockDim.x) {
       const int jj = i / nmr, rr = i - jj * nmr;
-      Tb[rr * n2 + j0 + jj] = w[jj * n1 + pmod(A.mrow_m[rr], n1)];
+      Tb[rr * n2p + j0 + jj] = w[ix(jj * n1 + pmod(A.mrow_m[rr], n1))];
     }
     __syncthreads();
   }
   // theta2 forward pass, extract the kept pairs
-  for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) W0[i] = Tb[i];
+  for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) {
+    const int rr = i / n2, jj = i - rr * n2;
+    W0[ix(i)] = Tb[rr * n2p + jj];
+  }
   __syncthreads();
   r = fft_any<T, N2>(W0, W1, A.p2, nmr, A.tw2, -1);
   for (int a = threadIdx.x; a < A.nA; a += blockDim.x)
-    Hc[a] = r[A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2)];
+    Hc[a] = r[ix(A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2))];
 }
 
 // --------------------------------------------------------------------------- host launcher
@@ -452,8 +467,8 @@ static FftDev to_dev(const FftPlan& p) {
 size_t slab_smem_bytes(const hw_ctx* ctx, size_t elem, int Jc) {
   const auto& hb = ctx->hb;
   const int nmr = (int)hb.mrow_m.size();
-  const size_t wsz = std::max((size_t)nmr * hb.prm.Nth2, (size_t)Jc * hb.prm.Nth1);
-  return elem * ((size_t)nmr * hb.prm.Nth2 + 2 * wsz);
+  const size_t wsz = (size_t)pd_size((int)std::max((size_t)nmr * hb.prm.Nth2, (size_t)Jc * hb.prm.Nth1));
+  return elem * ((size_t)nmr * (hb.prm.Nth2 + 1) + 2 * wsz);
 }
 
 int slab_pick_jc(const hw_ctx* ctx, size_t elem) {
