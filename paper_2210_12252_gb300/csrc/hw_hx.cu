@@ -114,10 +114,11 @@ __device__ cplx_t<T>* fft_batch(cplx_t<T>* src, cplx_t<T>* dst, const FftDev& pl
 __device__ __forceinline__ int pd(int i) { return i + (i >> 4); }
 __host__ __device__ inline int pd_size(int n) { return n + (n >> 4) + 1; }
 
-template <typename T, int N, int Ns>
+template <typename T, int N, int Ns, bool PAD>
 __device__ __forceinline__ void fft_ct_stages(cplx_t<T>*& src, cplx_t<T>*& dst, int nb,
                                               const cplx_t<T>* __restrict__ tw, int sign) {
   using V = cplx_t<T>;
+  auto pd = [](int i) { return PAD ? i + (i >> 4) : i; };
   if constexpr (Ns < N) {
     constexpr int Rem = N / Ns;
     constexpr int R = (Rem % 4 == 0) ? 4 : ((Rem % 3 == 0) ? 3 : 2);
@@ -175,16 +176,16 @@ __device__ __forceinline__ void fft_ct_stages(cplx_t<T>*& src, cplx_t<T>*& dst, 
     V* tmp = src;
     src = dst;
     dst = tmp;
-    fft_ct_stages<T, N, Ns * R>(src, dst, nb, tw, sign);
+    fft_ct_stages<T, N, Ns * R, PAD>(src, dst, nb, tw, sign);
   }
 }
 
-// length N at compile time when N > 0, else the runtime plan
-template <typename T, int N>
+// length N at compile time when N > 0, else the runtime plan; PAD: buffers addressed through pd
+template <typename T, int N, bool PAD>
 __device__ __forceinline__ cplx_t<T>* fft_any(cplx_t<T>* src, cplx_t<T>* dst, const FftDev& pl, int nb,
                                               const cplx_t<T>* __restrict__ tw, int sign) {
   if constexpr (N > 0) {
-    fft_ct_stages<T, N, 1>(src, dst, nb, tw, sign);
+    fft_ct_stages<T, N, 1, PAD>(src, dst, nb, tw, sign);
     return src;
   } else {
     return fft_batch<T>(src, dst, pl, nb, tw, sign);
@@ -376,15 +377,17 @@ constexpr int SLAB_THREADS = 256;
 template <typename T, int N1 = 0, int N2 = 0>
 __global__ void __launch_bounds__(SLAB_THREADS) k_slab(SlabArgs<T> A) {
   using V = cplx_t<T>;
-  constexpr bool PAD = N1 > 0;   // the specialised FFTs address their buffers through pd
+  // the specialised FP32 FFTs address their buffers through pd (16-byte FP64 elements spread
+  // over the banks already; padding them measured slower)
+  constexpr bool PAD = N1 > 0 && sizeof(T) == sizeof(float);
   auto ix = [](int i) { return PAD ? pd(i) : i; };
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = blockIdx.x, p = blockIdx.y;
   const int n1 = N1 > 0 ? N1 : A.Nth1, n2 = N2 > 0 ? N2 : A.Nth2, nmr = A.nmr;
   const int n2p = PAD ? n2 + 1 : n2;   // row stride of Tb
-  const int wsz = pd_size(max(nmr * n2, A.Jc * n1));
+  const int wsz = PAD ? pd_size(max(nmr * n2, A.Jc * n1)) : max(nmr * n2, A.Jc * n1);
   V* Tb = reinterpret_cast<V*>(smem_raw);     // [nmr][n2p]
-  V* W0 = Tb + nmr * (n2 + 1);
+  V* W0 = Tb + nmr * n2p;
   V* W1 = W0 + wsz;
   const V zero = mk<T>(T(0), T(0));
   const V* Gc = A.G + ((size_t)c * A.Nr + p) * A.nA;
@@ -395,7 +398,7 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab(SlabArgs<T> A) {
   for (int a = threadIdx.x; a < A.nA; a += blockDim.x)
     W0[ix(A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2))] = Gc[a];
   __syncthreads();
-  V* r = fft_any<T, N2>(W0, W1, A.p2, nmr, A.tw2, +1);
+  V* r = fft_any<T, N2, PAD>(W0, W1, A.p2, nmr, A.tw2, +1);
   for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) {
     const int rr = i / n2, jj = i - rr * n2;
     Tb[rr * n2p + jj] = r[ix(i)];
@@ -412,7 +415,7 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab(SlabArgs<T> A) {
       W0[ix(jj * n1 + pmod(A.mrow_m[rr], n1))] = Tb[rr * n2p + j0 + jj];
     }
     __syncthreads();
-    V* u = fft_any<T, N1>(W0, W1, A.p1, jn, A.tw1, +1);
+    V* u = fft_any<T, N1, PAD>(W0, W1, A.p1, jn, A.tw1, +1);
     for (int i = threadIdx.x; i < jn * n1; i += blockDim.x) {
       const T v = Vp[(size_t)j0 * n1 + i];
       V x = u[ix(i)];
@@ -421,7 +424,7 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab(SlabArgs<T> A) {
       u[ix(i)] = x;
     }
     __syncthreads();
-    V* w = fft_any<T, N1>(u, u == W0 ? W1 : W0, A.p1, jn, A.tw1, -1);
+    V* w = fft_any<T, N1, PAD>(u, u == W0 ? W1 : W0, A.p1, jn, A.tw1, -1);
     for (int i = threadIdx.x; i < jn * nmr; i += blockDim.x) {
       const int jj = i / nmr, rr = i - jj * nmr;
       Tb[rr * n2p + j0 + jj] = w[ix(jj * n1 + pmod(A.mrow_m[rr], n1))];
@@ -434,7 +437,7 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab(SlabArgs<T> A) {
     W0[ix(i)] = Tb[rr * n2p + jj];
   }
   __syncthreads();
-  r = fft_any<T, N2>(W0, W1, A.p2, nmr, A.tw2, -1);
+  r = fft_any<T, N2, PAD>(W0, W1, A.p2, nmr, A.tw2, -1);
   for (int a = threadIdx.x; a < A.nA; a += blockDim.x)
     Hc[a] = r[ix(A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2))];
 }
@@ -467,14 +470,21 @@ static FftDev to_dev(const FftPlan& p) {
 size_t slab_smem_bytes(const hw_ctx* ctx, size_t elem, int Jc) {
   const auto& hb = ctx->hb;
   const int nmr = (int)hb.mrow_m.size();
-  const size_t wsz = (size_t)pd_size((int)std::max((size_t)nmr * hb.prm.Nth2, (size_t)Jc * hb.prm.Nth1));
-  return elem * ((size_t)nmr * (hb.prm.Nth2 + 1) + 2 * wsz);
+  const int n1 = hb.prm.Nth1, n2 = hb.prm.Nth2;
+  // padded layout: the FP32 kernels specialised for the grid (k_slab's PAD)
+  const bool pad = elem == sizeof(float2) && slab_kernel<float>(n1, n2) != (void*)k_slab<float, 0, 0>;
+  const int w = std::max(nmr * n2, Jc * n1);
+  const size_t wsz = (size_t)(pad ? pd_size(w) : w);
+  return elem * ((size_t)nmr * (n2 + (pad ? 1 : 0)) + 2 * wsz);
 }
 
 int slab_pick_jc(const hw_ctx* ctx, size_t elem) {
-  // largest theta2 chunk whose shared memory fits in ~110 KB (two CTAs per SM)
+  // halve the column chunk while the slab's shared memory is above 110 KB (two CTAs per SM)
+  // and halving still shrinks it (the theta2 rows set a floor)
   int Jc = ctx->hb.prm.Nth2;
-  while (Jc > 1 && slab_smem_bytes(ctx, elem, Jc) > 110 * 1024) Jc = (Jc + 1) / 2;
+  while (Jc > 1 && slab_smem_bytes(ctx, elem, Jc) > 110 * 1024 &&
+         slab_smem_bytes(ctx, elem, (Jc + 1) / 2) < slab_smem_bytes(ctx, elem, Jc))
+    Jc = (Jc + 1) / 2;
   return Jc;
 }
 
