@@ -921,7 +921,9 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     }
     if (hyb_stall || (gemm.lowp && (maxres < lowp_thr || nclaim > 0 || it - lowp_best_it >= 4))) {
       // leave the FP32 (or hybrid) products: X re-orthonormalised and its H X recomputed in
-      // FP64, a Rayleigh-Ritz step on X alone, and the conjugate directions restarted
+      // FP64; the conjugate directions P kept, orthogonalised against the new X and
+      // orthonormalised in FP64 (H P transformed alongside); a Rayleigh-Ritz step on X alone;
+      // then this iteration starts over from the residuals (no step is lost)
       gemm.lowp = false;
       hyb_best = 1e300;
       hyb_best_it = it;
@@ -931,11 +933,53 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       if (hs != HW_OK) return hs;
       hs = apply_block(ctx, w, kidx, S, HS, 0, nb, true);
       if (hs != HW_OK) return hs;
-      hs = rr_on_x(cur);
+      if (np > 0) {
+        double2* P = S + (size_t)nb * Lpad;
+        double2* HP = HS + (size_t)nb * Lpad;
+        gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, np, (int)Lpad, 1.0, S, Lpad, sK, P, Lpad, sK, 0.0, w->C, nb,
+             (int64_t)2 * nb * nb, nk);
+        gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, np, nb, -1.0, S, Lpad, sK, w->C, nb, (int64_t)2 * nb * nb, 1.0, P,
+             Lpad, sK, nk);
+        gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, np, nb, -1.0, HS, Lpad, sK, w->C, nb, (int64_t)2 * nb * nb, 1.0,
+             HP, Lpad, sK, nk);
+        cudaMemcpyAsync(dnv, npv.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
+        gemm(CUBLAS_OP_C, CUBLAS_OP_N, np, np, (int)Lpad, 1.0, P, Lpad, sK, P, Lpad, sK, 0.0, w->G, np,
+             (int64_t)np * np, nk);
+        {
+          ProfScope ps_(ctx, HW_PH_OTHER);
+          k_pad_gram<<<dim3(8, nk), 256, 0, st>>>(w->G, np, dnv);
+          ctx->launches++;
+        }
+        {
+          ProfScope ps_(ctx, HW_PH_CHOL, nk * ((8.0 / 3.0) * np * (double)np * np + 8.0 * (double)Lpad * np * np));
+          dense_hermitize(st, w->G, np, nk);
+          dense_chol(st, w->G, np, nk, w->fail, false);
+          cudaError_t te = dense_trsm_lh(st, w->G, np, nk, P, Lpad, Lpad, sK, false, w->fail);
+          if (te == cudaSuccess) te = dense_trsm_lh(st, w->G, np, nk, HP, Lpad, Lpad, sK, false, w->fail);
+          if (te != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("P at the switch: ") + cudaGetErrorString(te));
+          ctx->launches += 4;
+        }
+        std::vector<int> f(nk);
+        cudaMemcpyAsync(f.data(), w->fail, nk * sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        bool pf = false;
+        for (int b = 0; b < nk; ++b) pf = pf || (f[b] && npv[b] > 0);
+        if (pf) {
+          np = 0;   // P not usable: restart the conjugate directions
+          std::fill(npv.begin(), npv.end(), 0);
+        }
+      }
+      hs = rr_on_x(cur);   // X, H X into the other buffer
       if (hs != HW_OK) return hs;
+      if (np > 0) {         // P, H P follow them
+        const int from = 1 - cur;
+        cudaMemcpy2DAsync(w->SB[cur] + (size_t)nb * Lpad, (size_t)sK * 16, w->SB[from] + (size_t)nb * Lpad,
+                          (size_t)sK * 16, (size_t)Lpad * np * 16, nk, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpy2DAsync(w->HSB[cur] + (size_t)nb * Lpad, (size_t)sK * 16, w->HSB[from] + (size_t)nb * Lpad,
+                          (size_t)sK * 16, (size_t)Lpad * np * 16, nk, cudaMemcpyDeviceToDevice, st);
+      }
       refreshed = true;
-      np = 0;
-      std::fill(npv.begin(), npv.end(), 0);
+      --it;   // the same iteration, from the residuals of the new X
       continue;
     }
     if (mixed && ((!refreshed && maxres < 1e-3) || nclaim > 0)) {
