@@ -292,6 +292,25 @@ def ours_main(args):
             hx[prec] = {"vec_per_s": round(ns / (t / 1e3), 1), "ms_per_call": round(float(t), 4),
                         "kernel_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in pr.items() if v[1]}}
         result["hx"] = hx
+        # ---- electron density from 64 states (the step after the solve)
+        dens = {}
+        occ = np.ones((1, ns))
+        for prec in ("fp64", "mixed"):
+            ctx.density([0], [Xb], occ, [1.0], prec=prec)
+            with torch.cuda.stream(stream):
+                evs = []
+                for _ in range(5):
+                    flush.fill_(1.0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ctx.density([0], [Xb], occ, [1.0], prec=prec)
+                    e1.record(stream)
+                    evs.append((e0, e1))
+            torch.cuda.synchronize(dev)
+            t = np.mean([a.elapsed_time(b) for a, b in evs])
+            dens[prec] = {"states_per_s": round(ns / (t / 1e3), 1), "ms_per_call": round(float(t), 4)}
+        result["density"] = {"workload": f"{w.name}, {ns} states", **dens}
         # ---- batched k-points: 32 eta points x 48 eigenpairs in one lockstep solve vs one by one
         result["batched_kpoints"] = batched_kpoints(hw, inputs, local, stream, flush, precond)
         # ---- H X on the large nanowire-like basis (L ~ 40.6k, 192 x 96 x 192 grid)

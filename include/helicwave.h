@@ -224,6 +224,22 @@ hw_status hw_solve_eigs_traced(hw_ctx* ctx, int k, int n_eig, int block, double 
 hw_status hw_heev(hw_ctx* ctx, int n, int nprob, int nw, const double* A, double* w, double* Z,
                   int method);
 
+/* Electron density on the real-space grid (Sec. "Convergence Studies", the electron-density
+ * equation): rho = (2 / Ncyc) sum_b w[b] sum_j occ[b*ns + j] |phi_{b,j}|^2, where phi_{b,j} is the
+ * inverse basis transform (eq. Naive_Inverse_Transform, by Algorithms 1-2) of column j of the
+ * state block X[b] at k-point kidx[b] (nu = 0: the sum over nu has one term).  X: nk device
+ * pointers to complex128 L_k x ns blocks with leading dimension ld; occ: host [nk*ns]
+ * occupations; w: host [nk] k-point weights (the Monkhorst-Pack weights 1/N_eta for a uniform
+ * set); rho: device, N_th1*N_th2*N_r doubles in eq. wavefun_storage_real order (the order of
+ * hw_set_potential), overwritten.  prec: HW_FP64 transforms, or HW_MIXED (FP32 transforms and
+ * FP32 accumulation of |phi|^2, FP64 sum over CTAs).  HW_EINVAL when one radial node's
+ * accumulator and transform buffers exceed 200 KB of shared memory at that precision (the
+ * 192 x 96 nanowire grid in FP64; its mixed density fits).  Synchronous.  The column weights
+ * are kept in a small device array of the context (allocated on first use, grown when
+ * needed). */
+hw_status hw_density(hw_ctx* ctx, int nk, const int* kidx, const double* const* X, int ns, int64_t ld,
+                     const double* occ, const double* w, double* rho, hw_prec prec);
+
 /* Gram product of the eigensolver's mixed form (Sec. "Eigensolvers and Preconditioning": the
  * Rayleigh-Ritz matrices S^H H S and the orthogonalisations): C_b = A_b^H B_b for nprob
  * problems, A_b: K x m, B_b: K x n complex128 column-major device blocks (leading dimensions
@@ -290,7 +306,8 @@ typedef enum {
   HW_PH_OTHER = 7,        /* residuals, gathers, padding                                     */
   HW_PH_MLP = 8,          /* preconditioner network (inference and training)                 */
   HW_PH_TRIDIAG = 9,      /* Householder reduction of the Rayleigh-Ritz matrix (FP32)        */
-  HW_NPHASE = 10
+  HW_PH_DENSITY = 10,     /* inverse angular passes and |phi|^2 accumulation of hw_density  */
+  HW_NPHASE = 11
 } hw_phase;
 
 /* Turn per-phase profiling on (enable != 0) or off; either resets the accumulators.  While on,

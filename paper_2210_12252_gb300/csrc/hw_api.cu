@@ -162,6 +162,7 @@ void hw_destroy(hw_ctx* ctx) {
     free_basis(ctx);
     mlp_free(ctx);
     if (ctx->dflag) cudaFree(ctx->dflag);
+    if (ctx->dens_w) cudaFree(ctx->dens_w);
     if (ctx->cublas) cublasDestroy(ctx->cublas);
   }
   delete ctx;
@@ -383,6 +384,56 @@ hw_status hw_apply_H(hw_ctx* ctx, int k, const double* X, double* Y, int ns, int
 hw_status hw_apply_H_batched(hw_ctx* ctx, int nk, const int* kidx, const double* const* X,
                              double* const* Y, int ns, int64_t ld, hw_prec prec) {
   return apply_common(ctx, nk, kidx, X, Y, ns, ld, prec);
+}
+
+hw_status hw_density(hw_ctx* ctx, int nk, const int* kidx, const double* const* X, int ns, int64_t ld,
+                     const double* occ, const double* w, double* rho, hw_prec prec) {
+  hw_status st = check_device_call(ctx);
+  if (st != HW_OK) return st;
+  if (nk < 1 || ns < 1 || !kidx || !X || !occ || !w || !rho) return hw_fail(ctx, HW_EINVAL, "bad density arguments");
+  if (prec != HW_FP64 && prec != HW_MIXED) return hw_fail(ctx, HW_EINVAL, "bad precision");
+  int64_t maxL = 0;
+  for (int b = 0; b < nk; ++b) {
+    if (kidx[b] < 0 || kidx[b] >= ctx->hb.nk) return hw_fail(ctx, HW_EINVAL, "k-point index out of range");
+    if (!X[b]) return hw_fail(ctx, HW_EINVAL, "null block pointer");
+    maxL = std::max(maxL, ctx->hb.L[kidx[b]]);
+  }
+  if (ld < maxL) return hw_fail(ctx, HW_EINVAL, "ld < L");
+  if (!density_fits(ctx, prec == HW_FP64 ? sizeof(double) : sizeof(float)))
+    return hw_fail(ctx, HW_EINVAL, "angular grid too large for the density kernel at this precision");
+  DeviceGuard g(ctx->device);
+  const size_t ncol = (size_t)nk * ns;
+  if (ctx->dens_w_n < ncol) {
+    if (ctx->dens_w) cudaFree(ctx->dens_w);
+    ctx->dens_w = nullptr;
+    ctx->dens_w_n = 0;
+    if (cudaMalloc((void**)&ctx->dens_w, ncol * sizeof(double)) != cudaSuccess)
+      return hw_fail(ctx, HW_ENOMEM, "density weights");
+    ctx->dens_w_n = ncol;
+  }
+  // column weight (2 / Ncyc) w_b occ_{b,j}
+  std::vector<double> wc(ncol);
+  const double f = 2.0 / ctx->hb.prm.ncyc;
+  for (int b = 0; b < nk; ++b)
+    for (int j = 0; j < ns; ++j) wc[(size_t)b * ns + j] = f * w[b] * occ[(size_t)b * ns + j];
+  cudaError_t e = cudaMemcpyAsync(ctx->dens_w, wc.data(), ncol * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+  const size_t G = (size_t)ctx->hb.prm.Nth1 * ctx->hb.prm.Nth2 * ctx->hb.prm.Nr;
+  if (e == cudaSuccess) e = cudaMemsetAsync(rho, 0, G * sizeof(double), ctx->stream);
+  for (int b0 = 0; b0 < nk && e == cudaSuccess; b0 += MAXSLOT) {
+    Blocks blk;
+    blk.nslot = std::min(MAXSLOT, nk - b0);
+    for (int i = 0; i < blk.nslot; ++i) {
+      blk.x[i] = X[b0 + i];
+      blk.y[i] = nullptr;
+      blk.kb[i] = kidx[b0 + i];
+    }
+    const double* wb = ctx->dens_w + (size_t)b0 * ns;
+    e = prec == HW_FP64 ? launch_density<double>(ctx, blk, ns, ld, wb, rho)
+                        : launch_density<float>(ctx, blk, ns, ld, wb, rho);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);   // wc must outlive the copy
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "density");
+  return HW_OK;
 }
 
 hw_status hw_apply_precond(hw_ctx* ctx, int k, const double* R, double* Z, int ns, int64_t ld,

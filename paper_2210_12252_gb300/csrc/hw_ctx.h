@@ -88,6 +88,8 @@ struct hw_ctx {
   hw::MlpState* mlp = nullptr;
   int* dflag = nullptr;        // device status word for bounded waits
   int64_t launches = 0;        // kernels of this library launched on the stream
+  double* dens_w = nullptr;    // column weights of hw_density (grown when needed)
+  size_t dens_w_n = 0;
   int rr_method = 0;           // HW_OPT_RR_METHOD
   int lowp_exp = 5;            // HW_OPT_LOWP_SWITCH
   int gram_mixed = 0;          // HW_OPT_GRAM_KERNEL
@@ -117,6 +119,9 @@ namespace hw {
 template <typename T>
 cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld);
 cudaError_t hx_configure(hw_ctx* ctx);
+bool density_fits(const hw_ctx* ctx, size_t tsz);
+template <typename T>
+cudaError_t launch_density(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, const double* wcol, double* rho);
 cudaError_t hx_autotune(hw_ctx* ctx, int k, int ns, std::vector<float>& log);
 template <typename T>
 cudaError_t launch_hx_into(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, void* gbuf, void* hbuf, int cols);

@@ -636,6 +636,180 @@ cudaError_t launch_hx_into(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, v
 template cudaError_t launch_hx_into<double>(hw_ctx*, const Blocks&, int, int64_t, void*, void*, int);
 template cudaError_t launch_hx_into<float>(hw_ctx*, const Blocks&, int, int64_t, void*, void*, int);
 
+// --------------------------------------------------------------------------- electron density
+// rho(theta1, theta2, r) += w_c |phi_c|^2 over columns (states) c (Sec. "Convergence Studies",
+// the electron-density equation): the inverse radial transform is k_radial_inv; this kernel
+// takes each column's (r_p, pair) values through the same inverse angular passes as k_slab
+// and accumulates w_c |u|^2 for its radial node in shared memory, then adds the slab into rho
+// ([i][j][p] order, like the potential handed to hw_set_potential).
+template <typename T>
+struct DensArgs {
+  int Nr, Nth1, Nth2, nA, nmr, ncols, Jc, cpg;   // cpg: columns per CTA (blockIdx.y groups)
+  FftDev p1, p2;
+  const int* pair_n;
+  const int* pair_mrow;
+  const int* mrow_m;
+  const cplx_t<T>* tw1;
+  const cplx_t<T>* tw2;
+  const cplx_t<T>* G;     // [column][r_p][pair] of this pass
+  const double* wcol;     // [column] weight of each column of this pass
+  double* rho;            // [N_th1][N_th2][N_r]
+};
+
+__host__ __device__ inline size_t dens_acc_bytes(int n1, int n2, size_t tsz) {
+  return ((size_t)n1 * n2 * tsz + 15) & ~size_t(15);
+}
+
+template <typename T, int N1 = 0, int N2 = 0>
+__global__ void __launch_bounds__(SLAB_THREADS) k_density(DensArgs<T> A) {
+  using V = cplx_t<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = blockIdx.x, grp = blockIdx.y;
+  const int n1 = N1 > 0 ? N1 : A.Nth1, n2 = N2 > 0 ? N2 : A.Nth2, nmr = A.nmr;
+  T* acc = reinterpret_cast<T*>(smem_raw);                                      // [n2][n1]
+  V* Tb = reinterpret_cast<V*>(smem_raw + dens_acc_bytes(n1, n2, sizeof(T)));   // [nmr][n2]
+  const int wsz = max(nmr * n2, A.Jc * n1);
+  V* W0 = Tb + nmr * n2;
+  V* W1 = W0 + wsz;
+  const V zero = mk<T>(T(0), T(0));
+  for (int i = threadIdx.x; i < n1 * n2; i += blockDim.x) acc[i] = T(0);
+  const int cbeg = grp * A.cpg, cend = min(A.ncols, cbeg + A.cpg);
+  for (int c = cbeg; c < cend; ++c) {
+    const T wc = (T)A.wcol[c];
+    if (wc == T(0)) continue;   // uniform over the CTA
+    const V* Gc = A.G + ((size_t)c * A.Nr + p) * A.nA;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) W0[i] = zero;
+    __syncthreads();
+    for (int a = threadIdx.x; a < A.nA; a += blockDim.x)
+      W0[A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2)] = Gc[a];
+    __syncthreads();
+    V* r = fft_any<T, N2, false>(W0, W1, A.p2, nmr, A.tw2, +1);
+    for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) Tb[i] = r[i];
+    __syncthreads();
+    for (int j0 = 0; j0 < n2; j0 += A.Jc) {
+      const int jn = min(A.Jc, n2 - j0);
+      for (int i = threadIdx.x; i < jn * n1; i += blockDim.x) W0[i] = zero;
+      __syncthreads();
+      for (int i = threadIdx.x; i < jn * nmr; i += blockDim.x) {
+        const int jj = i / nmr, rr = i - jj * nmr;
+        W0[jj * n1 + pmod(A.mrow_m[rr], n1)] = Tb[rr * n2 + j0 + jj];
+      }
+      __syncthreads();
+      V* u = fft_any<T, N1, false>(W0, W1, A.p1, jn, A.tw1, +1);
+      for (int i = threadIdx.x; i < jn * n1; i += blockDim.x) {
+        const V x = u[i];
+        acc[j0 * n1 + i] += wc * (x.x * x.x + x.y * x.y);
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n1 * n2; t += blockDim.x) {
+    const int j = t / n1, i = t - j * n1;
+    atomicAdd(&A.rho[((size_t)i * n2 + j) * A.Nr + p], (double)acc[t]);
+  }
+}
+
+template <typename T>
+static void* density_kernel(int n1, int n2) {
+  if (n1 == 64 && n2 == 48) return (void*)k_density<T, 64, 48>;
+  if (n1 == 192 && n2 == 96) return (void*)k_density<T, 192, 96>;
+  return (void*)k_density<T, 0, 0>;
+}
+
+static size_t density_smem_bytes(const hw_ctx* ctx, size_t tsz, int Jc) {
+  const auto& hb = ctx->hb;
+  const int nmr = (int)hb.mrow_m.size(), n1 = hb.prm.Nth1, n2 = hb.prm.Nth2;
+  const size_t w = (size_t)std::max(nmr * n2, Jc * n1);
+  return dens_acc_bytes(n1, n2, tsz) + 2 * tsz * ((size_t)nmr * n2 + 2 * w);
+}
+
+// whether the density kernel's shared memory fits for this basis (arithmetic of size tsz)
+bool density_fits(const hw_ctx* ctx, size_t tsz) { return density_smem_bytes(ctx, tsz, 1) <= 200 * 1024; }
+
+// rho += sum over the columns of blk (ns per block) of wcol[column] |phi_column|^2; wcol is a
+// device array of blk.nslot * ns weights; rho must hold N_th1 N_th2 N_r doubles.
+template <typename T>
+cudaError_t launch_density(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, const double* wcol, double* rho) {
+  auto& hb = ctx->hb;
+  auto& db = ctx->db;
+  const DevTables<T>& tb = *reinterpret_cast<const DevTables<T>*>(
+      sizeof(T) == 8 ? (const void*)&db.t64 : (const void*)&db.t32);
+  const int ncols_total = blk.nslot * ns;
+  const int chunk = (int)ctx->ws.cols;
+  if (chunk <= 0 || blk.nslot > MAXSLOT) return cudaErrorInvalidValue;
+  const int Nr = hb.prm.Nr, K = hb.K;
+  int Jc = hb.prm.Nth2;
+  while (Jc > 1 && density_smem_bytes(ctx, sizeof(T), Jc) > 200 * 1024 &&
+         density_smem_bytes(ctx, sizeof(T), (Jc + 1) / 2) < density_smem_bytes(ctx, sizeof(T), Jc))
+    Jc = (Jc + 1) / 2;
+  const size_t sm = density_smem_bytes(ctx, sizeof(T), Jc);
+  if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  int maxna = 0;
+  for (int g = 0; g <= hb.N; ++g) maxna = std::max(maxna, hb.group_start[g + 1] - hb.group_start[g]);
+  void* kf = density_kernel<T>(hb.prm.Nth1, hb.prm.Nth2);
+  cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  for (int c0 = 0; c0 < ncols_total; c0 += chunk) {
+    const int nc = std::min(chunk, ncols_total - c0);
+    RadArgs<T> ra;
+    ra.Nr = Nr;
+    ra.K = K;
+    ra.nA = hb.nA;
+    ra.ncols = nc;
+    ra.ns = ns;
+    ra.c0 = c0;
+    ra.group_start = db.group_start;
+    ra.off = db.off;
+    ra.Ka = db.Ka;
+    ra.ld = ld;
+    ra.ke = db.ke;
+    for (int i = 0; i < blk.nslot; ++i) ra.keoff[i] = db.ke_off[blk.kb[i]];
+    ra.blk = blk;
+    ra.gh = reinterpret_cast<cplx_t<T>*>(ctx->ws.gbuf);
+    ra.rtab = tb.rinv;
+    dim3 grid((unsigned)(((long)maxna * nc + RAD_Q - 1) / RAD_Q), hb.N + 1);
+    const size_t sm_inv = ((size_t(Nr) * K * sizeof(T) + 15) & ~size_t(15)) +
+                          (size_t)K * RAD_Q * sizeof(cplx_t<T>);
+    {
+      ProfScope ps(ctx, HW_PH_RADIAL_INV);
+      k_radial_inv<T><<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra);
+      ctx->launches++;
+    }
+    DensArgs<T> da;
+    da.Nr = Nr;
+    da.Nth1 = hb.prm.Nth1;
+    da.Nth2 = hb.prm.Nth2;
+    da.nA = hb.nA;
+    da.nmr = (int)hb.mrow_m.size();
+    da.ncols = nc;
+    da.Jc = Jc;
+    const int ncg = std::max(1, std::min(nc, (2 * 152 + Nr - 1) / Nr));
+    da.cpg = (nc + ncg - 1) / ncg;
+    da.p1 = to_dev(ctx->plan1);
+    da.p2 = to_dev(ctx->plan2);
+    da.pair_n = db.pair_n;
+    da.pair_mrow = db.pair_mrow;
+    da.mrow_m = db.mrow_m;
+    da.tw1 = reinterpret_cast<const cplx_t<T>*>(tb.tw1);
+    da.tw2 = reinterpret_cast<const cplx_t<T>*>(tb.tw2);
+    da.G = reinterpret_cast<const cplx_t<T>*>(ctx->ws.gbuf);
+    da.wcol = wcol + c0;
+    da.rho = rho;
+    void* args[] = {(void*)&da};
+    {
+      ProfScope ps(ctx, HW_PH_DENSITY);
+      e = cudaLaunchKernel(kf, dim3(Nr, (nc + da.cpg - 1) / da.cpg), dim3(SLAB_THREADS), args, sm, ctx->stream);
+      ctx->launches++;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_density<double>(hw_ctx*, const Blocks&, int, int64_t, const double*, double*);
+template cudaError_t launch_density<float>(hw_ctx*, const Blocks&, int, int64_t, const double*, double*);
+
 // opt in to large dynamic shared memory for every instantiation (called once at setup)
 cudaError_t hx_configure(hw_ctx* ctx) {
   cudaError_t e = cudaSuccess;

@@ -71,6 +71,8 @@ _SIGS = {
                               C.POINTER(C.c_int)]),
     "hw_heev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                           C.c_int]),
+    "hw_density": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_void_p), C.c_int, C.c_int64,
+                             _D, _D, C.c_void_p, C.c_int]),
     "hw_gram": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_int64,
                           C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_int64]),
     "hw_profile": (C.c_int, [C.c_void_p, C.c_int]),
@@ -92,7 +94,8 @@ _SIGS = {
 
 MLP_NPARAM = 4673
 
-PHASES = ["radial_inv", "slab", "radial_fwd", "precond", "gemm", "chol", "eig", "other", "mlp", "tridiag"]
+PHASES = ["radial_inv", "slab", "radial_fwd", "precond", "gemm", "chol", "eig", "other", "mlp", "tridiag",
+          "density"]
 
 _lib = None
 
@@ -253,6 +256,18 @@ HW_OPT_HYBRID = 4
 
 def hw_set_option(h, option, value):
     _check(h, load_library().hw_set_option(h, option, value))
+
+
+def hw_density(h, kidx, X, ns, ld, occ, w, rho_ptr, prec=HW_FP64):
+    """rho (device pointer, N_th1*N_th2*N_r doubles) = (2/Ncyc) sum_b w[b] sum_j occ[b][j] |phi_bj|^2."""
+    nk = len(kidx)
+    ki = (C.c_int * nk)(*[int(k) for k in kidx])
+    xp = (C.c_void_p * nk)(*[int(x) for x in X])
+    occ = np.ascontiguousarray(occ, dtype=np.float64).reshape(-1)
+    w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1)
+    if occ.size != nk * ns or w.size != nk:
+        raise ValueError("occ must hold nk*ns values and w nk")
+    _check(h, load_library().hw_density(h, nk, ki, xp, ns, ld, _dptr(occ), _dptr(w), C.c_void_p(rho_ptr), prec))
 
 
 def hw_gram(h, A, B):
@@ -490,6 +505,18 @@ class Context:
 
     def synchronize(self):
         hw_synchronize(self.h)
+
+    def density(self, kidx, X, occ, w, prec="fp64"):
+        """Electron density from state blocks X[b] (torch complex128 (ns, ld) on the device),
+        occupations occ (nk, ns) and k-point weights w (nk); returns a device tensor of shape
+        (N_th1, N_th2, N_r) (the potential's order)."""
+        import torch
+        code = {"fp64": HW_FP64, "mixed": HW_MIXED}[prec]
+        ns, ld = X[0].shape
+        g = (self.geom.Nth1, self.geom.Nth2, self.geom.Nr)
+        rho = torch.empty(g, dtype=torch.float64, device=X[0].device)
+        hw_density(self.h, list(kidx), [x.data_ptr() for x in X], ns, ld, occ, w, rho.data_ptr(), code)
+        return rho
 
     def set_option(self, option, value):
         hw_set_option(self.h, option, value)
