@@ -12,7 +12,8 @@ Follows arXiv 2210.12252:
     N_theta ~ 4*M_max+1, N_r = 4*K_max);
   * kinetic-energy cutoff and mask: eq. Energy_cutoff and the mask definition after it,
     "modified appropriately" at each (eta, nu);
-  * reciprocal-space diagonal terms: eq. constants_abc and Algorithm 5 (the a, b, c terms).
+  * reciprocal-space diagonal terms: eq. constants_abc and Algorithm 5 (the a, b, c terms);
+  * the 1/r^2 integrals I(n, k, k'): eq. I_nkk_prime.
 
 Readings taken where the paper is silent (also listed in the design notes):
   R3  the basis box follows from the grids: M = floor((N_th1-1)/s), N = floor((N_th2-1)/s),
@@ -22,6 +23,8 @@ Readings taken where the paper is silent (also listed in the design notes):
       relative slack of 1e-12 guards against rounding flips.
   R6  Gauss-Jacobi with (alpha, beta) = (0, 1) on x in [-1, 1], r = R(1+x)/2, and the radial
       weights omega_r = (R^2/4) w absorb the r dr of the inner product.
+  I0  for nu != 0 the table I(0, k, k') of eq. I_nkk_prime is a divergent integral (J_0 does not
+      vanish at r = 0); it is replaced by its value under the radial rule above, and flagged.
 """
 from __future__ import annotations
 
@@ -175,6 +178,37 @@ class Basis:
         ph = np.exp(2j * np.pi * (m * np.asarray(th1) + n * self.ncyc * np.asarray(th2)))
         return ph * self.xi(n, k, r)
 
+    def itable(self, n):
+        """K x K table I(n, k, k') of eq. I_nkk_prime (k, k' 0-based), the radial integral of the
+        1/r^2 terms (eqs. ell_coeff and ell_mnk):
+
+            I(n, k, k') = int_0^1 J_p(b_k q) J_p(b_k' q) / q dq / (J_{p+1}(b_k) J_{p+1}(b_k')),
+
+        p = n Ncyc, b_k = b_k^p.  For p != 0 the integrand is smooth (it behaves as q^(2|p|-1)) and
+        the integral is taken as written by Gauss-Legendre quadrature on [0, 1] with enough nodes
+        for the band limit b_k + b_k' (the paper's recurrence of Appendix D only serves to remove
+        the 1/q, which plain Gauss-Legendre does not need).  For p = 0 the integral diverges at
+        q = 0; reading: it is replaced by the transform's own radial rule, sum_p w_p J J / r_p^2
+        (nodes avoid r = 0, so the value is finite), and KPoint.n0_quadrature flags its use."""
+        cache = self.__dict__.setdefault("_itable_cache", {})
+        if n in cache:
+            return cache[n]
+        p = n * self.ncyc
+        zs = self.zeros[abs(n)]
+        jp1 = special.jv(p + 1, zs)
+        if p == 0:
+            Jr = special.jv(0, np.outer(self.r / self.R, zs))            # [Nr, K]
+            integ = (Jr * (self.wr / self.r ** 2)[:, None]).T @ Jr
+        else:
+            nq = 64 + 2 * int(math.ceil(zs[-1]))
+            x, w = np.polynomial.legendre.leggauss(nq)
+            q = 0.5 * (x + 1.0)
+            w = 0.5 * w
+            Jq = special.jv(p, np.outer(q, zs))                          # [nq, K]
+            integ = (Jq * (w / q)[:, None]).T @ Jq
+        cache[n] = integ / np.outer(jp1, jp1)
+        return cache[n]
+
     def lambda0(self, m, n, k):
         """eq. Laplacian_of_f_mnk."""
         b = np.vectorize(self.bzero)(n, k)
@@ -222,9 +256,6 @@ class KPoint:
     """One (eta, nu) point with its cutoff mask; compact order = box order restricted to the mask."""
 
     def __init__(self, basis: Basis, eta: float, nu: float, ecut: float | None):
-        if nu != 0:
-            # the 1/r^2 terms (eqs. ell_mnk, I_nkk_prime) are not part of this oracle
-            raise NotImplementedError("nu != 0 needs the I(n,k,k') terms")
         self.basis = basis
         self.eta = float(eta)
         self.nu = float(nu)
@@ -235,6 +266,9 @@ class KPoint:
         m, n, k = basis.box_mnk()
         self.m, self.n, self.k = m[self.idx], n[self.idx], k[self.idx]
         self.ke = basis.kinetic(eta, nu)[self.idx]
+        # nu != 0 with n = 0 modes kept: their 1/r^2 integrals diverge and take the radial-rule
+        # value (see Basis.itable)
+        self.n0_quadrature = bool(self.nu != 0 and np.any(self.n == 0))
 
     def to_box(self, Xc):
         Xc = np.asarray(Xc)

@@ -16,8 +16,10 @@ dense_H_conv  the same matrix written out as D + B^H W diag(V) B, with the angul
               columns would be too slow.
 eigh_lowest   direct diagonalisation (numpy.linalg.eigh).
 
-The 1/r^2 terms that appear when nu != 0 (eqs. ell_mnk, I_nkk_prime and the I_n loop of
-Algorithm 5) are not implemented: every workload here has nu = 0.
+For nu != 0 the 1/r^2 terms are added as in the I_n loop of Algorithm 5: per angular pair,
+T = (nu^2/R^2) Zhat + (i nu/(pi R^2)) Qhat with Zhat = I_n applied to the pair's radial
+coefficients and Qhat = I_n applied to (i 2 pi n Ncyc) times them (eqs. ell_mnk and the
+expression for the sixth term after it), I_n from Basis.itable.
 """
 from __future__ import annotations
 
@@ -28,8 +30,6 @@ from . import transforms
 
 def apply_H_box(basis, V, eta, nu, Xbox):
     """Algorithm 5 on box vectors.  Xbox: (box_size,) or (box_size, ns) complex."""
-    if nu != 0:
-        raise NotImplementedError("nu != 0: I_n term not implemented")
     X = np.asarray(Xbox, dtype=np.complex128)
     one = X.ndim == 1
     if one:
@@ -48,8 +48,27 @@ def apply_H_box(basis, V, eta, nu, Xbox):
         y = y - a * Z - b * P - c * Q
         Zr = transforms.fast_inverse(basis, Z.reshape(basis.box_shape))
         y = y + transforms.fast_forward(basis, Zr * V).ravel()
+        if nu != 0:
+            y = y + _inverse_square_terms(basis, nu, Z, Q)
         Y[:, j] = y
     return Y[:, 0] if one else Y
+
+
+def _inverse_square_terms(basis, nu, Z, Q):
+    """The I_n loop of Algorithm 5 on one box vector: for every pair (m, n), the K radial
+    coefficients i .. i+K-1 give T = (nu^2/R^2) Zhat + (i nu/(pi R^2)) Qhat, Zhat_k' =
+    sum_k Z_k I(n, k, k'), Qhat_k' = sum_k Q_k I(n, k, k'), Q = (i 2 pi n Ncyc) Z."""
+    Zb = Z.reshape(basis.box_shape)
+    Qb = Q.reshape(basis.box_shape)
+    T = np.zeros(basis.box_shape, dtype=np.complex128)
+    R2 = basis.R ** 2
+    for n in range(-basis.N, basis.N + 1):
+        I = basis.itable(n)
+        i = n + basis.N
+        Zhat = Zb[:, i, :] @ I          # rows: m; columns: k'
+        Qhat = Qb[:, i, :] @ I
+        T[:, i, :] = (nu ** 2 / R2) * Zhat + (1j * nu / (np.pi * R2)) * Qhat
+    return T.ravel()
 
 
 def apply_H(kp, V, Xc):
@@ -78,6 +97,18 @@ def dense_H_conv(kp, V):
         Xi[:, sel] = basis.Rtab[n][:, kp.k[sel]]
     dm = (kp.m[:, None] - kp.m[None, :]) % basis.Nth1
     dn = (kp.n[:, None] - kp.n[None, :]) % basis.Nth2
+    if kp.nu != 0:
+        # the 1/r^2 terms: same (m, n), coefficient (nu^2 - 2 nu n Ncyc)/R^2 times I(n, k, k')
+        # (the two terms of the I_n loop of Algorithm 5 with i nu/(pi R^2) (i 2 pi n Ncyc)
+        # = -2 nu n Ncyc/R^2)
+        same = (kp.m[:, None] == kp.m[None, :]) & (kp.n[:, None] == kp.n[None, :])
+        coef = (kp.nu ** 2 - 2 * kp.nu * kp.n * basis.ncyc) / basis.R ** 2
+        tabs = {n: basis.itable(n) for n in np.unique(kp.n)}
+        Ik = np.zeros((L, L))
+        for n, I in tabs.items():
+            sel = np.nonzero(kp.n == n)[0]
+            Ik[np.ix_(sel, sel)] = I[np.ix_(kp.k[sel], kp.k[sel])]
+        H += np.where(same, Ik * coef[None, :], 0.0)
     pref = 2 * np.pi * basis.tau / basis.ncyc
     for p in range(basis.Nr):
         Vhat = np.fft.fft2(np.asarray(V[:, :, p]).T) / (basis.Nth1 * basis.Nth2)   # [n, m]

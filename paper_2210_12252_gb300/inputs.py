@@ -39,6 +39,7 @@ class Workload:
     n_eig: int
     seed: int
     ecuts: np.ndarray | None = None    # optional per-k-point cutoff (uneven-basis stressor)
+    nus: np.ndarray | None = None      # cyclic wavenumbers nu_b (None: all zero)
     notes: str = ""
     extra: dict = field(default_factory=dict)
 
@@ -116,6 +117,27 @@ def tiny_s2(seed=1):
     g = Geometry(**{**GEOM_TINY.__dict__, "oversample": 2})
     atoms = ring_atoms(4, 2.5, g.tau, 4.0, 0.8, seed)
     return Workload("tiny_R6_16x16x24_s2", g, atoms, np.array([0.0]), 8, seed)
+
+
+def tiny_cyclic(seed=1, ncyc=3):
+    """The tiny geometry with an Ncyc-fold cyclic symmetry (theta2 spans 1/Ncyc of a turn): 4
+    wells (Z=4, sigma=0.8) at r=2.5 per fundamental domain, repeated by the cyclic rotations;
+    k-points (eta, nu) = (0.1, 1), (-0.3, 2), (0.25, 0); 8 eigenpairs."""
+    g = Geometry(**{**GEOM_TINY.__dict__, "ncyc": ncyc})
+    atoms = ring_atoms(4, 2.5, g.tau, 4.0, 0.8, seed)
+    return Workload(f"tiny_c{ncyc}_R6_16x16x24", g, atoms, np.array([0.1, -0.3, 0.25]), 8, seed,
+                    nus=np.array([1.0, 2.0, 0.0]))
+
+
+def tube_cyclic(seed=4, ncyc=3, nk=3):
+    """The tube geometry (R=12, tau=4.6, alpha=0.05, 64x48x96 grid, 30 Ha) with a 3-fold cyclic
+    symmetry: 40 wells (Z=4, sigma=0.8) on r=6 in a chiral lattice per fundamental domain;
+    one k-point per nu = 0..nk-1 at seeded eta ~ U[-1/2, 1/2); 32 eigenpairs each."""
+    g = Geometry(**{**GEOM_TUBE.__dict__, "ncyc": ncyc})
+    atoms = chiral_lattice_atoms(40, 6.0, g.tau, 4.0, 0.8, seed)
+    etas = _rng(seed + 1).uniform(-0.5, 0.5, nk)
+    nus = np.arange(nk, dtype=np.float64) % ncyc
+    return Workload(f"tube_c{ncyc}_{nk}k", g, atoms, etas, 32, seed, nus=nus)
 
 
 def tube(seed=2):

@@ -45,6 +45,32 @@ def main(which):
 workload {w.name} (inputs.tiny(seed=1{', zero_potential=True' if zero else ''})), eta = 0, nu = 0
 basis L = {kp.L}; all eigenvalues of the dense Hamiltonian (Algorithm 5 columns), Hartree
 source: oracle.hamiltonian.dense_H + numpy.linalg.eigh""", ev)
+    if "cyclic" in which:
+        w = inputs.tiny_cyclic()
+        b = basis_of(w.geom)
+        V = P.gaussian_wells(b, w.atoms)
+        for i, (eta, nu) in enumerate(zip(w.etas, w.nus)):
+            kp = B.KPoint(b, eta, nu, w.geom.ecut)
+            ev = np.linalg.eigvalsh(Hm.dense_H(kp, V))
+            write(f"tiny_c3_k{i}_eigs.txt", f"""
+workload {w.name} (inputs.tiny_cyclic(seed=1, ncyc=3)), k-point {i}: eta = {eta!r}, nu = {nu!r}
+basis L = {kp.L}; all eigenvalues of the dense Hamiltonian (Algorithm 5 columns with the I_n
+loop; for nu != 0 the n = 0 table is the radial-rule value), Hartree
+source: oracle.hamiltonian.dense_H + numpy.linalg.eigh""", ev)
+    if "tube_cyclic" in which:
+        w = inputs.tube_cyclic()
+        b = basis_of(w.geom)
+        V = P.gaussian_wells(b, w.atoms)
+        for i, (eta, nu) in enumerate(zip(w.etas, w.nus)):
+            kp = B.KPoint(b, eta, nu, w.geom.ecut)
+            t = time.time()
+            ev = np.linalg.eigvalsh(Hm.dense_H_conv(kp, V))[:64]
+            print("k-point", i, "L", kp.L, time.time() - t)
+            write(f"tube_c3_k{i}_eigs.txt", f"""
+workload {w.name} (inputs.tube_cyclic(seed=4, ncyc=3, nk=3)), k-point {i}: eta = {eta!r}, nu = {nu!r}
+basis L = {kp.L}; lowest 64 eigenvalues of the dense Hamiltonian, Hartree
+source: oracle.hamiltonian.dense_H_conv (convolution form of Algorithm 5 with the I_n loop)
++ numpy.linalg.eigh""", ev)
     if "tube" in which:
         w = inputs.tube()
         b = basis_of(w.geom)
@@ -62,4 +88,4 @@ source: oracle.hamiltonian.dense_H_conv (convolution form of Algorithm 5) + nump
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["tiny", "tube"])
+    main(sys.argv[1:] or ["tiny", "cyclic", "tube", "tube_cyclic"])
