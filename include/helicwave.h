@@ -86,7 +86,12 @@ const char* hw_last_error(const hw_ctx* ctx);
 /* Basis set, radial quadrature, tables and cutoff masks for nk points (eta_b, nu_b)
  * (eqs. Phi_expanded_in_basis_set, Basis_fun_derived, Energy_cutoff; Sec. eta-space
  * discretization).  ecut_per_k (host, nullable) overrides params->ecut per point.
- * nu must be 0 (the 1/r^2 terms of eqs. ell_mnk and I_nkk_prime are not built).
+ * nu (host, [nk], nullable = all 0): the cyclic wavenumbers, physically 0 .. Ncyc-1 (any
+ * finite value is accepted).  For nu != 0 H carries the 1/r^2 terms of eqs. ell_mnk and
+ * I_nkk_prime; their radial integrals are tabulated here per |n| (a Gauss-Jacobi rule fine
+ * enough for the Bessel products).  For n = 0 that integral diverges at r = 0 (J_0 does not
+ * vanish there), and the table takes the value of the transform's radial rule instead: the
+ * n = 0 modes of a nu != 0 point are then a finite but grid-dependent approximation.
  * L_out (host, [nk]) receives the masked basis sizes.  Replaces any earlier basis. */
 hw_status hw_setup_basis(hw_ctx* ctx, const hw_basis_params* params, int nk, const double* eta,
                          const double* nu, const double* ecut_per_k, int64_t* L_out);
@@ -110,6 +115,12 @@ hw_status hw_get_kinetic(const hw_ctx* ctx, int k, double* ke);
 /* Radial table xi_{n,k}(r_p) for angular order n (host output [Nr*K], p-major). */
 hw_status hw_get_radial_table(const hw_ctx* ctx, int n, double* table);
 
+/* Table I(n, k, k') of eq. I_nkk_prime for angular order n (host output [K*K], symmetric),
+ * the radial integral of the nu != 0 terms: (nu^2 - 2 nu n Ncyc)/R^2 I(n, k, k') couples the
+ * coefficients (m, n, k) and (m, n, k').  For n = 0 the integral diverges; the value returned
+ * (and used) is that of the transform's radial rule (see hw_setup_basis). */
+hw_status hw_get_itable(const hw_ctx* ctx, int n, double* table);
+
 /* Install the real potential V on the grid (eq. wavefun_storage_real order, length
  * N_th1*N_th2*N_r).  on_device != 0: V is a device pointer (copied on the stream), else a
  * host pointer (copied synchronously). */
@@ -125,7 +136,8 @@ hw_status hw_set_potential(hw_ctx* ctx, const double* V, int on_device);
 hw_status hw_build_potential(hw_ctx* ctx, int n_atoms, const double* atoms, double* V_out);
 
 /* Y = H X at k-point k (Algorithm 5): reciprocal-space diagonal terms, inverse transform
- * (Algorithms 1-2), pointwise V, forward transform (Algorithms 3-4).  X, Y: device,
+ * (Algorithms 1-2), pointwise V, forward transform (Algorithms 3-4), and for nu != 0 the
+ * 1/r^2 terms (nu^2 - 2 nu n Ncyc)/R^2 I(n, k, k') within each (m, n) (the I_n loop).  X, Y: device,
  * complex128, L_k x ns, leading dimension ld.  X and Y must not overlap. */
 hw_status hw_apply_H(hw_ctx* ctx, int k, const double* X, double* Y, int ns, int64_t ld,
                      hw_prec prec);
@@ -227,7 +239,8 @@ hw_status hw_heev(hw_ctx* ctx, int n, int nprob, int nw, const double* A, double
 /* Electron density on the real-space grid (Sec. "Convergence Studies", the electron-density
  * equation): rho = (2 / Ncyc) sum_b w[b] sum_j occ[b*ns + j] |phi_{b,j}|^2, where phi_{b,j} is the
  * inverse basis transform (eq. Naive_Inverse_Transform, by Algorithms 1-2) of column j of the
- * state block X[b] at k-point kidx[b] (nu = 0: the sum over nu has one term).  X: nk device
+ * state block X[b] at k-point kidx[b] (the sum over (eta, nu) points is the sum over b, with the
+ * weights w; for Ncyc > 1 pass every nu).  X: nk device
  * pointers to complex128 L_k x ns blocks with leading dimension ld; occ: host [nk*ns]
  * occupations; w: host [nk] k-point weights (the Monkhorst-Pack weights 1/N_eta for a uniform
  * set); rho: device, N_th1*N_th2*N_r doubles in eq. wavefun_storage_real order (the order of

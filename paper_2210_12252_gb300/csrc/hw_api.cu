@@ -98,8 +98,8 @@ void free_basis(hw_ctx* ctx) {
   dfree(db.ke);
   dfree(db.vscratch);
   db.ke_off.clear();
-  for (auto* t : {&db.t64.rinv, &db.t64.rfwd, &db.t64.V, &db.t64.tw1, &db.t64.tw2}) dfree(*t);
-  for (auto* t : {&db.t32.rinv, &db.t32.rfwd, &db.t32.V, &db.t32.tw1, &db.t32.tw2}) dfree(*t);
+  for (auto* t : {&db.t64.rinv, &db.t64.rfwd, &db.t64.qtab, &db.t64.V, &db.t64.tw1, &db.t64.tw2}) dfree(*t);
+  for (auto* t : {&db.t32.rinv, &db.t32.rfwd, &db.t32.qtab, &db.t32.V, &db.t32.tw1, &db.t32.tw2}) dfree(*t);
   dfree(ctx->ws.gbuf);
   dfree(ctx->ws.hbuf);
   ctx->ws.cols = 0;
@@ -199,6 +199,7 @@ hw_status hw_setup_basis(hw_ctx* ctx, const hw_basis_params* params, int nk, con
           rfwd[((size_t)n * K + k) * Nr + p] = scale * hb.wr[p] * x;
         }
     std::vector<float> rinv32(rinv.begin(), rinv.end()), rfwd32(rfwd.begin(), rfwd.end());
+    std::vector<float> qtab32(hb.qtab.begin(), hb.qtab.end());
     std::vector<double> tw1 = twiddles(params->Nth1), tw2 = twiddles(params->Nth2);
     std::vector<float> tw1f(tw1.begin(), tw1.end()), tw2f(tw2.begin(), tw2.end());
     std::vector<double> keall;
@@ -220,6 +221,8 @@ hw_status hw_setup_basis(hw_ctx* ctx, const hw_basis_params* params, int nk, con
     UP(db.ke, keall);
     UP(db.t64.rinv, rinv);
     UP(db.t64.rfwd, rfwd);
+    UP(db.t64.qtab, hb.qtab);
+    UP(db.t32.qtab, qtab32);
     UP(db.t64.tw1, tw1);
     UP(db.t64.tw2, tw2);
     UP(db.t32.rinv, rinv32);
@@ -296,6 +299,18 @@ hw_status hw_get_radial_table(const hw_ctx* ctx, int n, double* table) {
   if (n < -hb.N || n > hb.N) return HW_EINVAL;
   const size_t sz = (size_t)hb.prm.Nr * hb.K;
   std::memcpy(table, hb.xi.data() + (size_t)std::abs(n) * sz, sz * sizeof(double));
+  return HW_OK;
+}
+
+hw_status hw_get_itable(const hw_ctx* ctx, int n, double* table) {
+  if (!ctx || !table) return HW_EINVAL;
+  if (!ctx->have_basis) return HW_ESTATE;
+  const auto& hb = ctx->hb;
+  if (n < -hb.N || n > hb.N) return HW_EINVAL;
+  const size_t sz = (size_t)hb.K * hb.K;
+  const double s = 0.5 * hb.prm.R * hb.prm.R;   // I = (R^2 / 2) <F_k', F_k / r^2>
+  const double* q = hb.qtab.data() + (size_t)std::abs(n) * sz;
+  for (size_t i = 0; i < sz; ++i) table[i] = s * q[i];
   return HW_OK;
 }
 

@@ -17,6 +17,7 @@ template <typename T>
 struct DevTables {
   T* rinv = nullptr;   // [(N+1)][Nr][K]      xi_{n,k}(r_p)
   T* rfwd = nullptr;   // [(N+1)][K][Nr]      (2 pi tau / Ncyc) w_p xi_{n,k}(r_p) / (Nth1 Nth2)
+  T* qtab = nullptr;   // [(N+1)][K][K]       <F_{m,n,k'}, F_{m,n,k} / r^2> (symmetric)
   T* V = nullptr;      // [Nr][Nth2][Nth1]    potential, slab layout
   T* tw1 = nullptr;    // [2*Nth1]            e^{-2 pi i t / Nth1} as (re, im)
   T* tw2 = nullptr;    // [2*Nth2]

@@ -204,6 +204,12 @@ struct RadArgs {
   const T* rtab;              // inverse [(N+1)][Nr][K] or forward [(N+1)][K][Nr]
   const double* ke;           // concatenated shifted kinetic energies (forward only)
   int64_t keoff[MAXSLOT];     // start of each block's k-point in ke
+  // nu != 0 terms (forward only): qtab [(N+1)][K][K] = <F_k', F_k / r^2>, the signed order n
+  // of every pair, the cyclic order and each block's nu
+  const T* qtab;
+  const int* pair_n;
+  int ncyc;
+  double nu[MAXSLOT];
   cplx_t<T>* gh;              // G (inverse output) or H (forward input)
   Blocks blk;
 };
@@ -346,11 +352,42 @@ __global__ void __launch_bounds__(RAD_THREADS) k_radial_fwd(RadArgs<T> A) {
     const double* x = A.blk.x[slot] + 2 * (o0 + (size_t)s * A.ld);
     double* y = A.blk.y[slot] + 2 * (o0 + (size_t)s * A.ld);
     const double* ke = A.ke + A.keoff[slot] + o0;
-    for (int k = lane; k < ka; k += 32) {
-      const V h = Ys[qq * (K + 1) + k];
-      const double d = ke[k];
-      y[2 * k] = d * x[2 * k] + double(h.x);
-      y[2 * k + 1] = d * x[2 * k + 1] + double(h.y);
+    const double nu = A.nu[slot];
+    if (nu == 0.0) {
+      for (int k = lane; k < ka; k += 32) {
+        const V h = Ys[qq * (K + 1) + k];
+        const double d = ke[k];
+        y[2 * k] = d * x[2 * k] + double(h.x);
+        y[2 * k + 1] = d * x[2 * k + 1] + double(h.y);
+      }
+      continue;
+    }
+    // nu != 0: the 1/r^2 terms of the I_n loop of Algorithm 5, which combine to
+    // (nu^2 - 2 nu n Ncyc)/2 <F_k', F_k / r^2> within the pair (m, n): lanes hold the pair's
+    // coefficients k = lane, lane + 32 (ka <= K <= 64) and broadcast them by shuffles
+    const T cf = T(0.5 * nu * (nu - 2.0 * (double)A.pair_n[aa] * A.ncyc));
+    const T* qt = A.qtab + (size_t)g * K * K;
+    V x0 = mk<T>(T(0), T(0)), x1 = mk<T>(T(0), T(0));
+    if (lane < ka) x0 = mk<T>(T(x[2 * lane]), T(x[2 * lane + 1]));
+    if (lane + 32 < ka) x1 = mk<T>(T(x[2 * (lane + 32)]), T(x[2 * (lane + 32) + 1]));
+    for (int kb = 0; kb < ka; kb += 32) {
+      const int k = kb + lane;
+      const T* qr = qt + (size_t)(k < ka ? k : 0) * K;
+      T sx = 0, sy = 0;
+      for (int j = 0; j < ka; ++j) {
+        const V xj = j < 32 ? x0 : x1;
+        const T vx = __shfl_sync(0xffffffffu, xj.x, j & 31);
+        const T vy = __shfl_sync(0xffffffffu, xj.y, j & 31);
+        const T qv = qr[j];
+        sx += qv * vx;
+        sy += qv * vy;
+      }
+      if (k < ka) {
+        const V h = Ys[qq * (K + 1) + k];
+        const double d = ke[k];
+        y[2 * k] = d * x[2 * k] + double(h.x + cf * sx);
+        y[2 * k + 1] = d * x[2 * k + 1] + double(h.y + cf * sy);
+      }
     }
   }
 }
@@ -488,6 +525,15 @@ int slab_pick_jc(const hw_ctx* ctx, size_t elem) {
   return Jc;
 }
 
+// nu != 0 arguments of the forward radial kernel
+template <typename T>
+static void set_nu_args(const hw_ctx* ctx, const Blocks& blk, const DevTables<T>& tb, RadArgs<T>& ra) {
+  ra.qtab = tb.qtab;
+  ra.pair_n = ctx->db.pair_n;
+  ra.ncyc = ctx->hb.prm.ncyc;
+  for (int i = 0; i < MAXSLOT; ++i) ra.nu[i] = i < blk.nslot ? ctx->hb.nu[blk.kb[i]] : 0.0;
+}
+
 // Launch the three kernels for the column blocks `blk` (ns columns each).  Columns are
 // processed in passes of at most ctx->ws.cols columns.
 template <typename T>
@@ -520,6 +566,7 @@ cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld) {
     ra.ld = ld;
     ra.ke = db.ke;
     for (int i = 0; i < blk.nslot; ++i) ra.keoff[i] = db.ke_off[blk.kb[i]];
+    set_nu_args(ctx, blk, tb, ra);
     ra.blk = blk;
     ra.gh = reinterpret_cast<cplx_t<T>*>(ctx->ws.gbuf);
     ra.rtab = tb.rinv;
@@ -597,6 +644,7 @@ cudaError_t launch_hx_into(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, v
     ra.ld = ld;
     ra.ke = db.ke;
     for (int i = 0; i < blk.nslot; ++i) ra.keoff[i] = db.ke_off[blk.kb[i]];
+    set_nu_args(ctx, blk, tb, ra);
     ra.blk = blk;
     ra.gh = reinterpret_cast<cplx_t<T>*>(gbuf);
     ra.rtab = tb.rinv;
@@ -766,6 +814,7 @@ cudaError_t launch_density(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, c
     ra.ld = ld;
     ra.ke = db.ke;
     for (int i = 0; i < blk.nslot; ++i) ra.keoff[i] = db.ke_off[blk.kb[i]];
+    set_nu_args(ctx, blk, tb, ra);
     ra.blk = blk;
     ra.gh = reinterpret_cast<cplx_t<T>*>(ctx->ws.gbuf);
     ra.rtab = tb.rinv;

@@ -16,6 +16,7 @@ struct HostBasis {
   std::vector<double> r, wr;                 // [Nr] radial nodes / weights (int f r dr)
   std::vector<std::vector<double>> zeros;    // zeros[|n|][k]: b_k^{|n| Ncyc}
   std::vector<double> xi;                    // [(N+1)][Nr][K]: xi_{n,k}(r_p), n >= 0
+  std::vector<double> qtab;                  // [(N+1)][K][K]: <F_{m,n,k'}, F_{m,n,k} / r^2>
   // k-points
   int nk = 0;
   std::vector<double> eta, nu, ecut;

@@ -1,5 +1,6 @@
 // Host-side setup of the helical-wave basis: Bessel zeros, the Gauss-Jacobi(0,1) radial rule,
-// the radial tables xi_{n,k}(r_p), the kinetic-energy cutoff masks and the compact index maps.
+// the radial tables xi_{n,k}(r_p), the 1/r^2 tables of the nu != 0 terms, the kinetic-energy
+// cutoff masks and the compact index maps.
 //
 // arXiv 2210.12252:
 //   basis functions and normalisation c_{m,n,k}   eq. Phi_expanded_in_basis_set, Appendix B
@@ -9,6 +10,7 @@
 //   grids and the 4x oversampling rule              Sec. "Wave function storage"
 //   cutoff mask at each (eta, nu)                   eq. Energy_cutoff and the mask after it
 //   Gauss-Jacobi radial nodes                       Sec. "Wave function storage"
+//   1/r^2 tables I(n, k, k')                        eqs. ell_coeff, ell_mnk, I_nkk_prime
 //
 // The Gauss-Jacobi(0,1) nodes are found by Sturm-sequence bisection on the Jacobi matrix of the
 // monic P_k^{(0,1)} and polished by Newton on the three-term recurrence; the weights are
@@ -201,6 +203,51 @@ std::string build_host_basis(const hw_basis_params& p, int nk, const double* eta
         hb.xi[(size_t(n) * Nr + q) * K + k] = c * besselj(ord, b * hb.r[q] / p.R);
     }
   }
+  // 1/r^2 matrix of each |n| group (eqs. ell_coeff, ell_mnk, I_nkk_prime):
+  //   qtab[g][k'][k] = <F_{m,n,k'}, F_{m,n,k} / r^2> = (2/R^2) I(n, k, k'),
+  //   I = int_0^1 J_p(b_k q) J_p(b_k' q) / q dq / (J_{p+1}(b_k) J_{p+1}(b_k')),  p = g Ncyc.
+  // For p >= 1 the integrand J J / q^2 (times the weight q) is smooth; a Gauss-Jacobi(0,1)
+  // rule with enough nodes for the band limit b_k + b_k' gives it to rounding.  For p = 0 the
+  // integral diverges at r = 0 (the paper's nu != 0 formulas meet J_0); the value of the
+  // transform's own radial rule (nodes avoid r = 0) is used instead.
+  hb.qtab.assign(size_t(N + 1) * K * K, 0.0);
+  {
+    double bmax = 0.0;
+    for (int n = 0; n <= N; ++n) bmax = std::max(bmax, hb.zeros[n][K - 1]);
+    const int nq = 64 + 2 * (int)std::ceil(bmax);
+    std::vector<double> xq, wq;
+    gauss_jacobi01(nq, xq, wq);
+    std::vector<double> Jq((size_t)nq * K);
+    for (int n = 0; n <= N; ++n) {
+      const int ord = n * p.ncyc;
+      double* Q = hb.qtab.data() + (size_t)n * K * K;
+      if (ord == 0) {
+        const double pref = 2.0 * pi * p.tau / p.ncyc;
+        for (int k = 0; k < K; ++k)
+          for (int kk = 0; kk < K; ++kk) {
+            double s = 0.0;
+            for (int q = 0; q < Nr; ++q)
+              s += hb.wr[q] / (hb.r[q] * hb.r[q]) * hb.xi[(size_t(n) * Nr + q) * K + k] *
+                   hb.xi[(size_t(n) * Nr + q) * K + kk];
+            Q[(size_t)kk * K + k] = pref * s;
+          }
+        continue;
+      }
+      for (int i = 0; i < nq; ++i) {
+        const double q = 0.5 * (1.0 + xq[i]);
+        for (int k = 0; k < K; ++k) Jq[(size_t)i * K + k] = besselj(ord, hb.zeros[n][k] * q) / q;
+      }
+      for (int k = 0; k < K; ++k)
+        for (int kk = 0; kk <= k; ++kk) {
+          double s = 0.0;   // int_0^1 (J J / q^2) q dq = sum_i (w_i / 4) J J / q_i^2
+          for (int i = 0; i < nq; ++i) s += 0.25 * wq[i] * Jq[(size_t)i * K + k] * Jq[(size_t)i * K + kk];
+          const double v = 2.0 / (p.R * p.R) * s /
+                           (besselj(ord + 1, hb.zeros[n][k]) * besselj(ord + 1, hb.zeros[n][kk]));
+          Q[(size_t)kk * K + k] = v;
+          Q[(size_t)k * K + kk] = v;
+        }
+    }
+  }
   // k-points, masks
   hb.nk = nk;
   hb.eta.assign(eta, eta + nk);
@@ -209,7 +256,7 @@ std::string build_host_basis(const hw_basis_params& p, int nk, const double* eta
   for (int b = 0; b < nk; ++b) {
     if (nu) hb.nu[b] = nu[b];
     if (ecut_per_k) hb.ecut[b] = ecut_per_k[b];
-    if (hb.nu[b] != 0.0) return "nu != 0 needs the 1/r^2 terms, which are not built";
+    if (!std::isfinite(hb.nu[b])) return "nu must be finite";
     if (!std::isfinite(hb.eta[b])) return "eta must be finite";
   }
   const double kz = 2.0 * pi / p.tau;

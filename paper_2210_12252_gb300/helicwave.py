@@ -50,6 +50,7 @@ _SIGS = {
     "hw_get_index_map": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int32)]),
     "hw_get_kinetic": (C.c_int, [C.c_void_p, C.c_int, _D]),
     "hw_get_radial_table": (C.c_int, [C.c_void_p, C.c_int, _D]),
+    "hw_get_itable": (C.c_int, [C.c_void_p, C.c_int, _D]),
     "hw_set_potential": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "hw_build_potential": (C.c_int, [C.c_void_p, C.c_int, _D, _D]),
     "hw_apply_H": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int64,
@@ -190,6 +191,12 @@ def hw_get_radial_table(h, n, Nr, K):
     out = np.zeros(Nr * K)
     _check(h, load_library().hw_get_radial_table(h, n, _dptr(out)))
     return out.reshape(Nr, K)
+
+
+def hw_get_itable(h, n, K):
+    out = np.zeros(K * K)
+    _check(h, load_library().hw_get_itable(h, n, _dptr(out)))
+    return out.reshape(K, K)
 
 
 def hw_set_potential(h, V_ptr: int, on_device: bool):
@@ -444,6 +451,9 @@ class Context:
 
     def radial_table(self, n):
         return hw_get_radial_table(self.h, n, self.geom.Nr, self.sizes["K"])
+
+    def itable(self, n):
+        return hw_get_itable(self.h, n, self.sizes["K"])
 
     def build_potential(self, atoms):
         return hw_build_potential(self.h, atoms, self.sizes["grid_points"])

@@ -105,7 +105,7 @@ def test_setup_rejects_bad_arguments(lib):
             ctx.setup_basis(g, [0.0])
         assert e.value.status == hw.HW_EINVAL
     with pytest.raises(hw.HwError) as e:
-        ctx.setup_basis(inputs.GEOM_TINY, [0.0], nus=[1.0])
+        ctx.setup_basis(inputs.GEOM_TINY, [0.0], nus=[float("nan")])
     assert e.value.status == hw.HW_EINVAL
 
 
@@ -132,3 +132,25 @@ def test_options_set_get_and_reject(lib):
     with pytest.raises(hw.HwError):
         ctx.get_option(99)
     ctx.close()
+
+
+def test_cyclic_masks_and_itable_match_oracle(lib):
+    """Ncyc = 3 with nu != 0: masks, compact order and shifted kinetic energies at each (eta, nu),
+    and the table I(n, k, k') of eq. I_nkk_prime (the library's Gauss-Jacobi rule against the
+    oracle's Gauss-Legendre sum; for n = 0 both take the radial-rule value)."""
+    g = inputs.Geometry(**{**inputs.GEOM_TUBE.__dict__, "ncyc": 3})
+    etas, nus = np.array([0.1, -0.3, 0.45]), np.array([1.0, 2.0, 0.0])
+    ctx = hw.Context(device=-1)
+    L = ctx.setup_basis(g, etas, nus)
+    b = oracle_basis(g)
+    for k, (eta, nu) in enumerate(zip(etas, nus)):
+        kp = B.KPoint(b, eta, nu, g.ecut)
+        assert L[k] == kp.L
+        mnk = ctx.index_map(k)
+        np.testing.assert_array_equal(mnk[:, 0], kp.m)
+        np.testing.assert_array_equal(mnk[:, 1], kp.n)
+        np.testing.assert_array_equal(mnk[:, 2], kp.k)
+        np.testing.assert_allclose(ctx.kinetic(k), kp.ke, rtol=1e-13, atol=1e-13)
+    for n in range(-b.N, b.N + 1):
+        I = b.itable(n)
+        np.testing.assert_allclose(ctx.itable(n), I, rtol=0, atol=1e-12 * np.abs(I).max())
