@@ -315,6 +315,8 @@ def ours_main(args):
         result["batched_kpoints"] = batched_kpoints(hw, inputs, local, stream, flush, precond)
         # ---- H X on the large nanowire-like basis (L ~ 40.6k, 192 x 96 x 192 grid)
         result["hx_wire"] = hx_wire(hw, inputs, local, stream, flush)
+        # ---- cyclic symmetry Ncyc = 3 with nu = 0, 1, 2
+        result["cyclic"] = cyclic(hw, inputs, local, stream, flush)
         # ---- roofline of the dominant kernel of the chosen-form step
         result["roofline"] = roofline(result, w, ctx, L, nb)
         # ---- end to end through the C ABI with host buffers
@@ -401,6 +403,59 @@ def hx_wire(hw, inputs, local, stream, flush):
         torch.cuda.synchronize()
         t = float(np.mean([a.elapsed_time(b) for a, b in evs]))
         out[prec] = {"vec_per_s": round(ns / (t / 1e3), 1), "ms_per_call": round(t, 3)}
+    ctx.close()
+    return out
+
+
+def cyclic(hw, inputs, local, stream, flush):
+    """Ncyc = 3 tube (nu = 0, 1, 2): H X vectors/s per nu (the nu != 0 points add the 1/r^2
+    terms in the forward radial kernel) and one batched mixed solve of the three points."""
+    import torch
+    w = inputs.tube_cyclic()
+    ctx = hw.Context(local, stream=stream)
+    L = [int(x) for x in ctx.setup_basis(w.geom, w.etas, w.nus)]
+    ctx.build_potential(w.atoms)
+    ns = 64
+    out = {"workload": w.name, "L": L, "nu": [float(x) for x in w.nus], "columns": ns}
+    for k in range(len(L)):
+        X = torch.from_numpy(np.ascontiguousarray(inputs.random_block(L[k], ns, 90 + k).T)).cuda()
+        Y = torch.empty_like(X)
+        row = {}
+        for prec in ("fp64", "mixed"):
+            for _ in range(2):
+                ctx.apply_H(k, X, Y, prec=prec)
+            evs = []
+            with torch.cuda.stream(stream):
+                for _ in range(5):
+                    flush.fill_(1.0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ctx.apply_H(k, X, Y, prec=prec)
+                    e1.record(stream)
+                    evs.append((e0, e1))
+            torch.cuda.synchronize()
+            t = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+            row[prec] = round(ns / (t / 1e3), 1)
+        out[f"hx_vec_per_s_nu{int(w.nus[k])}"] = row
+    kids = list(range(len(L)))
+    ctx.solve_eigs(kids, w.n_eig, tol=TOL, maxit=600, prec="mixed")
+    with torch.cuda.stream(stream):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = ctx.solve_eigs(kids, w.n_eig, tol=TOL, maxit=600, prec="mixed")
+        e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1)
+    err = 0.0
+    for k in kids:
+        ref = np.loadtxt(os.path.join(ROOT, "tests", "golden", f"tube_c3_k{k}_eigs.txt"))[: w.n_eig]
+        err = max(err, float(np.abs(r["evals"][k] - ref).max()))
+    out["solve_mixed"] = {"eigenpairs_per_s": round(len(kids) * w.n_eig / (t / 1e3), 1),
+                          "ms": round(float(t), 2), "converged": bool(r["converged"]),
+                          "iters": [int(i) for i in r["iters"]], "max_abs_err_vs_oracle_Ha": err}
     ctx.close()
     return out
 
