@@ -288,7 +288,7 @@ typedef enum {
                                A^H B over the basis dimension with hw_gram's kernel (FP32
                                products, FP64 accumulation every 32 rows); 0 (default) uses
                                cuBLAS CGEMM on FP32 copies, measured faster on the tube. */
-  HW_OPT_HYBRID = 4         /* mixed form, FP64 phase: 1 (default) first keeps FP64 only for
+  HW_OPT_HYBRID = 4,        /* mixed form, FP64 phase: 1 (default) first keeps FP64 only for
                                the products that involve X (its rows of the Rayleigh-Ritz matrix,
                                its share of the X / H X updates, one projection of W and of P
                                against X) and forms the rest of the W and P orthogonalisation,
@@ -296,6 +296,12 @@ typedef enum {
                                near 3e-7, so when the best residual has not dropped by 30% in 4
                                iterations every product becomes FP64.  0: FP64 throughout the
                                phase. */
+  HW_OPT_EIGENSOLVER = 5,   /* block eigensolver of hw_solve_eigs: 0 (default) LOBPCG with the
+                               preconditioner; 1 Chebyshev-filtered subspace iteration (the
+                               preconditioner argument is then not used; maxit counts filter +
+                               Rayleigh-Ritz cycles). */
+  HW_OPT_CHEB_DEGREE = 6    /* Chebyshev filter degree (H X products per cycle), 2..64;
+                               default 16. */
 } hw_option;
 /* Set an option (HW_EINVAL for an unknown option, a read-only one or a bad value). */
 hw_status hw_set_option(hw_ctx* ctx, int option, int value);

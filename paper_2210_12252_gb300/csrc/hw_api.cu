@@ -522,6 +522,16 @@ hw_status hw_set_option(hw_ctx* ctx, int option, int value) {
     ctx->hybrid = value;
     return HW_OK;
   }
+  if (option == HW_OPT_EIGENSOLVER) {
+    if (value != 0 && value != 1) return hw_fail(ctx, HW_EINVAL, "eigensolver 0 (LOBPCG) or 1 (Chebyshev filtering)");
+    ctx->eigensolver = value;
+    return HW_OK;
+  }
+  if (option == HW_OPT_CHEB_DEGREE) {
+    if (value < 2 || value > 64) return hw_fail(ctx, HW_EINVAL, "Chebyshev degree 2..64");
+    ctx->cheb_degree = value;
+    return HW_OK;
+  }
   return hw_fail(ctx, HW_EINVAL, "unknown or read-only option");
 }
 
@@ -532,6 +542,8 @@ hw_status hw_get_option(hw_ctx* ctx, int option, long long* value) {
   if (option == HW_OPT_LOWP_SWITCH) { *value = ctx->lowp_exp; return HW_OK; }
   if (option == HW_OPT_GRAM_KERNEL) { *value = ctx->gram_mixed; return HW_OK; }
   if (option == HW_OPT_HYBRID) { *value = ctx->hybrid; return HW_OK; }
+  if (option == HW_OPT_EIGENSOLVER) { *value = ctx->eigensolver; return HW_OK; }
+  if (option == HW_OPT_CHEB_DEGREE) { *value = ctx->cheb_degree; return HW_OK; }
   return hw_fail(ctx, HW_EINVAL, "unknown option");
 }
 

@@ -95,6 +95,8 @@ struct hw_ctx {
   int lowp_exp = 5;            // HW_OPT_LOWP_SWITCH
   int gram_mixed = 0;          // HW_OPT_GRAM_KERNEL
   int hybrid = 1;              // HW_OPT_HYBRID
+  int eigensolver = 0;         // HW_OPT_EIGENSOLVER
+  int cheb_degree = 16;        // HW_OPT_CHEB_DEGREE
   int64_t rr_fallbacks = 0;    // Householder results rejected by the check (Jacobi used)
   hw::Prof prof;
 };

@@ -286,6 +286,80 @@ __global__ void k_random_start(double2* S, int64_t Lpad, int64_t sK, const int64
   }
 }
 
+// ------------------------------------------------------------------ Chebyshev filter kernels
+// Per-k-point scalars of one step of the scaled three-term recurrence.
+struct ChebScal {
+  double al[MAXSLOT], c[MAXSLOT], be[MAXSLOT];
+};
+
+// One recurrence step on column blocks of S (block q = columns q nb .. q nb + nb - 1):
+//   S[dst] = al_b (HS[src] - c_b S[src]) - be_b S[dst]      (be_b = 0: S[dst] is not read)
+// i.e. Y_i = al (H Y_{i-1} - c Y_{i-1}) - be Y_{i-2} with Y_{i-2} in the destination block;
+// grid (nb, nk); src != dst
+__global__ void k_cheb(double2* S, const double2* HS, int64_t Lpad, int64_t sK, int nb, int src, int dst,
+                       ChebScal sc) {
+  const int j = blockIdx.x, b = blockIdx.y;
+  const double al = sc.al[b], c = sc.c[b], be = sc.be[b];
+  const size_t o = (size_t)b * sK;
+  const double2* x = S + o + (size_t)(src * nb + j) * Lpad;
+  const double2* hx = HS + o + (size_t)(src * nb + j) * Lpad;
+  double2* y = S + o + (size_t)(dst * nb + j) * Lpad;
+  for (int64_t i = threadIdx.x; i < Lpad; i += blockDim.x) {
+    const double2 v = x[i], h = hx[i];
+    double2 r = make_double2(al * (h.x - c * v.x), al * (h.y - c * v.y));
+    if (be != 0.0) {
+      const double2 yo = y[i];
+      r.x -= be * yo.x;
+      r.y -= be * yo.y;
+    }
+    y[i] = r;
+  }
+}
+
+// scale each of the nb columns of block q to unit 2-norm (zero columns stay zero); grid (nb, nk)
+__global__ void k_colnorm(double2* S, int64_t Lpad, int64_t sK, int nb, int q) {
+  __shared__ double red[32];
+  __shared__ double scale;
+  const int j = blockIdx.x, b = blockIdx.y;
+  double2* y = S + (size_t)b * sK + (size_t)(q * nb + j) * Lpad;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < Lpad; i += blockDim.x) {
+    const double2 v = y[i];
+    s += v.x * v.x + v.y * v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    scale = t > 0.0 ? 1.0 / sqrt(t) : 1.0;
+  }
+  __syncthreads();
+  const double f = scale;
+  for (int64_t i = threadIdx.x; i < Lpad; i += blockDim.x) {
+    double2 v = y[i];
+    v.x *= f;
+    v.y *= f;
+    y[i] = v;
+  }
+}
+
+// out[0] = max_i V[i]; one CTA
+__global__ void k_vmax(const double* V, int64_t n, double* out) {
+  __shared__ double red[32];
+  double m = -1e300;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, V[i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = red[0];
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) t = fmax(t, red[i]);
+    out[0] = t;
+  }
+}
+
 // copy the user's start block (L_b x nb, ld L_b) into S; grid (nb, nk)
 struct PtrArr {
   const double* p[MAXSLOT];
@@ -696,44 +770,86 @@ struct Trace {
 };
 }  // namespace
 
-static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, int block,
-                            double tol, int maxit, hw_prec prec, int precond_kind,
-                            const double* const* X0, double* evals, double* const* evecs,
-                            int64_t ld_evecs, int* iters, double* resid, Trace* trace) {
-  if (!ctx) return HW_EINVAL;
+// Rayleigh-Ritz on the nb columns of column block q of SB[from] (H times them in the same
+// block of HSB[from]): the Ritz vectors and their H products go to block 0 of SB[to] /
+// HSB[to] (to != from), the Ritz values to w->theta.  dnv: the device count array (its P and
+// W counts are zeroed).
+static hw_status rr_subspace(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int* dnv, int from, int q, int to) {
+  const int nk = w->nk, nb = w->nb;
+  const int64_t Lpad = w->Lpad, sK = Lpad * 3 * nb;
+  cudaStream_t st = ctx->stream;
+  const int n = nb + (nb & 1);
+  const double2* Y = w->SB[from] + (size_t)q * nb * Lpad;
+  const double2* HY = w->HSB[from] + (size_t)q * nb * Lpad;
+  gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, (int)Lpad, 1.0, Y, Lpad, sK, HY, Lpad, sK, 0.0, w->A, n, (int64_t)n * n,
+       nk);
+  std::vector<int> z(nk, 0);
+  cudaMemcpyAsync(dnv + nk, z.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(dnv + 2 * nk, z.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
+  {
+    ProfScope ps_(ctx, HW_PH_OTHER);
+    k_pad_rr<<<dim3(8, nk), 256, 0, st>>>(w->A, n, nb, 0, 0, dnv + nk, dnv + 2 * nk);
+    ctx->launches++;
+  }
+  cudaError_t e = rr_eig(ctx, w, gemm, n, nb, false, gemm.lowp);
+  if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
+  gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nb, 1.0, Y, Lpad, sK, w->Z, n, (int64_t)n * n, 0.0, w->SB[to],
+       Lpad, sK, nk);
+  gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nb, 1.0, HY, Lpad, sK, w->Z, n, (int64_t)n * n, 0.0, w->HSB[to],
+       Lpad, sK, nk);
+  for (int b = 0; b < nk; ++b)
+    cudaMemcpyAsync(w->theta + (size_t)b * nb, w->w + (size_t)b * n, nb * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  return HW_OK;
+}
+
+// Arguments and buffers shared by the block eigensolvers.
+struct SolveSetup {
+  std::vector<int> kidx;
+  std::vector<int64_t> Lb;   // basis size of each k-point
+  int nb = 0;
+  int64_t Lpad = 0, sK = 0;
+  int64_t* dL = nullptr;     // device copy of Lb
+  int* dnv = nullptr;        // device [3][nk]: valid column counts (CholQR / P / W)
+  ~SolveSetup() {
+    cudaFree(dL);
+    cudaFree(dnv);
+  }
+};
+
+// Validate the arguments common to the eigensolvers, size the workspace, point `gemm` at the
+// FP32 product buffers of the mixed form, and copy the per-k-point sizes to the device.
+static hw_status solve_setup(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, int block, double tol,
+                             int maxit, hw_prec prec, const double* evals, const double* const* evecs,
+                             int64_t ld_evecs, SolveSetup& su, Gemm& gemm) {
   if (ctx->device < 0) return hw_fail(ctx, HW_ESTATE, "host-only context has no device");
   if (!ctx->have_basis) return hw_fail(ctx, HW_ESTATE, "hw_setup_basis has not been called");
   if (!ctx->have_V) return hw_fail(ctx, HW_ESTATE, "no potential installed");
   if (nk < 1 || nk > MAXSLOT || !kidx_in || !evals) return hw_fail(ctx, HW_EINVAL, "bad k-point list");
   if (n_eig < 1 || !(tol > 0) || maxit < 1) return hw_fail(ctx, HW_EINVAL, "bad n_eig / tol / maxit");
   if (prec != HW_FP64 && prec != HW_MIXED) return hw_fail(ctx, HW_EINVAL, "bad precision");
-  if (precond_kind != HW_PRECOND_TPA && precond_kind != HW_PRECOND_NONE &&
-      !(precond_kind == HW_PRECOND_LEARNED && ctx->mlp))
-    return hw_fail(ctx, HW_EINVAL, "bad preconditioner kind (learned needs hw_set_mlp)");
-  std::vector<int> kidx(kidx_in, kidx_in + nk);
+  su.kidx.assign(kidx_in, kidx_in + nk);
   int64_t Lmax = 0, Lmin = INT64_MAX;
   for (int b = 0; b < nk; ++b) {
-    if (kidx[b] < 0 || kidx[b] >= ctx->hb.nk) return hw_fail(ctx, HW_EINVAL, "k-point index out of range");
-    Lmax = std::max(Lmax, ctx->hb.L[kidx[b]]);
-    Lmin = std::min(Lmin, ctx->hb.L[kidx[b]]);
+    if (su.kidx[b] < 0 || su.kidx[b] >= ctx->hb.nk) return hw_fail(ctx, HW_EINVAL, "k-point index out of range");
+    Lmax = std::max(Lmax, ctx->hb.L[su.kidx[b]]);
+    Lmin = std::min(Lmin, ctx->hb.L[su.kidx[b]]);
   }
-  int nb = block > 0 ? block : n_eig + std::max(4, n_eig / 8);
+  const int nb = block > 0 ? block : n_eig + std::max(4, n_eig / 8);
   if (nb < n_eig) return hw_fail(ctx, HW_EINVAL, "block < n_eig");
   if (nb > 112) return hw_fail(ctx, HW_EINVAL, "block > 112");
   if (3 * (int64_t)nb > Lmin) return hw_fail(ctx, HW_EINVAL, "block too large for the basis (3*block > L)");
   if (evecs && ld_evecs < Lmax) return hw_fail(ctx, HW_EINVAL, "ld_evecs < L");
-  const int64_t Lpad = (Lmax + 7) / 8 * 8;
+  su.nb = nb;
+  su.Lpad = (Lmax + 7) / 8 * 8;
+  su.sK = su.Lpad * 3 * nb;
+  const int64_t Lpad = su.Lpad;
   cudaSetDevice(ctx->device);
   hw_status hs = ensure_work(ctx, nk, nb, Lpad);
   if (hs != HW_OK) return hs;
   LobpcgWork* w = ctx->lw;
-  cudaStream_t st = ctx->stream;
-  Gemm gemm{ctx};
-  const int64_t sK = Lpad * 3 * nb;
   // mixed form: products over the basis dimension in complex FP32 until the residuals fall
-  // below 10^-lowp_exp, then FP64 (X re-orthonormalised, H X recomputed, P restarted)
-  const double lowp_thr = (prec == HW_MIXED && ctx->lowp_exp > 0) ? std::pow(10.0, -ctx->lowp_exp) : 0.0;
-  if (lowp_thr > 0.0) {
+  // below 10^-lowp_exp, then FP64
+  if (prec == HW_MIXED && ctx->lowp_exp > 0) {
     const size_t ab = (size_t)nk * Lpad * 3 * nb;
     const size_t cc = std::max((size_t)nk * Lpad * 2 * nb, (size_t)nk * w->ne * w->ne);
     if (w->f32_ab < ab || w->f32_c < cc) {
@@ -767,76 +883,79 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     gemm.gwork = w->gwork;
     gemm.gbytes = w->gbytes;
   }
-  std::vector<int64_t> Lb(nk);
-  for (int b = 0; b < nk; ++b) Lb[b] = ctx->hb.L[kidx[b]];
-  int64_t* dL = nullptr;
-  int* dnv = nullptr;   // [3][nk]: valid counts for CholQR / P / W
-  cudaMalloc((void**)&dL, nk * sizeof(int64_t));
-  cudaMalloc((void**)&dnv, 3 * nk * sizeof(int));
-  cudaMemcpy(dL, Lb.data(), nk * sizeof(int64_t), cudaMemcpyHostToDevice);
-  struct Cleanup {
-    void* a;
-    void* b;
-    ~Cleanup() {
-      cudaFree(a);
-      cudaFree(b);
-    }
-  } cleanup{dL, dnv};
-  cudaMemsetAsync(w->status, 0, sizeof(int), st);
-  std::vector<int> failed;
-  int cur = 0;
-  // ---- start block
+  su.Lb.resize(nk);
+  for (int b = 0; b < nk; ++b) su.Lb[b] = ctx->hb.L[su.kidx[b]];
+  if (cudaMalloc((void**)&su.dL, nk * sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc((void**)&su.dnv, 3 * nk * sizeof(int)) != cudaSuccess)
+    return hw_fail(ctx, HW_ENOMEM, "eigensolver size arrays");
+  cudaMemcpy(su.dL, su.Lb.data(), nk * sizeof(int64_t), cudaMemcpyHostToDevice);
+  cudaMemsetAsync(w->status, 0, sizeof(int), ctx->stream);
+  return HW_OK;
+}
+
+// Start block in the first nb columns of SB[0]: the caller's X0 (L_b x nb, ld L_b, zero padded)
+// or a seeded complex Gaussian block; then Cholesky-QR twice.
+static hw_status start_block(hw_ctx* ctx, SolveSetup& su, Gemm& gemm, const double* const* X0) {
+  LobpcgWork* w = ctx->lw;
+  const int nk = w->nk, nb = su.nb;
+  cudaStream_t st = ctx->stream;
   if (X0) {
     PtrArr pa;
     for (int b = 0; b < nk; ++b) {
       if (!X0[b]) return hw_fail(ctx, HW_EINVAL, "null start block");
       pa.p[b] = X0[b];
     }
-    {
-      ProfScope ps_(ctx, HW_PH_OTHER);
-      k_copy_start<<<dim3(nb, nk), 256, 0, st>>>(pa, w->SB[0], Lpad, sK, dL);
-      ctx->launches++;
-    }
+    ProfScope ps_(ctx, HW_PH_OTHER);
+    k_copy_start<<<dim3(nb, nk), 256, 0, st>>>(pa, w->SB[0], su.Lpad, su.sK, su.dL);
+    ctx->launches++;
   } else {
-    {
-      ProfScope ps_(ctx, HW_PH_OTHER);
-      k_random_start<<<dim3(nb, nk), 256, 0, st>>>(w->SB[0], Lpad, sK, dL, nb, 0x5eed1234abcdULL);
-      ctx->launches++;
-    }
+    ProfScope ps_(ctx, HW_PH_OTHER);
+    k_random_start<<<dim3(nb, nk), 256, 0, st>>>(w->SB[0], su.Lpad, su.sK, su.dL, nb, 0x5eed1234abcdULL);
+    ctx->launches++;
   }
   std::vector<int> nvh(3 * nk, nb);
-  cudaMemcpy(dnv, nvh.data(), 3 * nk * sizeof(int), cudaMemcpyHostToDevice);
-  hs = cholqr(ctx, w, gemm, w->SB[0], 0, nb, dnv, 2, failed);
+  cudaMemcpy(su.dnv, nvh.data(), 3 * nk * sizeof(int), cudaMemcpyHostToDevice);
+  std::vector<int> failed;
+  hw_status hs = cholqr(ctx, w, gemm, w->SB[0], 0, nb, su.dnv, 2, failed);
   if (hs != HW_OK) return hs;
   for (int b = 0; b < nk; ++b)
     if (failed[b]) return hw_fail(ctx, HW_EINVAL, "start block is rank deficient");
+  return HW_OK;
+}
+
+static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, int block,
+                            double tol, int maxit, hw_prec prec, int precond_kind,
+                            const double* const* X0, double* evals, double* const* evecs,
+                            int64_t ld_evecs, int* iters, double* resid, Trace* trace) {
+  if (!ctx) return HW_EINVAL;
+  if (precond_kind != HW_PRECOND_TPA && precond_kind != HW_PRECOND_NONE &&
+      !(precond_kind == HW_PRECOND_LEARNED && ctx->mlp))
+    return hw_fail(ctx, HW_EINVAL, "bad preconditioner kind (learned needs hw_set_mlp)");
+  Gemm gemm{ctx};
+  SolveSetup su;
+  hw_status hs = solve_setup(ctx, nk, kidx_in, n_eig, block, tol, maxit, prec, evals, evecs, ld_evecs, su, gemm);
+  if (hs != HW_OK) return hs;
+  const std::vector<int>& kidx = su.kidx;
+  const std::vector<int64_t>& Lb = su.Lb;
+  const int nb = su.nb;
+  const int64_t Lpad = su.Lpad, sK = su.sK;
+  int* dnv = su.dnv;
+  LobpcgWork* w = ctx->lw;
+  cudaStream_t st = ctx->stream;
+  const double lowp_thr = (prec == HW_MIXED && ctx->lowp_exp > 0) ? std::pow(10.0, -ctx->lowp_exp) : 0.0;
+  std::vector<int> failed;
+  int cur = 0;
+  hs = start_block(ctx, su, gemm, X0);
+  if (hs != HW_OK) return hs;
   const bool mixed = prec == HW_MIXED;
   bool fp64_products = !mixed;
   hs = apply_block(ctx, w, kidx, w->SB[0], w->HSB[0], 0, nb, fp64_products);
   if (hs != HW_OK) return hs;
   // Rayleigh-Ritz on X alone: SB[from] -> SB[1 - from]
   auto rr_on_x = [&](int from) -> hw_status {
-    const int n = nb + (nb & 1);
-    gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, (int)Lpad, 1.0, w->SB[from], Lpad, sK, w->HSB[from], Lpad, sK, 0.0, w->A,
-         n, (int64_t)n * n, nk);
-    std::vector<int> z(nk, 0);
-    cudaMemcpyAsync(dnv + nk, z.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(dnv + 2 * nk, z.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
-    {
-      ProfScope ps_(ctx, HW_PH_OTHER);
-      k_pad_rr<<<dim3(8, nk), 256, 0, st>>>(w->A, n, nb, 0, 0, dnv + nk, dnv + 2 * nk);
-      ctx->launches++;
-    }
-    cudaError_t e = rr_eig(ctx, w, gemm, n, nb, false, gemm.lowp);
-    if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
-    gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nb, 1.0, w->SB[from], Lpad, sK, w->Z, n, (int64_t)n * n, 0.0,
-         w->SB[1 - from], Lpad, sK, nk);
-    gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, nb, nb, 1.0, w->HSB[from], Lpad, sK, w->Z, n, (int64_t)n * n, 0.0,
-         w->HSB[1 - from], Lpad, sK, nk);
-    for (int b = 0; b < nk; ++b)
-      cudaMemcpyAsync(w->theta + (size_t)b * nb, w->w + (size_t)b * n, nb * sizeof(double), cudaMemcpyDeviceToDevice, st);
-    cur = 1 - from;
-    return HW_OK;
+    const hw_status h = rr_subspace(ctx, w, gemm, dnv, from, 0, 1 - from);
+    if (h == HW_OK) cur = 1 - from;
+    return h;
   };
   hs = rr_on_x(0);
   if (hs != HW_OK) return hs;
@@ -1273,6 +1392,241 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
   return HW_OK;
 }
 
+// Chebyshev-filtered subspace iteration (the alternative eigensolver the paper leaves to future
+// work, Sec. "Eigensolvers and Preconditioning"; the filter is the scaled three-term Chebyshev
+// recurrence of Zhou and Saad's filtered subspace iteration).  Per cycle and k-point, with Ritz
+// values theta_0 <= ... <= theta_{nb-1} of the current block X:
+//   damped interval [a, b]: a = theta_{nb-1}, b = an upper bound of the spectrum,
+//   e = (b - a)/2, c = (b + a)/2, sigma_1 = e/(theta_0 - c), tau = 2/sigma_1,
+//   Y_0 = X, Y_1 = (sigma_1/e)(H X - c X),
+//   Y_i = (2 sigma_i/e)(H Y_{i-1} - c Y_{i-1}) - sigma_{i-1} sigma_i Y_{i-2},
+//     sigma_i = 1/(tau - sigma_{i-1}),  i = 2 .. m,
+// so that p_m(theta_0) = 1 and the wanted end of the spectrum is amplified relative to [a, b];
+// then the columns of Y_m are normalised, orthonormalised (Cholesky-QR twice), multiplied by H,
+// and a Rayleigh-Ritz step on them gives the next X.  H X of the current X comes from the
+// Rayleigh-Ritz step, so a cycle costs m products H Y.
+// Upper bound: b = max KE + max V (+ the largest positive 1/r^2 term for nu != 0): H is the
+// diagonal KE plus B^H W diag(V) B (an orthogonal projection of V, so bounded by max V) plus
+// the nu terms, bounded by their coefficient times the row-sum norm of the I_n table.
+// Mixed form: the filter's H products, the Gram matrices and the Rayleigh-Ritz products are
+// FP32 until the residuals fall below 10^-lowp_exp (or stop falling), then FP64 (X
+// re-orthonormalised and H X recomputed in FP64); convergence claims are FP64 residuals.
+static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, int block, double tol, int maxit,
+                            hw_prec prec, const double* const* X0, double* evals, double* const* evecs,
+                            int64_t ld_evecs, int* iters, double* resid) {
+  Gemm gemm{ctx};
+  SolveSetup su;
+  hw_status hs = solve_setup(ctx, nk, kidx_in, n_eig, block, tol, maxit, prec, evals, evecs, ld_evecs, su, gemm);
+  if (hs != HW_OK) return hs;
+  const std::vector<int>& kidx = su.kidx;
+  const int nb = su.nb, m = ctx->cheb_degree;
+  const int64_t Lpad = su.Lpad, sK = su.sK;
+  int* dnv = su.dnv;
+  LobpcgWork* w = ctx->lw;
+  cudaStream_t st = ctx->stream;
+  const bool mixed = prec == HW_MIXED;
+  const double lowp_thr = (mixed && ctx->lowp_exp > 0) ? std::pow(10.0, -ctx->lowp_exp) : 0.0;
+  // ---- upper bounds of the spectra
+  double vmax = 0.0;
+  {
+    const auto& pr = ctx->hb.prm;
+    const int64_t grid = (int64_t)pr.Nth1 * pr.Nth2 * pr.Nr;
+    ProfScope ps_(ctx, HW_PH_OTHER);
+    k_vmax<<<1, 1024, 0, st>>>(ctx->db.t64.V, grid, w->res);
+    ctx->launches++;
+    cudaMemcpyAsync(&vmax, w->res, sizeof(double), cudaMemcpyDeviceToHost, st);
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("spectral bound: ") + cudaGetErrorString(e));
+  }
+  std::vector<double> bup(nk);
+  {
+    const auto& hb = ctx->hb;
+    const int K = hb.K;
+    std::vector<double> qnorm(hb.N + 1, 0.0);   // row-sum norm of each |n| table
+    for (int g = 0; g <= hb.N; ++g)
+      for (int k = 0; k < K; ++k) {
+        double r = 0.0;
+        for (int kk = 0; kk < K; ++kk) r += std::fabs(hb.qtab[((size_t)g * K + k) * K + kk]);
+        qnorm[g] = std::max(qnorm[g], r);
+      }
+    for (int b = 0; b < nk; ++b) {
+      const auto& ke = hb.ke[kidx[b]];
+      double kmax = -1e300;
+      for (double v : ke) kmax = std::max(kmax, v);
+      const double nu = hb.nu[kidx[b]];
+      double extra = 0.0;
+      if (nu != 0.0)
+        for (int n = -hb.N; n <= hb.N; ++n)
+          extra = std::max(extra, 0.5 * nu * (nu - 2.0 * n * hb.prm.ncyc) * qnorm[std::abs(n)]);
+      const double bound = kmax + vmax + extra;
+      bup[b] = bound + 1e-3 * std::fabs(bound) + 1e-3;
+    }
+  }
+  hs = start_block(ctx, su, gemm, X0);
+  if (hs != HW_OK) return hs;
+  bool lowp = gemm.lowp;   // FP32 phase of the mixed form
+  hs = apply_block(ctx, w, kidx, w->SB[0], w->HSB[0], 0, nb, !lowp);
+  if (hs != HW_OK) return hs;
+  hs = rr_subspace(ctx, w, gemm, dnv, 0, 0, 1);
+  if (hs != HW_OK) return hs;
+  int cur = 1;
+  std::vector<char> done(nk, 0);
+  std::vector<int> it_done(nk, maxit);
+  std::vector<double> resh((size_t)nk * nb), thh((size_t)nk * nb);
+  double lowp_best = 1e300;
+  int lowp_best_it = 0;
+  hw_status final_status = HW_ENOTCONV;
+  std::vector<int> failed;
+  int it = 0;
+  for (it = 0; it <= maxit; ++it) {
+    double2* S = w->SB[cur];
+    double2* HS = w->HSB[cur];
+    {
+      ProfScope ps_(ctx, HW_PH_OTHER);
+      k_residual<<<dim3(nb, nk), 256, 0, st>>>(S, HS, Lpad, sK, w->theta, nb, w->R, w->res);
+      ctx->launches++;
+    }
+    cudaMemcpyAsync(resh.data(), w->res, resh.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(thh.data(), w->theta, thh.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    int dstat = 0;
+    cudaMemcpyAsync(&dstat, w->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
+    if (dstat == HW_ETIMEOUT) return hw_fail(ctx, HW_ETIMEOUT, "dense eigensolver barrier timed out");
+    if (gemm.st != CUBLAS_STATUS_SUCCESS) return hw_fail(ctx, HW_ECUDA, "cuBLAS failure");
+    if (gemm.ce != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("Gram kernel: ") + cudaGetErrorString(gemm.ce));
+    double maxres = 0.0;
+    std::vector<int> claim(nk, 0);
+    int nclaim = 0;
+    for (int b = 0; b < nk; ++b) {
+      if (done[b]) continue;
+      double mr = 0.0;
+      for (int j = 0; j < n_eig; ++j) mr = std::max(mr, resh[(size_t)b * nb + j]);
+      maxres = std::max(maxres, mr);
+      if (mr <= tol) {
+        claim[b] = 1;
+        ++nclaim;
+      }
+    }
+    if (lowp) {
+      if (maxres < 0.7 * lowp_best) {
+        lowp_best = maxres;
+        lowp_best_it = it;
+      }
+      if (maxres < lowp_thr || nclaim > 0 || it - lowp_best_it >= 3) {
+        // leave the FP32 phase: X orthonormalised again and H X recomputed in FP64, then a
+        // Rayleigh-Ritz step; the cycle starts over from the new residuals
+        lowp = false;
+        gemm.lowp = false;
+        std::vector<int> nbv(nk, nb);
+        cudaMemcpyAsync(dnv, nbv.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
+        hs = cholqr(ctx, w, gemm, S, 0, nb, dnv, 2, failed);
+        if (hs != HW_OK) return hs;
+        hs = apply_block(ctx, w, kidx, S, HS, 0, nb, true);
+        if (hs != HW_OK) return hs;
+        hs = rr_subspace(ctx, w, gemm, dnv, cur, 0, 1 - cur);
+        if (hs != HW_OK) return hs;
+        cur = 1 - cur;
+        --it;
+        continue;
+      }
+      nclaim = 0;
+      std::fill(claim.begin(), claim.end(), 0);
+    }
+    for (int b = 0; b < nk; ++b) {
+      if (done[b] || !claim[b]) continue;
+      done[b] = 1;
+      it_done[b] = it;
+      for (int j = 0; j < n_eig; ++j) {
+        evals[(size_t)b * n_eig + j] = thh[(size_t)b * nb + j];
+        if (resid) resid[(size_t)b * n_eig + j] = resh[(size_t)b * nb + j];
+      }
+      if (evecs && evecs[b])
+        cudaMemcpy2DAsync(evecs[b], ld_evecs * 16, S + (size_t)b * sK, Lpad * 16, su.Lb[b] * 16, n_eig,
+                          cudaMemcpyDeviceToDevice, st);
+    }
+    bool all = true;
+    for (int b = 0; b < nk; ++b) all = all && done[b];
+    if (all) {
+      final_status = HW_OK;
+      break;
+    }
+    if (it == maxit) break;
+    // ---- the filter: Y_m = p_m(H) X in the column blocks of S (block i mod 2 holds Y_i; the
+    //      step writing Y_i reads Y_{i-2} from the same block, element by element)
+    // (k-points already done are filtered along with the rest: their blocks stay well defined)
+    ChebScal sc;
+    std::vector<double> sig(nk), tau(nk), ee(nk);
+    for (int b = 0; b < MAXSLOT; ++b) sc.al[b] = sc.c[b] = sc.be[b] = 0.0;
+    for (int b = 0; b < nk; ++b) {
+      const double a0 = thh[(size_t)b * nb], a = thh[(size_t)b * nb + nb - 1];
+      double bb = bup[b];
+      if (!(bb > a + 1e-8)) bb = a + std::max(1.0, std::fabs(a));   // bound below the block: widen
+      ee[b] = 0.5 * (bb - a);
+      sc.c[b] = 0.5 * (bb + a);
+      double den = a0 - sc.c[b];
+      if (!(den < -1e-12 * ee[b])) den = -ee[b];   // degenerate block (all Ritz values equal)
+      sig[b] = ee[b] / den;
+      tau[b] = 2.0 / sig[b];
+      sc.al[b] = sig[b] / ee[b];
+    }
+    {
+      ProfScope ps_(ctx, HW_PH_OTHER);
+      k_cheb<<<dim3(nb, nk), 256, 0, st>>>(S, HS, Lpad, sK, nb, 0, 1, sc);
+      ctx->launches++;
+    }
+    for (int i = 2; i <= m; ++i) {
+      const int src = (i - 1) % 2, dst = i % 2;
+      hs = apply_block(ctx, w, kidx, S, HS, src * nb, nb, !lowp);
+      if (hs != HW_OK) return hs;
+      for (int b = 0; b < nk; ++b) {
+        const double sn = 1.0 / (tau[b] - sig[b]);
+        sc.al[b] = 2.0 * sn / ee[b];
+        sc.be[b] = sig[b] * sn;
+        sig[b] = sn;
+      }
+      ProfScope ps_(ctx, HW_PH_OTHER);
+      k_cheb<<<dim3(nb, nk), 256, 0, st>>>(S, HS, Lpad, sK, nb, src, dst, sc);
+      ctx->launches++;
+    }
+    const int q = m % 2;
+    {
+      ProfScope ps_(ctx, HW_PH_OTHER);
+      k_colnorm<<<dim3(nb, nk), 256, 0, st>>>(S, Lpad, sK, nb, q);
+      ctx->launches++;
+    }
+    std::vector<int> nbv(nk, nb);
+    cudaMemcpyAsync(dnv, nbv.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
+    hs = cholqr(ctx, w, gemm, S, q * nb, nb, dnv, 2, failed);
+    if (hs != HW_OK) return hs;
+    for (int b = 0; b < nk; ++b)
+      if (failed[b] && !done[b])
+        return hw_fail(ctx, HW_ENOTCONV, "Chebyshev filter: the filtered block lost rank (lower the degree)");
+    hs = apply_block(ctx, w, kidx, S, HS, q * nb, nb, !lowp);
+    if (hs != HW_OK) return hs;
+    hs = rr_subspace(ctx, w, gemm, dnv, cur, q, 1 - cur);
+    if (hs != HW_OK) return hs;
+    cur = 1 - cur;
+  }
+  for (int b = 0; b < nk; ++b) {
+    if (!done[b]) {
+      for (int j = 0; j < n_eig; ++j) {
+        evals[(size_t)b * n_eig + j] = thh[(size_t)b * nb + j];
+        if (resid) resid[(size_t)b * n_eig + j] = resh[(size_t)b * nb + j];
+      }
+      if (evecs && evecs[b])
+        cudaMemcpy2DAsync(evecs[b], ld_evecs * 16, w->SB[cur] + (size_t)b * sK, Lpad * 16, su.Lb[b] * 16, n_eig,
+                          cudaMemcpyDeviceToDevice, st);
+    }
+    if (iters) iters[b] = it_done[b];
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
+  if (gemm.st != CUBLAS_STATUS_SUCCESS) return hw_fail(ctx, HW_ECUDA, "cuBLAS failure");
+  if (final_status != HW_OK) return hw_fail(ctx, HW_ENOTCONV, "maxit reached before convergence");
+  return HW_OK;
+}
+
 extern "C" hw_status hw_gram(hw_ctx* ctx, int m, int n, int K, int nprob, const double* A, int64_t lda, int64_t sA,
                               const double* B, int64_t ldb, int64_t sB, double* C, int64_t ldc, int64_t sC) {
   if (!ctx) return HW_EINVAL;
@@ -1334,6 +1688,8 @@ extern "C" hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx, int n_e
                                    int maxit, hw_prec prec, int precond_kind, const double* const* X0,
                                    double* evals, double* const* evecs, int64_t ld_evecs, int* iters,
                                    double* resid) {
+  if (ctx && ctx->eigensolver == 1)
+    return chfsi_impl(ctx, nk, kidx, n_eig, block, tol, maxit, prec, X0, evals, evecs, ld_evecs, iters, resid);
   return solve_impl(ctx, nk, kidx, n_eig, block, tol, maxit, prec, precond_kind, X0, evals, evecs, ld_evecs,
                     iters, resid, nullptr);
 }

@@ -259,6 +259,8 @@ HW_OPT_RR_FALLBACKS = 1
 HW_OPT_LOWP_SWITCH = 2
 HW_OPT_GRAM_KERNEL = 3
 HW_OPT_HYBRID = 4
+HW_OPT_EIGENSOLVER = 5
+HW_OPT_CHEB_DEGREE = 6
 
 
 def hw_set_option(h, option, value):
