@@ -15,6 +15,8 @@ Modules
   hamiltonian  Algorithm 5 (H times a block), dense assembly, direct diagonalisation
   eigensolver  plain LOBPCG with the Teter-Payne-Allan preconditioner
   mlp          reference forward/backward of the per-mode preconditioner network
+  density      electron density from converged states
+  gradient     Cartesian gradients of functions expressed in helical waves (Appendix C)
 
 Every function cites the passage of the paper it follows.  Readings of passages that are
 silent or ambiguous are listed in the repository's design notes and restated at the function.

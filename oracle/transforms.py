@@ -73,13 +73,15 @@ def angular_forward(basis, u: np.ndarray) -> np.ndarray:
     return V[np.ix_(nb, mb)].T                        # [m+M, n+N]
 
 
-def fast_inverse(basis, ghat: np.ndarray) -> np.ndarray:
+def fast_inverse(basis, ghat: np.ndarray, tables=None) -> np.ndarray:
     """Algorithm 1: G_{m,n}(r_p) = frak R_n ghat_{m,n,:} for every (m, n), then Algorithm 2 at
-    every radial node."""
+    every radial node.  tables (optional): other radial tables by n in place of frak R_n (the
+    functions B_n of Appendix C for the radial derivative)."""
+    tabs = basis.Rtab if tables is None else tables
     G = np.empty((2 * basis.M + 1, 2 * basis.N + 1, basis.Nr), dtype=np.complex128)
     for im in range(2 * basis.M + 1):
         for jn, n in enumerate(range(-basis.N, basis.N + 1)):
-            G[im, jn, :] = basis.Rtab[n] @ ghat[im, jn, :]
+            G[im, jn, :] = tabs[n] @ ghat[im, jn, :]
     g = np.empty((basis.Nth1, basis.Nth2, basis.Nr), dtype=np.complex128)
     for p in range(basis.Nr):
         g[:, :, p] = angular_inverse(basis, G[:, :, p])
