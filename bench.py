@@ -311,6 +311,26 @@ def ours_main(args):
             t = np.mean([a.elapsed_time(b) for a, b in evs])
             dens[prec] = {"states_per_s": round(ns / (t / 1e3), 1), "ms_per_call": round(float(t), 4)}
         result["density"] = {"workload": f"{w.name}, {ns} states", **dens}
+        # ---- Cartesian gradients on the grid (Appendix C) of 16 coefficient columns
+        grad = {}
+        ng = 16
+        Xg = Xb[:ng].contiguous()
+        for prec in ("fp64", "mixed"):
+            ctx.gradient(0, Xg, prec=prec)
+            with torch.cuda.stream(stream):
+                evs = []
+                for _ in range(5):
+                    flush.fill_(1.0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ctx.gradient(0, Xg, prec=prec)
+                    e1.record(stream)
+                    evs.append((e0, e1))
+            torch.cuda.synchronize(dev)
+            t = np.mean([a.elapsed_time(b) for a, b in evs])
+            grad[prec] = {"columns_per_s": round(ng / (t / 1e3), 1), "ms_per_call": round(float(t), 4)}
+        result["gradient"] = {"workload": f"{w.name}, {ng} columns, 3 Cartesian components on the grid", **grad}
         # ---- batched k-points: 32 eta points x 48 eigenpairs in one lockstep solve vs one by one
         result["batched_kpoints"] = batched_kpoints(hw, inputs, local, stream, flush, precond)
         # ---- H X on the large nanowire-like basis (L ~ 40.6k, 192 x 96 x 192 grid)

@@ -253,6 +253,18 @@ hw_status hw_heev(hw_ctx* ctx, int n, int nprob, int nw, const double* A, double
 hw_status hw_density(hw_ctx* ctx, int nk, const int* kidx, const double* const* X, int ns, int64_t ld,
                      const double* occ, const double* w, double* rho, hw_prec prec);
 
+/* Cartesian gradient on the real-space grid of E = sum Ehat_{m,n,k} F_{m,n,k} (Appendix C) for
+ * each of the ns coefficient columns X (device, complex128, L_k x ns, leading dimension ld,
+ * compact order of k-point k; no Bloch phase is applied): E_theta1 and E_theta2 are inverse
+ * transforms of (i 2 pi m) Ehat and (i 2 pi n Ncyc) Ehat (eq. Derivative_of_energy_wrt_theta),
+ * E_r the inverse transform with the radial derivative of the basis (eqs. E_r, B_r), combined by
+ * the chain rule of eq. Cartesian_Derivatives.  D: device, complex128, ns x 3 x N_th1 x N_th2 x
+ * N_r: for column c the components x, y, z, each in eq. wavefun_storage_real order (the order of
+ * hw_set_potential).  prec: HW_FP64 transforms, or HW_MIXED (FP32 radial and angular
+ * transforms, FP64 chain rule and output).  Asynchronous on the context's stream.  HW_EINVAL
+ * when one radial node's transform buffers exceed 200 KB of shared memory at that precision. */
+hw_status hw_gradient(hw_ctx* ctx, int k, const double* X, int ns, int64_t ld, double* D, hw_prec prec);
+
 /* Gram product of the eigensolver's mixed form (Sec. "Eigensolvers and Preconditioning": the
  * Rayleigh-Ritz matrices S^H H S and the orthogonalisations): C_b = A_b^H B_b for nprob
  * problems, A_b: K x m, B_b: K x n complex128 column-major device blocks (leading dimensions
@@ -326,7 +338,8 @@ typedef enum {
   HW_PH_MLP = 8,          /* preconditioner network (inference and training)                 */
   HW_PH_TRIDIAG = 9,      /* Householder reduction of the Rayleigh-Ritz matrix (FP32)        */
   HW_PH_DENSITY = 10,     /* inverse angular passes and |phi|^2 accumulation of hw_density  */
-  HW_NPHASE = 11
+  HW_PH_GRADIENT = 11,    /* inverse angular passes and chain rule of hw_gradient          */
+  HW_NPHASE = 12
 } hw_phase;
 
 /* Turn per-phase profiling on (enable != 0) or off; either resets the accumulators.  While on,

@@ -98,8 +98,11 @@ void free_basis(hw_ctx* ctx) {
   dfree(db.ke);
   dfree(db.vscratch);
   db.ke_off.clear();
-  for (auto* t : {&db.t64.rinv, &db.t64.rfwd, &db.t64.qtab, &db.t64.V, &db.t64.tw1, &db.t64.tw2}) dfree(*t);
-  for (auto* t : {&db.t32.rinv, &db.t32.rfwd, &db.t32.qtab, &db.t32.V, &db.t32.tw1, &db.t32.tw2}) dfree(*t);
+  for (auto* t : {&db.t64.rinv, &db.t64.rfwd, &db.t64.qtab, &db.t64.rder, &db.t64.V, &db.t64.tw1, &db.t64.tw2})
+    dfree(*t);
+  for (auto* t : {&db.t32.rinv, &db.t32.rfwd, &db.t32.qtab, &db.t32.rder, &db.t32.V, &db.t32.tw1, &db.t32.tw2})
+    dfree(*t);
+  dfree(db.rnodes);
   dfree(ctx->ws.gbuf);
   dfree(ctx->ws.hbuf);
   ctx->ws.cols = 0;
@@ -200,6 +203,7 @@ hw_status hw_setup_basis(hw_ctx* ctx, const hw_basis_params* params, int nk, con
         }
     std::vector<float> rinv32(rinv.begin(), rinv.end()), rfwd32(rfwd.begin(), rfwd.end());
     std::vector<float> qtab32(hb.qtab.begin(), hb.qtab.end());
+    std::vector<float> rder32(hb.xid.begin(), hb.xid.end());
     std::vector<double> tw1 = twiddles(params->Nth1), tw2 = twiddles(params->Nth2);
     std::vector<float> tw1f(tw1.begin(), tw1.end()), tw2f(tw2.begin(), tw2.end());
     std::vector<double> keall;
@@ -223,6 +227,9 @@ hw_status hw_setup_basis(hw_ctx* ctx, const hw_basis_params* params, int nk, con
     UP(db.t64.rfwd, rfwd);
     UP(db.t64.qtab, hb.qtab);
     UP(db.t32.qtab, qtab32);
+    UP(db.t64.rder, hb.xid);
+    UP(db.t32.rder, rder32);
+    UP(db.rnodes, hb.r);
     UP(db.t64.tw1, tw1);
     UP(db.t64.tw2, tw2);
     UP(db.t32.rinv, rinv32);
@@ -448,6 +455,26 @@ hw_status hw_density(hw_ctx* ctx, int nk, const int* kidx, const double* const* 
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);   // wc must outlive the copy
   if (e != cudaSuccess) return cuda_fail(ctx, e, "density");
+  return HW_OK;
+}
+
+hw_status hw_gradient(hw_ctx* ctx, int k, const double* X, int ns, int64_t ld, double* D, hw_prec prec) {
+  hw_status st = check_device_call(ctx);
+  if (st != HW_OK) return st;
+  if (k < 0 || k >= ctx->hb.nk) return hw_fail(ctx, HW_EINVAL, "k-point index out of range");
+  if (!X || !D || ns < 1 || ld < ctx->hb.L[k]) return hw_fail(ctx, HW_EINVAL, "bad gradient arguments");
+  if (prec != HW_FP64 && prec != HW_MIXED) return hw_fail(ctx, HW_EINVAL, "bad precision");
+  if (!gradient_fits(ctx, prec == HW_FP64 ? sizeof(double2) : sizeof(float2)))
+    return hw_fail(ctx, HW_EINVAL, "angular grid too large for the gradient kernel at this precision");
+  DeviceGuard g(ctx->device);
+  Blocks blk;
+  blk.nslot = 1;
+  blk.x[0] = X;
+  blk.y[0] = nullptr;
+  blk.kb[0] = k;
+  const cudaError_t e = prec == HW_FP64 ? launch_gradient<double>(ctx, blk, ns, ld, D)
+                                        : launch_gradient<float>(ctx, blk, ns, ld, D);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "gradient");
   return HW_OK;
 }
 

@@ -18,6 +18,7 @@ struct DevTables {
   T* rinv = nullptr;   // [(N+1)][Nr][K]      xi_{n,k}(r_p)
   T* rfwd = nullptr;   // [(N+1)][K][Nr]      (2 pi tau / Ncyc) w_p xi_{n,k}(r_p) / (Nth1 Nth2)
   T* qtab = nullptr;   // [(N+1)][K][K]       <F_{m,n,k'}, F_{m,n,k} / r^2> (symmetric)
+  T* rder = nullptr;   // [(N+1)][Nr][K]      d xi_{n,k} / dr at r_p (Appendix C's B_n)
   T* V = nullptr;      // [Nr][Nth2][Nth1]    potential, slab layout
   T* tw1 = nullptr;    // [2*Nth1]            e^{-2 pi i t / Nth1} as (re, im)
   T* tw2 = nullptr;    // [2*Nth2]
@@ -31,6 +32,7 @@ struct DevBasis {
   int* off = nullptr;          // [nk][nA]
   int* Ka = nullptr;           // [nk][nA]
   double* ke = nullptr;        // concatenated [sum L_b] shifted kinetic energies
+  double* rnodes = nullptr;    // [Nr] radial nodes r_p
   std::vector<int64_t> ke_off; // host: start of k-point b in ke
   double* vscratch = nullptr;  // [grid] staging for set_potential
   DevTables<double> t64;
@@ -123,6 +125,9 @@ template <typename T>
 cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld);
 cudaError_t hx_configure(hw_ctx* ctx);
 bool density_fits(const hw_ctx* ctx, size_t tsz);
+bool gradient_fits(const hw_ctx* ctx, size_t csz);
+template <typename T>
+cudaError_t launch_gradient(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, double* D);
 template <typename T>
 cudaError_t launch_density(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, const double* wcol, double* rho);
 cudaError_t hx_autotune(hw_ctx* ctx, int k, int ns, std::vector<float>& log);

@@ -210,6 +210,11 @@ struct RadArgs {
   const int* pair_n;
   int ncyc;
   double nu[MAXSLOT];
+  // inverse only: coefficients multiplied by i 2 pi m (scale_mode 1) or i 2 pi n Ncyc (2)
+  // before the transform (the theta derivatives of Appendix C); 0: as they are
+  int scale_mode;
+  const int* pair_mrow;
+  const int* mrow_m;
   cplx_t<T>* gh;              // G (inverse output) or H (forward input)
   Blocks blk;
 };
@@ -247,6 +252,11 @@ __global__ void __launch_bounds__(RAD_THREADS) k_radial_inv(RadArgs<T> A) {
       if (k < ka) {
         const double* x = A.blk.x[slot] + 2 * ((size_t)A.off[(size_t)kb * A.nA + a] + k + (size_t)s * A.ld);
         v = mk<T>(T(x[0]), T(x[1]));
+        if (A.scale_mode != 0) {   // times i s
+          const T sc = T(6.283185307179586 * (A.scale_mode == 1 ? (double)A.mrow_m[A.pair_mrow[a]]
+                                                                 : (double)A.pair_n[a] * A.ncyc));
+          v = mk<T>(-sc * v.y, sc * v.x);
+        }
       }
     }
     Xs[k * RAD_Q + q] = v;
@@ -532,6 +542,9 @@ static void set_nu_args(const hw_ctx* ctx, const Blocks& blk, const DevTables<T>
   ra.pair_n = ctx->db.pair_n;
   ra.ncyc = ctx->hb.prm.ncyc;
   for (int i = 0; i < MAXSLOT; ++i) ra.nu[i] = i < blk.nslot ? ctx->hb.nu[blk.kb[i]] : 0.0;
+  ra.scale_mode = 0;
+  ra.pair_mrow = ctx->db.pair_mrow;
+  ra.mrow_m = ctx->db.mrow_m;
 }
 
 // Launch the three kernels for the column blocks `blk` (ns columns each).  Columns are
@@ -858,6 +871,213 @@ cudaError_t launch_density(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, c
 }
 template cudaError_t launch_density<double>(hw_ctx*, const Blocks&, int, int64_t, const double*, double*);
 template cudaError_t launch_density<float>(hw_ctx*, const Blocks&, int, int64_t, const double*, double*);
+
+// --------------------------------------------------------------------------- gradients
+// Cartesian gradient of E = sum Ehat F on the grid (Appendix C): k_radial_inv gives the
+// (r_p, pair) values of E_r (radial table d xi / dr), E_theta2 (coefficients times i 2 pi n Ncyc)
+// and E_theta1 (times i 2 pi m) in three regions of G; this kernel takes each through the
+// inverse angular passes of k_slab and applies the chain rule of eq. Cartesian_Derivatives,
+//   E_x = -sin(v)/(2 pi r) E_theta2 + cos(v) E_r,  E_y = cos(v)/(2 pi r) E_theta2 + sin(v) E_r,
+//   E_z = (E_theta1 - alpha E_theta2)/tau,          v = 2 pi (alpha theta1 + theta2),
+// writing D[column][component][i][j][p] (FP64).  The three sources are taken one after the
+// other; each CTA owns its (column, r_p) outputs, so the later sources update them in place.
+template <typename T>
+struct GradArgs {
+  int Nr, Nth1, Nth2, nA, nmr, ncols, Jc, cpg, ncyc;
+  double alpha, tau;
+  FftDev p1, p2;
+  const int* pair_n;
+  const int* pair_mrow;
+  const int* mrow_m;
+  const cplx_t<T>* tw1;
+  const cplx_t<T>* tw2;
+  const cplx_t<T>* G;      // [3][column][r_p][pair]: E_r, E_theta2, E_theta1
+  const double* rnodes;    // [Nr]
+  double2* D;              // [column][3][N_th1][N_th2][N_r] of this pass
+};
+
+template <typename T, int N1 = 0, int N2 = 0>
+__global__ void __launch_bounds__(SLAB_THREADS) k_grad(GradArgs<T> A) {
+  using V = cplx_t<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = blockIdx.x, grp = blockIdx.y;
+  const int n1 = N1 > 0 ? N1 : A.Nth1, n2 = N2 > 0 ? N2 : A.Nth2, nmr = A.nmr;
+  V* Tb = reinterpret_cast<V*>(smem_raw);   // [nmr][n2]
+  const int wsz = max(nmr * n2, A.Jc * n1);
+  V* W0 = Tb + nmr * n2;
+  V* W1 = W0 + wsz;
+  const V zero = mk<T>(T(0), T(0));
+  const double r = A.rnodes[p];
+  const double inv2pir = 1.0 / (6.283185307179586 * r);
+  const size_t grid = (size_t)n1 * n2 * A.Nr;
+  const int cbeg = grp * A.cpg, cend = min(A.ncols, cbeg + A.cpg);
+  for (int c = cbeg; c < cend; ++c) {
+    double2* Dc = A.D + (size_t)c * 3 * grid;
+    for (int src = 0; src < 3; ++src) {
+      const V* Gc = A.G + (((size_t)src * A.ncols + c) * A.Nr + p) * A.nA;
+      __syncthreads();
+      for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) W0[i] = zero;
+      __syncthreads();
+      for (int a = threadIdx.x; a < A.nA; a += blockDim.x)
+        W0[A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2)] = Gc[a];
+      __syncthreads();
+      V* rr = fft_any<T, N2, false>(W0, W1, A.p2, nmr, A.tw2, +1);
+      for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) Tb[i] = rr[i];
+      __syncthreads();
+      for (int j0 = 0; j0 < n2; j0 += A.Jc) {
+        const int jn = min(A.Jc, n2 - j0);
+        for (int i = threadIdx.x; i < jn * n1; i += blockDim.x) W0[i] = zero;
+        __syncthreads();
+        for (int i = threadIdx.x; i < jn * nmr; i += blockDim.x) {
+          const int jj = i / nmr, q = i - jj * nmr;
+          W0[jj * n1 + pmod(A.mrow_m[q], n1)] = Tb[q * n2 + j0 + jj];
+        }
+        __syncthreads();
+        V* u = fft_any<T, N1, false>(W0, W1, A.p1, jn, A.tw1, +1);
+        for (int t = threadIdx.x; t < jn * n1; t += blockDim.x) {
+          const int jj = t / n1, i = t - jj * n1, j = j0 + jj;
+          const double2 x = make_double2((double)u[t].x, (double)u[t].y);
+          const size_t o = ((size_t)i * n2 + j) * A.Nr + p;
+          if (src == 2) {   // E_theta1
+            double2 z = Dc[2 * grid + o];
+            z.x += x.x / A.tau;
+            z.y += x.y / A.tau;
+            Dc[2 * grid + o] = z;
+            continue;
+          }
+          // v / pi = 2 (alpha theta1 + theta2), theta1 = i / N_th1, theta2 = j / (Ncyc N_th2)
+          double sv, cv;
+          sincospi(2.0 * (A.alpha * i / n1 + (double)j / ((double)A.ncyc * n2)), &sv, &cv);
+          if (src == 0) {   // E_r
+            Dc[o] = make_double2(cv * x.x, cv * x.y);
+            Dc[grid + o] = make_double2(sv * x.x, sv * x.y);
+            Dc[2 * grid + o] = make_double2(0.0, 0.0);
+          } else {          // E_theta2
+            const double fx = -sv * inv2pir, fy = cv * inv2pir, fz = -A.alpha / A.tau;
+            double2 a0 = Dc[o], a1 = Dc[grid + o], a2 = Dc[2 * grid + o];
+            a0.x += fx * x.x;
+            a0.y += fx * x.y;
+            a1.x += fy * x.x;
+            a1.y += fy * x.y;
+            a2.x += fz * x.x;
+            a2.y += fz * x.y;
+            Dc[o] = a0;
+            Dc[grid + o] = a1;
+            Dc[2 * grid + o] = a2;
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+template <typename T>
+static void* grad_kernel(int n1, int n2) {
+  if (n1 == 64 && n2 == 48) return (void*)k_grad<T, 64, 48>;
+  if (n1 == 192 && n2 == 96) return (void*)k_grad<T, 192, 96>;
+  return (void*)k_grad<T, 0, 0>;
+}
+
+static size_t grad_smem_bytes(const hw_ctx* ctx, size_t csz, int Jc) {
+  const auto& hb = ctx->hb;
+  const int nmr = (int)hb.mrow_m.size(), n1 = hb.prm.Nth1, n2 = hb.prm.Nth2;
+  const size_t w = (size_t)std::max(nmr * n2, Jc * n1);
+  return csz * ((size_t)nmr * n2 + 2 * w);
+}
+
+// whether the gradient kernel's shared memory fits (complex element size csz)
+bool gradient_fits(const hw_ctx* ctx, size_t csz) { return grad_smem_bytes(ctx, csz, 1) <= 200 * 1024; }
+
+// D = Cartesian gradient of the ns columns of blk (one k-point slot); D holds ns * 3 *
+// N_th1 N_th2 N_r complex128
+template <typename T>
+cudaError_t launch_gradient(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, double* D) {
+  auto& hb = ctx->hb;
+  auto& db = ctx->db;
+  const DevTables<T>& tb = *reinterpret_cast<const DevTables<T>*>(
+      sizeof(T) == 8 ? (const void*)&db.t64 : (const void*)&db.t32);
+  if (blk.nslot != 1) return cudaErrorInvalidValue;
+  const int chunk = (int)(ctx->ws.cols / 3);
+  if (chunk <= 0) return cudaErrorInvalidValue;
+  const int Nr = hb.prm.Nr, K = hb.K;
+  int Jc = hb.prm.Nth2;
+  const size_t csz = sizeof(cplx_t<T>);
+  while (Jc > 1 && grad_smem_bytes(ctx, csz, Jc) > 200 * 1024 &&
+         grad_smem_bytes(ctx, csz, (Jc + 1) / 2) < grad_smem_bytes(ctx, csz, Jc))
+    Jc = (Jc + 1) / 2;
+  const size_t sm = grad_smem_bytes(ctx, csz, Jc);
+  if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  int maxna = 0;
+  for (int g = 0; g <= hb.N; ++g) maxna = std::max(maxna, hb.group_start[g + 1] - hb.group_start[g]);
+  void* kf = grad_kernel<T>(hb.prm.Nth1, hb.prm.Nth2);
+  cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  const size_t grid_pts = (size_t)hb.prm.Nth1 * hb.prm.Nth2 * Nr;
+  for (int c0 = 0; c0 < ns; c0 += chunk) {
+    const int nc = std::min(chunk, ns - c0);
+    RadArgs<T> ra;
+    ra.Nr = Nr;
+    ra.K = K;
+    ra.nA = hb.nA;
+    ra.ncols = nc;
+    ra.ns = ns;
+    ra.c0 = c0;
+    ra.group_start = db.group_start;
+    ra.off = db.off;
+    ra.Ka = db.Ka;
+    ra.ld = ld;
+    ra.ke = db.ke;
+    ra.keoff[0] = db.ke_off[blk.kb[0]];
+    set_nu_args(ctx, blk, tb, ra);
+    ra.blk = blk;
+    dim3 grid((unsigned)(((long)maxna * nc + RAD_Q - 1) / RAD_Q), hb.N + 1);
+    const size_t sm_inv = ((size_t(Nr) * K * sizeof(T) + 15) & ~size_t(15)) + (size_t)K * RAD_Q * csz;
+    cplx_t<T>* g0 = reinterpret_cast<cplx_t<T>*>(ctx->ws.gbuf);
+    const size_t region = (size_t)nc * Nr * hb.nA;
+    for (int src = 0; src < 3; ++src) {
+      ra.gh = g0 + (size_t)src * region;
+      ra.rtab = src == 0 ? tb.rder : tb.rinv;
+      ra.scale_mode = src == 0 ? 0 : (src == 1 ? 2 : 1);
+      ProfScope ps(ctx, HW_PH_RADIAL_INV);
+      k_radial_inv<T><<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra);
+      ctx->launches++;
+    }
+    GradArgs<T> ga;
+    ga.Nr = Nr;
+    ga.Nth1 = hb.prm.Nth1;
+    ga.Nth2 = hb.prm.Nth2;
+    ga.nA = hb.nA;
+    ga.nmr = (int)hb.mrow_m.size();
+    ga.ncols = nc;
+    ga.Jc = Jc;
+    const int ncg = std::max(1, std::min(nc, (2 * 152 + Nr - 1) / Nr));
+    ga.cpg = (nc + ncg - 1) / ncg;
+    ga.ncyc = hb.prm.ncyc;
+    ga.alpha = hb.prm.alpha;
+    ga.tau = hb.prm.tau;
+    ga.p1 = to_dev(ctx->plan1);
+    ga.p2 = to_dev(ctx->plan2);
+    ga.pair_n = db.pair_n;
+    ga.pair_mrow = db.pair_mrow;
+    ga.mrow_m = db.mrow_m;
+    ga.tw1 = reinterpret_cast<const cplx_t<T>*>(tb.tw1);
+    ga.tw2 = reinterpret_cast<const cplx_t<T>*>(tb.tw2);
+    ga.G = g0;
+    ga.rnodes = db.rnodes;
+    ga.D = reinterpret_cast<double2*>(D) + (size_t)c0 * 3 * grid_pts;
+    void* args[] = {(void*)&ga};
+    {
+      ProfScope ps(ctx, HW_PH_GRADIENT);
+      e = cudaLaunchKernel(kf, dim3(Nr, (nc + ga.cpg - 1) / ga.cpg), dim3(SLAB_THREADS), args, sm, ctx->stream);
+      ctx->launches++;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_gradient<double>(hw_ctx*, const Blocks&, int, int64_t, double*);
+template cudaError_t launch_gradient<float>(hw_ctx*, const Blocks&, int, int64_t, double*);
 
 // opt in to large dynamic shared memory for every instantiation (called once at setup)
 cudaError_t hx_configure(hw_ctx* ctx) {

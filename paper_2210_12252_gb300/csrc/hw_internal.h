@@ -17,6 +17,7 @@ struct HostBasis {
   std::vector<std::vector<double>> zeros;    // zeros[|n|][k]: b_k^{|n| Ncyc}
   std::vector<double> xi;                    // [(N+1)][Nr][K]: xi_{n,k}(r_p), n >= 0
   std::vector<double> qtab;                  // [(N+1)][K][K]: <F_{m,n,k'}, F_{m,n,k} / r^2>
+  std::vector<double> xid;                   // [(N+1)][Nr][K]: d xi_{n,k} / dr at r_p
   // k-points
   int nk = 0;
   std::vector<double> eta, nu, ecut;

@@ -192,6 +192,7 @@ std::string build_host_basis(const hw_basis_params& p, int nk, const double* eta
   // J_{q-1} = -J_{q+1})
   hb.zeros.assign(N + 1, {});
   hb.xi.assign(size_t(N + 1) * Nr * K, 0.0);
+  hb.xid.assign(size_t(N + 1) * Nr * K, 0.0);
   const double pi = 3.14159265358979323846;
   for (int n = 0; n <= N; ++n) {
     const int ord = n * p.ncyc;
@@ -199,8 +200,12 @@ std::string build_host_basis(const hw_basis_params& p, int nk, const double* eta
     for (int k = 0; k < K; ++k) {
       const double b = hb.zeros[n][k];
       const double c = std::sqrt(p.ncyc / (pi * p.tau)) / (p.R * besselj(ord + 1, b));
-      for (int q = 0; q < Nr; ++q)
-        hb.xi[(size_t(n) * Nr + q) * K + k] = c * besselj(ord, b * hb.r[q] / p.R);
+      for (int q = 0; q < Nr; ++q) {
+        const double x = b * hb.r[q] / p.R;
+        hb.xi[(size_t(n) * Nr + q) * K + k] = c * besselj(ord, x);
+        // radial derivative (Appendix C, eq. B_r): c (b/R) J_p'(x), J_p' = (J_{p-1} - J_{p+1}) / 2
+        hb.xid[(size_t(n) * Nr + q) * K + k] = c * (b / p.R) * 0.5 * (besselj(ord - 1, x) - besselj(ord + 1, x));
+      }
     }
   }
   // 1/r^2 matrix of each |n| group (eqs. ell_coeff, ell_mnk, I_nkk_prime):

@@ -74,6 +74,7 @@ _SIGS = {
                           C.c_int]),
     "hw_density": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_void_p), C.c_int, C.c_int64,
                              _D, _D, C.c_void_p, C.c_int]),
+    "hw_gradient": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_int]),
     "hw_gram": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_int64,
                           C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_int64]),
     "hw_profile": (C.c_int, [C.c_void_p, C.c_int]),
@@ -96,7 +97,7 @@ _SIGS = {
 MLP_NPARAM = 4673
 
 PHASES = ["radial_inv", "slab", "radial_fwd", "precond", "gemm", "chol", "eig", "other", "mlp", "tridiag",
-          "density"]
+          "density", "gradient"]
 
 _lib = None
 
@@ -517,6 +518,18 @@ class Context:
 
     def synchronize(self):
         hw_synchronize(self.h)
+
+    def gradient(self, k, X, prec="fp64"):
+        """Cartesian gradient on the grid of the functions with coefficient columns X (torch
+        complex128 (ns, ld) on the device) at k-point k; returns a device tensor of shape
+        (ns, 3, N_th1, N_th2, N_r) (components x, y, z)."""
+        import torch
+        ns, ld = self._blk(X)
+        g = (ns, 3, self.geom.Nth1, self.geom.Nth2, self.geom.Nr)
+        D = torch.empty(g, dtype=torch.complex128, device=X.device)
+        _check(self.h, load_library().hw_gradient(self.h, k, C.c_void_p(X.data_ptr()), ns, ld,
+                                                   C.c_void_p(D.data_ptr()), _PREC[prec]))
+        return D
 
     def density(self, kidx, X, occ, w, prec="fp64"):
         """Electron density from state blocks X[b] (torch complex128 (ns, ld) on the device),
