@@ -40,6 +40,9 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precond", default="auto", choices=["auto", "tpa", "learned"])
+    ap.add_argument("--solver", default="chfsi", choices=["chfsi", "lobpcg"],
+                    help="eigensolver of the chosen form: Chebyshev-filtered FP32 phase then the "
+                         "LOBPCG mixed end phase (chfsi), or LOBPCG throughout")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="per-phase device times to stderr")
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
@@ -175,8 +178,18 @@ def ours_main(args):
     if precond == "learned":
         ctx.set_mlp(train_precond.load_weights())
 
-    def solve(prec, pc=precond, X=X0):
+    SOLVER = {"lobpcg": 0, "chfsi": 1}
+
+    def solve(prec, pc=precond, X=X0, solver=args.solver):
+        ctx.set_option(hw.HW_OPT_EIGENSOLVER, SOLVER[solver])
         return ctx.solve_eigs([0], n_eig, block=nb, tol=TOL, maxit=600, prec=prec, precond=pc, X0=[X])
+
+    if args.solver == "chfsi":
+        form = (f"Chebyshev-filtered subspace iteration (degree {ctx.get_option(hw.HW_OPT_CHEB_DEGREE)}, "
+                f"FP32 H X and products) until residual 1e-5, then LOBPCG mixed (FP32 H X, FP64 "
+                f"Gram/RR, FP64-verified claims) with the {precond} preconditioner")
+    else:
+        form = f"LOBPCG mixed: FP32 transforms + FP64 Gram/RR, {precond} preconditioner"
 
     def timed_steps(fn, steps):
         evs = []
@@ -222,7 +235,7 @@ def ours_main(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded Gaussian-well nanotube potential)",
         "config": {"workload": w.name, "L": L, "n_eig": n_eig, "block": nb, "kpoints": 1,
-                   "tol": TOL, "form": f"mixed FP32 transforms + FP64 Gram/RR, {precond} preconditioner",
+                   "tol": TOL, "form": form,
                    "l2": "flushed (512 MB write) before every step"},
         "chosen_form": {"iters": iters_mixed, "converged": conv,
                         "max_abs_err_vs_oracle_Ha": err_mixed,
@@ -251,7 +264,7 @@ def ours_main(args):
 
     if not args.quick:
         # ---- plain FP64 GPU method on the same inputs
-        ms64, r64 = timed_steps(lambda: solve("fp64", "tpa"), max(1, min(args.steps, 2)))
+        ms64, r64 = timed_steps(lambda: solve("fp64", "tpa", solver="lobpcg"), max(1, min(args.steps, 2)))
         v64 = n_eig * len(ms64) / (sum(ms64) / 1e3)
         result["plain_fp64"] = {"value": round(v64, 3), "unit": UNIT, "iters": int(r64["iters"][0]),
                                 "form": "FP64 transforms, FP64 Gram/RR, TPA preconditioner (the paper's method)",
@@ -262,7 +275,7 @@ def ours_main(args):
             ctx.profile(True)
             with torch.cuda.stream(stream):
                 flush.fill_(1.0)
-                solve("fp64", "tpa")
+                solve("fp64", "tpa", solver="lobpcg")
             print(json.dumps({"profile_fp64": ctx.profile_read()}), file=sys.stderr)
             ctx.profile(False)
         # ---- H X vec/s (64 columns, L2 flushed between reps)
@@ -332,22 +345,24 @@ def ours_main(args):
             grad[prec] = {"columns_per_s": round(ng / (t / 1e3), 1), "ms_per_call": round(float(t), 4)}
         result["gradient"] = {"workload": f"{w.name}, {ng} columns, 3 Cartesian components on the grid", **grad}
         # ---- batched k-points: 32 eta points x 48 eigenpairs in one lockstep solve vs one by one
-        result["batched_kpoints"] = batched_kpoints(hw, inputs, local, stream, flush, precond)
+        # (LOBPCG: the lockstep batch amortises its small dense steps, which dominate one
+        #  k-point; Chebyshev filtering is H X-bound and gains nothing from batching)
+        result["batched_kpoints"] = batched_kpoints(hw, inputs, local, stream, flush, precond, "lobpcg")
         # ---- H X on the large nanowire-like basis (L ~ 40.6k, 192 x 96 x 192 grid)
         result["hx_wire"] = hx_wire(hw, inputs, local, stream, flush)
-        # ---- the alternative eigensolver: Chebyshev-filtered subspace iteration, same inputs
-        cf = {"workload": w.name, "degree": None}
-        ctx.set_option(hw.HW_OPT_EIGENSOLVER, 1)
-        cf["degree"] = ctx.get_option(hw.HW_OPT_CHEB_DEGREE)
-        for prec in ("mixed", "fp64"):
-            solve(prec)
-            msc, rc = timed_steps(lambda: solve(prec), 2)
-            cf[prec] = {"eigenpairs_per_s": round(n_eig * len(msc) / (sum(msc) / 1e3), 3),
-                        "ms_per_step": round(sum(msc) / len(msc), 3), "cycles": int(rc["iters"][0]),
+        # ---- the eigensolver forms on the same inputs: the other mixed form, and Chebyshev
+        #      filtering in FP64 to the end
+        sv = {"workload": w.name, "degree": ctx.get_option(hw.HW_OPT_CHEB_DEGREE)}
+        other = "lobpcg" if args.solver == "chfsi" else "chfsi"
+        for name, prec, slv in ((f"{other}_mixed", "mixed", other), ("chfsi_fp64", "fp64", "chfsi")):
+            solve(prec, solver=slv)
+            msc, rc = timed_steps(lambda: solve(prec, solver=slv), 2)
+            sv[name] = {"eigenpairs_per_s": round(n_eig * len(msc) / (sum(msc) / 1e3), 3),
+                        "ms_per_step": round(sum(msc) / len(msc), 3), "iters": int(rc["iters"][0]),
                         "converged": bool(rc["converged"]),
                         "max_abs_err_vs_oracle_Ha": float(np.abs(rc["evals"][0] - ref).max())}
-        ctx.set_option(hw.HW_OPT_EIGENSOLVER, 0)
-        result["chfsi"] = cf
+        ctx.set_option(hw.HW_OPT_EIGENSOLVER, SOLVER[args.solver])
+        result["solvers"] = sv
         # ---- cyclic symmetry Ncyc = 3 with nu = 0, 1, 2
         result["cyclic"] = cyclic(hw, inputs, local, stream, flush)
         # ---- roofline of the dominant kernel of the chosen-form step
@@ -362,9 +377,10 @@ def ours_main(args):
         dist.destroy_process_group()
 
 
-def batched_kpoints(hw, inputs, local, stream, flush, precond):
+def batched_kpoints(hw, inputs, local, stream, flush, precond, solver="chfsi"):
     """32 k-points of the tube potential (eta ~ U[0,1), nu = 0), 48 eigenpairs each: one
-    lockstep solve of all points against the same points solved one after another."""
+    lockstep solve of all points against the same points solved one after another (with the
+    chosen eigensolver), and the lockstep solve with the other eigensolver."""
     import torch
     from paper_2210_12252_gb300 import train_precond
     wk = inputs.tube_kpoints(nk=32)
@@ -374,6 +390,8 @@ def batched_kpoints(hw, inputs, local, stream, flush, precond):
     if precond == "learned":
         ctx.set_mlp(train_precond.load_weights())
     nk, ne = len(wk.etas), wk.n_eig
+    codes = {"lobpcg": 0, "chfsi": 1}
+    ctx.set_option(hw.HW_OPT_EIGENSOLVER, codes[solver])
 
     def run(kids):
         with torch.cuda.stream(stream):
@@ -396,6 +414,10 @@ def batched_kpoints(hw, inputs, local, stream, flush, precond):
         t, r = run([k])
         ts += t
         iters_seq.append(int(r["iters"][0]))
+    other = "lobpcg" if solver == "chfsi" else "chfsi"
+    ctx.set_option(hw.HW_OPT_EIGENSOLVER, codes[other])
+    run(list(range(nk)))
+    to, ro = run(list(range(nk)))
     # time-reversal pairs are not in this set; consistency: batched = sequential eigenvalues
     out = {"workload": wk.name, "kpoints": nk, "n_eig": ne, "L_range": [int(Ls.min()), int(Ls.max())],
            "converged": bool(rb["converged"]),
@@ -404,7 +426,8 @@ def batched_kpoints(hw, inputs, local, stream, flush, precond):
            "speedup_vs_sequential": round(ts / tb, 3),
            "iters_batched_max": int(rb["iters"].max()), "iters_sequential_mean": float(np.mean(iters_seq)),
            "rr_jacobi_retries_batched": int(fb_batched),
-           "form": f"mixed, {precond} preconditioner, all k-points in lockstep"}
+           "form": f"{solver} (mixed, {precond} preconditioner), all k-points in lockstep",
+           f"value_{other}": round(nk * ne / to, 3), f"converged_{other}": bool(ro["converged"])}
     ctx.close()
     return out
 

@@ -309,11 +309,16 @@ typedef enum {
                                iterations every product becomes FP64.  0: FP64 throughout the
                                phase. */
   HW_OPT_EIGENSOLVER = 5,   /* block eigensolver of hw_solve_eigs: 0 (default) LOBPCG with the
-                               preconditioner; 1 Chebyshev-filtered subspace iteration (the
-                               preconditioner argument is then not used; maxit counts filter +
-                               Rayleigh-Ritz cycles). */
-  HW_OPT_CHEB_DEGREE = 6    /* Chebyshev filter degree (H X products per cycle), 2..64;
-                               default 16. */
+                               preconditioner; 1 Chebyshev-filtered subspace iteration: filter +
+                               Rayleigh-Ritz cycles (HW_FP64: to the end; HW_MIXED: with FP32
+                               products until the FP32 phase ends, then LOBPCG's mixed form with
+                               the preconditioner finishes from the filtered block).  iters and
+                               maxit count cycles plus LOBPCG iterations. */
+  HW_OPT_CHEB_DEGREE = 6,   /* Chebyshev filter degree (H X products per cycle), 2..64;
+                               default 24; the maximum when HW_OPT_CHEB_ADAPT is on. */
+  HW_OPT_CHEB_ADAPT = 7     /* 1 (default): each FP64 cycle takes the smallest degree (at most
+                               HW_OPT_CHEB_DEGREE) estimated to bring every unconverged wanted
+                               residual to tol; 0: always the full degree. */
 } hw_option;
 /* Set an option (HW_EINVAL for an unknown option, a read-only one or a bad value). */
 hw_status hw_set_option(hw_ctx* ctx, int option, int value);

@@ -98,7 +98,8 @@ struct hw_ctx {
   int gram_mixed = 0;          // HW_OPT_GRAM_KERNEL
   int hybrid = 1;              // HW_OPT_HYBRID
   int eigensolver = 0;         // HW_OPT_EIGENSOLVER
-  int cheb_degree = 16;        // HW_OPT_CHEB_DEGREE
+  int cheb_degree = 24;        // HW_OPT_CHEB_DEGREE
+  int cheb_adapt = 1;          // HW_OPT_CHEB_ADAPT
   int64_t rr_fallbacks = 0;    // Householder results rejected by the check (Jacobi used)
   hw::Prof prof;
 };

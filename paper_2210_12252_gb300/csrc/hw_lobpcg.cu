@@ -893,13 +893,15 @@ static hw_status solve_setup(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig,
   return HW_OK;
 }
 
-// Start block in the first nb columns of SB[0]: the caller's X0 (L_b x nb, ld L_b, zero padded)
-// or a seeded complex Gaussian block; then Cholesky-QR twice.
-static hw_status start_block(hw_ctx* ctx, SolveSetup& su, Gemm& gemm, const double* const* X0) {
+// Start block in the first nb columns of SB[0]: the caller's X0 (L_b x nb, ld L_b, zero padded),
+// a seeded complex Gaussian block, or (keep) the block already there; then Cholesky-QR twice.
+static hw_status start_block(hw_ctx* ctx, SolveSetup& su, Gemm& gemm, const double* const* X0, bool keep = false) {
   LobpcgWork* w = ctx->lw;
   const int nk = w->nk, nb = su.nb;
   cudaStream_t st = ctx->stream;
-  if (X0) {
+  if (keep) {
+    // the caller filled SB[0]
+  } else if (X0) {
     PtrArr pa;
     for (int b = 0; b < nk; ++b) {
       if (!X0[b]) return hw_fail(ctx, HW_EINVAL, "null start block");
@@ -926,7 +928,8 @@ static hw_status start_block(hw_ctx* ctx, SolveSetup& su, Gemm& gemm, const doub
 static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, int block,
                             double tol, int maxit, hw_prec prec, int precond_kind,
                             const double* const* X0, double* evals, double* const* evecs,
-                            int64_t ld_evecs, int* iters, double* resid, Trace* trace) {
+                            int64_t ld_evecs, int* iters, double* resid, Trace* trace,
+                            bool keep_start = false) {
   if (!ctx) return HW_EINVAL;
   if (precond_kind != HW_PRECOND_TPA && precond_kind != HW_PRECOND_NONE &&
       !(precond_kind == HW_PRECOND_LEARNED && ctx->mlp))
@@ -945,7 +948,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
   const double lowp_thr = (prec == HW_MIXED && ctx->lowp_exp > 0) ? std::pow(10.0, -ctx->lowp_exp) : 0.0;
   std::vector<int> failed;
   int cur = 0;
-  hs = start_block(ctx, su, gemm, X0);
+  hs = start_block(ctx, su, gemm, X0, keep_start);
   if (hs != HW_OK) return hs;
   const bool mixed = prec == HW_MIXED;
   bool fp64_products = !mixed;
@@ -1409,17 +1412,19 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
 // diagonal KE plus B^H W diag(V) B (an orthogonal projection of V, so bounded by max V) plus
 // the nu terms, bounded by their coefficient times the row-sum norm of the I_n table.
 // Mixed form: the filter's H products, the Gram matrices and the Rayleigh-Ritz products are
-// FP32 until the residuals fall below 10^-lowp_exp (or stop falling), then FP64 (X
-// re-orthonormalised and H X recomputed in FP64); convergence claims are FP64 residuals.
+// FP32 until the residuals fall below 10^-lowp_exp (or stop falling); then LOBPCG's mixed form
+// (with the given preconditioner) finishes from the filtered Ritz block.  FP64 form: filter
+// cycles to the end.
 static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, int block, double tol, int maxit,
-                            hw_prec prec, const double* const* X0, double* evals, double* const* evecs,
-                            int64_t ld_evecs, int* iters, double* resid) {
+                            hw_prec prec, int precond_kind, const double* const* X0, double* evals,
+                            double* const* evecs, int64_t ld_evecs, int* iters, double* resid) {
+  if (!ctx) return HW_EINVAL;
   Gemm gemm{ctx};
   SolveSetup su;
   hw_status hs = solve_setup(ctx, nk, kidx_in, n_eig, block, tol, maxit, prec, evals, evecs, ld_evecs, su, gemm);
   if (hs != HW_OK) return hs;
   const std::vector<int>& kidx = su.kidx;
-  const int nb = su.nb, m = ctx->cheb_degree;
+  const int nb = su.nb, mmax = ctx->cheb_degree;
   const int64_t Lpad = su.Lpad, sK = su.sK;
   int* dnv = su.dnv;
   LobpcgWork* w = ctx->lw;
@@ -1514,21 +1519,19 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
         lowp_best_it = it;
       }
       if (maxres < lowp_thr || nclaim > 0 || it - lowp_best_it >= 3) {
-        // leave the FP32 phase: X orthonormalised again and H X recomputed in FP64, then a
-        // Rayleigh-Ritz step; the cycle starts over from the new residuals
-        lowp = false;
-        gemm.lowp = false;
-        std::vector<int> nbv(nk, nb);
-        cudaMemcpyAsync(dnv, nbv.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
-        hs = cholqr(ctx, w, gemm, S, 0, nb, dnv, 2, failed);
-        if (hs != HW_OK) return hs;
-        hs = apply_block(ctx, w, kidx, S, HS, 0, nb, true);
-        if (hs != HW_OK) return hs;
-        hs = rr_subspace(ctx, w, gemm, dnv, cur, 0, 1 - cur);
-        if (hs != HW_OK) return hs;
-        cur = 1 - cur;
-        --it;
-        continue;
+        // leave the FP32 phase.  A further filter cycle would need FP64 H products (FP32 noise
+        // in a filtered block leaves residuals near ||H|| 1e-7); the end phase is handed to
+        // LOBPCG's mixed form instead (its corrections tolerate FP32 H products and every claim
+        // is an FP64 residual), started from the filtered Ritz block
+        if (cur != 0)
+          cudaMemcpy2DAsync(w->SB[0], (size_t)sK * 16, w->SB[cur], (size_t)sK * 16, (size_t)Lpad * nb * 16, nk,
+                            cudaMemcpyDeviceToDevice, st);
+        std::vector<int> itl(nk, 0);
+        hs = solve_impl(ctx, nk, kidx_in, n_eig, block, tol, std::max(1, maxit - it), prec, precond_kind, nullptr,
+                        evals, evecs, ld_evecs, itl.data(), resid, nullptr, true);
+        if (iters)
+          for (int b = 0; b < nk; ++b) iters[b] = it + itl[b];
+        return hs;
       }
       nclaim = 0;
       std::fill(claim.begin(), claim.end(), 0);
@@ -1569,6 +1572,30 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       sig[b] = ee[b] / den;
       tau[b] = 2.0 / sig[b];
       sc.al[b] = sig[b] / ee[b];
+    }
+    // degree of this cycle: the largest degree the option allows, or (adaptive, FP64 cycles)
+    // the smallest that reduces every unconverged wanted residual to tol, taking one cycle to
+    // shrink column j's error by the factor 1/T_m(|xi_j|), xi_j = (theta_j - c)/e (the filter's
+    // gain on theta_j over the damped interval).  FP32 cycles keep the full degree: their phase
+    // ends at a fixed residual anyway, and fewer products per cycle only add cycles there.
+    int m = mmax;
+    if (ctx->cheb_adapt && !lowp) {
+      const double target = tol;
+      int need = 2;
+      for (int b = 0; b < nk; ++b) {
+        if (done[b]) continue;
+        for (int j = 0; j < n_eig; ++j) {
+          const double rj = resh[(size_t)b * nb + j];
+          if (rj <= 0.5 * target) continue;
+          const double xi = std::fabs((thh[(size_t)b * nb + j] - sc.c[b]) / ee[b]);
+          if (!(xi > 1.0 + 1e-9)) {
+            need = mmax;
+            continue;
+          }
+          need = std::max(need, (int)std::ceil(std::acosh(2.0 * rj / target) / std::acosh(xi)));
+        }
+      }
+      m = std::max(2, std::min(mmax, need));
     }
     {
       ProfScope ps_(ctx, HW_PH_OTHER);
@@ -1689,7 +1716,8 @@ extern "C" hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx, int n_e
                                    double* evals, double* const* evecs, int64_t ld_evecs, int* iters,
                                    double* resid) {
   if (ctx && ctx->eigensolver == 1)
-    return chfsi_impl(ctx, nk, kidx, n_eig, block, tol, maxit, prec, X0, evals, evecs, ld_evecs, iters, resid);
+    return chfsi_impl(ctx, nk, kidx, n_eig, block, tol, maxit, prec, precond_kind, X0, evals, evecs, ld_evecs, iters,
+                      resid);
   return solve_impl(ctx, nk, kidx, n_eig, block, tol, maxit, prec, precond_kind, X0, evals, evecs, ld_evecs,
                     iters, resid, nullptr);
 }
