@@ -540,7 +540,7 @@ def roofline(result, w, ctx, L, nb):
         fl = slab_flops(w.geom, *nmr_nA) * cols * w.geom.Nr
         ach = fl / (hxm / 1e3) / 1e12
         rec.update({"bound": "alu", "achieved": round(ach, 3), "peak": round(fp32, 2), "unit": "TFLOP/s",
-                    "frac": round(ach / fp32, 4), "traffic": None,
+                    "frac": round(ach / fp32, 4), "traffic": _traffic("slab"),
                     "basis": "64-column H X launch, FP32 FMA peak 152x128x2 flop/clk at the sampled SM clock"})
     elif dom in ("radial_inv", "radial_fwd"):
         hxm = result["hx"]["mixed"]["kernel_ms"][dom]
@@ -564,13 +564,21 @@ def roofline(result, w, ctx, L, nb):
     return rec
 
 
+# committed ncu summary and kernel source of each phase whose traffic the roofline reports
+_TRAFFIC_SRC = {"tridiag": ("tridiag_tube_rr216.md", "hw_dense.cu"),
+                "slab": ("slab_mixed_tube.md", "hw_hx.cu")}
+
+
 def _traffic(phase):
     """DRAM bytes per launch of a phase's kernel from the committed ncu summary, when the
     summary was taken on the current kernel source (else None)."""
     import hashlib
     import re as _re
-    path = os.path.join(ROOT, "profiles", f"{phase}_tube_rr216.md")
-    src = os.path.join(ROOT, "paper_2210_12252_gb300", "csrc", "hw_dense.cu")
+    if phase not in _TRAFFIC_SRC:
+        return None
+    summary, source = _TRAFFIC_SRC[phase]
+    path = os.path.join(ROOT, "profiles", summary)
+    src = os.path.join(ROOT, "paper_2210_12252_gb300", "csrc", source)
     try:
         txt = open(path).read()
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -690,6 +698,7 @@ def kernel_case(args):
             pc = "learned"
         nb = w.n_eig + max(4, w.n_eig // 8)
         X0 = torch.from_numpy(np.ascontiguousarray(inputs.random_block(L, nb, 1234).T)).cuda()
+        ctx.set_option(hw.HW_OPT_EIGENSOLVER, {"lobpcg": 0, "chfsi": 1}[args.solver])
         ctx.solve_eigs([0], w.n_eig, block=nb, tol=TOL, maxit=600, prec="mixed", precond=pc, X0=[X0])
     torch.cuda.synchronize()
 
