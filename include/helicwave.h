@@ -316,9 +316,12 @@ typedef enum {
                                maxit count cycles plus LOBPCG iterations. */
   HW_OPT_CHEB_DEGREE = 6,   /* Chebyshev filter degree (H X products per cycle), 2..64;
                                default 24; the maximum when HW_OPT_CHEB_ADAPT is on. */
-  HW_OPT_CHEB_ADAPT = 7     /* 1 (default): each FP64 cycle takes the smallest degree (at most
+  HW_OPT_CHEB_ADAPT = 7,    /* 1 (default): each FP64 cycle takes the smallest degree (at most
                                HW_OPT_CHEB_DEGREE) estimated to bring every unconverged wanted
                                residual to tol; 0: always the full degree. */
+  HW_OPT_CHEB_LOCK = 8      /* 1 (default): leading Ritz columns whose residuals are below half
+                               the phase's target are not filtered (soft locking); 0: every
+                               column is filtered every cycle. */
 } hw_option;
 /* Set an option (HW_EINVAL for an unknown option, a read-only one or a bad value). */
 hw_status hw_set_option(hw_ctx* ctx, int option, int value);

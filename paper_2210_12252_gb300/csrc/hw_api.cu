@@ -564,6 +564,11 @@ hw_status hw_set_option(hw_ctx* ctx, int option, int value) {
     ctx->cheb_adapt = value;
     return HW_OK;
   }
+  if (option == HW_OPT_CHEB_LOCK) {
+    if (value != 0 && value != 1) return hw_fail(ctx, HW_EINVAL, "Chebyshev locking option 0 or 1");
+    ctx->cheb_lock = value;
+    return HW_OK;
+  }
   return hw_fail(ctx, HW_EINVAL, "unknown or read-only option");
 }
 
@@ -577,6 +582,7 @@ hw_status hw_get_option(hw_ctx* ctx, int option, long long* value) {
   if (option == HW_OPT_EIGENSOLVER) { *value = ctx->eigensolver; return HW_OK; }
   if (option == HW_OPT_CHEB_DEGREE) { *value = ctx->cheb_degree; return HW_OK; }
   if (option == HW_OPT_CHEB_ADAPT) { *value = ctx->cheb_adapt; return HW_OK; }
+  if (option == HW_OPT_CHEB_LOCK) { *value = ctx->cheb_lock; return HW_OK; }
   return hw_fail(ctx, HW_EINVAL, "unknown option");
 }
 

@@ -100,6 +100,7 @@ struct hw_ctx {
   int eigensolver = 0;         // HW_OPT_EIGENSOLVER
   int cheb_degree = 24;        // HW_OPT_CHEB_DEGREE
   int cheb_adapt = 1;          // HW_OPT_CHEB_ADAPT
+  int cheb_lock = 1;           // HW_OPT_CHEB_LOCK
   int64_t rr_fallbacks = 0;    // Householder results rejected by the check (Jacobi used)
   hw::Prof prof;
 };

@@ -295,10 +295,10 @@ struct ChebScal {
 // One recurrence step on column blocks of S (block q = columns q nb .. q nb + nb - 1):
 //   S[dst] = al_b (HS[src] - c_b S[src]) - be_b S[dst]      (be_b = 0: S[dst] is not read)
 // i.e. Y_i = al (H Y_{i-1} - c Y_{i-1}) - be Y_{i-2} with Y_{i-2} in the destination block;
-// grid (nb, nk); src != dst
-__global__ void k_cheb(double2* S, const double2* HS, int64_t Lpad, int64_t sK, int nb, int src, int dst,
+// columns j0 .. j0 + gridDim.x - 1 of each block; grid (columns, nk); src != dst
+__global__ void k_cheb(double2* S, const double2* HS, int64_t Lpad, int64_t sK, int nb, int src, int dst, int j0,
                        ChebScal sc) {
-  const int j = blockIdx.x, b = blockIdx.y;
+  const int j = j0 + blockIdx.x, b = blockIdx.y;
   const double al = sc.al[b], c = sc.c[b], be = sc.be[b];
   const size_t o = (size_t)b * sK;
   const double2* x = S + o + (size_t)(src * nb + j) * Lpad;
@@ -316,11 +316,12 @@ __global__ void k_cheb(double2* S, const double2* HS, int64_t Lpad, int64_t sK, 
   }
 }
 
-// scale each of the nb columns of block q to unit 2-norm (zero columns stay zero); grid (nb, nk)
-__global__ void k_colnorm(double2* S, int64_t Lpad, int64_t sK, int nb, int q) {
+// scale columns j0 .. j0 + gridDim.x - 1 of block q to unit 2-norm (zero columns stay zero);
+// grid (columns, nk)
+__global__ void k_colnorm(double2* S, int64_t Lpad, int64_t sK, int nb, int q, int j0) {
   __shared__ double red[32];
   __shared__ double scale;
-  const int j = blockIdx.x, b = blockIdx.y;
+  const int j = j0 + blockIdx.x, b = blockIdx.y;
   double2* y = S + (size_t)b * sK + (size_t)(q * nb + j) * Lpad;
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < Lpad; i += blockDim.x) {
@@ -1597,14 +1598,30 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       }
       m = std::max(2, std::min(mmax, need));
     }
+    // soft locking: the leading Ritz columns whose residuals are already below half the
+    // phase's target (1e-5 level in the FP32 phase, tol after it) are not filtered; they keep
+    // their place (and H X) in the block and take part in the Rayleigh-Ritz step.  The count is
+    // the smallest over the k-points still running (the batch filters one column range).
+    int nl = n_eig;
+    {
+      const double lthr = 0.5 * (lowp ? std::max(lowp_thr, tol) : tol);
+      for (int b = 0; b < nk; ++b) {
+        if (done[b]) continue;
+        int cnt = 0;
+        while (cnt < n_eig && resh[(size_t)b * nb + cnt] <= lthr) ++cnt;
+        nl = std::min(nl, cnt);
+      }
+      if (!ctx->cheb_lock) nl = 0;
+    }
+    const int na = nb - nl;   // filtered columns nl .. nb-1 (na >= nb - n_eig >= 1)
     {
       ProfScope ps_(ctx, HW_PH_OTHER);
-      k_cheb<<<dim3(nb, nk), 256, 0, st>>>(S, HS, Lpad, sK, nb, 0, 1, sc);
+      k_cheb<<<dim3(na, nk), 256, 0, st>>>(S, HS, Lpad, sK, nb, 0, 1, nl, sc);
       ctx->launches++;
     }
     for (int i = 2; i <= m; ++i) {
       const int src = (i - 1) % 2, dst = i % 2;
-      hs = apply_block(ctx, w, kidx, S, HS, src * nb, nb, !lowp);
+      hs = apply_block(ctx, w, kidx, S, HS, src * nb + nl, na, !lowp);
       if (hs != HW_OK) return hs;
       for (int b = 0; b < nk; ++b) {
         const double sn = 1.0 / (tau[b] - sig[b]);
@@ -1613,23 +1630,40 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
         sig[b] = sn;
       }
       ProfScope ps_(ctx, HW_PH_OTHER);
-      k_cheb<<<dim3(nb, nk), 256, 0, st>>>(S, HS, Lpad, sK, nb, src, dst, sc);
+      k_cheb<<<dim3(na, nk), 256, 0, st>>>(S, HS, Lpad, sK, nb, src, dst, nl, sc);
       ctx->launches++;
     }
     const int q = m % 2;
     {
       ProfScope ps_(ctx, HW_PH_OTHER);
-      k_colnorm<<<dim3(nb, nk), 256, 0, st>>>(S, Lpad, sK, nb, q);
+      k_colnorm<<<dim3(na, nk), 256, 0, st>>>(S, Lpad, sK, nb, q, nl);
       ctx->launches++;
     }
-    std::vector<int> nbv(nk, nb);
-    cudaMemcpyAsync(dnv, nbv.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
-    hs = cholqr(ctx, w, gemm, S, q * nb, nb, dnv, 2, failed);
+    double2* Yq = S + (size_t)q * nb * Lpad;    // the filtered block: [X_locked | Y_active]
+    double2* HYq = HS + (size_t)q * nb * Lpad;
+    if (nl > 0) {
+      if (q != 0) {   // the locked columns and their H products live in block 0
+        cudaMemcpy2DAsync(Yq, (size_t)sK * 16, S, (size_t)sK * 16, (size_t)nl * Lpad * 16, nk,
+                          cudaMemcpyDeviceToDevice, st);
+        cudaMemcpy2DAsync(HYq, (size_t)sK * 16, HS, (size_t)sK * 16, (size_t)nl * Lpad * 16, nk,
+                          cudaMemcpyDeviceToDevice, st);
+      }
+      // the active columns orthogonal to the locked ones (twice)
+      for (int pass = 0; pass < 2; ++pass) {
+        gemm(CUBLAS_OP_C, CUBLAS_OP_N, nl, na, (int)Lpad, 1.0, Yq, Lpad, sK, Yq + (size_t)nl * Lpad, Lpad, sK,
+             0.0, w->C, nl, (int64_t)2 * nb * nb, nk);
+        gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, na, nl, -1.0, Yq, Lpad, sK, w->C, nl, (int64_t)2 * nb * nb,
+             1.0, Yq + (size_t)nl * Lpad, Lpad, sK, nk);
+      }
+    }
+    std::vector<int> nav(nk, na);
+    cudaMemcpyAsync(dnv, nav.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
+    hs = cholqr(ctx, w, gemm, S, q * nb + nl, na, dnv, 2, failed);
     if (hs != HW_OK) return hs;
     for (int b = 0; b < nk; ++b)
       if (failed[b] && !done[b])
         return hw_fail(ctx, HW_ENOTCONV, "Chebyshev filter: the filtered block lost rank (lower the degree)");
-    hs = apply_block(ctx, w, kidx, S, HS, q * nb, nb, !lowp);
+    hs = apply_block(ctx, w, kidx, S, HS, q * nb + nl, na, !lowp);
     if (hs != HW_OK) return hs;
     hs = rr_subspace(ctx, w, gemm, dnv, cur, q, 1 - cur);
     if (hs != HW_OK) return hs;

@@ -263,6 +263,7 @@ HW_OPT_HYBRID = 4
 HW_OPT_EIGENSOLVER = 5
 HW_OPT_CHEB_DEGREE = 6
 HW_OPT_CHEB_ADAPT = 7
+HW_OPT_CHEB_LOCK = 8
 
 
 def hw_set_option(h, option, value):
