@@ -364,7 +364,7 @@ def ours_main(args):
         ctx.set_option(hw.HW_OPT_EIGENSOLVER, SOLVER[args.solver])
         result["solvers"] = sv
         # ---- cyclic symmetry Ncyc = 3 with nu = 0, 1, 2
-        result["cyclic"] = cyclic(hw, inputs, local, stream, flush)
+        result["cyclic"] = cyclic(hw, inputs, local, stream, flush, args.solver)
         # ---- roofline of the dominant kernel of the chosen-form step
         result["roofline"] = roofline(result, w, ctx, L, nb)
         # ---- end to end through the C ABI with host buffers
@@ -463,12 +463,14 @@ def hx_wire(hw, inputs, local, stream, flush):
     return out
 
 
-def cyclic(hw, inputs, local, stream, flush):
+def cyclic(hw, inputs, local, stream, flush, solver="chfsi"):
     """Ncyc = 3 tube (nu = 0, 1, 2): H X vectors/s per nu (the nu != 0 points add the 1/r^2
-    terms in the forward radial kernel) and one batched mixed solve of the three points."""
+    terms in the forward radial kernel) and one batched mixed solve of the three points with
+    the chosen eigensolver."""
     import torch
     w = inputs.tube_cyclic()
     ctx = hw.Context(local, stream=stream)
+    ctx.set_option(hw.HW_OPT_EIGENSOLVER, {"lobpcg": 0, "chfsi": 1}[solver])
     L = [int(x) for x in ctx.setup_basis(w.geom, w.etas, w.nus)]
     ctx.build_potential(w.atoms)
     ns = 64
@@ -606,7 +608,8 @@ def e2e(ctx, w, L, nb, n_eig, dev, stream, flush, args, precond):
     import torch
     from paper_2210_12252_gb300 import inputs
     V = torch.from_numpy(ctx.build_potential(w.atoms)).pin_memory()
-    X0h = torch.from_numpy(np.ascontiguousarray(inputs.random_block(L, nb, 4321).T)).pin_memory()
+    rank = int(os.environ.get("RANK", "0"))
+    X0h = torch.from_numpy(np.ascontiguousarray(inputs.random_block(L, nb, 1234 + rank).T)).pin_memory()
     Vd = torch.empty(V.shape, dtype=torch.float64, device=dev)
     X0d = torch.empty(X0h.shape, dtype=torch.complex128, device=dev)
     out = torch.empty((n_eig, L), dtype=torch.complex128).pin_memory()

@@ -222,10 +222,39 @@ struct RadArgs {
 constexpr int RAD_Q = 64;   // (column, pair) items per CTA
 constexpr int RAD_THREADS = 256;
 
+// table rows padded to a multiple of 4 entries (zeros), so that 4 consecutive entries load as
+// one (FP32) or two (FP64) 16-byte shared-memory words
+__host__ __device__ inline int pad4(int n) { return (n + 3) & ~3; }
+
+__device__ __forceinline__ void ld4(const float* p, float& a, float& b, float& c, float& d) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = v.x;
+  b = v.y;
+  c = v.z;
+  d = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double& a, double& b, double& c, double& d) {
+  const double2 v0 = reinterpret_cast<const double2*>(p)[0], v1 = reinterpret_cast<const double2*>(p)[1];
+  a = v0.x;
+  b = v0.y;
+  c = v1.x;
+  d = v1.y;
+}
+
+// dynamic shared memory of k_radial_inv / k_radial_fwd
+inline size_t rad_inv_smem(int Nr, int K, size_t tsz) {
+  return (((size_t)Nr * pad4(K) * tsz + 15) & ~size_t(15)) + (size_t)pad4(K) * RAD_Q * 2 * tsz;
+}
+inline size_t rad_fwd_smem(int Nr, int K, size_t tsz) {
+  return (((size_t)K * pad4(Nr) * tsz + 15) & ~size_t(15)) + 32 * RAD_Q * 2 * tsz + (size_t)RAD_Q * (K + 1) * 2 * tsz;
+}
+
 // grid: x = tile of items within group g, y = g.  Items of group g are (c, a) with
-// a in [gs, ge), flattened as c * na + (a - gs).
+// a in [gs, ge), flattened as c * na + (a - gs).  Each thread keeps the values of a block of
+// radial nodes of one item in registers; the table rows are read 4 entries at a time (the same
+// row for every lane of a warp: one broadcast word), the item's coefficients 4 at a time.
 template <typename T>
-__global__ void __launch_bounds__(RAD_THREADS) k_radial_inv(RadArgs<T> A) {
+__global__ void __launch_bounds__(RAD_THREADS, sizeof(T) == 4 ? 2 : 1) k_radial_inv(RadArgs<T> A) {
   using V = cplx_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = blockIdx.y;
@@ -233,14 +262,17 @@ __global__ void __launch_bounds__(RAD_THREADS) k_radial_inv(RadArgs<T> A) {
   const long nitems = (long)na * A.ncols;
   const long q0 = (long)blockIdx.x * RAD_Q;
   if (na == 0 || q0 >= nitems) return;
-  const int K = A.K, Nr = A.Nr;
-  T* Rs = reinterpret_cast<T*>(smem_raw);                 // [Nr][K]
-  V* Xs = reinterpret_cast<V*>(smem_raw + (((size_t)Nr * K * sizeof(T) + 15) & ~size_t(15)));  // [K][RAD_Q]
+  const int K = A.K, Nr = A.Nr, Kp = pad4(K);
+  T* Rs = reinterpret_cast<T*>(smem_raw);                 // [Nr][Kp]
+  V* Xs = reinterpret_cast<V*>(smem_raw + (((size_t)Nr * Kp * sizeof(T) + 15) & ~size_t(15)));  // [Kp][RAD_Q]
   const T* tab = A.rtab + (size_t)g * Nr * K;
-  for (int i = threadIdx.x; i < Nr * K; i += blockDim.x) Rs[i] = tab[i];
+  for (int i = threadIdx.x; i < Nr * Kp; i += blockDim.x) {
+    const int p = i / Kp, k = i - p * Kp;
+    Rs[i] = k < K ? tab[(size_t)p * K + k] : T(0);
+  }
   // gather the kept coefficients of each item (zero beyond Ka)
-  for (int i = threadIdx.x; i < RAD_Q * K; i += blockDim.x) {
-    const int q = i / K, k = i - q * K;
+  for (int i = threadIdx.x; i < RAD_Q * Kp; i += blockDim.x) {
+    const int q = i / Kp, k = i - q * Kp;
     const long item = q0 + q;
     V v = mk<T>(T(0), T(0));
     if (item < nitems) {
@@ -267,22 +299,48 @@ __global__ void __launch_bounds__(RAD_THREADS) k_radial_inv(RadArgs<T> A) {
   if (item >= nitems) return;
   const int c = (int)(item / na), a = gs + (int)(item - (long)c * na);
   V* out = A.gh + ((size_t)c * Nr) * A.nA + a;
-  for (int p = threadIdx.x / RAD_Q; p < Nr; p += RAD_THREADS / RAD_Q) {
-    T ax = 0, ay = 0;
-    const T* rr = Rs + p * K;
+  constexpr int PG = RAD_THREADS / RAD_Q;            // node groups
+  if constexpr (sizeof(T) == 8) {
+    // FP64: bound by the FP64 pipe; one node at a time keeps more CTAs resident
+    for (int p = threadIdx.x / RAD_Q; p < Nr; p += PG) {
+      T ax = 0, ay = 0;
+      const T* rr = Rs + (size_t)p * Kp;
 #pragma unroll 4
-    for (int k = 0; k < K; ++k) {
-      const V xv = Xs[k * RAD_Q + q];
-      ax += rr[k] * xv.x;
-      ay += rr[k] * xv.y;
+      for (int k = 0; k < K; ++k) {
+        const V xv = Xs[k * RAD_Q + q];
+        ax += rr[k] * xv.x;
+        ay += rr[k] * xv.y;
+      }
+      out[(size_t)p * A.nA] = mk<T>(ax, ay);
     }
-    out[(size_t)p * A.nA] = mk<T>(ax, ay);
+    return;
+  }
+  constexpr int PP = 12;                             // nodes per register block
+  for (int pb = (threadIdx.x / RAD_Q) * PP; pb < Nr; pb += PG * PP) {
+    T ax[PP], ay[PP];
+#pragma unroll
+    for (int i = 0; i < PP; ++i) ax[i] = ay[i] = T(0);
+    for (int k0 = 0; k0 < Kp; k0 += 4) {
+      const V x0 = Xs[k0 * RAD_Q + q], x1 = Xs[(k0 + 1) * RAD_Q + q];
+      const V x2 = Xs[(k0 + 2) * RAD_Q + q], x3 = Xs[(k0 + 3) * RAD_Q + q];
+#pragma unroll
+      for (int i = 0; i < PP; ++i) {
+        const int p = min(pb + i, Nr - 1);   // nodes past Nr are computed, not stored
+        T r0, r1, r2, r3;
+        ld4(Rs + (size_t)p * Kp + k0, r0, r1, r2, r3);
+        ax[i] += r0 * x0.x + r1 * x1.x + r2 * x2.x + r3 * x3.x;
+        ay[i] += r0 * x0.y + r1 * x1.y + r2 * x2.y + r3 * x3.y;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < PP; ++i)
+      if (pb + i < Nr) out[(size_t)(pb + i) * A.nA] = mk<T>(ax[i], ay[i]);
   }
 }
 
 // forward radial quadrature + diagonal term + scatter
 template <typename T>
-__global__ void __launch_bounds__(RAD_THREADS) k_radial_fwd(RadArgs<T> A) {
+__global__ void __launch_bounds__(RAD_THREADS, sizeof(T) == 4 ? 2 : 1) k_radial_fwd(RadArgs<T> A) {
   using V = cplx_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = blockIdx.y;
@@ -290,15 +348,18 @@ __global__ void __launch_bounds__(RAD_THREADS) k_radial_fwd(RadArgs<T> A) {
   const long nitems = (long)na * A.ncols;
   const long q0 = (long)blockIdx.x * RAD_Q;
   if (na == 0 || q0 >= nitems) return;
-  const int K = A.K, Nr = A.Nr;
+  const int K = A.K, Nr = A.Nr, Nrp = pad4(Nr);
   constexpr int PC = 32;                                   // radial nodes per chunk
-  T* Rs = reinterpret_cast<T*>(smem_raw);                  // [K][Nr]
-  size_t o = (((size_t)K * Nr * sizeof(T)) + 15) & ~size_t(15);
+  T* Rs = reinterpret_cast<T*>(smem_raw);                  // [K][Nrp]
+  size_t o = (((size_t)K * Nrp * sizeof(T)) + 15) & ~size_t(15);
   V* Hs = reinterpret_cast<V*>(smem_raw + o);              // [PC][RAD_Q]
   o += (size_t)PC * RAD_Q * sizeof(V);
   V* Ys = reinterpret_cast<V*>(smem_raw + o);              // [RAD_Q][K+1]
   const T* tab = A.rtab + (size_t)g * K * Nr;
-  for (int i = threadIdx.x; i < K * Nr; i += blockDim.x) Rs[i] = tab[i];
+  for (int i = threadIdx.x; i < K * Nrp; i += blockDim.x) {
+    const int k = i / Nrp, pp = i - k * Nrp;
+    Rs[i] = pp < Nr ? tab[(size_t)k * Nr + pp] : T(0);
+  }
   const int q = threadIdx.x % RAD_Q;
   const int kg = threadIdx.x / RAD_Q;                      // 4 groups of k
   constexpr int KG = RAD_THREADS / RAD_Q;
@@ -315,30 +376,48 @@ __global__ void __launch_bounds__(RAD_THREADS) k_radial_fwd(RadArgs<T> A) {
   for (int p0 = 0; p0 < Nr; p0 += PC) {
     const int pc = min(PC, Nr - p0);
     __syncthreads();
-    for (int i = threadIdx.x; i < pc * RAD_Q; i += blockDim.x) {
+    for (int i = threadIdx.x; i < PC * RAD_Q; i += blockDim.x) {   // zero past pc
       const int pp = i / RAD_Q, qq = i - pp * RAD_Q;
       const long it = q0 + qq;
       V v = mk<T>(T(0), T(0));
-      if (it < nitems) {
+      if (it < nitems && pp < pc) {
         const int cc = (int)(it / na), aa = gs + (int)(it - (long)cc * na);
         v = A.gh[((size_t)cc * Nr + p0 + pp) * A.nA + aa];
       }
       Hs[pp * RAD_Q + qq] = v;
     }
     __syncthreads();
+    if constexpr (sizeof(T) == 8) {   // FP64: one node at a time (bound by the FP64 pipe)
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int k = kg + j * KG;
-      if (j < kper && k < K) {
-        T ax = acc[2 * j], ay = acc[2 * j + 1];
-        const T* rr = Rs + (size_t)k * Nr + p0;
-        for (int pp = 0; pp < pc; ++pp) {
-          const V hv = Hs[pp * RAD_Q + q];
-          ax += rr[pp] * hv.x;
-          ay += rr[pp] * hv.y;
+      for (int j = 0; j < 16; ++j) {
+        const int k = kg + j * KG;
+        if (j < kper && k < K) {
+          T ax = acc[2 * j], ay = acc[2 * j + 1];
+          const T* rr = Rs + (size_t)k * Nrp + p0;
+          for (int pp = 0; pp < pc; ++pp) {
+            const V hv = Hs[pp * RAD_Q + q];
+            ax += rr[pp] * hv.x;
+            ay += rr[pp] * hv.y;
+          }
+          acc[2 * j] = ax;
+          acc[2 * j + 1] = ay;
         }
-        acc[2 * j] = ax;
-        acc[2 * j + 1] = ay;
+      }
+      continue;
+    }
+    // 4 nodes at a time: the item's 4 values once, each table row's 4 entries as one word
+    for (int pp = 0; pp < pc; pp += 4) {
+      const V h0 = Hs[pp * RAD_Q + q], h1 = Hs[(pp + 1) * RAD_Q + q];
+      const V h2 = Hs[(pp + 2) * RAD_Q + q], h3 = Hs[(pp + 3) * RAD_Q + q];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int k = kg + j * KG;
+        if (j < kper && k < K) {
+          T r0, r1, r2, r3;
+          ld4(Rs + (size_t)k * Nrp + p0 + pp, r0, r1, r2, r3);
+          acc[2 * j] += r0 * h0.x + r1 * h1.x + r2 * h2.x + r3 * h3.x;
+          acc[2 * j + 1] += r0 * h0.y + r1 * h1.y + r2 * h2.y + r3 * h3.y;
+        }
       }
     }
   }
@@ -584,8 +663,7 @@ cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld) {
     ra.gh = reinterpret_cast<cplx_t<T>*>(ctx->ws.gbuf);
     ra.rtab = tb.rinv;
     dim3 grid((unsigned)(((long)maxna * nc + RAD_Q - 1) / RAD_Q), hb.N + 1);
-    const size_t sm_inv = ((size_t(Nr) * K * sizeof(T) + 15) & ~size_t(15)) +
-                          (size_t)K * RAD_Q * sizeof(cplx_t<T>);
+    const size_t sm_inv = rad_inv_smem(Nr, K, sizeof(T));
     {
       ProfScope ps(ctx, HW_PH_RADIAL_INV);
       k_radial_inv<T><<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra);
@@ -617,8 +695,7 @@ cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld) {
     }
     ra.gh = reinterpret_cast<cplx_t<T>*>(ctx->ws.hbuf);
     ra.rtab = tb.rfwd;
-    const size_t sm_fwd = ((size_t(K) * Nr * sizeof(T) + 15) & ~size_t(15)) +
-                          32 * RAD_Q * sizeof(cplx_t<T>) + (size_t)RAD_Q * (K + 1) * sizeof(cplx_t<T>);
+    const size_t sm_fwd = rad_fwd_smem(Nr, K, sizeof(T));
     {
       ProfScope ps(ctx, HW_PH_RADIAL_FWD);
       k_radial_fwd<T><<<grid, RAD_THREADS, sm_fwd, ctx->stream>>>(ra);
@@ -662,8 +739,7 @@ cudaError_t launch_hx_into(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, v
     ra.gh = reinterpret_cast<cplx_t<T>*>(gbuf);
     ra.rtab = tb.rinv;
     dim3 grid((unsigned)(((long)maxna * nc + RAD_Q - 1) / RAD_Q), hb.N + 1);
-    const size_t sm_inv = ((size_t(Nr) * K * sizeof(T) + 15) & ~size_t(15)) +
-                          (size_t)K * RAD_Q * sizeof(cplx_t<T>);
+    const size_t sm_inv = rad_inv_smem(Nr, K, sizeof(T));
     k_radial_inv<T><<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra);
     SlabArgs<T> sa;
     sa.Nr = Nr;
@@ -686,8 +762,7 @@ cudaError_t launch_hx_into(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, v
     launch_slab<T>(ctx, dim3(nc, Nr), slab_smem_bytes(ctx, sizeof(cplx_t<T>), Jc), sa);
     ra.gh = reinterpret_cast<cplx_t<T>*>(hbuf);
     ra.rtab = tb.rfwd;
-    const size_t sm_fwd = ((size_t(K) * Nr * sizeof(T) + 15) & ~size_t(15)) +
-                          32 * RAD_Q * sizeof(cplx_t<T>) + (size_t)RAD_Q * (K + 1) * sizeof(cplx_t<T>);
+    const size_t sm_fwd = rad_fwd_smem(Nr, K, sizeof(T));
     k_radial_fwd<T><<<grid, RAD_THREADS, sm_fwd, ctx->stream>>>(ra);
     ctx->launches += 3;
   }
@@ -832,8 +907,7 @@ cudaError_t launch_density(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, c
     ra.gh = reinterpret_cast<cplx_t<T>*>(ctx->ws.gbuf);
     ra.rtab = tb.rinv;
     dim3 grid((unsigned)(((long)maxna * nc + RAD_Q - 1) / RAD_Q), hb.N + 1);
-    const size_t sm_inv = ((size_t(Nr) * K * sizeof(T) + 15) & ~size_t(15)) +
-                          (size_t)K * RAD_Q * sizeof(cplx_t<T>);
+    const size_t sm_inv = rad_inv_smem(Nr, K, sizeof(T));
     {
       ProfScope ps(ctx, HW_PH_RADIAL_INV);
       k_radial_inv<T><<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra);
@@ -1032,7 +1106,7 @@ cudaError_t launch_gradient(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, 
     set_nu_args(ctx, blk, tb, ra);
     ra.blk = blk;
     dim3 grid((unsigned)(((long)maxna * nc + RAD_Q - 1) / RAD_Q), hb.N + 1);
-    const size_t sm_inv = ((size_t(Nr) * K * sizeof(T) + 15) & ~size_t(15)) + (size_t)K * RAD_Q * csz;
+    const size_t sm_inv = rad_inv_smem(Nr, K, sizeof(T));
     cplx_t<T>* g0 = reinterpret_cast<cplx_t<T>*>(ctx->ws.gbuf);
     const size_t region = (size_t)nc * Nr * hb.nA;
     for (int src = 0; src < 3; ++src) {

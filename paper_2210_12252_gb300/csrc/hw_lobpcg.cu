@@ -1479,7 +1479,7 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
   std::vector<char> done(nk, 0);
   std::vector<int> it_done(nk, maxit);
   std::vector<double> resh((size_t)nk * nb), thh((size_t)nk * nb);
-  double lowp_best = 1e300;
+  double lowp_best = 1e300, lowp_prev = 1e300;
   int lowp_best_it = 0;
   hw_status final_status = HW_ENOTCONV;
   std::vector<int> failed;
@@ -1519,7 +1519,11 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
         lowp_best = maxres;
         lowp_best_it = it;
       }
-      if (maxres < lowp_thr || nclaim > 0 || it - lowp_best_it >= 3) {
+      // a filter cycle shrinks the residuals by an order of magnitude or more until the FP32
+      // rounding floor; less than a halving means the floor is reached
+      const bool stalled = maxres > 0.5 * lowp_prev;
+      lowp_prev = maxres;
+      if (maxres < lowp_thr || nclaim > 0 || stalled || it - lowp_best_it >= 3) {
         // leave the FP32 phase.  A further filter cycle would need FP64 H products (FP32 noise
         // in a filtered block leaves residuals near ||H|| 1e-7); the end phase is handed to
         // LOBPCG's mixed form instead (its corrections tolerate FP32 H products and every claim
