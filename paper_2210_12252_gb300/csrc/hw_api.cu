@@ -569,6 +569,11 @@ hw_status hw_set_option(hw_ctx* ctx, int option, int value) {
     ctx->cheb_lock = value;
     return HW_OK;
   }
+  if (option == HW_OPT_SLAB_KERNEL) {
+    if (value != 0 && value != 1) return hw_fail(ctx, HW_EINVAL, "slab kernel option 0 (FFT) or 1 (4 x 16)");
+    ctx->slab_r16 = value;
+    return HW_OK;
+  }
   return hw_fail(ctx, HW_EINVAL, "unknown or read-only option");
 }
 
@@ -583,6 +588,7 @@ hw_status hw_get_option(hw_ctx* ctx, int option, long long* value) {
   if (option == HW_OPT_CHEB_DEGREE) { *value = ctx->cheb_degree; return HW_OK; }
   if (option == HW_OPT_CHEB_ADAPT) { *value = ctx->cheb_adapt; return HW_OK; }
   if (option == HW_OPT_CHEB_LOCK) { *value = ctx->cheb_lock; return HW_OK; }
+  if (option == HW_OPT_SLAB_KERNEL) { *value = ctx->slab_r16; return HW_OK; }
   return hw_fail(ctx, HW_EINVAL, "unknown option");
 }
 

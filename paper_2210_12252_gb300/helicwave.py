@@ -264,6 +264,7 @@ HW_OPT_EIGENSOLVER = 5
 HW_OPT_CHEB_DEGREE = 6
 HW_OPT_CHEB_ADAPT = 7
 HW_OPT_CHEB_LOCK = 8
+HW_OPT_SLAB_KERNEL = 9
 
 
 def hw_set_option(h, option, value):

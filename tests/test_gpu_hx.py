@@ -148,3 +148,20 @@ def test_set_potential_from_device_matches_host_build(tube):
     Y = from_dev(tube.ctx.apply_H(0, to_dev(X)), kp.L)
     assert rel_err(Y, Hm.apply_H(kp, tube.V, X)) < FP64_TOL
     tube.ctx.build_potential(tube.w.atoms)   # restore the library-built V
+
+
+def test_apply_H_mixed_tube_slab_variants_agree(tube, hwmod):
+    """The FP32 angular kernel on the 64 x 48 grid: the 4 x 16 register-DFT theta1 variant
+    (default) and the Stockham FFTs agree with each other at FP32 rounding and with the oracle
+    within the mixed tolerance."""
+    kp = tube.kps[0]
+    X = inputs.random_block(kp.L, 5, 81)
+    Yref = Hm.apply_H(kp, tube.V, X)
+    Xd = to_dev(X)
+    out = {}
+    for v in (1, 0):
+        tube.ctx.set_option(hwmod.HW_OPT_SLAB_KERNEL, v)
+        out[v] = from_dev(tube.ctx.apply_H(0, Xd, prec="mixed"), kp.L)
+        assert rel_err(out[v], Yref) < MIXED_TOL
+    tube.ctx.set_option(hwmod.HW_OPT_SLAB_KERNEL, 1)
+    assert rel_err(out[1], out[0]) < MIXED_TOL
