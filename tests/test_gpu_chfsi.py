@@ -58,6 +58,20 @@ def test_chfsi_tiny_fp64_matches_dense_oracle(hwmod, degree):
     assert res.max().item() <= 1.01e-6
 
 
+@pytest.mark.parametrize("lock,adapt", [(0, 0), (0, 1), (1, 0)])
+def test_chfsi_tube_fp64_option_paths(hwmod, lock, adapt):
+    """The non-default paths: every column filtered every cycle and/or the full degree in every
+    FP64 cycle reach the same eigenvalues."""
+    w = inputs.tube()
+    ctx, L = make_ctx(hwmod, w)
+    ctx.set_option(hwmod.HW_OPT_CHEB_LOCK, lock)
+    ctx.set_option(hwmod.HW_OPT_CHEB_ADAPT, adapt)
+    r = ctx.solve_eigs([0], 32, tol=1e-6, maxit=100)
+    assert r["converged"]
+    assert np.abs(r["evals"][0] - golden("tube_eigs.txt")[:32]).max() < 1e-8
+    assert r["resid"].max() <= 1e-6
+
+
 def test_chfsi_tiny_cyclic_nu_fp64(hwmod):
     """nu != 0 points (the spectral bound carries the 1/r^2 term) in one batched solve."""
     w = inputs.tiny_cyclic()
