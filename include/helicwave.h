@@ -322,10 +322,15 @@ typedef enum {
   HW_OPT_CHEB_LOCK = 8,     /* 1 (default): leading Ritz columns whose residuals are below half
                                the phase's target are not filtered (soft locking); 0: every
                                column is filtered every cycle. */
-  HW_OPT_SLAB_KERNEL = 9    /* FP32 angular kernel on the 64 x 48 grid: 1 (default) the theta1
+  HW_OPT_SLAB_KERNEL = 9,   /* FP32 angular kernel on the 64 x 48 grid: 1 (default) the theta1
                                transforms split 64 = 4 x 16 over the 4 lanes of a theta2 row
                                (register DFTs, shuffles), 0 the Stockham FFTs (every other grid
                                and FP64 use the FFTs). */
+  HW_OPT_TAIL_NO_P = 10     /* Chebyshev solver, mixed form: 1 (default) starts the LOBPCG end
+                               phase without conjugate directions (Rayleigh-Ritz on [X W], each
+                               iteration cheaper) and switches them on for good once an
+                               iteration fails to halve the largest wanted residual; 0: with
+                               them from the start. */
 } hw_option;
 /* Set an option (HW_EINVAL for an unknown option, a read-only one or a bad value). */
 hw_status hw_set_option(hw_ctx* ctx, int option, int value);

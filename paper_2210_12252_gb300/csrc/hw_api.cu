@@ -564,6 +564,11 @@ hw_status hw_set_option(hw_ctx* ctx, int option, int value) {
     ctx->cheb_adapt = value;
     return HW_OK;
   }
+  if (option == HW_OPT_TAIL_NO_P) {
+    if (value != 0 && value != 1) return hw_fail(ctx, HW_EINVAL, "end-phase option 0 or 1");
+    ctx->tail_no_p = value;
+    return HW_OK;
+  }
   if (option == HW_OPT_CHEB_LOCK) {
     if (value != 0 && value != 1) return hw_fail(ctx, HW_EINVAL, "Chebyshev locking option 0 or 1");
     ctx->cheb_lock = value;
@@ -588,6 +593,7 @@ hw_status hw_get_option(hw_ctx* ctx, int option, long long* value) {
   if (option == HW_OPT_CHEB_DEGREE) { *value = ctx->cheb_degree; return HW_OK; }
   if (option == HW_OPT_CHEB_ADAPT) { *value = ctx->cheb_adapt; return HW_OK; }
   if (option == HW_OPT_CHEB_LOCK) { *value = ctx->cheb_lock; return HW_OK; }
+  if (option == HW_OPT_TAIL_NO_P) { *value = ctx->tail_no_p; return HW_OK; }
   if (option == HW_OPT_SLAB_KERNEL) { *value = ctx->slab_r16; return HW_OK; }
   return hw_fail(ctx, HW_EINVAL, "unknown option");
 }

@@ -930,7 +930,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
                             double tol, int maxit, hw_prec prec, int precond_kind,
                             const double* const* X0, double* evals, double* const* evecs,
                             int64_t ld_evecs, int* iters, double* resid, Trace* trace,
-                            bool keep_start = false) {
+                            bool keep_start = false, bool no_p = false) {
   if (!ctx) return HW_EINVAL;
   if (precond_kind != HW_PRECOND_TPA && precond_kind != HW_PRECOND_NONE &&
       !(precond_kind == HW_PRECOND_LEARNED && ctx->mlp))
@@ -975,6 +975,11 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
   double hyb_best = 1e300;
   int hyb_best_it = 0;
   int it = 0;
+  // no_p: start without conjugate directions; they are switched on for good once an iteration
+  // fails to halve the largest wanted residual
+  bool p_off = no_p;
+  double p_prev = 1e300;
+  int p_it = -1;
   hw_status final_status = HW_ENOTCONV;
   for (it = 0; it <= maxit; ++it) {
     double2* S = w->SB[cur];
@@ -1032,6 +1037,11 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     }
     // the hybrid FP64 phase stalls near residual 3e-7: it hands over to all-FP64 products when
     // the best residual has not dropped by 30% in 4 iterations
+    if (p_off) {   // (a repeated check of the same iteration, after a precision switch, only updates)
+      if (it > p_it && p_it >= 0 && maxres > 0.5 * p_prev) p_off = false;
+      p_prev = maxres;
+      p_it = it;
+    }
     bool hyb_stall = false;
     if (mixed && !gemm.lowp && hyb_on) {
       if (maxres < 0.7 * hyb_best) {
@@ -1275,6 +1285,8 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     gemm.lowp = lowp_now || hyb;
     for (int b = 0; b < nk; ++b)
       cudaMemcpyAsync(w->theta + (size_t)b * nb, w->w + (size_t)b * n, nb * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    bool pfail = p_off;   // p_off: no conjugate directions this iteration (subspace [X W])
+    if (!p_off) {
     // ---- P = S Y (active columns), Y orthogonal to Z[:, :nb] and orthonormal
     {
       ProfScope ps_(ctx, HW_PH_OTHER);
@@ -1288,7 +1300,6 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
            w->Y, n, (int64_t)n * na, nk);
     }
     // small-space Cholesky-QR of Y (FP32 factor in the FP32-product phase, FP64 retry)
-    bool pfail = false;
     for (int pass = 0; pass < 2; ++pass) {
       for (int attempt = gemm.lowp ? 0 : 1; attempt < 2; ++attempt) {
         const bool fp32 = attempt == 0;
@@ -1318,6 +1329,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
         if (!anyf) break;
         if (!fp32) pfail = true;
       }
+    }
     }
     if (pfail) {
       np = 0;   // restart the conjugate directions everywhere
@@ -1414,8 +1426,8 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
 // the nu terms, bounded by their coefficient times the row-sum norm of the I_n table.
 // Mixed form: the filter's H products, the Gram matrices and the Rayleigh-Ritz products are
 // FP32 until the residuals fall below 10^-lowp_exp (or stop falling); then LOBPCG's mixed form
-// (with the given preconditioner) finishes from the filtered Ritz block.  FP64 form: filter
-// cycles to the end.
+// (with the given preconditioner; by default without conjugate directions, HW_OPT_TAIL_NO_P)
+// finishes from the filtered Ritz block.  FP64 form: filter cycles to the end.
 static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, int block, double tol, int maxit,
                             hw_prec prec, int precond_kind, const double* const* X0, double* evals,
                             double* const* evecs, int64_t ld_evecs, int* iters, double* resid) {
@@ -1533,7 +1545,7 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
                             cudaMemcpyDeviceToDevice, st);
         std::vector<int> itl(nk, 0);
         hs = solve_impl(ctx, nk, kidx_in, n_eig, block, tol, std::max(1, maxit - it), prec, precond_kind, nullptr,
-                        evals, evecs, ld_evecs, itl.data(), resid, nullptr, true);
+                        evals, evecs, ld_evecs, itl.data(), resid, nullptr, true, ctx->tail_no_p != 0);
         if (iters)
           for (int b = 0; b < nk; ++b) iters[b] = it + itl[b];
         return hs;

@@ -265,6 +265,7 @@ HW_OPT_CHEB_DEGREE = 6
 HW_OPT_CHEB_ADAPT = 7
 HW_OPT_CHEB_LOCK = 8
 HW_OPT_SLAB_KERNEL = 9
+HW_OPT_TAIL_NO_P = 10
 
 
 def hw_set_option(h, option, value):
