@@ -594,24 +594,35 @@ def roofline(result, w, ctx, L, nb):
     return rec
 
 
-# committed ncu summary and kernel source of each phase whose traffic the roofline reports
-_TRAFFIC_SRC = {"tridiag": ("tridiag_tube_rr216.md", "hw_dense.cu"),
-                "slab": ("slab_mixed_tube.md", "hw_hx.cu")}
+# committed ncu summary of each phase whose traffic the roofline reports, the kernel's source
+# file and the markers delimiting the kernel's own source text in it (None: the whole file)
+_TRAFFIC_SRC = {"tridiag": ("tridiag_tube_rr216.md", "hw_dense.cu", None),
+                "slab": ("slab_mixed_tube.md", "hw_hx.cu",
+                         ("// 16-point DFT in registers", "static size_t slab_r16_smem_bytes"))}
+
+
+def kernel_source_sha(source, markers):
+    """sha256[:16] of a kernel's source text (between the markers, or the whole file)."""
+    import hashlib
+    data = open(os.path.join(ROOT, "paper_2210_12252_gb300", "csrc", source), "rb").read()
+    if markers is not None:
+        a = data.index(markers[0].encode())
+        b = data.index(markers[1].encode(), a)
+        data = data[a:b]
+    return hashlib.sha256(data).hexdigest()[:16]
 
 
 def _traffic(phase):
     """DRAM bytes per launch of a phase's kernel from the committed ncu summary, when the
     summary was taken on the current kernel source (else None)."""
-    import hashlib
     import re as _re
     if phase not in _TRAFFIC_SRC:
         return None
-    summary, source = _TRAFFIC_SRC[phase]
+    summary, source, markers = _TRAFFIC_SRC[phase]
     path = os.path.join(ROOT, "profiles", summary)
-    src = os.path.join(ROOT, "paper_2210_12252_gb300", "csrc", source)
     try:
         txt = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = kernel_source_sha(source, markers)
         m = _re.search(r"source sha256\[:16\]: `([0-9a-f]+)`", txt)
         t = _re.search(r"dram bytes per launch: ([0-9]+)", txt)
         if m and t and m.group(1) == sha:

@@ -209,6 +209,7 @@ struct RadArgs {
   const T* qtab;
   const int* pair_n;
   int ncyc;
+  int any_nu;                 // some block of this launch has nu != 0
   double nu[MAXSLOT];
   // inverse only: coefficients multiplied by i 2 pi m (scale_mode 1) or i 2 pi n Ncyc (2)
   // before the transform (the theta derivatives of Appendix C); 0: as they are
@@ -427,6 +428,30 @@ __global__ void __launch_bounds__(RAD_THREADS, sizeof(T) == 4 ? 2 : 1) k_radial_
     if (j < kper && k < K) Ys[q * (K + 1) + k] = mk<T>(acc[2 * j], acc[2 * j + 1]);
   }
   __syncthreads();
+  if (!A.any_nu) {
+    // scatter without nu terms: (item, k) pairs over all threads, several independent global
+    // round trips in flight per thread
+#pragma unroll 2
+    for (int idx = threadIdx.x; idx < RAD_Q * K; idx += RAD_THREADS) {
+      const int qq = idx / K, k = idx - qq * K;
+      const long it = q0 + qq;
+      if (it >= nitems) continue;
+      const int cc = (int)(it / na), aa = gs + (int)(it - (long)cc * na);
+      const int cg = A.c0 + cc;
+      const int slot = cg / A.ns, s = cg - slot * A.ns;
+      const int kb = A.blk.kb[slot];
+      if (k >= A.Ka[(size_t)kb * A.nA + aa]) continue;
+      const size_t o = (size_t)A.off[(size_t)kb * A.nA + aa] + k;
+      const double* x = A.blk.x[slot] + 2 * (o + (size_t)s * A.ld);   // 8-byte aligned (ABI)
+      double* y = A.blk.y[slot] + 2 * (o + (size_t)s * A.ld);
+      const double d = A.ke[A.keoff[slot] + o];
+      const V h = Ys[qq * (K + 1) + k];
+      const double x0 = x[0], x1 = x[1];
+      y[0] = d * x0 + double(h.x);
+      y[1] = d * x1 + double(h.y);
+    }
+    return;
+  }
   // scatter: one warp per item, lanes over k (contiguous in the compact order)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int qq = warp; qq < RAD_Q; qq += RAD_THREADS / 32) {
@@ -787,7 +812,11 @@ static void set_nu_args(const hw_ctx* ctx, const Blocks& blk, const DevTables<T>
   ra.qtab = tb.qtab;
   ra.pair_n = ctx->db.pair_n;
   ra.ncyc = ctx->hb.prm.ncyc;
-  for (int i = 0; i < MAXSLOT; ++i) ra.nu[i] = i < blk.nslot ? ctx->hb.nu[blk.kb[i]] : 0.0;
+  ra.any_nu = 0;
+  for (int i = 0; i < MAXSLOT; ++i) {
+    ra.nu[i] = i < blk.nslot ? ctx->hb.nu[blk.kb[i]] : 0.0;
+    if (ra.nu[i] != 0.0) ra.any_nu = 1;
+  }
   ra.scale_mode = 0;
   ra.pair_mrow = ctx->db.pair_mrow;
   ra.mrow_m = ctx->db.mrow_m;
