@@ -56,6 +56,13 @@ struct Blocks {
   int nslot;
 };
 
+// One step of a three-term recurrence fused into an H X launch: the forward radial kernel
+// writes y = al_b (H x - c_b x) - be_b y (y's old content read only when be_b != 0) instead of
+// H x, per column block b (the scaled Chebyshev filter).
+struct ChebStep {
+  double al[MAXSLOT], c[MAXSLOT], be[MAXSLOT];
+};
+
 struct LobpcgWork;
 struct MlpState;
 
@@ -126,7 +133,7 @@ class ProfScope {
 
 namespace hw {
 template <typename T>
-cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld);
+cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, const ChebStep* step = nullptr);
 cudaError_t hx_configure(hw_ctx* ctx);
 bool density_fits(const hw_ctx* ctx, size_t tsz);
 bool gradient_fits(const hw_ctx* ctx, size_t csz);

@@ -211,6 +211,9 @@ struct RadArgs {
   int ncyc;
   int any_nu;                 // some block of this launch has nu != 0
   double nu[MAXSLOT];
+  // forward only: a fused recurrence step (y = al (H x - c x) - be y), or none
+  int step;
+  ChebStep cs;
   // inverse only: coefficients multiplied by i 2 pi m (scale_mode 1) or i 2 pi n Ncyc (2)
   // before the transform (the theta derivatives of Appendix C); 0: as they are
   int scale_mode;
@@ -339,6 +342,23 @@ __global__ void __launch_bounds__(RAD_THREADS, sizeof(T) == 4 ? 2 : 1) k_radial_
   }
 }
 
+// store H x (hx, hy) for one coefficient, or the fused recurrence step of A.step
+template <typename T>
+__device__ __forceinline__ void step_store(const RadArgs<T>& A, int slot, double* y, double x0, double x1,
+                                           double hx, double hy) {
+  if (A.step) {
+    const double al = A.cs.al[slot], c = A.cs.c[slot], be = A.cs.be[slot];
+    hx = al * (hx - c * x0);
+    hy = al * (hy - c * x1);
+    if (be != 0.0) {
+      hx -= be * y[0];
+      hy -= be * y[1];
+    }
+  }
+  y[0] = hx;
+  y[1] = hy;
+}
+
 // forward radial quadrature + diagonal term + scatter
 template <typename T>
 __global__ void __launch_bounds__(RAD_THREADS, sizeof(T) == 4 ? 2 : 1) k_radial_fwd(RadArgs<T> A) {
@@ -447,8 +467,18 @@ __global__ void __launch_bounds__(RAD_THREADS, sizeof(T) == 4 ? 2 : 1) k_radial_
       const double d = A.ke[A.keoff[slot] + o];
       const V h = Ys[qq * (K + 1) + k];
       const double x0 = x[0], x1 = x[1];
-      y[0] = d * x0 + double(h.x);
-      y[1] = d * x1 + double(h.y);
+      double y0 = d * x0 + double(h.x), y1 = d * x1 + double(h.y);
+      if (A.step) {
+        const double al = A.cs.al[slot], cc2 = A.cs.c[slot], be = A.cs.be[slot];
+        y0 = al * (y0 - cc2 * x0);
+        y1 = al * (y1 - cc2 * x1);
+        if (be != 0.0) {
+          y0 -= be * y[0];
+          y1 -= be * y[1];
+        }
+      }
+      y[0] = y0;
+      y[1] = y1;
     }
     return;
   }
@@ -471,8 +501,8 @@ __global__ void __launch_bounds__(RAD_THREADS, sizeof(T) == 4 ? 2 : 1) k_radial_
       for (int k = lane; k < ka; k += 32) {
         const V h = Ys[qq * (K + 1) + k];
         const double d = ke[k];
-        y[2 * k] = d * x[2 * k] + double(h.x);
-        y[2 * k + 1] = d * x[2 * k + 1] + double(h.y);
+        step_store(A, slot, y + 2 * k, x[2 * k], x[2 * k + 1], d * x[2 * k] + double(h.x),
+                   d * x[2 * k + 1] + double(h.y));
       }
       continue;
     }
@@ -499,8 +529,8 @@ __global__ void __launch_bounds__(RAD_THREADS, sizeof(T) == 4 ? 2 : 1) k_radial_
       if (k < ka) {
         const V h = Ys[qq * (K + 1) + k];
         const double d = ke[k];
-        y[2 * k] = d * x[2 * k] + double(h.x + cf * sx);
-        y[2 * k + 1] = d * x[2 * k + 1] + double(h.y + cf * sy);
+        step_store(A, slot, y + 2 * k, x[2 * k], x[2 * k + 1], d * x[2 * k] + double(h.x + cf * sx),
+                   d * x[2 * k + 1] + double(h.y + cf * sy));
       }
     }
   }
@@ -818,6 +848,7 @@ static void set_nu_args(const hw_ctx* ctx, const Blocks& blk, const DevTables<T>
     if (ra.nu[i] != 0.0) ra.any_nu = 1;
   }
   ra.scale_mode = 0;
+  ra.step = 0;
   ra.pair_mrow = ctx->db.pair_mrow;
   ra.mrow_m = ctx->db.mrow_m;
 }
@@ -825,7 +856,7 @@ static void set_nu_args(const hw_ctx* ctx, const Blocks& blk, const DevTables<T>
 // Launch the three kernels for the column blocks `blk` (ns columns each).  Columns are
 // processed in passes of at most ctx->ws.cols columns.
 template <typename T>
-cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld) {
+cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, const ChebStep* step) {
   auto& hb = ctx->hb;
   auto& db = ctx->db;
   const DevTables<T>& tb = *reinterpret_cast<const DevTables<T>*>(
@@ -891,6 +922,10 @@ cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld) {
     }
     ra.gh = reinterpret_cast<cplx_t<T>*>(ctx->ws.hbuf);
     ra.rtab = tb.rfwd;
+    if (step) {
+      ra.step = 1;
+      ra.cs = *step;
+    }
     const size_t sm_fwd = rad_fwd_smem(Nr, K, sizeof(T));
     {
       ProfScope ps(ctx, HW_PH_RADIAL_FWD);
@@ -1446,7 +1481,7 @@ cudaError_t hx_autotune(hw_ctx* ctx, int k, int ns, std::vector<float>& log) {
   return e;
 }
 
-template cudaError_t launch_hx<double>(hw_ctx*, const Blocks&, int, int64_t);
-template cudaError_t launch_hx<float>(hw_ctx*, const Blocks&, int, int64_t);
+template cudaError_t launch_hx<double>(hw_ctx*, const Blocks&, int, int64_t, const ChebStep*);
+template cudaError_t launch_hx<float>(hw_ctx*, const Blocks&, int, int64_t, const ChebStep*);
 
 }  // namespace hw

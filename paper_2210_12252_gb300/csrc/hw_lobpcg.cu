@@ -675,22 +675,33 @@ static cudaError_t rr_eig(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int nb,
   return e;
 }
 
-// apply H to `ncol` columns of S at column offset c0, result at the same offset of HS
+// apply H to `ncol` columns of S at column offset c0, result at the same offset of HS; or, with
+// `step` (per k-point scalars) and dst, the fused recurrence step
+//   S[:, dst ..] = al (H S[:, c0 ..] - c S[:, c0 ..]) - be S[:, dst ..]
 static hw_status apply_block(hw_ctx* ctx, LobpcgWork* w, const std::vector<int>& kidx, double2* S, double2* HS,
-                             int c0, int ncol, bool fp64, const std::vector<int>* only = nullptr) {
+                             int c0, int ncol, bool fp64, const std::vector<int>* only = nullptr,
+                             const ChebStep* step = nullptr, int dst = 0) {
   if (ncol <= 0) return HW_OK;
   const int64_t sK = w->Lpad * 3 * w->nb;
   Blocks blk;
   blk.nslot = 0;
+  ChebStep cs;
   for (int b = 0; b < w->nk; ++b) {
     if (only && !(*only)[b]) continue;
     blk.x[blk.nslot] = reinterpret_cast<const double*>(S + (size_t)b * sK + (size_t)c0 * w->Lpad);
-    blk.y[blk.nslot] = reinterpret_cast<double*>(HS + (size_t)b * sK + (size_t)c0 * w->Lpad);
+    blk.y[blk.nslot] = step ? reinterpret_cast<double*>(S + (size_t)b * sK + (size_t)dst * w->Lpad)
+                            : reinterpret_cast<double*>(HS + (size_t)b * sK + (size_t)c0 * w->Lpad);
     blk.kb[blk.nslot] = kidx[b];
+    if (step) {
+      cs.al[blk.nslot] = step->al[b];
+      cs.c[blk.nslot] = step->c[b];
+      cs.be[blk.nslot] = step->be[b];
+    }
     ++blk.nslot;
   }
   if (blk.nslot == 0) return HW_OK;
-  cudaError_t e = fp64 ? launch_hx<double>(ctx, blk, ncol, w->Lpad) : launch_hx<float>(ctx, blk, ncol, w->Lpad);
+  const ChebStep* sp = step ? &cs : nullptr;
+  cudaError_t e = fp64 ? launch_hx<double>(ctx, blk, ncol, w->Lpad, sp) : launch_hx<float>(ctx, blk, ncol, w->Lpad, sp);
   if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("apply_H: ") + cudaGetErrorString(e));
   return HW_OK;
 }
@@ -1635,19 +1646,18 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       k_cheb<<<dim3(na, nk), 256, 0, st>>>(S, HS, Lpad, sK, nb, 0, 1, nl, sc);
       ctx->launches++;
     }
-    for (int i = 2; i <= m; ++i) {
+    for (int i = 2; i <= m; ++i) {   // each step fused into the H Y launch
       const int src = (i - 1) % 2, dst = i % 2;
-      hs = apply_block(ctx, w, kidx, S, HS, src * nb + nl, na, !lowp);
-      if (hs != HW_OK) return hs;
+      ChebStep step;
       for (int b = 0; b < nk; ++b) {
         const double sn = 1.0 / (tau[b] - sig[b]);
-        sc.al[b] = 2.0 * sn / ee[b];
-        sc.be[b] = sig[b] * sn;
+        step.al[b] = 2.0 * sn / ee[b];
+        step.c[b] = sc.c[b];
+        step.be[b] = sig[b] * sn;
         sig[b] = sn;
       }
-      ProfScope ps_(ctx, HW_PH_OTHER);
-      k_cheb<<<dim3(na, nk), 256, 0, st>>>(S, HS, Lpad, sK, nb, src, dst, nl, sc);
-      ctx->launches++;
+      hs = apply_block(ctx, w, kidx, S, HS, src * nb + nl, na, !lowp, nullptr, &step, dst * nb + nl);
+      if (hs != HW_OK) return hs;
     }
     const int q = m % 2;
     {
