@@ -121,6 +121,43 @@ def slab_flops(geom, nmr, nA):
     return 2 * nmr * f2 + 2 * n2 * f1 + 2 * n1 * n2
 
 
+def fp64_peak_tflops(sm_mhz):
+    """FP64 pipe: 152 SMs x 2 DFMA x 2 flop per clock (1.26 TFLOP/s at 2070 MHz, the nominal)."""
+    return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def hx_roofline(geom, ctx, L, ns, prec, kernel_ms):
+    """Each H X kernel against its binding roofline (one launch of ns columns): the radial
+    transforms against the measured HBM copy bandwidth (algorithmic bytes: the coefficient
+    blocks in complex128 and the (r, pair) intermediate), the slab against the FP32 (mixed) or
+    FP64 pipe (algorithmic flops of slab_flops)."""
+    peaks, src = load_peaks()
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    elem = 4 if prec == "mixed" else 8
+    nmr, nA = _slab_sizes(ctx)
+    out = {"peak_source": src}
+    inv_b = radial_bytes(L, ns, geom.Nr, nA, elem)
+    fwd_b = inv_b + L * ns * 16   # the forward kernel also writes Y
+    # radial work: every kept coefficient meets N_r table entries (a complex x real MAC, 4 flop)
+    rad_fl = 4.0 * geom.Nr * L * ns
+    apk = fp32_alu_peak_tflops(mhz) if prec == "mixed" else fp64_peak_tflops(mhz)
+    for name, by in (("radial_inv", inv_b), ("radial_fwd", fwd_b)):
+        if name in kernel_ms:
+            sec = kernel_ms[name] / 1e3
+            gbs, tf = by / sec / 1e9, rad_fl / sec / 1e12
+            fh, fa = gbs / peaks["hbm_gbs"], tf / apk
+            out[name] = {"bound": "hbm" if fh >= fa else "alu", "achieved_gbs": round(gbs, 1),
+                         "hbm_frac": round(fh, 4), "achieved_tflops": round(tf, 3),
+                         "alu_frac": round(fa, 4), "frac": round(max(fh, fa), 4)}
+    if "slab" in kernel_ms:
+        fl = slab_flops(geom, nmr, nA) * ns * geom.Nr
+        pk = fp32_alu_peak_tflops(mhz) if prec == "mixed" else fp64_peak_tflops(mhz)
+        tf = fl / (kernel_ms["slab"] / 1e3) / 1e12
+        out["slab"] = {"bound": "alu", "achieved_tflops": round(tf, 3), "peak_tflops": round(pk, 2),
+                       "frac": round(tf / pk, 4), "pipe": "fp32" if prec == "mixed" else "fp64"}
+    return out
+
+
 def radial_bytes(L, ns, Nr, nA, elem):
     """Algorithmic bytes of one radial-transform launch: the X (or Y) block in complex128 plus
     the (r, pair) intermediate in the working precision (complex of `elem`-byte reals)."""
@@ -309,8 +346,9 @@ def ours_main(args):
             pr = ctx.profile_read()
             ctx.profile(False)
             t = np.mean([a.elapsed_time(b) for a, b in evs])
+            kms = {k: round(v[0] / max(v[1], 1), 4) for k, v in pr.items() if v[1]}
             hx[prec] = {"vec_per_s": round(ns / (t / 1e3), 1), "ms_per_call": round(float(t), 4),
-                        "kernel_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in pr.items() if v[1]}}
+                        "kernel_ms": kms, "roofline": hx_roofline(w.geom, ctx, L, ns, prec, kms)}
         result["hx"] = hx
         # ---- electron density from 64 states (the step after the solve)
         dens = {}
