@@ -169,7 +169,9 @@ hw_status hw_apply_precond(hw_ctx* ctx, int k, const double* R, double* Z, int n
                            const double* ritz, int kind);
 
 /* Lowest n_eig eigenpairs at the nk k-points kidx[] by block LOBPCG (Sec. Eigensolvers and
- * Preconditioning) on blocks of `block` >= n_eig columns (0: n_eig + max(4, n_eig/8)),
+ * Preconditioning), or by Chebyshev-filtered subspace iteration (HW_OPT_EIGENSOLVER), on blocks
+ * of `block` >= n_eig columns (0: n_eig + max(4, n_eig/8) for LOBPCG, n_eig + max(8, n_eig/8)
+ * for the Chebyshev solver),
  * at most 112 columns (HW_EINVAL above: the Cholesky-QR keeps its factor in shared memory).
  * A column is converged when ||H x - theta x||_2 <= tol with ||x|| = 1.  X0 (nullable):
  * nk device pointers to L_k x block complex128 start blocks (leading dimension L_k); NULL
