@@ -101,3 +101,30 @@ def test_chfsi_batched_uneven_cyclic_mixed(hwmod):
     for k in range(3):
         assert np.abs(r["evals"][k] - golden(f"tube_c3_k{k}_eigs.txt")[: w.n_eig]).max() < 1e-6, k
     assert r["resid"].max() <= 1e-6
+
+
+def test_chfsi_tube_fp64_maximum_block(hwmod):
+    """The largest block the solvers take (112 columns) with the Chebyshev solver in FP64."""
+    w = inputs.tube()
+    ctx, L = make_ctx(hwmod, w)
+    r = ctx.solve_eigs([0], 64, block=112, tol=1e-6, maxit=100)
+    assert r["converged"]
+    assert np.abs(r["evals"][0] - golden("tube_eigs.txt")[:64]).max() < 1e-8
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+def test_solve_rejects_bad_arguments(hwmod, solver):
+    w = inputs.tiny()
+    ctx = hwmod.Context(0)
+    ctx.setup_basis(w.geom, w.etas)
+    ctx.build_potential(w.atoms)
+    ctx.set_option(hwmod.HW_OPT_EIGENSOLVER, solver)
+    for kw in [dict(kidx=[1], n_eig=8), dict(kidx=[0], n_eig=0), dict(kidx=[0], n_eig=8, block=6),
+               dict(kidx=[0], n_eig=8, block=113), dict(kidx=[0], n_eig=8, block=99),
+               dict(kidx=[0], n_eig=8, tol=0.0)]:
+        args = dict(block=0, tol=1e-6)
+        args.update(kw)
+        kidx, n_eig = args.pop("kidx"), args.pop("n_eig")
+        with pytest.raises(hwmod.HwError) as e:
+            ctx.solve_eigs(kidx, n_eig, **args)
+        assert e.value.status == hwmod.HW_EINVAL, kw
