@@ -625,20 +625,21 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab(SlabArgs<T> A) {
 
 // 16-point DFT in registers, X[k] = sum_n x[n] W^(S n k), W = e^{2 pi i / 16}, as two radix-4
 // passes (n = 4 n1 + n2, k = k1 + 4 k2) with the twiddles W^(S n2 k1) between them
-template <int S>
-__device__ __forceinline__ void dft16(float (&xr)[16], float (&xi)[16]) {
-  constexpr float C8 = 0.92387953251128674f, S8 = 0.38268343236508977f, R2 = 0.70710678118654752f;
+template <int S, typename R>
+__device__ __forceinline__ void dft16(R (&xr)[16], R (&xi)[16]) {
+  constexpr R C8 = R(0.923879532511286756128183189396788933), S8 = R(0.382683432365089771728459984030398866);
+  constexpr R R2 = R(0.707106781186547524400844362104849039);
   // W^e for e = 0..9 (cos, sin); forward (S = -1) takes the conjugates
-  constexpr float wc[10] = {1.f, C8, R2, S8, 0.f, -S8, -R2, -C8, -1.f, -C8};
-  constexpr float ws[10] = {0.f, S8, R2, C8, 1.f, C8, R2, S8, 0.f, -S8};
+  constexpr R wc[10] = {R(1), C8, R2, S8, R(0), -S8, -R2, -C8, R(-1), -C8};
+  constexpr R ws[10] = {R(0), S8, R2, C8, R(1), C8, R2, S8, R(0), -S8};
 #pragma unroll
   for (int n2 = 0; n2 < 4; ++n2) {   // 4-point DFTs over n1
-    const float a0r = xr[n2], a0i = xi[n2], a1r = xr[4 + n2], a1i = xi[4 + n2];
-    const float a2r = xr[8 + n2], a2i = xi[8 + n2], a3r = xr[12 + n2], a3i = xi[12 + n2];
-    const float t0r = a0r + a2r, t0i = a0i + a2i, t1r = a0r - a2r, t1i = a0i - a2i;
-    const float t2r = a1r + a3r, t2i = a1i + a3i;
-    const float dr = a1r - a3r, di = a1i - a3i;
-    const float t3r = -S * di, t3i = S * dr;   // (a1 - a3) (S i)
+    const R a0r = xr[n2], a0i = xi[n2], a1r = xr[4 + n2], a1i = xi[4 + n2];
+    const R a2r = xr[8 + n2], a2i = xi[8 + n2], a3r = xr[12 + n2], a3i = xi[12 + n2];
+    const R t0r = a0r + a2r, t0i = a0i + a2i, t1r = a0r - a2r, t1i = a0i - a2i;
+    const R t2r = a1r + a3r, t2i = a1i + a3i;
+    const R dr = a1r - a3r, di = a1i - a3i;
+    const R t3r = -S * di, t3i = S * dr;   // (a1 - a3) (S i)
     xr[n2] = t0r + t2r;
     xi[n2] = t0i + t2i;
     xr[4 + n2] = t1r + t3r;
@@ -653,20 +654,20 @@ __device__ __forceinline__ void dft16(float (&xr)[16], float (&xi)[16]) {
 #pragma unroll
     for (int n2 = 1; n2 < 4; ++n2) {   // twiddle W^(S n2 k1)
       const int e = n2 * k1;
-      const float c = wc[e], sn = S * ws[e];
-      const float r = xr[4 * k1 + n2], i = xi[4 * k1 + n2];
+      const R c = wc[e], sn = S * ws[e];
+      const R r = xr[4 * k1 + n2], i = xi[4 * k1 + n2];
       xr[4 * k1 + n2] = r * c - i * sn;
       xi[4 * k1 + n2] = r * sn + i * c;
     }
-  float orr[16], oi[16];
+  R orr[16], oi[16];
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1) {   // 4-point DFTs over n2
-    const float a0r = xr[4 * k1], a0i = xi[4 * k1], a1r = xr[4 * k1 + 1], a1i = xi[4 * k1 + 1];
-    const float a2r = xr[4 * k1 + 2], a2i = xi[4 * k1 + 2], a3r = xr[4 * k1 + 3], a3i = xi[4 * k1 + 3];
-    const float t0r = a0r + a2r, t0i = a0i + a2i, t1r = a0r - a2r, t1i = a0i - a2i;
-    const float t2r = a1r + a3r, t2i = a1i + a3i;
-    const float dr = a1r - a3r, di = a1i - a3i;
-    const float t3r = -S * di, t3i = S * dr;
+    const R a0r = xr[4 * k1], a0i = xi[4 * k1], a1r = xr[4 * k1 + 1], a1i = xi[4 * k1 + 1];
+    const R a2r = xr[4 * k1 + 2], a2i = xi[4 * k1 + 2], a3r = xr[4 * k1 + 3], a3i = xi[4 * k1 + 3];
+    const R t0r = a0r + a2r, t0i = a0i + a2i, t1r = a0r - a2r, t1i = a0i - a2i;
+    const R t2r = a1r + a3r, t2i = a1i + a3i;
+    const R dr = a1r - a3r, di = a1i - a3i;
+    const R t3r = -S * di, t3i = S * dr;
     orr[k1] = t0r + t2r;
     oi[k1] = t0i + t2i;
     orr[k1 + 4] = t1r + t3r;
@@ -691,38 +692,40 @@ __device__ __forceinline__ void dft16(float (&xr)[16], float (&xi)[16]) {
 // potential multiply the forward value of row m is sum_q omega^(-m q) D_q[m mod 16], D_q the
 // lane's 16-point forward DFT, summed over the row's 4 lanes by shuffles.  No barrier or table
 // of the 64-point transform is involved; the theta2 passes are k_slab's FFTs.
-template <int N1, int N2>
-__global__ void __launch_bounds__(SLAB_THREADS) k_slab_r16(SlabArgs<float> A) {
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(SLAB_THREADS) k_slab_r16(SlabArgs<T> A) {
   static_assert(N1 == 64 && (4 * N2) % 32 == 0 && 4 * N2 <= SLAB_THREADS, "4 lanes of 16 points per theta2 row");
-  using V = float2;
+  using V = cplx_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = blockIdx.x, p = blockIdx.y;
   constexpr int n1 = N1, n2 = N2, n2p = N2 + 1, CS = 17;   // CS: padded 16-bin row per lane
   const int nmr = A.nmr;
-  const int wsz = pd_size(nmr * n2);
+  constexpr bool PADW = sizeof(T) == sizeof(float);
+  const int wsz = PADW ? pd_size(nmr * n2) : nmr * n2;
+  auto ix = [](int i) { return PADW ? pd(i) : i; };
   V* Tb = reinterpret_cast<V*>(smem_raw);   // [nmr][n2p]
   V* W0 = Tb + nmr * n2p;
   V* W1 = W0 + wsz;
   V* E4 = W1 + wsz;                         // [nmr][4]: omega^(m q)
   V* Cs = E4 + 4 * nmr;                     // [4 N2][CS]: one lane's 16 bins
-  const V zero = make_float2(0.f, 0.f);
+  const V zero = mk<T>(T(0), T(0));
   const V* Gc = A.G + ((size_t)c * A.Nr + p) * A.nA;
   V* Hc = A.H + ((size_t)c * A.Nr + p) * A.nA;
   for (int t = threadIdx.x; t < 4 * nmr; t += blockDim.x) {
     const int r = t >> 2, q = t & 3;
     const V w = A.tw1[pmod(A.mrow_m[r] * q, n1)];   // e^{-2 pi i m q / 64}
-    E4[t] = make_float2(w.x, -w.y);
+    E4[t] = mk<T>(w.x, -w.y);
   }
   // theta2 inverse pass over the kept m rows
-  for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) W0[pd(i)] = zero;
+  for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) W0[ix(i)] = zero;
   __syncthreads();
   for (int a = threadIdx.x; a < A.nA; a += blockDim.x)
-    W0[pd(A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2))] = Gc[a];
+    W0[ix(A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2))] = Gc[a];
   __syncthreads();
-  V* r2 = fft_any<float, N2, true>(W0, W1, A.p2, nmr, A.tw2, +1);
+  V* r2 = fft_any<T, N2, PADW>(W0, W1, A.p2, nmr, A.tw2, +1);
   for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) {
     const int rr = i / n2, jj = i - rr * n2;
-    Tb[rr * n2p + jj] = r2[pd(i)];
+    Tb[rr * n2p + jj] = r2[ix(i)];
   }
   __syncthreads();
   if (threadIdx.x < 4 * n2) {
@@ -738,55 +741,56 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab_r16(SlabArgs<float> A) {
       v.y += t.x * e.y + t.y * e.x;
       cs[b] = v;
     }
-    float xr[16], xi[16];
+    T xr[16], xi[16];
 #pragma unroll
     for (int b = 0; b < 16; ++b) {
       xr[b] = cs[b].x;
       xi[b] = cs[b].y;
     }
-    dft16<+1>(xr, xi);   // xr[t] + i xi[t] = u(theta1 = 4 t + q)
-    const float* Vrow = A.V + ((size_t)p * n2 + j) * n1 + q;
+    dft16<+1, T>(xr, xi);   // xr[t] + i xi[t] = u(theta1 = 4 t + q)
+    const T* Vrow = A.V + ((size_t)p * n2 + j) * n1 + q;
 #pragma unroll
     for (int t = 0; t < 16; ++t) {
-      const float v = Vrow[4 * t];
+      const T v = Vrow[4 * t];
       xr[t] *= v;
       xi[t] *= v;
     }
-    dft16<-1>(xr, xi);
+    dft16<-1, T>(xr, xi);
 #pragma unroll
-    for (int b = 0; b < 16; ++b) cs[b] = make_float2(xr[b], xi[b]);
+    for (int b = 0; b < 16; ++b) cs[b] = mk<T>(xr[b], xi[b]);
     __syncwarp();   // every lane of this row has read its column of Tb
     for (int r = 0; r < nmr; ++r) {
       const V d = cs[A.mrow_m[r] & 15], e = E4[4 * r + q];   // times conj(omega^(m q))
-      float sr = d.x * e.x + d.y * e.y, si = d.y * e.x - d.x * e.y;
+      T sr = d.x * e.x + d.y * e.y, si = d.y * e.x - d.x * e.y;
       sr += __shfl_xor_sync(0xffffffffu, sr, 1);
       si += __shfl_xor_sync(0xffffffffu, si, 1);
       sr += __shfl_xor_sync(0xffffffffu, sr, 2);
       si += __shfl_xor_sync(0xffffffffu, si, 2);
-      if (q == (r & 3)) Tb[r * n2p + j] = make_float2(sr, si);
+      if (q == (r & 3)) Tb[r * n2p + j] = mk<T>(sr, si);
     }
   }
   __syncthreads();
   // theta2 forward pass, extract the kept pairs
   for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) {
     const int rr = i / n2, jj = i - rr * n2;
-    W0[pd(i)] = Tb[rr * n2p + jj];
+    W0[ix(i)] = Tb[rr * n2p + jj];
   }
   __syncthreads();
-  r2 = fft_any<float, N2, true>(W0, W1, A.p2, nmr, A.tw2, -1);
+  r2 = fft_any<T, N2, PADW>(W0, W1, A.p2, nmr, A.tw2, -1);
   for (int a = threadIdx.x; a < A.nA; a += blockDim.x)
-    Hc[a] = r2[pd(A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2))];
+    Hc[a] = r2[ix(A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2))];
 }
 
-static size_t slab_r16_smem_bytes(int nmr, int n2) {
-  return sizeof(float2) * ((size_t)nmr * (n2 + 1) + 2 * (size_t)pd_size(nmr * n2) + 4 * (size_t)nmr +
-                           (size_t)4 * n2 * 17);
+static size_t slab_r16_smem_bytes(int nmr, int n2, size_t elem) {
+  const size_t w = elem == sizeof(float2) ? (size_t)pd_size(nmr * n2) : (size_t)nmr * n2;
+  return elem * ((size_t)nmr * (n2 + 1) + 2 * w + 4 * (size_t)nmr + (size_t)4 * n2 * 17);
 }
 
 // FP32 on the 64 x 48 grid: the 4 x 16 theta1 variant (unless HW_OPT_SLAB_KERNEL selects the
 // Stockham FFTs)
 static bool use_slab_r16(const hw_ctx* ctx, size_t elem) {
-  return elem == sizeof(float2) && ctx->slab_r16 && ctx->hb.prm.Nth1 == 64 && ctx->hb.prm.Nth2 == 48;
+  (void)elem;
+  return ctx->slab_r16 && ctx->hb.prm.Nth1 == 64 && ctx->hb.prm.Nth2 == 48;
 }
 
 // --------------------------------------------------------------------------- host launcher
@@ -801,7 +805,7 @@ static void* slab_kernel(int n1, int n2) {
 
 template <typename T>
 static cudaError_t launch_slab(const hw_ctx* ctx, dim3 grid, size_t smem, const SlabArgs<T>& sa) {
-  void* f = use_slab_r16(ctx, sizeof(cplx_t<T>)) ? (void*)k_slab_r16<64, 48> : slab_kernel<T>(sa.Nth1, sa.Nth2);
+  void* f = use_slab_r16(ctx, sizeof(cplx_t<T>)) ? (void*)k_slab_r16<T, 64, 48> : slab_kernel<T>(sa.Nth1, sa.Nth2);
   void* args[] = {(void*)&sa};
   return cudaLaunchKernel(f, grid, dim3(SLAB_THREADS), args, smem, ctx->stream);
 }
@@ -818,7 +822,7 @@ size_t slab_smem_bytes(const hw_ctx* ctx, size_t elem, int Jc) {
   const auto& hb = ctx->hb;
   const int nmr = (int)hb.mrow_m.size();
   const int n1 = hb.prm.Nth1, n2 = hb.prm.Nth2;
-  if (use_slab_r16(ctx, elem)) return slab_r16_smem_bytes(nmr, n2);   // no theta2 chunks
+  if (use_slab_r16(ctx, elem)) return slab_r16_smem_bytes(nmr, n2, elem);   // no theta2 chunks
   // padded layout: the FP32 kernels specialised for the grid (k_slab's PAD)
   const bool pad = elem == sizeof(float2) && slab_kernel<float>(n1, n2) != (void*)k_slab<float, 0, 0>;
   const int w = std::max(nmr * n2, Jc * n1);
@@ -1394,7 +1398,7 @@ cudaError_t hx_configure(hw_ctx* ctx) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radial_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   for (void* f : {(void*)k_slab<double, 0, 0>, (void*)k_slab<float, 0, 0>, (void*)k_slab<double, 64, 48>,
                   (void*)k_slab<float, 64, 48>, (void*)k_slab<double, 192, 96>, (void*)k_slab<float, 192, 96>,
-                  (void*)k_slab_r16<64, 48>})
+                  (void*)k_slab_r16<float, 64, 48>, (void*)k_slab_r16<double, 64, 48>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   (void)ctx;
   return e;
