@@ -173,6 +173,15 @@ hw_status hw_apply_precond(hw_ctx* ctx, int k, const double* R, double* Z, int n
  * of `block` >= n_eig columns (0: n_eig + max(4, n_eig/8) for LOBPCG, n_eig + max(8, n_eig/8)
  * for the Chebyshev solver),
  * at most 112 columns (HW_EINVAL above: the Cholesky-QR keeps its factor in shared memory).
+ * More than HW_OPT_WINDOW eigenpairs (default 80) are solved in w = ceil(n_eig / window)
+ * consecutive windows of ceil(n_eig / w) eigenpairs (the last one the rest).  Each window is a
+ * block solve as above (`block` then applies to one window; default for the Chebyshev solver
+ * min(112, L_min / 3), the largest block the basis allows; for LOBPCG the solver's own
+ * default) restricted to the orthogonal complement of the eigenvectors the earlier windows
+ * converged: the start block and, every iteration, the new search directions (LOBPCG) or the
+ * filtered block (Chebyshev) are projected against them (in FP64; in the FP32 and hybrid
+ * phases of the mixed form with FP32 products).  The windows run in lockstep over the k-points; X0
+ * must be NULL then (HW_EINVAL); iters is the sum over the windows.
  * A column is converged when ||H x - theta x||_2 <= tol with ||x|| = 1.  X0 (nullable):
  * nk device pointers to L_k x block complex128 start blocks (leading dimension L_k); NULL
  * draws a seeded Gaussian start on the device.  Outputs: evals (host, [nk*n_eig]), iters
@@ -328,11 +337,14 @@ typedef enum {
                                transforms split 64 = 4 x 16 over the 4 lanes of a theta2 row
                                (register DFTs, shuffles), 0 the Stockham FFTs (every other grid
                                and FP64 use the FFTs). */
-  HW_OPT_TAIL_NO_P = 10     /* Chebyshev solver, mixed form: 1 (default) starts the LOBPCG end
+  HW_OPT_TAIL_NO_P = 10,    /* Chebyshev solver, mixed form: 1 (default) starts the LOBPCG end
                                phase without conjugate directions (Rayleigh-Ritz on [X W], each
                                iteration cheaper) and switches them on for good once an
                                iteration fails to halve the largest wanted residual; 0: with
                                them from the start. */
+  HW_OPT_WINDOW = 11        /* hw_solve_eigs: largest number of eigenpairs one block solves,
+                               1..100; 0 (default) means 80.  More eigenpairs than this are
+                               solved in consecutive windows of equal size (see hw_solve_eigs). */
 } hw_option;
 /* Set an option (HW_EINVAL for an unknown option, a read-only one or a bad value). */
 hw_status hw_set_option(hw_ctx* ctx, int option, int value);

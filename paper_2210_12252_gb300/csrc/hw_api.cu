@@ -579,6 +579,11 @@ hw_status hw_set_option(hw_ctx* ctx, int option, int value) {
     ctx->slab_r16 = value;
     return HW_OK;
   }
+  if (option == HW_OPT_WINDOW) {
+    if (value < 0 || value > 100) return hw_fail(ctx, HW_EINVAL, "window 0 (100) or 1..100 eigenpairs");
+    ctx->window = value;
+    return HW_OK;
+  }
   return hw_fail(ctx, HW_EINVAL, "unknown or read-only option");
 }
 
@@ -595,6 +600,7 @@ hw_status hw_get_option(hw_ctx* ctx, int option, long long* value) {
   if (option == HW_OPT_CHEB_LOCK) { *value = ctx->cheb_lock; return HW_OK; }
   if (option == HW_OPT_TAIL_NO_P) { *value = ctx->tail_no_p; return HW_OK; }
   if (option == HW_OPT_SLAB_KERNEL) { *value = ctx->slab_r16; return HW_OK; }
+  if (option == HW_OPT_WINDOW) { *value = ctx->window; return HW_OK; }
   return hw_fail(ctx, HW_EINVAL, "unknown option");
 }
 

@@ -109,6 +109,7 @@ struct hw_ctx {
   int cheb_adapt = 1;          // HW_OPT_CHEB_ADAPT
   int cheb_lock = 1;           // HW_OPT_CHEB_LOCK
   int tail_no_p = 1;           // HW_OPT_TAIL_NO_P
+  int window = 0;              // HW_OPT_WINDOW (0: 100)
   int slab_r16 = 1;            // HW_OPT_SLAB_KERNEL
   int64_t rr_fallbacks = 0;    // Householder results rejected by the check (Jacobi used)
   hw::Prof prof;

@@ -905,9 +905,42 @@ static hw_status solve_setup(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig,
   return HW_OK;
 }
 
+// Deflation of a windowed solve: the eigenvectors the earlier windows converged (per k-point
+// at Q[b], leading dimension ld, the first nq columns), against which a window's start block and
+// new search directions are projected.
+struct Deflate {
+  int nq = 0;
+  const double2* Q[MAXSLOT] = {};
+  int64_t ld = 0;
+  double2* C = nullptr;   // scratch: nq x (at most 112) coefficients
+};
+
+// columns c0 .. c0 + ncol - 1 of every k-point's block in S (rows Lb[b], leading dimension
+// Lpad, k-point stride sK) minus their components along Q[b]: X -= Q (Q^H X), twice, in FP64,
+// or (fp32) with complex FP32 products, which round the columns to FP32 as well: for search
+// directions only, whose FP32-level traces along Q enter the Ritz vectors scaled by their
+// coefficients (of the order of the residuals)
+static void deflate_cols(Gemm& gemm, const Deflate* df, const std::vector<int64_t>& Lb, double2* S, int64_t Lpad,
+                         int64_t sK, int c0, int ncol, bool fp32 = false) {
+  if (!df || df->nq == 0 || ncol <= 0) return;
+  const bool keep = gemm.lowp;
+  gemm.lowp = fp32;
+  for (int pass = 0; pass < 2; ++pass)
+    for (size_t b = 0; b < Lb.size(); ++b) {
+      double2* X = S + (size_t)b * sK + (size_t)c0 * Lpad;
+      gemm(CUBLAS_OP_C, CUBLAS_OP_N, df->nq, ncol, (int)Lb[b], 1.0, df->Q[b], df->ld, 0, X, Lpad, 0, 0.0, df->C,
+           df->nq, 0, 1);
+      gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lb[b], ncol, df->nq, -1.0, df->Q[b], df->ld, 0, df->C, df->nq, 0, 1.0, X,
+           Lpad, 0, 1);
+    }
+  gemm.lowp = keep;
+}
+
 // Start block in the first nb columns of SB[0]: the caller's X0 (L_b x nb, ld L_b, zero padded),
-// a seeded complex Gaussian block, or (keep) the block already there; then Cholesky-QR twice.
-static hw_status start_block(hw_ctx* ctx, SolveSetup& su, Gemm& gemm, const double* const* X0, bool keep = false) {
+// a seeded complex Gaussian block, or (keep) the block already there; projected against the
+// deflation set (if any); then Cholesky-QR twice.
+static hw_status start_block(hw_ctx* ctx, SolveSetup& su, Gemm& gemm, const double* const* X0, bool keep = false,
+                             const Deflate* df = nullptr) {
   LobpcgWork* w = ctx->lw;
   const int nk = w->nk, nb = su.nb;
   cudaStream_t st = ctx->stream;
@@ -927,6 +960,7 @@ static hw_status start_block(hw_ctx* ctx, SolveSetup& su, Gemm& gemm, const doub
     k_random_start<<<dim3(nb, nk), 256, 0, st>>>(w->SB[0], su.Lpad, su.sK, su.dL, nb, 0x5eed1234abcdULL);
     ctx->launches++;
   }
+  deflate_cols(gemm, df, su.Lb, w->SB[0], su.Lpad, su.sK, 0, nb);
   std::vector<int> nvh(3 * nk, nb);
   cudaMemcpy(su.dnv, nvh.data(), 3 * nk * sizeof(int), cudaMemcpyHostToDevice);
   std::vector<int> failed;
@@ -941,7 +975,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
                             double tol, int maxit, hw_prec prec, int precond_kind,
                             const double* const* X0, double* evals, double* const* evecs,
                             int64_t ld_evecs, int* iters, double* resid, Trace* trace,
-                            bool keep_start = false, bool no_p = false) {
+                            bool keep_start = false, bool no_p = false, const Deflate* df = nullptr) {
   if (!ctx) return HW_EINVAL;
   if (precond_kind != HW_PRECOND_TPA && precond_kind != HW_PRECOND_NONE &&
       !(precond_kind == HW_PRECOND_LEARNED && ctx->mlp))
@@ -960,7 +994,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
   const double lowp_thr = (prec == HW_MIXED && ctx->lowp_exp > 0) ? std::pow(10.0, -ctx->lowp_exp) : 0.0;
   std::vector<int> failed;
   int cur = 0;
-  hs = start_block(ctx, su, gemm, X0, keep_start);
+  hs = start_block(ctx, su, gemm, X0, keep_start, df);
   if (hs != HW_OK) return hs;
   const bool mixed = prec == HW_MIXED;
   bool fp64_products = !mixed;
@@ -1073,6 +1107,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       hyb_best_it = it;
       std::vector<int> nbv(nk, nb);
       cudaMemcpyAsync(dnv, nbv.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
+      deflate_cols(gemm, df, Lb, S, Lpad, sK, 0, nb);   // FP32 rounding leaves traces along Q
       hs = cholqr(ctx, w, gemm, S, 0, nb, dnv, 2, failed);
       if (hs != HW_OK) return hs;
       hs = apply_block(ctx, w, kidx, S, HS, 0, nb, true);
@@ -1227,6 +1262,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     // their mutual orthogonalisation, their Gram block and the P update are formed in FP32.
     const bool hyb = mixed && !gemm.lowp && hyb_on;
     const bool lowp_now = gemm.lowp;
+    deflate_cols(gemm, df, Lb, S, Lpad, sK, woff, na, lowp_now || hyb);   // W against the earlier windows
     gemm.lowp = lowp_now || hyb;
     // ---- project out [X P], twice
     for (int pass = 0; pass < 2; ++pass) {
@@ -1441,7 +1477,8 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
 // finishes from the filtered Ritz block.  FP64 form: filter cycles to the end.
 static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, int block, double tol, int maxit,
                             hw_prec prec, int precond_kind, const double* const* X0, double* evals,
-                            double* const* evecs, int64_t ld_evecs, int* iters, double* resid) {
+                            double* const* evecs, int64_t ld_evecs, int* iters, double* resid,
+                            const Deflate* df = nullptr) {
   if (!ctx) return HW_EINVAL;
   Gemm gemm{ctx};
   SolveSetup su;
@@ -1494,7 +1531,7 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       bup[b] = bound + 1e-3 * std::fabs(bound) + 1e-3;
     }
   }
-  hs = start_block(ctx, su, gemm, X0);
+  hs = start_block(ctx, su, gemm, X0, false, df);
   if (hs != HW_OK) return hs;
   bool lowp = gemm.lowp;   // FP32 phase of the mixed form
   hs = apply_block(ctx, w, kidx, w->SB[0], w->HSB[0], 0, nb, !lowp);
@@ -1559,7 +1596,7 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
                             cudaMemcpyDeviceToDevice, st);
         std::vector<int> itl(nk, 0);
         hs = solve_impl(ctx, nk, kidx_in, n_eig, nb, tol, std::max(1, maxit - it), prec, precond_kind, nullptr,
-                        evals, evecs, ld_evecs, itl.data(), resid, nullptr, true, ctx->tail_no_p != 0);
+                        evals, evecs, ld_evecs, itl.data(), resid, nullptr, true, ctx->tail_no_p != 0, df);
         if (iters)
           for (int b = 0; b < nk; ++b) iters[b] = it + itl[b];
         return hs;
@@ -1670,6 +1707,10 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     }
     double2* Yq = S + (size_t)q * nb * Lpad;    // the filtered block: [X_locked | Y_active]
     double2* HYq = HS + (size_t)q * nb * Lpad;
+    // windowed solve: the filter amplifies the earlier windows' eigenvectors most (their
+    // eigenvalues lie below the block's), so the traces of them that rounding leaves are
+    // projected out before the orthonormalisation
+    deflate_cols(gemm, df, su.Lb, S, Lpad, sK, q * nb + nl, na, lowp);
     if (nl > 0) {
       if (q != 0) {   // the locked columns and their H products live in block 0
         cudaMemcpy2DAsync(Yq, (size_t)sK * 16, S, (size_t)sK * 16, (size_t)nl * Lpad * 16, nk,
@@ -1774,15 +1815,102 @@ extern "C" hw_status hw_heev(hw_ctx* ctx, int n, int nprob, int nw, const double
   return HW_OK;
 }
 
+static hw_status solve_window(hw_ctx* ctx, int nk, const int* kidx, int n_eig, int block, double tol, int maxit,
+                              hw_prec prec, int precond_kind, const double* const* X0, double* evals,
+                              double* const* evecs, int64_t ld_evecs, int* iters, double* resid, const Deflate* df) {
+  if (ctx->eigensolver == 1)
+    return chfsi_impl(ctx, nk, kidx, n_eig, block, tol, maxit, prec, precond_kind, X0, evals, evecs, ld_evecs, iters,
+                      resid, df);
+  return solve_impl(ctx, nk, kidx, n_eig, block, tol, maxit, prec, precond_kind, X0, evals, evecs, ld_evecs,
+                    iters, resid, nullptr, false, false, df);
+}
+
 extern "C" hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx, int n_eig, int block, double tol,
                                    int maxit, hw_prec prec, int precond_kind, const double* const* X0,
                                    double* evals, double* const* evecs, int64_t ld_evecs, int* iters,
                                    double* resid) {
-  if (ctx && ctx->eigensolver == 1)
-    return chfsi_impl(ctx, nk, kidx, n_eig, block, tol, maxit, prec, precond_kind, X0, evals, evecs, ld_evecs, iters,
-                      resid);
-  return solve_impl(ctx, nk, kidx, n_eig, block, tol, maxit, prec, precond_kind, X0, evals, evecs, ld_evecs,
-                    iters, resid, nullptr);
+  if (!ctx) return HW_EINVAL;
+  const int wmax = ctx->window > 0 ? ctx->window : 80;
+  if (n_eig <= wmax)
+    return solve_window(ctx, nk, kidx, n_eig, block, tol, maxit, prec, precond_kind, X0, evals, evecs, ld_evecs,
+                        iters, resid, nullptr);
+  // windows of equal size, each solved in the complement of the ones before
+  if (ctx->device < 0) return hw_fail(ctx, HW_ESTATE, "host-only context has no device");
+  if (!ctx->have_basis) return hw_fail(ctx, HW_ESTATE, "hw_setup_basis has not been called");
+  if (nk < 1 || nk > MAXSLOT || !kidx || !evals) return hw_fail(ctx, HW_EINVAL, "bad k-point list");
+  if (X0) return hw_fail(ctx, HW_EINVAL, "a windowed solve takes no start block (X0 must be NULL)");
+  int64_t Lmax = 0, Lmin = INT64_MAX;
+  for (int b = 0; b < nk; ++b) {
+    if (kidx[b] < 0 || kidx[b] >= ctx->hb.nk) return hw_fail(ctx, HW_EINVAL, "k-point index out of range");
+    Lmax = std::max(Lmax, ctx->hb.L[kidx[b]]);
+    Lmin = std::min(Lmin, ctx->hb.L[kidx[b]]);
+  }
+  if (evecs) {
+    if (ld_evecs < Lmax) return hw_fail(ctx, HW_EINVAL, "ld_evecs < L");
+    for (int b = 0; b < nk; ++b)
+      if (!evecs[b]) return hw_fail(ctx, HW_EINVAL, "null eigenvector block");
+  }
+  const int nwin = (n_eig + wmax - 1) / wmax;
+  const int wsz = (n_eig + nwin - 1) / nwin;
+  cudaSetDevice(ctx->device);
+  // the converged vectors: the caller's evecs, or a scratch block when the caller wants none
+  const int64_t ldq = evecs ? ld_evecs : Lmax;
+  double2* own = nullptr;
+  if (!evecs && cudaMalloc((void**)&own, (size_t)nk * ldq * n_eig * sizeof(double2)) != cudaSuccess)
+    return hw_fail(ctx, HW_ENOMEM, "windowed solve: eigenvector scratch");
+  Deflate df;
+  df.ld = ldq;
+  if (cudaMalloc((void**)&df.C, (size_t)n_eig * 112 * sizeof(double2)) != cudaSuccess) {
+    cudaFree(own);
+    return hw_fail(ctx, HW_ENOMEM, "windowed solve: projection scratch");
+  }
+  std::vector<double2*> Qp(nk);
+  for (int b = 0; b < nk; ++b) {
+    Qp[b] = evecs ? reinterpret_cast<double2*>(evecs[b]) : own + (size_t)b * ldq * n_eig;
+    df.Q[b] = Qp[b];
+  }
+  std::vector<double> ev((size_t)nk * wsz), rs((size_t)nk * wsz);
+  std::vector<int> itw(nk, 0);
+  for (size_t i = 0; i < (size_t)nk * n_eig; ++i) {
+    evals[i] = std::nan("");
+    if (resid) resid[i] = std::nan("");
+  }
+  if (iters)
+    for (int b = 0; b < nk; ++b) iters[b] = 0;
+  hw_status result = HW_OK;
+  for (int w0 = 0; w0 < n_eig; w0 += wsz) {
+    const int nw = std::min(wsz, n_eig - w0);
+    df.nq = w0;
+    std::vector<double*> out(nk);
+    for (int b = 0; b < nk; ++b) out[b] = reinterpret_cast<double*>(Qp[b] + (size_t)w0 * ldq);
+    // default block of the Chebyshev solver: the largest the basis allows (the top columns of a
+    // window converge at the rate of the gap to the first column outside the block); LOBPCG
+    // keeps its own default
+    int bw = block;
+    if (bw <= 0 && ctx->eigensolver == 1) {
+      bw = (int)std::min<int64_t>(112, Lmin / 3);
+      if (bw < nw) bw = 0;   // the solver's own default (and its error if that does not fit)
+    }
+    const hw_status hs = solve_window(ctx, nk, kidx, nw, bw, tol, maxit, prec, precond_kind, nullptr, ev.data(),
+                                      out.data(), ldq, itw.data(), rs.data(), &df);
+    if (hs == HW_OK || hs == HW_ENOTCONV) {
+      for (int b = 0; b < nk; ++b) {
+        for (int j = 0; j < nw; ++j) {
+          evals[(size_t)b * n_eig + w0 + j] = ev[(size_t)b * nw + j];
+          if (resid) resid[(size_t)b * n_eig + w0 + j] = rs[(size_t)b * nw + j];
+        }
+        if (iters) iters[b] += itw[b];
+      }
+    }
+    if (hs != HW_OK) {   // a window that did not converge ends the solve (its message is kept)
+      result = hs;
+      break;
+    }
+  }
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(df.C);
+  cudaFree(own);
+  return result;
 }
 
 extern "C" hw_status hw_solve_eigs_traced(hw_ctx* ctx, int k, int n_eig, int block, double tol, int maxit,

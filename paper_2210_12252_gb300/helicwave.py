@@ -266,6 +266,7 @@ HW_OPT_CHEB_ADAPT = 7
 HW_OPT_CHEB_LOCK = 8
 HW_OPT_SLAB_KERNEL = 9
 HW_OPT_TAIL_NO_P = 10
+HW_OPT_WINDOW = 11
 
 
 def hw_set_option(h, option, value):
