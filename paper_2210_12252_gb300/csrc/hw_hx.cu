@@ -684,27 +684,27 @@ __device__ __forceinline__ void dft16(R (&xr)[16], R (&xi)[16]) {
   }
 }
 
-// FP32 slab for the 64 x 48 angular grid with the theta1 transforms split 64 = 4 x 16 over the
+// Slab for the 64 x 48 angular grid with the theta1 transforms split 64 = 4 x 16 over the
 // 4 lanes of a theta2 row: lane q owns the points i = 4 t + q (t = 0..15).  With omega =
 // e^{2 pi i / 64} and W = omega^4, a kept row m contributes T_m omega^(m q) W^(m t) to point
 // 4 t + q, so the inverse transform is, per lane, the 16-point inverse DFT of the bins
 // b = m mod 16 filled with T_m omega^(m q) (rows sharing a bin add, which is exact); after the
 // potential multiply the forward value of row m is sum_q omega^(-m q) D_q[m mod 16], D_q the
 // lane's 16-point forward DFT, summed over the row's 4 lanes by shuffles.  No barrier or table
-// of the 64-point transform is involved; the theta2 passes are k_slab's FFTs.
+// of the 64-point transform is involved; the theta2 passes are k_slab's FFTs, and the theta1
+// pass works in place on the inverse theta2 pass's output buffer.
 template <typename T, int N1, int N2>
 __global__ void __launch_bounds__(SLAB_THREADS) k_slab_r16(SlabArgs<T> A) {
   static_assert(N1 == 64 && (4 * N2) % 32 == 0 && 4 * N2 <= SLAB_THREADS, "4 lanes of 16 points per theta2 row");
   using V = cplx_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int c = blockIdx.x, p = blockIdx.y;
-  constexpr int n1 = N1, n2 = N2, n2p = N2 + 1, CS = 17;   // CS: padded 16-bin row per lane
+  constexpr int n1 = N1, n2 = N2, CS = 17;   // CS: padded 16-bin row per lane
   const int nmr = A.nmr;
   constexpr bool PADW = sizeof(T) == sizeof(float);
   const int wsz = PADW ? pd_size(nmr * n2) : nmr * n2;
   auto ix = [](int i) { return PADW ? pd(i) : i; };
-  V* Tb = reinterpret_cast<V*>(smem_raw);   // [nmr][n2p]
-  V* W0 = Tb + nmr * n2p;
+  V* W0 = reinterpret_cast<V*>(smem_raw);   // the theta2 FFT buffers, [nmr][n2] each
   V* W1 = W0 + wsz;
   V* E4 = W1 + wsz;                         // [nmr][4]: omega^(m q)
   V* Cs = E4 + 4 * nmr;                     // [4 N2][CS]: one lane's 16 bins
@@ -722,19 +722,16 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab_r16(SlabArgs<T> A) {
   for (int a = threadIdx.x; a < A.nA; a += blockDim.x)
     W0[ix(A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2))] = Gc[a];
   __syncthreads();
-  V* r2 = fft_any<T, N2, PADW>(W0, W1, A.p2, nmr, A.tw2, +1);
-  for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) {
-    const int rr = i / n2, jj = i - rr * n2;
-    Tb[rr * n2p + jj] = r2[ix(i)];
-  }
-  __syncthreads();
+  // Tb: the rows at the theta2 points, updated in place by the theta1 pass (the 4 lanes that
+  // read and write the point j of every row are one warp's)
+  V* Tb = fft_any<T, N2, PADW>(W0, W1, A.p2, nmr, A.tw2, +1);
   if (threadIdx.x < 4 * n2) {
     const int j = threadIdx.x >> 2, q = threadIdx.x & 3;
     V* cs = Cs + threadIdx.x * CS;
 #pragma unroll
     for (int b = 0; b < 16; ++b) cs[b] = zero;
     for (int r = 0; r < nmr; ++r) {   // bins of this lane (its own row of Cs: no other writer)
-      const V t = Tb[r * n2p + j], e = E4[4 * r + q];
+      const V t = Tb[ix(r * n2 + j)], e = E4[4 * r + q];
       const int b = A.mrow_m[r] & 15;
       V v = cs[b];
       v.x += t.x * e.x - t.y * e.y;
@@ -758,7 +755,7 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab_r16(SlabArgs<T> A) {
     dft16<-1, T>(xr, xi);
 #pragma unroll
     for (int b = 0; b < 16; ++b) cs[b] = mk<T>(xr[b], xi[b]);
-    __syncwarp();   // every lane of this row has read its column of Tb
+    __syncwarp();   // every lane of this point has read its column of Tb
     for (int r = 0; r < nmr; ++r) {
       const V d = cs[A.mrow_m[r] & 15], e = E4[4 * r + q];   // times conj(omega^(m q))
       T sr = d.x * e.x + d.y * e.y, si = d.y * e.x - d.x * e.y;
@@ -766,24 +763,19 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab_r16(SlabArgs<T> A) {
       si += __shfl_xor_sync(0xffffffffu, si, 1);
       sr += __shfl_xor_sync(0xffffffffu, sr, 2);
       si += __shfl_xor_sync(0xffffffffu, si, 2);
-      if (q == (r & 3)) Tb[r * n2p + j] = mk<T>(sr, si);
+      if (q == (r & 3)) Tb[ix(r * n2 + j)] = mk<T>(sr, si);
     }
   }
   __syncthreads();
-  // theta2 forward pass, extract the kept pairs
-  for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) {
-    const int rr = i / n2, jj = i - rr * n2;
-    W0[ix(i)] = Tb[rr * n2p + jj];
-  }
-  __syncthreads();
-  r2 = fft_any<T, N2, PADW>(W0, W1, A.p2, nmr, A.tw2, -1);
+  // theta2 forward pass from Tb, extract the kept pairs
+  V* r2 = fft_any<T, N2, PADW>(Tb, Tb == W0 ? W1 : W0, A.p2, nmr, A.tw2, -1);
   for (int a = threadIdx.x; a < A.nA; a += blockDim.x)
     Hc[a] = r2[ix(A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2))];
 }
 
 static size_t slab_r16_smem_bytes(int nmr, int n2, size_t elem) {
   const size_t w = elem == sizeof(float2) ? (size_t)pd_size(nmr * n2) : (size_t)nmr * n2;
-  return elem * ((size_t)nmr * (n2 + 1) + 2 * w + 4 * (size_t)nmr + (size_t)4 * n2 * 17);
+  return elem * (2 * w + 4 * (size_t)nmr + (size_t)4 * n2 * 17);
 }
 
 // FP32 on the 64 x 48 grid: the 4 x 16 theta1 variant (unless HW_OPT_SLAB_KERNEL selects the
