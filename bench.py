@@ -608,8 +608,10 @@ def roofline(result, w, ctx, L, nb):
         fl = slab_flops(w.geom, *nmr_nA) * cols * w.geom.Nr
         ach = fl / (hxm / 1e3) / 1e12
         rec.update({"bound": "alu", "achieved": round(ach, 3), "peak": round(fp32, 2), "unit": "TFLOP/s",
-                    "frac": round(ach / fp32, 4), "traffic": _traffic("slab"),
-                    "basis": "64-column H X launch, FP32 FMA peak 152x128x2 flop/clk at the sampled SM clock"})
+                    "frac": round(ach / fp32, 4), "traffic": _traffic("slab"), "launch_ms": hxm,
+                    "basis": "64-column FP32 H X launch (launch_ms, CUDA events; avg_ms is the step's "
+                             "mean over both precisions' slab launches), FP32 FMA peak 152x128x2 flop/clk "
+                             "at the sampled SM clock"})
     elif dom in ("radial_inv", "radial_fwd"):
         hxm = result["hx"]["mixed"]["kernel_ms"][dom]
         by = radial_bytes(L, 64, w.geom.Nr, s["n_pairs"], 4)
