@@ -93,6 +93,7 @@ void free_basis(hw_ctx* ctx) {
   dfree(db.pair_n);
   dfree(db.pair_mrow);
   dfree(db.mrow_m);
+  dfree(db.slot_pair);
   dfree(db.off);
   dfree(db.Ka);
   dfree(db.ke);
@@ -220,6 +221,7 @@ hw_status hw_setup_basis(hw_ctx* ctx, const hw_basis_params* params, int nk, con
     UP(db.pair_n, hb.pair_n);
     UP(db.pair_mrow, hb.pair_mrow);
     UP(db.mrow_m, hb.mrow_m);
+    UP(db.slot_pair, hb.slot_pair);
     UP(db.off, hb.off);
     UP(db.Ka, hb.Ka);
     UP(db.ke, keall);

@@ -29,6 +29,7 @@ struct DevBasis {
   int* pair_n = nullptr;       // [nA]
   int* pair_mrow = nullptr;    // [nA]
   int* mrow_m = nullptr;       // [nmr]
+  int* slot_pair = nullptr;    // [nmr][Nth2]: pair index or -1
   int* off = nullptr;          // [nk][nA]
   int* Ka = nullptr;           // [nk][nA]
   double* ke = nullptr;        // concatenated [sum L_b] shifted kinetic energies

@@ -544,6 +544,7 @@ struct SlabArgs {
   const int* pair_n;
   const int* pair_mrow;
   const int* mrow_m;
+  const int* slot_pair;   // [nmr][Nth2]: pair index or -1 (the lane-split slab only)
   const T* V;        // [Nr][Nth2][Nth1]
   const cplx_t<T>* tw1;
   const cplx_t<T>* tw2;
@@ -716,15 +717,39 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab_r16(SlabArgs<T> A) {
     const V w = A.tw1[pmod(A.mrow_m[r] * q, n1)];   // e^{-2 pi i m q / 64}
     E4[t] = mk<T>(w.x, -w.y);
   }
-  // theta2 inverse pass over the kept m rows
-  for (int i = threadIdx.x; i < nmr * n2; i += blockDim.x) W0[ix(i)] = zero;
-  __syncthreads();
-  for (int a = threadIdx.x; a < A.nA; a += blockDim.x)
-    W0[ix(A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2))] = Gc[a];
-  __syncthreads();
+  // theta2 inverse pass over the kept m rows.  Its first radix-4 Stockham pass (stride 1, no
+  // twiddles) reads G through the (row, point) -> pair table, zero where no pair is kept, and
+  // writes W1; the remaining passes start at stride 4.
+  static_assert(N2 % 4 == 0, "first theta2 pass radix 4");
+  {
+    constexpr int nbf = N2 / 4;
+    for (int idx = threadIdx.x; idx < nmr * nbf; idx += blockDim.x) {
+      const int b = idx / nbf, j = idx - b * nbf;
+      const int* sp = A.slot_pair + b * n2 + j;
+      V v[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int a = sp[t * nbf];
+        v[t] = a >= 0 ? Gc[a] : zero;
+      }
+      const V s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+      const V s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
+      const V t = cmul_i(d13, +1);
+      const int base = b * n2 + 4 * j;
+      W1[ix(base)] = cadd(s02, s13);
+      W1[ix(base + 1)] = cadd(d02, t);
+      W1[ix(base + 2)] = csub(s02, s13);
+      W1[ix(base + 3)] = csub(d02, t);
+    }
+    __syncthreads();
+  }
   // Tb: the rows at the theta2 points, updated in place by the theta1 pass (the 4 lanes that
   // read and write the point j of every row are one warp's)
-  V* Tb = fft_any<T, N2, PADW>(W0, W1, A.p2, nmr, A.tw2, +1);
+  V* Tb = W1;
+  {
+    V* dst = W0;
+    fft_ct_stages<T, N2, 4, PADW>(Tb, dst, nmr, A.tw2, +1);
+  }
   if (threadIdx.x < 4 * n2) {
     const int j = threadIdx.x >> 2, q = threadIdx.x & 3;
     V* cs = Cs + threadIdx.x * CS;
@@ -905,6 +930,7 @@ cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, const 
     sa.pair_n = db.pair_n;
     sa.pair_mrow = db.pair_mrow;
     sa.mrow_m = db.mrow_m;
+    sa.slot_pair = db.slot_pair;
     sa.V = tb.V;
     sa.tw1 = reinterpret_cast<const cplx_t<T>*>(tb.tw1);
     sa.tw2 = reinterpret_cast<const cplx_t<T>*>(tb.tw2);
@@ -981,6 +1007,7 @@ cudaError_t launch_hx_into(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, v
     sa.pair_n = db.pair_n;
     sa.pair_mrow = db.pair_mrow;
     sa.mrow_m = db.mrow_m;
+    sa.slot_pair = db.slot_pair;
     sa.V = tb.V;
     sa.tw1 = reinterpret_cast<const cplx_t<T>*>(tb.tw1);
     sa.tw2 = reinterpret_cast<const cplx_t<T>*>(tb.tw2);

@@ -28,6 +28,7 @@ struct HostBasis {
   std::vector<int> group_start;              // [N+2]: pairs of |n| = g are [gs[g], gs[g+1])
   std::vector<int> mrow_m;                   // active m values (ascending)
   std::vector<int> pair_mrow;                // [nA] index into mrow_m
+  std::vector<int> slot_pair;                // [nmr][Nth2]: the pair at (m row, n mod Nth2), or -1
   // per k-point / per pair: compact offset and kept radial count
   std::vector<int> off;                      // [nk][nA]
   std::vector<int> Ka;                       // [nk][nA]

@@ -320,6 +320,9 @@ std::string build_host_basis(const hw_basis_params& p, int nk, const double* eta
   }
   hb.pair_mrow.resize(hb.nA);
   for (int a = 0; a < hb.nA; ++a) hb.pair_mrow[a] = mset[hb.pair_m[a]];
+  hb.slot_pair.assign(hb.mrow_m.size() * (size_t)p.Nth2, -1);
+  for (int a = 0; a < hb.nA; ++a)
+    hb.slot_pair[(size_t)hb.pair_mrow[a] * p.Nth2 + ((hb.pair_n[a] % p.Nth2) + p.Nth2) % p.Nth2] = a;
   // compact offsets (box order restricted to the mask), kinetic energies, index maps
   hb.off.assign(size_t(nk) * hb.nA, 0);
   hb.Ka.assign(size_t(nk) * hb.nA, 0);
