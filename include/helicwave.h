@@ -175,13 +175,15 @@ hw_status hw_apply_precond(hw_ctx* ctx, int k, const double* R, double* Z, int n
  * at most 112 columns (HW_EINVAL above: the Cholesky-QR keeps its factor in shared memory).
  * More than HW_OPT_WINDOW eigenpairs (default 80) are solved in w = ceil(n_eig / window)
  * consecutive windows of ceil(n_eig / w) eigenpairs (the last one the rest).  Each window is a
- * block solve as above (`block` then applies to one window; default for the Chebyshev solver
- * min(112, L_min / 3), the largest block the basis allows; for LOBPCG the solver's own
- * default) restricted to the orthogonal complement of the eigenvectors the earlier windows
- * converged: the start block and, every iteration, the new search directions (LOBPCG) or the
- * filtered block (Chebyshev) are projected against them (in FP64; in the FP32 and hybrid
- * phases of the mixed form with FP32 products).  The windows run in lockstep over the k-points; X0
- * must be NULL then (HW_EINVAL); iters is the sum over the windows.
+ * block solve as above (`block` then applies to one window; default the window plus
+ * max(32, window / 2) buffer columns, at most 112 and L_min / 3) restricted to the orthogonal
+ * complement of the eigenvectors the earlier windows converged: the start block and, every
+ * iteration, the new search directions (LOBPCG) or the filtered block (Chebyshev) are
+ * projected against them (in FP64; in the FP32 and hybrid phases of the mixed form with FP32
+ * products).  Windows before the last aim at tol / 2 (their residuals leak into the later
+ * windows' eigenvectors, which the projection cannot remove) and are accepted at tol once
+ * their residuals stop falling.  The windows run in lockstep over the k-points; X0 must be
+ * NULL then (HW_EINVAL); iters is the sum over the windows.
  * A column is converged when ||H x - theta x||_2 <= tol with ||x|| = 1.  X0 (nullable):
  * nk device pointers to L_k x block complex128 start blocks (leading dimension L_k); NULL
  * draws a seeded Gaussian start on the device.  Outputs: evals (host, [nk*n_eig]), iters

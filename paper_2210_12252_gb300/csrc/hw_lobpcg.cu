@@ -975,7 +975,8 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
                             double tol, int maxit, hw_prec prec, int precond_kind,
                             const double* const* X0, double* evals, double* const* evecs,
                             int64_t ld_evecs, int* iters, double* resid, Trace* trace,
-                            bool keep_start = false, bool no_p = false, const Deflate* df = nullptr) {
+                            bool keep_start = false, bool no_p = false, const Deflate* df = nullptr,
+                            double tol_accept = 0.0) {
   if (!ctx) return HW_EINVAL;
   if (precond_kind != HW_PRECOND_TPA && precond_kind != HW_PRECOND_NONE &&
       !(precond_kind == HW_PRECOND_LEARNED && ctx->mlp))
@@ -1025,6 +1026,8 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
   bool p_off = no_p;
   double p_prev = 1e300;
   int p_it = -1;
+  double acc_best = 1e300;   // best largest residual since the FP32 phase (tol_accept)
+  int acc_best_it = 0;
   hw_status final_status = HW_ENOTCONV;
   for (it = 0; it <= maxit; ++it) {
     double2* S = w->SB[cur];
@@ -1059,6 +1062,10 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       }
     }
     // mixed: refresh HX in FP64 once the residuals are small, and before accepting convergence
+    // tol_accept > tol (a window of a windowed solve): tol is the target, and once the largest
+    // residual has stopped falling (past the FP32 phase, no 30% drop in 8 iterations: the
+    // precision's floor) a k-point whose residuals are at most tol_accept is accepted
+    const double thr = (tol_accept > tol && !gemm.lowp && it - acc_best_it >= 8) ? tol_accept : tol;
     double maxres = 0.0;
     std::vector<int> claim(nk, 0);
     int nclaim = 0;
@@ -1067,10 +1074,14 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       double mr = 0.0;
       for (int j = 0; j < n_eig; ++j) mr = std::max(mr, resh[(size_t)b * nb + j]);
       maxres = std::max(maxres, mr);
-      if (mr <= tol) {
+      if (mr <= thr) {
         claim[b] = 1;
         ++nclaim;
       }
+    }
+    if (gemm.lowp || maxres < 0.7 * acc_best) {
+      acc_best = maxres;
+      acc_best_it = it;
     }
     // FP32 products stall near residual 1e-5: leave them also when the best residual has not
     // dropped by 30% in 4 iterations
@@ -1180,7 +1191,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
         if (done[b]) continue;
         double mr = 0.0;
         for (int j = 0; j < n_eig; ++j) mr = std::max(mr, resh[(size_t)b * nb + j]);
-        claim[b] = mr <= tol;
+        claim[b] = mr <= thr;
       }
     } else if (!mixed) {
       // FP64 products: residuals are already exact
@@ -1478,7 +1489,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
 static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, int block, double tol, int maxit,
                             hw_prec prec, int precond_kind, const double* const* X0, double* evals,
                             double* const* evecs, int64_t ld_evecs, int* iters, double* resid,
-                            const Deflate* df = nullptr) {
+                            const Deflate* df = nullptr, double tol_accept = 0.0) {
   if (!ctx) return HW_EINVAL;
   Gemm gemm{ctx};
   SolveSetup su;
@@ -1596,7 +1607,8 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
                             cudaMemcpyDeviceToDevice, st);
         std::vector<int> itl(nk, 0);
         hs = solve_impl(ctx, nk, kidx_in, n_eig, nb, tol, std::max(1, maxit - it), prec, precond_kind, nullptr,
-                        evals, evecs, ld_evecs, itl.data(), resid, nullptr, true, ctx->tail_no_p != 0, df);
+                        evals, evecs, ld_evecs, itl.data(), resid, nullptr, true, ctx->tail_no_p != 0, df,
+                        tol_accept);
         if (iters)
           for (int b = 0; b < nk; ++b) iters[b] = it + itl[b];
         return hs;
@@ -1817,12 +1829,13 @@ extern "C" hw_status hw_heev(hw_ctx* ctx, int n, int nprob, int nw, const double
 
 static hw_status solve_window(hw_ctx* ctx, int nk, const int* kidx, int n_eig, int block, double tol, int maxit,
                               hw_prec prec, int precond_kind, const double* const* X0, double* evals,
-                              double* const* evecs, int64_t ld_evecs, int* iters, double* resid, const Deflate* df) {
+                              double* const* evecs, int64_t ld_evecs, int* iters, double* resid, const Deflate* df,
+                              double tol_accept = 0.0) {
   if (ctx->eigensolver == 1)
     return chfsi_impl(ctx, nk, kidx, n_eig, block, tol, maxit, prec, precond_kind, X0, evals, evecs, ld_evecs, iters,
-                      resid, df);
+                      resid, df, tol_accept);
   return solve_impl(ctx, nk, kidx, n_eig, block, tol, maxit, prec, precond_kind, X0, evals, evecs, ld_evecs,
-                    iters, resid, nullptr, false, false, df);
+                    iters, resid, nullptr, false, false, df, tol_accept);
 }
 
 extern "C" hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx, int n_eig, int block, double tol,
@@ -1883,16 +1896,23 @@ extern "C" hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx, int n_e
     df.nq = w0;
     std::vector<double*> out(nk);
     for (int b = 0; b < nk; ++b) out[b] = reinterpret_cast<double*>(Qp[b] + (size_t)w0 * ldq);
-    // default block of the Chebyshev solver: the largest the basis allows (the top columns of a
-    // window converge at the rate of the gap to the first column outside the block); LOBPCG
-    // keeps its own default
+    // default block: a wide buffer (the top columns of a window converge at the rate of the gap
+    // to the first column outside the block), at most 112 columns and what the basis allows
     int bw = block;
-    if (bw <= 0 && ctx->eigensolver == 1) {
-      bw = (int)std::min<int64_t>(112, Lmin / 3);
+    if (bw <= 0) {
+      bw = (int)std::min<int64_t>(std::min(112, nw + std::max(32, nw / 2)), Lmin / 3);
       if (bw < nw) bw = 0;   // the solver's own default (and its error if that does not fit)
     }
-    const hw_status hs = solve_window(ctx, nk, kidx, nw, bw, tol, maxit, prec, precond_kind, nullptr, ev.data(),
-                                      out.data(), ldq, itw.data(), rs.data(), &df);
+    // a locked eigenvector's residual r_i is orthogonal to its own window's block and points
+    // mostly at the first eigenvectors beyond it, which later windows solve for in the
+    // complement of the locked set: an eigenvector y there keeps the true residual
+    // ||R^H y|| whatever the window does.  Windows before the last therefore aim at tol / 2,
+    // which keeps that floor below tol; where the precision's own floor stops them above it
+    // (the mixed form's FP32 products), they are accepted at tol.
+    const bool last = w0 + nw >= n_eig;
+    const double tw = last ? tol : std::max(0.5 * tol, std::min(tol, 1e-11));
+    const hw_status hs = solve_window(ctx, nk, kidx, nw, bw, tw, maxit, prec, precond_kind, nullptr, ev.data(),
+                                      out.data(), ldq, itw.data(), rs.data(), &df, last ? 0.0 : tol);
     if (hs == HW_OK || hs == HW_ENOTCONV) {
       for (int b = 0; b < nk; ++b) {
         for (int j = 0; j < nw; ++j) {
