@@ -114,6 +114,15 @@ def test_device_calls_on_host_context_are_rejected(lib):
     with pytest.raises(hw.HwError) as e:
         hw.hw_apply_H(ctx.h, 0, 0, 0, 1, int(L[0]))
     assert e.value.status == hw.HW_ESTATE
+    # a solve, within one block and windowed (more eigenpairs than HW_OPT_WINDOW)
+    for n_eig in (8, 120):
+        with pytest.raises(hw.HwError) as e:
+            hw.hw_solve_eigs(ctx.h, [0], n_eig)
+        assert e.value.status == hw.HW_ESTATE, n_eig
+    ctx.set_option(hw.HW_OPT_WINDOW, 4)
+    with pytest.raises(hw.HwError) as e:
+        hw.hw_solve_eigs(ctx.h, [0], 8)
+    assert e.value.status == hw.HW_ESTATE
 
 
 def test_options_set_get_and_reject(lib):
