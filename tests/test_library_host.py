@@ -177,3 +177,19 @@ def test_cyclic_masks_and_itable_match_oracle(lib):
     for n in range(-b.N, b.N + 1):
         I = b.itable(n)
         np.testing.assert_allclose(ctx.itable(n), I, rtol=0, atol=1e-12 * np.abs(I).max())
+
+
+def test_binding_constants_match_the_header():
+    """Every enumerator of include/helicwave.h (statuses, precisions, preconditioners, options,
+    profiler phases) has the same value in the Python binding, and the binding's phase names
+    follow the header's HW_PH_ order."""
+    hdr = open(os.path.join(ROOT, "include", "helicwave.h")).read()
+    enums = dict((k, int(v)) for k, v in re.findall(r"\b(HW_[A-Z0-9_]+)\s*=\s*(\d+)", hdr))
+    assert len(enums) > 30
+    for name, value in enums.items():
+        if name.startswith("HW_PH_") or name == "HW_NPHASE":
+            continue
+        assert getattr(hw, name) == value, name
+    phases = sorted((v, k) for k, v in enums.items() if k.startswith("HW_PH_"))
+    assert [k[len("HW_PH_"):].lower() for _, k in phases] == hw.PHASES
+    assert len(hw.PHASES) == enums["HW_NPHASE"]
