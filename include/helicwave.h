@@ -150,7 +150,9 @@ hw_status hw_apply_H(hw_ctx* ctx, int k, const double* X, double* Y, int ns, int
  * before any stream capture).  Columns are processed in passes that fit the array; a basis
  * whose single column does not fit (2 * N_r * n_pairs complex values) is rejected with
  * HW_EINVAL.  Calls share the array: calls that overlap on the GPU race and must be ordered
- * by the caller.  Arguments as for hw_apply_H. */
+ * by the caller.  The array's address is resolved once per device for the life of the
+ * process, so resetting a device (cudaDeviceReset) while this library is loaded is not
+ * supported.  Arguments as for hw_apply_H; X and Y must not overlap at all (HW_EINVAL). */
 hw_status hw_apply_H_noalloc(hw_ctx* ctx, int k, const double* X, double* Y, int ns, int64_t ld,
                              hw_prec prec);
 
@@ -238,6 +240,18 @@ hw_status hw_solve_eigs_traced(hw_ctx* ctx, int k, int n_eig, int block, double 
                                const int* rec_iters, double* rec_R, double* rec_E,
                                double* rec_theta, double* rec_res, int64_t ld, double* evals,
                                int* iters);
+
+/* Self-test of the bounded device wait (no counterpart in the paper; failure detection).  The
+ * library's grid-wide barrier (used by the FP64 Jacobi eigensolver) gives up after a bounded
+ * number of polls, sets the device status word to HW_ETIMEOUT and lets every CTA leave, so a
+ * barrier that can never complete ends the kernel instead of hanging the GPU.  This call runs
+ * three such barriers over `nblocks` co-resident CTAs (2 .. SM count) with a wait bound of
+ * `spin_limit` polls of 100 ns (1 .. 2^24); CTA `skip_block` (-1: none) leaves before the first
+ * barrier, so the others can never be released.  On return *wait_status (host) holds the
+ * kernel's status word: HW_OK when every barrier completed, HW_ETIMEOUT when a wait ran out.
+ * Synchronises the context's stream.  Returns HW_EINVAL for arguments out of range. */
+hw_status hw_selftest_barrier(hw_ctx* ctx, int nblocks, long long spin_limit, int skip_block,
+                              int* wait_status);
 
 /* The Rayleigh-Ritz step's dense Hermitian eigensolver on its own (Sec. "Eigensolvers and
  * Preconditioning": the small projected eigenproblem of LOBPCG).  A: device, nprob Hermitian

@@ -27,9 +27,22 @@ import numpy as np
 
 
 def gaussian_wells(basis, atoms: np.ndarray) -> np.ndarray:
-    atoms = np.asarray(atoms, dtype=np.float64).reshape(-1, 5)
+    """V on the whole helical grid, shape (N_th1, N_th2, N_r)."""
     th1, th2 = basis.theta_grid()
     T1, T2, RR = np.meshgrid(th1, th2, basis.r, indexing="ij")
+    return well_sum(basis, atoms, T1, T2, RR)
+
+
+def gaussian_wells_at(basis, atoms: np.ndarray, i, j, p) -> np.ndarray:
+    """V at the grid points (theta1_i, theta2_j, r_p) only (integer index arrays of one shape)."""
+    th1, th2 = basis.theta_grid()
+    return well_sum(basis, atoms, th1[np.asarray(i)], th2[np.asarray(j)], basis.r[np.asarray(p)])
+
+
+def well_sum(basis, atoms, T1, T2, RR):
+    """The image sum of eq. sim_atoms evaluated at helical coordinates (T1, T2, RR) (arrays of one
+    shape): z = tau theta1, vartheta = 2 pi (theta2 + alpha theta1)."""
+    atoms = np.asarray(atoms, dtype=np.float64).reshape(-1, 5)
     z = basis.tau * T1
     vth = 2 * np.pi * (T2 + basis.alpha * T1)
     V = np.zeros_like(z)

@@ -43,16 +43,19 @@ __device__ __forceinline__ V cmul_i(V a, int s) {
 
 // FP64 <-> FP32 by integer bit operations.  This GPU executes the hardware conversions on its
 // FP64 pipe (1/64 of the FP32 rate), which otherwise bounds kernels that convert every operand.
-// d2f: round to nearest (ties away from zero), magnitudes below 2^-126 flush to zero, overflow
-// to infinity.  f2d: exact for normal numbers and zero (subnormal floats flush to zero).
+// d2f: round to nearest, ties to even (as a cast); magnitudes below 2^-126 flush to zero,
+// overflow to infinity, NaN stays NaN (quiet, sign kept).  f2d: exact for normal numbers, zero,
+// infinities and NaN (subnormal floats flush to zero).
 __device__ __forceinline__ float d2f(double x) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
   const unsigned long long v = u & 0x7FFFFFFFFFFFFFFFull;
-  const unsigned long long r = ((v >> 28) + 1ull) >> 1;   // exponent | 23-bit mantissa, rounded
+  if (v > 0x7FF0000000000000ull) return __uint_as_float(sign | 0x7FC00000u);
+  // drop 29 mantissa bits: add just under half an ulp, plus one when the kept last bit is odd
+  const unsigned long long r = (v + 0x0FFFFFFFull + ((v >> 29) & 1ull)) >> 29;   // exponent | 23 bits
   const unsigned long long lo = 897ull << 23, hi = 1151ull << 23;
-  unsigned int bits = r < lo ? 0u : (r >= hi ? 0x7F800000u : (unsigned int)(r - (896ull << 23)));
-  bits |= (unsigned int)(u >> 32) & 0x80000000u;
-  return __uint_as_float(bits);
+  const unsigned int bits = r < lo ? 0u : (r >= hi ? 0x7F800000u : (unsigned int)(r - (896ull << 23)));
+  return __uint_as_float(bits | sign);
 }
 __device__ __forceinline__ double f2d(float x) {
   const unsigned int u = __float_as_uint(x);

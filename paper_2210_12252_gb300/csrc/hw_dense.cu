@@ -222,8 +222,13 @@ struct GridBar {
   int pad;
 };
 
-// returns false when the barrier gave up (error flag set; the caller leaves the kernel)
-__device__ bool grid_sync(GridBar* bar, int* status) {
+// Default bound of a barrier wait: 2^24 polls with 100 ns sleeps, about 2 s.
+constexpr long GRID_SPIN_LIMIT = 1L << 24;
+
+// returns false when the barrier gave up (error flag set; the caller leaves the kernel).  A
+// CTA that waits more than spin_limit polls sets bar->abort and *status = HW_ETIMEOUT; the
+// CTAs still waiting see the abort and leave too.
+__device__ bool grid_sync(GridBar* bar, int* status, long spin_limit = GRID_SPIN_LIMIT) {
   __syncthreads();
   __shared__ int ok;
   if (threadIdx.x == 0) {
@@ -241,7 +246,7 @@ __device__ bool grid_sync(GridBar* bar, int* status) {
       long spins = 0;
       while (*vgen == g) {
         if (*vab) { ok = 0; break; }
-        if (++spins > (1L << 24)) {   // ~2 s with the sleeps below
+        if (++spins > spin_limit) {
           atomicExch(&bar->abort, 1);
           atomicExch(status, HW_ETIMEOUT);
           ok = 0;
@@ -518,6 +523,36 @@ void dense_free(DenseWork*& dw) {
     if (p) cudaFree(p);
   delete dw;
   dw = nullptr;
+}
+
+// Self-test of the bounded barrier wait: `rounds` grid barriers over the grid; the CTA
+// `skip_block` (if >= 0) leaves before the first one, so the others can never be released and
+// must give up after spin_limit polls with HW_ETIMEOUT in *status.
+__global__ void k_barrier_selftest(GridBar* bar, int* status, long spin_limit, int skip_block, int rounds) {
+  if ((int)blockIdx.x == skip_block) return;
+  for (int r = 0; r < rounds; ++r)
+    if (!grid_sync(bar, status, spin_limit)) return;
+}
+
+// Runs k_barrier_selftest as a cooperative launch (all CTAs co-resident) of nblocks CTAs on
+// `st`, waits for it, and returns the device status word (HW_OK or HW_ETIMEOUT) in *wait_status.
+cudaError_t dense_barrier_selftest(cudaStream_t st, int nblocks, long spin_limit, int skip_block,
+                                   int* wait_status) {
+  GridBar* bar = nullptr;
+  int* status = nullptr;
+  cudaError_t e = cudaMalloc((void**)&bar, sizeof(GridBar));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(bar, 0, sizeof(GridBar), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
+  int rounds = 3;
+  void* args[] = {&bar, &status, &spin_limit, &skip_block, &rounds};
+  if (e == cudaSuccess)
+    e = cudaLaunchCooperativeKernel((void*)k_barrier_selftest, dim3(nblocks), dim3(128), args, 0, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(wait_status, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (bar) cudaFree(bar);
+  if (status) cudaFree(status);
+  return e;
 }
 
 // Eigen-decomposition of nprob Hermitian n x n matrices A (contiguous, n*n each; destroyed):

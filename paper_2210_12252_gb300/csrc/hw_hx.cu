@@ -874,17 +874,20 @@ static void set_nu_args(const hw_ctx* ctx, const Blocks& blk, const DevTables<T>
   ra.mrow_m = ctx->db.mrow_m;
 }
 
-// Launch the three kernels for the column blocks `blk` (ns columns each).  Columns are
-// processed in passes of at most ctx->ws.cols columns.
+// Launch the three kernels for the column blocks `blk` (ns columns each) with the G / H
+// intermediates in `gbuf` / `hbuf`, which hold `cols` columns each; columns are processed in
+// passes of at most that many (fewer when the autotuner chose a narrower pass).  Every pass
+// writes each intermediate value before reading it, so the buffers need no initialisation.
 template <typename T>
-cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, const ChebStep* step) {
+static cudaError_t launch_hx_bufs(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, const ChebStep* step,
+                                  void* gbuf, void* hbuf, int cols) {
   auto& hb = ctx->hb;
   auto& db = ctx->db;
   const DevTables<T>& tb = *reinterpret_cast<const DevTables<T>*>(
       sizeof(T) == 8 ? (const void*)&db.t64 : (const void*)&db.t32);
   const int ncols_total = blk.nslot * ns;
   const int ti = sizeof(T) == 8 ? 0 : 1;
-  int chunk = (int)ctx->ws.cols;
+  int chunk = cols;
   if (ctx->ws.pass_cols[ti] > 0) chunk = std::min(chunk, ctx->ws.pass_cols[ti]);
   if (chunk <= 0 || blk.nslot > MAXSLOT) return cudaErrorInvalidValue;
   const int Nr = hb.prm.Nr, K = hb.K;
@@ -908,7 +911,7 @@ cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, const 
     for (int i = 0; i < blk.nslot; ++i) ra.keoff[i] = db.ke_off[blk.kb[i]];
     set_nu_args(ctx, blk, tb, ra);
     ra.blk = blk;
-    ra.gh = reinterpret_cast<cplx_t<T>*>(ctx->ws.gbuf);
+    ra.gh = reinterpret_cast<cplx_t<T>*>(gbuf);
     ra.rtab = tb.rinv;
     dim3 grid((unsigned)(((long)maxna * nc + RAD_Q - 1) / RAD_Q), hb.N + 1);
     const size_t sm_inv = rad_inv_smem(Nr, K, sizeof(T));
@@ -934,15 +937,15 @@ cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, const 
     sa.V = tb.V;
     sa.tw1 = reinterpret_cast<const cplx_t<T>*>(tb.tw1);
     sa.tw2 = reinterpret_cast<const cplx_t<T>*>(tb.tw2);
-    sa.G = reinterpret_cast<const cplx_t<T>*>(ctx->ws.gbuf);
-    sa.H = reinterpret_cast<cplx_t<T>*>(ctx->ws.hbuf);
+    sa.G = reinterpret_cast<const cplx_t<T>*>(gbuf);
+    sa.H = reinterpret_cast<cplx_t<T>*>(hbuf);
     const size_t sm_slab = slab_smem_bytes(ctx, sizeof(cplx_t<T>), Jc);
     {
       ProfScope ps(ctx, HW_PH_SLAB);
       launch_slab<T>(ctx, dim3(nc, Nr), sm_slab, sa);
       ctx->launches++;
     }
-    ra.gh = reinterpret_cast<cplx_t<T>*>(ctx->ws.hbuf);
+    ra.gh = reinterpret_cast<cplx_t<T>*>(hbuf);
     ra.rtab = tb.rfwd;
     if (step) {
       ra.step = 1;
@@ -958,69 +961,17 @@ cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, const 
   return cudaGetLastError();
 }
 
-// The same three kernels with caller-chosen G / H buffers holding `cols` columns per pass
-// (used by the entry point that allocates nothing).
+// H X with the intermediates in the context's workspace.
+template <typename T>
+cudaError_t launch_hx(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, const ChebStep* step) {
+  return launch_hx_bufs<T>(ctx, blk, ns, ld, step, ctx->ws.gbuf, ctx->ws.hbuf, (int)ctx->ws.cols);
+}
+
+// H X with caller-chosen G / H buffers of `cols` columns each (the entry point that
+// allocates nothing); the same launch configuration as launch_hx.
 template <typename T>
 cudaError_t launch_hx_into(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, void* gbuf, void* hbuf, int cols) {
-  auto& hb = ctx->hb;
-  auto& db = ctx->db;
-  const DevTables<T>& tb = *reinterpret_cast<const DevTables<T>*>(
-      sizeof(T) == 8 ? (const void*)&db.t64 : (const void*)&db.t32);
-  const int ncols_total = blk.nslot * ns;
-  if (cols <= 0 || blk.nslot > MAXSLOT) return cudaErrorInvalidValue;
-  const int Nr = hb.prm.Nr, K = hb.K;
-  int maxna = 0;
-  for (int g = 0; g <= hb.N; ++g) maxna = std::max(maxna, hb.group_start[g + 1] - hb.group_start[g]);
-  const int Jc = slab_pick_jc(ctx, sizeof(cplx_t<T>));
-  for (int c0 = 0; c0 < ncols_total; c0 += cols) {
-    const int nc = std::min(cols, ncols_total - c0);
-    RadArgs<T> ra;
-    ra.Nr = Nr;
-    ra.K = K;
-    ra.nA = hb.nA;
-    ra.ncols = nc;
-    ra.ns = ns;
-    ra.c0 = c0;
-    ra.group_start = db.group_start;
-    ra.off = db.off;
-    ra.Ka = db.Ka;
-    ra.ld = ld;
-    ra.ke = db.ke;
-    for (int i = 0; i < blk.nslot; ++i) ra.keoff[i] = db.ke_off[blk.kb[i]];
-    set_nu_args(ctx, blk, tb, ra);
-    ra.blk = blk;
-    ra.gh = reinterpret_cast<cplx_t<T>*>(gbuf);
-    ra.rtab = tb.rinv;
-    dim3 grid((unsigned)(((long)maxna * nc + RAD_Q - 1) / RAD_Q), hb.N + 1);
-    const size_t sm_inv = rad_inv_smem(Nr, K, sizeof(T));
-    k_radial_inv<T><<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra);
-    SlabArgs<T> sa;
-    sa.Nr = Nr;
-    sa.Nth1 = hb.prm.Nth1;
-    sa.Nth2 = hb.prm.Nth2;
-    sa.nA = hb.nA;
-    sa.nmr = (int)hb.mrow_m.size();
-    sa.ncols = nc;
-    sa.Jc = Jc;
-    sa.p1 = to_dev(ctx->plan1);
-    sa.p2 = to_dev(ctx->plan2);
-    sa.pair_n = db.pair_n;
-    sa.pair_mrow = db.pair_mrow;
-    sa.mrow_m = db.mrow_m;
-    sa.slot_pair = db.slot_pair;
-    sa.V = tb.V;
-    sa.tw1 = reinterpret_cast<const cplx_t<T>*>(tb.tw1);
-    sa.tw2 = reinterpret_cast<const cplx_t<T>*>(tb.tw2);
-    sa.G = reinterpret_cast<const cplx_t<T>*>(gbuf);
-    sa.H = reinterpret_cast<cplx_t<T>*>(hbuf);
-    launch_slab<T>(ctx, dim3(nc, Nr), slab_smem_bytes(ctx, sizeof(cplx_t<T>), Jc), sa);
-    ra.gh = reinterpret_cast<cplx_t<T>*>(hbuf);
-    ra.rtab = tb.rfwd;
-    const size_t sm_fwd = rad_fwd_smem(Nr, K, sizeof(T));
-    k_radial_fwd<T><<<grid, RAD_THREADS, sm_fwd, ctx->stream>>>(ra);
-    ctx->launches += 3;
-  }
-  return cudaGetLastError();
+  return launch_hx_bufs<T>(ctx, blk, ns, ld, nullptr, gbuf, hbuf, cols);
 }
 
 template cudaError_t launch_hx_into<double>(hw_ctx*, const Blocks&, int, int64_t, void*, void*, int);

@@ -37,6 +37,7 @@ void dense_free(DenseWork*& dw);
 cudaError_t dense_heev(DenseWork* dw, cudaStream_t st, double2* A, int n, int nprob, double* w,
                        double2* Z, int* status, double tol);
 cudaError_t dense_chol(cudaStream_t st, double2* G, int n, int nprob, int* fail, bool fp32 = false);
+cudaError_t dense_barrier_selftest(cudaStream_t st, int nblocks, long spin_limit, int skip_block, int* wait_status);
 size_t gram_work_bytes(int m, int n, int K, int batch);
 cudaError_t gram_cf(cudaStream_t st, int m, int n, int K, double alpha, const double2* A, int64_t lda, int64_t sA,
                     const double2* B, int64_t ldb, int64_t sB, double beta, double2* C, int64_t ldc, int64_t sC,
@@ -1824,6 +1825,23 @@ extern "C" hw_status hw_heev(hw_ctx* ctx, int n, int nprob, int nw, const double
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("heev: ") + cudaGetErrorString(e));
   if (gemm.st != CUBLAS_STATUS_SUCCESS) return hw_fail(ctx, HW_ECUDA, "cuBLAS failure in heev");
+  return HW_OK;
+}
+
+extern "C" hw_status hw_selftest_barrier(hw_ctx* ctx, int nblocks, long long spin_limit, int skip_block,
+                                         int* wait_status) {
+  if (!ctx) return HW_EINVAL;
+  if (ctx->device < 0) return hw_fail(ctx, HW_ESTATE, "host-only context has no device");
+  int nsm = 0;
+  cudaSetDevice(ctx->device);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (nblocks < 2 || nblocks > nsm || spin_limit < 1 || spin_limit > (1LL << 24) || skip_block < -1 ||
+      skip_block >= nblocks || !wait_status)
+    return hw_fail(ctx, HW_EINVAL, "need 2 <= nblocks <= SM count, 1 <= spin_limit <= 2^24, -1 <= skip_block < nblocks");
+  int ws = -1;
+  const cudaError_t e = dense_barrier_selftest(ctx->stream, nblocks, (long)spin_limit, skip_block, &ws);
+  if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("barrier self-test: ") + cudaGetErrorString(e));
+  *wait_status = ws;
   return HW_OK;
 }
 

@@ -11,7 +11,9 @@
 // The array is shared by every call on a device and keeps the last call's contents; nothing in
 // it needs to start at zero (each pass writes every intermediate value before reading it).
 // Calls whose work overlaps on the GPU (different streams, or different contexts on one device)
-// race on the array and must be ordered by the caller.
+// race on the array and must be ordered by the caller.  The array's device address is resolved
+// once per device and kept for the life of the process (a device reset is not supported).
+#include <cstdint>
 #include <mutex>
 
 #include "hw_ctx.h"
@@ -57,7 +59,12 @@ extern "C" hw_status hw_apply_H_noalloc(hw_ctx* ctx, int k, const double* X, dou
   if (!ctx->have_V) return hw_fail(ctx, HW_ESTATE, "no potential installed");
   if (k < 0 || k >= ctx->hb.nk) return hw_fail(ctx, HW_EINVAL, "k-point index out of range");
   if (!X || !Y || ns < 1 || ld < ctx->hb.L[k]) return hw_fail(ctx, HW_EINVAL, "bad block arguments");
-  if (X == Y) return hw_fail(ctx, HW_EINVAL, "X and Y must not overlap");
+  {
+    // the byte ranges the block arguments span, [p, p + 16 ((ns - 1) ld + L))
+    const uintptr_t span = 16u * ((uintptr_t)(ns - 1) * (uintptr_t)ld + (uintptr_t)ctx->hb.L[k]);
+    const uintptr_t x0 = (uintptr_t)X, y0 = (uintptr_t)Y;
+    if (x0 < y0 + span && y0 < x0 + span) return hw_fail(ctx, HW_EINVAL, "X and Y must not overlap");
+  }
   if (prec != HW_FP64 && prec != HW_MIXED) return hw_fail(ctx, HW_EINVAL, "bad precision");
   const size_t elem = prec == HW_FP64 ? sizeof(double2) : sizeof(float2);
   const size_t per_buf = (size_t)ctx->hb.prm.Nr * ctx->hb.nA * elem;   // one column of G (or H)

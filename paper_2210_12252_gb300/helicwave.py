@@ -72,6 +72,7 @@ _SIGS = {
                               C.POINTER(C.c_int)]),
     "hw_heev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                           C.c_int]),
+    "hw_selftest_barrier": (C.c_int, [C.c_void_p, C.c_int, C.c_longlong, C.c_int, C.POINTER(C.c_int)]),
     "hw_density": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_void_p), C.c_int, C.c_int64,
                              _D, _D, C.c_void_p, C.c_int]),
     "hw_gradient": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_int]),
@@ -325,6 +326,14 @@ def hw_heev(h, A, nw, method=1):
     _check(h, load_library().hw_heev(h, n, nprob, nw, C.c_void_p(A.data_ptr()), C.c_void_p(w.data_ptr()),
                                      C.c_void_p(Z.data_ptr()), method))
     return w, Z
+
+
+def hw_selftest_barrier(h, nblocks, spin_limit, skip_block):
+    """Run the bounded grid-barrier self-test; returns the kernel's status word (HW_OK or
+    HW_ETIMEOUT)."""
+    ws = C.c_int(-1)
+    _check(h, load_library().hw_selftest_barrier(h, nblocks, spin_limit, skip_block, C.byref(ws)))
+    return int(ws.value)
 
 
 def hw_profile(h, enable: bool):

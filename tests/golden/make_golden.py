@@ -87,5 +87,59 @@ basis L = {kp.L}; lowest 128 eigenvalues of the dense Hamiltonian, Hartree
 source: oracle.hamiltonian.dense_H_conv (convolution form of Algorithm 5) + numpy.linalg.eigh""", ev)
 
 
+    if "tube32" in which:
+        # the 32 k-points of the batched workload: lowest 48 eigenvalues per point
+        w = inputs.tube_kpoints(nk=32)
+        b = basis_of(w.geom)
+        V = P.gaussian_wells(b, w.atoms)
+        for i, eta in enumerate(w.etas):
+            kp = B.KPoint(b, eta, 0.0, w.geom.ecut)
+            t = time.time()
+            ev = np.linalg.eigvalsh(Hm.dense_H_conv(kp, V))[:w.n_eig]
+            print("k-point", i, "L", kp.L, time.time() - t, flush=True)
+            write(f"tube32_k{i:02d}_eigs.txt", f"""
+workload {w.name} (inputs.tube_kpoints(seed=3, nk=32)), k-point {i}: eta = {eta!r}, nu = 0
+basis L = {kp.L}; lowest {w.n_eig} eigenvalues of the dense Hamiltonian, Hartree
+source: oracle.hamiltonian.dense_H_conv (convolution form of Algorithm 5) + numpy.linalg.eigh""", ev)
+    if "oracle_runs" in which:
+        oracle_runs()
+
+
+def oracle_runs():
+    """The oracle's own LOBPCG (literal Algorithm 5 products, TPA preconditioner) run to
+    convergence (every wanted residual <= 1e-6) on the tiny and tube workloads from the seeded
+    start blocks the benchmark uses; records the oracle's iteration count and, per iteration,
+    how many columns were still above the tolerance (each of those costs one H X column in the
+    next search direction).  Its wall time here is informational: the benchmark times the
+    oracle on the machine it runs on."""
+    import json
+    import platform
+    from oracle import eigensolver as E
+    out = {}
+    for name, w, seed in (("tiny", inputs.tiny(), 1234), ("tube", inputs.tube(), 1234)):
+        b = basis_of(w.geom)
+        V = P.gaussian_wells(b, w.atoms)
+        kp = B.KPoint(b, 0.0, 0.0, w.geom.ecut)
+        nb = w.n_eig + max(4, w.n_eig // 8)
+        X0 = inputs.random_block(kp.L, nb, seed)
+        active = []   # columns still above tol at each iteration (they get a new direction)
+        t = time.time()
+        th, X, it, res = E.lobpcg(lambda X: Hm.apply_H(kp, V, X), kp.ke, X0, w.n_eig, tol=1e-6, maxit=500,
+                                  callback=lambda i, theta, r: active.append(int((r > 1e-6).sum())))
+        dt = time.time() - t
+        out[name] = {"workload": w.name, "L": int(kp.L), "n_eig": int(w.n_eig), "block": int(nb),
+                     "start_seed": seed, "tol": 1e-6, "iterations": int(it),
+                     "active_per_iteration": active,
+                     "hx_columns": int(nb + sum(active)),
+                     "max_residual": float(np.max(res[: w.n_eig])), "seconds_here": round(dt, 2),
+                     "cores_here": len(os.sched_getaffinity(0)), "machine_here": platform.machine()}
+        print(name, out[name], flush=True)
+    path = os.path.join(HERE, "oracle_lobpcg_runs.json")
+    with open(path, "w") as f:
+        json.dump({"source": "tests/golden/make_golden.py oracle_runs (oracle.eigensolver.lobpcg with "
+                             "oracle.hamiltonian.apply_H, TPA preconditioner)", "runs": out}, f, indent=1)
+    print("wrote", path)
+
+
 if __name__ == "__main__":
     main(sys.argv[1:] or ["tiny", "cyclic", "tube", "tube_cyclic"])

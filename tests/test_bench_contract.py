@@ -35,25 +35,26 @@ def test_parser_defaults_and_flags():
 
 
 def test_roofline_traffic_only_for_the_captured_kernel_source(tmp_path, monkeypatch):
-    """The bench reports a kernel's DRAM traffic from its committed ncu summary only while the
-    summary's source hash matches the kernel's current source text; otherwise null."""
+    """The bench reports a kernel's DRAM traffic from the committed counter record
+    (profiles/dram_traffic.json) only while the recorded source hash matches the kernel's
+    current source text; otherwise null.  Every record names its summary, which quotes the same
+    byte count and hash."""
     sys.path.insert(0, ROOT)
     import bench
-    for phase, (summary, source, markers) in bench._TRAFFIC_SRC.items():
-        txt = open(os.path.join(ROOT, "profiles", summary)).read()
-        assert bench.kernel_source_sha(source, markers) in txt, phase   # captured on this source
-        assert bench._traffic(phase) > 0, phase
-        stale = tmp_path / "profiles"
-        stale.mkdir(exist_ok=True)
-        (stale / summary).write_text(txt.replace(bench.kernel_source_sha(source, markers), "0" * 16))
-        real_root = bench.ROOT
-        monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-        (tmp_path / "paper_2210_12252_gb300").mkdir(exist_ok=True)
-        src = tmp_path / "paper_2210_12252_gb300" / "csrc"
-        src.mkdir(exist_ok=True)
-        (src / source).write_bytes(open(os.path.join(real_root, "paper_2210_12252_gb300", "csrc", source), "rb").read())
+    rec = json.load(open(bench.TRAFFIC_JSON))["kernels"]
+    assert rec
+    for phase, r in rec.items():
+        txt = open(os.path.join(ROOT, "profiles", r["summary"])).read()
+        assert str(r["dram_bytes_per_launch"]) in txt and r["source_sha16"] in txt, phase
+        current = bench.kernel_source_sha(r["source"], r.get("markers")) == r["source_sha16"]
+        assert (bench._traffic(phase) == r["dram_bytes_per_launch"]) if current else bench._traffic(phase) is None
+    # a record whose hash no longer matches the source is not reported
+    stale = {"kernels": {p: dict(r, source_sha16="0" * 16) for p, r in rec.items()}}
+    path = tmp_path / "dram_traffic.json"
+    path.write_text(json.dumps(stale))
+    monkeypatch.setattr(bench, "TRAFFIC_JSON", str(path))
+    for phase in rec:
         assert bench._traffic(phase) is None, phase
-        monkeypatch.setattr(bench, "ROOT", real_root)
 
 
 def test_profile_commands_run_committed_files_only():
@@ -61,6 +62,8 @@ def test_profile_commands_run_committed_files_only():
     files (no scratch scripts)."""
     pdir = os.path.join(ROOT, "profiles")
     for name in os.listdir(pdir):
+        if not name.endswith((".md", ".txt")):
+            continue
         txt = open(os.path.join(pdir, name)).read()
         assert "_work/" not in txt, name
         assert "--clock-control none" in txt or "nvidia-smi" in txt, name

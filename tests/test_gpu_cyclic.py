@@ -3,8 +3,9 @@
 eigensolver against the oracle's dense eigenvalues (tests/golden/, written by
 tests/golden/make_golden.py from the oracle alone).
 
-Tolerances as for nu = 0: H X to 1e-10 relative (FP64) and 2e-6 (mixed); eigenvalues to 1e-8 Ha
-(FP64) and 1e-6 Ha (mixed).
+Tolerances as for nu = 0: H X to 1e-10 relative (FP64) and 2e-6 (mixed) per column, and every
+entry within tol |Y_ij| + floor max_i |Y_ij| (floors 1e-13 / 2e-7, as in test_gpu_hx.py);
+eigenvalues to 1e-8 Ha (FP64) and 1e-6 Ha (mixed).
 """
 import os
 
@@ -17,11 +18,14 @@ from oracle import basis as B
 from oracle import hamiltonian as Hm
 from oracle import potential as P
 from paper_2210_12252_gb300 import inputs
+from _parity import assert_entrywise
 
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
 MIXED_TOL = 2e-6
+FP64_FLOOR = 1e-13
+MIXED_FLOOR = 2e-7
 GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
@@ -85,6 +89,7 @@ def test_apply_H_fp64_tiny_each_nu(tiny, ns):
         Yref = Hm.apply_H(kp, tiny.V, X)
         Y = from_dev(tiny.ctx.apply_H(k, to_dev(X)), kp.L)
         assert rel_err(Y, Yref) < FP64_TOL, (k, kp.nu)
+        assert_entrywise(Y, Yref, FP64_TOL, FP64_FLOOR, f"tiny k{k} nu={kp.nu}")
 
 
 def test_apply_H_mixed_tiny_nu(tiny):
@@ -94,6 +99,7 @@ def test_apply_H_mixed_tiny_nu(tiny):
     Y = from_dev(tiny.ctx.apply_H(1, to_dev(X), prec="mixed"), kp.L)
     e = rel_err(Y, Yref)
     assert 1e-12 < e < MIXED_TOL
+    assert_entrywise(Y, Yref, MIXED_TOL, MIXED_FLOOR, "tiny mixed nu")
 
 
 def test_apply_H_is_hermitian_with_nu(tiny):
@@ -119,9 +125,11 @@ def test_apply_H_batched_tube_cyclic_ragged(tube):
     tube.ctx.apply_H_batched([0, 1, 2], Xs, Ys)
     for k, kp in enumerate(tube.kps):
         assert rel_err(from_dev(Ys[k], kp.L), refs[k]) < FP64_TOL, k
+        assert_entrywise(from_dev(Ys[k], kp.L), refs[k], FP64_TOL, FP64_FLOOR, f"tube c3 k{k} fp64")
     tube.ctx.apply_H_batched([0, 1, 2], Xs, Ys, prec="mixed")
     for k, kp in enumerate(tube.kps):
         assert rel_err(from_dev(Ys[k], kp.L), refs[k]) < MIXED_TOL, k
+        assert_entrywise(from_dev(Ys[k], kp.L), refs[k], MIXED_TOL, MIXED_FLOOR, f"tube c3 k{k} mixed")
 
 
 def test_solve_tiny_cyclic_fp64_matches_dense_oracle(tiny, hwmod):

@@ -11,6 +11,7 @@ torch = pytest.importorskip("torch")
 from oracle import basis as B
 from oracle import density as D
 from paper_2210_12252_gb300 import inputs
+from _parity import assert_entrywise
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +57,8 @@ def test_tiny_two_kpoints_match_oracle(hwmod, prec, bar):
     rho = ctx.density([0, 1], list(Xs), occ, wk, prec=prec).cpu().numpy()
     ref = D.density(kps, list(Qs), list(occ), list(wk))
     assert np.abs(rho - ref).max() <= bar * np.abs(ref).max()
+    # every grid value on its own (the density is smallest near the wall)
+    assert_entrywise(rho.ravel(), ref.ravel(), bar, bar * (1e-2 if prec == "fp64" else 1e-1), f"tiny {prec}")
     assert abs(D.charge(b, rho) - 2 * (wk[:, None] * occ).sum()) < (1e-9 if prec == "fp64" else 1e-5)
     ctx.close()
 
@@ -69,6 +72,7 @@ def test_tube_converged_states_match_oracle(hwmod):
     rho = ctx.density([0], [X], occ, [1.0]).cpu().numpy()
     ref = D.density(kps, [X.cpu().numpy().T], list(occ), [1.0])
     assert np.abs(rho - ref).max() <= 1e-11 * np.abs(ref).max()
+    assert_entrywise(rho.ravel(), ref.ravel(), 1e-11, 1e-13, "tube fp64")
     assert abs(D.charge(b, rho) - 32.0) < 1e-6
     ctx.close()
 

@@ -13,6 +13,7 @@ torch = pytest.importorskip("torch")
 from oracle import basis as B
 from oracle import gradient as Gr
 from paper_2210_12252_gb300 import inputs
+from _parity import assert_entrywise
 
 pytestmark = pytest.mark.gpu
 
@@ -58,6 +59,8 @@ def check(hwmod, w, k, ns, seed, precs=("fp64", "mixed"), ld_pad=0):
                 ref = refs[c][comp]
                 err = np.abs(D[c, comp] - ref).max() / np.abs(ref).max()
                 assert err < tol, (prec, c, comp, err)
+                assert_entrywise(D[c, comp].ravel(), ref.ravel(), tol, tol * 1e-1 if prec == "mixed" else tol * 1e-3,
+                                 f"gradient {prec} column {c} component {comp}")
                 if prec == "mixed":
                     assert err > 1e-13   # really ran in reduced precision
     ctx.close()

@@ -2,7 +2,11 @@
 
 Tolerances: the FP64 path must match Algorithm 5 of the oracle to 1e-10 relative (per column,
 in the 2-norm); the mixed path (FP32 transforms, FP64 diagonal) to 2e-6 relative, the FP32
-rounding of O(100) accumulated terms.
+rounding of O(100) accumulated terms.  Every entry is bounded too (tests/_parity.py):
+|dY_ij| <= tol |Y_ij| + floor max_i |Y_ij| with floor 1e-13 (FP64: a few ulps of the column's
+largest entry) and 2e-7 (mixed: the FP32 transforms leave absolute errors of a few 1e-8 of the
+column's largest entry, measured by an FP32 emulation of Algorithms 1-4 on the tube; the
+diagonal term, the largest part of most entries, is FP64).
 """
 import numpy as np
 import pytest
@@ -14,11 +18,14 @@ from oracle import eigensolver as E
 from oracle import hamiltonian as Hm
 from oracle import potential as P
 from paper_2210_12252_gb300 import inputs
+from _parity import assert_entrywise
 
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
 MIXED_TOL = 2e-6
+FP64_FLOOR = 1e-13
+MIXED_FLOOR = 2e-7
 
 
 @pytest.fixture(scope="module")
@@ -83,6 +90,7 @@ def test_apply_H_fp64_tiny(tiny, ns):
     Yref = Hm.apply_H(kp, tiny.V, X)
     Y = from_dev(tiny.ctx.apply_H(0, to_dev(X)), kp.L)
     assert rel_err(Y, Yref) < FP64_TOL
+    assert_entrywise(Y, Yref, FP64_TOL, FP64_FLOOR, "tiny fp64")
 
 
 def test_apply_H_fp64_tube_ragged_with_padding(tube):
@@ -95,6 +103,7 @@ def test_apply_H_fp64_tube_ragged_with_padding(tube):
     Y = from_dev(Yd, kp.L)
     Yref = Hm.apply_H(kp, tube.V, X)
     assert rel_err(Y, Yref) < FP64_TOL
+    assert_entrywise(Y, Yref, FP64_TOL, FP64_FLOOR, "tube fp64")
     # padding rows untouched
     assert torch.all(Yd[:, kp.L:] == complex(7.0, -3.0))
 
@@ -106,6 +115,7 @@ def test_apply_H_mixed_tube(tube):
     Y = from_dev(tube.ctx.apply_H(0, to_dev(X), prec="mixed"), kp.L)
     e = rel_err(Y, Yref)
     assert e < MIXED_TOL and e > 1e-12   # really ran in reduced precision
+    assert_entrywise(Y, Yref, MIXED_TOL, MIXED_FLOOR, "tube mixed")
 
 
 def test_apply_H_is_hermitian_on_device(tiny):
@@ -130,6 +140,7 @@ def test_apply_H_batched_uneven_kpoints(hwmod):
     case.ctx.apply_H_batched(list(range(len(case.kps))), Xs, Ys)
     for b, kp in enumerate(case.kps):
         assert rel_err(from_dev(Ys[b], kp.L), refs[b]) < FP64_TOL
+        assert_entrywise(from_dev(Ys[b], kp.L), refs[b], FP64_TOL, FP64_FLOOR, f"batched k{b}")
 
 
 def test_tpa_preconditioner_matches_oracle(tube):
@@ -138,6 +149,7 @@ def test_tpa_preconditioner_matches_oracle(tube):
     Z = from_dev(tube.ctx.apply_precond(0, to_dev(R)), kp.L)
     Zref = E.tpa(kp.ke, R)
     assert rel_err(Z, Zref) < 1e-13
+    assert_entrywise(Z, Zref, 1e-13, 1e-15, "tpa")
 
 
 def test_set_potential_from_device_matches_host_build(tube):
@@ -146,7 +158,9 @@ def test_set_potential_from_device_matches_host_build(tube):
     tube.ctx.set_potential(V)       # oracle-built V from device memory
     X = inputs.random_block(kp.L, 2, 5)
     Y = from_dev(tube.ctx.apply_H(0, to_dev(X)), kp.L)
-    assert rel_err(Y, Hm.apply_H(kp, tube.V, X)) < FP64_TOL
+    Yref = Hm.apply_H(kp, tube.V, X)
+    assert rel_err(Y, Yref) < FP64_TOL
+    assert_entrywise(Y, Yref, FP64_TOL, FP64_FLOOR, "V from device")
     tube.ctx.build_potential(tube.w.atoms)   # restore the library-built V
 
 
@@ -163,5 +177,6 @@ def test_apply_H_mixed_tube_slab_variants_agree(tube, hwmod):
         tube.ctx.set_option(hwmod.HW_OPT_SLAB_KERNEL, v)
         out[v] = from_dev(tube.ctx.apply_H(0, Xd, prec="mixed"), kp.L)
         assert rel_err(out[v], Yref) < MIXED_TOL
+        assert_entrywise(out[v], Yref, MIXED_TOL, MIXED_FLOOR, f"slab variant {v}")
     tube.ctx.set_option(hwmod.HW_OPT_SLAB_KERNEL, 1)
     assert rel_err(out[1], out[0]) < MIXED_TOL

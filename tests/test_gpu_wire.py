@@ -20,6 +20,7 @@ from oracle import gradient as Gr
 from oracle import hamiltonian as Hm
 from oracle import potential as P
 from paper_2210_12252_gb300 import inputs
+from _parity import assert_entrywise
 
 pytestmark = pytest.mark.gpu
 N_ATOMS = 20
@@ -65,9 +66,11 @@ def test_wire_apply_H_sampled_columns(wire):
     Xd = to_dev(X)
     Y64 = ctx.apply_H(0, Xd).cpu().numpy().T
     assert rel_err(Y64, Yref) < 1e-10
+    assert_entrywise(Y64, Yref, 1e-10, 1e-13, "wire fp64")
     Y32 = ctx.apply_H(0, Xd, prec="mixed").cpu().numpy().T
     e = rel_err(Y32, Yref)
     assert 1e-12 < e < 2e-6
+    assert_entrywise(Y32, Yref, 2e-6, 2e-7, "wire mixed")
 
 
 def test_wire_density_mixed_two_states(wire):
@@ -78,6 +81,7 @@ def test_wire_density_mixed_two_states(wire):
     rho = ctx.density([0], [to_dev(Q)], occ, [1.0], prec="mixed").cpu().numpy()
     ref = D.density([kp], [Q], occ, [1.0])
     assert np.abs(rho - ref).max() < 2e-6 * np.abs(ref).max()
+    assert_entrywise(rho.ravel(), ref.ravel(), 2e-6, 2e-7, "wire density mixed")
 
 
 def test_wire_gradient_fp64_one_column(wire):
@@ -87,3 +91,23 @@ def test_wire_gradient_fp64_one_column(wire):
     ref = Gr.gradient(kp, X[:, 0])
     for comp in range(3):
         assert np.abs(Dd[0, comp] - ref[comp]).max() < 1e-10 * np.abs(ref[comp]).max()
+        assert_entrywise(Dd[0, comp].ravel(), ref[comp].ravel(), 1e-10, 1e-13, f"wire gradient {comp}")
+
+
+def test_wire_potential_all_300_wells_at_sampled_points(hwmod):
+    """The library's host-built potential of the nanowire workload with all 300 wells, against
+    the oracle's image sum at 20,000 seeded grid points (the oracle's full-grid build of 300
+    wells takes minutes; the image sum is the same at each point)."""
+    w = inputs.wire(nk=1)
+    g = w.geom
+    assert len(w.atoms) == 300
+    ctx = hwmod.Context(0)
+    ctx.setup_basis(g, w.etas[:1])
+    V = ctx.build_potential(w.atoms).reshape(g.Nth1, g.Nth2, g.Nr)
+    b = B.Basis(g.R, g.tau, g.alpha, g.Nr, g.Nth1, g.Nth2, g.ncyc, g.oversample)
+    rng = np.random.default_rng(301)
+    i, j, p = (rng.integers(0, n, 20000) for n in (g.Nth1, g.Nth2, g.Nr))
+    ref = P.gaussian_wells_at(b, w.atoms, i, j, p)
+    assert np.abs(ref).max() > 1.0                    # the sample sees the wells
+    assert_entrywise(V[i, j, p], ref, 1e-12, 1e-13, "300-well potential")
+    ctx.close()

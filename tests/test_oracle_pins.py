@@ -345,6 +345,31 @@ def test_tpa_formula_values():
     assert abs(E.tpa(np.array([3.0]), np.ones((1, 1)))[0, 0] - 65 / 81) < 1e-15
 
 
+def test_tpa_weights_the_residual_kinetic_energy_by_r_squared():
+    """Reading 9 of the TPA (Sec. "Eigensolvers and Preconditioning"): KE_res is the
+    |r_i|^2-weighted mean of KE_i.  Worked by hand for KE = (1, 2, 4):
+      column 0, |r|^2 = (2, 1, 1): KE_res = (2 + 2 + 4) / 4 = 2, so g = (1/2, 1, 2) and
+        P(1/2) = 27 + 9 + 3 + 1 = 40,         16 g^4 = 1    -> K = 40/41
+        P(1)   = 27 + 18 + 12 + 8 = 65,        16 g^4 = 16   -> K = 65/81
+        P(2)   = 27 + 36 + 48 + 64 = 175,      16 g^4 = 256  -> K = 175/431
+      column 1, r = (0, 0, 1): KE_res = 4, g = (1/4, 1/2, 1): only the third entry is
+        nonzero, scaled by 65/81.
+    A |r|-weighted mean gives KE_res = (sqrt2 + 2 + 4)/(sqrt2 + 2) = 2.17 for column 0, an
+    unweighted one 7/3; both move every scale of column 0 by more than 1e-3."""
+    ke = np.array([1.0, 2.0, 4.0])
+    r0 = np.array([np.sqrt(2.0) * np.exp(0.25j * np.pi), -1.0, 1j])
+    r1 = np.array([0.0, 0.0, 0.5 - 0.5j])
+    Z = E.tpa(ke, np.stack([r0, r1], axis=1))
+    np.testing.assert_allclose(Z[:, 0], np.array([40 / 41, 65 / 81, 175 / 431]) * r0, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(Z[:, 1], np.array([0.0, 0.0, 65 / 81]) * r1, rtol=1e-14, atol=0)
+    # the other two readings of "kinetic energy of the residual vector" fail this pin
+    for w in (np.abs(r0), np.ones(3)):
+        ke_res = (ke * w).sum() / w.sum()
+        g = ke / ke_res
+        Pg = 27 + 18 * g + 12 * g ** 2 + 8 * g ** 3
+        assert np.abs(Pg / (Pg + 16 * g ** 4) - np.array([40 / 41, 65 / 81, 175 / 431])).max() > 1e-3
+
+
 def test_lobpcg_matches_direct_diagonalisation(tiny_case):
     w, b, V = tiny_case
     kp = B.KPoint(b, 0.0, 0.0, 0.0)
@@ -354,3 +379,13 @@ def test_lobpcg_matches_direct_diagonalisation(tiny_case):
     th, X, it, res = E.lobpcg(lambda X: H @ X, kp.ke, X0, 8, tol=1e-9)
     assert np.abs(th - ev[:8]).max() < 1e-12
     assert res[:8].max() <= 1e-9
+
+
+def test_potential_at_points_equals_the_grid_potential(tiny_case):
+    """gaussian_wells_at (used to check the nanowire's 300-well potential at sampled points) is
+    the same image sum as the full-grid gaussian_wells."""
+    w, b, V = tiny_case
+    g = np.random.default_rng(3)
+    i, j, p = (g.integers(0, n, 200) for n in (b.Nth1, b.Nth2, b.Nr))
+    np.testing.assert_allclose(P.gaussian_wells_at(b, w.atoms, i, j, p), V[i, j, p], rtol=1e-13,
+                               atol=1e-15 * np.abs(V).max())
