@@ -44,6 +44,9 @@ def parse(argv=None):
                     help="eigensolver of the chosen form: Chebyshev-filtered FP32 phase then the "
                          "LOBPCG mixed end phase (chfsi), or LOBPCG throughout")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tc-gemm", type=int, default=None, choices=[0, 1, 2],
+                    help="block products of the eigensolver: the library default (unset), 0 cuBLAS, "
+                         "1 tensor-core kernel over the basis dimension, 2 tensor-core kernel for all")
     ap.add_argument("--profile", action="store_true", help="per-phase device times to stderr")
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--kernel-case", default=None, choices=["hx_fp64", "hx_mixed", "solve_mixed"],
@@ -223,6 +226,8 @@ def ours_main(args):
     stream = torch.cuda.Stream(dev)
     w = inputs.tube()
     ctx = hw.Context(local, stream=stream)
+    if args.tc_gemm is not None:
+        ctx.set_option(hw.HW_OPT_TC_GEMM, args.tc_gemm)
     L = int(ctx.setup_basis(w.geom, w.etas)[0])
     ctx.build_potential(w.atoms)
     n_eig = w.n_eig

@@ -302,6 +302,23 @@ hw_status hw_gradient(hw_ctx* ctx, int k, const double* X, int ns, int64_t ld, d
 hw_status hw_gram(hw_ctx* ctx, int m, int n, int K, int nprob, const double* A, int64_t lda, int64_t sA,
                   const double* B, int64_t ldb, int64_t sB, double* C, int64_t ldc, int64_t sC);
 
+/* Block product of the eigensolver (Sec. "Eigensolvers and Preconditioning": Gram matrices,
+ * Rayleigh-Ritz projections, block updates) on the tensor cores: for b < batch,
+ *   C_b = alpha op(A_b) B_b + beta C_b,   op(A) = A^H (transA = 1, A_b: k x m) or A (0, m x k),
+ * B_b: k x n, C_b: m x n; complex128, column-major device blocks with leading dimensions lda,
+ * ldb, ldc and batch strides sA, sB, sC (complex elements).  Every real row of op(A) and of B
+ * (complex entries as interleaved real pairs) is scaled by a power of two and cut into BF16
+ * integer digits; the digit products are summed by tcgen05 MMAs in TMEM.  cls 0 (FP64 class):
+ * 8 digits of 7 bits, exact group sums added into a 64-bit fixed point, error below
+ * 2^-46 max|op(A)_i,:| max|B_:,j| per reduction element (tighter than an FP64 GEMM's bound for
+ * vectors without a wide dynamic range); cls 1 (FP32 class): 3 digits of 8 bits, FP32 sums,
+ * about 2^-24 of the same scale.  Deterministic (fixed-order split reduction).  The library
+ * grows a workspace for the digit planes (up to 1 GiB; larger batches run in chunks).
+ * Asynchronous on the context's stream.  HW_EINVAL on bad sizes (n <= 4096, m, k <= 2^20). */
+hw_status hw_block_product(hw_ctx* ctx, int transA, int m, int n, int k, double alpha, const double* A,
+                           int64_t lda, int64_t sA, const double* B, int64_t ldb, int64_t sB, double beta,
+                           double* C, int64_t ldc, int64_t sC, int batch, int cls);
+
 /* Autotune the H X kernels' tile shapes for blocks of ns columns at k-point k: the slab
  * kernel's theta2 chunk and the number of columns per pass are timed (CUDA events, best of
  * 2 after a warm-up) for every candidate in FP64 and FP32 and the fastest are kept for later
@@ -358,9 +375,15 @@ typedef enum {
                                iteration cheaper) and switches them on for good once an
                                iteration fails to halve the largest wanted residual; 0: with
                                them from the start. */
-  HW_OPT_WINDOW = 11        /* hw_solve_eigs: largest number of eigenpairs one block solves,
+  HW_OPT_WINDOW = 11,       /* hw_solve_eigs: largest number of eigenpairs one block solves,
                                1..100; 0 (default) means 80.  More eigenpairs than this are
                                solved in consecutive windows of equal size (see hw_solve_eigs). */
+  HW_OPT_TC_GEMM = 12       /* the eigensolver's block products: 1 (default) the tensor-core
+                               kernel of hw_block_product (FP64 class in the FP64 phases, FP32
+                               class in the FP32-product phase) for every product with an extent
+                               over the basis dimension (m or k >= 1024), cuBLAS for the small
+                               dense products of the Rayleigh-Ritz step; 2 the tensor-core kernel
+                               for every product; 0 cuBLAS (ZGEMM, or CGEMM on FP32 copies). */
 } hw_option;
 /* Set an option (HW_EINVAL for an unknown option, a read-only one or a bad value). */
 hw_status hw_set_option(hw_ctx* ctx, int option, int value);

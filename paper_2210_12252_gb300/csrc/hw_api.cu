@@ -167,6 +167,7 @@ void hw_destroy(hw_ctx* ctx) {
     mlp_free(ctx);
     if (ctx->dflag) cudaFree(ctx->dflag);
     if (ctx->dens_w) cudaFree(ctx->dens_w);
+    zgemm_free(ctx->zg);
     if (ctx->cublas) cublasDestroy(ctx->cublas);
   }
   delete ctx;
@@ -586,6 +587,11 @@ hw_status hw_set_option(hw_ctx* ctx, int option, int value) {
     ctx->window = value;
     return HW_OK;
   }
+  if (option == HW_OPT_TC_GEMM) {
+    if (value < 0 || value > 2) return hw_fail(ctx, HW_EINVAL, "block-product option 0, 1 or 2");
+    ctx->tc_gemm = value;
+    return HW_OK;
+  }
   return hw_fail(ctx, HW_EINVAL, "unknown or read-only option");
 }
 
@@ -603,6 +609,7 @@ hw_status hw_get_option(hw_ctx* ctx, int option, long long* value) {
   if (option == HW_OPT_TAIL_NO_P) { *value = ctx->tail_no_p; return HW_OK; }
   if (option == HW_OPT_SLAB_KERNEL) { *value = ctx->slab_r16; return HW_OK; }
   if (option == HW_OPT_WINDOW) { *value = ctx->window; return HW_OK; }
+  if (option == HW_OPT_TC_GEMM) { *value = ctx->tc_gemm; return HW_OK; }
   return hw_fail(ctx, HW_EINVAL, "unknown option");
 }
 

@@ -66,6 +66,7 @@ struct ChebStep {
 
 struct LobpcgWork;
 struct MlpState;
+struct ZgemmWork;
 
 // Per-phase timing with CUDA events on the context's stream (enabled by hw_profile).
 struct Prof {
@@ -97,6 +98,8 @@ struct hw_ctx {
   hw::Workspace ws;
   hw::LobpcgWork* lw = nullptr;
   hw::MlpState* mlp = nullptr;
+  hw::ZgemmWork* zg = nullptr;   // workspace of the tensor-core block products
+  int tc_gemm = 1;             // HW_OPT_TC_GEMM
   int* dflag = nullptr;        // device status word for bounded waits
   int64_t launches = 0;        // kernels of this library launched on the stream
   double* dens_w = nullptr;    // column weights of hw_density (grown when needed)
@@ -147,6 +150,13 @@ cudaError_t hx_autotune(hw_ctx* ctx, int k, int ns, std::vector<float>& log);
 template <typename T>
 cudaError_t launch_hx_into(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, void* gbuf, void* hbuf, int cols);
 cudaError_t launch_tpa(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld);
+// C = alpha op(A) B + beta C on the tensor cores (hw_zgemm.cu): cls 0 FP64 class, 1 FP32 class
+cudaError_t zgemm_tc(ZgemmWork*& w, cudaStream_t st, int cls, bool transA, int m, int n, int k, double alpha,
+                     const double2* A, int64_t lda, int64_t sA, const double2* B, int64_t ldb, int64_t sB,
+                     double beta, double2* C, int64_t ldc, int64_t sC, int batch, int* launches);
+void zgemm_free(ZgemmWork*& w);
+int zgemm_status(ZgemmWork* w, cudaStream_t st, bool reset);
+int* zgemm_status_ptr(ZgemmWork* w);
 cudaError_t launch_precond_learned(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld,
                                    const double* const* ritz);
 cudaError_t mlp_refresh_potential(hw_ctx* ctx);

@@ -424,6 +424,16 @@ struct Gemm {
       if (beta == 1.0) return;
     }
     ProfScope ps(ctx, HW_PH_GEMM);
+    // the tensor-core kernel: products over the basis dimension (or all, option 2)
+    if (ctx->tc_gemm && k >= 1 && tb == CUBLAS_OP_N && (ta == CUBLAS_OP_C || ta == CUBLAS_OP_N) &&
+        (ctx->tc_gemm == 2 || (ta == CUBLAS_OP_C ? k : m) >= 1024) && n <= 4096) {
+      int nl = 0;
+      const cudaError_t e = zgemm_tc(ctx->zg, ctx->stream, lowp ? 1 : 0, ta == CUBLAS_OP_C, m, n, k, alpha, A, lda,
+                                     sA, B, ldb, sB, beta, C, ldc, sC, batch, &nl);
+      ctx->launches += nl;
+      if (e != cudaSuccess && ce == cudaSuccess) ce = e;
+      return;
+    }
     if (gram && lowp && ta == CUBLAS_OP_C && tb == CUBLAS_OP_N && k >= 256 &&
         gram_work_bytes(m, n, k, batch) <= gbytes) {
       int nl = 0;
@@ -1040,11 +1050,16 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     }
     cudaMemcpyAsync(resh.data(), w->res, resh.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(thh.data(), w->theta, thh.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
-    int dstat = 0;
+    int dstat = 0, zstat = 0;
     cudaMemcpyAsync(&dstat, w->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ctx->zg) cudaMemcpyAsync(&zstat, zgemm_status_ptr(ctx->zg), sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
     if (dstat == HW_ETIMEOUT) return hw_fail(ctx, HW_ETIMEOUT, "dense eigensolver barrier timed out");
+    if (zstat == HW_ETIMEOUT) {
+      zgemm_status(ctx->zg, st, true);
+      return hw_fail(ctx, HW_ETIMEOUT, "a wait in the tensor-core block product timed out");
+    }
     if (gemm.st != CUBLAS_STATUS_SUCCESS) return hw_fail(ctx, HW_ECUDA, "cuBLAS failure");
     if (gemm.ce != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("Gram kernel: ") + cudaGetErrorString(gemm.ce));
     if (trace) {
@@ -1569,11 +1584,16 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     }
     cudaMemcpyAsync(resh.data(), w->res, resh.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(thh.data(), w->theta, thh.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
-    int dstat = 0;
+    int dstat = 0, zstat = 0;
     cudaMemcpyAsync(&dstat, w->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ctx->zg) cudaMemcpyAsync(&zstat, zgemm_status_ptr(ctx->zg), sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("eigensolver: ") + cudaGetErrorString(e));
     if (dstat == HW_ETIMEOUT) return hw_fail(ctx, HW_ETIMEOUT, "dense eigensolver barrier timed out");
+    if (zstat == HW_ETIMEOUT) {
+      zgemm_status(ctx->zg, st, true);
+      return hw_fail(ctx, HW_ETIMEOUT, "a wait in the tensor-core block product timed out");
+    }
     if (gemm.st != CUBLAS_STATUS_SUCCESS) return hw_fail(ctx, HW_ECUDA, "cuBLAS failure");
     if (gemm.ce != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("Gram kernel: ") + cudaGetErrorString(gemm.ce));
     double maxres = 0.0;

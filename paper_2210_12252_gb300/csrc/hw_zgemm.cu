@@ -1,0 +1,1067 @@
+// Complex block products of the eigensolver on the tensor cores (tcgen05, TMA, TMEM).
+//
+// The LOBPCG / Chebyshev steps of Sec. "Eigensolvers and Preconditioning" need, per iteration,
+// products over the basis dimension L (Gram matrices S^H S and S^H H S, projections, the block
+// updates [X P] = S Z): C = alpha op(A) B + beta C with op(A) = A^H (the reduction runs over L)
+// or op(A) = A (the rows of C run over L), complex FP64 operands.  This GPU's FP64 rate is 1/64
+// of its FP32 rate, while its tensor cores run at ~1-2 PFLOP/s; the products are computed there
+// from split operands, in two accuracy classes:
+//
+// FP64 class (the FP64 phases): "digit planes" in the manner of Ozaki et al.  Every real row x of
+//   an operand (complex entries as interleaved real pairs) is scaled by a power of two 2^-e so
+//   that |x| < 1/2 and cut into S = 8 balanced base-2^7 digits,
+//   x 2^-e = sum_{q=1..8} d_q 2^{-7 q} + eps, |d_q| <= 64, |eps| <= 2^-57;
+//   the digits are small integers, exact in BF16.  A product sum_k x_k y_k is the sum over digit
+//   pairs (p, q) with p + q <= 9 of 2^{-7 (p+q)} sum_k d_p,k d'_q,k; the pairs with p + q = t
+//   form "group" t.  The tensor cores sum a group's integer products in FP32, exactly while the
+//   sum stays below 2^24: every group's sum is drained from TMEM every 512 reduction elements
+//   and added exactly to a 64-bit fixed-point accumulator.
+// FP32 class (the FP32-product phase of the mixed form): "3 x TF32".  Every real entry x is
+//   split as x = hi + lo + r with hi, lo TF32 numbers (hi = x rounded to 11 significant bits,
+//   lo = x - hi rounded likewise; |r| <= 2^-22 |x|), and sum_k x_k y_k is taken as
+//   hi hi' + hi lo' + lo hi' by three tcgen05 TF32 MMAs into one FP32 accumulator: per-entry
+//   exponents, the accuracy of an FP32 product.
+//
+// Real forms (K = 2 x complex length, interleaved re/im):
+//   op = ^H : D[i][j]     = sum_l a_il^re b_lj^re + a_il^im b_lj^im     = Re (A^H B)_ij
+//             D[i][n + j] = sum_l a_il^re b_lj^im - a_il^im b_lj^re     = Im (A^H B)_ij
+//             A-side rows: columns of A as (re, im); B-side rows j: (re, im), n + j: (im, -re)
+//   op = N  : D[l][j]     = sum_c a_lc^re b_cj^re - a_lc^im b_cj^im     = Re (A B)_lj
+//             D[l][n + j] = sum_c a_lc^re b_cj^im + a_lc^im b_cj^re     = Im (A B)_lj
+//             A-side rows: rows of A as (re, im); B-side rows j: (re, -im), n + j: (im, re)
+//
+// Kernels: k_colmax / k_rowmax (FP64 class: the rows' largest magnitudes), k_split_cols /
+// k_split_rows (the split planes [batch][plane][row][Kp], K contiguous, zero-padded to Kp),
+// k_mma_digits / k_mma_tf32 (one CTA per 128 x BN output tile and K range: a TMA producer warp,
+// an MMA warp issuing tcgen05.mma from shared memory into TMEM, eight epilogue warps draining
+// TMEM), writing per-split partial sums [split][column][row]; k_zgemm_out adds the splits in a
+// fixed order (deterministic) and applies the scales, alpha and beta.
+// Every wait on an mbarrier is bounded; a wait that runs out sets HW_ETIMEOUT in the status word
+// and the CTA leaves after its in-flight copies and tensor-core work have completed (or their
+// own bounded waits ran out).
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+#include <string>
+
+#include "hw_common.cuh"
+#include "hw_ctx.h"
+
+namespace hw {
+
+// ----------------------------------------------------------------------------- configuration
+template <int CLS> struct ZCfg;
+template <> struct ZCfg<0> {      // FP64 class: BF16 digit planes, exact group sums
+  static constexpr int S = 8, BITS = 7, BN = 64, SWZ = 64, STAGES = 2, WINDOW = 512;
+};
+constexpr int TF_PLANES = 2, TF_BN_MAX = 256, TF_STAGES = 2;   // FP32 class: TF32 hi / lo planes
+constexpr int ZG_BM = 128;          // output rows per CTA (TMEM lanes)
+constexpr int ZG_KALIGN = 64;       // Kp: reduction length padded to a multiple of this
+// fixed point of the FP64 class: unit 2^-U with U = 61 - ceil(log2 Kp) (at most 56): the sum of
+// Kp products of two numbers below 1/2 stays below 2^59 units, inside a signed 64-bit integer
+inline int zg_fix_unit(int64_t Kp) {
+  int l = 0;
+  while ((int64_t(1) << l) < Kp) ++l;
+  return std::min(56, 61 - l);
+}
+constexpr int ZG_THREADS = 320;     // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (2 per TMEM lane quadrant)
+constexpr long ZG_SPIN = 1L << 22;  // polls (with ~64 ns sleeps) before a wait gives up
+
+template <int CLS>
+constexpr size_t zg_stage_bytes() {
+  return (size_t)ZCfg<CLS>::S * (ZG_BM + ZCfg<CLS>::BN) * ZCfg<CLS>::SWZ;
+}
+template <int CLS>
+constexpr size_t zg_smem_bytes() {
+  return (size_t)ZCfg<CLS>::STAGES * zg_stage_bytes<CLS>() + 1024;   // + alignment slack
+}
+__host__ __device__ constexpr size_t tf_stage_bytes() { return (size_t)TF_PLANES * (ZG_BM + TF_BN_MAX) * 128; }
+__host__ __device__ constexpr size_t tf_smem_bytes() { return (size_t)TF_STAGES * tf_stage_bytes() + 1024; }
+
+// ----------------------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+// true once the phase of the given parity has completed; false after ZG_SPIN polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  const uint32_t a = smem_u32(b);
+  for (long i = 0; i < ZG_SPIN; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    __nanosleep(64);
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+// shared-memory matrix descriptor: K-major operand tile, rows of SWZ bytes swizzled in 8-row
+// atoms (SWZ = 128 or 64), consecutive 8-row atoms 8 * SWZ bytes apart
+template <int SWZ>
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)((8 * SWZ) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)(SWZ == 128 ? 2 : 4) << 61;
+  return d;
+}
+// instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(ZG_BM >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(accum));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// ----------------------------------------------------------------------------- digit planes
+// |x| as the ordered bit pattern of the magnitude (max of non-negative doubles = max of bits);
+// zero for subnormals and zero (they take no part in the row scale)
+__device__ __forceinline__ unsigned long long mag_bits(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  return (u >> 52) == 0 ? 0ull : u;
+}
+// the row exponent e with max|x| 2^-e < 1/2 (e = E + 2 for max|x| in [2^E, 2^(E+1)))
+__device__ __forceinline__ int row_exponent(unsigned long long mb) {
+  return mb == 0 ? 0 : (int)(mb >> 52) - 1023 + 2;
+}
+// x 2^(bits s - e) rounded to the nearest integer (ties to even), exactly, by integer arithmetic
+// on the FP64 encoding; |result| < 2^(bits s - 1) because |x| 2^-e < 1/2
+template <int BITS, int S>
+__device__ __forceinline__ long long fixed_of(double x, int e) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((u >> 52) & 0x7FF);
+  if (E == 0) return 0;                                  // zero / subnormal
+  const long long m = (long long)((u & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+  const int sh = E - 1075 - e + BITS * S;                // value = m 2^sh
+  long long N;
+  if (sh >= 0) {
+    N = m << sh;
+  } else {
+    const int r = -sh;
+    if (r > 62) {
+      N = 0;
+    } else {
+      const long long q = m >> r, rem = m - (q << r), half = 1LL << (r - 1);
+      N = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+    }
+  }
+  return (long long)(u >> 63) ? -N : N;
+}
+// balanced base-2^BITS digits of N, most significant first: d[0] 2^(BITS (S-1)) + ... + d[S-1]
+template <int BITS, int S>
+__device__ __forceinline__ void digits_of(long long N, float (&d)[S]) {
+  constexpr long long B = 1LL << BITS, H = B >> 1;
+#pragma unroll
+  for (int q = S - 1; q >= 0; --q) {
+    const long long r = ((N + H) & (B - 1)) - H;
+    d[q] = (float)r;
+    N = (N - r) >> BITS;
+  }
+  d[0] += (float)(N << BITS);   // N is zero here for |x| 2^-e < 1/2; kept for exactness
+}
+
+// TF32 rounding of an FP32 number: 10 explicit mantissa bits, to nearest (ties to even); the
+// tensor core reads the upper 19 bits of the container, which are then exact
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t u = __float_as_uint(x);
+  if ((u & 0x7F800000u) != 0x7F800000u) u = (u + 0x0FFFu + ((u >> 13) & 1u)) & 0xFFFFE000u;
+  return __uint_as_float(u);
+}
+// x = hi + lo + r, |r| <= 2^-22 |x| (FP64 -> FP32 by bit operations, one FP64 subtraction)
+__device__ __forceinline__ void tf32_split(double x, float& hi, float& lo) {
+  hi = tf32_rn(d2f(x));
+  lo = tf32_rn(d2f(x - f2d(hi)));
+}
+
+// ----------------------------------------------------------------------------- split planes
+struct SplitArgs {
+  const double2* X;      // source matrix, column-major complex, leading dimension ld
+  int64_t ld, sX;        // leading dimension, batch stride (complex elements)
+  int rows, cols;        // source shape (complex rows x columns)
+  int mode;              // column sides: 0 out row c = (re, im) of column c; 1 rows c, cols+c =
+                         // (re, im), (im, -re); 2 rows c, cols+c = (re, -im), (im, re)
+                         // (row side: out row l = row l of X as (re, im))
+  int nrow_out;          // rows of each output plane
+  int64_t Kp;            // padded reduction length (real)
+  void* P;               // planes [batch][plane][nrow_out][Kp] (BF16 digits or TF32 in FP32)
+  const unsigned long long* mb;   // FP64 class: largest magnitude bits per source column / row
+  int* ex;               // FP64 class: the exponents used, per output scale row [batch][cols or rows]
+};
+
+// |x| bits of every column's entries -> atomicMax into mb[batch][col]; grid (segments, cols, batch)
+__global__ void k_colmax(const double2* X, int64_t ld, int64_t sX, int rows, int cols, unsigned long long* mb) {
+  const int c = blockIdx.y, b = blockIdx.z;
+  const double2* x = X + (size_t)b * sX + (size_t)c * ld;
+  unsigned long long m = 0;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < rows; l += gridDim.x * blockDim.x) {
+    const double2 v = x[l];
+    m = max(m, max(mag_bits(v.x), mag_bits(v.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(mb + (size_t)b * cols + c, m);
+}
+
+// |x| bits of every row's entries (rows of a column-major matrix); grid (row blocks, batch)
+__global__ void k_rowmax(const double2* X, int64_t ld, int64_t sX, int rows, int cols, unsigned long long* mb) {
+  const int b = blockIdx.y;
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= rows) return;
+  const double2* x = X + (size_t)b * sX + l;
+  unsigned long long m = 0;
+  for (int c = 0; c < cols; ++c) {
+    const double2 v = x[(size_t)c * ld];
+    m = max(m, max(mag_bits(v.x), mag_bits(v.y)));
+  }
+  mb[(size_t)b * rows + l] = m;
+}
+
+// Column sides: one thread per complex entry (grid (entry blocks over Kp/2, cols, batch)).
+// CLS 0 writes S BF16 digit planes with the column's exponent, CLS 1 the TF32 hi / lo planes.
+template <int CLS>
+__global__ void __launch_bounds__(256) k_split_cols(SplitArgs a) {
+  const int c = blockIdx.y, b = blockIdx.z;
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= (int)(a.Kp >> 1)) return;
+  double2 v = make_double2(0.0, 0.0);
+  if (l < a.rows) v = a.X[(size_t)b * a.sX + (size_t)c * a.ld + l];
+  const size_t plane = (size_t)a.nrow_out * a.Kp;
+  const size_t r0 = (size_t)c * a.Kp, r1 = (size_t)(a.cols + c) * a.Kp;
+  if constexpr (CLS == 0) {
+    constexpr int S = ZCfg<0>::S, BITS = ZCfg<0>::BITS;
+    const int e = row_exponent(a.mb[(size_t)b * a.cols + c]);
+    if (l == 0) a.ex[(size_t)b * a.cols + c] = e;
+    float dr[S], di[S];
+    digits_of<BITS, S>(fixed_of<BITS, S>(v.x, e), dr);
+    digits_of<BITS, S>(fixed_of<BITS, S>(v.y, e), di);
+    __nv_bfloat16* P = reinterpret_cast<__nv_bfloat16*>(a.P) + (size_t)b * S * plane;
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      __nv_bfloat162* p0 = reinterpret_cast<__nv_bfloat162*>(P + q * plane + r0) + l;
+      __nv_bfloat162* p1 = reinterpret_cast<__nv_bfloat162*>(P + q * plane + r1) + l;
+      if (a.mode == 0) {
+        *p0 = __floats2bfloat162_rn(dr[q], di[q]);
+      } else if (a.mode == 1) {
+        *p0 = __floats2bfloat162_rn(dr[q], di[q]);
+        *p1 = __floats2bfloat162_rn(di[q], -dr[q]);
+      } else {
+        *p0 = __floats2bfloat162_rn(dr[q], -di[q]);
+        *p1 = __floats2bfloat162_rn(di[q], dr[q]);
+      }
+    }
+  } else {
+    float hr, lr, hi_, li;
+    tf32_split(v.x, hr, lr);
+    tf32_split(v.y, hi_, li);
+    float* P = reinterpret_cast<float*>(a.P) + (size_t)b * TF_PLANES * plane;
+    float2* h0 = reinterpret_cast<float2*>(P + r0) + l;
+    float2* q0 = reinterpret_cast<float2*>(P + plane + r0) + l;
+    float2* h1 = reinterpret_cast<float2*>(P + r1) + l;
+    float2* q1 = reinterpret_cast<float2*>(P + plane + r1) + l;
+    if (a.mode == 0) {
+      *h0 = make_float2(hr, hi_);
+      *q0 = make_float2(lr, li);
+    } else if (a.mode == 1) {
+      *h0 = make_float2(hr, hi_);
+      *q0 = make_float2(lr, li);
+      *h1 = make_float2(hi_, -hr);
+      *q1 = make_float2(li, -lr);
+    } else {
+      *h0 = make_float2(hr, -hi_);
+      *q0 = make_float2(lr, -li);
+      *h1 = make_float2(hi_, hr);
+      *q1 = make_float2(li, lr);
+    }
+  }
+}
+
+// Row side (rows of a column-major matrix become K-major rows): a 32 x 32 tile of complex
+// entries through shared memory, read along the rows' index, written along K.
+// Block (32, 8); grid (row tiles, column tiles over Kp/2, batch).
+template <int CLS>
+__global__ void __launch_bounds__(256) k_split_rows(SplitArgs a) {
+  __shared__ double2 T[32][33];
+  const int b = blockIdx.z, l0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const double2* X = a.X + (size_t)b * a.sX;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = c0 + ty + 8 * j, l = l0 + tx;
+    T[ty + 8 * j][tx] = (l < a.rows && c < a.cols) ? X[(size_t)c * a.ld + l] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const size_t plane = (size_t)a.nrow_out * a.Kp;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int l = l0 + ty + 8 * j, c = c0 + tx;
+    if (l >= a.rows || c >= (int)(a.Kp >> 1)) continue;
+    const double2 v = T[tx][ty + 8 * j];
+    if constexpr (CLS == 0) {
+      constexpr int S = ZCfg<0>::S, BITS = ZCfg<0>::BITS;
+      const int e = row_exponent(a.mb[(size_t)b * a.rows + l]);
+      if (c == 0) a.ex[(size_t)b * a.rows + l] = e;
+      float dr[S], di[S];
+      digits_of<BITS, S>(fixed_of<BITS, S>(v.x, e), dr);
+      digits_of<BITS, S>(fixed_of<BITS, S>(v.y, e), di);
+      __nv_bfloat16* P = reinterpret_cast<__nv_bfloat16*>(a.P) + (size_t)b * S * plane + (size_t)l * a.Kp;
+#pragma unroll
+      for (int q = 0; q < S; ++q)
+        reinterpret_cast<__nv_bfloat162*>(P + q * plane)[c] = __floats2bfloat162_rn(dr[q], di[q]);
+    } else {
+      float hr, lr, hi_, li;
+      tf32_split(v.x, hr, lr);
+      tf32_split(v.y, hi_, li);
+      float* P = reinterpret_cast<float*>(a.P) + (size_t)b * TF_PLANES * plane + (size_t)l * a.Kp;
+      reinterpret_cast<float2*>(P)[c] = make_float2(hr, hi_);
+      reinterpret_cast<float2*>(P + plane)[c] = make_float2(lr, li);
+    }
+  }
+}
+
+struct MmaArgs {
+  int Mr, Nr;            // real output rows / columns (D = A_r B_r^T)
+  int kchunks;           // reduction chunks (of KC) in total
+  int chunks_per_split;  // chunks handled by one CTA (the last split may have fewer)
+  int nsplit;
+  int BN;                // output columns per CTA (the TF32 kernel: a multiple of 32, <= 256)
+  int64_t ldp;           // partial column pitch (elements; partials are [column][row])
+  int64_t split_stride;  // partial elements per split (Nr_pad * ldp)
+  int64_t batch_stride;  // partial elements per batch entry (nsplit * split_stride)
+  void* part;            // int64 (FP64 class) or float (FP32 class) partials
+  int fix_unit;          // FP64 class: fixed-point unit 2^-fix_unit
+  int* status;
+};
+
+// group t = p + q (digits p, q numbered from 1) has weight 2^(-BITS t); for the FP64 class it
+// enters the fixed point with unit 2^-U as g << (U - BITS t), or rounded g >> (BITS t - U)
+__device__ __forceinline__ long long fix_add(long long acc, int g, int sh) {
+  if (sh >= 0) return acc + ((long long)g << sh);
+  const int r = -sh;
+  return acc + (long long)((g + (1 << (r - 1))) >> r);
+}
+
+// add group T's FP32 sums (exact integers) of this thread's HB columns to the fixed point 2^-U
+template <int BITS, int T, int S, int BN, int HB>
+__device__ __forceinline__ void drain_group(uint32_t tl, long long (&acc)[HB], int U) {
+  if constexpr (T <= S + 1) {
+    const int sh = U - BITS * T;
+#pragma unroll
+    for (int c0 = 0; c0 < HB; c0 += 16) {
+      uint32_t v[16];
+      tmem_ld16(tl + (uint32_t)((T - 2) * BN + c0), v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[c0 + j] = fix_add(acc[c0 + j], __float2int_rn(__uint_as_float(v[j])), sh);
+    }
+  }
+}
+
+// FP64 class: digit-plane products with exact group sums (see the head of this file)
+__global__ void __launch_bounds__(ZG_THREADS, 1)
+    k_mma_digits(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, MmaArgs a) {
+  using Cfg = ZCfg<0>;
+  constexpr int S = Cfg::S, BITS = Cfg::BITS, BN = Cfg::BN, SWZ = Cfg::SWZ, STAGES = Cfg::STAGES;
+  constexpr int KC = SWZ / 2;                             // reduction elements per stage
+  constexpr int NG = S;                                   // groups t = 2 .. S + 1
+  constexpr uint32_t TMEM_COLS = (NG * BN <= 256) ? ((NG * BN <= 128) ? 128 : 256) : 512;
+  static_assert(NG * BN <= 512, "TMEM holds every group's accumulator");
+  constexpr int WCH = Cfg::WINDOW / KC;                  // chunks per drain window
+  constexpr uint32_t A_BYTES = S * ZG_BM * SWZ, B_BYTES = S * BN * SWZ;
+
+  extern __shared__ __align__(1024) unsigned char zsm_raw[];
+  unsigned char* zsm = (unsigned char*)(((uintptr_t)zsm_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_acc_full, bar_acc_empty, bar_done;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tm = blockIdx.x, tn = blockIdx.y;
+  const int split = blockIdx.z % a.nsplit, batch = blockIdx.z / a.nsplit;
+  const int c_begin = split * a.chunks_per_split;
+  const int c_end = min(a.kchunks, c_begin + a.chunks_per_split);
+  const int nch = max(0, c_end - c_begin);
+  const int nwin = nch == 0 ? 0 : (nch + WCH - 1) / WCH;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&bar_full[s], 1);
+      mbar_init(&bar_empty[s], 1);
+    }
+    mbar_init(&bar_acc_full, 1);
+    mbar_init(&bar_acc_empty, 256);
+    mbar_init(&bar_done, 1);
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  auto fail = [&](int where) {
+    abort_s = 1;
+    atomicExch(a.status, HW_ETIMEOUT);
+    (void)where;
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      uint32_t in_flight = 0, parity = 0;       // per stage: a load was issued; its phase parity
+      for (int it = 0; it < nch; ++it) {
+        const int st = it % STAGES;
+        const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+        if (*(volatile int*)&abort_s) break;
+        if (!mbar_wait(&bar_empty[st], ph ^ 1u)) {
+          fail(1);
+          break;
+        }
+        unsigned char* sA = zsm + (size_t)st * (A_BYTES + B_BYTES);
+        unsigned char* sB = sA + A_BYTES;
+        mbar_expect_tx(&bar_full[st], A_BYTES + B_BYTES);
+        const int k0 = (c_begin + it) * KC;
+        tma_load_3d(sA, &tmA, k0, tm * ZG_BM, batch * S, &bar_full[st]);
+        tma_load_3d(sB, &tmB, k0, tn * BN, batch * S, &bar_full[st]);
+        in_flight |= 1u << st;
+        parity = (parity & ~(1u << st)) | (ph << st);
+      }
+      // the copies this thread issued must land before the CTA may leave
+      for (int s = 0; s < STAGES; ++s)
+        if (((in_flight >> s) & 1u) && !mbar_wait(&bar_full[s], (parity >> s) & 1u)) fail(2);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = umma_idesc_bf16(BN);
+      int it = 0;
+      bool issued_any = false;
+      for (int w = 0; w < nwin && !*(volatile int*)&abort_s; ++w) {
+        if (w > 0 && !mbar_wait(&bar_acc_empty, (uint32_t)((w - 1) & 1))) {
+          fail(3);
+          break;
+        }
+        tc_fence_after();
+        const int wend = min(nch, (w + 1) * WCH);
+        bool first = true;
+        for (; it < wend; ++it) {
+          const int st = it % STAGES;
+          if (!mbar_wait(&bar_full[st], (uint32_t)((it / STAGES) & 1))) {
+            fail(4);
+            break;
+          }
+          tc_fence_after();
+          const uint32_t aBase = smem_u32(zsm + (size_t)st * (A_BYTES + B_BYTES));
+          const uint32_t bBase = aBase + A_BYTES;
+#pragma unroll 1
+          for (int t = 2; t <= S + 1; ++t) {
+            const uint32_t dt = tmem + (uint32_t)((t - 2) * BN);
+            bool first_t = first;
+#pragma unroll 1
+            for (int p = max(1, t - S); p <= min(S, t - 1); ++p) {
+              const int q = t - p;
+              const uint64_t da = umma_desc<SWZ>(aBase + (uint32_t)((p - 1) * ZG_BM * SWZ));
+              const uint64_t db = umma_desc<SWZ>(bBase + (uint32_t)((q - 1) * BN * SWZ));
+#pragma unroll
+              for (int kk = 0; kk < KC / 16; ++kk) {
+                umma_bf16(dt, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, first_t ? 0u : 1u);
+                first_t = false;
+              }
+            }
+          }
+          issued_any = true;
+          first = false;
+          umma_commit(&bar_empty[st]);   // frees the stage once these MMAs have read it
+        }
+        if (*(volatile int*)&abort_s) break;
+        umma_commit(&bar_acc_full);      // the window's sums are complete in TMEM
+      }
+      // no tensor-core work may be in flight when TMEM is released
+      if (issued_any) {
+        umma_commit(&bar_done);
+        if (!mbar_wait(&bar_done, 0)) fail(5);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------- epilogue (warps 2-9)
+    constexpr int HB = BN / 2;                 // columns per epilogue thread
+    const int quad = warp & 3;                 // TMEM lanes 32 quad .. 32 quad + 31
+    const int hc = ((warp - 2) >> 2) * HB;     // first column of this warp's half
+    const int row = quad * 32 + lane;          // output row within the tile
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)hc;
+    const int grow = tm * ZG_BM + row;
+    const int gcol = tn * BN + hc;
+    long long acc[HB];
+#pragma unroll
+    for (int c = 0; c < HB; ++c) acc[c] = 0;
+    bool ok = true;
+    for (int w = 0; w < nwin; ++w) {
+      if (!mbar_wait(&bar_acc_full, (uint32_t)(w & 1))) {
+        fail(6);
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      // group t's column block [(t - 2) BN, (t - 1) BN)
+      drain_group<BITS, 2, S, BN, HB>(tl, acc, a.fix_unit);
+      drain_group<BITS, 3, S, BN, HB>(tl, acc, a.fix_unit);
+      drain_group<BITS, 4, S, BN, HB>(tl, acc, a.fix_unit);
+      drain_group<BITS, 5, S, BN, HB>(tl, acc, a.fix_unit);
+      drain_group<BITS, 6, S, BN, HB>(tl, acc, a.fix_unit);
+      drain_group<BITS, 7, S, BN, HB>(tl, acc, a.fix_unit);
+      drain_group<BITS, 8, S, BN, HB>(tl, acc, a.fix_unit);
+      drain_group<BITS, 9, S, BN, HB>(tl, acc, a.fix_unit);
+      tc_fence_before();
+      mbar_arrive(&bar_acc_empty);
+    }
+    if (ok && !*(volatile int*)&abort_s && grow < a.Mr) {
+      long long* P = reinterpret_cast<long long*>(a.part) + (size_t)batch * a.batch_stride +
+                     (size_t)split * a.split_stride + (size_t)gcol * a.ldp + grow;
+#pragma unroll
+      for (int c = 0; c < HB; ++c)
+        if (gcol + c < a.Nr) P[(size_t)c * a.ldp] = acc[c];
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+// TF32 x TF32 -> FP32 instruction descriptor: both operands K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t umma_idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(ZG_BM >> 4) << 24);
+}
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(accum));
+}
+
+// FP32 class: per stage the hi / lo TF32 planes of a 128 x 32 tile of A and a BN x 32 tile of B
+// (128-byte swizzled rows); hi hi' + hi lo' + lo hi' accumulate into one FP32 tile in TMEM
+// (BN columns); the epilogue writes the tile's FP32 partial sums.
+__global__ void __launch_bounds__(ZG_THREADS, 1)
+    k_mma_tf32(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, MmaArgs a) {
+  constexpr int KC = 32;                                  // FP32 entries per 128-byte row
+  constexpr uint32_t TMEM_COLS = TF_BN_MAX;
+  const int BN = a.BN;
+  const uint32_t A_BYTES = TF_PLANES * ZG_BM * 128, B_BYTES = (uint32_t)(TF_PLANES * BN * 128);
+  const uint32_t STAGE = (uint32_t)tf_stage_bytes();
+
+  extern __shared__ __align__(1024) unsigned char zsm_raw[];
+  unsigned char* zsm = (unsigned char*)(((uintptr_t)zsm_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t bar_full[TF_STAGES], bar_empty[TF_STAGES], bar_acc_full, bar_done;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tm = blockIdx.x, tn = blockIdx.y;
+  const int split = blockIdx.z % a.nsplit, batch = blockIdx.z / a.nsplit;
+  const int c_begin = split * a.chunks_per_split;
+  const int c_end = min(a.kchunks, c_begin + a.chunks_per_split);
+  const int nch = max(0, c_end - c_begin);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TF_STAGES; ++s) {
+      mbar_init(&bar_full[s], 1);
+      mbar_init(&bar_empty[s], 1);
+    }
+    mbar_init(&bar_acc_full, 1);
+    mbar_init(&bar_done, 1);
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  auto fail = [&]() {
+    abort_s = 1;
+    atomicExch(a.status, HW_ETIMEOUT);
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      uint32_t in_flight = 0, parity = 0;
+      for (int it = 0; it < nch; ++it) {
+        const int st = it % TF_STAGES;
+        const uint32_t ph = (uint32_t)((it / TF_STAGES) & 1);
+        if (*(volatile int*)&abort_s) break;
+        if (!mbar_wait(&bar_empty[st], ph ^ 1u)) {
+          fail();
+          break;
+        }
+        unsigned char* sA = zsm + (size_t)st * STAGE;
+        unsigned char* sB = sA + A_BYTES;
+        mbar_expect_tx(&bar_full[st], A_BYTES + B_BYTES);
+        const int k0 = (c_begin + it) * KC;
+        tma_load_3d(sA, &tmA, k0, tm * ZG_BM, batch * TF_PLANES, &bar_full[st]);
+        tma_load_3d(sB, &tmB, k0, tn * BN, batch * TF_PLANES, &bar_full[st]);
+        in_flight |= 1u << st;
+        parity = (parity & ~(1u << st)) | (ph << st);
+      }
+      for (int s = 0; s < TF_STAGES; ++s)
+        if (((in_flight >> s) & 1u) && !mbar_wait(&bar_full[s], (parity >> s) & 1u)) fail();
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = umma_idesc_tf32(BN);
+      bool issued_any = false;
+      for (int it = 0; it < nch; ++it) {
+        const int st = it % TF_STAGES;
+        if (*(volatile int*)&abort_s) break;
+        if (!mbar_wait(&bar_full[st], (uint32_t)((it / TF_STAGES) & 1))) {
+          fail();
+          break;
+        }
+        tc_fence_after();
+        const uint32_t aHi = smem_u32(zsm + (size_t)st * STAGE), aLo = aHi + ZG_BM * 128;
+        const uint32_t bHi = aHi + A_BYTES, bLo = bHi + (uint32_t)(BN * 128);
+#pragma unroll
+        for (int kk = 0; kk < KC / 8; ++kk) {
+          const uint64_t o = (uint64_t)(kk * 2);   // 8 TF32 entries = 32 bytes
+          umma_tf32(tmem, umma_desc<128>(aHi) + o, umma_desc<128>(bHi) + o, idesc, (it | kk) ? 1u : 0u);
+          umma_tf32(tmem, umma_desc<128>(aHi) + o, umma_desc<128>(bLo) + o, idesc, 1u);
+          umma_tf32(tmem, umma_desc<128>(aLo) + o, umma_desc<128>(bHi) + o, idesc, 1u);
+        }
+        issued_any = true;
+        umma_commit(&bar_empty[st]);
+      }
+      if (issued_any) {
+        if (!*(volatile int*)&abort_s) umma_commit(&bar_acc_full);
+        umma_commit(&bar_done);
+        if (!mbar_wait(&bar_done, 0)) fail();
+      }
+    }
+  } else {
+    // ------------------------------------------------------------- epilogue (warps 2-9)
+    const int HB = BN / 2;                     // a multiple of 16
+    const int quad = warp & 3;
+    const int hc = ((warp - 2) >> 2) * HB;
+    const int row = quad * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)hc;
+    const int grow = tm * ZG_BM + row;
+    const int gcol = tn * BN + hc;
+    bool ok = nch > 0 && mbar_wait(&bar_acc_full, 0u);
+    if (nch > 0 && !ok) fail();
+    tc_fence_after();
+    float* P = reinterpret_cast<float*>(a.part) + (size_t)batch * a.batch_stride + (size_t)split * a.split_stride +
+               (size_t)gcol * a.ldp + grow;
+    const bool store = grow < a.Mr && !*(volatile int*)&abort_s;
+    for (int c0 = 0; c0 < HB; c0 += 16) {
+      uint32_t v[16];
+      if (ok) tmem_ld16(tl + (uint32_t)c0, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (store && gcol + c0 + j < a.Nr) P[(size_t)(c0 + j) * a.ldp] = ok ? __uint_as_float(v[j]) : 0.f;
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+// ----------------------------------------------------------------------------- reduction + output
+struct OutArgs {
+  int m, n, nsplit, cls, fix_unit;
+  const void* part;
+  int64_t ldp, split_stride, batch_stride;
+  const int* exA;        // FP64 class: [batch][m]
+  const int* exB;        // FP64 class: [batch][n]
+  double alpha, beta;
+  double2* C;
+  int64_t ldc, sC;
+};
+
+// 2^e for the exponents that occur here (a normal FP64 number)
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// C_ij = alpha (Re + i Im) scale + beta C_ij, the splits added in a fixed order (the FP64 class's
+// 64-bit integer sums are exact in any order).  grid (row blocks of 128, n, batch): the partial
+// reads ([split][column][row]) and the writes of C (column-major) are coalesced.
+__global__ void __launch_bounds__(128) k_zgemm_out(OutArgs a) {
+  const int b = blockIdx.z, j = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.m) return;
+  double re, im, sc;
+  if (a.cls == 0) {
+    const long long* P = reinterpret_cast<const long long*>(a.part) + (size_t)b * a.batch_stride + i;
+    const size_t oR = (size_t)j * a.ldp, oI = (size_t)(a.n + j) * a.ldp;
+    long long r0 = 0, r1 = 0, i0 = 0, i1 = 0;
+    int s = 0;
+    for (; s + 1 < a.nsplit; s += 2) {
+      const size_t o0 = (size_t)s * a.split_stride, o1 = o0 + a.split_stride;
+      r0 += P[o0 + oR];
+      i0 += P[o0 + oI];
+      r1 += P[o1 + oR];
+      i1 += P[o1 + oI];
+    }
+    if (s < a.nsplit) {
+      r0 += P[(size_t)s * a.split_stride + oR];
+      i0 += P[(size_t)s * a.split_stride + oI];
+    }
+    re = (double)(r0 + r1);
+    im = (double)(i0 + i1);
+    sc = a.alpha * pow2(a.exA[(size_t)b * a.m + i] + a.exB[(size_t)b * a.n + j] - a.fix_unit);
+  } else {
+    const float* P = reinterpret_cast<const float*>(a.part) + (size_t)b * a.batch_stride + i;
+    const size_t oR = (size_t)j * a.ldp, oI = (size_t)(a.n + j) * a.ldp;
+    double r0 = 0.0, r1 = 0.0, i0 = 0.0, i1 = 0.0;
+    int s = 0;
+    for (; s + 1 < a.nsplit; s += 2) {
+      const size_t o0 = (size_t)s * a.split_stride, o1 = o0 + a.split_stride;
+      r0 += (double)P[o0 + oR];
+      i0 += (double)P[o0 + oI];
+      r1 += (double)P[o1 + oR];
+      i1 += (double)P[o1 + oI];
+    }
+    if (s < a.nsplit) {
+      r0 += (double)P[(size_t)s * a.split_stride + oR];
+      i0 += (double)P[(size_t)s * a.split_stride + oI];
+    }
+    re = r0 + r1;
+    im = i0 + i1;
+    sc = a.alpha;
+  }
+  double2* c = a.C + (size_t)b * a.sC + (size_t)j * a.ldc + i;
+  double2 v = make_double2(sc * re, sc * im);
+  if (a.beta != 0.0) {
+    const double2 o = *c;
+    v.x += a.beta * o.x;
+    v.y += a.beta * o.y;
+  }
+  *c = v;
+}
+
+// ----------------------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// 3-D map over planes [planes][rows][Kp], box {swz / esz, box_rows, box_planes}
+static bool make_plane_map(CUtensorMap* m, const void* base, bool fp32, int64_t Kp, int rows, int planes,
+                           int box_rows, int box_planes, int swz) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const int esz = fp32 ? 4 : 2;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * esz, (cuuint64_t)Kp * esz * rows};
+  cuuint32_t box[3] = {(cuuint32_t)(swz / esz), (cuuint32_t)box_rows, (cuuint32_t)box_planes};
+  cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base),
+             dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             swz == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct ZgemmWork {
+  void* buf = nullptr;   // planes A | planes B | partials | exponents | magnitude bits
+  size_t cap = 0;
+  int* status = nullptr;
+  int nsm = 0;
+  bool attr_set = false;
+};
+
+void zgemm_free(ZgemmWork*& w) {
+  if (!w) return;
+  if (w->buf) cudaFree(w->buf);
+  if (w->status) cudaFree(w->status);
+  delete w;
+  w = nullptr;
+}
+
+static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static cudaError_t zgemm_run(ZgemmWork* w, cudaStream_t st, int cls, bool transA, int m, int n, int k, double alpha,
+                             const double2* A, int64_t lda, int64_t sA, const double2* B, int64_t ldb, int64_t sB,
+                             double beta, double2* C, int64_t ldc, int64_t sC, int batch, int* launches) {
+  const bool fp64 = cls == 0;
+  const int planes = fp64 ? ZCfg<0>::S : TF_PLANES;
+  const size_t esz = fp64 ? 2 : 4;
+  const int Mr = m, Nr = 2 * n;
+  const int64_t Kp = ((int64_t)2 * k + ZG_KALIGN - 1) / ZG_KALIGN * ZG_KALIGN;
+  const int BN = fp64 ? ZCfg<0>::BN : std::min(TF_BN_MAX, (Nr + 31) / 32 * 32);
+  const int KC = 32;   // reduction entries per stage in both classes
+  const int mt = (Mr + ZG_BM - 1) / ZG_BM, nt = (Nr + BN - 1) / BN;
+  const int kchunks = (int)(Kp / KC);
+  // reduction splits: about one wave of CTAs, each at least 4 chunks
+  const int tiles = mt * nt * batch;
+  int nsplit = std::max(1, std::min(std::max(1, kchunks / 4), (w->nsm + tiles - 1) / tiles));
+  const int cps = (kchunks + nsplit - 1) / nsplit;
+  nsplit = (kchunks + cps - 1) / cps;
+  const int64_t ldp = (int64_t)mt * ZG_BM;
+  const int64_t split_stride = (int64_t)nt * BN * ldp;
+  const int64_t batch_stride = split_stride * nsplit;
+  const size_t elem_part = fp64 ? 8 : 4;
+  // per batch entry
+  const size_t bytesA = (size_t)planes * Mr * Kp * esz, bytesB = (size_t)planes * Nr * Kp * esz;
+  const size_t bytesP = (size_t)batch_stride * elem_part;
+  const size_t bytesE = (size_t)(m + n) * sizeof(int), bytesM = (size_t)(m + n) * 8;
+  const size_t per = al256(bytesA) + al256(bytesB) + al256(bytesP) + al256(bytesE) + al256(bytesM) + 5 * 256;
+  // process the batch in chunks that fit the workspace (grown up to 1 GiB)
+  const size_t limit = size_t(1) << 30;
+  const int bchunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)batch, limit / per));
+  const size_t need = per * bchunk;
+  if (need > w->cap) {
+    if (w->buf) cudaFree(w->buf);
+    w->buf = nullptr;
+    w->cap = 0;
+    cudaError_t e = cudaMalloc(&w->buf, need);
+    if (e != cudaSuccess) return e;
+    w->cap = need;
+  }
+  if (!w->attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_mma_digits, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)zg_smem_bytes<0>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_mma_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tf_smem_bytes());
+    if (e != cudaSuccess) return e;
+    w->attr_set = true;
+  }
+  for (int b0 = 0; b0 < batch; b0 += bchunk) {
+    const int nb = std::min(bchunk, batch - b0);
+    unsigned char* p = static_cast<unsigned char*>(w->buf);
+    void* PA = p;
+    p += al256(bytesA * nb);
+    void* PB = p;
+    p += al256(bytesB * nb);
+    void* part = p;
+    p += al256(bytesP * nb);
+    int* exA = reinterpret_cast<int*>(p);
+    int* exB = exA + (size_t)nb * m;
+    p += al256(bytesE * nb);
+    unsigned long long* mbA = reinterpret_cast<unsigned long long*>(p);
+    unsigned long long* mbB = mbA + (size_t)nb * m;
+    // split planes of the A side (columns of A for op = ^H, rows of A otherwise)
+    SplitArgs sa;
+    sa.X = A + (size_t)b0 * sA;
+    sa.ld = lda;
+    sa.sX = sA;
+    sa.rows = transA ? k : m;
+    sa.cols = transA ? m : k;
+    sa.mode = 0;
+    sa.nrow_out = Mr;
+    sa.Kp = Kp;
+    sa.P = PA;
+    sa.mb = mbA;
+    sa.ex = exA;
+    SplitArgs sb;
+    sb.X = B + (size_t)b0 * sB;
+    sb.ld = ldb;
+    sb.sX = sB;
+    sb.rows = k;
+    sb.cols = n;
+    sb.mode = transA ? 1 : 2;
+    sb.nrow_out = Nr;
+    sb.Kp = Kp;
+    sb.P = PB;
+    sb.mb = mbB;
+    sb.ex = exB;
+    const int kh = (int)(Kp >> 1);
+    if (fp64) {
+      cudaMemsetAsync(mbA, 0, bytesM * nb, st);
+      const int segs = std::max(1, std::min(64, (k + 2047) / 2048));
+      if (transA)
+        k_colmax<<<dim3(segs, m, nb), 256, 0, st>>>(sa.X, lda, sA, k, m, mbA);
+      else
+        k_rowmax<<<dim3((m + 255) / 256, nb), 256, 0, st>>>(sa.X, lda, sA, m, k, mbA);
+      k_colmax<<<dim3(segs, n, nb), 256, 0, st>>>(sb.X, ldb, sB, k, n, mbB);
+      *launches += 2;
+    }
+    if (transA) {
+      if (fp64)
+        k_split_cols<0><<<dim3((kh + 255) / 256, m, nb), 256, 0, st>>>(sa);
+      else
+        k_split_cols<1><<<dim3((kh + 255) / 256, m, nb), 256, 0, st>>>(sa);
+    } else {
+      const dim3 g((m + 31) / 32, (kh + 31) / 32, nb);
+      if (fp64)
+        k_split_rows<0><<<g, dim3(32, 8), 0, st>>>(sa);
+      else
+        k_split_rows<1><<<g, dim3(32, 8), 0, st>>>(sa);
+    }
+    if (fp64)
+      k_split_cols<0><<<dim3((kh + 255) / 256, n, nb), 256, 0, st>>>(sb);
+    else
+      k_split_cols<1><<<dim3((kh + 255) / 256, n, nb), 256, 0, st>>>(sb);
+    CUtensorMap mA, mB;
+    const int swz = fp64 ? ZCfg<0>::SWZ : 128;
+    if (!make_plane_map(&mA, PA, !fp64, Kp, Mr, planes * nb, ZG_BM, planes, swz) ||
+        !make_plane_map(&mB, PB, !fp64, Kp, Nr, planes * nb, BN, planes, swz))
+      return cudaErrorInvalidValue;
+    MmaArgs ma;
+    ma.Mr = Mr;
+    ma.Nr = Nr;
+    ma.kchunks = kchunks;
+    ma.chunks_per_split = cps;
+    ma.nsplit = nsplit;
+    ma.BN = BN;
+    ma.ldp = ldp;
+    ma.split_stride = split_stride;
+    ma.batch_stride = batch_stride;
+    ma.part = part;
+    ma.fix_unit = zg_fix_unit(Kp);
+    ma.status = w->status;
+    const dim3 grid(mt, nt, nsplit * nb);
+    if (fp64)
+      k_mma_digits<<<grid, ZG_THREADS, zg_smem_bytes<0>(), st>>>(mA, mB, ma);
+    else
+      k_mma_tf32<<<grid, ZG_THREADS, tf_smem_bytes(), st>>>(mA, mB, ma);
+    OutArgs oa;
+    oa.m = m;
+    oa.n = n;
+    oa.nsplit = nsplit;
+    oa.cls = cls;
+    oa.fix_unit = zg_fix_unit(Kp);
+    oa.part = part;
+    oa.ldp = ldp;
+    oa.split_stride = split_stride;
+    oa.batch_stride = batch_stride;
+    oa.exA = exA;
+    oa.exB = exB;
+    oa.alpha = alpha;
+    oa.beta = beta;
+    oa.C = C + (size_t)b0 * sC;
+    oa.ldc = ldc;
+    oa.sC = sC;
+    k_zgemm_out<<<dim3((m + 127) / 128, n, nb), 128, 0, st>>>(oa);
+    *launches += 4;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t zgemm_tc(ZgemmWork*& w, cudaStream_t st, int cls, bool transA, int m, int n, int k, double alpha,
+                     const double2* A, int64_t lda, int64_t sA, const double2* B, int64_t ldb, int64_t sB,
+                     double beta, double2* C, int64_t ldc, int64_t sC, int batch, int* launches) {
+  if (m <= 0 || n <= 0 || batch <= 0) return cudaSuccess;
+  if (k <= 0 || (cls != 0 && cls != 1)) return cudaErrorInvalidValue;
+  if (!w) {
+    w = new ZgemmWork();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&w->nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaMalloc((void**)&w->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(w->status, 0, sizeof(int));
+    if (e != cudaSuccess) return e;
+  }
+  return zgemm_run(w, st, cls, transA, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, launches);
+}
+
+int* zgemm_status_ptr(ZgemmWork* w) { return w ? w->status : nullptr; }
+
+// status word of the tensor-core kernels (HW_OK, or HW_ETIMEOUT after a wait ran out); reset
+int zgemm_status(ZgemmWork* w, cudaStream_t st, bool reset) {
+  if (!w || !w->status) return HW_OK;
+  int v = 0;
+  cudaMemcpyAsync(&v, w->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  if (reset && v != 0) cudaMemsetAsync(w->status, 0, sizeof(int), st);
+  return v;
+}
+
+}  // namespace hw
+
+using namespace hw;
+
+extern "C" hw_status hw_block_product(hw_ctx* ctx, int transA, int m, int n, int k, double alpha, const double* A,
+                                      int64_t lda, int64_t sA, const double* B, int64_t ldb, int64_t sB, double beta,
+                                      double* C, int64_t ldc, int64_t sC, int batch, int cls) {
+  if (!ctx) return HW_EINVAL;
+  if (ctx->device < 0) return hw_fail(ctx, HW_ESTATE, "host-only context has no device");
+  if ((transA != 0 && transA != 1) || (cls != 0 && cls != 1) || m < 1 || n < 1 || k < 1 || batch < 1 || !A ||
+      !B || !C)
+    return hw_fail(ctx, HW_EINVAL, "hw_block_product: bad arguments");
+  if (lda < (transA ? k : m) || ldb < k || ldc < m || (batch > 1 && (sA < 0 || sB < 0 || sC < 0)))
+    return hw_fail(ctx, HW_EINVAL, "hw_block_product: bad leading dimensions or strides");
+  if ((int64_t)m > (1 << 20) || (int64_t)n > 4096 || (int64_t)k > (1 << 20))
+    return hw_fail(ctx, HW_EINVAL, "hw_block_product: sizes out of range");
+  cudaSetDevice(ctx->device);
+  int nl = 0;
+  cudaError_t e = zgemm_tc(ctx->zg, ctx->stream, cls, transA != 0, m, n, k, alpha,
+                           reinterpret_cast<const double2*>(A), lda, sA, reinterpret_cast<const double2*>(B), ldb,
+                           sB, beta, reinterpret_cast<double2*>(C), ldc, sC, batch, &nl);
+  ctx->launches += nl;
+  if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("hw_block_product: ") + cudaGetErrorString(e));
+  return HW_OK;
+}

@@ -78,6 +78,9 @@ _SIGS = {
     "hw_gradient": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_int]),
     "hw_gram": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_int64,
                           C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_int64]),
+    "hw_block_product": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p,
+                                   C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_double,
+                                   C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_int]),
     "hw_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "hw_profile_read": (C.c_int, [C.c_void_p, _D, C.POINTER(C.c_int64)]),
     "hw_profile_work": (C.c_int, [C.c_void_p, _D]),
@@ -268,6 +271,7 @@ HW_OPT_CHEB_LOCK = 8
 HW_OPT_SLAB_KERNEL = 9
 HW_OPT_TAIL_NO_P = 10
 HW_OPT_WINDOW = 11
+HW_OPT_TC_GEMM = 12
 
 
 def hw_set_option(h, option, value):
@@ -334,6 +338,20 @@ def hw_selftest_barrier(h, nblocks, spin_limit, skip_block):
     ws = C.c_int(-1)
     _check(h, load_library().hw_selftest_barrier(h, nblocks, spin_limit, skip_block, C.byref(ws)))
     return int(ws.value)
+
+
+def hw_block_product(h, trans_a, m, n, k, A, B, C, alpha=1.0, beta=0.0, cls=0):
+    """C_b = alpha op(A_b) B_b + beta C_b on the tensor cores.  A, B, C: contiguous CUDA complex128
+    tensors of shape (batch, columns, ld): block b's column c is A[b, c, :ld] (column-major
+    blocks, leading dimension = the last extent).  op = conjugate transpose when trans_a
+    (A_b: k x m), else none (A_b: m x k).  cls 0: FP64 class, 1: FP32 class."""
+    for T in (A, B, C):
+        assert T.is_contiguous() and T.dim() == 3
+    batch = C.shape[0]
+    _check(h, load_library().hw_block_product(
+        h, int(trans_a), m, n, k, float(alpha), A.data_ptr(),
+        A.shape[2], A.shape[1] * A.shape[2], B.data_ptr(), B.shape[2], B.shape[1] * B.shape[2], float(beta),
+        C.data_ptr(), C.shape[2], C.shape[1] * C.shape[2], batch, cls))
 
 
 def hw_profile(h, enable: bool):
