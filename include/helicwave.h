@@ -241,6 +241,21 @@ hw_status hw_solve_eigs_traced(hw_ctx* ctx, int k, int n_eig, int block, double 
                                double* rec_theta, double* rec_res, int64_t ld, double* evals,
                                int* iters);
 
+/* Residual history of the last hw_solve_eigs (metrics; the paper plots such histories for its
+ * LOBPCG + TPA runs, Sec. "Eigensolvers and Preconditioning"): for k-point k, one entry per
+ * filter cycle or LOBPCG iteration (windows follow each other), phase[i] its HW_HIST_* code and
+ * res[i] the largest residual ||H x - theta x|| over the wanted columns at its start.  Writes
+ * min(n, max_n) entries (phase and res may be NULL) and the count n to *n_out (0 when k took no
+ * part).  Host arrays; no device work. */
+enum {
+  HW_HIST_FILTER_FP32 = 0,    /* Chebyshev filter cycle, FP32 H X and products */
+  HW_HIST_FILTER_FP64 = 1,    /* Chebyshev filter cycle, FP64 */
+  HW_HIST_LOBPCG_FP32 = 2,    /* LOBPCG iteration, FP32-class products */
+  HW_HIST_LOBPCG_HYBRID = 3,  /* LOBPCG iteration, FP64-class products for X only */
+  HW_HIST_LOBPCG_FP64 = 4     /* LOBPCG iteration, FP64-class products */
+};
+hw_status hw_get_residual_history(hw_ctx* ctx, int k, int* phase, double* res, int max_n, int* n_out);
+
 /* Self-test of the bounded device wait (no counterpart in the paper; failure detection).  The
  * library's grid-wide barrier (used by the FP64 Jacobi eigensolver) gives up after a bounded
  * number of polls, sets the device status word to HW_ETIMEOUT and lets every CTA leave, so a
@@ -370,11 +385,12 @@ typedef enum {
                                transforms split 64 = 4 x 16 over the 4 lanes of a theta2 row
                                (register DFTs, shuffles), 0 the Stockham FFTs (every other grid
                                and FP64 use the FFTs). */
-  HW_OPT_TAIL_NO_P = 10,    /* Chebyshev solver, mixed form: 1 (default) starts the LOBPCG end
-                               phase without conjugate directions (Rayleigh-Ritz on [X W], each
+  HW_OPT_TAIL_NO_P = 10,    /* Chebyshev solver, mixed form: 1 starts the LOBPCG end phase
+                               without conjugate directions (Rayleigh-Ritz on [X W], each
                                iteration cheaper) and switches them on for good once an
-                               iteration fails to halve the largest wanted residual; 0: with
-                               them from the start. */
+                               iteration fails to halve the largest wanted residual; 0 (default):
+                               with them from the start (over 8 start blocks of the tube
+                               workload: 8-10 end-to-end iterations against 9-14). */
   HW_OPT_WINDOW = 11,       /* hw_solve_eigs: largest number of eigenpairs one block solves,
                                1..100; 0 (default) means 80.  More eigenpairs than this are
                                solved in consecutive windows of equal size (see hw_solve_eigs). */

@@ -112,10 +112,15 @@ struct hw_ctx {
   int cheb_degree = 24;        // HW_OPT_CHEB_DEGREE
   int cheb_adapt = 1;          // HW_OPT_CHEB_ADAPT
   int cheb_lock = 1;           // HW_OPT_CHEB_LOCK
-  int tail_no_p = 1;           // HW_OPT_TAIL_NO_P
+  int tail_no_p = 0;           // HW_OPT_TAIL_NO_P
   int window = 0;              // HW_OPT_WINDOW (0: 100)
   int slab_r16 = 1;            // HW_OPT_SLAB_KERNEL
   int64_t rr_fallbacks = 0;    // Householder results rejected by the check (Jacobi used)
+  // residual history of the last hw_solve_eigs: per k-point slot, per iteration (filter cycle
+  // or LOBPCG iteration) the phase code (HW_HIST_*) and the largest wanted residual
+  std::vector<std::vector<int>> hist_phase;
+  std::vector<std::vector<double>> hist_res;
+  std::vector<int> hist_k;     // k-point index of each slot
   hw::Prof prof;
 };
 

@@ -472,6 +472,19 @@ struct Gemm {
 
 }  // namespace
 
+// append one iteration's largest wanted residual of k-point kidx to the context's history
+static void hist_push(hw_ctx* ctx, int kidx, int phase, double res) {
+  size_t slot = 0;
+  while (slot < ctx->hist_k.size() && ctx->hist_k[slot] != kidx) ++slot;
+  if (slot == ctx->hist_k.size()) {
+    ctx->hist_k.push_back(kidx);
+    ctx->hist_phase.emplace_back();
+    ctx->hist_res.emplace_back();
+  }
+  ctx->hist_phase[slot].push_back(phase);
+  ctx->hist_res[slot].push_back(res);
+}
+
 // Orthonormalise `ncol` columns of S at column offset c0 for every k-point by Cholesky-QR
 // (Gram, Cholesky, triangular inverse, GEMM), `passes` times.  nv[b]: valid columns of k-point
 // b (device).  On a failed factorisation the k-point's fail flag is set.
@@ -1090,6 +1103,8 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       double mr = 0.0;
       for (int j = 0; j < n_eig; ++j) mr = std::max(mr, resh[(size_t)b * nb + j]);
       maxres = std::max(maxres, mr);
+      hist_push(ctx, kidx[b], gemm.lowp ? HW_HIST_LOBPCG_FP32 : (mixed && hyb_on ? HW_HIST_LOBPCG_HYBRID
+                                                                                   : HW_HIST_LOBPCG_FP64), mr);
       if (mr <= thr) {
         claim[b] = 1;
         ++nclaim;
@@ -1604,6 +1619,7 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       double mr = 0.0;
       for (int j = 0; j < n_eig; ++j) mr = std::max(mr, resh[(size_t)b * nb + j]);
       maxres = std::max(maxres, mr);
+      hist_push(ctx, kidx[b], lowp ? HW_HIST_FILTER_FP32 : HW_HIST_FILTER_FP64, mr);
       if (mr <= tol) {
         claim[b] = 1;
         ++nclaim;
@@ -1865,6 +1881,23 @@ extern "C" hw_status hw_selftest_barrier(hw_ctx* ctx, int nblocks, long long spi
   return HW_OK;
 }
 
+extern "C" hw_status hw_get_residual_history(hw_ctx* ctx, int k, int* phase, double* res, int max_n, int* n_out) {
+  if (!ctx || !n_out) return HW_EINVAL;
+  size_t slot = 0;
+  while (slot < ctx->hist_k.size() && ctx->hist_k[slot] != k) ++slot;
+  if (slot == ctx->hist_k.size()) {
+    *n_out = 0;
+    return HW_OK;
+  }
+  const int n = (int)ctx->hist_res[slot].size();
+  *n_out = n;
+  for (int i = 0; i < std::min(n, max_n); ++i) {
+    if (phase) phase[i] = ctx->hist_phase[slot][i];
+    if (res) res[i] = ctx->hist_res[slot][i];
+  }
+  return HW_OK;
+}
+
 static hw_status solve_window(hw_ctx* ctx, int nk, const int* kidx, int n_eig, int block, double tol, int maxit,
                               hw_prec prec, int precond_kind, const double* const* X0, double* evals,
                               double* const* evecs, int64_t ld_evecs, int* iters, double* resid, const Deflate* df,
@@ -1881,6 +1914,9 @@ extern "C" hw_status hw_solve_eigs(hw_ctx* ctx, int nk, const int* kidx, int n_e
                                    double* evals, double* const* evecs, int64_t ld_evecs, int* iters,
                                    double* resid) {
   if (!ctx) return HW_EINVAL;
+  ctx->hist_k.clear();
+  ctx->hist_phase.clear();
+  ctx->hist_res.clear();
   const int wmax = ctx->window > 0 ? ctx->window : 80;
   if (n_eig <= wmax)
     return solve_window(ctx, nk, kidx, n_eig, block, tol, maxit, prec, precond_kind, X0, evals, evecs, ld_evecs,

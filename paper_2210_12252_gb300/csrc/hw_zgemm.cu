@@ -251,18 +251,27 @@ __global__ void k_colmax(const double2* X, int64_t ld, int64_t sX, int rows, int
   if ((threadIdx.x & 31) == 0 && m) atomicMax(mb + (size_t)b * cols + c, m);
 }
 
-// |x| bits of every row's entries (rows of a column-major matrix); grid (row blocks, batch)
-__global__ void k_rowmax(const double2* X, int64_t ld, int64_t sX, int rows, int cols, unsigned long long* mb) {
-  const int b = blockIdx.y;
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= rows) return;
-  const double2* x = X + (size_t)b * sX + l;
+// |x| bits of every row's entries (rows of a column-major matrix): block (32 rows, 8 column
+// groups), grid (row blocks, batch)
+__global__ void __launch_bounds__(256) k_rowmax(const double2* X, int64_t ld, int64_t sX, int rows, int cols,
+                                                unsigned long long* mb) {
+  __shared__ unsigned long long red[8][32];
+  const int b = blockIdx.y, tx = threadIdx.x, ty = threadIdx.y;
+  const int l = blockIdx.x * 32 + tx;
   unsigned long long m = 0;
-  for (int c = 0; c < cols; ++c) {
-    const double2 v = x[(size_t)c * ld];
-    m = max(m, max(mag_bits(v.x), mag_bits(v.y)));
+  if (l < rows) {
+    const double2* x = X + (size_t)b * sX + l;
+    for (int c = ty; c < cols; c += 8) {
+      const double2 v = x[(size_t)c * ld];
+      m = max(m, max(mag_bits(v.x), mag_bits(v.y)));
+    }
   }
-  mb[(size_t)b * rows + l] = m;
+  red[ty][tx] = m;
+  __syncthreads();
+  if (ty == 0 && l < rows) {
+    for (int g = 1; g < 8; ++g) m = max(m, red[g][tx]);
+    mb[(size_t)b * rows + l] = m;
+  }
 }
 
 // Column sides: one thread per complex entry (grid (entry blocks over Kp/2, cols, batch)).
@@ -744,51 +753,74 @@ struct OutArgs {
 // 2^e for the exponents that occur here (a normal FP64 number)
 __device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 
-// C_ij = alpha (Re + i Im) scale + beta C_ij, the splits added in a fixed order (the FP64 class's
-// 64-bit integer sums are exact in any order).  grid (row blocks of 128, n, batch): the partial
-// reads ([split][column][row]) and the writes of C (column-major) are coalesced.
-__global__ void __launch_bounds__(128) k_zgemm_out(OutArgs a) {
-  const int b = blockIdx.z, j = blockIdx.y;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// C_ij = alpha (Re + i Im) scale + beta C_ij.  Block (64 rows, 4 thread groups), grid (row
+// blocks, n or n / 4, batch).  With four or more splits group g adds the splits g, g + 4, ...
+// of one column and the four group sums are added in the order g = 0..3; otherwise each group
+// adds every split of its own column.  Deterministic (the FP64 class's 64-bit integer sums are
+// exact in any order).  Partial reads ([split][column][row]) and writes of C are coalesced.
+template <typename T, typename Acc>
+__device__ __forceinline__ void sum_splits(const T* P, int nsplit, int g, int step, int64_t split_stride, size_t oR,
+                                           size_t oI, Acc& re, Acc& im) {
+  Acc r0 = 0, r1 = 0, i0 = 0, i1 = 0;
+  int s = g;
+  for (; s + step < nsplit; s += 2 * step) {
+    const size_t o0 = (size_t)s * split_stride, o1 = o0 + (size_t)step * split_stride;
+    r0 += (Acc)P[o0 + oR];
+    i0 += (Acc)P[o0 + oI];
+    r1 += (Acc)P[o1 + oR];
+    i1 += (Acc)P[o1 + oI];
+  }
+  if (s < nsplit) {
+    r0 += (Acc)P[(size_t)s * split_stride + oR];
+    i0 += (Acc)P[(size_t)s * split_stride + oI];
+  }
+  re = r0 + r1;
+  im = i0 + i1;
+}
+
+__global__ void __launch_bounds__(256) k_zgemm_out(OutArgs a) {
+  __shared__ double sre[4][64], sim[4][64];
+  __shared__ long long ire[4][64], iim[4][64];
+  const int b = blockIdx.z, r = threadIdx.x, g = threadIdx.y;
+  const int i = blockIdx.x * 64 + r;
+  // four or more splits: the four thread groups share one column's splits; fewer: each group
+  // takes its own column (four columns per CTA) and all of its splits
+  const bool by_split = a.nsplit >= 4;
+  const int j = by_split ? blockIdx.y : blockIdx.y * 4 + g;
+  const int gs = by_split ? g : 0, gstep = by_split ? 4 : 1;
+  if (!by_split && j >= a.n) return;
+  const size_t oR = (size_t)j * a.ldp, oI = (size_t)(a.n + j) * a.ldp;
+  long long ir = 0, ii = 0;
+  double dr = 0.0, di = 0.0;
+  if (i < a.m) {
+    if (a.cls == 0)
+      sum_splits(reinterpret_cast<const long long*>(a.part) + (size_t)b * a.batch_stride + i, a.nsplit, gs, gstep,
+                 a.split_stride, oR, oI, ir, ii);
+    else
+      sum_splits(reinterpret_cast<const float*>(a.part) + (size_t)b * a.batch_stride + i, a.nsplit, gs, gstep,
+                 a.split_stride, oR, oI, dr, di);
+  }
+  if (by_split) {
+    ire[g][r] = ir;
+    iim[g][r] = ii;
+    sre[g][r] = dr;
+    sim[g][r] = di;
+    __syncthreads();
+    if (g != 0) return;
+    ir = ire[0][r] + ire[1][r] + ire[2][r] + ire[3][r];
+    ii = iim[0][r] + iim[1][r] + iim[2][r] + iim[3][r];
+    dr = ((sre[0][r] + sre[1][r]) + sre[2][r]) + sre[3][r];
+    di = ((sim[0][r] + sim[1][r]) + sim[2][r]) + sim[3][r];
+  }
   if (i >= a.m) return;
   double re, im, sc;
   if (a.cls == 0) {
-    const long long* P = reinterpret_cast<const long long*>(a.part) + (size_t)b * a.batch_stride + i;
-    const size_t oR = (size_t)j * a.ldp, oI = (size_t)(a.n + j) * a.ldp;
-    long long r0 = 0, r1 = 0, i0 = 0, i1 = 0;
-    int s = 0;
-    for (; s + 1 < a.nsplit; s += 2) {
-      const size_t o0 = (size_t)s * a.split_stride, o1 = o0 + a.split_stride;
-      r0 += P[o0 + oR];
-      i0 += P[o0 + oI];
-      r1 += P[o1 + oR];
-      i1 += P[o1 + oI];
-    }
-    if (s < a.nsplit) {
-      r0 += P[(size_t)s * a.split_stride + oR];
-      i0 += P[(size_t)s * a.split_stride + oI];
-    }
-    re = (double)(r0 + r1);
-    im = (double)(i0 + i1);
+    re = (double)ir;
+    im = (double)ii;
     sc = a.alpha * pow2(a.exA[(size_t)b * a.m + i] + a.exB[(size_t)b * a.n + j] - a.fix_unit);
   } else {
-    const float* P = reinterpret_cast<const float*>(a.part) + (size_t)b * a.batch_stride + i;
-    const size_t oR = (size_t)j * a.ldp, oI = (size_t)(a.n + j) * a.ldp;
-    double r0 = 0.0, r1 = 0.0, i0 = 0.0, i1 = 0.0;
-    int s = 0;
-    for (; s + 1 < a.nsplit; s += 2) {
-      const size_t o0 = (size_t)s * a.split_stride, o1 = o0 + a.split_stride;
-      r0 += (double)P[o0 + oR];
-      i0 += (double)P[o0 + oI];
-      r1 += (double)P[o1 + oR];
-      i1 += (double)P[o1 + oI];
-    }
-    if (s < a.nsplit) {
-      r0 += (double)P[(size_t)s * a.split_stride + oR];
-      i0 += (double)P[(size_t)s * a.split_stride + oI];
-    }
-    re = r0 + r1;
-    im = i0 + i1;
+    re = dr;
+    im = di;
     sc = a.alpha;
   }
   double2* c = a.C + (size_t)b * a.sC + (size_t)j * a.ldc + i;
@@ -865,9 +897,9 @@ static cudaError_t zgemm_run(ZgemmWork* w, cudaStream_t st, int cls, bool transA
   const int KC = 32;   // reduction entries per stage in both classes
   const int mt = (Mr + ZG_BM - 1) / ZG_BM, nt = (Nr + BN - 1) / BN;
   const int kchunks = (int)(Kp / KC);
-  // reduction splits: about one wave of CTAs, each at least 4 chunks
+  // reduction splits: about one wave of CTAs, each at least 4 chunks, at most 32 splits
   const int tiles = mt * nt * batch;
-  int nsplit = std::max(1, std::min(std::max(1, kchunks / 4), (w->nsm + tiles - 1) / tiles));
+  int nsplit = std::max(1, std::min({32, std::max(1, kchunks / 4), (w->nsm + tiles - 1) / tiles}));
   const int cps = (kchunks + nsplit - 1) / nsplit;
   nsplit = (kchunks + cps - 1) / cps;
   const int64_t ldp = (int64_t)mt * ZG_BM;
@@ -945,7 +977,7 @@ static cudaError_t zgemm_run(ZgemmWork* w, cudaStream_t st, int cls, bool transA
       if (transA)
         k_colmax<<<dim3(segs, m, nb), 256, 0, st>>>(sa.X, lda, sA, k, m, mbA);
       else
-        k_rowmax<<<dim3((m + 255) / 256, nb), 256, 0, st>>>(sa.X, lda, sA, m, k, mbA);
+        k_rowmax<<<dim3((m + 31) / 32, nb), dim3(32, 8), 0, st>>>(sa.X, lda, sA, m, k, mbA);
       k_colmax<<<dim3(segs, n, nb), 256, 0, st>>>(sb.X, ldb, sB, k, n, mbB);
       *launches += 2;
     }
@@ -1005,7 +1037,7 @@ static cudaError_t zgemm_run(ZgemmWork* w, cudaStream_t st, int cls, bool transA
     oa.C = C + (size_t)b0 * sC;
     oa.ldc = ldc;
     oa.sC = sC;
-    k_zgemm_out<<<dim3((m + 127) / 128, n, nb), 128, 0, st>>>(oa);
+    k_zgemm_out<<<dim3((m + 63) / 64, nsplit >= 4 ? n : (n + 3) / 4, nb), dim3(64, 4), 0, st>>>(oa);
     *launches += 4;
   }
   return cudaGetLastError();

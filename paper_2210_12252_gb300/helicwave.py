@@ -72,6 +72,8 @@ _SIGS = {
                               C.POINTER(C.c_int)]),
     "hw_heev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                           C.c_int]),
+    "hw_get_residual_history": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), _D, C.c_int,
+                                         C.POINTER(C.c_int)]),
     "hw_selftest_barrier": (C.c_int, [C.c_void_p, C.c_int, C.c_longlong, C.c_int, C.POINTER(C.c_int)]),
     "hw_density": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_void_p), C.c_int, C.c_int64,
                              _D, _D, C.c_void_p, C.c_int]),
@@ -330,6 +332,22 @@ def hw_heev(h, A, nw, method=1):
     _check(h, load_library().hw_heev(h, n, nprob, nw, C.c_void_p(A.data_ptr()), C.c_void_p(w.data_ptr()),
                                      C.c_void_p(Z.data_ptr()), method))
     return w, Z
+
+
+HW_HIST_FILTER_FP32, HW_HIST_FILTER_FP64, HW_HIST_LOBPCG_FP32, HW_HIST_LOBPCG_HYBRID, HW_HIST_LOBPCG_FP64 = range(5)
+HIST_PHASES = ["filter_fp32", "filter_fp64", "lobpcg_fp32", "lobpcg_hybrid", "lobpcg_fp64"]
+
+
+def hw_get_residual_history(h, k):
+    """Residual history of the last solve at k-point k: list of (phase name, largest wanted
+    residual) per filter cycle / LOBPCG iteration."""
+    n = C.c_int(0)
+    _check(h, load_library().hw_get_residual_history(h, k, None, None, 0, C.byref(n)))
+    ph = np.zeros(max(n.value, 1), dtype=np.int32)
+    res = np.zeros(max(n.value, 1))
+    _check(h, load_library().hw_get_residual_history(h, k, ph.ctypes.data_as(C.POINTER(C.c_int)), _dptr(res),
+                                                      n.value, C.byref(n)))
+    return [(HIST_PHASES[int(p)], float(r)) for p, r in zip(ph[:n.value], res[:n.value])]
 
 
 def hw_selftest_barrier(h, nblocks, spin_limit, skip_block):
