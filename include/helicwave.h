@@ -394,12 +394,17 @@ typedef enum {
   HW_OPT_WINDOW = 11,       /* hw_solve_eigs: largest number of eigenpairs one block solves,
                                1..100; 0 (default) means 80.  More eigenpairs than this are
                                solved in consecutive windows of equal size (see hw_solve_eigs). */
-  HW_OPT_TC_GEMM = 12       /* the eigensolver's block products: 1 (default) the tensor-core
+  HW_OPT_TC_GEMM = 12,      /* the eigensolver's block products: 1 (default) the tensor-core
                                kernel of hw_block_product (FP64 class in the FP64 phases, FP32
                                class in the FP32-product phase) for every product with an extent
                                over the basis dimension (m or k >= 1024), cuBLAS for the small
                                dense products of the Rayleigh-Ritz step; 2 the tensor-core kernel
                                for every product; 0 cuBLAS (ZGEMM, or CGEMM on FP32 copies). */
+  HW_OPT_RADIAL_KERNEL = 13 /* radial transforms of the mixed-precision H X: 1 (default) on the
+                               tensor cores (3 x TF32 tcgen05 MMAs, one CTA per 64 (column,
+                               pair) items of an |n| group; the forward kernel of launches with
+                               nu != 0 stays on the FP32 SIMT kernel); 0 the FP32 SIMT kernels.
+                               FP64 H X always uses the FP64 SIMT kernels. */
 } hw_option;
 /* Set an option (HW_EINVAL for an unknown option, a read-only one or a bad value). */
 hw_status hw_set_option(hw_ctx* ctx, int option, int value);

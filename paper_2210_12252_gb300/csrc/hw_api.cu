@@ -104,6 +104,9 @@ void free_basis(hw_ctx* ctx) {
   for (auto* t : {&db.t32.rinv, &db.t32.rfwd, &db.t32.qtab, &db.t32.rder, &db.t32.V, &db.t32.tw1, &db.t32.tw2})
     dfree(*t);
   dfree(db.rnodes);
+  dfree(db.rt_inv);
+  dfree(db.rt_fwd);
+  db.rt_ok = false;
   dfree(ctx->ws.gbuf);
   dfree(ctx->ws.hbuf);
   ctx->ws.cols = 0;
@@ -243,6 +246,7 @@ hw_status hw_setup_basis(hw_ctx* ctx, const hw_basis_params* params, int nk, con
     if (e == cudaSuccess) e = cudaMalloc((void**)&db.t64.V, grid * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void**)&db.t32.V, grid * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&db.vscratch, grid * sizeof(double));
+    if (e == cudaSuccess) e = radial_tc_setup(ctx, hb, rinv, rfwd);
     // G / H workspace: passes of up to `cols` columns, ~1 GiB for both buffers
     const size_t per_col = 2 * (size_t)Nr * hb.nA * sizeof(double2);
     size_t cols = std::max<size_t>(16, std::min<size_t>(2048, (size_t(1) << 30) / per_col));
@@ -592,6 +596,11 @@ hw_status hw_set_option(hw_ctx* ctx, int option, int value) {
     ctx->tc_gemm = value;
     return HW_OK;
   }
+  if (option == HW_OPT_RADIAL_KERNEL) {
+    if (value != 0 && value != 1) return hw_fail(ctx, HW_EINVAL, "radial kernel option 0 (SIMT) or 1 (tensor cores)");
+    ctx->radial_tc = value;
+    return HW_OK;
+  }
   return hw_fail(ctx, HW_EINVAL, "unknown or read-only option");
 }
 
@@ -610,6 +619,7 @@ hw_status hw_get_option(hw_ctx* ctx, int option, long long* value) {
   if (option == HW_OPT_SLAB_KERNEL) { *value = ctx->slab_r16; return HW_OK; }
   if (option == HW_OPT_WINDOW) { *value = ctx->window; return HW_OK; }
   if (option == HW_OPT_TC_GEMM) { *value = ctx->tc_gemm; return HW_OK; }
+  if (option == HW_OPT_RADIAL_KERNEL) { *value = ctx->radial_tc; return HW_OK; }
   return hw_fail(ctx, HW_EINVAL, "unknown option");
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cublas_v2.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -38,6 +39,11 @@ struct DevBasis {
   double* vscratch = nullptr;  // [grid] staging for set_potential
   DevTables<double> t64;
   DevTables<float> t32;
+  // tensor-core radial transforms of the FP32 H X: BF16 three-part tables per |n| group
+  __nv_bfloat16* rt_inv = nullptr;   // [(N+1)][3][rt_npad][rt_kb * 32]   xi rows p, columns k
+  __nv_bfloat16* rt_fwd = nullptr;   // [(N+1)][3][rt_kpad][rt_kbp * 32]  O rows k, columns p
+  int rt_npad = 0, rt_kb = 0, rt_kpad = 0, rt_kbp = 0;
+  bool rt_ok = false;          // the shapes fit the kernels (N_r <= 256, K <= 64)
 };
 
 // G / H intermediates for `cols` columns per pass, [column][r_p][pair] complex FP64-sized
@@ -115,6 +121,7 @@ struct hw_ctx {
   int tail_no_p = 0;           // HW_OPT_TAIL_NO_P
   int window = 0;              // HW_OPT_WINDOW (0: 100)
   int slab_r16 = 1;            // HW_OPT_SLAB_KERNEL
+  int radial_tc = 1;           // HW_OPT_RADIAL_KERNEL
   int64_t rr_fallbacks = 0;    // Householder results rejected by the check (Jacobi used)
   // residual history of the last hw_solve_eigs: per k-point slot, per iteration (filter cycle
   // or LOBPCG iteration) the phase code (HW_HIST_*) and the largest wanted residual
@@ -155,6 +162,13 @@ cudaError_t hx_autotune(hw_ctx* ctx, int k, int ns, std::vector<float>& log);
 template <typename T>
 cudaError_t launch_hx_into(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, void* gbuf, void* hbuf, int cols);
 cudaError_t launch_tpa(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld);
+// tensor-core radial transforms of the FP32 H X (hw_radial_tc.cu)
+cudaError_t radial_tc_setup(hw_ctx* ctx, const HostBasis& hb, const std::vector<double>& rinv,
+                            const std::vector<double>& rfwd);
+cudaError_t launch_rinv_tc(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, int nc, int c0, void* gbuf,
+                           int scale_mode);
+cudaError_t launch_rfwd_tc(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, int nc, int c0, void* hbuf,
+                           const ChebStep* step);
 // C = alpha op(A) B + beta C on the tensor cores (hw_zgemm.cu): cls 0 FP64 class, 1 FP32 class
 cudaError_t zgemm_tc(ZgemmWork*& w, cudaStream_t st, int cls, bool transA, int m, int n, int k, double alpha,
                      const double2* A, int64_t lda, int64_t sA, const double2* B, int64_t ldb, int64_t sB,

@@ -274,25 +274,47 @@ __global__ void __launch_bounds__(RAD_THREADS, sizeof(T) == 4 ? 2 : 1) k_radial_
     const int p = i / Kp, k = i - p * Kp;
     Rs[i] = k < K ? tab[(size_t)p * K + k] : T(0);
   }
-  // gather the kept coefficients of each item (zero beyond Ka)
-  for (int i = threadIdx.x; i < RAD_Q * Kp; i += blockDim.x) {
-    const int q = i / Kp, k = i - q * Kp;
+  // per item: where its kept coefficients start, how many there are, and the derivative scale
+  // (one thread per item, so the element loop below has no dependent index loads)
+  __shared__ const double* s_x[RAD_Q];
+  __shared__ int s_ka[RAD_Q];
+  __shared__ T s_sc[RAD_Q];
+  if (threadIdx.x < RAD_Q) {
+    const int q = threadIdx.x;
     const long item = q0 + q;
-    V v = mk<T>(T(0), T(0));
+    const double* xp = nullptr;
+    int ka = 0;
+    T sc = T(0);
     if (item < nitems) {
       const int c = (int)(item / na), a = gs + (int)(item - (long)c * na);
       const int cg = A.c0 + c;
-      const int slot = cg / A.ns, s = cg - slot * A.ns;
+      const int slot = cg / A.ns, sl = cg - slot * A.ns;
       const int kb = A.blk.kb[slot];
-      const int ka = A.Ka[(size_t)kb * A.nA + a];
-      if (k < ka) {
-        const double* x = A.blk.x[slot] + 2 * ((size_t)A.off[(size_t)kb * A.nA + a] + k + (size_t)s * A.ld);
-        v = mk<T>(T(x[0]), T(x[1]));
-        if (A.scale_mode != 0) {   // times i s
-          const T sc = T(6.283185307179586 * (A.scale_mode == 1 ? (double)A.mrow_m[A.pair_mrow[a]]
-                                                                 : (double)A.pair_n[a] * A.ncyc));
-          v = mk<T>(-sc * v.y, sc * v.x);
-        }
+      ka = A.Ka[(size_t)kb * A.nA + a];
+      xp = A.blk.x[slot] + 2 * ((size_t)A.off[(size_t)kb * A.nA + a] + (size_t)sl * A.ld);
+      if (A.scale_mode != 0)
+        sc = T(6.283185307179586 * (A.scale_mode == 1 ? (double)A.mrow_m[A.pair_mrow[a]]
+                                                       : (double)A.pair_n[a] * A.ncyc));
+    }
+    s_x[q] = xp;
+    s_ka[q] = ka;
+    s_sc[q] = sc;
+  }
+  __syncthreads();
+  // gather the kept coefficients of each item (zero beyond Ka); independent loads, unrolled
+#pragma unroll 4
+  for (int i = threadIdx.x; i < RAD_Q * Kp; i += blockDim.x) {
+    const int q = i / Kp, k = i - q * Kp;
+    V v = mk<T>(T(0), T(0));
+    if (k < s_ka[q]) {
+      const double* x = s_x[q] + 2 * k;
+      if constexpr (sizeof(T) == 4)
+        v = mk<T>(d2f(x[0]), d2f(x[1]));
+      else
+        v = mk<T>(x[0], x[1]);
+      if (A.scale_mode != 0) {   // times i s
+        const T sc = s_sc[q];
+        v = mk<T>(-sc * v.y, sc * v.x);
       }
     }
     Xs[k * RAD_Q + q] = v;
@@ -381,6 +403,37 @@ __global__ void __launch_bounds__(RAD_THREADS, sizeof(T) == 4 ? 2 : 1) k_radial_
     const int k = i / Nrp, pp = i - k * Nrp;
     Rs[i] = pp < Nr ? tab[(size_t)k * Nr + pp] : T(0);
   }
+  // per item: its H column (the (r, pair) intermediate at r_0), its coefficient offset in X / Y,
+  // block slot and kept count (one thread per item; the loops below index these from shared
+  // memory instead of chains of dependent global loads)
+  __shared__ const V* s_h[RAD_Q];
+  __shared__ int64_t s_o[RAD_Q], s_cs[RAD_Q];
+  __shared__ int s_ka[RAD_Q], s_slot[RAD_Q];
+  if (threadIdx.x < RAD_Q) {
+    const int qq = threadIdx.x;
+    const long it = q0 + qq;
+    const V* hp = nullptr;
+    int64_t o = 0, cs = 0;
+    int ka = 0, slot = 0, aa = gs;
+    if (it < nitems) {
+      const int cc = (int)(it / na);
+      aa = gs + (int)(it - (long)cc * na);
+      const int cg = A.c0 + cc;
+      slot = cg / A.ns;
+      const int sl = cg - slot * A.ns;
+      const int kb = A.blk.kb[slot];
+      ka = A.Ka[(size_t)kb * A.nA + aa];
+      o = (int64_t)A.off[(size_t)kb * A.nA + aa];
+      cs = (int64_t)sl * A.ld;
+      hp = A.gh + (size_t)cc * Nr * A.nA + aa;
+    }
+    s_h[qq] = hp;
+    s_o[qq] = o;
+    s_cs[qq] = cs;
+    s_ka[qq] = ka;
+    s_slot[qq] = slot;
+  }
+  __syncthreads();
   const int q = threadIdx.x % RAD_Q;
   const int kg = threadIdx.x / RAD_Q;                      // 4 groups of k
   constexpr int KG = RAD_THREADS / RAD_Q;
@@ -397,14 +450,12 @@ __global__ void __launch_bounds__(RAD_THREADS, sizeof(T) == 4 ? 2 : 1) k_radial_
   for (int p0 = 0; p0 < Nr; p0 += PC) {
     const int pc = min(PC, Nr - p0);
     __syncthreads();
+#pragma unroll 4
     for (int i = threadIdx.x; i < PC * RAD_Q; i += blockDim.x) {   // zero past pc
       const int pp = i / RAD_Q, qq = i - pp * RAD_Q;
-      const long it = q0 + qq;
       V v = mk<T>(T(0), T(0));
-      if (it < nitems && pp < pc) {
-        const int cc = (int)(it / na), aa = gs + (int)(it - (long)cc * na);
-        v = A.gh[((size_t)cc * Nr + p0 + pp) * A.nA + aa];
-      }
+      const V* hp = s_h[qq];
+      if (hp && pp < pc) v = hp[(size_t)(p0 + pp) * A.nA];
       Hs[pp * RAD_Q + qq] = v;
     }
     __syncthreads();
@@ -451,19 +502,14 @@ __global__ void __launch_bounds__(RAD_THREADS, sizeof(T) == 4 ? 2 : 1) k_radial_
   if (!A.any_nu) {
     // scatter without nu terms: (item, k) pairs over all threads, several independent global
     // round trips in flight per thread
-#pragma unroll 2
+#pragma unroll 4
     for (int idx = threadIdx.x; idx < RAD_Q * K; idx += RAD_THREADS) {
       const int qq = idx / K, k = idx - qq * K;
-      const long it = q0 + qq;
-      if (it >= nitems) continue;
-      const int cc = (int)(it / na), aa = gs + (int)(it - (long)cc * na);
-      const int cg = A.c0 + cc;
-      const int slot = cg / A.ns, s = cg - slot * A.ns;
-      const int kb = A.blk.kb[slot];
-      if (k >= A.Ka[(size_t)kb * A.nA + aa]) continue;
-      const size_t o = (size_t)A.off[(size_t)kb * A.nA + aa] + k;
-      const double* x = A.blk.x[slot] + 2 * (o + (size_t)s * A.ld);   // 8-byte aligned (ABI)
-      double* y = A.blk.y[slot] + 2 * (o + (size_t)s * A.ld);
+      if (k >= s_ka[qq]) continue;
+      const int slot = s_slot[qq];
+      const int64_t o = s_o[qq] + k;   // compact index of coefficient k of the item
+      const double* x = A.blk.x[slot] + 2 * (o + s_cs[qq]);   // 8-byte aligned (ABI)
+      double* y = A.blk.y[slot] + 2 * (o + s_cs[qq]);
       const double d = A.ke[A.keoff[slot] + o];
       const V h = Ys[qq * (K + 1) + k];
       const double x0 = x[0], x1 = x[1];
@@ -915,9 +961,15 @@ static cudaError_t launch_hx_bufs(hw_ctx* ctx, const Blocks& blk, int ns, int64_
     ra.rtab = tb.rinv;
     dim3 grid((unsigned)(((long)maxna * nc + RAD_Q - 1) / RAD_Q), hb.N + 1);
     const size_t sm_inv = rad_inv_smem(Nr, K, sizeof(T));
+    const bool tc = sizeof(T) == 4 && ctx->radial_tc && db.rt_ok;
     {
       ProfScope ps(ctx, HW_PH_RADIAL_INV);
-      k_radial_inv<T><<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra);
+      if (tc) {
+        const cudaError_t e = launch_rinv_tc(ctx, blk, ns, ld, nc, c0, gbuf, 0);
+        if (e != cudaSuccess) return e;
+      } else {
+        k_radial_inv<T><<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra);
+      }
       ctx->launches++;
     }
     SlabArgs<T> sa;
@@ -954,7 +1006,12 @@ static cudaError_t launch_hx_bufs(hw_ctx* ctx, const Blocks& blk, int ns, int64_
     const size_t sm_fwd = rad_fwd_smem(Nr, K, sizeof(T));
     {
       ProfScope ps(ctx, HW_PH_RADIAL_FWD);
-      k_radial_fwd<T><<<grid, RAD_THREADS, sm_fwd, ctx->stream>>>(ra);
+      if (tc && !ra.any_nu) {
+        const cudaError_t e = launch_rfwd_tc(ctx, blk, ns, ld, nc, c0, hbuf, step);
+        if (e != cudaSuccess) return e;
+      } else {
+        k_radial_fwd<T><<<grid, RAD_THREADS, sm_fwd, ctx->stream>>>(ra);
+      }
       ctx->launches++;
     }
   }

@@ -50,6 +50,7 @@
 
 #include "hw_common.cuh"
 #include "hw_ctx.h"
+#include "hw_tc.cuh"
 
 namespace hw {
 
@@ -69,7 +70,6 @@ inline int zg_fix_unit(int64_t Kp) {
   return std::min(56, 61 - l);
 }
 constexpr int ZG_THREADS = 320;     // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (2 per TMEM lane quadrant)
-constexpr long ZG_SPIN = 1L << 22;  // polls (with ~64 ns sleeps) before a wait gives up
 
 template <int CLS>
 constexpr size_t zg_stage_bytes() {
@@ -81,87 +81,6 @@ constexpr size_t zg_smem_bytes() {
 }
 __host__ __device__ constexpr size_t tf_stage_bytes() { return (size_t)TF_PLANES * (ZG_BM + TF_BN_MAX) * 128; }
 __host__ __device__ constexpr size_t tf_smem_bytes() { return (size_t)TF_STAGES * tf_stage_bytes() + 1024; }
-
-// ----------------------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-// true once the phase of the given parity has completed; false after ZG_SPIN polls
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-  const uint32_t a = smem_u32(b);
-  for (long i = 0; i < ZG_SPIN; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    __nanosleep(64);
-  }
-  return false;
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
-          smem_u32(dst)),
-      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-      : "memory");
-}
-// shared-memory matrix descriptor: K-major operand tile, rows of SWZ bytes swizzled in 8-row
-// atoms (SWZ = 128 or 64), consecutive 8-row atoms 8 * SWZ bytes apart
-template <int SWZ>
-__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
-  uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)((8 * SWZ) >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)(SWZ == 128 ? 2 : 4) << 61;
-  return d;
-}
-// instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M = 128, N = n
-__host__ __device__ constexpr uint32_t umma_idesc_bf16(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(ZG_BM >> 4) << 24);
-}
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          tmem_d),
-      "l"(da), "l"(db), "r"(idesc), "r"(accum));
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // ----------------------------------------------------------------------------- digit planes
 // |x| as the ordered bit pattern of the magnitude (max of non-negative doubles = max of bits);
@@ -210,13 +129,6 @@ __device__ __forceinline__ void digits_of(long long N, float (&d)[S]) {
   d[0] += (float)(N << BITS);   // N is zero here for |x| 2^-e < 1/2; kept for exactness
 }
 
-// TF32 rounding of an FP32 number: 10 explicit mantissa bits, to nearest (ties to even); the
-// tensor core reads the upper 19 bits of the container, which are then exact
-__device__ __forceinline__ float tf32_rn(float x) {
-  uint32_t u = __float_as_uint(x);
-  if ((u & 0x7F800000u) != 0x7F800000u) u = (u + 0x0FFFu + ((u >> 13) & 1u)) & 0xFFFFE000u;
-  return __uint_as_float(u);
-}
 // x = hi + lo + r, |r| <= 2^-22 |x| (FP64 -> FP32 by bit operations, one FP64 subtraction)
 __device__ __forceinline__ void tf32_split(double x, float& hi, float& lo) {
   hi = tf32_rn(d2f(x));
@@ -589,17 +501,6 @@ __global__ void __launch_bounds__(ZG_THREADS, 1)
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
   }
-}
-
-// TF32 x TF32 -> FP32 instruction descriptor: both operands K-major, M = 128, N = n
-__host__ __device__ constexpr uint32_t umma_idesc_tf32(int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(ZG_BM >> 4) << 24);
-}
-__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          tmem_d),
-      "l"(da), "l"(db), "r"(idesc), "r"(accum));
 }
 
 // FP32 class: per stage the hi / lo TF32 planes of a 128 x 32 tile of A and a BN x 32 tile of B

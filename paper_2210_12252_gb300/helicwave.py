@@ -274,6 +274,7 @@ HW_OPT_SLAB_KERNEL = 9
 HW_OPT_TAIL_NO_P = 10
 HW_OPT_WINDOW = 11
 HW_OPT_TC_GEMM = 12
+HW_OPT_RADIAL_KERNEL = 13
 
 
 def hw_set_option(h, option, value):
