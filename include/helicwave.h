@@ -381,10 +381,16 @@ typedef enum {
   HW_OPT_CHEB_LOCK = 8,     /* 1 (default): leading Ritz columns whose residuals are below half
                                the phase's target are not filtered (soft locking); 0: every
                                column is filtered every cycle. */
-  HW_OPT_SLAB_KERNEL = 9,   /* FP32 angular kernel on the 64 x 48 grid: 1 (default) the theta1
-                               transforms split 64 = 4 x 16 over the 4 lanes of a theta2 row
-                               (register DFTs, shuffles), 0 the Stockham FFTs (every other grid
-                               and FP64 use the FFTs). */
+  HW_OPT_SLAB_KERNEL = 9,   /* angular kernel on the 64 x 48 grid (Algorithms 2 and 4 with the
+                               potential multiply): 2 (default) every transform in registers for
+                               FP32 -- theta2 as 4 lanes x 12-point DFTs joined by a 4-point DFT
+                               across the lanes, theta1 as 4 lanes x 16-point DFTs, several
+                               slabs per CTA -- and for FP64 the 1 kernel; 3 the register kernel
+                               in both precisions; 1 the theta1 transforms split 64 = 4 x 16 over
+                               the 4 lanes of a theta2 point with Stockham theta2 passes in
+                               shared memory; 0 the Stockham FFTs throughout.  The register
+                               kernel needs at most 16 kept m rows, consecutive in m; other
+                               bases take 1.  Every other grid uses the Stockham FFTs. */
   HW_OPT_TAIL_NO_P = 10,    /* Chebyshev solver, mixed form: 1 starts the LOBPCG end phase
                                without conjugate directions (Rayleigh-Ritz on [X W], each
                                iteration cheaper) and switches them on for good once an

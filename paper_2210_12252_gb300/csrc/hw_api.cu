@@ -582,7 +582,9 @@ hw_status hw_set_option(hw_ctx* ctx, int option, int value) {
     return HW_OK;
   }
   if (option == HW_OPT_SLAB_KERNEL) {
-    if (value != 0 && value != 1) return hw_fail(ctx, HW_EINVAL, "slab kernel option 0 (FFT) or 1 (4 x 16)");
+    if (value < 0 || value > 3)
+      return hw_fail(ctx, HW_EINVAL,
+                     "slab kernel option 0 (FFT), 1 (4 x 16), 2 (registers, FP32) or 3 (registers, both)");
     ctx->slab_r16 = value;
     return HW_OK;
   }

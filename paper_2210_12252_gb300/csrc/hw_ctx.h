@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cublas_v2.h>
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -44,6 +45,8 @@ struct DevBasis {
   __nv_bfloat16* rt_fwd = nullptr;   // [(N+1)][3][rt_kpad][rt_kbp * 32]  O rows k, columns p
   int rt_npad = 0, rt_kb = 0, rt_kpad = 0, rt_kbp = 0;
   bool rt_ok = false;          // the shapes fit the kernels (N_r <= 256, K <= 64)
+  // TMA maps over the two tables: 3-D {32-column block, rows, group x part}, 64-byte swizzle
+  CUtensorMap rt_map_inv, rt_map_fwd;
 };
 
 // G / H intermediates for `cols` columns per pass, [column][r_p][pair] complex FP64-sized
@@ -120,7 +123,7 @@ struct hw_ctx {
   int cheb_lock = 1;           // HW_OPT_CHEB_LOCK
   int tail_no_p = 0;           // HW_OPT_TAIL_NO_P
   int window = 0;              // HW_OPT_WINDOW (0: 100)
-  int slab_r16 = 1;            // HW_OPT_SLAB_KERNEL
+  int slab_r16 = 2;            // HW_OPT_SLAB_KERNEL
   int radial_tc = 1;           // HW_OPT_RADIAL_KERNEL
   int64_t rr_fallbacks = 0;    // Householder results rejected by the check (Jacobi used)
   // residual history of the last hw_solve_eigs: per k-point slot, per iteration (filter cycle
@@ -163,6 +166,11 @@ template <typename T>
 cudaError_t launch_hx_into(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, void* gbuf, void* hbuf, int cols);
 cudaError_t launch_tpa(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld);
 // tensor-core radial transforms of the FP32 H X (hw_radial_tc.cu)
+// 3-D TMA map over [planes][rows][Kp] BF16 (fp32 = false) or FP32 elements, box
+// {swz / element size, box_rows, box_planes}, swz = 64 or 128-byte swizzle; false if the driver
+// entry point is missing or the shape is rejected
+bool make_plane_map(CUtensorMap* m, const void* base, bool fp32, int64_t Kp, int rows, int planes, int box_rows,
+                    int box_planes, int swz);
 cudaError_t radial_tc_setup(hw_ctx* ctx, const HostBasis& hb, const std::vector<double>& rinv,
                             const std::vector<double>& rfwd);
 cudaError_t launch_rinv_tc(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, int nc, int c0, void* gbuf,

@@ -844,16 +844,262 @@ __global__ void __launch_bounds__(SLAB_THREADS) k_slab_r16(SlabArgs<T> A) {
     Hc[a] = r2[ix(A.pair_mrow[a] * n2 + pmod(A.pair_n[a], n2))];
 }
 
+// 12-point DFT in registers, X[k] = sum_n x[n] e^(S 2 pi i n k / 12), as 4-point DFTs over n1
+// (n = 3 n1 + n2), the twiddles e^(S 2 pi i n2 k1 / 12), then 3-point DFTs over n2 (k = k1 + 4 k2)
+template <int S, typename R>
+__device__ __forceinline__ void dft12(R (&xr)[12], R (&xi)[12]) {
+  constexpr R H3 = R(0.866025403784438646763723170752936183);   // sin(pi / 3)
+  // e^(2 pi i e / 12) for e = 0..6 (cos, sin); the sign S is applied to the sine
+  constexpr R wc[7] = {R(1), H3, R(0.5), R(0), R(-0.5), -H3, R(-1)};
+  constexpr R ws[7] = {R(0), R(0.5), H3, R(1), H3, R(0.5), R(0)};
+  R ar[12], ai[12];   // a[4 n2 + k1]
+#pragma unroll
+  for (int n2 = 0; n2 < 3; ++n2) {
+    const R x0r = xr[n2], x0i = xi[n2], x1r = xr[3 + n2], x1i = xi[3 + n2];
+    const R x2r = xr[6 + n2], x2i = xi[6 + n2], x3r = xr[9 + n2], x3i = xi[9 + n2];
+    const R t0r = x0r + x2r, t0i = x0i + x2i, t1r = x0r - x2r, t1i = x0i - x2i;
+    const R t2r = x1r + x3r, t2i = x1i + x3i;
+    const R dr = x1r - x3r, di = x1i - x3i;
+    const R t3r = -S * di, t3i = S * dr;   // (x1 - x3) (S i)
+    ar[4 * n2] = t0r + t2r;
+    ai[4 * n2] = t0i + t2i;
+    ar[4 * n2 + 1] = t1r + t3r;
+    ai[4 * n2 + 1] = t1i + t3i;
+    ar[4 * n2 + 2] = t0r - t2r;
+    ai[4 * n2 + 2] = t0i - t2i;
+    ar[4 * n2 + 3] = t1r - t3r;
+    ai[4 * n2 + 3] = t1i - t3i;
+  }
+#pragma unroll
+  for (int n2 = 1; n2 < 3; ++n2)
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1) {
+      const int e = n2 * k1;
+      const R c = wc[e], sn = S * ws[e];
+      const R r = ar[4 * n2 + k1], i = ai[4 * n2 + k1];
+      ar[4 * n2 + k1] = r * c - i * sn;
+      ai[4 * n2 + k1] = r * sn + i * c;
+    }
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    const R a0r = ar[k1], a0i = ai[k1];
+    const R sr = ar[4 + k1] + ar[8 + k1], si = ai[4 + k1] + ai[8 + k1];
+    const R dr = ar[4 + k1] - ar[8 + k1], di = ai[4 + k1] - ai[8 + k1];
+    const R tr = a0r - R(0.5) * sr, ti = a0i - R(0.5) * si;
+    const R ur = -S * H3 * di, ui = S * H3 * dr;   // (a1 - a2) S i sin(pi / 3)
+    xr[k1] = a0r + sr;
+    xi[k1] = a0i + si;
+    xr[k1 + 4] = tr + ur;
+    xi[k1 + 4] = ti + ui;
+    xr[k1 + 8] = tr - ur;
+    xi[k1 + 8] = ti - ui;
+  }
+}
+
+// 4-point DFT across the 4 lanes q = q0 + 2 q1 of an aligned quad, X[d] = sum_q v_q (S i)^(q d),
+// as two radix-2 steps over the lane bits; lane q ends with X[q1 + 2 q0]
+template <int S, typename R>
+__device__ __forceinline__ void quad_dft(R& vr, R& vi, int q) {
+  R pr = __shfl_xor_sync(0xffffffffu, vr, 2), pi = __shfl_xor_sync(0xffffffffu, vi, 2);
+  if (q & 2) {
+    vr = pr - vr;
+    vi = pi - vi;
+  } else {
+    vr += pr;
+    vi += pi;
+  }
+  if (q == 3) {   // (S i)^(q0 d0) with q0 = d0 = 1
+    const R t = vr;
+    vr = -S * vi;
+    vi = S * t;
+  }
+  pr = __shfl_xor_sync(0xffffffffu, vr, 1);
+  pi = __shfl_xor_sync(0xffffffffu, vi, 1);
+  if (q & 1) {
+    vr = pr - vr;
+    vi = pi - vi;
+  } else {
+    vr += pr;
+    vi += pi;
+  }
+}
+
+// Slab kernel for the 64 x 48 grid with every transform in registers, SQ slabs (the columns
+// blockIdx.x * SQ .. of the radial node blockIdx.y) per CTA and two block barriers per CTA.
+//   theta2 (48 = 12 x 4): the 4 lanes of a (slab, kept row) quad hold the points n = 4 a + q
+//     (inverse: read from G through the (row, point) -> pair table) or j = c + 12 q (forward);
+//     a lane's 12-point DFT, the twiddles e^(+-2 pi i q c / 48) and a 4-point DFT across the
+//     quad by shuffles make the 48-point transform.
+//   theta1 (64 = 16 x 4): as in k_slab_r16, lane q of a (slab, theta2 point) quad owns the
+//     points 4 t + q; with the kept rows m_r = m_0 + r (r < nmr <= 16) the row values
+//     T_r omega^(m_r q) sit in DFT slot r: the inverse DFT then misses the factor W^(m_0 t) of
+//     the true bins m_r mod 16, and the forward DFT of row r, taken at slot r, misses
+//     W^(-m_0 t) -- the two cancel through the (real) potential multiply, so no bin table
+//     or shared-memory bins are needed; the 4 lanes' row sums are a reduce-scatter of 16
+//     values by shuffles (lane q ends with the rows 4 q .. 4 q + 3).
+// Tb[s][r][j]: the rows at the theta2 points, row stride SQ_RS = 49 (odd multiple of 16 + 1:
+// the quads' accesses spread over the banks).
+constexpr int SQ_RS = 49;
+
+template <typename T>
+__global__ void __launch_bounds__(SLAB_THREADS, sizeof(T) == 4 ? 2 : 1) k_slab_q(SlabArgs<T> A, int SQ) {
+  using V = cplx_t<T>;
+  constexpr int n1 = 64, n2 = 48;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nmr = A.nmr, p = blockIdx.y, c0 = blockIdx.x * SQ;
+  V* Tb = reinterpret_cast<V*>(smem_raw);   // [SQ][nmr][SQ_RS]
+  V* E4 = Tb + (size_t)SQ * nmr * SQ_RS;    // [16][4]: omega^(m_r q), zero past nmr
+  V* T48 = E4 + 64;                         // [48]: e^(-2 pi i t / 48)
+  for (int t = threadIdx.x; t < 64; t += blockDim.x) {
+    const int r = t >> 2, q = t & 3;
+    V e = mk<T>(T(0), T(0));
+    if (r < nmr) {
+      const V w = A.tw1[pmod(A.mrow_m[r] * q, n1)];   // e^{-2 pi i m q / 64}
+      e = mk<T>(w.x, -w.y);
+    }
+    E4[t] = e;
+  }
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) T48[t] = A.tw2[t];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, q = lane & 3;
+  const int nq2 = SQ * nmr * 4;   // theta2 lanes
+  // ---- inverse theta2: G -> Tb
+  if (threadIdx.x - lane < nq2) {
+    const int t = threadIdx.x, sr = t >> 2, s = sr / nmr, r = sr - s * nmr;
+    const int c = c0 + s;
+    const bool valid = t < nq2 && c < A.ncols;
+    const V* Gc = A.G + ((size_t)(valid ? c : 0) * A.Nr + p) * A.nA;
+    const int* sp = A.slot_pair + (size_t)(valid ? r : 0) * n2 + q;
+    T xr[12], xi[12];
+#pragma unroll
+    for (int a = 0; a < 12; ++a) {
+      const int pa = valid ? sp[4 * a] : -1;
+      V v = mk<T>(T(0), T(0));
+      if (pa >= 0) v = Gc[pa];
+      xr[a] = v.x;
+      xi[a] = v.y;
+    }
+    dft12<+1, T>(xr, xi);
+    V* row = Tb + ((size_t)s * nmr + r) * SQ_RS + 12 * ((q >> 1) + 2 * (q & 1));
+#pragma unroll
+    for (int cc = 0; cc < 12; ++cc) {
+      const V w = T48[q * cc];   // times e^{+2 pi i q c / 48}
+      T vr = xr[cc] * w.x + xi[cc] * w.y, vi = xi[cc] * w.x - xr[cc] * w.y;
+      quad_dft<+1, T>(vr, vi, q);
+      if (valid) row[cc] = mk<T>(vr, vi);
+    }
+  }
+  __syncthreads();
+  // ---- theta1 inverse, x V, theta1 forward, in place on Tb
+  const T* Vp = A.V + (size_t)p * n2 * n1;
+  for (int t = threadIdx.x; t < SQ * n2 * 4; t += blockDim.x) {
+    const int sj = t >> 2, s = sj / n2, j = sj - s * n2;
+    V* col = Tb + (size_t)s * nmr * SQ_RS + j;
+    T xr[16], xi[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      xr[r] = T(0);
+      xi[r] = T(0);
+      if (r < nmr) {
+        const V u = col[r * SQ_RS], e = E4[4 * r + q];
+        xr[r] = u.x * e.x - u.y * e.y;
+        xi[r] = u.x * e.y + u.y * e.x;
+      }
+    }
+    dft16<+1, T>(xr, xi);   // the points 4 t + q, up to W^(m_0 t)
+    const T* Vrow = Vp + (size_t)j * n1 + q;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const T v = Vrow[4 * k];
+      xr[k] *= v;
+      xi[k] *= v;
+    }
+    dft16<-1, T>(xr, xi);   // slot r: this lane's share of row r, up to omega^(-m_r q)
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const V e = E4[4 * r + q];   // times conj(omega^(m_r q))
+      const T vr = xr[r] * e.x + xi[r] * e.y, vi = xi[r] * e.x - xr[r] * e.y;
+      xr[r] = vr;
+      xi[r] = vi;
+    }
+    // reduce-scatter over the quad: rows 8 h .. 8 h + 7 (h = q >> 1), then 4 q .. 4 q + 3
+    const bool h = q & 2, l = q & 1;
+    T kr[8], ki[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const T sr = h ? xr[i] : xr[8 + i], si = h ? xi[i] : xi[8 + i];
+      kr[i] = (h ? xr[8 + i] : xr[i]) + __shfl_xor_sync(0xffffffffu, sr, 2);
+      ki[i] = (h ? xi[8 + i] : xi[i]) + __shfl_xor_sync(0xffffffffu, si, 2);
+    }
+    __syncwarp();   // every lane of the quad has read its column of Tb
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const T sr = l ? kr[i] : kr[4 + i], si = l ? ki[i] : ki[4 + i];
+      const T vr = (l ? kr[4 + i] : kr[i]) + __shfl_xor_sync(0xffffffffu, sr, 1);
+      const T vi = (l ? ki[4 + i] : ki[i]) + __shfl_xor_sync(0xffffffffu, si, 1);
+      const int r = 4 * q + i;
+      if (r < nmr) col[r * SQ_RS] = mk<T>(vr, vi);
+    }
+  }
+  __syncthreads();
+  // ---- forward theta2: Tb -> H (kept pairs only)
+  if (threadIdx.x - lane < nq2) {
+    const int t = threadIdx.x, sr = t >> 2, s = sr / nmr, r = sr - s * nmr;
+    const int c = c0 + s;
+    const bool valid = t < nq2 && c < A.ncols;
+    const V* row = Tb + ((size_t)(valid ? s * nmr + r : 0)) * SQ_RS + 12 * q;
+    const int b = (q >> 1) + 2 * (q & 1);   // this lane's n mod 4 after the quad DFT
+    T xr[12], xi[12];
+#pragma unroll
+    for (int cc = 0; cc < 12; ++cc) {
+      const V u = row[cc];
+      T vr = u.x, vi = u.y;
+      quad_dft<-1, T>(vr, vi, q);
+      const V w = T48[b * cc];   // times e^{-2 pi i b c / 48}
+      xr[cc] = vr * w.x - vi * w.y;
+      xi[cc] = vr * w.y + vi * w.x;
+    }
+    dft12<-1, T>(xr, xi);   // F[4 a + b]
+    if (valid) {
+      V* Hc = A.H + ((size_t)c * A.Nr + p) * A.nA;
+      const int* sp = A.slot_pair + (size_t)r * n2 + b;
+#pragma unroll
+      for (int a = 0; a < 12; ++a) {
+        const int pa = sp[4 * a];
+        if (pa >= 0) Hc[pa] = mk<T>(xr[a], xi[a]);
+      }
+    }
+  }
+}
+
+// slabs per CTA of k_slab_q: as many (slab, row) quads as fit the CTA's threads, at most 8
+static int slab_q_per_cta(int nmr) { return std::max(1, std::min(8, SLAB_THREADS / (4 * std::max(nmr, 1)))); }
+static size_t slab_q_smem_bytes(int nmr, size_t elem) {
+  return elem * ((size_t)slab_q_per_cta(nmr) * nmr * SQ_RS + 64 + 48);
+}
+
 static size_t slab_r16_smem_bytes(int nmr, int n2, size_t elem) {
   const size_t w = elem == sizeof(float2) ? (size_t)pd_size(nmr * n2) : (size_t)nmr * n2;
   return elem * (2 * w + 4 * (size_t)nmr + (size_t)4 * n2 * 17);
 }
 
-// FP32 on the 64 x 48 grid: the 4 x 16 theta1 variant (unless HW_OPT_SLAB_KERNEL selects the
-// Stockham FFTs)
+// the 64 x 48 grid: the 4 x 16 theta1 variant (unless HW_OPT_SLAB_KERNEL selects the Stockham
+// FFTs)
 static bool use_slab_r16(const hw_ctx* ctx, size_t elem) {
   (void)elem;
   return ctx->slab_r16 && ctx->hb.prm.Nth1 == 64 && ctx->hb.prm.Nth2 == 48;
+}
+
+// the all-register variant (HW_OPT_SLAB_KERNEL = 2: FP32 only, the FP64 transforms stay on
+// k_slab_r16, whose FP64-pipe work the register variant does not lower; 3: both precisions):
+// 64 x 48 grid, at most 16 kept m rows, and those consecutive (m_r = m_0 + r)
+static bool use_slab_q(const hw_ctx* ctx, size_t elem) {
+  const auto& mm = ctx->hb.mrow_m;
+  const bool want = ctx->slab_r16 == 3 || (ctx->slab_r16 == 2 && elem == sizeof(float2));
+  if (!want || !use_slab_r16(ctx, elem) || mm.empty() || mm.size() > 16) return false;
+  for (size_t r = 1; r < mm.size(); ++r)
+    if (mm[r] != mm[0] + (int)r) return false;
+  return true;
 }
 
 // --------------------------------------------------------------------------- host launcher
@@ -868,6 +1114,12 @@ static void* slab_kernel(int n1, int n2) {
 
 template <typename T>
 static cudaError_t launch_slab(const hw_ctx* ctx, dim3 grid, size_t smem, const SlabArgs<T>& sa) {
+  if (use_slab_q(ctx, sizeof(cplx_t<T>))) {
+    const int sq = slab_q_per_cta(sa.nmr);
+    const dim3 g((grid.x + sq - 1) / sq, grid.y);
+    k_slab_q<T><<<g, SLAB_THREADS, smem, ctx->stream>>>(sa, sq);
+    return cudaGetLastError();
+  }
   void* f = use_slab_r16(ctx, sizeof(cplx_t<T>)) ? (void*)k_slab_r16<T, 64, 48> : slab_kernel<T>(sa.Nth1, sa.Nth2);
   void* args[] = {(void*)&sa};
   return cudaLaunchKernel(f, grid, dim3(SLAB_THREADS), args, smem, ctx->stream);
@@ -885,7 +1137,8 @@ size_t slab_smem_bytes(const hw_ctx* ctx, size_t elem, int Jc) {
   const auto& hb = ctx->hb;
   const int nmr = (int)hb.mrow_m.size();
   const int n1 = hb.prm.Nth1, n2 = hb.prm.Nth2;
-  if (use_slab_r16(ctx, elem)) return slab_r16_smem_bytes(nmr, n2, elem);   // no theta2 chunks
+  if (use_slab_q(ctx, elem)) return slab_q_smem_bytes(nmr, elem);            // no theta2 chunks
+  if (use_slab_r16(ctx, elem)) return slab_r16_smem_bytes(nmr, n2, elem);
   // padded layout: the FP32 kernels specialised for the grid (k_slab's PAD)
   const bool pad = elem == sizeof(float2) && slab_kernel<float>(n1, n2) != (void*)k_slab<float, 0, 0>;
   const int w = std::max(nmr * n2, Jc * n1);
@@ -1425,7 +1678,8 @@ cudaError_t hx_configure(hw_ctx* ctx) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radial_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   for (void* f : {(void*)k_slab<double, 0, 0>, (void*)k_slab<float, 0, 0>, (void*)k_slab<double, 64, 48>,
                   (void*)k_slab<float, 64, 48>, (void*)k_slab<double, 192, 96>, (void*)k_slab<float, 192, 96>,
-                  (void*)k_slab_r16<float, 64, 48>, (void*)k_slab_r16<double, 64, 48>})
+                  (void*)k_slab_r16<float, 64, 48>, (void*)k_slab_r16<double, 64, 48>, (void*)k_slab_q<float>,
+                  (void*)k_slab_q<double>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   (void)ctx;
   return e;

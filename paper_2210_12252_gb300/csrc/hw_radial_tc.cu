@@ -11,7 +11,9 @@
 // Both operands are split into three BF16 parts, x = b0 + b1 + b2 (24 significant bits: the
 // FP32 value exactly), and the products taken as the six part pairs (p, q) with p + q <= 2 by
 // tcgen05 kind::f16 MMAs with FP32 accumulation in TMEM: the accuracy of the FP32 transforms.
-// The tables are split once at setup; the coefficients are split while they are staged into
+// The tables are split once at setup and brought into shared memory by one TMA copy per K
+// block (cp.async.bulk.tensor, 64-byte swizzle), which overlaps the staging of the other
+// operand; the coefficients are split while they are staged into
 // shared memory (K-major rows of 32 BF16, 64-byte swizzle), their global loads issued
 // together before any is used.  The epilogue reads TMEM with one thread per (item, part) row: the inverse writes G
 // rows of consecutive pairs (coalesced), the forward stages Y in shared memory and scatters it
@@ -42,7 +44,6 @@ struct RadTcArgs {
   const int* off;
   const int* Ka;
   int64_t ld;
-  const __nv_bfloat16* tab16;   // inverse [(N+1)][3][npad][kb*32] or forward [(N+1)][3][kpad][kbp*32]
   const double* ke;
   int64_t keoff[MAXSLOT];
   int step;
@@ -61,16 +62,13 @@ constexpr int RT_PLANES = 3;        // BF16 parts of every operand
 constexpr int RT_ROWB = 64;         // bytes per K-major row: 32 BF16
 constexpr int RT_ATILE = RT_PLANES * 128 * RT_ROWB;   // one K block of A, all parts
 
-// copy group g's split table ([plane][rows][kblocks*32] BF16) into swizzled shared memory:
-// [kblock][plane][rows][64 B]
-__device__ __forceinline__ void load_table_sw64(const __nv_bfloat16* src, int rows, int kblocks, unsigned char* dst) {
-  const int chunks = kblocks * RT_PLANES * rows * 4;   // 16-byte chunks
-#pragma unroll 4
-  for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
-    const int j = i & 3, r = (i >> 2) % rows, pk = (i >> 2) / rows, plane = pk % RT_PLANES, kb = pk / RT_PLANES;
-    const uint4 v = *reinterpret_cast<const uint4*>(src + ((size_t)plane * rows + r) * (kblocks * 32) + kb * 32 + j * 8);
-    *reinterpret_cast<uint4*>(dst + ((size_t)(kb * RT_PLANES + plane) * rows) * RT_ROWB + sw64_off(r, j * 8)) = v;
-  }
+// one thread: the TMA copies of group g's table, K block kb to [kb][3][rows][64 B] (the three
+// parts of a block are one box), completing on bar
+__device__ __forceinline__ void load_table_tma(const CUtensorMap* map, int g, int rows, int kblocks,
+                                               unsigned char* dst, uint64_t* bar) {
+  mbar_expect_tx(bar, (uint32_t)(kblocks * RT_PLANES * rows * RT_ROWB));
+  for (int kb = 0; kb < kblocks; ++kb)
+    tma_load_3d(dst + (size_t)kb * RT_PLANES * rows * RT_ROWB, map, kb * 32, 0, g * RT_PLANES, bar);
 }
 
 // the six part products of one 32-element K block (two K steps of 16), A_p B_q with p + q <= 2:
@@ -106,7 +104,7 @@ __device__ __forceinline__ void put3(unsigned char* tile, int row, int col, floa
 
 // ------------------------------------------------------------------------------- inverse
 // grid: x = tile of RT_ITEMS items within group g, y = g
-__global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(RadTcArgs A) {
+__global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(const __grid_constant__ CUtensorMap tmT, RadTcArgs A) {
   extern __shared__ __align__(1024) unsigned char rsm_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)rsm_raw + 1023) & ~(uintptr_t)1023);
   const int g = blockIdx.y;
@@ -117,7 +115,7 @@ __global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(RadTcArgs A) {
   const int KB = A.kb, NP = A.npad;
   unsigned char* sA = sm;                                   // [KB][3][128][64 B]
   unsigned char* sB = sm + (size_t)KB * RT_ATILE;           // [KB][3][NP][64 B]
-  __shared__ __align__(8) uint64_t bar_mma;
+  __shared__ __align__(8) uint64_t bar_mma, bar_tab;
   __shared__ uint32_t tmem_s;
   __shared__ const double* s_x[RT_ITEMS];
   __shared__ float2* s_g[RT_ITEMS];
@@ -127,7 +125,9 @@ __global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(RadTcArgs A) {
   const uint32_t tcols = 2 * NP <= 32 ? 32 : (2 * NP <= 64 ? 64 : (2 * NP <= 128 ? 128 : (2 * NP <= 256 ? 256 : 512)));
   if (threadIdx.x == 0) {
     mbar_init(&bar_mma, 1);
+    mbar_init(&bar_tab, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    load_table_tma(&tmT, g, NP, KB, sB, &bar_tab);
   }
   if (warp == 0) tmem_alloc(&tmem_s, tcols);
   if (threadIdx.x < RT_ITEMS) {
@@ -154,7 +154,6 @@ __global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(RadTcArgs A) {
     s_ka[q] = ka;
     s_sc[q] = sc;
   }
-  load_table_sw64(A.tab16 + (size_t)g * RT_PLANES * NP * KB * 32, NP, KB, sB);
   __syncthreads();
   // A rows (2q + part) over k: a warp takes the items warp, warp + 8, ...; lanes over k.  Every
   // load of the warp's items is issued before the first is used.
@@ -191,15 +190,22 @@ __global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(RadTcArgs A) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_s;
+  __shared__ int s_tab_ok;
   if (threadIdx.x == 0) {
-    const uint32_t idesc = umma_idesc_bf16(NP);
-    for (int kb = 0; kb < KB; ++kb)
-      mma_bf16x3(tmem, tmem + (uint32_t)NP, smem_u32(sA + (size_t)kb * RT_ATILE),
-                 smem_u32(sB + (size_t)kb * RT_PLANES * NP * RT_ROWB), NP, idesc, kb == 0);
-    umma_commit(&bar_mma);
+    s_tab_ok = mbar_wait(&bar_tab, 0);
+    if (s_tab_ok) {
+      const uint32_t idesc = umma_idesc_bf16(NP);
+      for (int kb = 0; kb < KB; ++kb)
+        mma_bf16x3(tmem, tmem + (uint32_t)NP, smem_u32(sA + (size_t)kb * RT_ATILE),
+                   smem_u32(sB + (size_t)kb * RT_PLANES * NP * RT_ROWB), NP, idesc, kb == 0);
+      umma_commit(&bar_mma);
+    } else {
+      atomicExch(A.status, HW_ETIMEOUT);
+    }
   }
-  __syncwarp();
-  bool ok = mbar_wait(&bar_mma, 0);
+  __syncthreads();
+  const bool tab_ok = s_tab_ok;
+  bool ok = tab_ok && mbar_wait(&bar_mma, 0);
   if (!ok && threadIdx.x == 0) atomicExch(A.status, HW_ETIMEOUT);
   tc_fence_after();
   if (warp < 4 && ok) {
@@ -220,9 +226,10 @@ __global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(RadTcArgs A) {
       }
     }
   }
-  if (!ok) {   // the tensor core must be done with TMEM before it is released
+  if (!ok && tab_ok) {   // the tensor core must be done with TMEM before it is released
     if (!mbar_wait(&bar_mma, 0) && threadIdx.x == 0) atomicExch(A.status, HW_ETIMEOUT);
   }
+  if (!tab_ok && threadIdx.x == 0) mbar_wait(&bar_tab, 0);   // the copies in flight land before exit
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(RadTcArgs A) {
 // ------------------------------------------------------------------------------- forward
 // grid: x = tile of RT_ITEMS items within group g, y = g.  No nu != 0 terms (the SIMT kernel
 // takes those launches).
-__global__ void __launch_bounds__(RT_THREADS) k_rfwd_tc(RadTcArgs A) {
+__global__ void __launch_bounds__(RT_THREADS, 2) k_rfwd_tc(const __grid_constant__ CUtensorMap tmT, RadTcArgs A) {
   extern __shared__ __align__(1024) unsigned char rsm_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)rsm_raw + 1023) & ~(uintptr_t)1023);
   const int g = blockIdx.y;
@@ -246,7 +253,7 @@ __global__ void __launch_bounds__(RT_THREADS) k_rfwd_tc(RadTcArgs A) {
   unsigned char* sA = sm;                                   // 2 stages x [3][128][64 B]
   unsigned char* sB = sm + 2 * RT_ATILE;                    // [KBP][3][KP][64 B]
   float2* Ys = reinterpret_cast<float2*>(sm);               // [RT_ITEMS][K + 1], after the MMAs
-  __shared__ __align__(8) uint64_t bar_mma[2];
+  __shared__ __align__(8) uint64_t bar_mma[2], bar_tab;
   __shared__ uint32_t tmem_s;
   __shared__ const float2* s_h[RT_ITEMS];
   __shared__ int64_t s_o[RT_ITEMS], s_cs[RT_ITEMS];
@@ -257,8 +264,10 @@ __global__ void __launch_bounds__(RT_THREADS) k_rfwd_tc(RadTcArgs A) {
   if (threadIdx.x == 0) {
     mbar_init(&bar_mma[0], 1);
     mbar_init(&bar_mma[1], 1);
+    mbar_init(&bar_tab, 1);
     s_bad = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    load_table_tma(&tmT, g, KP, KBP, sB, &bar_tab);
   }
   if (warp == 0) tmem_alloc(&tmem_s, tcols);
   if (threadIdx.x < RT_ITEMS) {
@@ -284,7 +293,6 @@ __global__ void __launch_bounds__(RT_THREADS) k_rfwd_tc(RadTcArgs A) {
     s_ka[qq] = ka;
     s_slot[qq] = slot;
   }
-  load_table_sw64(A.tab16 + (size_t)g * RT_PLANES * KP * KBP * 32, KP, KBP, sB);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -316,6 +324,7 @@ __global__ void __launch_bounds__(RT_THREADS) k_rfwd_tc(RadTcArgs A) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (threadIdx.x == 0 && j == 0 && !mbar_wait(&bar_tab, 0)) s_bad = 2;   // the table is in
     if (threadIdx.x == 0 && !s_bad) {
       mma_bf16x3(tmem, tmem + (uint32_t)KP, smem_u32(tile), smem_u32(sB + (size_t)j * RT_PLANES * KP * RT_ROWB), KP,
                  idesc, j == 0);
@@ -324,7 +333,9 @@ __global__ void __launch_bounds__(RT_THREADS) k_rfwd_tc(RadTcArgs A) {
   }
   // the last chunk's MMAs (and with them all earlier ones) complete
   const int jl = KBP - 1;
-  bool ok = !s_bad && mbar_wait(&bar_mma[jl & 1], (uint32_t)((jl >> 1) & 1));
+  __syncthreads();   // s_bad as the MMA thread left it
+  const int bad = s_bad;
+  bool ok = !bad && mbar_wait(&bar_mma[jl & 1], (uint32_t)((jl >> 1) & 1));
   if (!ok && threadIdx.x == 0) atomicExch(A.status, HW_ETIMEOUT);
   tc_fence_after();
   __syncthreads();   // every thread is past its reads of the A stages (Ys reuses them)
@@ -370,9 +381,11 @@ __global__ void __launch_bounds__(RT_THREADS) k_rfwd_tc(RadTcArgs A) {
       y[0] = y0;
       y[1] = y1;
     }
-  } else {   // the tensor core must be done with TMEM before it is released
+  } else if (bad != 2) {   // the tensor core must be done with TMEM before it is released
     if (!mbar_wait(&bar_mma[jl & 1], (uint32_t)((jl >> 1) & 1)) && threadIdx.x == 0)
       atomicExch(A.status, HW_ETIMEOUT);
+  } else if (threadIdx.x == 0) {   // no MMA issued; the table copies land before exit
+    mbar_wait(&bar_tab, 0);
   }
   __syncthreads();
   if (warp == 0) {
@@ -433,6 +446,14 @@ cudaError_t radial_tc_setup(hw_ctx* ctx, const HostBasis& hb, const std::vector<
   if (e == cudaSuccess) e = cudaMemcpy(db.rt_inv, ti.data(), ti.size() * 2, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc((void**)&db.rt_fwd, tf.size() * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMemcpy(db.rt_fwd, tf.data(), tf.size() * 2, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess &&
+      !(make_plane_map(&db.rt_map_inv, db.rt_inv, false, (int64_t)db.rt_kb * 32, db.rt_npad, G * RT_PLANES,
+                       db.rt_npad, RT_PLANES, 64) &&
+        make_plane_map(&db.rt_map_fwd, db.rt_fwd, false, (int64_t)db.rt_kbp * 32, db.rt_kpad, G * RT_PLANES,
+                       db.rt_kpad, RT_PLANES, 64))) {
+    db.rt_ok = false;   // no TMA map: the SIMT kernels take the launches
+    return cudaSuccess;
+  }
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_rinv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)rinv_tc_smem(db.rt_npad, db.rt_kb));
@@ -485,20 +506,18 @@ cudaError_t launch_rinv_tc(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, i
                            int scale_mode) {
   RadTcArgs a = tc_args(ctx, blk, ns, ld, nc, c0, gbuf);
   a.scale_mode = scale_mode;
-  a.tab16 = ctx->db.rt_inv;
-  k_rinv_tc<<<tc_grid(ctx, nc), RT_THREADS, rinv_tc_smem(a.npad, a.kb), ctx->stream>>>(a);
+  k_rinv_tc<<<tc_grid(ctx, nc), RT_THREADS, rinv_tc_smem(a.npad, a.kb), ctx->stream>>>(ctx->db.rt_map_inv, a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rfwd_tc(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, int nc, int c0, void* hbuf,
                            const ChebStep* step) {
   RadTcArgs a = tc_args(ctx, blk, ns, ld, nc, c0, hbuf);
-  a.tab16 = ctx->db.rt_fwd;
   if (step) {
     a.step = 1;
     a.cs = *step;
   }
-  k_rfwd_tc<<<tc_grid(ctx, nc), RT_THREADS, rfwd_tc_smem(a.kpad, a.kbp), ctx->stream>>>(a);
+  k_rfwd_tc<<<tc_grid(ctx, nc), RT_THREADS, rfwd_tc_smem(a.kpad, a.kbp), ctx->stream>>>(ctx->db.rt_map_fwd, a);
   return cudaGetLastError();
 }
 

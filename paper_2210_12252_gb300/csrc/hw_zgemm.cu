@@ -753,7 +753,7 @@ static EncodeTiledFn encode_fn() {
 }
 
 // 3-D map over planes [planes][rows][Kp], box {swz / esz, box_rows, box_planes}
-static bool make_plane_map(CUtensorMap* m, const void* base, bool fp32, int64_t Kp, int rows, int planes,
+bool make_plane_map(CUtensorMap* m, const void* base, bool fp32, int64_t Kp, int rows, int planes,
                            int box_rows, int box_planes, int swz) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;

@@ -165,18 +165,42 @@ def test_set_potential_from_device_matches_host_build(tube):
 
 
 def test_apply_H_mixed_tube_slab_variants_agree(tube, hwmod):
-    """The FP32 angular kernel on the 64 x 48 grid: the 4 x 16 register-DFT theta1 variant
-    (default) and the Stockham FFTs agree with each other at FP32 rounding and with the oracle
-    within the mixed tolerance."""
+    """The angular kernels on the 64 x 48 grid: the all-register variant (theta2 as 4 lanes x
+    12-point DFTs joined by a 4-point DFT across the lanes, theta1 bins in registers; 2), the
+    4 x 16 register-DFT theta1 variant with Stockham theta2 passes (1) and the Stockham FFTs
+    (0) agree with each other at FP32 rounding and with the oracle within the mixed tolerance.
+    5 columns: the all-register kernel takes 4 slabs per CTA, so its second CTA has one."""
     kp = tube.kps[0]
     X = inputs.random_block(kp.L, 5, 81)
     Yref = Hm.apply_H(kp, tube.V, X)
     Xd = to_dev(X)
     out = {}
-    for v in (1, 0):
-        tube.ctx.set_option(hwmod.HW_OPT_SLAB_KERNEL, v)
-        out[v] = from_dev(tube.ctx.apply_H(0, Xd, prec="mixed"), kp.L)
-        assert rel_err(out[v], Yref) < MIXED_TOL
-        assert_entrywise(out[v], Yref, MIXED_TOL, MIXED_FLOOR, f"slab variant {v}")
-    tube.ctx.set_option(hwmod.HW_OPT_SLAB_KERNEL, 1)
+    keep = tube.ctx.get_option(hwmod.HW_OPT_SLAB_KERNEL)
+    try:
+        for v in (2, 1, 0):
+            tube.ctx.set_option(hwmod.HW_OPT_SLAB_KERNEL, v)
+            out[v] = from_dev(tube.ctx.apply_H(0, Xd, prec="mixed"), kp.L)
+            assert rel_err(out[v], Yref) < MIXED_TOL
+            assert_entrywise(out[v], Yref, MIXED_TOL, MIXED_FLOOR, f"slab variant {v}")
+    finally:
+        tube.ctx.set_option(hwmod.HW_OPT_SLAB_KERNEL, keep)
     assert rel_err(out[1], out[0]) < MIXED_TOL
+    assert rel_err(out[2], out[0]) < MIXED_TOL
+
+
+def test_apply_H_fp64_tube_slab_variants_agree(tube, hwmod):
+    """The same three angular kernels in FP64 (the register kernel by option 3) against the
+    oracle (FP64 tolerance, entry-wise), on 7 ragged columns with a padded leading dimension."""
+    kp = tube.kps[0]
+    X = inputs.random_block(kp.L, 7, 83)
+    Yref = Hm.apply_H(kp, tube.V, X)
+    Xd = to_dev(X, kp.L + 6)
+    keep = tube.ctx.get_option(hwmod.HW_OPT_SLAB_KERNEL)
+    try:
+        for v in (3, 1, 0):
+            tube.ctx.set_option(hwmod.HW_OPT_SLAB_KERNEL, v)
+            Y = from_dev(tube.ctx.apply_H(0, Xd, prec="fp64"), kp.L)
+            assert rel_err(Y, Yref) < FP64_TOL, v
+            assert_entrywise(Y, Yref, FP64_TOL, FP64_FLOOR, f"FP64 slab variant {v}")
+    finally:
+        tube.ctx.set_option(hwmod.HW_OPT_SLAB_KERNEL, keep)
