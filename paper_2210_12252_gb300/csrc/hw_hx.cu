@@ -941,8 +941,10 @@ __device__ __forceinline__ void quad_dft(R& vr, R& vi, int q) {
 // the quads' accesses spread over the banks).
 constexpr int SQ_RS = 49;
 
+// FP32: three CTAs per SM (80 registers, a few spilled: 60.6 us per 64-column launch against
+// 65.9 at two CTAs and 112 registers, 63.9 at four and 64)
 template <typename T>
-__global__ void __launch_bounds__(SLAB_THREADS, sizeof(T) == 4 ? 2 : 1) k_slab_q(SlabArgs<T> A, int SQ) {
+__global__ void __launch_bounds__(SLAB_THREADS, sizeof(T) == 4 ? 3 : 1) k_slab_q(SlabArgs<T> A, int SQ) {
   using V = cplx_t<T>;
   constexpr int n1 = 64, n2 = 48;
   extern __shared__ __align__(16) unsigned char smem_raw[];
