@@ -147,6 +147,14 @@ def slab_flops(geom, nmr, nA):
     return 2 * nmr * f2 + 2 * n2 * f1 + 2 * n1 * n2
 
 
+def slab_flops_full(geom):
+    """Algorithmic flops of one radial-node slab counted on the full angular grid G = N_th1 N_th2:
+    a complete 2-D FFT each way at 5 G log2 G, plus 2 flops per potential multiply (the count
+    the roofline reports; slab_flops is the pruned shape the kernel works on)."""
+    g = geom.Nth1 * geom.Nth2
+    return 2 * 5 * g * math.log2(g) + 2 * g
+
+
 def fp64_peak_tflops(sm_mhz):
     """FP64 pipe: SMs x 2 DFMA x 2 flop per clock (1.26 TFLOP/s at 152 SMs and 2070 MHz, the
     nominal)."""
@@ -157,7 +165,7 @@ def hx_roofline(geom, ctx, L, ns, prec, kernel_ms):
     """Each H X kernel against its binding roofline (one launch of ns columns): the radial
     transforms against the measured HBM copy bandwidth (algorithmic bytes: the coefficient
     blocks in complex128 and the (r, pair) intermediate), the slab against the FP32 (mixed) or
-    FP64 pipe (algorithmic flops of slab_flops)."""
+    FP64 pipe (algorithmic flops of slab_flops_full; the pruned count beside it)."""
     peaks, src = load_peaks()
     mhz = peaks.get("sm_max_mhz", 2070.0)
     elem = 4 if prec == "mixed" else 8
@@ -177,11 +185,15 @@ def hx_roofline(geom, ctx, L, ns, prec, kernel_ms):
                          "hbm_frac": round(fh, 4), "achieved_tflops": round(tf, 3),
                          "alu_frac": round(fa, 4), "frac": round(max(fh, fa), 4)}
     if "slab" in kernel_ms:
-        fl = slab_flops(geom, nmr, nA) * ns * geom.Nr
+        fl = slab_flops_full(geom) * ns * geom.Nr
+        flp = slab_flops(geom, nmr, nA) * ns * geom.Nr
         pk = fp32_alu_peak_tflops(mhz) if prec == "mixed" else fp64_peak_tflops(mhz)
-        tf = fl / (kernel_ms["slab"] / 1e3) / 1e12
+        sec = kernel_ms["slab"] / 1e3
+        tf, tfp = fl / sec / 1e12, flp / sec / 1e12
         out["slab"] = {"bound": "alu", "achieved_tflops": round(tf, 3), "peak_tflops": round(pk, 2),
-                       "frac": round(tf / pk, 4), "pipe": "fp32" if prec == "mixed" else "fp64"}
+                       "frac": round(tf / pk, 4), "pipe": "fp32" if prec == "mixed" else "fp64",
+                       "count": "full 2-D FFTs each way + potential multiply",
+                       "achieved_tflops_pruned": round(tfp, 3), "frac_pruned": round(tfp / pk, 4)}
     return out
 
 
@@ -690,13 +702,18 @@ def roofline(result, w, ctx, L, nb):
         # one slab launch processes (columns x N_r) slabs; mixed form runs in FP32
         hxm = result["hx"]["mixed"]["kernel_ms"]["slab"]
         cols = 64
-        fl = slab_flops(w.geom, *nmr_nA) * cols * w.geom.Nr
-        ach = fl / (hxm / 1e3) / 1e12
+        fl = slab_flops_full(w.geom) * cols * w.geom.Nr
+        flp = slab_flops(w.geom, *nmr_nA) * cols * w.geom.Nr
+        ach, achp = fl / (hxm / 1e3) / 1e12, flp / (hxm / 1e3) / 1e12
         rec.update({"bound": "alu", "achieved": round(ach, 3), "peak": round(fp32, 2), "unit": "TFLOP/s",
                     "frac": round(ach / fp32, 4), "traffic": _traffic("slab"), "launch_ms": hxm,
+                    "flop_per_launch": round(fl), "achieved_pruned": round(achp, 3),
+                    "frac_pruned": round(achp / fp32, 4), "flop_per_launch_pruned": round(flp),
                     "basis": "64-column FP32 H X launch (launch_ms, CUDA events; avg_ms is the step's "
-                             "mean over both precisions' slab launches), FP32 FMA peak SMs x128x2 flop/clk "
-                             "at the sampled SM clock"})
+                             "mean over both precisions' slab launches); work counted as full 2-D FFTs "
+                             "(5 G log2 G each way, G = N_th1 N_th2) + 2 flop per potential multiply per "
+                             "radial node and column (the _pruned keys: the kept-row shape the kernel "
+                             "transforms); FP32 FMA peak SMs x128x2 flop/clk at the sampled SM clock"})
     elif dom in ("radial_inv", "radial_fwd"):
         hxm = result["hx"]["mixed"]["kernel_ms"][dom]
         by = radial_bytes(L, 64, w.geom.Nr, s["n_pairs"], 4)

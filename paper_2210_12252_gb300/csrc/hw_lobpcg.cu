@@ -171,6 +171,16 @@ __global__ void k_pad_gram(double2* G, int n, const int* nv) {
   }
 }
 
+// Newton-Schulz coefficient in place of the Gram matrix: G <- (3 I - G) / 2
+__global__ void k_ns_coef(double2* G, int n) {
+  double2* g = G + (size_t)blockIdx.y * n * n;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * n; t += gridDim.x * blockDim.x) {
+    const int i = t % n, j = t / n;
+    const double2 x = g[t];
+    g[t] = make_double2((i == j ? 1.5 : 0.0) - 0.5 * x.x, -0.5 * x.y);
+  }
+}
+
 // pad the Rayleigh-Ritz matrix: index j of S = [X(nb) P(np) W(na)] is valid iff j < nb, or
 // j in the P block below npv[b], or j in the W block below nav[b]; invalid rows/cols get a
 // huge distinct diagonal so they sort last.  n may exceed nb+np+na by one (even size).
@@ -531,6 +541,51 @@ static hw_status cholqr(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, double2* S, int 
     }
   }
   return gemm.st == CUBLAS_STATUS_SUCCESS ? HW_OK : hw_fail(ctx, HW_ECUDA, "cuBLAS failure in Cholesky-QR");
+}
+
+// Orthonormalise `ncol` nearly orthonormal columns of S at column offset c0 (all valid, every
+// k-point) by `passes` Newton-Schulz steps X <- X (3 I - X^H X) / 2 in FP64 products: the
+// deviation from orthonormality E = X^H X - I goes to (3/4) E^2 + O(E^3) per step, so two steps
+// take the FP32 phase's 1e-6 to the products' rounding.  The product X C goes through w->R
+// (free here: the caller recomputes the residuals).  ok = false, with S untouched, when some
+// k-point's Gram is more than 0.1 from the identity in an entry: the caller then uses
+// Cholesky-QR.
+static hw_status ns_orth(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, double2* S, int c0, int ncol, int passes,
+                         bool& ok) {
+  const int nk = w->nk;
+  const int64_t Lpad = w->Lpad, sK = Lpad * 3 * w->nb;
+  double2* Xb = S + (size_t)c0 * Lpad;
+  cudaStream_t st = ctx->stream;
+  ok = true;
+  for (int pass = 0; pass < passes; ++pass) {
+    gemm(CUBLAS_OP_C, CUBLAS_OP_N, ncol, ncol, (int)Lpad, 1.0, Xb, Lpad, sK, Xb, Lpad, sK, 0.0, w->G, ncol,
+         (int64_t)ncol * ncol, nk);
+    if (pass == 0) {
+      std::vector<double2> g((size_t)nk * ncol * ncol);
+      cudaMemcpyAsync(g.data(), w->G, g.size() * sizeof(double2), cudaMemcpyDeviceToHost, st);
+      const cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("Newton-Schulz: ") + cudaGetErrorString(e));
+      double dev = 0.0;
+      for (size_t t = 0; t < g.size(); ++t) {
+        const int i = (int)(t % ncol), j = (int)((t / ncol) % ncol);
+        dev = std::max(dev, std::hypot(g[t].x - (i == j ? 1.0 : 0.0), g[t].y));
+      }
+      if (!(dev <= 0.1)) {
+        ok = false;
+        return HW_OK;
+      }
+    }
+    {
+      ProfScope ps_(ctx, HW_PH_CHOL);
+      k_ns_coef<<<dim3(8, nk), 256, 0, st>>>(w->G, ncol);
+      ctx->launches++;
+    }
+    gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, ncol, ncol, 1.0, Xb, Lpad, sK, w->G, ncol, (int64_t)ncol * ncol, 0.0,
+         w->R, Lpad, Lpad * w->nb, nk);
+    cudaMemcpy2DAsync(Xb, (size_t)sK * sizeof(double2), w->R, (size_t)Lpad * w->nb * sizeof(double2),
+                      (size_t)Lpad * ncol * sizeof(double2), nk, cudaMemcpyDeviceToDevice, st);
+  }
+  return gemm.st == CUBLAS_STATUS_SUCCESS ? HW_OK : hw_fail(ctx, HW_ECUDA, "cuBLAS failure in Newton-Schulz");
 }
 
 // Rayleigh-Ritz eigenpairs of the nk matrices w->A (n x n, padded, Hermitian): w->w ascending,
@@ -1150,7 +1205,9 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       std::vector<int> nbv(nk, nb);
       cudaMemcpyAsync(dnv, nbv.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
       deflate_cols(gemm, df, Lb, S, Lpad, sK, 0, nb);   // FP32 rounding leaves traces along Q
-      hs = cholqr(ctx, w, gemm, S, 0, nb, dnv, 2, failed);
+      bool ns_ok = false;
+      hs = ns_orth(ctx, w, gemm, S, 0, nb, 2, ns_ok);
+      if (hs == HW_OK && !ns_ok) hs = cholqr(ctx, w, gemm, S, 0, nb, dnv, 2, failed);
       if (hs != HW_OK) return hs;
       hs = apply_block(ctx, w, kidx, S, HS, 0, nb, true);
       if (hs != HW_OK) return hs;
