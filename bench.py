@@ -203,6 +203,11 @@ def radial_bytes(L, ns, Nr, nA, elem):
     return L * ns * 16 + Nr * nA * ns * 2 * elem
 
 
+def solver_blocks(n_eig):
+    """The library's default block of each eigensolver for n_eig eigenpairs."""
+    return {"lobpcg": n_eig + max(4, n_eig // 8), "chfsi": n_eig + max(8, 3 * n_eig // 16)}
+
+
 def max_over_ranks(total_ms, world, device):
     """The slowest rank's time (every rank gets it): the job ends when its last rank does."""
     if world <= 1:
@@ -249,11 +254,14 @@ def ours_main(args):
     L = int(ctx.setup_basis(w.geom, w.etas)[0])
     ctx.build_potential(w.atoms)
     n_eig = w.n_eig
-    nb = n_eig + max(4, n_eig // 8)
+    # each solver's default block (the library's rule); the start blocks are drawn at the wider
+    # one and a solver with the narrower block starts from their leading columns
+    NB = solver_blocks(n_eig)
+    nb = NB[args.solver]
     # every step solves from the next of NSTART seeded start blocks (the iteration count of one
-    # start block is not representative: 8-10 across these blocks)
-    X0s = [torch.from_numpy(np.ascontiguousarray(inputs.random_block(L, nb, start_seed(rank, i)).T)).to(dev)
-           for i in range(NSTART)]
+    # start block is not representative: 6-10 across these blocks)
+    X0s = [torch.from_numpy(np.ascontiguousarray(
+        inputs.random_block(L, max(NB.values()), start_seed(rank, i)).T)).to(dev) for i in range(NSTART)]
     X0 = X0s[0]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     from paper_2210_12252_gb300 import train_precond
@@ -272,7 +280,8 @@ def ours_main(args):
 
     def solve(prec, pc=precond, X=X0, solver=args.solver):
         ctx.set_option(hw.HW_OPT_EIGENSOLVER, SOLVER[solver])
-        return ctx.solve_eigs([0], n_eig, block=nb, tol=TOL, maxit=600, prec=prec, precond=pc, X0=[X])
+        k = NB[solver]
+        return ctx.solve_eigs([0], n_eig, block=k, tol=TOL, maxit=600, prec=prec, precond=pc, X0=[X[:k]])
 
     if args.solver == "chfsi":
         form = (f"Chebyshev-filtered subspace iteration (degree {ctx.get_option(hw.HW_OPT_CHEB_DEGREE)}, "
@@ -480,7 +489,8 @@ def ours_main(args):
 
         def solve_on(c, prec, pcv, slv):
             c.set_option(hw.HW_OPT_EIGENSOLVER, SOLVER[slv])
-            return c.solve_eigs([0], n_eig, block=nb, tol=TOL, maxit=600, prec=prec, precond=pcv, X0=[X0])
+            k = NB[slv]
+            return c.solve_eigs([0], n_eig, block=k, tol=TOL, maxit=600, prec=prec, precond=pcv, X0=[X0[:k]])
 
         for name, prec, slv, pcv in runs:
             c = ctx_l if pcv == "learned" else ctx
@@ -782,7 +792,8 @@ def e2e(ctx, w, L, nb, n_eig, dev, stream, flush, args, precond):
     from paper_2210_12252_gb300 import inputs
     V = torch.from_numpy(ctx.build_potential(w.atoms)).pin_memory()
     rank = int(os.environ.get("RANK", "0"))
-    X0hs = [torch.from_numpy(np.ascontiguousarray(inputs.random_block(L, nb, start_seed(rank, i)).T)).pin_memory()
+    X0hs = [torch.from_numpy(np.ascontiguousarray(
+        inputs.random_block(L, max(solver_blocks(n_eig).values()), start_seed(rank, i)).T[:nb])).pin_memory()
             for i in range(NSTART)]
     X0h = X0hs[0]
     Vd = torch.empty(V.shape, dtype=torch.float64, device=dev)
@@ -1051,7 +1062,7 @@ def kernel_case(args):
         if args.solver == "lobpcg" and os.path.exists(train_precond.WEIGHTS):
             ctx.set_mlp(train_precond.load_weights())
             pc = "learned"
-        nb = w.n_eig + max(4, w.n_eig // 8)
+        nb = solver_blocks(w.n_eig)[args.solver]
         X0 = torch.from_numpy(np.ascontiguousarray(inputs.random_block(L, nb, 1234).T)).cuda()
         ctx.set_option(hw.HW_OPT_EIGENSOLVER, {"lobpcg": 0, "chfsi": 1}[args.solver])
         ctx.solve_eigs([0], w.n_eig, block=nb, tol=TOL, maxit=600, prec="mixed", precond=pc, X0=[X0])

@@ -172,7 +172,7 @@ hw_status hw_apply_precond(hw_ctx* ctx, int k, const double* R, double* Z, int n
 
 /* Lowest n_eig eigenpairs at the nk k-points kidx[] by block LOBPCG (Sec. Eigensolvers and
  * Preconditioning), or by Chebyshev-filtered subspace iteration (HW_OPT_EIGENSOLVER), on blocks
- * of `block` >= n_eig columns (0: n_eig + max(4, n_eig/8) for LOBPCG, n_eig + max(8, n_eig/8)
+ * of `block` >= n_eig columns (0: n_eig + max(4, n_eig/8) for LOBPCG, n_eig + max(8, 3 n_eig/16)
  * for the Chebyshev solver),
  * at most 112 columns (HW_EINVAL above: the Cholesky-QR keeps its factor in shared memory).
  * More than HW_OPT_WINDOW eigenpairs (default 80) are solved in w = ceil(n_eig / window)

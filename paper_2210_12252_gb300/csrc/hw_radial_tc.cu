@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(const __grid_constant__ 
 // ------------------------------------------------------------------------------- forward
 // grid: x = tile of RT_ITEMS items within group g, y = g.  No nu != 0 terms (the SIMT kernel
 // takes those launches).
-__global__ void __launch_bounds__(RT_THREADS, 2) k_rfwd_tc(const __grid_constant__ CUtensorMap tmT, RadTcArgs A) {
+__global__ void __launch_bounds__(RT_THREADS, 3) k_rfwd_tc(const __grid_constant__ CUtensorMap tmT, RadTcArgs A) {
   extern __shared__ __align__(1024) unsigned char rsm_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)rsm_raw + 1023) & ~(uintptr_t)1023);
   const int g = blockIdx.y;
