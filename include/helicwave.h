@@ -50,8 +50,14 @@ typedef enum {
 
 typedef enum {
   HW_FP64 = 0,       /* every step in FP64                                                 */
-  HW_MIXED = 1       /* transforms in FP32 (FP32 accumulate); diagonal terms, Gram,
+  HW_MIXED = 1,      /* transforms in FP32 (FP32 accumulate); diagonal terms, Gram,
                         Cholesky, Rayleigh-Ritz and the final residual check in FP64      */
+  HW_FP64_DF = 2     /* hw_apply_H only: FP64 storage, radial transforms and diagonal in
+                        FP64, the angular transforms (Algorithms 2, 4 and the potential
+                        multiply) in double-float arithmetic -- pairs of FP32 numbers, about
+                        48 significant bits, on the FP32 pipe -- on the 64 x 48 grid with at
+                        most 16 consecutive kept m rows (other bases: as HW_FP64).  What the
+                        mixed-precision solver uses for its FP64 H X (HW_OPT_FP64_HX).      */
 } hw_prec;
 
 typedef enum {
@@ -406,11 +412,17 @@ typedef enum {
                                over the basis dimension (m or k >= 1024), cuBLAS for the small
                                dense products of the Rayleigh-Ritz step; 2 the tensor-core kernel
                                for every product; 0 cuBLAS (ZGEMM, or CGEMM on FP32 copies). */
-  HW_OPT_RADIAL_KERNEL = 13 /* radial transforms of the mixed-precision H X: 1 (default) on the
-                               tensor cores (3 x TF32 tcgen05 MMAs, one CTA per 64 (column,
-                               pair) items of an |n| group; the forward kernel of launches with
-                               nu != 0 stays on the FP32 SIMT kernel); 0 the FP32 SIMT kernels.
-                               FP64 H X always uses the FP64 SIMT kernels. */
+  HW_OPT_RADIAL_KERNEL = 13, /* radial transforms of the mixed-precision H X: 1 (default) on
+                               the tensor cores (both operands split into three BF16 parts, the
+                               six part products as tcgen05 MMAs, the leading one in its own TMEM
+                               accumulator; one CTA per 64 (column, pair) items of an |n| group;
+                               the forward kernel of launches with nu != 0 stays on the FP32 SIMT
+                               kernel); 0 the FP32 SIMT kernels.  FP64 H X always uses the FP64
+                               SIMT kernels. */
+  HW_OPT_FP64_HX = 14       /* the FP64 H X of a HW_MIXED solve (its hand-over to FP64 products
+                               and the FP64 check of every convergence claim): 1 (default) the
+                               angular transforms in double-float arithmetic (as hw_apply_H with
+                               HW_FP64_DF), 0 in FP64.  HW_FP64 solves always use FP64. */
 } hw_option;
 /* Set an option (HW_EINVAL for an unknown option, a read-only one or a bad value). */
 hw_status hw_set_option(hw_ctx* ctx, int option, int value);

@@ -50,7 +50,7 @@ void dfree(T*& p) {
 
 // V[i][j][p] (eq. wavefun_storage_real) -> Vd[p][j][i] in FP64 and FP32
 __global__ void k_v_relayout(const double* __restrict__ V, double* __restrict__ V64,
-                             float* __restrict__ V32, int n1, int n2, int nr) {
+                             float* __restrict__ V32, float2* __restrict__ Vff, int n1, int n2, int nr) {
   const long total = (long)n1 * n2 * nr;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
     const int i = (int)(t % n1);
@@ -59,7 +59,9 @@ __global__ void k_v_relayout(const double* __restrict__ V, double* __restrict__ 
     const int p = (int)(rest / n2);
     const double v = V[((size_t)i * n2 + j) * nr + p];
     V64[t] = v;
-    V32[t] = (float)v;
+    const float h = (float)v;
+    V32[t] = h;
+    Vff[t] = make_float2(h, (float)(v - (double)h));   // the pair hi + lo (double-float)
   }
 }
 
@@ -98,6 +100,7 @@ void free_basis(hw_ctx* ctx) {
   dfree(db.Ka);
   dfree(db.ke);
   dfree(db.vscratch);
+  dfree(db.vff);
   db.ke_off.clear();
   for (auto* t : {&db.t64.rinv, &db.t64.rfwd, &db.t64.qtab, &db.t64.rder, &db.t64.V, &db.t64.tw1, &db.t64.tw2})
     dfree(*t);
@@ -246,6 +249,7 @@ hw_status hw_setup_basis(hw_ctx* ctx, const hw_basis_params* params, int nk, con
     if (e == cudaSuccess) e = cudaMalloc((void**)&db.t64.V, grid * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void**)&db.t32.V, grid * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&db.vscratch, grid * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&db.vff, grid * sizeof(float2));
     if (e == cudaSuccess) e = radial_tc_setup(ctx, hb, rinv, rfwd);
     // G / H workspace: passes of up to `cols` columns, ~1 GiB for both buffers
     const size_t per_col = 2 * (size_t)Nr * hb.nA * sizeof(double2);
@@ -345,8 +349,8 @@ hw_status hw_set_potential(hw_ctx* ctx, const double* V, int on_device) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "set_potential copy");
-  k_v_relayout<<<1024, 256, 0, ctx->stream>>>(ctx->db.vscratch, ctx->db.t64.V, ctx->db.t32.V, p.Nth1,
-                                              p.Nth2, p.Nr);
+  k_v_relayout<<<1024, 256, 0, ctx->stream>>>(ctx->db.vscratch, ctx->db.t64.V, ctx->db.t32.V, ctx->db.vff,
+                                              p.Nth1, p.Nth2, p.Nr);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "set_potential relayout");
   ctx->launches++;
@@ -381,7 +385,7 @@ static hw_status apply_common(hw_ctx* ctx, int nk, const int* kidx, const double
   if (st != HW_OK) return st;
   if (!ctx->have_V) return hw_fail(ctx, HW_ESTATE, "no potential installed");
   if (nk < 1 || ns < 1 || !kidx || !X || !Y) return hw_fail(ctx, HW_EINVAL, "bad block arguments");
-  if (prec != HW_FP64 && prec != HW_MIXED) return hw_fail(ctx, HW_EINVAL, "bad precision");
+  if (prec != HW_FP64 && prec != HW_MIXED && prec != HW_FP64_DF) return hw_fail(ctx, HW_EINVAL, "bad precision");
   int64_t maxL = 0;
   for (int b = 0; b < nk; ++b) {
     if (kidx[b] < 0 || kidx[b] >= ctx->hb.nk) return hw_fail(ctx, HW_EINVAL, "k-point index out of range");
@@ -399,7 +403,9 @@ static hw_status apply_common(hw_ctx* ctx, int nk, const int* kidx, const double
       blk.y[i] = Y[b0 + i];
       blk.kb[i] = kidx[b0 + i];
     }
-    cudaError_t e = prec == HW_FP64 ? launch_hx<double>(ctx, blk, ns, ld) : launch_hx<float>(ctx, blk, ns, ld);
+    ctx->ff_now = prec == HW_FP64_DF;
+    cudaError_t e = prec == HW_MIXED ? launch_hx<float>(ctx, blk, ns, ld) : launch_hx<double>(ctx, blk, ns, ld);
+    ctx->ff_now = false;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "apply_H launch");
   }
   return HW_OK;
@@ -420,7 +426,7 @@ hw_status hw_density(hw_ctx* ctx, int nk, const int* kidx, const double* const* 
   hw_status st = check_device_call(ctx);
   if (st != HW_OK) return st;
   if (nk < 1 || ns < 1 || !kidx || !X || !occ || !w || !rho) return hw_fail(ctx, HW_EINVAL, "bad density arguments");
-  if (prec != HW_FP64 && prec != HW_MIXED) return hw_fail(ctx, HW_EINVAL, "bad precision");
+  if (prec != HW_FP64 && prec != HW_MIXED && prec != HW_FP64_DF) return hw_fail(ctx, HW_EINVAL, "bad precision");
   int64_t maxL = 0;
   for (int b = 0; b < nk; ++b) {
     if (kidx[b] < 0 || kidx[b] >= ctx->hb.nk) return hw_fail(ctx, HW_EINVAL, "k-point index out of range");
@@ -603,6 +609,11 @@ hw_status hw_set_option(hw_ctx* ctx, int option, int value) {
     ctx->radial_tc = value;
     return HW_OK;
   }
+  if (option == HW_OPT_FP64_HX) {
+    if (value != 0 && value != 1) return hw_fail(ctx, HW_EINVAL, "FP64 H X option 0 (FP64) or 1 (double-float)");
+    ctx->fp64_hx_ff = value;
+    return HW_OK;
+  }
   return hw_fail(ctx, HW_EINVAL, "unknown or read-only option");
 }
 
@@ -622,6 +633,7 @@ hw_status hw_get_option(hw_ctx* ctx, int option, long long* value) {
   if (option == HW_OPT_WINDOW) { *value = ctx->window; return HW_OK; }
   if (option == HW_OPT_TC_GEMM) { *value = ctx->tc_gemm; return HW_OK; }
   if (option == HW_OPT_RADIAL_KERNEL) { *value = ctx->radial_tc; return HW_OK; }
+  if (option == HW_OPT_FP64_HX) { *value = ctx->fp64_hx_ff; return HW_OK; }
   return hw_fail(ctx, HW_EINVAL, "unknown option");
 }
 

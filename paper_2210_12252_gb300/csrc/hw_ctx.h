@@ -38,6 +38,7 @@ struct DevBasis {
   double* rnodes = nullptr;    // [Nr] radial nodes r_p
   std::vector<int64_t> ke_off; // host: start of k-point b in ke
   double* vscratch = nullptr;  // [grid] staging for set_potential
+  float2* vff = nullptr;       // [Nr][Nth2][Nth1] the potential as FP32 pairs (hi, lo), slab layout
   DevTables<double> t64;
   DevTables<float> t32;
   // tensor-core radial transforms of the FP32 H X: BF16 three-part tables per |n| group
@@ -124,6 +125,9 @@ struct hw_ctx {
   int tail_no_p = 0;           // HW_OPT_TAIL_NO_P
   int window = 0;              // HW_OPT_WINDOW (0: 100)
   int slab_r16 = 2;            // HW_OPT_SLAB_KERNEL
+  int fp64_hx_ff = 1;          // HW_OPT_FP64_HX: the mixed solver's FP64 H X with double-float angular transforms
+  bool ff_solve = false;       // a mixed-precision solve with fp64_hx_ff is running
+  bool ff_now = false;         // the FP64 H X being launched uses the double-float angular kernel
   int radial_tc = 1;           // HW_OPT_RADIAL_KERNEL
   int64_t rr_fallbacks = 0;    // Householder results rejected by the check (Jacobi used)
   // residual history of the last hw_solve_eigs: per k-point slot, per iteration (filter cycle

@@ -21,11 +21,13 @@
 // pass extracts only the kept bins.  T is double (FP64 path) or float (mixed path); the
 // diagonal term is always applied in FP64.
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 #include <vector>
 
 #include "hw_common.cuh"
 #include "hw_ctx.h"
+#include "hw_ff.cuh"
 
 namespace hw {
 
@@ -900,7 +902,7 @@ __device__ __forceinline__ void dft12(R (&xr)[12], R (&xi)[12]) {
 // as two radix-2 steps over the lane bits; lane q ends with X[q1 + 2 q0]
 template <int S, typename R>
 __device__ __forceinline__ void quad_dft(R& vr, R& vi, int q) {
-  R pr = __shfl_xor_sync(0xffffffffu, vr, 2), pi = __shfl_xor_sync(0xffffffffu, vi, 2);
+  R pr = shfl_xor(vr, 2), pi = shfl_xor(vi, 2);
   if (q & 2) {
     vr = pr - vr;
     vi = pi - vi;
@@ -913,8 +915,8 @@ __device__ __forceinline__ void quad_dft(R& vr, R& vi, int q) {
     vr = -S * vi;
     vi = S * t;
   }
-  pr = __shfl_xor_sync(0xffffffffu, vr, 1);
-  pi = __shfl_xor_sync(0xffffffffu, vi, 1);
+  pr = shfl_xor(vr, 1);
+  pi = shfl_xor(vi, 1);
   if (q & 1) {
     vr = pr - vr;
     vi = pi - vi;
@@ -941,27 +943,37 @@ __device__ __forceinline__ void quad_dft(R& vr, R& vi, int q) {
 // the quads' accesses spread over the banks).
 constexpr int SQ_RS = 49;
 
+// T: the storage type of G, H, the tables and the potential; R: the arithmetic type (T itself,
+// or double-float `ff` for T = double, with the potential given as FP32 pairs in Vr).
 // FP32: three CTAs per SM (80 registers, a few spilled: 60.6 us per 64-column launch against
-// 65.9 at two CTAs and 112 registers, 63.9 at four and 64)
-template <typename T>
-__global__ void __launch_bounds__(SLAB_THREADS, sizeof(T) == 4 ? 3 : 1) k_slab_q(SlabArgs<T> A, int SQ) {
+// 65.9 at two CTAs and 112 registers, 63.9 at four and 64).  Double-float: two CTAs per SM
+// (128 registers, none spilled: 557 us per 76-column launch against 816 at one CTA and 193
+// registers; three CTAs spill 420 bytes).
+template <typename T, typename R = T>
+__global__ void __launch_bounds__(SLAB_THREADS, sizeof(R) == 4 ? 3 : (std::is_same<T, R>::value ? 1 : 2))
+    k_slab_q(SlabArgs<T> A, const R* __restrict__ Vr, int SQ) {
   using V = cplx_t<T>;
+  using C = rc_t<R>;
   constexpr int n1 = 64, n2 = 48;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nmr = A.nmr, p = blockIdx.y, c0 = blockIdx.x * SQ;
-  V* Tb = reinterpret_cast<V*>(smem_raw);   // [SQ][nmr][SQ_RS]
-  V* E4 = Tb + (size_t)SQ * nmr * SQ_RS;    // [16][4]: omega^(m_r q), zero past nmr
-  V* T48 = E4 + 64;                         // [48]: e^(-2 pi i t / 48)
+  C* Tb = reinterpret_cast<C*>(smem_raw);   // [SQ][nmr][SQ_RS]
+  C* E4 = Tb + (size_t)SQ * nmr * SQ_RS;    // [16][4]: omega^(m_r q), zero past nmr
+  C* T48 = E4 + 64;                         // [48]: e^(-2 pi i t / 48)
+  const R zr = R(0);
   for (int t = threadIdx.x; t < 64; t += blockDim.x) {
     const int r = t >> 2, q = t & 3;
-    V e = mk<T>(T(0), T(0));
+    C e = mkr<R>(zr, zr);
     if (r < nmr) {
       const V w = A.tw1[pmod(A.mrow_m[r] * q, n1)];   // e^{-2 pi i m q / 64}
-      e = mk<T>(w.x, -w.y);
+      e = mkr<R>(to_r<R>(w.x), to_r<R>(-w.y));
     }
     E4[t] = e;
   }
-  for (int t = threadIdx.x; t < n2; t += blockDim.x) T48[t] = A.tw2[t];
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+    const V w = A.tw2[t];
+    T48[t] = mkr<R>(to_r<R>(w.x), to_r<R>(w.y));
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31, q = lane & 3;
   const int nq2 = SQ * nmr * 4;   // theta2 lanes
@@ -972,75 +984,75 @@ __global__ void __launch_bounds__(SLAB_THREADS, sizeof(T) == 4 ? 3 : 1) k_slab_q
     const bool valid = t < nq2 && c < A.ncols;
     const V* Gc = A.G + ((size_t)(valid ? c : 0) * A.Nr + p) * A.nA;
     const int* sp = A.slot_pair + (size_t)(valid ? r : 0) * n2 + q;
-    T xr[12], xi[12];
+    R xr[12], xi[12];
 #pragma unroll
     for (int a = 0; a < 12; ++a) {
       const int pa = valid ? sp[4 * a] : -1;
       V v = mk<T>(T(0), T(0));
       if (pa >= 0) v = Gc[pa];
-      xr[a] = v.x;
-      xi[a] = v.y;
+      xr[a] = to_r<R>(v.x);
+      xi[a] = to_r<R>(v.y);
     }
-    dft12<+1, T>(xr, xi);
-    V* row = Tb + ((size_t)s * nmr + r) * SQ_RS + 12 * ((q >> 1) + 2 * (q & 1));
+    dft12<+1, R>(xr, xi);
+    C* row = Tb + ((size_t)s * nmr + r) * SQ_RS + 12 * ((q >> 1) + 2 * (q & 1));
 #pragma unroll
     for (int cc = 0; cc < 12; ++cc) {
-      const V w = T48[q * cc];   // times e^{+2 pi i q c / 48}
-      T vr = xr[cc] * w.x + xi[cc] * w.y, vi = xi[cc] * w.x - xr[cc] * w.y;
-      quad_dft<+1, T>(vr, vi, q);
-      if (valid) row[cc] = mk<T>(vr, vi);
+      const C w = T48[q * cc];   // times e^{+2 pi i q c / 48}
+      R vr = xr[cc] * w.x + xi[cc] * w.y, vi = xi[cc] * w.x - xr[cc] * w.y;
+      quad_dft<+1, R>(vr, vi, q);
+      if (valid) row[cc] = mkr<R>(vr, vi);
     }
   }
   __syncthreads();
   // ---- theta1 inverse, x V, theta1 forward, in place on Tb
-  const T* Vp = A.V + (size_t)p * n2 * n1;
+  const R* Vp = Vr + (size_t)p * n2 * n1;
   for (int t = threadIdx.x; t < SQ * n2 * 4; t += blockDim.x) {
     const int sj = t >> 2, s = sj / n2, j = sj - s * n2;
-    V* col = Tb + (size_t)s * nmr * SQ_RS + j;
-    T xr[16], xi[16];
+    C* col = Tb + (size_t)s * nmr * SQ_RS + j;
+    R xr[16], xi[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-      xr[r] = T(0);
-      xi[r] = T(0);
+      xr[r] = zr;
+      xi[r] = zr;
       if (r < nmr) {
-        const V u = col[r * SQ_RS], e = E4[4 * r + q];
+        const C u = col[r * SQ_RS], e = E4[4 * r + q];
         xr[r] = u.x * e.x - u.y * e.y;
         xi[r] = u.x * e.y + u.y * e.x;
       }
     }
-    dft16<+1, T>(xr, xi);   // the points 4 t + q, up to W^(m_0 t)
-    const T* Vrow = Vp + (size_t)j * n1 + q;
+    dft16<+1, R>(xr, xi);   // the points 4 t + q, up to W^(m_0 t)
+    const R* Vrow = Vp + (size_t)j * n1 + q;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      const T v = Vrow[4 * k];
+      const R v = Vrow[4 * k];
       xr[k] *= v;
       xi[k] *= v;
     }
-    dft16<-1, T>(xr, xi);   // slot r: this lane's share of row r, up to omega^(-m_r q)
+    dft16<-1, R>(xr, xi);   // slot r: this lane's share of row r, up to omega^(-m_r q)
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-      const V e = E4[4 * r + q];   // times conj(omega^(m_r q))
-      const T vr = xr[r] * e.x + xi[r] * e.y, vi = xi[r] * e.x - xr[r] * e.y;
+      const C e = E4[4 * r + q];   // times conj(omega^(m_r q))
+      const R vr = xr[r] * e.x + xi[r] * e.y, vi = xi[r] * e.x - xr[r] * e.y;
       xr[r] = vr;
       xi[r] = vi;
     }
     // reduce-scatter over the quad: rows 8 h .. 8 h + 7 (h = q >> 1), then 4 q .. 4 q + 3
     const bool h = q & 2, l = q & 1;
-    T kr[8], ki[8];
+    R kr[8], ki[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const T sr = h ? xr[i] : xr[8 + i], si = h ? xi[i] : xi[8 + i];
-      kr[i] = (h ? xr[8 + i] : xr[i]) + __shfl_xor_sync(0xffffffffu, sr, 2);
-      ki[i] = (h ? xi[8 + i] : xi[i]) + __shfl_xor_sync(0xffffffffu, si, 2);
+      const R sr = h ? xr[i] : xr[8 + i], si = h ? xi[i] : xi[8 + i];
+      kr[i] = (h ? xr[8 + i] : xr[i]) + shfl_xor(sr, 2);
+      ki[i] = (h ? xi[8 + i] : xi[i]) + shfl_xor(si, 2);
     }
     __syncwarp();   // every lane of the quad has read its column of Tb
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const T sr = l ? kr[i] : kr[4 + i], si = l ? ki[i] : ki[4 + i];
-      const T vr = (l ? kr[4 + i] : kr[i]) + __shfl_xor_sync(0xffffffffu, sr, 1);
-      const T vi = (l ? ki[4 + i] : ki[i]) + __shfl_xor_sync(0xffffffffu, si, 1);
+      const R sr = l ? kr[i] : kr[4 + i], si = l ? ki[i] : ki[4 + i];
+      const R vr = (l ? kr[4 + i] : kr[i]) + shfl_xor(sr, 1);
+      const R vi = (l ? ki[4 + i] : ki[i]) + shfl_xor(si, 1);
       const int r = 4 * q + i;
-      if (r < nmr) col[r * SQ_RS] = mk<T>(vr, vi);
+      if (r < nmr) col[r * SQ_RS] = mkr<R>(vr, vi);
     }
   }
   __syncthreads();
@@ -1049,26 +1061,26 @@ __global__ void __launch_bounds__(SLAB_THREADS, sizeof(T) == 4 ? 3 : 1) k_slab_q
     const int t = threadIdx.x, sr = t >> 2, s = sr / nmr, r = sr - s * nmr;
     const int c = c0 + s;
     const bool valid = t < nq2 && c < A.ncols;
-    const V* row = Tb + ((size_t)(valid ? s * nmr + r : 0)) * SQ_RS + 12 * q;
+    const C* row = Tb + ((size_t)(valid ? s * nmr + r : 0)) * SQ_RS + 12 * q;
     const int b = (q >> 1) + 2 * (q & 1);   // this lane's n mod 4 after the quad DFT
-    T xr[12], xi[12];
+    R xr[12], xi[12];
 #pragma unroll
     for (int cc = 0; cc < 12; ++cc) {
-      const V u = row[cc];
-      T vr = u.x, vi = u.y;
-      quad_dft<-1, T>(vr, vi, q);
-      const V w = T48[b * cc];   // times e^{-2 pi i b c / 48}
+      const C u = row[cc];
+      R vr = u.x, vi = u.y;
+      quad_dft<-1, R>(vr, vi, q);
+      const C w = T48[b * cc];   // times e^{-2 pi i b c / 48}
       xr[cc] = vr * w.x - vi * w.y;
       xi[cc] = vr * w.y + vi * w.x;
     }
-    dft12<-1, T>(xr, xi);   // F[4 a + b]
+    dft12<-1, R>(xr, xi);   // F[4 a + b]
     if (valid) {
       V* Hc = A.H + ((size_t)c * A.Nr + p) * A.nA;
       const int* sp = A.slot_pair + (size_t)r * n2 + b;
 #pragma unroll
       for (int a = 0; a < 12; ++a) {
         const int pa = sp[4 * a];
-        if (pa >= 0) Hc[pa] = mk<T>(xr[a], xi[a]);
+        if (pa >= 0) Hc[pa] = mk<T>(from_r<T>(xr[a]), from_r<T>(xi[a]));
       }
     }
   }
@@ -1095,13 +1107,20 @@ static bool use_slab_r16(const hw_ctx* ctx, size_t elem) {
 // the all-register variant (HW_OPT_SLAB_KERNEL = 2: FP32 only, the FP64 transforms stay on
 // k_slab_r16, whose FP64-pipe work the register variant does not lower; 3: both precisions):
 // 64 x 48 grid, at most 16 kept m rows, and those consecutive (m_r = m_0 + r)
-static bool use_slab_q(const hw_ctx* ctx, size_t elem) {
+static bool slab_q_shape(const hw_ctx* ctx) {
   const auto& mm = ctx->hb.mrow_m;
-  const bool want = ctx->slab_r16 == 3 || (ctx->slab_r16 == 2 && elem == sizeof(float2));
-  if (!want || !use_slab_r16(ctx, elem) || mm.empty() || mm.size() > 16) return false;
+  if (ctx->hb.prm.Nth1 != 64 || ctx->hb.prm.Nth2 != 48 || mm.empty() || mm.size() > 16) return false;
   for (size_t r = 1; r < mm.size(); ++r)
     if (mm[r] != mm[0] + (int)r) return false;
   return true;
+}
+static bool use_slab_q(const hw_ctx* ctx, size_t elem) {
+  const bool want = ctx->slab_r16 == 3 || (ctx->slab_r16 == 2 && elem == sizeof(float2));
+  return want && slab_q_shape(ctx);
+}
+// an FP64 H X (elem = 16 bytes) launched with double-float angular transforms
+static bool use_slab_ff(const hw_ctx* ctx, size_t elem) {
+  return ctx->ff_now && elem == sizeof(double2) && slab_q_shape(ctx);
 }
 
 // --------------------------------------------------------------------------- host launcher
@@ -1116,10 +1135,16 @@ static void* slab_kernel(int n1, int n2) {
 
 template <typename T>
 static cudaError_t launch_slab(const hw_ctx* ctx, dim3 grid, size_t smem, const SlabArgs<T>& sa) {
-  if (use_slab_q(ctx, sizeof(cplx_t<T>))) {
+  if (use_slab_ff(ctx, sizeof(cplx_t<T>)) || use_slab_q(ctx, sizeof(cplx_t<T>))) {
     const int sq = slab_q_per_cta(sa.nmr);
     const dim3 g((grid.x + sq - 1) / sq, grid.y);
-    k_slab_q<T><<<g, SLAB_THREADS, smem, ctx->stream>>>(sa, sq);
+    if constexpr (sizeof(T) == sizeof(double)) {
+      if (use_slab_ff(ctx, sizeof(cplx_t<T>))) {
+        k_slab_q<double, ff><<<g, SLAB_THREADS, smem, ctx->stream>>>(sa, reinterpret_cast<const ff*>(ctx->db.vff), sq);
+        return cudaGetLastError();
+      }
+    }
+    k_slab_q<T><<<g, SLAB_THREADS, smem, ctx->stream>>>(sa, sa.V, sq);
     return cudaGetLastError();
   }
   void* f = use_slab_r16(ctx, sizeof(cplx_t<T>)) ? (void*)k_slab_r16<T, 64, 48> : slab_kernel<T>(sa.Nth1, sa.Nth2);
@@ -1139,7 +1164,7 @@ size_t slab_smem_bytes(const hw_ctx* ctx, size_t elem, int Jc) {
   const auto& hb = ctx->hb;
   const int nmr = (int)hb.mrow_m.size();
   const int n1 = hb.prm.Nth1, n2 = hb.prm.Nth2;
-  if (use_slab_q(ctx, elem)) return slab_q_smem_bytes(nmr, elem);            // no theta2 chunks
+  if (use_slab_q(ctx, elem) || use_slab_ff(ctx, elem)) return slab_q_smem_bytes(nmr, elem);   // no theta2 chunks
   if (use_slab_r16(ctx, elem)) return slab_r16_smem_bytes(nmr, n2, elem);
   // padded layout: the FP32 kernels specialised for the grid (k_slab's PAD)
   const bool pad = elem == sizeof(float2) && slab_kernel<float>(n1, n2) != (void*)k_slab<float, 0, 0>;
@@ -1681,7 +1706,7 @@ cudaError_t hx_configure(hw_ctx* ctx) {
   for (void* f : {(void*)k_slab<double, 0, 0>, (void*)k_slab<float, 0, 0>, (void*)k_slab<double, 64, 48>,
                   (void*)k_slab<float, 64, 48>, (void*)k_slab<double, 192, 96>, (void*)k_slab<float, 192, 96>,
                   (void*)k_slab_r16<float, 64, 48>, (void*)k_slab_r16<double, 64, 48>, (void*)k_slab_q<float>,
-                  (void*)k_slab_q<double>})
+                  (void*)k_slab_q<double>, (void*)k_slab_q<double, ff>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   (void)ctx;
   return e;

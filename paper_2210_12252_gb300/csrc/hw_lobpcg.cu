@@ -770,7 +770,9 @@ static hw_status apply_block(hw_ctx* ctx, LobpcgWork* w, const std::vector<int>&
   }
   if (blk.nslot == 0) return HW_OK;
   const ChebStep* sp = step ? &cs : nullptr;
+  ctx->ff_now = fp64 && ctx->ff_solve;   // a mixed solve's FP64 H X: double-float angular transforms
   cudaError_t e = fp64 ? launch_hx<double>(ctx, blk, ncol, w->Lpad, sp) : launch_hx<float>(ctx, blk, ncol, w->Lpad, sp);
+  ctx->ff_now = false;
   if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("apply_H: ") + cudaGetErrorString(e));
   return HW_OK;
 }
@@ -1949,10 +1951,18 @@ extern "C" hw_status hw_get_residual_history(hw_ctx* ctx, int k, int* phase, dou
   return HW_OK;
 }
 
+// marks a mixed-precision solve whose FP64 H X takes the double-float angular kernel
+struct FfSolveScope {
+  hw_ctx* c;
+  FfSolveScope(hw_ctx* ctx, hw_prec prec) : c(ctx) { c->ff_solve = prec == HW_MIXED && c->fp64_hx_ff; }
+  ~FfSolveScope() { c->ff_solve = false; }
+};
+
 static hw_status solve_window(hw_ctx* ctx, int nk, const int* kidx, int n_eig, int block, double tol, int maxit,
                               hw_prec prec, int precond_kind, const double* const* X0, double* evals,
                               double* const* evecs, int64_t ld_evecs, int* iters, double* resid, const Deflate* df,
                               double tol_accept = 0.0) {
+  FfSolveScope ffs(ctx, prec);
   if (ctx->eigensolver == 1)
     return chfsi_impl(ctx, nk, kidx, n_eig, block, tol, maxit, prec, precond_kind, X0, evals, evecs, ld_evecs, iters,
                       resid, df, tol_accept);
@@ -2070,6 +2080,7 @@ extern "C" hw_status hw_solve_eigs_traced(hw_ctx* ctx, int k, int n_eig, int blo
     return hw_fail(ctx, HW_EINVAL, "bad k-point or ld");
   Trace tr{n_rec, rec_iters, rec_R, rec_E, rec_theta, rec_res, ld, std::vector<char>(std::max(n_rec, 0), 0)};
   const double* x0[1] = {X0};
+  FfSolveScope ffs(ctx, prec);
   return solve_impl(ctx, 1, &k, n_eig, block, tol, maxit, prec, precond_kind, X0 ? x0 : nullptr, evals, nullptr,
                     0, iters, nullptr, &tr);
 }

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhelicwave.so")
 
 HW_OK, HW_EINVAL, HW_ENOMEM, HW_ECUDA, HW_ESTATE, HW_ENOTCONV, HW_ETIMEOUT = range(7)
-HW_FP64, HW_MIXED = 0, 1
+HW_FP64, HW_MIXED, HW_FP64_DF = 0, 1, 2
 HW_PRECOND_TPA, HW_PRECOND_LEARNED, HW_PRECOND_NONE = 0, 1, 2
 STATUS_NAMES = ["HW_OK", "HW_EINVAL", "HW_ENOMEM", "HW_ECUDA", "HW_ESTATE", "HW_ENOTCONV",
                 "HW_ETIMEOUT"]
@@ -275,6 +275,7 @@ HW_OPT_TAIL_NO_P = 10
 HW_OPT_WINDOW = 11
 HW_OPT_TC_GEMM = 12
 HW_OPT_RADIAL_KERNEL = 13
+HW_OPT_FP64_HX = 14
 
 
 def hw_set_option(h, option, value):
@@ -453,7 +454,7 @@ def hw_solve_eigs_traced(h, k, n_eig, block, tol, maxit, prec, precond, X0_ptr, 
 
 # ----------------------------------------------------------------------------- Context
 
-_PREC = {"fp64": HW_FP64, "mixed": HW_MIXED}
+_PREC = {"fp64": HW_FP64, "mixed": HW_MIXED, "fp64_df": HW_FP64_DF}
 _PRECOND = {"tpa": HW_PRECOND_TPA, "learned": HW_PRECOND_LEARNED, "none": HW_PRECOND_NONE}
 
 

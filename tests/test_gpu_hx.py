@@ -204,3 +204,20 @@ def test_apply_H_fp64_tube_slab_variants_agree(tube, hwmod):
             assert_entrywise(Y, Yref, FP64_TOL, FP64_FLOOR, f"FP64 slab variant {v}")
     finally:
         tube.ctx.set_option(hwmod.HW_OPT_SLAB_KERNEL, keep)
+
+
+def test_apply_H_fp64_df_tube_matches_oracle(tube, hwmod):
+    """hw_apply_H with HW_FP64_DF: the angular transforms in double-float arithmetic (FP32 pairs),
+    radial transforms and diagonal in FP64.  Entry-wise within the FP64 tolerance of the oracle,
+    and within 1e-12 (column norms) of the FP64 kernel; 9 ragged columns (three CTAs of 4 slabs,
+    the last with one), padded leading dimension."""
+    kp = tube.kps[0]
+    X = inputs.random_block(kp.L, 9, 85)
+    Yref = Hm.apply_H(kp, tube.V, X)
+    Xd = to_dev(X, kp.L + 2)
+    Ydf = from_dev(tube.ctx.apply_H(0, Xd, prec="fp64_df"), kp.L)
+    Y64 = from_dev(tube.ctx.apply_H(0, Xd, prec="fp64"), kp.L)
+    assert rel_err(Ydf, Yref) < FP64_TOL
+    assert_entrywise(Ydf, Yref, FP64_TOL, FP64_FLOOR, "double-float angular transforms")
+    assert rel_err(Ydf, Y64) < 1e-12
+    print(f"double-float vs FP64 kernel: {rel_err(Ydf, Y64):.2e}; vs oracle {rel_err(Ydf, Yref):.2e}")
