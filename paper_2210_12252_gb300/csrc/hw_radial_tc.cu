@@ -129,7 +129,6 @@ __global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(const __grid_constant__ 
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     load_table_tma(&tmT, g, NP, KB, sB, &bar_tab);
   }
-  if (warp == 0) tmem_alloc(&tmem_s, tcols);
   if (threadIdx.x < RT_ITEMS) {
     const int q = threadIdx.x;
     const long item = q0 + q;
@@ -185,6 +184,9 @@ __global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(const __grid_constant__ 
       put3(tile, 2 * q + 1, lane, im);
     }
   }
+  // TMEM only now: a CTA waiting for columns (2 N_r of them, so that at most two CTAs per SM
+  // hold TMEM) has done its gathers meanwhile
+  if (warp == 0) tmem_alloc(&tmem_s, tcols);
   fence_proxy_async();
   tc_fence_before();
   __syncthreads();
@@ -208,21 +210,25 @@ __global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(const __grid_constant__ 
   bool ok = tab_ok && mbar_wait(&bar_mma, 0);
   if (!ok && threadIdx.x == 0) atomicExch(A.status, HW_ETIMEOUT);
   tc_fence_after();
-  if (warp < 4 && ok) {
-    // lane quadrant = warp: row 2q + part holds D[row][p] for all p
-    const int row = warp * 32 + lane, q = row >> 1, part = row & 1;
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+  if (ok) {
+    // lane quadrant = warp % 4: row 2q + part holds D[row][p] for all p; warps w and w + 4 take
+    // alternate 16-column chunks.  The lanes of an item's re and im rows swap halves so that
+    // each stores one complex entry per column pair: the re lane column p, the im lane p + 1.
+    const int quad = warp & 3, half = warp >> 2;
+    const int row = quad * 32 + lane, q = row >> 1, part = row & 1;
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
     float2* gp = s_g[q];
-    for (int p0 = 0; p0 < NP; p0 += 16) {
+    for (int p0 = 16 * half; p0 < NP; p0 += 32) {
       uint32_t v[16], u[16];
       tmem_ld16(tl + (uint32_t)p0, v);
       tmem_ld16(tl + (uint32_t)(NP + p0), u);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float mine = __uint_as_float(v[j]) + __uint_as_float(u[j]);
-        const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
-        const int p = p0 + j;
-        if (part == 0 && gp && p < A.Nr) gp[(size_t)p * A.nA] = make_float2(mine, other);
+      for (int j = 0; j < 16; j += 2) {
+        const float a0 = __uint_as_float(v[j]) + __uint_as_float(u[j]);           // this part, column p0 + j
+        const float a1 = __uint_as_float(v[j + 1]) + __uint_as_float(u[j + 1]);   // column p0 + j + 1
+        const float got = __shfl_xor_sync(0xffffffffu, part ? a0 : a1, 1);
+        const int p = p0 + j + part;
+        if (gp && p < A.Nr) gp[(size_t)p * A.nA] = part ? make_float2(got, a1) : make_float2(a0, got);
       }
     }
   }
@@ -303,16 +309,16 @@ __global__ void __launch_bounds__(RT_THREADS, 3) k_rfwd_tc(const __grid_constant
   const int li = lane & 7, lp = lane >> 3;
   for (int j = 0; j < KBP; ++j) {
     const int st = j & 1;
-    if (j >= 2 && !mbar_wait(&bar_mma[st], (uint32_t)(((j - 2) >> 1) & 1))) s_bad = 1;
     unsigned char* tile = sA + (size_t)st * RT_ATILE;
     float2 h[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 8; ++i) {   // the loads first: they overlap the wait for the stage
       const int t = warp + 8 * i;
       const int q = (t & 7) * 8 + li, p = j * 32 + (t >> 3) * 4 + lp;
       const float2* hp = s_h[q];
       h[i] = (hp && p < Nr) ? hp[(size_t)p * A.nA] : make_float2(0.f, 0.f);
     }
+    if (j >= 2 && !mbar_wait(&bar_mma[st], (uint32_t)(((j - 2) >> 1) & 1))) s_bad = 1;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int t = warp + 8 * i;
@@ -339,10 +345,11 @@ __global__ void __launch_bounds__(RT_THREADS, 3) k_rfwd_tc(const __grid_constant
   if (!ok && threadIdx.x == 0) atomicExch(A.status, HW_ETIMEOUT);
   tc_fence_after();
   __syncthreads();   // every thread is past its reads of the A stages (Ys reuses them)
-  if (warp < 4 && ok) {
-    const int row = warp * 32 + lane, q = row >> 1, part = row & 1;
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int k0 = 0; k0 < KP; k0 += 16) {
+  if (ok) {   // lane quadrant = warp % 4; warps w and w + 4 take alternate 16-column chunks
+    const int quad = warp & 3, half = warp >> 2;
+    const int row = quad * 32 + lane, q = row >> 1, part = row & 1;
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+    for (int k0 = 16 * half; k0 < KP; k0 += 32) {
       uint32_t v[16], u[16];
       tmem_ld16(tl + (uint32_t)k0, v);
       tmem_ld16(tl + (uint32_t)(KP + k0), u);
