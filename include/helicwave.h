@@ -274,6 +274,18 @@ hw_status hw_get_residual_history(hw_ctx* ctx, int k, int* phase, double* res, i
 hw_status hw_selftest_barrier(hw_ctx* ctx, int nblocks, long long spin_limit, int skip_block,
                               int* wait_status);
 
+/* The eigensolver's Cholesky factorisation on its own (the factor step of its Cholesky-QR
+ * orthonormalisation, Sec. "Eigensolvers and Preconditioning"): G = L L^H for nprob Hermitian
+ * positive definite n x n matrices.  G: device, complex128 column-major, problem b at
+ * G + 2 n^2 b doubles, only its lower triangle read, overwritten (used as scratch); L: device,
+ * same layout, distinct from G, receives the lower factor with zeros above the diagonal.
+ * prec: HW_FP64 (FP64 arithmetic) or HW_MIXED (FP32 arithmetic, as in the mixed solver's first
+ * phase; n <= 160).  n <= 112 runs the unblocked kernel (one barrier per column), larger n
+ * the blocked one.  fail: host [nprob]: 0, or 1 + the column of the first pivot that is not
+ * positive and finite (that problem's L is then not a factor).  1 <= nprob <= 64.
+ * Synchronous. */
+hw_status hw_cholesky(hw_ctx* ctx, int n, int nprob, double* G, double* L, int* fail, hw_prec prec);
+
 /* The Rayleigh-Ritz step's dense Hermitian eigensolver on its own (Sec. "Eigensolvers and
  * Preconditioning": the small projected eigenproblem of LOBPCG).  A: device, nprob Hermitian
  * n x n complex128 matrices (column-major, contiguous, n even, read only); w: device

@@ -189,6 +189,80 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol(double2* G, int n, int64_
   if (threadIdx.x == 0) fail[b] = bad;
 }
 
+// Unblocked right-looking Cholesky for the solver's block sizes (n <= CHS_NMAX), one CTA of
+// CHS_THREADS per problem, one barrier per column: the lower triangle sits row-major in shared
+// memory with an odd row pitch (n | 1: a warp's reads down a column fall in distinct banks);
+// every thread reads the pivot d = a[c][c] itself and applies
+//   a[i][k] -= a[i][c] conj(a[k][c]) / d,   c < k <= i,
+// a warp per trailing row i (round robin), its lanes across k; the columns are scaled by
+// 1 / sqrt(d) at the end.  Same input, output and fail[] contract as k_chol (a pivot that is
+// not positive and finite stops the factorisation: fail = 1 + its column).
+constexpr int CHS_THREADS = 512;
+constexpr int CHS_NMAX = 112;
+
+template <typename T>
+__global__ void __launch_bounds__(CHS_THREADS) k_chol_small(double2* G, int n, int64_t sG, int* fail) {
+  using C = typename Cx<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* a = reinterpret_cast<C*>(smem_raw);
+  const int b = blockIdx.x, ld = n | 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  double2* g = G + (size_t)b * sG;
+  for (int k = warp; k < n; k += nwarp)   // column k of the source (column-major), rows i >= k
+    for (int i = k + lane; i < n; i += 32) a[i * ld + k] = ld_c<T>(g[i + (size_t)k * n]);
+  __syncthreads();
+  int bad = 0;
+  for (int c = 0; c < n; ++c) {
+    const T d = a[c * ld + c].x;   // the same value for every thread: a uniform stop
+    if (!(d > (T)0) || !isfinite(d)) {
+      bad = c + 1;
+      break;
+    }
+    const T id = (T)1 / d;
+    for (int i = c + 1 + warp; i < n; i += nwarp) {
+      const C li = a[i * ld + c];
+      for (int k = c + 1 + lane; k <= i; k += 32) {
+        const C lk = a[k * ld + c];
+        C v = a[i * ld + k];
+        v.x -= (li.x * lk.x + li.y * lk.y) * id;
+        v.y -= (li.y * lk.x - li.x * lk.y) * id;
+        a[i * ld + k] = v;
+      }
+    }
+    __syncthreads();
+  }
+  if (!bad) {   // (uniform) scale: L[i][c] = a[i][c] / sqrt(a[c][c]), the roots taken first
+    T* sq = reinterpret_cast<T*>(a + (size_t)n * ld);   // [n]
+    for (int c = threadIdx.x; c < n; c += blockDim.x) sq[c] = sqrt(a[c * ld + c].x);
+    __syncthreads();
+    for (int i = warp; i < n; i += nwarp)
+      for (int c = lane; c <= i; c += 32) {
+        C v = a[i * ld + c];
+        if (i == c) {
+          v.x = sq[c];
+          v.y = (T)0;
+        } else {
+          v.x /= sq[c];
+          v.y /= sq[c];
+        }
+        a[i * ld + c] = v;
+      }
+  }
+  __syncthreads();
+  // out: column-major, zeros above the diagonal; complex64 into the first n*n*8 bytes of the
+  // problem's slot for T = float (what the FP32 triangular solve reads), complex128 otherwise
+  for (int k = warp; k < n; k += nwarp)
+    for (int i = lane; i < n; i += 32) {
+      const C v = i >= k ? a[i * ld + k] : C{(T)0, (T)0};
+      const size_t t = i + (size_t)k * n;
+      if (sizeof(T) == sizeof(float))
+        reinterpret_cast<float2*>(g)[t] = make_float2((float)v.x, (float)v.y);
+      else
+        g[t] = make_double2((double)v.x, (double)v.y);
+    }
+  if (threadIdx.x == 0) fail[b] = bad;
+}
+
 // Given lower L (n x n), write Uinv = (L^H)^{-1} (upper triangular) into Ui.  Column j of
 // L^{-1} by forward substitution (one thread per column); Uinv = (L^{-1})^H.
 __global__ void k_trinv(const double2* L, int64_t sL, double2* Ui, int64_t sU, int n) {
@@ -591,7 +665,20 @@ cudaError_t dense_heev(DenseWork* dw, cudaStream_t st, double2* A, int n, int np
   return cudaGetLastError();
 }
 
+static size_t chol_small_smem(int n, size_t elem) { return (size_t)n * (n | 1) * elem + (size_t)n * (elem / 2); }
+
 cudaError_t dense_chol(cudaStream_t st, double2* G, int n, int nprob, int* fail, bool fp32) {
+  if (n <= CHS_NMAX) {   // the solver's block sizes: the unblocked kernel
+    if (fp32) {
+      cudaFuncSetAttribute(k_chol_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      k_chol_small<float><<<nprob, CHS_THREADS, chol_small_smem(n, sizeof(float2)), st>>>(G, n, (int64_t)n * n, fail);
+    } else {
+      cudaFuncSetAttribute(k_chol_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+      k_chol_small<double><<<nprob, CHS_THREADS, chol_small_smem(n, sizeof(double2)), st>>>(G, n, (int64_t)n * n,
+                                                                                             fail);
+    }
+    return cudaGetLastError();
+  }
   if (fp32) {
     const size_t bytes = (size_t)n * n * sizeof(float2);
     if (bytes > 200 * 1024) return cudaErrorInvalidValue;

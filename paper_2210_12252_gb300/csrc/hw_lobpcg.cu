@@ -1917,6 +1917,47 @@ extern "C" hw_status hw_heev(hw_ctx* ctx, int n, int nprob, int nw, const double
   return HW_OK;
 }
 
+// complex64 factors in the first n*n*8 bytes of each n*n*16-byte slot -> complex128 in dst
+__global__ void k_factor_c64_to_c128(const double2* slots, double2* dst, int n) {
+  const float2* f = reinterpret_cast<const float2*>(slots + (size_t)blockIdx.y * n * n);
+  double2* d = dst + (size_t)blockIdx.y * n * n;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * n; t += gridDim.x * blockDim.x)
+    d[t] = make_double2((double)f[t].x, (double)f[t].y);
+}
+
+extern "C" hw_status hw_cholesky(hw_ctx* ctx, int n, int nprob, double* G, double* L, int* fail, hw_prec prec) {
+  if (!ctx) return HW_EINVAL;
+  if (ctx->device < 0) return hw_fail(ctx, HW_ESTATE, "host-only context has no device");
+  if (n < 1 || nprob < 1 || nprob > MAXSLOT || !G || !L || !fail || G == L)
+    return hw_fail(ctx, HW_EINVAL, "need n >= 1, 1 <= nprob <= 64, distinct G and L, a fail array");
+  if (prec != HW_FP64 && prec != HW_MIXED) return hw_fail(ctx, HW_EINVAL, "precision HW_FP64 or HW_MIXED");
+  if (prec == HW_MIXED && (size_t)n * n * sizeof(float2) > 200 * 1024)
+    return hw_fail(ctx, HW_EINVAL, "n too large for the FP32 factorisation (shared-memory bound, n <= 160)");
+  cudaSetDevice(ctx->device);
+  hw_status hs = ensure_work(ctx, nprob, 4, 8);
+  if (hs != HW_OK) return hs;
+  cudaStream_t st = ctx->stream;
+  const size_t bytes = (size_t)nprob * n * n * sizeof(double2);
+  double2* g = reinterpret_cast<double2*>(G);
+  double2* l = reinterpret_cast<double2*>(L);
+  cudaError_t e = cudaMemcpyAsync(l, g, bytes, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) {
+    ProfScope ps_(ctx, HW_PH_CHOL);
+    e = dense_chol(st, l, n, nprob, ctx->lw->fail, prec == HW_MIXED);
+    ctx->launches++;
+  }
+  if (e == cudaSuccess && prec == HW_MIXED) {   // the FP32 factor, widened through G
+    k_factor_c64_to_c128<<<dim3(16, nprob), 256, 0, st>>>(l, g, n);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(l, g, bytes, cudaMemcpyDeviceToDevice, st);
+    ctx->launches++;
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(fail, ctx->lw->fail, (size_t)nprob * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("cholesky: ") + cudaGetErrorString(e));
+  return HW_OK;
+}
+
 extern "C" hw_status hw_selftest_barrier(hw_ctx* ctx, int nblocks, long long spin_limit, int skip_block,
                                          int* wait_status) {
   if (!ctx) return HW_EINVAL;

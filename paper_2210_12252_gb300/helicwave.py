@@ -72,6 +72,8 @@ _SIGS = {
                               C.POINTER(C.c_int)]),
     "hw_heev": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                           C.c_int]),
+    "hw_cholesky": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_int),
+                              C.c_int]),
     "hw_get_residual_history": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), _D, C.c_int,
                                          C.POINTER(C.c_int)]),
     "hw_selftest_barrier": (C.c_int, [C.c_void_p, C.c_int, C.c_longlong, C.c_int, C.POINTER(C.c_int)]),
@@ -334,6 +336,20 @@ def hw_heev(h, A, nw, method=1):
     _check(h, load_library().hw_heev(h, n, nprob, nw, C.c_void_p(A.data_ptr()), C.c_void_p(w.data_ptr()),
                                      C.c_void_p(Z.data_ptr()), method))
     return w, Z
+
+
+def hw_cholesky(h, G, prec="fp64"):
+    """G: (nprob, n, n) complex128 CUDA tensor of Hermitian positive definite matrices (row j of
+    G[b] holds column j; only the lower triangle of each matrix is read; G is overwritten).
+    Returns (L, fail): L (nprob, n, n) with L[b][j] column j of the lower factor, fail a list of
+    0 or 1 + the column of a bad pivot."""
+    import torch
+    nprob, n, _ = G.shape
+    L = torch.zeros_like(G)
+    fail = (C.c_int * nprob)()
+    _check(h, load_library().hw_cholesky(h, n, nprob, C.c_void_p(G.data_ptr()), C.c_void_p(L.data_ptr()), fail,
+                                         _PREC[prec]))
+    return L, list(fail)
 
 
 HW_HIST_FILTER_FP32, HW_HIST_FILTER_FP64, HW_HIST_LOBPCG_FP32, HW_HIST_LOBPCG_HYBRID, HW_HIST_LOBPCG_FP64 = range(5)

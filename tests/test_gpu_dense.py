@@ -64,3 +64,57 @@ def test_heev_matches_numpy(hwmod, method, n):
         R = A[b] @ Zb - Zb * w[b, :nw]
         assert np.linalg.norm(R, axis=0).max() < 1e-10 * scale
     ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("mixed", 2e-5)])
+@pytest.mark.parametrize("n", [1, 17, 76, 112, 130])
+def test_cholesky_matches_numpy(hwmod, prec, tol, n):
+    """hw_cholesky (the Cholesky-QR's factor step): lower factors of Gram matrices X^H X of
+    random tall complex blocks (condition ~1e2) against numpy.linalg.cholesky, entry-wise
+    relative to the largest entry of the factor; n <= 112 is the unblocked kernel, 130 the
+    blocked one.  The upper triangle comes back zero; only the lower triangle of G is read
+    (the strict upper triangle here holds garbage)."""
+    ctx = hwmod.Context(0)
+    g = np.random.default_rng(100 + n)
+    mats = []
+    for b in range(3):
+        X = g.standard_normal((2 * n + 8, n)) + 1j * g.standard_normal((2 * n + 8, n))
+        X *= np.exp(g.uniform(-1.0, 1.0, n))        # column scales
+        mats.append(X.conj().T @ X)
+    A = np.stack(mats)
+    Ag = A.copy()
+    iu = np.triu_indices(n, 1)
+    for b in range(3):
+        Ag[b][iu] = 7.0 - 5.0j                        # never read
+    Gt = torch.from_numpy(np.ascontiguousarray(np.transpose(Ag, (0, 2, 1)))).cuda()
+    L, fail = hwmod.hw_cholesky(ctx.h, Gt, prec)
+    assert fail == [0, 0, 0]
+    L = np.transpose(L.cpu().numpy(), (0, 2, 1))      # back to L[b][i][j]
+    for b in range(3):
+        ref = np.linalg.cholesky(A[b])
+        err = np.abs(L[b] - ref).max() / np.abs(ref).max()
+        assert err < tol, (b, err)
+        assert np.all(L[b][iu] == 0)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("n", [40, 130])
+def test_cholesky_reports_the_first_bad_pivot(hwmod, prec, n):
+    """A Hermitian matrix whose leading 9 x 9 block is positive definite and whose 10th pivot is
+    negative: fail = 10 (1 + its column); the other problem of the batch factors normally."""
+    ctx = hwmod.Context(0)
+    g = np.random.default_rng(7)
+    X = g.standard_normal((2 * n, n)) + 1j * g.standard_normal((2 * n, n))
+    good = X.conj().T @ X
+    bad = good.copy()
+    # make the Schur complement at column 9 negative: set G[9][9] below the part explained by
+    # the first 9 columns
+    L9 = np.linalg.cholesky(good[:9, :9])
+    v = np.linalg.solve(L9, good[:9, 9])
+    bad[9, 9] = np.vdot(v, v).real - 1.0
+    A = np.stack([good, bad])
+    Gt = torch.from_numpy(np.ascontiguousarray(np.transpose(A, (0, 2, 1)))).cuda()
+    _, fail = hwmod.hw_cholesky(ctx.h, Gt, prec)
+    assert fail == [0, 10]
+    ctx.close()
