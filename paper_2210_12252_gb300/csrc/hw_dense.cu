@@ -1035,16 +1035,21 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
   __shared__ int nv_s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   const double2* a = H.A + (size_t)b * n * n;
+  // the diagonal into shared memory by all threads (in the v buffer, free until the first
+  // reflection), then thread 0 builds the index map from it: no serial global loads
+  double* dg = reinterpret_cast<double*>(v);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dg[i] = a[i + (size_t)i * n].x;
+  __syncthreads();
   if (threadIdx.x == 0) {
     int c = 0;
     for (int i = 0; i < n; ++i)
-      if (fabs(a[i + (size_t)i * n].x) < 1e9) mp[c++] = i;
+      if (fabs(dg[i]) < 1e9) mp[c++] = i;
     const int nvalid = c;
     for (int i = 0; i < n; ++i) {   // padding after, ascending by diagonal value
-      const double x = a[i + (size_t)i * n].x;
+      const double x = dg[i];
       if (fabs(x) < 1e9) continue;
       int q = c++;
-      while (q > nvalid && a[mp[q - 1] + (size_t)mp[q - 1] * n].x > x) {
+      while (q > nvalid && dg[mp[q - 1]] > x) {
         mp[q] = mp[q - 1];
         --q;
       }
@@ -1058,7 +1063,7 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) H.map[(size_t)b * n + i] = mp[i];
   // shift = mean of the valid diagonal
   float sd = 0.f;
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) sd += (float)a[mp[i] + (size_t)mp[i] * n].x;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) sd += (float)dg[mp[i]];
   sd = block_sum_f(sd, red);
   const double mu = nv > 0 ? (double)(sd / (float)nv) : 0.0;
   // load the valid lower triangle, FP64 -> FP32, shifted: row i of the lower triangle is the
@@ -1072,14 +1077,24 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
   }
   __syncthreads();
   float2* vq = H.vq + (size_t)b * n * n;
+  // Three block barriers per reflection: the squared norm of the next column below the diagonal
+  // is summed per warp during the rank-2 update (red_s), v^H p per warp during the product
+  // (red_k), and w = p - K v is formed on the fly in the update.
+  __shared__ float red_s[32], red_k[32];
+  {
+    float s0 = 0.f;
+    for (int i = threadIdx.x; i < nv - 1; i += blockDim.x) {
+      const float2 x = S[tri(1 + i, 0)];
+      s0 += x.x * x.x + x.y * x.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    if (lane == 0) red_s[warp] = s0;
+  }
+  __syncthreads();
   for (int k = 0; k < nv - 2; ++k) {
     const int m = nv - k - 1;   // length of the column below the diagonal
     float s = 0.f;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      const float2 x = S[tri(k + 1 + i, k)];
-      s += x.x * x.x + x.y * x.y;
-    }
-    s = block_sum_f(s, red);
+    for (int w = 0; w < nwarp; ++w) s += red_s[w];
     // every thread forms the reflector scalars from the same values (no broadcast barrier)
     float bet;
     float2 alpha;
@@ -1102,8 +1117,16 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
       H.e[(size_t)b * n + k] = alpha;
       H.d[(size_t)b * n + k] = S[tri(k, k)].x;
     }
-    if (bet == 0.f) {
+    if (bet == 0.f) {   // (uniform) nothing to reflect; the next column's norm directly
       for (int i = threadIdx.x; i < m; i += blockDim.x) vq[(size_t)k * n + k + 1 + i] = make_float2(0.f, 0.f);
+      __syncthreads();   // every thread has read red_s
+      float s1 = 0.f;
+      for (int i = threadIdx.x; i < m - 1; i += blockDim.x) {
+        const float2 x = S[tri(k + 2 + i, k + 1)];
+        s1 += x.x * x.x + x.y * x.y;
+      }
+      for (int o = 16; o > 0; o >>= 1) s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      if (lane == 0) red_s[warp] = s1;
       __syncthreads();
       continue;
     }
@@ -1114,9 +1137,8 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
       v[i] = x;
       vq[(size_t)k * n + k + 1 + i] = x;
     }
-    __syncthreads();
-    // p = beta A' v   (A' = A[k+1:, k+1:]); 4 threads per row, uniform shuffles; the same pass
-    // accumulates v^H p for K
+    __syncthreads();   // B1: v published (and every thread past its reads of red_s)
+    // p = beta A' v   (A' = A[k+1:, k+1:]); 4 threads per row, uniform shuffles; v^H p per warp
     float kkp = 0.f;
     for (int t0 = 0; t0 < 4 * m; t0 += blockDim.x) {
       const int t = t0 + threadIdx.x;
@@ -1128,6 +1150,16 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
         // j <= i: row r of the packed lower triangle (contiguous)
         const float2* row = S + tri(r, k + 1);
         int j = part;
+        float qr = 0.f, qi = 0.f;   // a second accumulator: two independent chains
+#pragma unroll 4
+        for (; j + 4 <= i; j += 8) {
+          const float2 a0 = row[j], a1 = row[j + 4];
+          const float2 v0 = v[j], v1 = v[j + 4];
+          pr += a0.x * v0.x - a0.y * v0.y;
+          pi += a0.x * v0.y + a0.y * v0.x;
+          qr += a1.x * v1.x - a1.y * v1.y;
+          qi += a1.x * v1.y + a1.y * v1.x;
+        }
         for (; j <= i; j += 4) {
           const float2 aij = row[j];
           const float2 vj = v[j];
@@ -1137,6 +1169,17 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
         // j > i: conj(A[c][r]) with c = k + 1 + j, packed index tri(c, r) advanced incrementally
         int c = k + 1 + j;
         int idx = tri(c, r);
+#pragma unroll 4
+        for (; j + 4 < m; j += 8) {
+          const float2 a0 = S[idx], a1 = S[idx + 4 * c + 10];
+          const float2 v0 = v[j], v1 = v[j + 4];
+          pr += a0.x * v0.x + a0.y * v0.y;
+          pi += a0.x * v0.y - a0.y * v0.x;
+          qr += a1.x * v1.x + a1.y * v1.y;
+          qi += a1.x * v1.y - a1.y * v1.x;
+          idx += 8 * c + 36;   // tri(c + 8, r) - tri(c, r)
+          c += 8;
+        }
         for (; j < m; j += 4) {
           const float2 a = S[idx];
           const float2 vj = v[j];
@@ -1145,6 +1188,8 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
           idx += 4 * c + 10;
           c += 4;
         }
+        pr += qr;
+        pi += qi;
       }
       pr += __shfl_xor_sync(0xffffffffu, pr, 1);
       pi += __shfl_xor_sync(0xffffffffu, pi, 1);
@@ -1156,25 +1201,32 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
         kkp += v[i].x * pv.x + v[i].y * pv.y;
       }
     }
-    // K = (beta / 2) v^H p  (real for Hermitian A'); the reduction's barriers publish p
-    const float kk = 0.5f * bet * block_sum_f(kkp, red);
-    // w = p - K v  (in place in p)
-    for (int i = threadIdx.x; i < m; i += blockDim.x) p[i] = make_float2(p[i].x - kk * v[i].x, p[i].y - kk * v[i].y);
-    __syncthreads();
-    // A' -= v w^H + w v^H on the lower triangle, one warp per row
+    for (int o = 16; o > 0; o >>= 1) kkp += __shfl_xor_sync(0xffffffffu, kkp, o);
+    if (lane == 0) red_k[warp] = kkp;
+    __syncthreads();   // B2: p and the v^H p partials published
+    // K = (beta / 2) v^H p (real for Hermitian A'); A' -= v w^H + w v^H, w = p - K v, on the
+    // lower triangle, one warp per row; lane 0 (column k + 1) sums the next column's norm
+    float kk = 0.f;
+    for (int w = 0; w < nwarp; ++w) kk += red_k[w];
+    kk *= 0.5f * bet;
+    float s1 = 0.f;
     for (int i = warp; i < m; i += nwarp) {
-      const float2 vi = v[i], wi = p[i];
+      const float2 vi = v[i], pi2 = p[i];
+      const float2 wi = make_float2(pi2.x - kk * vi.x, pi2.y - kk * vi.y);
       float2* row = S + tri(k + 1 + i, k + 1);
       for (int j = lane; j <= i; j += 32) {
-        const float2 vj = v[j], wj = p[j];
+        const float2 vj = v[j], pj = p[j];
+        const float2 wj = make_float2(pj.x - kk * vj.x, pj.y - kk * vj.y);
         float2 x = row[j];
         x.x -= (vi.x * wj.x + vi.y * wj.y) + (wi.x * vj.x + wi.y * vj.y);
         x.y -= (vi.y * wj.x - vi.x * wj.y) + (wi.y * vj.x - wi.x * vj.y);
         if (i == j) x.y = 0.f;
         row[j] = x;
+        if (j == 0 && i >= 1) s1 += x.x * x.x + x.y * x.y;
       }
     }
-    __syncthreads();
+    if (lane == 0) red_s[warp] = s1;   // only lane 0 ever sees column k + 1 (j = 0)
+    __syncthreads();   // B3: the trailing matrix and the next norm partials published
   }
   if (threadIdx.x == 0) {
     if (nv >= 2) {
@@ -1279,14 +1331,17 @@ __global__ void __launch_bounds__(32 * TRI_WARPS) k_tri_eig(HhArgs H) {
     b0 = nb;
   }
   const float lamj = 0.5f * (a0 + b0);
-  float* __restrict__ y = H.Y + ((size_t)b * nw + j) * n;
+  // the warp's vector, reciprocal pivots and multipliers in shared memory (the factorisation
+  // and the two solves below are serial recurrences on lane 0)
+  float* __restrict__ y = ee2 + n + (size_t)warp * 3 * n;
+  float* __restrict__ ru = y + n;   // reciprocal pivots
+  float* __restrict__ l = ru + n;   // multipliers
   for (int i = lane; i < nv; i += 32) y[i] = hash_unit(b, j, i, 0);
   if (lane == 0) {
     H.lam[(size_t)b * nw + j] = lamj;
     if (H.lam64) H.lam64[(size_t)b * n + j] = (double)lamj + H.shift[b];
   }
-  float* __restrict__ ru = H.work + ((size_t)b * nw + j) * 2 * n;   // reciprocal pivots
-  float* __restrict__ l = ru + n;                                   // multipliers
+  __syncwarp();
   const float guard = 1e-7f * scale;
   // perturb the shift slightly so equal eigenvalues give different vectors
   const float sh = lamj + (float)(j % 7) * 1e-7f * scale;
@@ -1325,6 +1380,8 @@ __global__ void __launch_bounds__(32 * TRI_WARPS) k_tri_eig(HhArgs H) {
     for (int i = lane; i < nv; i += 32) y[i] *= s;
     __syncwarp();
   }
+  float* yg = H.Y + ((size_t)b * nw + j) * n;
+  for (int i = lane; i < nv; i += 32) yg[i] = y[i];
 }
 
 // Gram-Schmidt inside groups of near-equal eigenvalues (gap < 1e-4 * scale, at most 32), one
@@ -1334,18 +1391,26 @@ __global__ void __launch_bounds__(256) k_tri_gs(HhArgs H) {
   const int n = H.n, nw = H.nw, b = blockIdx.x;
   const int nv = H.nv[b];
   const float* lam = H.lam + (size_t)b * nw;
+  // |e_k| and the unit phases e_k / |e_k| into shared memory by all threads (the chain below and
+  // the spectrum scale then read no global memory serially)
+  extern __shared__ float tgs[];   // [n] |e| then [2n] unit phases
+  float* ae_s = tgs;
+  float2* u_s = reinterpret_cast<float2*>(tgs + ((n + 1) & ~1));
+  for (int i = threadIdx.x; i < nv - 1; i += blockDim.x) {
+    const float2 ek = H.e[(size_t)b * n + i];
+    const float ae = sqrtf(ek.x * ek.x + ek.y * ek.y);
+    ae_s[i] = ae;
+    u_s[i] = ae > 0.f ? make_float2(ek.x / ae, ek.y / ae) : make_float2(1.f, 0.f);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     float2 ph = make_float2(1.f, 0.f);
     float2* out = H.ph + (size_t)b * n;
     for (int i = 0; i < nv; ++i) {
       out[i] = ph;
       if (i < nv - 1) {
-        const float2 ek = H.e[(size_t)b * n + i];
-        const float ae = sqrtf(ek.x * ek.x + ek.y * ek.y);
-        if (ae > 0.f) {
-          const float2 u = make_float2(ek.x / ae, ek.y / ae);
-          ph = make_float2(ph.x * u.x - ph.y * u.y, ph.x * u.y + ph.y * u.x);
-        }
+        const float2 u = u_s[i];
+        ph = make_float2(ph.x * u.x - ph.y * u.y, ph.x * u.y + ph.y * u.x);
       }
     }
   }
@@ -1353,10 +1418,7 @@ __global__ void __launch_bounds__(256) k_tri_gs(HhArgs H) {
   float scale = 0.f;
   const int nvw = nv < nw ? nv : nw;
   for (int i = 0; i < nvw; ++i) scale = fmaxf(scale, fabsf(lam[i]));
-  for (int i = 0; i < nv - 1; ++i) {
-    const float2 ek = H.e[(size_t)b * n + i];
-    scale = fmaxf(scale, sqrtf(ek.x * ek.x + ek.y * ek.y));
-  }
+  for (int i = 0; i < nv - 1; ++i) scale = fmaxf(scale, ae_s[i]);
   scale = fmaxf(scale, 1e-6f);
   for (int j = threadIdx.x; j < nvw; j += blockDim.x) {
     if (j > 0 && lam[j] - lam[j - 1] < 1e-4f * scale) continue;   // not a group start
@@ -1537,8 +1599,9 @@ cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, in
     k_hh_tridiag<<<nprob, HH_THREADS, hh_smem(n), st>>>(H);
   }
   if (!(stage & 2)) return cudaGetLastError();
-  k_tri_eig<<<dim3((nw + TRI_WARPS - 1) / TRI_WARPS, nprob), 32 * TRI_WARPS, 3 * n * sizeof(float), st>>>(H);
-  k_tri_gs<<<nprob, 256, 0, st>>>(H);
+  k_tri_eig<<<dim3((nw + TRI_WARPS - 1) / TRI_WARPS, nprob), 32 * TRI_WARPS, (3 + 3 * TRI_WARPS) * n * sizeof(float),
+              st>>>(H);
+  k_tri_gs<<<nprob, 256, (size_t)(((n + 1) & ~1) + 2 * n) * sizeof(float), st>>>(H);
   k_hh_back<<<dim3((nw + 7) / 8, nprob), 256, (size_t)HB_RC * n * sizeof(float2), st>>>(H);
   return cudaGetLastError();
 }
@@ -1715,12 +1778,16 @@ __global__ void k_first_order(const double2* Sp, int nw, const int* grp, double2
   const double2* s = Sp + (size_t)b * nw * nw;
   double2* f = F + (size_t)b * nw * nw;
   const int* g = grp + (size_t)b * nw;
-  extern __shared__ int gid[];
+  extern __shared__ int gid[];   // [nw] the group flags, then in place the group starts
+  for (int j = threadIdx.x; j < nw; j += blockDim.x) gid[j] = g[j];
+  __syncthreads();
   if (threadIdx.x == 0) {
-    int cur = 0;
+    int cur = 0, prev = 0;
     for (int j = 0; j < nw; ++j) {
-      if (j > 0 && !g[j - 1]) cur = j;
+      const int flag = gid[j];
+      if (j > 0 && !prev) cur = j;
       gid[j] = cur;
+      prev = flag;
     }
   }
   __syncthreads();
@@ -1739,7 +1806,7 @@ __global__ void k_first_order(const double2* Sp, int nw, const int* grp, double2
 }
 
 cudaError_t launch_first_order(cudaStream_t st, const double2* Sp, int nw, int nprob, const int* grp, double2* F) {
-  k_first_order<<<nprob, 128, nw * sizeof(int), st>>>(Sp, nw, grp, F);
+  k_first_order<<<nprob, 512, nw * sizeof(int), st>>>(Sp, nw, grp, F);
   return cudaGetLastError();
 }
 
