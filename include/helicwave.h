@@ -344,10 +344,16 @@ hw_status hw_gram(hw_ctx* ctx, int m, int n, int K, int nprob, const double* A, 
  * integer digits; the digit products are summed by tcgen05 MMAs in TMEM.  cls 0 (FP64 class):
  * 8 digits of 7 bits, exact group sums added into a 64-bit fixed point, error below
  * 2^-46 max|op(A)_i,:| max|B_:,j| per reduction element (tighter than an FP64 GEMM's bound for
- * vectors without a wide dynamic range); cls 1 (FP32 class): 3 digits of 8 bits, FP32 sums,
- * about 2^-24 of the same scale.  Deterministic (fixed-order split reduction).  The library
- * grows a workspace for the digit planes (up to 1 GiB; larger batches run in chunks).
- * Asynchronous on the context's stream.  HW_EINVAL on bad sizes (n <= 4096, m, k <= 2^20). */
+ * vectors without a wide dynamic range); cls 1 (FP32 class): every operand as a TF32 pair
+ * hi + lo, the products hi hi' + hi lo' + lo hi' summed in FP32 by tcgen05 kind::tf32 MMAs,
+ * about 2^-22 of the same scale.  Deterministic (fixed-order split reduction).  The library
+ * grows a workspace for the planes (up to 1 GiB; larger batches run in chunks).
+ * cls 2 and 3: the small-product kernel instead (every extent below 1024, no workspace): SIMT
+ * on the FP32 pipe, one CTA per 8 x 8 output tile with a four-way split of each reduction
+ * added in a fixed order; cls 2 rounds the FP64 operands to double-float pairs (~48-bit
+ * significands, error ~2^-44 of sum |op(A)||B|), cls 3 to FP32.
+ * Asynchronous on the context's stream.  HW_EINVAL on bad sizes (n <= 4096, m, k <= 2^20;
+ * below 1024 for cls 2, 3). */
 hw_status hw_block_product(hw_ctx* ctx, int transA, int m, int n, int k, double alpha, const double* A,
                            int64_t lda, int64_t sA, const double* B, int64_t ldb, int64_t sB, double beta,
                            double* C, int64_t ldc, int64_t sC, int batch, int cls);
@@ -431,10 +437,20 @@ typedef enum {
                                the forward kernel of launches with nu != 0 stays on the FP32 SIMT
                                kernel); 0 the FP32 SIMT kernels.  FP64 H X always uses the FP64
                                SIMT kernels. */
-  HW_OPT_FP64_HX = 14       /* the FP64 H X of a HW_MIXED solve (its hand-over to FP64 products
+  HW_OPT_FP64_HX = 14,      /* the FP64 H X of a HW_MIXED solve (its hand-over to FP64 products
                                and the FP64 check of every convergence claim): 1 (default) the
                                angular transforms in double-float arithmetic (as hw_apply_H with
                                HW_FP64_DF), 0 in FP64.  HW_FP64 solves always use FP64. */
+  HW_OPT_SMALL_GEMM = 15    /* the eigensolver's small products (every extent below 1024: the
+                               Rayleigh-Ritz refinement, the Newton-Schulz steps): 1 (default)
+                               the library's SIMT kernel for the FP32 class (FP64 operands
+                               rounded to FP32, as hw_block_product class 3) and, inside
+                               HW_MIXED solves, for the FP64 class in double-float (class 2: its
+                               ~1e-14 errors, divided by eigenvalue gaps in the first-order
+                               refinement, leave the refined Ritz vectors orthonormal to ~1e-11,
+                               within the solver's 1e-9 check); HW_FP64 solves and hw_heev take
+                               cuBLAS ZGEMM for the FP64 class; 2 the SIMT kernel for both classes
+                               everywhere; 0 cuBLAS for both. */
 } hw_option;
 /* Set an option (HW_EINVAL for an unknown option, a read-only one or a bad value). */
 hw_status hw_set_option(hw_ctx* ctx, int option, int value);

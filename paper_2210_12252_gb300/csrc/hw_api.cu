@@ -614,6 +614,12 @@ hw_status hw_set_option(hw_ctx* ctx, int option, int value) {
     ctx->fp64_hx_ff = value;
     return HW_OK;
   }
+  if (option == HW_OPT_SMALL_GEMM) {
+    if (value < 0 || value > 2)
+      return hw_fail(ctx, HW_EINVAL, "small-product option 0 (cuBLAS), 1 (SIMT kernel, FP32 class) or 2 (both classes)");
+    ctx->small_gemm = value;
+    return HW_OK;
+  }
   return hw_fail(ctx, HW_EINVAL, "unknown or read-only option");
 }
 
@@ -634,6 +640,7 @@ hw_status hw_get_option(hw_ctx* ctx, int option, long long* value) {
   if (option == HW_OPT_TC_GEMM) { *value = ctx->tc_gemm; return HW_OK; }
   if (option == HW_OPT_RADIAL_KERNEL) { *value = ctx->radial_tc; return HW_OK; }
   if (option == HW_OPT_FP64_HX) { *value = ctx->fp64_hx_ff; return HW_OK; }
+  if (option == HW_OPT_SMALL_GEMM) { *value = ctx->small_gemm; return HW_OK; }
   return hw_fail(ctx, HW_EINVAL, "unknown option");
 }
 

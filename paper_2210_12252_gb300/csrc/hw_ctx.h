@@ -126,7 +126,9 @@ struct hw_ctx {
   int window = 0;              // HW_OPT_WINDOW (0: 100)
   int slab_r16 = 2;            // HW_OPT_SLAB_KERNEL
   int fp64_hx_ff = 1;          // HW_OPT_FP64_HX: the mixed solver's FP64 H X with double-float angular transforms
+  int small_gemm = 1;          // HW_OPT_SMALL_GEMM: the solver's small products on the library's SIMT kernel
   bool ff_solve = false;       // a mixed-precision solve with fp64_hx_ff is running
+  bool mixed_solve = false;    // a mixed-precision solve is running
   bool ff_now = false;         // the FP64 H X being launched uses the double-float angular kernel
   int radial_tc = 1;           // HW_OPT_RADIAL_KERNEL
   int64_t rr_fallbacks = 0;    // Householder results rejected by the check (Jacobi used)
@@ -175,6 +177,11 @@ cudaError_t launch_tpa(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld);
 // entry point is missing or the shape is rejected
 bool make_plane_map(CUtensorMap* m, const void* base, bool fp32, int64_t Kp, int rows, int planes, int box_rows,
                     int box_planes, int swz);
+// C_b = alpha op(A_b) B_b + beta C_b for small products (every extent below 1024) on the FP32
+// pipe: cls 0 double-float (FP64 class), 1 FP32
+cudaError_t zgemm_small(cudaStream_t st, int cls, bool transA, int m, int n, int k, double alpha, const double2* A,
+                        int64_t lda, int64_t sA, const double2* B, int64_t ldb, int64_t sB, double beta, double2* C,
+                        int64_t ldc, int64_t sC, int batch);
 cudaError_t radial_tc_setup(hw_ctx* ctx, const HostBasis& hb, const std::vector<double>& rinv,
                             const std::vector<double>& rfwd);
 cudaError_t launch_rinv_tc(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, int nc, int c0, void* gbuf,

@@ -434,6 +434,19 @@ struct Gemm {
       if (e != cudaSuccess && ce == cudaSuccess) ce = e;
       return;
     }
+    // the small products (every extent below 1024: the Rayleigh-Ritz step) on the FP32 pipe
+    // (HW_OPT_SMALL_GEMM): the FP32 class always; the FP64 class in double-float inside
+    // mixed-precision solves (the FP64 refinement divides its products' errors by eigenvalue
+    // gaps: double-float's ~1e-14 leaves the refined vectors orthonormal to ~1e-11, within the
+    // mixed solver's 1e-9 check; FP64 solves and hw_heev keep FP64 products)
+    if (ctx->small_gemm && (lowp || ctx->mixed_solve || ctx->small_gemm == 2) && k >= 1 && tb == CUBLAS_OP_N &&
+        (ta == CUBLAS_OP_C || ta == CUBLAS_OP_N) && m < 1024 && n < 1024 && k < 1024 && batch <= 65535) {
+      const cudaError_t e = zgemm_small(ctx->stream, lowp ? 1 : 0, ta == CUBLAS_OP_C, m, n, k, alpha, A, lda, sA, B,
+                                        ldb, sB, beta, C, ldc, sC, batch);
+      ctx->launches++;
+      if (e != cudaSuccess && ce == cudaSuccess) ce = e;
+      return;
+    }
     if (gram && lowp && ta == CUBLAS_OP_C && tb == CUBLAS_OP_N && k >= 256 &&
         gram_work_bytes(m, n, k, batch) <= gbytes) {
       int nl = 0;
@@ -1992,11 +2005,15 @@ extern "C" hw_status hw_get_residual_history(hw_ctx* ctx, int k, int* phase, dou
   return HW_OK;
 }
 
-// marks a mixed-precision solve whose FP64 H X takes the double-float angular kernel
+// marks a mixed-precision solve: its FP64 H X takes the double-float angular kernel
+// (HW_OPT_FP64_HX) and its small FP64-class products the double-float kernel (HW_OPT_SMALL_GEMM)
 struct FfSolveScope {
   hw_ctx* c;
-  FfSolveScope(hw_ctx* ctx, hw_prec prec) : c(ctx) { c->ff_solve = prec == HW_MIXED && c->fp64_hx_ff; }
-  ~FfSolveScope() { c->ff_solve = false; }
+  FfSolveScope(hw_ctx* ctx, hw_prec prec) : c(ctx) {
+    c->ff_solve = prec == HW_MIXED && c->fp64_hx_ff;
+    c->mixed_solve = prec == HW_MIXED;
+  }
+  ~FfSolveScope() { c->ff_solve = c->mixed_solve = false; }
 };
 
 static hw_status solve_window(hw_ctx* ctx, int nk, const int* kidx, int n_eig, int block, double tol, int maxit,

@@ -51,6 +51,7 @@
 #include "hw_common.cuh"
 #include "hw_ctx.h"
 #include "hw_tc.cuh"
+#include "hw_ff.cuh"
 
 namespace hw {
 
@@ -961,6 +962,98 @@ cudaError_t zgemm_tc(ZgemmWork*& w, cudaStream_t st, int cls, bool transA, int m
   return zgemm_run(w, st, cls, transA, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, launches);
 }
 
+// ----------------------------------------------------------------------------- small products
+// C_b = alpha op(A_b) B_b + beta C_b for the Rayleigh-Ritz step's small products (every extent
+// below ZS_MAX), on the FP32 pipe: R = float for the FP32 class, double-float `ff` (~48-bit
+// significands) for the FP64 class.  Operands are read in FP64 and rounded to R while they are
+// staged; one CTA of 256 threads per 8 x 8 output tile, each output's reduction split four ways
+// (k = part mod 4 within each 32-deep chunk) and the four partial sums added in a fixed order.
+constexpr int ZS_T = 8, ZS_KC = 32, ZS_MAX = 1024;
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_zgemm_small(int transA, int m, int n, int k, double alpha, const double2* A,
+                                                      int64_t lda, int64_t sA, const double2* B, int64_t ldb,
+                                                      int64_t sB, double beta, double2* C, int64_t ldc, int64_t sC) {
+  using Cr = rc_t<R>;
+  __shared__ Cr As[ZS_T][ZS_KC + 1];   // op(A) rows of the tile, a chunk of the reduction
+  __shared__ Cr Bs[ZS_KC][ZS_T];       // B rows (reduction index) x the tile's columns
+  __shared__ Cr part_s[3][ZS_T * ZS_T];
+  const int b = blockIdx.z;
+  const int i0 = blockIdx.x * ZS_T, j0 = blockIdx.y * ZS_T;
+  const int t = threadIdx.x, o = t & 63, p = t >> 6;   // output (tx, ty) = (o % 8, o / 8), reduction part p
+  const int tx = o & 7, ty = o >> 3;
+  const double2* a = A + (size_t)b * sA;
+  const double2* bb = B + (size_t)b * sB;
+  const R zr = R(0);
+  R accr = zr, acci = zr;
+  for (int k0 = 0; k0 < k; k0 += ZS_KC) {
+    {   // one op(A) and one B element per thread, rounded to R
+      // A tile: row r (0..7), reduction kk (0..31); consecutive threads along the operand's
+      // contiguous index (the reduction for op = ^H, the rows otherwise)
+      const int r = transA ? t >> 5 : t & 7, kk = transA ? t & 31 : t >> 3;
+      const int gi = i0 + r, gk = k0 + kk;
+      double2 x = make_double2(0.0, 0.0);
+      if (gi < m && gk < k) {
+        if (transA) {   // op(A)[i][k] = conj(A[k + i lda])
+          x = a[gk + (size_t)gi * lda];
+          x.y = -x.y;
+        } else {
+          x = a[gi + (size_t)gk * lda];
+        }
+      }
+      As[r][kk] = mkr<R>(to_r<R>(x.x), to_r<R>(x.y));
+      const int kb = t & 31, c = t >> 5;   // B tile: reduction kb, column c
+      const int gkb = k0 + kb, gj = j0 + c;
+      double2 y = make_double2(0.0, 0.0);
+      if (gkb < k && gj < n) y = bb[gkb + (size_t)gj * ldb];
+      Bs[kb][c] = mkr<R>(to_r<R>(y.x), to_r<R>(y.y));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = p; kk < ZS_KC; kk += 4) {
+      const Cr x = As[tx][kk], y = Bs[kk][ty];
+      accr += x.x * y.x - x.y * y.y;
+      acci += x.x * y.y + x.y * y.x;
+    }
+    __syncthreads();
+  }
+  if (p > 0) part_s[p - 1][o] = mkr<R>(accr, acci);
+  __syncthreads();
+  if (p == 0) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {   // fixed order: part 0 + 1 + 2 + 3
+      accr += part_s[q][o].x;
+      acci += part_s[q][o].y;
+    }
+    const int gi = i0 + tx, gj = j0 + ty;
+    if (gi < m && gj < n) {
+      double2* c = C + (size_t)b * sC + gi + (size_t)gj * ldc;
+      double2 v = make_double2(alpha * from_r<double>(accr), alpha * from_r<double>(acci));
+      if (beta != 0.0) {   // C is not read when beta = 0
+        const double2 c0 = *c;
+        v.x += beta * c0.x;
+        v.y += beta * c0.y;
+      }
+      *c = v;
+    }
+  }
+}
+
+// cls 0: FP64 class (double-float), 1: FP32 class
+cudaError_t zgemm_small(cudaStream_t st, int cls, bool transA, int m, int n, int k, double alpha, const double2* A,
+                        int64_t lda, int64_t sA, const double2* B, int64_t ldb, int64_t sB, double beta, double2* C,
+                        int64_t ldc, int64_t sC, int batch) {
+  if (m <= 0 || n <= 0 || batch <= 0) return cudaSuccess;
+  if (k <= 0 || m >= ZS_MAX || n >= ZS_MAX || k >= ZS_MAX || batch > 65535 || (cls != 0 && cls != 1))
+    return cudaErrorInvalidValue;
+  const dim3 grid((m + ZS_T - 1) / ZS_T, (n + ZS_T - 1) / ZS_T, batch);
+  if (cls == 0)
+    k_zgemm_small<ff><<<grid, 256, 0, st>>>(transA, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+  else
+    k_zgemm_small<float><<<grid, 256, 0, st>>>(transA, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+  return cudaGetLastError();
+}
+
 int* zgemm_status_ptr(ZgemmWork* w) { return w ? w->status : nullptr; }
 
 // status word of the tensor-core kernels (HW_OK, or HW_ETIMEOUT after a wait ran out); reset
@@ -982,14 +1075,23 @@ extern "C" hw_status hw_block_product(hw_ctx* ctx, int transA, int m, int n, int
                                       double* C, int64_t ldc, int64_t sC, int batch, int cls) {
   if (!ctx) return HW_EINVAL;
   if (ctx->device < 0) return hw_fail(ctx, HW_ESTATE, "host-only context has no device");
-  if ((transA != 0 && transA != 1) || (cls != 0 && cls != 1) || m < 1 || n < 1 || k < 1 || batch < 1 || !A ||
-      !B || !C)
+  if ((transA != 0 && transA != 1) || cls < 0 || cls > 3 || m < 1 || n < 1 || k < 1 || batch < 1 || !A || !B || !C)
     return hw_fail(ctx, HW_EINVAL, "hw_block_product: bad arguments");
+  if (cls >= 2 && (m >= 1024 || n >= 1024 || k >= 1024))
+    return hw_fail(ctx, HW_EINVAL, "hw_block_product: the small-product classes take extents below 1024");
   if (lda < (transA ? k : m) || ldb < k || ldc < m || (batch > 1 && (sA < 0 || sB < 0 || sC < 0)))
     return hw_fail(ctx, HW_EINVAL, "hw_block_product: bad leading dimensions or strides");
   if ((int64_t)m > (1 << 20) || (int64_t)n > 4096 || (int64_t)k > (1 << 20))
     return hw_fail(ctx, HW_EINVAL, "hw_block_product: sizes out of range");
   cudaSetDevice(ctx->device);
+  if (cls >= 2) {
+    const cudaError_t e = zgemm_small(ctx->stream, cls - 2, transA != 0, m, n, k, alpha,
+                                      reinterpret_cast<const double2*>(A), lda, sA, reinterpret_cast<const double2*>(B),
+                                      ldb, sB, beta, reinterpret_cast<double2*>(C), ldc, sC, batch);
+    ctx->launches++;
+    if (e != cudaSuccess) return hw_fail(ctx, HW_ECUDA, std::string("hw_block_product: ") + cudaGetErrorString(e));
+    return HW_OK;
+  }
   int nl = 0;
   cudaError_t e = zgemm_tc(ctx->zg, ctx->stream, cls, transA != 0, m, n, k, alpha,
                            reinterpret_cast<const double2*>(A), lda, sA, reinterpret_cast<const double2*>(B), ldb,

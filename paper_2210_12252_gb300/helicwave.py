@@ -278,6 +278,7 @@ HW_OPT_WINDOW = 11
 HW_OPT_TC_GEMM = 12
 HW_OPT_RADIAL_KERNEL = 13
 HW_OPT_FP64_HX = 14
+HW_OPT_SMALL_GEMM = 15
 
 
 def hw_set_option(h, option, value):
@@ -380,7 +381,8 @@ def hw_block_product(h, trans_a, m, n, k, A, B, C, alpha=1.0, beta=0.0, cls=0):
     """C_b = alpha op(A_b) B_b + beta C_b on the tensor cores.  A, B, C: contiguous CUDA complex128
     tensors of shape (batch, columns, ld): block b's column c is A[b, c, :ld] (column-major
     blocks, leading dimension = the last extent).  op = conjugate transpose when trans_a
-    (A_b: k x m), else none (A_b: m x k).  cls 0: FP64 class, 1: FP32 class."""
+    (A_b: k x m), else none (A_b: m x k).  cls 0: FP64 class, 1: FP32 class (tensor cores);
+    2, 3: the small-product kernel (every extent below 1024) in double-float and FP32."""
     for T in (A, B, C):
         assert T.is_contiguous() and T.dim() == 3
     batch = C.shape[0]

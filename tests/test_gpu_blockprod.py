@@ -115,5 +115,47 @@ def test_block_product_rejects_bad_arguments(hwmod, ctx):
             hwmod.hw_block_product(ctx.h, args[0], args[1], args[2], args[3], A, A, A)
         assert e.value.status == hwmod.HW_EINVAL
     with pytest.raises(hwmod.HwError) as e:
-        hwmod.hw_block_product(ctx.h, 1, 4, 4, 8, A, A, A, cls=2)
+        hwmod.hw_block_product(ctx.h, 1, 4, 4, 8, A, A, A, cls=4)
+    assert e.value.status == hwmod.HW_EINVAL
+
+
+SMALL_TOL = {2: 1e-12, 3: 2e-6}
+
+
+@pytest.mark.parametrize("cls", [2, 3])
+def test_small_products_refinement_shapes(hwmod, ctx, cls):
+    """The small-product classes (the Rayleigh-Ritz refinement's shapes: n x nb x n with
+    n = 228, nb = 76; the Newton-Schulz nb x nb x n), both ops, alpha/beta, a batch of 2,
+    ragged tiles (n not a multiple of 8), padded leading dimensions; entry-wise against FP64
+    relative to (|op(A)||B|)_ij."""
+    worst = 0.0
+    for (trans, m, n, k, pad, alpha, beta, seed) in ((0, 228, 76, 228, (0, 0, 0), 1.0, 0.0, 11),
+                                                    (1, 228, 76, 228, (3, 0, 5), 1.0, 0.0, 12),
+                                                    (1, 76, 76, 228, (0, 2, 0), 0.5, -1.0, 13),
+                                                    (0, 228, 76, 76, (5, 0, 1), -1.0, 1.0, 14),
+                                                    (1, 5, 3, 1, (0, 0, 0), 1.0, 0.0, 15)):
+        rng = np.random.default_rng(seed)
+        ra, ca = (k, m) if trans else (m, k)
+        A = blocks(rng, 2, ca, ra, ra + pad[0])
+        B = blocks(rng, 2, n, k, k + pad[1])
+        C0 = blocks(rng, 2, n, m, m + pad[2])
+        Ad, Bd, Cd = (torch.from_numpy(x.copy()).cuda() for x in (A, B, C0))
+        hwmod.hw_block_product(ctx.h, trans, m, n, k, Ad, Bd, Cd, alpha, beta, cls)
+        C = Cd.cpu().numpy()
+        for b in range(2):
+            a = A[b, :, :ra].T
+            opA = a.conj().T if trans else a
+            ref = alpha * (opA @ B[b, :, :k].T) + beta * C0[b, :, :m].T
+            scale = abs(alpha) * (np.abs(opA) @ np.abs(B[b, :, :k].T)) + abs(beta) * np.abs(C0[b, :, :m].T)
+            r = float((np.abs(C[b, :, :m].T - ref) / scale).max())
+            worst = max(worst, r)
+            assert r <= SMALL_TOL[cls], (trans, m, n, k, b, r)
+            assert np.all(C[b, :, m:] == 7.0 - 3.0j)
+    print(f"small products, class {cls}: max |dC|/(|op(A)||B|) = {worst:.3e}")
+
+
+def test_small_products_reject_large_extents(hwmod, ctx):
+    A = torch.zeros((1, 1024, 1024), dtype=torch.complex128, device="cuda")
+    with pytest.raises(hwmod.HwError) as e:
+        hwmod.hw_block_product(ctx.h, 0, 1024, 8, 8, A, A, A, cls=2)
     assert e.value.status == hwmod.HW_EINVAL
