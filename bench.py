@@ -382,6 +382,10 @@ def ours_main(args):
             i[0] += 1
             return out
 
+        # one untimed solve first: the FP64 method is the first user of cuBLAS ZGEMM in this
+        # process (the chosen form's products are the library's own kernels), and the first
+        # ZGEMM calls load their kernels (measured: 6.6 s for the first solve, then 0.35-0.38 s)
+        solve("fp64", "tpa", X=X0s[NSTART - 1], solver="lobpcg")
         ms64, r64 = timed_steps(plain_step, NSTART, record=(it64, err64, ref))
         v64 = n_eig * len(ms64) / (sum(ms64) / 1e3)
         result["plain_fp64"] = {"value": round(v64, 3), "unit": UNIT, "iters_per_step": it64,
@@ -577,6 +581,7 @@ def batched_kpoints(hw, inputs, local, stream, flush, precond, solver="chfsi"):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3, r
 
+    run64(list(range(nk)))                    # warm-up (the FP64 batch's first products)
     t64, r64 = run64(list(range(nk)))
     # eigenvalue error against the oracle's dense eigenvalues of every point (tests/golden)
     errs = {}
