@@ -52,12 +52,12 @@ typedef enum {
   HW_FP64 = 0,       /* every step in FP64                                                 */
   HW_MIXED = 1,      /* transforms in FP32 (FP32 accumulate); diagonal terms, Gram,
                         Cholesky, Rayleigh-Ritz and the final residual check in FP64      */
-  HW_FP64_DF = 2     /* hw_apply_H only: FP64 storage, radial transforms and diagonal in
-                        FP64, the angular transforms (Algorithms 2, 4 and the potential
-                        multiply) in double-float arithmetic -- pairs of FP32 numbers, about
-                        48 significant bits, on the FP32 pipe -- on the 64 x 48 grid with at
-                        most 16 consecutive kept m rows (other bases: as HW_FP64).  What the
-                        mixed-precision solver uses for its FP64 H X (HW_OPT_FP64_HX).      */
+  HW_FP64_DF = 2     /* hw_apply_H only: FP64 blocks and diagonal term; the radial and
+                        angular transforms (Algorithms 1-4 with the potential multiply) in
+                        double-float arithmetic -- pairs of FP32 numbers, about 48
+                        significant bits, on the FP32 pipe -- on the 64 x 48 grid with at most
+                        16 consecutive kept m rows and nu = 0 (other cases: as HW_FP64).  What
+                        the mixed-precision solver uses for its FP64 H X (HW_OPT_FP64_HX).  */
 } hw_prec;
 
 typedef enum {

@@ -101,6 +101,8 @@ void free_basis(hw_ctx* ctx) {
   dfree(db.ke);
   dfree(db.vscratch);
   dfree(db.vff);
+  dfree(db.ff_rinv);
+  dfree(db.ff_rfwd);
   db.ke_off.clear();
   for (auto* t : {&db.t64.rinv, &db.t64.rfwd, &db.t64.qtab, &db.t64.rder, &db.t64.V, &db.t64.tw1, &db.t64.tw2})
     dfree(*t);
@@ -210,6 +212,16 @@ hw_status hw_setup_basis(hw_ctx* ctx, const hw_basis_params* params, int nk, con
           rfwd[((size_t)n * K + k) * Nr + p] = scale * hb.wr[p] * x;
         }
     std::vector<float> rinv32(rinv.begin(), rinv.end()), rfwd32(rfwd.begin(), rfwd.end());
+    // the radial tables as double-float pairs (hi = FP32 rounding, lo = FP32 rounding of the rest)
+    auto pairs = [](const std::vector<double>& v) {
+      std::vector<float2> o(v.size());
+      for (size_t i = 0; i < v.size(); ++i) {
+        const float h = (float)v[i];
+        o[i] = make_float2(h, (float)(v[i] - (double)h));
+      }
+      return o;
+    };
+    const std::vector<float2> rinvff = pairs(rinv), rfwdff = pairs(rfwd);
     std::vector<float> qtab32(hb.qtab.begin(), hb.qtab.end());
     std::vector<float> rder32(hb.xid.begin(), hb.xid.end());
     std::vector<double> tw1 = twiddles(params->Nth1), tw2 = twiddles(params->Nth2);
@@ -241,6 +253,8 @@ hw_status hw_setup_basis(hw_ctx* ctx, const hw_basis_params* params, int nk, con
     UP(db.rnodes, hb.r);
     UP(db.t64.tw1, tw1);
     UP(db.t64.tw2, tw2);
+    UP(db.ff_rinv, rinvff);
+    UP(db.ff_rfwd, rfwdff);
     UP(db.t32.rinv, rinv32);
     UP(db.t32.rfwd, rfwd32);
     UP(db.t32.tw1, tw1f);

@@ -39,6 +39,8 @@ struct DevBasis {
   std::vector<int64_t> ke_off; // host: start of k-point b in ke
   double* vscratch = nullptr;  // [grid] staging for set_potential
   float2* vff = nullptr;       // [Nr][Nth2][Nth1] the potential as FP32 pairs (hi, lo), slab layout
+  float2* ff_rinv = nullptr;   // the radial tables of DevTables as FP32 pairs (hi, lo)
+  float2* ff_rfwd = nullptr;
   DevTables<double> t64;
   DevTables<float> t32;
   // tensor-core radial transforms of the FP32 H X: BF16 three-part tables per |n| group

@@ -584,6 +584,201 @@ __global__ void __launch_bounds__(RAD_THREADS, sizeof(T) == 4 ? 2 : 1) k_radial_
   }
 }
 
+// ------------------------------------------------------------ radial transforms, double-float
+// The FP64 H X of a mixed-precision solve in double-float arithmetic (the angular kernel's
+// `ff`), nu = 0: the tables as FP32 pairs, the G / H intermediates stored as pairs (the same 16
+// bytes per complex value as complex128), X read and Y written in FP64 with the diagonal term
+// in FP64.  Item and table layout as k_radial_inv / k_radial_fwd; one node per thread at a time.
+__global__ void __launch_bounds__(RAD_THREADS, 2) k_radial_inv_ff(RadArgs<double> A, const ff* __restrict__ tabff) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int g = blockIdx.y;
+  const int gs = A.group_start[g], na = A.group_start[g + 1] - gs;
+  const long nitems = (long)na * A.ncols;
+  const long q0 = (long)blockIdx.x * RAD_Q;
+  if (na == 0 || q0 >= nitems) return;
+  const int K = A.K, Nr = A.Nr, Kp = pad4(K);
+  ff* Rs = reinterpret_cast<ff*>(smem_raw);   // [Nr][Kp]
+  ffc* Xs = reinterpret_cast<ffc*>(smem_raw + (((size_t)Nr * Kp * sizeof(ff) + 15) & ~size_t(15)));   // [Kp][RAD_Q]
+  const ff* tab = tabff + (size_t)g * Nr * K;
+  for (int i = threadIdx.x; i < Nr * Kp; i += blockDim.x) {
+    const int p = i / Kp, k = i - p * Kp;
+    Rs[i] = k < K ? tab[(size_t)p * K + k] : ff(0);
+  }
+  __shared__ const double* s_x[RAD_Q];
+  __shared__ int s_ka[RAD_Q];
+  if (threadIdx.x < RAD_Q) {
+    const int q = threadIdx.x;
+    const long item = q0 + q;
+    const double* xp = nullptr;
+    int ka = 0;
+    if (item < nitems) {
+      const int c = (int)(item / na), a = gs + (int)(item - (long)c * na);
+      const int cg = A.c0 + c;
+      const int slot = cg / A.ns, sl = cg - slot * A.ns;
+      const int kb = A.blk.kb[slot];
+      ka = A.Ka[(size_t)kb * A.nA + a];
+      xp = A.blk.x[slot] + 2 * ((size_t)A.off[(size_t)kb * A.nA + a] + (size_t)sl * A.ld);
+    }
+    s_x[q] = xp;
+    s_ka[q] = ka;
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int i = threadIdx.x; i < RAD_Q * Kp; i += blockDim.x) {
+    const int q = i / Kp, k = i - q * Kp;
+    ffc v;
+    v.x = ff(0);
+    v.y = ff(0);
+    if (k < s_ka[q]) {
+      const double* x = s_x[q] + 2 * k;
+      v.x = ff_from(x[0]);
+      v.y = ff_from(x[1]);
+    }
+    Xs[k * RAD_Q + q] = v;
+  }
+  __syncthreads();
+  const int q = threadIdx.x % RAD_Q;
+  const long item = q0 + q;
+  if (item >= nitems) return;
+  const int c = (int)(item / na), a = gs + (int)(item - (long)c * na);
+  ffc* out = reinterpret_cast<ffc*>(A.gh) + ((size_t)c * Nr) * A.nA + a;
+  constexpr int PG = RAD_THREADS / RAD_Q;
+  for (int p = threadIdx.x / RAD_Q; p < Nr; p += PG) {
+    ff ax = ff(0), ay = ff(0);
+    const ff* rr = Rs + (size_t)p * Kp;
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+      const ffc xv = Xs[k * RAD_Q + q];
+      ax += rr[k] * xv.x;
+      ay += rr[k] * xv.y;
+    }
+    ffc o;
+    o.x = ax;
+    o.y = ay;
+    out[(size_t)p * A.nA] = o;
+  }
+}
+
+__global__ void __launch_bounds__(RAD_THREADS, 2) k_radial_fwd_ff(RadArgs<double> A, const ff* __restrict__ tabff) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int g = blockIdx.y;
+  const int gs = A.group_start[g], na = A.group_start[g + 1] - gs;
+  const long nitems = (long)na * A.ncols;
+  const long q0 = (long)blockIdx.x * RAD_Q;
+  if (na == 0 || q0 >= nitems) return;
+  const int K = A.K, Nr = A.Nr, Nrp = pad4(Nr);
+  constexpr int PC = 32;
+  ff* Rs = reinterpret_cast<ff*>(smem_raw);                // [K][Nrp]
+  size_t o = (((size_t)K * Nrp * sizeof(ff)) + 15) & ~size_t(15);
+  ffc* Hs = reinterpret_cast<ffc*>(smem_raw + o);          // [PC][RAD_Q]
+  o += (size_t)PC * RAD_Q * sizeof(ffc);
+  ffc* Ys = reinterpret_cast<ffc*>(smem_raw + o);          // [RAD_Q][K+1]
+  const ff* tab = tabff + (size_t)g * K * Nr;
+  for (int i = threadIdx.x; i < K * Nrp; i += blockDim.x) {
+    const int k = i / Nrp, pp = i - k * Nrp;
+    Rs[i] = pp < Nr ? tab[(size_t)k * Nr + pp] : ff(0);
+  }
+  __shared__ const ffc* s_h[RAD_Q];
+  __shared__ int64_t s_o[RAD_Q], s_cs[RAD_Q];
+  __shared__ int s_ka[RAD_Q], s_slot[RAD_Q];
+  if (threadIdx.x < RAD_Q) {
+    const int qq = threadIdx.x;
+    const long it = q0 + qq;
+    const ffc* hp = nullptr;
+    int64_t oo = 0, cs = 0;
+    int ka = 0, slot = 0;
+    if (it < nitems) {
+      const int cc = (int)(it / na), aa = gs + (int)(it - (long)cc * na);
+      const int cg = A.c0 + cc;
+      slot = cg / A.ns;
+      const int sl = cg - slot * A.ns;
+      const int kb = A.blk.kb[slot];
+      ka = A.Ka[(size_t)kb * A.nA + aa];
+      oo = (int64_t)A.off[(size_t)kb * A.nA + aa];
+      cs = (int64_t)sl * A.ld;
+      hp = reinterpret_cast<const ffc*>(A.gh) + (size_t)cc * Nr * A.nA + aa;
+    }
+    s_h[qq] = hp;
+    s_o[qq] = oo;
+    s_cs[qq] = cs;
+    s_ka[qq] = ka;
+    s_slot[qq] = slot;
+  }
+  __syncthreads();
+  const int q = threadIdx.x % RAD_Q;
+  const int kg = threadIdx.x / RAD_Q;
+  constexpr int KG = RAD_THREADS / RAD_Q;
+  ff acc[2 * 16];   // up to 16 k per thread: K <= 64
+#pragma unroll
+  for (int i = 0; i < 32; ++i) acc[i] = ff(0);
+  const int kper = (K + KG - 1) / KG;
+  for (int p0 = 0; p0 < Nr; p0 += PC) {
+    const int pc = min(PC, Nr - p0);
+    __syncthreads();
+#pragma unroll 4
+    for (int i = threadIdx.x; i < PC * RAD_Q; i += blockDim.x) {
+      const int pp = i / RAD_Q, qq = i - pp * RAD_Q;
+      ffc v;
+      v.x = ff(0);
+      v.y = ff(0);
+      const ffc* hp = s_h[qq];
+      if (hp && pp < pc) v = hp[(size_t)(p0 + pp) * A.nA];
+      Hs[pp * RAD_Q + qq] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int k = kg + j * KG;
+      if (j < kper && k < K) {
+        ff ax = acc[2 * j], ay = acc[2 * j + 1];
+        const ff* rr = Rs + (size_t)k * Nrp + p0;
+        for (int pp = 0; pp < pc; ++pp) {
+          const ffc hv = Hs[pp * RAD_Q + q];
+          ax += rr[pp] * hv.x;
+          ay += rr[pp] * hv.y;
+        }
+        acc[2 * j] = ax;
+        acc[2 * j + 1] = ay;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int k = kg + j * KG;
+    if (j < kper && k < K) {
+      ffc v;
+      v.x = acc[2 * j];
+      v.y = acc[2 * j + 1];
+      Ys[q * (K + 1) + k] = v;
+    }
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < RAD_Q * K; idx += RAD_THREADS) {
+    const int qq = idx / K, k = idx - qq * K;
+    if (k >= s_ka[qq]) continue;
+    const int slot = s_slot[qq];
+    const int64_t oo = s_o[qq] + k;
+    const double* x = A.blk.x[slot] + 2 * (oo + s_cs[qq]);
+    double* y = A.blk.y[slot] + 2 * (oo + s_cs[qq]);
+    const double d = A.ke[A.keoff[slot] + oo];
+    const ffc h = Ys[qq * (K + 1) + k];
+    const double x0 = x[0], x1 = x[1];
+    double y0 = d * x0 + ff_to(h.x), y1 = d * x1 + ff_to(h.y);
+    if (A.step) {
+      const double al = A.cs.al[slot], cc2 = A.cs.c[slot], be = A.cs.be[slot];
+      y0 = al * (y0 - cc2 * x0);
+      y1 = al * (y1 - cc2 * x1);
+      if (be != 0.0) {
+        y0 -= be * y[0];
+        y1 -= be * y[1];
+      }
+    }
+    y[0] = y0;
+    y[1] = y1;
+  }
+}
+
 // --------------------------------------------------------------------------- slab
 template <typename T>
 struct SlabArgs {
@@ -988,10 +1183,19 @@ __global__ void __launch_bounds__(SLAB_THREADS, sizeof(R) == 4 ? 3 : (std::is_sa
 #pragma unroll
     for (int a = 0; a < 12; ++a) {
       const int pa = valid ? sp[4 * a] : -1;
-      V v = mk<T>(T(0), T(0));
-      if (pa >= 0) v = Gc[pa];
-      xr[a] = to_r<R>(v.x);
-      xi[a] = to_r<R>(v.y);
+      if constexpr (std::is_same<R, ff>::value) {   // G holds double-float pairs
+        ffc v;
+        v.x = ff(0);
+        v.y = ff(0);
+        if (pa >= 0) v = reinterpret_cast<const ffc*>(Gc)[pa];
+        xr[a] = v.x;
+        xi[a] = v.y;
+      } else {
+        V v = mk<T>(T(0), T(0));
+        if (pa >= 0) v = Gc[pa];
+        xr[a] = to_r<R>(v.x);
+        xi[a] = to_r<R>(v.y);
+      }
     }
     dft12<+1, R>(xr, xi);
     C* row = Tb + ((size_t)s * nmr + r) * SQ_RS + 12 * ((q >> 1) + 2 * (q & 1));
@@ -1080,7 +1284,16 @@ __global__ void __launch_bounds__(SLAB_THREADS, sizeof(R) == 4 ? 3 : (std::is_sa
 #pragma unroll
       for (int a = 0; a < 12; ++a) {
         const int pa = sp[4 * a];
-        if (pa >= 0) Hc[pa] = mk<T>(from_r<T>(xr[a]), from_r<T>(xi[a]));
+        if constexpr (std::is_same<R, ff>::value) {   // H holds double-float pairs
+          if (pa >= 0) {
+            ffc v;
+            v.x = xr[a];
+            v.y = xi[a];
+            reinterpret_cast<ffc*>(Hc)[pa] = v;
+          }
+        } else {
+          if (pa >= 0) Hc[pa] = mk<T>(from_r<T>(xr[a]), from_r<T>(xi[a]));
+        }
       }
     }
   }
@@ -1118,10 +1331,7 @@ static bool use_slab_q(const hw_ctx* ctx, size_t elem) {
   const bool want = ctx->slab_r16 == 3 || (ctx->slab_r16 == 2 && elem == sizeof(float2));
   return want && slab_q_shape(ctx);
 }
-// an FP64 H X (elem = 16 bytes) launched with double-float angular transforms
-static bool use_slab_ff(const hw_ctx* ctx, size_t elem) {
-  return ctx->ff_now && elem == sizeof(double2) && slab_q_shape(ctx);
-}
+
 
 // --------------------------------------------------------------------------- host launcher
 // the slab kernel for this basis's angular grid: specialised for the grids in use, generic
@@ -1133,13 +1343,14 @@ static void* slab_kernel(int n1, int n2) {
   return (void*)k_slab<T, 0, 0>;
 }
 
+// ffp: the double-float FP64 path (G and H hold FP32 pairs)
 template <typename T>
-static cudaError_t launch_slab(const hw_ctx* ctx, dim3 grid, size_t smem, const SlabArgs<T>& sa) {
-  if (use_slab_ff(ctx, sizeof(cplx_t<T>)) || use_slab_q(ctx, sizeof(cplx_t<T>))) {
+static cudaError_t launch_slab(const hw_ctx* ctx, dim3 grid, size_t smem, const SlabArgs<T>& sa, bool ffp = false) {
+  if (ffp || use_slab_q(ctx, sizeof(cplx_t<T>))) {
     const int sq = slab_q_per_cta(sa.nmr);
     const dim3 g((grid.x + sq - 1) / sq, grid.y);
     if constexpr (sizeof(T) == sizeof(double)) {
-      if (use_slab_ff(ctx, sizeof(cplx_t<T>))) {
+      if (ffp) {
         k_slab_q<double, ff><<<g, SLAB_THREADS, smem, ctx->stream>>>(sa, reinterpret_cast<const ff*>(ctx->db.vff), sq);
         return cudaGetLastError();
       }
@@ -1164,7 +1375,7 @@ size_t slab_smem_bytes(const hw_ctx* ctx, size_t elem, int Jc) {
   const auto& hb = ctx->hb;
   const int nmr = (int)hb.mrow_m.size();
   const int n1 = hb.prm.Nth1, n2 = hb.prm.Nth2;
-  if (use_slab_q(ctx, elem) || use_slab_ff(ctx, elem)) return slab_q_smem_bytes(nmr, elem);   // no theta2 chunks
+  if (use_slab_q(ctx, elem)) return slab_q_smem_bytes(nmr, elem);   // no theta2 chunks
   if (use_slab_r16(ctx, elem)) return slab_r16_smem_bytes(nmr, n2, elem);
   // padded layout: the FP32 kernels specialised for the grid (k_slab's PAD)
   const bool pad = elem == sizeof(float2) && slab_kernel<float>(n1, n2) != (void*)k_slab<float, 0, 0>;
@@ -1239,6 +1450,9 @@ static cudaError_t launch_hx_bufs(hw_ctx* ctx, const Blocks& blk, int ns, int64_
     ra.blk = blk;
     ra.gh = reinterpret_cast<cplx_t<T>*>(gbuf);
     ra.rtab = tb.rinv;
+    // FP64 H X in double-float (a mixed solve's, or HW_FP64_DF): all three kernels, which pass
+    // FP32 pairs through G and H, on the register slab's shape and without nu != 0 terms
+    const bool ffp = sizeof(T) == 8 && ctx->ff_now && slab_q_shape(ctx) && !ra.any_nu;
     dim3 grid((unsigned)(((long)maxna * nc + RAD_Q - 1) / RAD_Q), hb.N + 1);
     const size_t sm_inv = rad_inv_smem(Nr, K, sizeof(T));
     const bool tc = sizeof(T) == 4 && ctx->radial_tc && db.rt_ok;
@@ -1247,6 +1461,9 @@ static cudaError_t launch_hx_bufs(hw_ctx* ctx, const Blocks& blk, int ns, int64_
       if (tc) {
         const cudaError_t e = launch_rinv_tc(ctx, blk, ns, ld, nc, c0, gbuf, 0);
         if (e != cudaSuccess) return e;
+      } else if (ffp) {
+        if constexpr (sizeof(T) == 8)
+          k_radial_inv_ff<<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra, reinterpret_cast<const ff*>(db.ff_rinv));
       } else {
         k_radial_inv<T><<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra);
       }
@@ -1271,10 +1488,10 @@ static cudaError_t launch_hx_bufs(hw_ctx* ctx, const Blocks& blk, int ns, int64_
     sa.tw2 = reinterpret_cast<const cplx_t<T>*>(tb.tw2);
     sa.G = reinterpret_cast<const cplx_t<T>*>(gbuf);
     sa.H = reinterpret_cast<cplx_t<T>*>(hbuf);
-    const size_t sm_slab = slab_smem_bytes(ctx, sizeof(cplx_t<T>), Jc);
+    const size_t sm_slab = ffp ? slab_q_smem_bytes(sa.nmr, sizeof(double2)) : slab_smem_bytes(ctx, sizeof(cplx_t<T>), Jc);
     {
       ProfScope ps(ctx, HW_PH_SLAB);
-      launch_slab<T>(ctx, dim3(nc, Nr), sm_slab, sa);
+      launch_slab<T>(ctx, dim3(nc, Nr), sm_slab, sa, ffp);
       ctx->launches++;
     }
     ra.gh = reinterpret_cast<cplx_t<T>*>(hbuf);
@@ -1289,6 +1506,9 @@ static cudaError_t launch_hx_bufs(hw_ctx* ctx, const Blocks& blk, int ns, int64_
       if (tc && !ra.any_nu) {
         const cudaError_t e = launch_rfwd_tc(ctx, blk, ns, ld, nc, c0, hbuf, step);
         if (e != cudaSuccess) return e;
+      } else if (ffp) {
+        if constexpr (sizeof(T) == 8)
+          k_radial_fwd_ff<<<grid, RAD_THREADS, sm_fwd, ctx->stream>>>(ra, reinterpret_cast<const ff*>(db.ff_rfwd));
       } else {
         k_radial_fwd<T><<<grid, RAD_THREADS, sm_fwd, ctx->stream>>>(ra);
       }
@@ -1703,6 +1923,8 @@ cudaError_t hx_configure(hw_ctx* ctx) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radial_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radial_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radial_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radial_inv_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_radial_fwd_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   for (void* f : {(void*)k_slab<double, 0, 0>, (void*)k_slab<float, 0, 0>, (void*)k_slab<double, 64, 48>,
                   (void*)k_slab<float, 64, 48>, (void*)k_slab<double, 192, 96>, (void*)k_slab<float, 192, 96>,
                   (void*)k_slab_r16<float, 64, 48>, (void*)k_slab_r16<double, 64, 48>, (void*)k_slab_q<float>,

@@ -207,8 +207,8 @@ def test_apply_H_fp64_tube_slab_variants_agree(tube, hwmod):
 
 
 def test_apply_H_fp64_df_tube_matches_oracle(tube, hwmod):
-    """hw_apply_H with HW_FP64_DF: the angular transforms in double-float arithmetic (FP32 pairs),
-    radial transforms and diagonal in FP64.  Entry-wise within the FP64 tolerance of the oracle,
+    """hw_apply_H with HW_FP64_DF: the radial and angular transforms in double-float arithmetic
+    (FP32 pairs), the diagonal in FP64.  Entry-wise within the FP64 tolerance of the oracle,
     and within 1e-12 (column norms) of the FP64 kernel; 9 ragged columns (three CTAs of 4 slabs,
     the last with one), padded leading dimension."""
     kp = tube.kps[0]
