@@ -1093,8 +1093,9 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
   __syncthreads();
   for (int k = 0; k < nv - 2; ++k) {
     const int m = nv - k - 1;   // length of the column below the diagonal
-    float s = 0.f;
-    for (int w = 0; w < nwarp; ++w) s += red_s[w];
+    // the per-warp partials summed by a shuffle tree in every warp (lane w holds warp w's)
+    float s = lane < nwarp ? red_s[lane] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     // every thread forms the reflector scalars from the same values (no broadcast barrier)
     float bet;
     float2 alpha;
@@ -1206,8 +1207,8 @@ __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
     __syncthreads();   // B2: p and the v^H p partials published
     // K = (beta / 2) v^H p (real for Hermitian A'); A' -= v w^H + w v^H, w = p - K v, on the
     // lower triangle, one warp per row; lane 0 (column k + 1) sums the next column's norm
-    float kk = 0.f;
-    for (int w = 0; w < nwarp; ++w) kk += red_k[w];
+    float kk = lane < nwarp ? red_k[lane] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) kk += __shfl_xor_sync(0xffffffffu, kk, o);
     kk *= 0.5f * bet;
     float s1 = 0.f;
     for (int i = warp; i < m; i += nwarp) {
