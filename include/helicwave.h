@@ -381,8 +381,9 @@ typedef enum {
                                0 disables (FP64 throughout); 1..12; default 5. */
   HW_OPT_GRAM_KERNEL = 3,   /* mixed form, FP32-product phase only: 1 forms the products
                                A^H B over the basis dimension with hw_gram's kernel (FP32
-                               products, FP64 accumulation every 32 rows); 0 (default) uses
-                               cuBLAS CGEMM on FP32 copies, measured faster on the tube. */
+                               products, FP64 accumulation every 32 rows); 0 (default) leaves
+                               them to HW_OPT_TC_GEMM's route (the tensor-core kernel), measured
+                               faster on the tube. */
   HW_OPT_HYBRID = 4,        /* mixed form, FP64 phase: 1 (default) first keeps FP64 only for
                                the products that involve X (its rows of the Rayleigh-Ritz matrix,
                                its share of the X / H X updates, one projection of W and of P
@@ -427,9 +428,10 @@ typedef enum {
   HW_OPT_TC_GEMM = 12,      /* the eigensolver's block products: 1 (default) the tensor-core
                                kernel of hw_block_product (FP64 class in the FP64 phases, FP32
                                class in the FP32-product phase) for every product with an extent
-                               over the basis dimension (m or k >= 1024), cuBLAS for the small
-                               dense products of the Rayleigh-Ritz step; 2 the tensor-core kernel
-                               for every product; 0 cuBLAS (ZGEMM, or CGEMM on FP32 copies). */
+                               over the basis dimension (m or k >= 1024), the small dense
+                               products of the Rayleigh-Ritz step as HW_OPT_SMALL_GEMM says; 2 the
+                               tensor-core kernel for every product; 0 cuBLAS over the basis
+                               dimension (ZGEMM, or CGEMM on FP32 copies). */
   HW_OPT_RADIAL_KERNEL = 13, /* radial transforms of the mixed-precision H X: 1 (default) on
                                the tensor cores (both operands split into three BF16 parts, the
                                six part products as tcgen05 MMAs, the leading one in its own TMEM
@@ -467,7 +469,8 @@ typedef enum {
   HW_PH_SLAB = 1,         /* angular FFTs with the potential multiply (Algorithms 2, 4)     */
   HW_PH_RADIAL_FWD = 2,   /* forward radial quadrature + diagonal + scatter (Algorithm 3)   */
   HW_PH_PRECOND = 3,      /* diagonal preconditioner                                        */
-  HW_PH_GEMM = 4,         /* block products of the eigensolver (cuBLAS ZGEMM / CGEMM)       */
+  HW_PH_GEMM = 4,         /* block products of the eigensolver (tensor-core, small-product
+                             and, where an option selects it, cuBLAS kernels)               */
   HW_PH_CHOL = 5,         /* Cholesky factorisations + triangular solves                    */
   HW_PH_EIG = 6,          /* rest of the Rayleigh-Ritz eigensolver (eigenvalues, vectors,
                              FP64 refinement)                                               */
