@@ -443,7 +443,7 @@ typedef enum {
                                and the FP64 check of every convergence claim): 1 (default) the
                                angular transforms in double-float arithmetic (as hw_apply_H with
                                HW_FP64_DF), 0 in FP64.  HW_FP64 solves always use FP64. */
-  HW_OPT_SMALL_GEMM = 15    /* the eigensolver's small products (every extent below 1024: the
+  HW_OPT_SMALL_GEMM = 15,   /* the eigensolver's small products (every extent below 1024: the
                                Rayleigh-Ritz refinement, the Newton-Schulz steps): 1 (default)
                                the library's SIMT kernel for the FP32 class (FP64 operands
                                rounded to FP32, as hw_block_product class 3) and, inside
@@ -453,6 +453,12 @@ typedef enum {
                                within the solver's 1e-9 check); HW_FP64 solves and hw_heev take
                                cuBLAS ZGEMM for the FP64 class; 2 the SIMT kernel for both classes
                                everywhere; 0 cuBLAS for both. */
+  HW_OPT_OVERLAP_LAUNCH = 16 /* the FP32 H X's three kernels (tensor-core radial inverse, register
+                               slab, tensor-core radial forward): 1 (default) launched with
+                               programmatic stream serialisation, so that each starts its CTAs
+                               while the one before it drains and waits on the device for that
+                               kernel's results (the same order and results as 0); 0 plain
+                               stream-ordered launches. */
 } hw_option;
 /* Set an option (HW_EINVAL for an unknown option, a read-only one or a bad value). */
 hw_status hw_set_option(hw_ctx* ctx, int option, int value);

@@ -634,6 +634,11 @@ hw_status hw_set_option(hw_ctx* ctx, int option, int value) {
     ctx->small_gemm = value;
     return HW_OK;
   }
+  if (option == HW_OPT_OVERLAP_LAUNCH) {
+    if (value != 0 && value != 1) return hw_fail(ctx, HW_EINVAL, "overlapped-launch option 0 or 1");
+    ctx->overlap_launch = value;
+    return HW_OK;
+  }
   return hw_fail(ctx, HW_EINVAL, "unknown or read-only option");
 }
 
@@ -655,6 +660,7 @@ hw_status hw_get_option(hw_ctx* ctx, int option, long long* value) {
   if (option == HW_OPT_RADIAL_KERNEL) { *value = ctx->radial_tc; return HW_OK; }
   if (option == HW_OPT_FP64_HX) { *value = ctx->fp64_hx_ff; return HW_OK; }
   if (option == HW_OPT_SMALL_GEMM) { *value = ctx->small_gemm; return HW_OK; }
+  if (option == HW_OPT_OVERLAP_LAUNCH) { *value = ctx->overlap_launch; return HW_OK; }
   return hw_fail(ctx, HW_EINVAL, "unknown option");
 }
 

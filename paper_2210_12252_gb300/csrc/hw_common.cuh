@@ -41,6 +41,15 @@ __device__ __forceinline__ V cmul_i(V a, int s) {
   return r;
 }
 
+// Programmatic dependent launch.  A kernel launched with the programmatic-serialisation
+// attribute may start while the kernel before it in the stream is still running; it touches
+// nothing that kernel writes or reads, and allocates no tensor memory, before griddep_wait(),
+// which returns once that kernel has completed and its writes are visible (at once in a launch
+// without the attribute).  griddep_launch() lets the next such kernel start its CTAs early, as
+// this grid's resources free up.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 // FP64 <-> FP32 by integer bit operations.  This GPU executes the hardware conversions on its
 // FP64 pipe (1/64 of the FP32 rate), which otherwise bounds kernels that convert every operand.
 // d2f: round to nearest, ties to even (as a cast); magnitudes below 2^-126 flush to zero,

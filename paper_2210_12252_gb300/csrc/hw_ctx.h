@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "hw_internal.h"
@@ -133,6 +134,7 @@ struct hw_ctx {
   bool mixed_solve = false;    // a mixed-precision solve is running
   bool ff_now = false;         // the FP64 H X being launched uses the double-float angular kernel
   int radial_tc = 1;           // HW_OPT_RADIAL_KERNEL
+  int overlap_launch = 1;      // HW_OPT_OVERLAP_LAUNCH: the FP32 H X chain by programmatic dependent launch
   int64_t rr_fallbacks = 0;    // Householder results rejected by the check (Jacobi used)
   // residual history of the last hw_solve_eigs: per k-point slot, per iteration (filter cycle
   // or LOBPCG iteration) the phase code (HW_HIST_*) and the largest wanted residual
@@ -158,6 +160,28 @@ class ProfScope {
   cudaEvent_t a_ = nullptr;
 };
 }  // namespace hw
+
+#ifdef __CUDACC__
+namespace hw {
+// Launch k on the context's stream; overlap: with the programmatic-serialisation attribute (the
+// kernel waits for its predecessor with griddep_wait before it touches that kernel's data).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_ex(const hw_ctx* ctx, bool overlap, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = overlap ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+}  // namespace hw
+#endif
 
 namespace hw {
 template <typename T>

@@ -1169,6 +1169,7 @@ __global__ void __launch_bounds__(SLAB_THREADS, sizeof(R) == 4 ? 3 : (std::is_sa
     const V w = A.tw2[t];
     T48[t] = mkr<R>(to_r<R>(w.x), to_r<R>(w.y));
   }
+  griddep_wait();   // G is the radial inverse's output (the tables above are the basis's)
   __syncthreads();
   const int lane = threadIdx.x & 31, q = lane & 3;
   const int nq2 = SQ * nmr * 4;   // theta2 lanes
@@ -1259,6 +1260,7 @@ __global__ void __launch_bounds__(SLAB_THREADS, sizeof(R) == 4 ? 3 : (std::is_sa
       if (r < nmr) col[r * SQ_RS] = mkr<R>(vr, vi);
     }
   }
+  griddep_launch();   // only the forward theta2 pass is left: the next kernel's CTAs may start
   __syncthreads();
   // ---- forward theta2: Tb -> H (kept pairs only)
   if (threadIdx.x - lane < nq2) {
@@ -1355,8 +1357,9 @@ static cudaError_t launch_slab(const hw_ctx* ctx, dim3 grid, size_t smem, const 
         return cudaGetLastError();
       }
     }
-    k_slab_q<T><<<g, SLAB_THREADS, smem, ctx->stream>>>(sa, sa.V, sq);
-    return cudaGetLastError();
+    // the FP32 slab between the tensor-core radial kernels starts while the inverse drains
+    return launch_ex(ctx, sizeof(T) == 4 && ctx->overlap_launch != 0, k_slab_q<T, T>, g, dim3(SLAB_THREADS), smem, sa,
+                     sa.V, sq);
   }
   void* f = use_slab_r16(ctx, sizeof(cplx_t<T>)) ? (void*)k_slab_r16<T, 64, 48> : slab_kernel<T>(sa.Nth1, sa.Nth2);
   void* args[] = {(void*)&sa};

@@ -103,8 +103,16 @@ __device__ __forceinline__ void put3(unsigned char* tile, int row, int col, floa
 }
 
 // ------------------------------------------------------------------------------- inverse
-// grid: x = tile of RT_ITEMS items within group g, y = g
-__global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(const __grid_constant__ CUtensorMap tmT, RadTcArgs A) {
+// grid: x = tile of RT_ITEMS items within group g, y = g.  Nine warps: warps 0-7 gather the
+// coefficients and drain TMEM, warp 8 allocates TMEM and issues the MMAs.  A CTA of a kernel that
+// allocates TMEM holds the SM's allocation permit until it has allocated: no further CTA of the
+// kernel starts on that SM meanwhile.  So the allocation comes first, in its own warp, and the
+// third CTA of an SM (two hold their 2 N_r columns at once) gathers while that warp waits for a
+// sibling's columns.  Before griddep_wait only the basis's constant tables are read, and no TMEM
+// is allocated.
+constexpr int RI_THREADS = RT_THREADS + 32;
+constexpr int RI_MMA_WARP = RT_THREADS / 32;
+__global__ void __launch_bounds__(RI_THREADS, 3) k_rinv_tc(const __grid_constant__ CUtensorMap tmT, RadTcArgs A) {
   extern __shared__ __align__(1024) unsigned char rsm_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)rsm_raw + 1023) & ~(uintptr_t)1023);
   const int g = blockIdx.y;
@@ -121,79 +129,84 @@ __global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(const __grid_constant__ 
   __shared__ float2* s_g[RT_ITEMS];
   __shared__ int s_ka[RT_ITEMS];
   __shared__ float s_sc[RT_ITEMS];
+  __shared__ int s_tab_ok;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool mw = warp == RI_MMA_WARP;
   const uint32_t tcols = 2 * NP <= 32 ? 32 : (2 * NP <= 64 ? 64 : (2 * NP <= 128 ? 128 : (2 * NP <= 256 ? 256 : 512)));
-  if (threadIdx.x == 0) {
-    mbar_init(&bar_mma, 1);
-    mbar_init(&bar_tab, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    load_table_tma(&tmT, g, NP, KB, sB, &bar_tab);
-  }
-  if (threadIdx.x < RT_ITEMS) {
-    const int q = threadIdx.x;
-    const long item = q0 + q;
-    const double* xp = nullptr;
-    float2* gp = nullptr;
-    int ka = 0;
-    float sc = 0.f;
-    if (item < nitems) {
-      const int c = (int)(item / na), a = gs + (int)(item - (long)c * na);
-      const int cg = A.c0 + c;
-      const int slot = cg / A.ns, sl = cg - slot * A.ns;
-      const int kbk = A.blk.kb[slot];
-      ka = A.Ka[(size_t)kbk * A.nA + a];
-      xp = A.blk.x[slot] + 2 * ((size_t)A.off[(size_t)kbk * A.nA + a] + (size_t)sl * A.ld);
-      gp = A.gh + (size_t)c * A.Nr * A.nA + a;
-      if (A.scale_mode != 0)
-        sc = (float)(6.283185307179586 * (A.scale_mode == 1 ? (double)A.mrow_m[A.pair_mrow[a]]
-                                                             : (double)A.pair_n[a] * A.ncyc));
+  if (mw) {
+    if (lane == 0) {
+      mbar_init(&bar_mma, 1);
+      mbar_init(&bar_tab, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      load_table_tma(&tmT, g, NP, KB, sB, &bar_tab);
     }
-    s_x[q] = xp;
-    s_g[q] = gp;
-    s_ka[q] = ka;
-    s_sc[q] = sc;
-  }
-  __syncthreads();
-  // A rows (2q + part) over k: a warp takes the items warp, warp + 8, ...; lanes over k.  Every
-  // load of the warp's items is issued before the first is used.
-  constexpr int IW = RT_ITEMS / (RT_THREADS / 32);   // items per warp
-  for (int kb = 0; kb < KB; ++kb) {
-    const int k = kb * 32 + lane;
-    double xr[IW], xi[IW];
+    __syncwarp();
+    griddep_wait();
+    tmem_alloc(&tmem_s, tcols);
+  } else {
+    if (threadIdx.x < RT_ITEMS) {
+      const int q = threadIdx.x;
+      const long item = q0 + q;
+      const double* xp = nullptr;
+      float2* gp = nullptr;
+      int ka = 0;
+      float sc = 0.f;
+      if (item < nitems) {
+        const int c = (int)(item / na), a = gs + (int)(item - (long)c * na);
+        const int cg = A.c0 + c;
+        const int slot = cg / A.ns, sl = cg - slot * A.ns;
+        const int kbk = A.blk.kb[slot];
+        ka = A.Ka[(size_t)kbk * A.nA + a];
+        xp = A.blk.x[slot] + 2 * ((size_t)A.off[(size_t)kbk * A.nA + a] + (size_t)sl * A.ld);
+        gp = A.gh + (size_t)c * A.Nr * A.nA + a;
+        if (A.scale_mode != 0)
+          sc = (float)(6.283185307179586 * (A.scale_mode == 1 ? (double)A.mrow_m[A.pair_mrow[a]]
+                                                               : (double)A.pair_n[a] * A.ncyc));
+      }
+      s_x[q] = xp;
+      s_g[q] = gp;
+      s_ka[q] = ka;
+      s_sc[q] = sc;
+    }
+    griddep_wait();   // X is the previous kernels' output
+    asm volatile("bar.sync 1, %0;" ::"r"(RT_THREADS) : "memory");   // the gather warps only
+    // A rows (2q + part) over k: a warp takes the items warp, warp + 8, ...; lanes over k.  Every
+    // load of the warp's items is issued before the first is used.
+    constexpr int IW = RT_ITEMS / (RT_THREADS / 32);   // items per warp
+    for (int kb = 0; kb < KB; ++kb) {
+      const int k = kb * 32 + lane;
+      double xr[IW], xi[IW];
 #pragma unroll
-    for (int i = 0; i < IW; ++i) {
-      const int q = warp + 8 * i;
-      xr[i] = 0.0;
-      xi[i] = 0.0;
-      if (k < s_ka[q]) {
-        xr[i] = s_x[q][2 * k];
-        xi[i] = s_x[q][2 * k + 1];
+      for (int i = 0; i < IW; ++i) {
+        const int q = warp + 8 * i;
+        xr[i] = 0.0;
+        xi[i] = 0.0;
+        if (k < s_ka[q]) {
+          xr[i] = s_x[q][2 * k];
+          xi[i] = s_x[q][2 * k + 1];
+        }
+      }
+      unsigned char* tile = sA + (size_t)kb * RT_ATILE;
+#pragma unroll
+      for (int i = 0; i < IW; ++i) {
+        const int q = warp + 8 * i;
+        float re = d2f(xr[i]), im = d2f(xi[i]);
+        if (A.scale_mode != 0) {   // times i s
+          const float sc = s_sc[q], t = re;
+          re = -sc * im;
+          im = sc * t;
+        }
+        put3(tile, 2 * q, lane, re);
+        put3(tile, 2 * q + 1, lane, im);
       }
     }
-    unsigned char* tile = sA + (size_t)kb * RT_ATILE;
-#pragma unroll
-    for (int i = 0; i < IW; ++i) {
-      const int q = warp + 8 * i;
-      float re = d2f(xr[i]), im = d2f(xi[i]);
-      if (A.scale_mode != 0) {   // times i s
-        const float sc = s_sc[q], t = re;
-        re = -sc * im;
-        im = sc * t;
-      }
-      put3(tile, 2 * q, lane, re);
-      put3(tile, 2 * q + 1, lane, im);
-    }
+    fence_proxy_async();
   }
-  // TMEM only now: a CTA waiting for columns (2 N_r of them, so that at most two CTAs per SM
-  // hold TMEM) has done its gathers meanwhile
-  if (warp == 0) tmem_alloc(&tmem_s, tcols);
-  fence_proxy_async();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_s;
-  __shared__ int s_tab_ok;
-  if (threadIdx.x == 0) {
+  if (mw && lane == 0) {
     s_tab_ok = mbar_wait(&bar_tab, 0);
     if (s_tab_ok) {
       const uint32_t idesc = umma_idesc_bf16(NP);
@@ -208,9 +221,10 @@ __global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(const __grid_constant__ 
   __syncthreads();
   const bool tab_ok = s_tab_ok;
   bool ok = tab_ok && mbar_wait(&bar_mma, 0);
+  griddep_launch();   // only the drain is left: the next kernel's CTAs may start
   if (!ok && threadIdx.x == 0) atomicExch(A.status, HW_ETIMEOUT);
   tc_fence_after();
-  if (ok) {
+  if (ok && !mw) {
     // lane quadrant = warp % 4: row 2q + part holds D[row][p] for all p; warps w and w + 4 take
     // alternate 16-column chunks.  The lanes of an item's re and im rows swap halves so that
     // each stores one complex entry per column pair: the re lane column p, the im lane p + 1.
@@ -235,10 +249,10 @@ __global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(const __grid_constant__ 
   if (!ok && tab_ok) {   // the tensor core must be done with TMEM before it is released
     if (!mbar_wait(&bar_mma, 0) && threadIdx.x == 0) atomicExch(A.status, HW_ETIMEOUT);
   }
-  if (!tab_ok && threadIdx.x == 0) mbar_wait(&bar_tab, 0);   // the copies in flight land before exit
+  if (!tab_ok && mw && lane == 0) mbar_wait(&bar_tab, 0);   // the copies in flight land before exit
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (mw) {
     tc_fence_after();
     tmem_dealloc(tmem, tcols);
   }
@@ -246,7 +260,12 @@ __global__ void __launch_bounds__(RT_THREADS) k_rinv_tc(const __grid_constant__ 
 
 // ------------------------------------------------------------------------------- forward
 // grid: x = tile of RT_ITEMS items within group g, y = g.  No nu != 0 terms (the SIMT kernel
-// takes those launches).
+// takes those launches).  Before griddep_wait only the basis's constant tables are read.  TMEM
+// (2 K_p columns, three CTAs per SM within the 512) is allocated first, so that the SM's
+// allocation permit passes on at once and all three CTAs start while the slab drains: the kernel
+// before this one is always a slab kernel, which holds no TMEM, and that kernel signals its
+// dependents only after its own wait, so every earlier kernel has completed when a CTA of this
+// one starts.
 __global__ void __launch_bounds__(RT_THREADS, 3) k_rfwd_tc(const __grid_constant__ CUtensorMap tmT, RadTcArgs A) {
   extern __shared__ __align__(1024) unsigned char rsm_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)rsm_raw + 1023) & ~(uintptr_t)1023);
@@ -299,6 +318,7 @@ __global__ void __launch_bounds__(RT_THREADS, 3) k_rfwd_tc(const __grid_constant
     s_ka[qq] = ka;
     s_slot[qq] = slot;
   }
+  griddep_wait();   // H, X and Y are the previous kernels' data
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -342,6 +362,7 @@ __global__ void __launch_bounds__(RT_THREADS, 3) k_rfwd_tc(const __grid_constant
   __syncthreads();   // s_bad as the MMA thread left it
   const int bad = s_bad;
   bool ok = !bad && mbar_wait(&bar_mma[jl & 1], (uint32_t)((jl >> 1) & 1));
+  griddep_launch();   // only the drain and the output are left: the next kernel's CTAs may start
   if (!ok && threadIdx.x == 0) atomicExch(A.status, HW_ETIMEOUT);
   tc_fence_after();
   __syncthreads();   // every thread is past its reads of the A stages (Ys reuses them)
@@ -467,6 +488,12 @@ cudaError_t radial_tc_setup(hw_ctx* ctx, const HostBasis& hb, const std::vector<
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_rfwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)rfwd_tc_smem(db.rt_kpad, db.rt_kbp));
+  // the largest shared-memory carveout: without it the driver's choice held two inverse CTAs per
+  // SM, and the third of an SM started only when one of the first two had finished
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_rinv_tc, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_rfwd_tc, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   return e;
 }
 
@@ -513,8 +540,8 @@ cudaError_t launch_rinv_tc(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, i
                            int scale_mode) {
   RadTcArgs a = tc_args(ctx, blk, ns, ld, nc, c0, gbuf);
   a.scale_mode = scale_mode;
-  k_rinv_tc<<<tc_grid(ctx, nc), RT_THREADS, rinv_tc_smem(a.npad, a.kb), ctx->stream>>>(ctx->db.rt_map_inv, a);
-  return cudaGetLastError();
+  return launch_ex(ctx, ctx->overlap_launch != 0, k_rinv_tc, tc_grid(ctx, nc), dim3(RI_THREADS),
+                   rinv_tc_smem(a.npad, a.kb), ctx->db.rt_map_inv, a);
 }
 
 cudaError_t launch_rfwd_tc(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, int nc, int c0, void* hbuf,
@@ -524,8 +551,8 @@ cudaError_t launch_rfwd_tc(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, i
     a.step = 1;
     a.cs = *step;
   }
-  k_rfwd_tc<<<tc_grid(ctx, nc), RT_THREADS, rfwd_tc_smem(a.kpad, a.kbp), ctx->stream>>>(ctx->db.rt_map_fwd, a);
-  return cudaGetLastError();
+  return launch_ex(ctx, ctx->overlap_launch != 0, k_rfwd_tc, tc_grid(ctx, nc), dim3(RT_THREADS),
+                   rfwd_tc_smem(a.kpad, a.kbp), ctx->db.rt_map_fwd, a);
 }
 
 }  // namespace hw

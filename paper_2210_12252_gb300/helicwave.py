@@ -279,6 +279,7 @@ HW_OPT_TC_GEMM = 12
 HW_OPT_RADIAL_KERNEL = 13
 HW_OPT_FP64_HX = 14
 HW_OPT_SMALL_GEMM = 15
+HW_OPT_OVERLAP_LAUNCH = 16
 
 
 def hw_set_option(h, option, value):

@@ -128,3 +128,22 @@ def test_solve_rejects_bad_arguments(hwmod, solver):
         with pytest.raises(hwmod.HwError) as e:
             ctx.solve_eigs(kidx, n_eig, **args)
         assert e.value.status == hwmod.HW_EINVAL, kw
+
+
+def test_chfsi_tube_mixed_overlap_bit_identical(hwmod):
+    """The chosen form with and without overlapped launches of the FP32 H X chain (the filter's
+    recurrence steps fused into the forward radial kernel): the same start block gives the same
+    eigenvalues bit for bit and the same number of cycles + iterations."""
+    w = inputs.tube()
+    res = {}
+    for ov in (1, 0):
+        ctx, L = make_ctx(hwmod, w)
+        ctx.set_option(hwmod.HW_OPT_OVERLAP_LAUNCH, ov)
+        X0 = torch.from_numpy(np.ascontiguousarray(inputs.random_block(int(L[0]), 76, 1234).T)).cuda()
+        r = ctx.solve_eigs([0], w.n_eig, block=76, tol=1e-6, maxit=100, prec="mixed", X0=[X0])
+        assert r["converged"]
+        res[ov] = r
+        ctx.close()
+    assert np.array_equal(res[1]["evals"][0], res[0]["evals"][0])
+    assert np.array_equal(np.asarray(res[1]["iters"]), np.asarray(res[0]["iters"]))
+    assert np.abs(res[1]["evals"][0] - golden("tube_eigs.txt")[: w.n_eig]).max() < 1e-6

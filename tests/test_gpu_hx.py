@@ -221,3 +221,28 @@ def test_apply_H_fp64_df_tube_matches_oracle(tube, hwmod):
     assert_entrywise(Ydf, Yref, FP64_TOL, FP64_FLOOR, "double-float angular transforms")
     assert rel_err(Ydf, Y64) < 1e-12
     print(f"double-float vs FP64 kernel: {rel_err(Ydf, Y64):.2e}; vs oracle {rel_err(Ydf, Yref):.2e}")
+
+
+def test_apply_H_mixed_overlapped_launches_bit_identical(tube, hwmod):
+    """HW_OPT_OVERLAP_LAUNCH only changes when the FP32 H X's three kernels start, not what they
+    compute: 76 columns (the Chebyshev block; ragged tiles in every |n| group), four chained
+    products (each output the next input), bit for bit the same with the option on and off."""
+    kp = tube.kps[0]
+    X = to_dev(inputs.random_block(kp.L, 76, 85))
+    keep = tube.ctx.get_option(hwmod.HW_OPT_OVERLAP_LAUNCH)
+    out = {}
+    try:
+        for ov in (1, 0):
+            tube.ctx.set_option(hwmod.HW_OPT_OVERLAP_LAUNCH, ov)
+            Z = X
+            chain = []
+            for _ in range(4):
+                Z = tube.ctx.apply_H(0, Z, prec="mixed")
+                chain.append(Z.clone())
+            torch.cuda.synchronize()
+            out[ov] = chain
+    finally:
+        tube.ctx.set_option(hwmod.HW_OPT_OVERLAP_LAUNCH, keep)
+    for a, b in zip(out[1], out[0]):
+        assert torch.equal(a, b)
+    assert torch.isfinite(torch.view_as_real(out[1][-1])).all()

@@ -147,6 +147,7 @@ def test_options_set_get_and_reject(lib):
     assert ctx.get_option(hw.HW_OPT_SLAB_KERNEL) == 2
     assert ctx.get_option(hw.HW_OPT_FP64_HX) == 1
     assert ctx.get_option(hw.HW_OPT_SMALL_GEMM) == 1
+    assert ctx.get_option(hw.HW_OPT_OVERLAP_LAUNCH) == 1
     ctx.set_option(hw.HW_OPT_SLAB_KERNEL, 3)
     assert ctx.get_option(hw.HW_OPT_SLAB_KERNEL) == 3
     ctx.set_option(hw.HW_OPT_WINDOW, 24)
@@ -160,7 +161,7 @@ def test_options_set_get_and_reject(lib):
                      (hw.HW_OPT_TAIL_NO_P, 2), (hw.HW_OPT_WINDOW, -1), (hw.HW_OPT_WINDOW, 101),
                      (hw.HW_OPT_TC_GEMM, 3), (hw.HW_OPT_TC_GEMM, -1), (hw.HW_OPT_RADIAL_KERNEL, 2),
                      (hw.HW_OPT_SLAB_KERNEL, 4), (hw.HW_OPT_SLAB_KERNEL, -1), (hw.HW_OPT_FP64_HX, 2),
-                     (hw.HW_OPT_SMALL_GEMM, 3)):
+                     (hw.HW_OPT_SMALL_GEMM, 3), (hw.HW_OPT_OVERLAP_LAUNCH, 2)):
         with pytest.raises(hw.HwError) as e:
             ctx.set_option(opt, val)
         assert e.value.status == hw.HW_EINVAL
