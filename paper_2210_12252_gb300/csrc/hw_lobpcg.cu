@@ -828,7 +828,10 @@ static hw_status ensure_work(hw_ctx* ctx, int nk, int nb, int64_t Lpad) {
   if (e == cudaSuccess) e = dense_alloc(w->dw, nk * ne2, nk);
   w->gbytes = gram_work_bytes(w->ne, w->ne, (int)Lpad, nk);
   A(&w->gwork, w->gbytes);
-  if (e == cudaSuccess && hh_smem(w->ne) <= 226 * 1024) {
+  // the Householder route wherever one of the Rayleigh-Ritz sizes fits a CTA's shared memory
+  // (nb: a filter cycle's; 2 nb: [X W]; 3 nb: [X W P]); rr_eig checks the size of each call,
+  // so a block whose 3 nb does not fit (above 78 columns) still takes it for the smaller ones
+  if (e == cudaSuccess && hh_smem(nb) <= 226 * 1024) {
     w->hh_bytes = hh_scratch_bytes(w->ne, w->ne, nk);
     e = cudaMalloc(&w->hh, w->hh_bytes);
     A((void**)&w->B1, (size_t)nk * w->ne * nb * sizeof(double2));
