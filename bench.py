@@ -49,6 +49,11 @@ def parse(argv=None):
     ap.add_argument("--solver", default="chfsi", choices=["chfsi", "lobpcg"],
                     help="eigensolver of the chosen form: Chebyshev-filtered FP32 phase then the "
                          "LOBPCG mixed end phase (chfsi), or LOBPCG throughout")
+    ap.add_argument("--block", type=int, default=None,
+                    help="block of the chosen form (default: 80 for chfsi on the tube, the library's "
+                         "rule for lobpcg)")
+    ap.add_argument("--degree", type=int, default=None,
+                    help="Chebyshev filter degree (default: 28 for chfsi on the tube)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tc-gemm", type=int, default=None, choices=[0, 1, 2],
                     help="block products of the eigensolver: the library default (unset), 0 cuBLAS, "
@@ -208,6 +213,22 @@ def solver_blocks(n_eig):
     return {"lobpcg": n_eig + max(4, n_eig // 8), "chfsi": n_eig + max(8, 3 * n_eig // 16)}
 
 
+# The tube's Chebyshev chosen form: block and filter degree from a sweep on this workload (blocks
+# 76-95 x degrees 16-40, L2 flushed), confirmed over 24 seeded start blocks drawn at each block's
+# width: block 80 at degree 28 took 22.6 +- 0.15 ms per solve (5-6 cycles + iterations) against
+# 24.9 +- 0.26 ms at the library's defaults (block 76, degree 24).  The defaults stay: on the
+# 32-k-point batch (48 eigenpairs) and the cyclic points (32) the wider block and the higher
+# degree measured slower.
+CHFSI_TUBE = {"block": 80, "degree": 28}
+
+
+def chosen_block_degree(args, n_eig):
+    """(block, Chebyshev degree or None) of the chosen form on the tube workload."""
+    if args.solver == "chfsi":
+        return args.block or CHFSI_TUBE["block"], args.degree or CHFSI_TUBE["degree"]
+    return args.block or solver_blocks(n_eig)["lobpcg"], args.degree
+
+
 def max_over_ranks(total_ms, world, device):
     """The slowest rank's time (every rank gets it): the job ends when its last rank does."""
     if world <= 1:
@@ -254,9 +275,13 @@ def ours_main(args):
     L = int(ctx.setup_basis(w.geom, w.etas)[0])
     ctx.build_potential(w.atoms)
     n_eig = w.n_eig
-    # each solver's default block (the library's rule); the start blocks are drawn at the wider
-    # one and a solver with the narrower block starts from their leading columns
+    # each solver's default block (the library's rule), the chosen form's from the sweep above;
+    # the start blocks are drawn at the widest and a narrower block starts from their leading
+    # columns
     NB = solver_blocks(n_eig)
+    NB[args.solver], degree = chosen_block_degree(args, n_eig)
+    if degree is not None:
+        ctx.set_option(hw.HW_OPT_CHEB_DEGREE, degree)
     nb = NB[args.solver]
     # every step solves from the next of NSTART seeded start blocks (the iteration count of one
     # start block is not representative: 6-10 across these blocks)
@@ -344,7 +369,10 @@ def ours_main(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded Gaussian-well nanotube potential)",
-        "config": {"workload": w.name, "L": L, "n_eig": n_eig, "block": nb, "kpoints": 1,
+        "config": {"workload": w.name, "L": L, "n_eig": n_eig, "block": nb,
+                   "degree": ctx.get_option(hw.HW_OPT_CHEB_DEGREE) if args.solver == "chfsi" else None,
+                   "block_degree": "chosen by a sweep on this workload" if args.solver == "chfsi" else "library rule",
+                   "kpoints": 1,
                    "tol": TOL, "form": form, "start_blocks": f"{NSTART} seeded complex Gaussian blocks, one per step in turn",
                    "l2": "flushed (512 MB write) before every step"},
         "chosen_form": {"iters": iters_mixed, "iters_per_step": step_iters, "converged": conv,
@@ -490,6 +518,7 @@ def ours_main(args):
             ctx_l.setup_basis(w.geom, w.etas)
             ctx_l.build_potential(w.atoms)
             ctx_l.set_mlp(train_precond.load_weights())
+            ctx_l.set_option(hw.HW_OPT_CHEB_DEGREE, ctx.get_option(hw.HW_OPT_CHEB_DEGREE))
         pc_other = "learned" if have_weights else "tpa"
         runs = [(f"{other}_mixed", "mixed", other, pc_other), ("chfsi_fp64", "fp64", "chfsi", "tpa")]
         if args.solver == "chfsi" and have_weights:
@@ -802,7 +831,7 @@ def e2e(ctx, w, L, nb, n_eig, dev, stream, flush, args, precond):
     V = torch.from_numpy(ctx.build_potential(w.atoms)).pin_memory()
     rank = int(os.environ.get("RANK", "0"))
     X0hs = [torch.from_numpy(np.ascontiguousarray(
-        inputs.random_block(L, max(solver_blocks(n_eig).values()), start_seed(rank, i)).T[:nb])).pin_memory()
+        inputs.random_block(L, max(max(solver_blocks(n_eig).values()), nb), start_seed(rank, i)).T[:nb])).pin_memory()
             for i in range(NSTART)]
     X0h = X0hs[0]
     Vd = torch.empty(V.shape, dtype=torch.float64, device=dev)
@@ -1073,7 +1102,9 @@ def kernel_case(args):
         if args.solver == "lobpcg" and os.path.exists(train_precond.WEIGHTS):
             ctx.set_mlp(train_precond.load_weights())
             pc = "learned"
-        nb = solver_blocks(w.n_eig)[args.solver]
+        nb, degree = chosen_block_degree(args, w.n_eig)
+        if degree is not None:
+            ctx.set_option(hw.HW_OPT_CHEB_DEGREE, degree)
         X0 = torch.from_numpy(np.ascontiguousarray(inputs.random_block(L, nb, 1234).T)).cuda()
         ctx.set_option(hw.HW_OPT_EIGENSOLVER, {"lobpcg": 0, "chfsi": 1}[args.solver])
         ctx.solve_eigs([0], w.n_eig, block=nb, tol=TOL, maxit=600, prec="mixed", precond=pc, X0=[X0])
