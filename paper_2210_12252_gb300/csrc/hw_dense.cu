@@ -26,6 +26,7 @@ namespace hw {
 // ---------------------------------------------------------------------- padding helpers
 // G[b] (n x n, column-major, stride sG): zero rows/cols >= nv[b], diagonal = diagval (+ index)
 __global__ void k_pad_square(double2* G, int n, int64_t sG, const int* nv, double diagval, int ramp) {
+  griddep_entry();
   const int b = blockIdx.y;
   double2* g = G + (size_t)b * sG;
   const int v = nv[b];
@@ -42,6 +43,7 @@ __global__ void k_pad_square(double2* G, int n, int64_t sG, const int* nv, doubl
 
 // A = (A + A^H) / 2 in place
 __global__ void k_hermitize(double2* A, int n, int64_t sA) {
+  griddep_entry();
   const int b = blockIdx.y;
   double2* a = A + (size_t)b * sA;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * n; t += gridDim.x * blockDim.x) {
@@ -82,6 +84,7 @@ template <> __device__ __forceinline__ float2 ld_c<float>(const double2& x) { re
 
 template <typename T>
 __global__ void __launch_bounds__(CHOL_THREADS) k_chol(double2* G, int n, int64_t sG, int* fail, int use_smem) {
+  griddep_entry();
   using C = typename Cx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x;
@@ -202,6 +205,7 @@ constexpr int CHS_NMAX = 112;
 
 template <typename T>
 __global__ void __launch_bounds__(CHS_THREADS) k_chol_small(double2* G, int n, int64_t sG, int* fail) {
+  griddep_entry();
   using C = typename Cx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* a = reinterpret_cast<C*>(smem_raw);
@@ -266,6 +270,7 @@ __global__ void __launch_bounds__(CHS_THREADS) k_chol_small(double2* G, int n, i
 // Given lower L (n x n), write Uinv = (L^H)^{-1} (upper triangular) into Ui.  Column j of
 // L^{-1} by forward substitution (one thread per column); Uinv = (L^{-1})^H.
 __global__ void k_trinv(const double2* L, int64_t sL, double2* Ui, int64_t sU, int n) {
+  griddep_entry();
   const int b = blockIdx.y;
   const double2* l = L + (size_t)b * sL;
   double2* u = Ui + (size_t)b * sU;
@@ -525,6 +530,7 @@ __global__ void __launch_bounds__(256) k_jacobi(JacArgs J) {
 
 // eigenvalues ascending: w[b][i], vectors Z[b] columns permuted (Z may not alias V)
 __global__ void k_eig_sort(const double2* A, const double2* V, int n, double* w, double2* Z) {
+  griddep_entry();
   const int b = blockIdx.x;
   const double2* a = A + (size_t)b * n * n;
   const double2* v = V + (size_t)b * n * n;
@@ -541,6 +547,7 @@ __global__ void k_eig_sort(const double2* A, const double2* V, int n, double* w,
 }
 
 __global__ void k_identity(double2* V, int n, int nprob) {
+  griddep_entry();
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < (long)nprob * n * n;
        t += (long)gridDim.x * blockDim.x) {
     const int r = (int)(t % n), c = (int)((t / n) % n);
@@ -635,7 +642,7 @@ cudaError_t dense_heev(DenseWork* dw, cudaStream_t st, double2* A, int n, int np
                        double2* Z, int* status, double tol) {
   const size_t elems = (size_t)nprob * n * n;
   if (elems > dw->cap || (n & 1)) return cudaErrorInvalidValue;
-  k_identity<<<256, 256, 0, st>>>(dw->V, n, nprob);
+  launch_dep(st, k_identity, 256, 256, 0, dw->V, n, nprob);
   cudaMemsetAsync(dw->rotated, 0, (size_t)(dw->maxsweep + 1) * sizeof(int), st);
   cudaMemsetAsync(dw->fro, 0, (size_t)nprob * sizeof(double), st);
   cudaMemsetAsync(dw->bar, 0, sizeof(GridBar), st);
@@ -661,7 +668,7 @@ cudaError_t dense_heev(DenseWork* dw, cudaStream_t st, double2* A, int n, int np
   cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaError_t e = cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(blocks), dim3(256), args, smem, st);
   if (e != cudaSuccess) return e;
-  k_eig_sort<<<nprob, 256, 0, st>>>(A, dw->V, n, w, Z);
+  launch_dep(st, k_eig_sort, nprob, 256, 0, A, dw->V, n, w, Z);
   return cudaGetLastError();
 }
 
@@ -671,10 +678,10 @@ cudaError_t dense_chol(cudaStream_t st, double2* G, int n, int nprob, int* fail,
   if (n <= CHS_NMAX) {   // the solver's block sizes: the unblocked kernel
     if (fp32) {
       cudaFuncSetAttribute(k_chol_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      k_chol_small<float><<<nprob, CHS_THREADS, chol_small_smem(n, sizeof(float2)), st>>>(G, n, (int64_t)n * n, fail);
+      launch_dep(st, k_chol_small<float>, nprob, CHS_THREADS, chol_small_smem(n, sizeof(float2)), G, n, (int64_t)n * n, fail);
     } else {
       cudaFuncSetAttribute(k_chol_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-      k_chol_small<double><<<nprob, CHS_THREADS, chol_small_smem(n, sizeof(double2)), st>>>(G, n, (int64_t)n * n,
+      launch_dep(st, k_chol_small<double>, nprob, CHS_THREADS, chol_small_smem(n, sizeof(double2)), G, n, (int64_t)n * n,
                                                                                              fail);
     }
     return cudaGetLastError();
@@ -683,28 +690,28 @@ cudaError_t dense_chol(cudaStream_t st, double2* G, int n, int nprob, int* fail,
     const size_t bytes = (size_t)n * n * sizeof(float2);
     if (bytes > 200 * 1024) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(k_chol<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    k_chol<float><<<nprob, CHOL_THREADS, bytes, st>>>(G, n, (int64_t)n * n, fail, 1);
+    launch_dep(st, k_chol<float>, nprob, CHOL_THREADS, bytes, G, n, (int64_t)n * n, fail, 1);
     return cudaGetLastError();
   }
   const size_t bytes = (size_t)n * n * sizeof(double2);
   const int use_smem = bytes <= 200 * 1024;
   if (use_smem) cudaFuncSetAttribute(k_chol<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  k_chol<double><<<nprob, CHOL_THREADS, use_smem ? bytes : 0, st>>>(G, n, (int64_t)n * n, fail, use_smem);
+  launch_dep(st, k_chol<double>, nprob, CHOL_THREADS, use_smem ? bytes : 0, G, n, (int64_t)n * n, fail, use_smem);
   return cudaGetLastError();
 }
 
 cudaError_t dense_trinv(cudaStream_t st, const double2* L, double2* Ui, int n, int nprob) {
-  k_trinv<<<dim3((n + 63) / 64, nprob), 64, 0, st>>>(L, (int64_t)n * n, Ui, (int64_t)n * n, n);
+  launch_dep(st, k_trinv, dim3((n + 63) / 64, nprob), 64, 0, L, (int64_t)n * n, Ui, (int64_t)n * n, n);
   return cudaGetLastError();
 }
 
 cudaError_t dense_pad(cudaStream_t st, double2* G, int n, int nprob, const int* nv, double diag, int ramp) {
-  k_pad_square<<<dim3(32, nprob), 256, 0, st>>>(G, n, (int64_t)n * n, nv, diag, ramp);
+  launch_dep(st, k_pad_square, dim3(32, nprob), 256, 0, G, n, (int64_t)n * n, nv, diag, ramp);
   return cudaGetLastError();
 }
 
 cudaError_t dense_hermitize(cudaStream_t st, double2* A, int n, int nprob) {
-  k_hermitize<<<dim3(32, nprob), 256, 0, st>>>(A, n, (int64_t)n * n);
+  launch_dep(st, k_hermitize, dim3(32, nprob), 256, 0, A, n, (int64_t)n * n);
   return cudaGetLastError();
 }
 
@@ -741,6 +748,7 @@ constexpr int J32_THREADS = 1024;
 // log: [nprob][maxsweep][n-1][n/2] rotations.  w: [nprob][n] eigenvalues (unsorted, FP64).
 __global__ void __launch_bounds__(J32_THREADS) k_jac32(const double2* A, int n, int maxsweep, double* shift,
                                                       Rot32* log, double* w, int* sweeps) {
+  griddep_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int h = n / 2;
   float2* S = reinterpret_cast<float2*>(smem_raw);
@@ -887,6 +895,7 @@ __global__ void __launch_bounds__(J32_THREADS) k_jac32(const double2* A, int n, 
 constexpr int JV_ROWS = 8;
 __global__ void __launch_bounds__(256) k_jac32_vectors(const Rot32* log, int n, int maxsweep, const int* sweeps,
                                                        double2* Z) {
+  griddep_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* V = reinterpret_cast<float2*>(smem_raw);   // [JV_ROWS][n]
   const int b = blockIdx.y, r0 = blockIdx.x * JV_ROWS;
@@ -923,6 +932,7 @@ __global__ void __launch_bounds__(256) k_jac32_vectors(const Rot32* log, int n, 
 
 // sort eigenvalues ascending and permute the eigenvector columns; grid nprob
 __global__ void k_sort_pairs(const double* w_in, const double2* Zin, int n, double* w_out, double2* Zout) {
+  griddep_entry();
   const int b = blockIdx.x;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double di = w_in[(size_t)b * n + i];
@@ -960,10 +970,10 @@ cudaError_t dense_heev32(cudaStream_t st, const double2* A, int n, int nprob, do
   p += (((size_t)nprob * sizeof(int)) + 255) & ~size_t(255);
   double2* Zu = reinterpret_cast<double2*>(p);
   cudaFuncSetAttribute(k_jac32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_jac32<<<nprob, J32_THREADS, smem, st>>>(A, n, maxsweep, shift, log, wu, sweeps);
-  k_jac32_vectors<<<dim3((n + JV_ROWS - 1) / JV_ROWS, nprob), 256, JV_ROWS * n * sizeof(float2), st>>>(
+  launch_dep(st, k_jac32, nprob, J32_THREADS, smem, A, n, maxsweep, shift, log, wu, sweeps);
+  launch_dep(st, k_jac32_vectors, dim3((n + JV_ROWS - 1) / JV_ROWS, nprob), 256, JV_ROWS * n * sizeof(float2), 
       log, n, maxsweep, sweeps, Zu);
-  k_sort_pairs<<<nprob, 256, 0, st>>>(wu, Zu, n, w, Z);
+  launch_dep(st, k_sort_pairs, nprob, 256, 0, wu, Zu, n, w, Z);
   return cudaGetLastError();
 }
 
@@ -1025,6 +1035,7 @@ __device__ __forceinline__ float block_sum_f(float v, float* red) {
 // Padding rows (diagonal >= 1e9, zero off the diagonal) are decoupled: they are moved out of
 // the reduction (compacted index map) and come back as exact unit eigenvectors.
 __global__ void __launch_bounds__(HH_THREADS) k_hh_tridiag(HhArgs H) {
+  griddep_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = H.n, b = blockIdx.x;
   float2* S = reinterpret_cast<float2*>(smem_raw);                       // packed lower triangle
@@ -1290,6 +1301,7 @@ constexpr int TRI_WARPS = 8;
 // the recurrences with reciprocal pivots, the warp normalises); grid (ceil(nw / 8), nprob).
 // Padding pairs (j >= nv) take their diagonal value.
 __global__ void __launch_bounds__(32 * TRI_WARPS) k_tri_eig(HhArgs H) {
+  griddep_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = H.n, nw = H.nw, b = blockIdx.y;
   const int nv = H.nv[b];
@@ -1389,6 +1401,7 @@ __global__ void __launch_bounds__(32 * TRI_WARPS) k_tri_eig(HhArgs H) {
 // thread per group start; thread 0 first writes the phase chain d_0 = 1, d_{k+1} = d_k e_k/|e_k|.
 // grid nprob
 __global__ void __launch_bounds__(256) k_tri_gs(HhArgs H) {
+  griddep_entry();
   const int n = H.n, nw = H.nw, b = blockIdx.x;
   const int nv = H.nv[b];
   const float* lam = H.lam + (size_t)b * nw;
@@ -1467,6 +1480,7 @@ constexpr int HB_RC = 16;   // reflectors staged in shared memory per round
 // shared memory (coalesced loads shared by its 8 vectors).  grid (ceil(nw / 8), nprob), 256
 // threads, dynamic smem HB_RC * n complex64
 __global__ void __launch_bounds__(256) k_hh_back(HhArgs H) {
+  griddep_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* vs = reinterpret_cast<float2*>(smem_raw);   // [HB_RC][n]
   __shared__ float bs[HB_RC];
@@ -1597,13 +1611,12 @@ cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, in
   H.lam64 = lam64;
   if (stage & 1) {
     cudaFuncSetAttribute(k_hh_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hh_smem(n));
-    k_hh_tridiag<<<nprob, HH_THREADS, hh_smem(n), st>>>(H);
+    launch_dep(st, k_hh_tridiag, nprob, HH_THREADS, hh_smem(n), H);
   }
   if (!(stage & 2)) return cudaGetLastError();
-  k_tri_eig<<<dim3((nw + TRI_WARPS - 1) / TRI_WARPS, nprob), 32 * TRI_WARPS, (3 + 3 * TRI_WARPS) * n * sizeof(float),
-              st>>>(H);
-  k_tri_gs<<<nprob, 256, (size_t)(((n + 1) & ~1) + 2 * n) * sizeof(float), st>>>(H);
-  k_hh_back<<<dim3((nw + 7) / 8, nprob), 256, (size_t)HB_RC * n * sizeof(float2), st>>>(H);
+  launch_dep(st, k_tri_eig, dim3((nw + TRI_WARPS - 1) / TRI_WARPS, nprob), 32 * TRI_WARPS, (3 + 3 * TRI_WARPS) * n * sizeof(float), H);
+  launch_dep(st, k_tri_gs, nprob, 256, (size_t)(((n + 1) & ~1) + 2 * n) * sizeof(float), H);
+  launch_dep(st, k_hh_back, dim3((nw + 7) / 8, nprob), 256, (size_t)HB_RC * n * sizeof(float2), H);
   return cudaGetLastError();
 }
 
@@ -1614,6 +1627,7 @@ cudaError_t dense_heev_hh32(cudaStream_t st, const double2* A, int n, int nw, in
 // is below 0.1 in size, else the orthogonality fix -R_ij/2 (near-degenerate pair).  Adds the
 // identity in rows < nw so that Z_w <- Z E is one GEMM.  grid (blocks, nprob)
 __global__ void k_oa_correction(const double2* R, const double2* S, int n, int nw, const double* lamall, double2* E) {
+  griddep_entry();
   const int b = blockIdx.y;
   const double2* r = R + (size_t)b * n * nw;
   const double2* s = S + (size_t)b * n * nw;
@@ -1653,6 +1667,7 @@ __global__ void k_oa_correction(const double2* R, const double2* S, int n, int n
 // (pairs at most 15 apart).  The strong-link bits of all such pairs are formed first, from
 // the diagonal in shared memory.  grid nprob, dynamic smem nw doubles + nw 16-bit masks
 __global__ void k_group_links(const double2* S, int nw, int* grp) {
+  griddep_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* dg = reinterpret_cast<double*>(smem_raw);
   unsigned short* lk = reinterpret_cast<unsigned short*>(dg + nw);   // bit d-1: a links to a+d
@@ -1689,6 +1704,7 @@ __global__ void k_group_links(const double2* S, int nw, int* grp) {
 // FP64) restricted to a group is diagonalised by a serial cyclic Jacobi (one thread per group);
 // the group's rotation U is written into E (identity elsewhere) and the eigenvalues into lam.
 __global__ void k_group_rr(const double2* S, int nw, const int* grp, double* lam, int lstride, double2* U) {
+  griddep_entry();
   const int b = blockIdx.x;
   const double2* s = S + (size_t)b * nw * nw;
   double2* u = U + (size_t)b * nw * nw;
@@ -1768,13 +1784,14 @@ __global__ void k_group_rr(const double2* S, int nw, const int* grp, double* lam
 
 cudaError_t launch_oa_correction(cudaStream_t st, const double2* R, const double2* S, int n, int nw, int nprob,
                                  const double* lamall, double2* E) {
-  k_oa_correction<<<dim3(16, nprob), 256, 0, st>>>(R, S, n, nw, lamall, E);
+  launch_dep(st, k_oa_correction, dim3(16, nprob), 256, 0, R, S, n, nw, lamall, E);
   return cudaGetLastError();
 }
 
 // F = I + first-order rotation between groups, from S' = V_g^H S_w V_g (already rotated inside
 // groups, so only between-group entries remain): F_ij = S'_ij / (lambda_j - lambda_i)
 __global__ void k_first_order(const double2* Sp, int nw, const int* grp, double2* F) {
+  griddep_entry();
   const int b = blockIdx.x;
   const double2* s = Sp + (size_t)b * nw * nw;
   double2* f = F + (size_t)b * nw * nw;
@@ -1807,13 +1824,14 @@ __global__ void k_first_order(const double2* Sp, int nw, const int* grp, double2
 }
 
 cudaError_t launch_first_order(cudaStream_t st, const double2* Sp, int nw, int nprob, const int* grp, double2* F) {
-  k_first_order<<<nprob, 512, nw * sizeof(int), st>>>(Sp, nw, grp, F);
+  launch_dep(st, k_first_order, nprob, 512, nw * sizeof(int), Sp, nw, grp, F);
   return cudaGetLastError();
 }
 
 // order the wanted pairs by eigenvalue: column rank(j) of Uout = column j of U
 __global__ void k_sort_wanted(const double* lam_in, int lstride, const double2* U, int nw, double* lam_out,
                               double2* Uout) {
+  griddep_entry();
   const int b = blockIdx.x;
   const double* l = lam_in + (size_t)b * lstride;
   for (int j = threadIdx.x; j < nw; j += blockDim.x) {
@@ -1828,14 +1846,14 @@ __global__ void k_sort_wanted(const double* lam_in, int lstride, const double2* 
 // group links and exact group rotations: Ug (identity outside groups), lam (unsorted)
 cudaError_t launch_group_rr(cudaStream_t st, const double2* Sw, int nw, int nprob, int* grp, double* lam,
                             int lstride, double2* Ug) {
-  k_group_links<<<nprob, 256, nw * sizeof(double) + ((nw + 1) / 2) * 4 + 16, st>>>(Sw, nw, grp);
-  k_group_rr<<<nprob, 64, 0, st>>>(Sw, nw, grp, lam, lstride, Ug);
+  launch_dep(st, k_group_links, nprob, 256, nw * sizeof(double) + ((nw + 1) / 2) * 4 + 16, Sw, nw, grp);
+  launch_dep(st, k_group_rr, nprob, 64, 0, Sw, nw, grp, lam, lstride, Ug);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sort_wanted(cudaStream_t st, const double* lam_in, int lstride, const double2* U, int nw, int nprob,
                                double* lam_out, double2* Uout) {
-  k_sort_wanted<<<nprob, 128, 0, st>>>(lam_in, lstride, U, nw, lam_out, Uout);
+  launch_dep(st, k_sort_wanted, nprob, 128, 0, lam_in, lstride, U, nw, lam_out, Uout);
   return cudaGetLastError();
 }
 
@@ -1862,6 +1880,7 @@ constexpr int TRSM_THREADS = 128;   // 4 rows per block, one warp per row
 template <typename T, int NPER>
 __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_lh(const double2* __restrict__ L, int m, double2* W,
                                                           int64_t rows, int64_t ld, int64_t sW, const int* skip) {
+  griddep_entry();
   using C = typename Cx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* dinv = reinterpret_cast<T*>(smem_raw);
@@ -1926,7 +1945,7 @@ template <typename T, int NPER>
 static cudaError_t trsm_launch(cudaStream_t st, const double2* L, int m, int nprob, double2* W, int64_t rows,
                                int64_t ld, int64_t sW, const int* skip) {
   const int rpb = TRSM_THREADS / 32;
-  k_trsm_lh<T, NPER><<<dim3((unsigned)((rows + rpb - 1) / rpb), nprob), TRSM_THREADS, m * sizeof(T), st>>>(
+  launch_dep(st, k_trsm_lh<T, NPER>, dim3((unsigned)((rows + rpb - 1) / rpb), nprob), TRSM_THREADS, m * sizeof(T), 
       L, m, W, rows, ld, sW, skip);
   return cudaGetLastError();
 }

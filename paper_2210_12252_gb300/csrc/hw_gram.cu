@@ -16,6 +16,8 @@
 
 #include <cstdint>
 
+#include "hw_common.cuh"
+
 namespace hw {
 
 namespace {
@@ -40,6 +42,7 @@ __device__ __forceinline__ float d2f_rn(double x) {
 __global__ void __launch_bounds__(G_THREADS) k_gram(const double2* __restrict__ A, int64_t lda, int64_t sA,
                                                     const double2* __restrict__ B, int64_t ldb, int64_t sB, int m,
                                                     int n, int K, int kc, double2* __restrict__ part) {
+  griddep_entry();
   __shared__ float2 As[GK][GT + 1];
   __shared__ float2 Bs[GK][GT + 1];
   const int tiles_m = (m + GT - 1) / GT;
@@ -109,6 +112,7 @@ __global__ void __launch_bounds__(G_THREADS) k_gram(const double2* __restrict__ 
 // C[b] = alpha sum_chunks part[b][chunk] + beta C[b]
 __global__ void k_gram_reduce(const double2* __restrict__ part, int m, int n, int nchunk, int batch, double alpha,
                               double beta, double2* C, int64_t ldc, int64_t sC) {
+  griddep_entry();
   const int64_t per = (int64_t)m * n, tot = per * batch;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = t / per, q = t - b * per;
@@ -158,10 +162,10 @@ cudaError_t gram_cf(cudaStream_t st, int m, int n, int K, double alpha, const do
   nchunk = (K + kc - 1) / kc;
   if (nchunk < 1) nchunk = 1;
   double2* part = reinterpret_cast<double2*>(work);
-  k_gram<<<dim3(tiles, nchunk, batch), G_THREADS, 0, st>>>(A, lda, sA, B, ldb, sB, m, n, K, kc, part);
+  launch_dep(st, k_gram, dim3(tiles, nchunk, batch), G_THREADS, 0, A, lda, sA, B, ldb, sB, m, n, K, kc, part);
   const int64_t tot = (int64_t)m * n * batch;
   const int grid = (int)((tot + 255) / 256 < 152 * 8 ? (tot + 255) / 256 : 152 * 8);
-  k_gram_reduce<<<grid, 256, 0, st>>>(part, m, n, nchunk, batch, alpha, beta, C, ldc, sC);
+  launch_dep(st, k_gram_reduce, grid, 256, 0, part, m, n, nchunk, batch, alpha, beta, C, ldc, sC);
   if (launches) *launches += 2;
   return cudaGetLastError();
 }

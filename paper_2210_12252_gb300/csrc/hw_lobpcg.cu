@@ -125,6 +125,7 @@ namespace {
 // R = HX - X theta and ||r_j||_2 (FP64); grid (nb, nk)
 __global__ void k_residual(const double2* S, const double2* HS, int64_t Lpad, int64_t sK,
                            const double* theta, int nb, double2* R, double* res) {
+  griddep_entry();
   __shared__ double red[8];
   const int j = blockIdx.x, b = blockIdx.y;
   const double2* x = S + (size_t)b * sK + (size_t)j * Lpad;
@@ -153,6 +154,7 @@ __global__ void k_residual(const double2* S, const double2* HS, int64_t Lpad, in
 // W[:, i] = R[:, iact[b][i]] (zero for -1); W lives in S at column offset woff; grid (na, nk)
 __global__ void k_gather_w(const double2* R, int nb, int64_t Lpad, const int* iact, int na, double2* S,
                            int64_t sK, int woff) {
+  griddep_entry();
   const int i = blockIdx.x, b = blockIdx.y;
   const int src = iact[(size_t)b * nb + i];
   double2* w = S + (size_t)b * sK + (size_t)(woff + i) * Lpad;
@@ -162,6 +164,7 @@ __global__ void k_gather_w(const double2* R, int nb, int64_t Lpad, const int* ia
 
 // pad an n x n Gram matrix: rows/cols i >= nv[b] become identity
 __global__ void k_pad_gram(double2* G, int n, const int* nv) {
+  griddep_entry();
   const int b = blockIdx.y;
   double2* g = G + (size_t)b * n * n;
   const int v = nv[b];
@@ -175,6 +178,7 @@ __global__ void k_pad_gram(double2* G, int n, const int* nv) {
 // j in the P block below npv[b], or j in the W block below nav[b]; invalid rows/cols get a
 // huge distinct diagonal so they sort last.  n may exceed nb+np+na by one (even size).
 __global__ void k_pad_rr(double2* A, int n, int nb, int np, int na, const int* npv, const int* nav) {
+  griddep_entry();
   const int b = blockIdx.y;
   double2* a = A + (size_t)b * n * n;
   auto valid = [&](int j) {
@@ -191,6 +195,7 @@ __global__ void k_pad_rr(double2* A, int n, int nb, int np, int na, const int* n
 
 // Y[:, i] = Z[:, iact[b][i]] with the X rows (< nb) zeroed; zero column for padding; grid (na, nk)
 __global__ void k_build_y(const double2* Z, int ne, int nb, const int* iact, int na, double2* Y) {
+  griddep_entry();
   const int i = blockIdx.x, b = blockIdx.y;
   const int src = iact[(size_t)b * nb + i];
   double2* y = Y + (size_t)b * ne * na + (size_t)i * ne;
@@ -201,6 +206,7 @@ __global__ void k_build_y(const double2* Z, int ne, int nb, const int* iact, int
 
 // C = 1.5 I - 0.5 G (one Newton-Schulz step towards orthonormal columns); grid (8, nk)
 __global__ void k_ns_coef(const double2* G, int m, double2* C) {
+  griddep_entry();
   const int b = blockIdx.y;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m * m; t += gridDim.x * blockDim.x) {
     const int i = t % m, j = t / m;
@@ -211,6 +217,7 @@ __global__ void k_ns_coef(const double2* G, int m, double2* C) {
 
 // w[b][j] = Re(z_j^H t_j) for the first m columns (Z and T with leading dimension n); grid (m, nk)
 __global__ void k_rq_diag(const double2* Z, const double2* T, int n, int64_t sZ, int64_t sT, double* w, int64_t sw) {
+  griddep_entry();
   __shared__ double red[8];
   const int j = blockIdx.x, b = blockIdx.y;
   const double2* z = Z + (size_t)b * sZ + (size_t)j * n;
@@ -230,6 +237,7 @@ __global__ void k_rq_diag(const double2* Z, const double2* T, int n, int64_t sZ,
 // check of the Householder route's wanted block: fail[b] = 1 when an entry of Z_w^H Z_w - I
 // (G, m x m) exceeds tol in modulus or an eigenvalue is not finite; grid nk
 __global__ void k_check_gram(const double2* G, int m, const double* w, int wstride, double tol, int* fail) {
+  griddep_entry();
   __shared__ int bad;
   const int b = blockIdx.x;
   if (threadIdx.x == 0) bad = 0;
@@ -252,6 +260,7 @@ __global__ void k_check_gram(const double2* G, int m, const double* w, int wstri
 // Rayleigh-Ritz matrix are formed in FP64; their mirror image replaces the lower-left blocks).
 // grid (8, nk)
 __global__ void k_mirror_xrows(double2* A, int n, int nb, int nS) {
+  griddep_entry();
   const int b = blockIdx.y;
   double2* a = A + (size_t)b * n * n;
   const int rows = nS - nb;
@@ -270,6 +279,7 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   return x ^ (x >> 31);
 }
 __global__ void k_random_start(double2* S, int64_t Lpad, int64_t sK, const int64_t* L, int nb, uint64_t seed) {
+  griddep_entry();
   const int j = blockIdx.x, b = blockIdx.y;
   double2* x = S + (size_t)b * sK + (size_t)j * Lpad;
   for (int64_t i = threadIdx.x; i < Lpad; i += blockDim.x) {
@@ -299,6 +309,7 @@ struct ChebScal {
 // columns j0 .. j0 + gridDim.x - 1 of each block; grid (columns, nk); src != dst
 __global__ void k_cheb(double2* S, const double2* HS, int64_t Lpad, int64_t sK, int nb, int src, int dst, int j0,
                        ChebScal sc) {
+  griddep_entry();
   const int j = j0 + blockIdx.x, b = blockIdx.y;
   const double al = sc.al[b], c = sc.c[b], be = sc.be[b];
   const size_t o = (size_t)b * sK;
@@ -320,6 +331,7 @@ __global__ void k_cheb(double2* S, const double2* HS, int64_t Lpad, int64_t sK, 
 // scale columns j0 .. j0 + gridDim.x - 1 of block q to unit 2-norm (zero columns stay zero);
 // grid (columns, nk)
 __global__ void k_colnorm(double2* S, int64_t Lpad, int64_t sK, int nb, int q, int j0) {
+  griddep_entry();
   __shared__ double red[32];
   __shared__ double scale;
   const int j = j0 + blockIdx.x, b = blockIdx.y;
@@ -349,6 +361,7 @@ __global__ void k_colnorm(double2* S, int64_t Lpad, int64_t sK, int nb, int q, i
 
 // out[0] = max_i V[i]; one CTA
 __global__ void k_vmax(const double* V, int64_t n, double* out) {
+  griddep_entry();
   __shared__ double red[32];
   double m = -1e300;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, V[i]);
@@ -367,6 +380,7 @@ struct PtrArr {
   const double* p[MAXSLOT];
 };
 __global__ void k_copy_start(PtrArr src, double2* S, int64_t Lpad, int64_t sK, const int64_t* L) {
+  griddep_entry();
   const int j = blockIdx.x, b = blockIdx.y;
   const double2* s = reinterpret_cast<const double2*>(src.p[b]) + (size_t)j * L[b];
   double2* x = S + (size_t)b * sK + (size_t)j * Lpad;
@@ -377,6 +391,7 @@ __global__ void k_copy_start(PtrArr src, double2* S, int64_t Lpad, int64_t sK, c
 // dst[b][c][r] = src[b][c*ld + r] (FP64 -> FP32 complex, packed columns); grid-stride
 __global__ void k_cvt_d2f(const double2* __restrict__ src, int64_t ld, int rows, int cols, int64_t sSrc,
                           float2* __restrict__ dst, int batch) {
+  griddep_entry();
   const int64_t per = (int64_t)rows * cols, tot = per * batch;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = t / per, q = t - b * per, c = q / rows, r = q - c * rows;
@@ -387,6 +402,7 @@ __global__ void k_cvt_d2f(const double2* __restrict__ src, int64_t ld, int rows,
 // dst[b][c*ld + r] = src[b][c][r] (FP32 -> FP64)
 __global__ void k_cvt_f2d(const float2* __restrict__ src, int rows, int cols, double2* __restrict__ dst, int64_t ld,
                           int64_t sDst, int batch) {
+  griddep_entry();
   const int64_t per = (int64_t)rows * cols, tot = per * batch;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = t / per, q = t - b * per, c = q / rows, r = q - c * rows;
@@ -413,7 +429,7 @@ struct Gemm {
   void cvt_in(const double2* src, int64_t ld, int rows, int cols, int64_t s, float2* dst, int batch) {
     const int64_t tot = (int64_t)rows * cols * batch;
     const int grid = (int)std::min<int64_t>((tot + 255) / 256, 152 * 16);
-    k_cvt_d2f<<<grid, 256, 0, ctx->stream>>>(src, ld, rows, cols, s, dst, batch);
+    launch_dep(ctx->stream, k_cvt_d2f, grid, 256, 0, src, ld, rows, cols, s, dst, batch);
     ctx->launches++;
   }
   void operator()(cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, double alpha,
@@ -471,7 +487,7 @@ struct Gemm {
                                      batch);
       const int64_t tot = (int64_t)m * n * batch;
       const int grid = (int)std::min<int64_t>((tot + 255) / 256, 152 * 16);
-      k_cvt_f2d<<<grid, 256, 0, ctx->stream>>>(c32, m, n, C, ldc, sC, batch);
+      launch_dep(ctx->stream, k_cvt_f2d, grid, 256, 0, c32, m, n, C, ldc, sC, batch);
       ctx->launches++;
       return;
     }
@@ -519,7 +535,7 @@ static hw_status cholqr(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, double2* S, int 
       gemm.lowp = keep;
       {
         ProfScope ps_(ctx, HW_PH_OTHER);
-        k_pad_gram<<<dim3(8, nk), 256, 0, ctx->stream>>>(w->G, ncol, d_nv);
+        launch_dep(ctx->stream, k_pad_gram, dim3(8, nk), 256, 0, w->G, ncol, d_nv);
         ctx->launches++;
       }
       {
@@ -580,7 +596,7 @@ static hw_status ns_orth(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, double2* S, int
     }
     {
       ProfScope ps_(ctx, HW_PH_CHOL);
-      k_ns_coef<<<dim3(8, nk), 256, 0, st>>>(w->G, ncol, w->Ui);
+      launch_dep(st, k_ns_coef, dim3(8, nk), 256, 0, w->G, ncol, w->Ui);
       ctx->launches++;
     }
     gemm(CUBLAS_OP_N, CUBLAS_OP_N, (int)Lpad, ncol, ncol, 1.0, Xb, Lpad, sK, w->Ui, ncol, (int64_t)ncol * ncol, 0.0,
@@ -626,7 +642,7 @@ static cudaError_t rr_eig_hh(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int 
       gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, n, 1.0, w->Z, n, sZ, w->Z, n, sZ, 0.0, w->G, nb, (int64_t)nb * nb, nk);
       {
         ProfScope ps_(ctx, HW_PH_EIG);
-        k_ns_coef<<<dim3(8, nk), 256, 0, st>>>(w->G, nb, w->Ui);
+        launch_dep(st, k_ns_coef, dim3(8, nk), 256, 0, w->G, nb, w->Ui);
         ctx->launches++;
       }
       gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, nb, 1.0, w->Z, n, sZ, w->Ui, nb, (int64_t)nb * nb, 0.0, w->B2, n, sB, nk);
@@ -652,7 +668,7 @@ static cudaError_t rr_eig_hh(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int 
     gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, n, 1.0, w->Z, n, sZ, w->Z, n, sZ, 0.0, w->G, nb, (int64_t)nb * nb, nk);
     {
       ProfScope ps_(ctx, HW_PH_EIG);
-      k_ns_coef<<<dim3(8, nk), 256, 0, st>>>(w->G, nb, w->Ui);
+      launch_dep(st, k_ns_coef, dim3(8, nk), 256, 0, w->G, nb, w->Ui);
       ctx->launches++;
     }
     gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, nb, 1.0, w->Z, n, sZ, w->Ui, nb, (int64_t)nb * nb, 0.0, w->B2, n, sB, nk);
@@ -705,7 +721,7 @@ static cudaError_t rr_eig(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int nb,
     {
       ProfScope ps_(ctx, HW_PH_EIG);
       // FP64 route: orthonormal to 1e-9; FP32-product phase: to 1e-5
-      k_check_gram<<<nk, 256, 0, st>>>(w->G, nb, w->w, n, lite ? 1e-5 : 1e-9, w->fail);
+      launch_dep(st, k_check_gram, nk, 256, 0, w->G, nb, w->w, n, lite ? 1e-5 : 1e-9, w->fail);
       ctx->launches++;
     }
     std::vector<int> f(nk);
@@ -731,7 +747,7 @@ static cudaError_t rr_eig(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int nb,
       gemm(CUBLAS_OP_C, CUBLAS_OP_N, nb, nb, n, 1.0, w->Z, n, sZ, w->Z, n, sZ, 0.0, w->G, nb, (int64_t)nb * nb, nk);
       {
         ProfScope ps_(ctx, HW_PH_OTHER);
-        k_ns_coef<<<dim3(8, nk), 256, 0, st>>>(w->G, nb, w->Ui);
+        launch_dep(st, k_ns_coef, dim3(8, nk), 256, 0, w->G, nb, w->Ui);
         ctx->launches++;
       }
       gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, nb, 1.0, w->Z, n, sZ, w->Ui, nb, (int64_t)nb * nb, 0.0, w->Y2, n,
@@ -743,7 +759,7 @@ static cudaError_t rr_eig(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int n, int nb,
     gemm(CUBLAS_OP_N, CUBLAS_OP_N, n, nb, n, 1.0, w->A, n, sZ, w->Z, n, sZ, 0.0, w->Y2, n, (int64_t)n * nb, nk);
     {
       ProfScope ps_(ctx, HW_PH_OTHER);
-      k_rq_diag<<<dim3(nb, nk), 256, 0, st>>>(w->Z, w->Y2, n, sZ, (int64_t)n * nb, w->w, n);
+      launch_dep(st, k_rq_diag, dim3(nb, nk), 256, 0, w->Z, w->Y2, n, sZ, (int64_t)n * nb, w->w, n);
       ctx->launches++;
     }
     return cudaGetLastError();
@@ -887,7 +903,7 @@ static hw_status rr_subspace(hw_ctx* ctx, LobpcgWork* w, Gemm& gemm, int* dnv, i
   cudaMemcpyAsync(dnv + 2 * nk, z.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st);
   {
     ProfScope ps_(ctx, HW_PH_OTHER);
-    k_pad_rr<<<dim3(8, nk), 256, 0, st>>>(w->A, n, nb, 0, 0, dnv + nk, dnv + 2 * nk);
+    launch_dep(st, k_pad_rr, dim3(8, nk), 256, 0, w->A, n, nb, 0, 0, dnv + nk, dnv + 2 * nk);
     ctx->launches++;
   }
   cudaError_t e = rr_eig(ctx, w, gemm, n, nb, false, gemm.lowp);
@@ -1044,11 +1060,11 @@ static hw_status start_block(hw_ctx* ctx, SolveSetup& su, Gemm& gemm, const doub
       pa.p[b] = X0[b];
     }
     ProfScope ps_(ctx, HW_PH_OTHER);
-    k_copy_start<<<dim3(nb, nk), 256, 0, st>>>(pa, w->SB[0], su.Lpad, su.sK, su.dL);
+    launch_dep(st, k_copy_start, dim3(nb, nk), 256, 0, pa, w->SB[0], su.Lpad, su.sK, su.dL);
     ctx->launches++;
   } else {
     ProfScope ps_(ctx, HW_PH_OTHER);
-    k_random_start<<<dim3(nb, nk), 256, 0, st>>>(w->SB[0], su.Lpad, su.sK, su.dL, nb, 0x5eed1234abcdULL);
+    launch_dep(st, k_random_start, dim3(nb, nk), 256, 0, w->SB[0], su.Lpad, su.sK, su.dL, nb, 0x5eed1234abcdULL);
     ctx->launches++;
   }
   deflate_cols(gemm, df, su.Lb, w->SB[0], su.Lpad, su.sK, 0, nb);
@@ -1125,7 +1141,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     double2* HS = w->HSB[cur];
     {
       ProfScope ps_(ctx, HW_PH_OTHER);
-      k_residual<<<dim3(nb, nk), 256, 0, st>>>(S, HS, Lpad, sK, w->theta, nb, w->R, w->res);
+      launch_dep(st, k_residual, dim3(nb, nk), 256, 0, S, HS, Lpad, sK, w->theta, nb, w->R, w->res);
       ctx->launches++;
     }
     cudaMemcpyAsync(resh.data(), w->res, resh.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -1237,7 +1253,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
              (int64_t)np * np, nk);
         {
           ProfScope ps_(ctx, HW_PH_OTHER);
-          k_pad_gram<<<dim3(8, nk), 256, 0, st>>>(w->G, np, dnv);
+          launch_dep(st, k_pad_gram, dim3(8, nk), 256, 0, w->G, np, dnv);
           ctx->launches++;
         }
         {
@@ -1280,7 +1296,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       refreshed = true;
       {
         ProfScope ps_(ctx, HW_PH_OTHER);
-        k_residual<<<dim3(nb, nk), 256, 0, st>>>(S, HS, Lpad, sK, w->theta, nb, w->R, w->res);
+        launch_dep(st, k_residual, dim3(nb, nk), 256, 0, S, HS, Lpad, sK, w->theta, nb, w->R, w->res);
         ctx->launches++;
       }
       cudaMemcpyAsync(resh.data(), w->res, resh.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -1338,7 +1354,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     // ---- W = K R[:, act]
     {
       ProfScope ps_(ctx, HW_PH_OTHER);
-      k_gather_w<<<dim3(na, nk), 256, 0, st>>>(w->R, nb, Lpad, w->iact, na, S, sK, woff);
+      launch_dep(st, k_gather_w, dim3(na, nk), 256, 0, w->R, nb, Lpad, w->iact, na, S, sK, woff);
       ctx->launches++;
     }
     {
@@ -1422,7 +1438,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
       gemm.lowp = false;
       {
         ProfScope ps_(ctx, HW_PH_OTHER);
-        k_mirror_xrows<<<dim3(8, nk), 256, 0, st>>>(w->A, n, nb, nS);
+        launch_dep(st, k_mirror_xrows, dim3(8, nk), 256, 0, w->A, n, nb, nS);
         ctx->launches++;
       }
     } else {
@@ -1431,7 +1447,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     }
     {
       ProfScope ps_(ctx, HW_PH_OTHER);
-      k_pad_rr<<<dim3(8, nk), 256, 0, st>>>(w->A, n, nb, np, na, dnv + nk, dnv + 2 * nk);
+      launch_dep(st, k_pad_rr, dim3(8, nk), 256, 0, w->A, n, nb, np, na, dnv + nk, dnv + 2 * nk);
       ctx->launches++;
     }
     e = rr_eig(ctx, w, gemm, n, nb, maxres > FP32_RR_ABOVE, gemm.lowp);
@@ -1448,7 +1464,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     // ---- P = S Y (active columns), Y orthogonal to Z[:, :nb] and orthonormal
     {
       ProfScope ps_(ctx, HW_PH_OTHER);
-      k_build_y<<<dim3(na, nk), 128, 0, st>>>(w->Z, n, nb, w->iact, na, w->Y);
+      launch_dep(st, k_build_y, dim3(na, nk), 128, 0, w->Z, n, nb, w->iact, na, w->Y);
       ctx->launches++;
     }
     for (int pass = 0; pass < 2; ++pass) {
@@ -1468,7 +1484,7 @@ static hw_status solve_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
         gemm.lowp = keep;
         {
           ProfScope ps_(ctx, HW_PH_OTHER);
-          k_pad_gram<<<dim3(8, nk), 256, 0, st>>>(w->G, na, dnv + 2 * nk);
+          launch_dep(st, k_pad_gram, dim3(8, nk), 256, 0, w->G, na, dnv + 2 * nk);
           ctx->launches++;
         }
         {
@@ -1612,7 +1628,7 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     const auto& pr = ctx->hb.prm;
     const int64_t grid = (int64_t)pr.Nth1 * pr.Nth2 * pr.Nr;
     ProfScope ps_(ctx, HW_PH_OTHER);
-    k_vmax<<<1, 1024, 0, st>>>(ctx->db.t64.V, grid, w->res);
+    launch_dep(st, k_vmax, 1, 1024, 0, ctx->db.t64.V, grid, w->res);
     ctx->launches++;
     cudaMemcpyAsync(&vmax, w->res, sizeof(double), cudaMemcpyDeviceToHost, st);
     const cudaError_t e = cudaStreamSynchronize(st);
@@ -1663,7 +1679,7 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     double2* HS = w->HSB[cur];
     {
       ProfScope ps_(ctx, HW_PH_OTHER);
-      k_residual<<<dim3(nb, nk), 256, 0, st>>>(S, HS, Lpad, sK, w->theta, nb, w->R, w->res);
+      launch_dep(st, k_residual, dim3(nb, nk), 256, 0, S, HS, Lpad, sK, w->theta, nb, w->R, w->res);
       ctx->launches++;
     }
     cudaMemcpyAsync(resh.data(), w->res, resh.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -1801,7 +1817,7 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     const int na = nb - nl;   // filtered columns nl .. nb-1 (na >= nb - n_eig >= 1)
     {
       ProfScope ps_(ctx, HW_PH_OTHER);
-      k_cheb<<<dim3(na, nk), 256, 0, st>>>(S, HS, Lpad, sK, nb, 0, 1, nl, sc);
+      launch_dep(st, k_cheb, dim3(na, nk), 256, 0, S, HS, Lpad, sK, nb, 0, 1, nl, sc);
       ctx->launches++;
     }
     for (int i = 2; i <= m; ++i) {   // each step fused into the H Y launch
@@ -1820,7 +1836,7 @@ static hw_status chfsi_impl(hw_ctx* ctx, int nk, const int* kidx_in, int n_eig, 
     const int q = m % 2;
     {
       ProfScope ps_(ctx, HW_PH_OTHER);
-      k_colnorm<<<dim3(na, nk), 256, 0, st>>>(S, Lpad, sK, nb, q, nl);
+      launch_dep(st, k_colnorm, dim3(na, nk), 256, 0, S, Lpad, sK, nb, q, nl);
       ctx->launches++;
     }
     double2* Yq = S + (size_t)q * nb * Lpad;    // the filtered block: [X_locked | Y_active]
@@ -1935,6 +1951,7 @@ extern "C" hw_status hw_heev(hw_ctx* ctx, int n, int nprob, int nw, const double
 
 // complex64 factors in the first n*n*8 bytes of each n*n*16-byte slot -> complex128 in dst
 __global__ void k_factor_c64_to_c128(const double2* slots, double2* dst, int n) {
+  griddep_entry();
   const float2* f = reinterpret_cast<const float2*>(slots + (size_t)blockIdx.y * n * n);
   double2* d = dst + (size_t)blockIdx.y * n * n;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * n; t += gridDim.x * blockDim.x)
@@ -1963,7 +1980,7 @@ extern "C" hw_status hw_cholesky(hw_ctx* ctx, int n, int nprob, double* G, doubl
     ctx->launches++;
   }
   if (e == cudaSuccess && prec == HW_MIXED) {   // the FP32 factor, widened through G
-    k_factor_c64_to_c128<<<dim3(16, nprob), 256, 0, st>>>(l, g, n);
+    launch_dep(st, k_factor_c64_to_c128, dim3(16, nprob), 256, 0, l, g, n);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(l, g, bytes, cudaMemcpyDeviceToDevice, st);
     ctx->launches++;

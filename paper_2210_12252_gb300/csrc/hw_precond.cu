@@ -34,6 +34,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 // grid: x = column within block, y = block slot
 __global__ void __launch_bounds__(TPA_THREADS) k_tpa(TpaArgs A) {
+  griddep_entry();
   __shared__ double red[TPA_THREADS / 32];
   const int slot = blockIdx.y, s = blockIdx.x;
   const int64_t L = A.L[slot];
@@ -75,7 +76,7 @@ cudaError_t launch_tpa(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld) {
   }
   a.blk = blk;
   ProfScope ps(ctx, HW_PH_PRECOND);
-  k_tpa<<<dim3(ns, blk.nslot), TPA_THREADS, 0, ctx->stream>>>(a);
+  launch_dep(ctx->stream, k_tpa, dim3(ns, blk.nslot), TPA_THREADS, 0, a);
   ctx->launches++;
   return cudaGetLastError();
 }

@@ -153,6 +153,7 @@ struct SplitArgs {
 
 // |x| bits of every column's entries -> atomicMax into mb[batch][col]; grid (segments, cols, batch)
 __global__ void k_colmax(const double2* X, int64_t ld, int64_t sX, int rows, int cols, unsigned long long* mb) {
+  griddep_entry();
   const int c = blockIdx.y, b = blockIdx.z;
   const double2* x = X + (size_t)b * sX + (size_t)c * ld;
   unsigned long long m = 0;
@@ -168,6 +169,7 @@ __global__ void k_colmax(const double2* X, int64_t ld, int64_t sX, int rows, int
 // groups), grid (row blocks, batch)
 __global__ void __launch_bounds__(256) k_rowmax(const double2* X, int64_t ld, int64_t sX, int rows, int cols,
                                                 unsigned long long* mb) {
+  griddep_entry();
   __shared__ unsigned long long red[8][32];
   const int b = blockIdx.y, tx = threadIdx.x, ty = threadIdx.y;
   const int l = blockIdx.x * 32 + tx;
@@ -191,6 +193,7 @@ __global__ void __launch_bounds__(256) k_rowmax(const double2* X, int64_t ld, in
 // CLS 0 writes S BF16 digit planes with the column's exponent, CLS 1 the TF32 hi / lo planes.
 template <int CLS>
 __global__ void __launch_bounds__(256) k_split_cols(SplitArgs a) {
+  griddep_entry();
   const int c = blockIdx.y, b = blockIdx.z;
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= (int)(a.Kp >> 1)) return;
@@ -251,6 +254,7 @@ __global__ void __launch_bounds__(256) k_split_cols(SplitArgs a) {
 // Block (32, 8); grid (row tiles, column tiles over Kp/2, batch).
 template <int CLS>
 __global__ void __launch_bounds__(256) k_split_rows(SplitArgs a) {
+  griddep_entry();
   __shared__ double2 T[32][33];
   const int b = blockIdx.z, l0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -329,6 +333,7 @@ __device__ __forceinline__ void drain_group(uint32_t tl, long long (&acc)[HB], i
 // FP64 class: digit-plane products with exact group sums (see the head of this file)
 __global__ void __launch_bounds__(ZG_THREADS, 1)
     k_mma_digits(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, MmaArgs a) {
+  griddep_entry();
   using Cfg = ZCfg<0>;
   constexpr int S = Cfg::S, BITS = Cfg::BITS, BN = Cfg::BN, SWZ = Cfg::SWZ, STAGES = Cfg::STAGES;
   constexpr int KC = SWZ / 2;                             // reduction elements per stage
@@ -509,6 +514,7 @@ __global__ void __launch_bounds__(ZG_THREADS, 1)
 // (BN columns); the epilogue writes the tile's FP32 partial sums.
 __global__ void __launch_bounds__(ZG_THREADS, 1)
     k_mma_tf32(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, MmaArgs a) {
+  griddep_entry();
   constexpr int KC = 32;                                  // FP32 entries per 128-byte row
   constexpr uint32_t TMEM_COLS = TF_BN_MAX;
   const int BN = a.BN;
@@ -681,6 +687,7 @@ __device__ __forceinline__ void sum_splits(const T* P, int nsplit, int g, int st
 }
 
 __global__ void __launch_bounds__(256) k_zgemm_out(OutArgs a) {
+  griddep_entry();
   __shared__ double sre[4][64], sim[4][64];
   __shared__ long long ire[4][64], iim[4][64];
   const int b = blockIdx.z, r = threadIdx.x, g = threadIdx.y;
@@ -877,28 +884,28 @@ static cudaError_t zgemm_run(ZgemmWork* w, cudaStream_t st, int cls, bool transA
       cudaMemsetAsync(mbA, 0, bytesM * nb, st);
       const int segs = std::max(1, std::min(64, (k + 2047) / 2048));
       if (transA)
-        k_colmax<<<dim3(segs, m, nb), 256, 0, st>>>(sa.X, lda, sA, k, m, mbA);
+        launch_dep(st, k_colmax, dim3(segs, m, nb), 256, 0, sa.X, lda, sA, k, m, mbA);
       else
-        k_rowmax<<<dim3((m + 31) / 32, nb), dim3(32, 8), 0, st>>>(sa.X, lda, sA, m, k, mbA);
-      k_colmax<<<dim3(segs, n, nb), 256, 0, st>>>(sb.X, ldb, sB, k, n, mbB);
+        launch_dep(st, k_rowmax, dim3((m + 31) / 32, nb), dim3(32, 8), 0, sa.X, lda, sA, m, k, mbA);
+      launch_dep(st, k_colmax, dim3(segs, n, nb), 256, 0, sb.X, ldb, sB, k, n, mbB);
       *launches += 2;
     }
     if (transA) {
       if (fp64)
-        k_split_cols<0><<<dim3((kh + 255) / 256, m, nb), 256, 0, st>>>(sa);
+        launch_dep(st, k_split_cols<0>, dim3((kh + 255) / 256, m, nb), 256, 0, sa);
       else
-        k_split_cols<1><<<dim3((kh + 255) / 256, m, nb), 256, 0, st>>>(sa);
+        launch_dep(st, k_split_cols<1>, dim3((kh + 255) / 256, m, nb), 256, 0, sa);
     } else {
       const dim3 g((m + 31) / 32, (kh + 31) / 32, nb);
       if (fp64)
-        k_split_rows<0><<<g, dim3(32, 8), 0, st>>>(sa);
+        launch_dep(st, k_split_rows<0>, g, dim3(32, 8), 0, sa);
       else
-        k_split_rows<1><<<g, dim3(32, 8), 0, st>>>(sa);
+        launch_dep(st, k_split_rows<1>, g, dim3(32, 8), 0, sa);
     }
     if (fp64)
-      k_split_cols<0><<<dim3((kh + 255) / 256, n, nb), 256, 0, st>>>(sb);
+      launch_dep(st, k_split_cols<0>, dim3((kh + 255) / 256, n, nb), 256, 0, sb);
     else
-      k_split_cols<1><<<dim3((kh + 255) / 256, n, nb), 256, 0, st>>>(sb);
+      launch_dep(st, k_split_cols<1>, dim3((kh + 255) / 256, n, nb), 256, 0, sb);
     CUtensorMap mA, mB;
     const int swz = fp64 ? ZCfg<0>::SWZ : 128;
     if (!make_plane_map(&mA, PA, !fp64, Kp, Mr, planes * nb, ZG_BM, planes, swz) ||
@@ -919,9 +926,9 @@ static cudaError_t zgemm_run(ZgemmWork* w, cudaStream_t st, int cls, bool transA
     ma.status = w->status;
     const dim3 grid(mt, nt, nsplit * nb);
     if (fp64)
-      k_mma_digits<<<grid, ZG_THREADS, zg_smem_bytes<0>(), st>>>(mA, mB, ma);
+      launch_dep(st, k_mma_digits, grid, ZG_THREADS, zg_smem_bytes<0>(), mA, mB, ma);
     else
-      k_mma_tf32<<<grid, ZG_THREADS, tf_smem_bytes(), st>>>(mA, mB, ma);
+      launch_dep(st, k_mma_tf32, grid, ZG_THREADS, tf_smem_bytes(), mA, mB, ma);
     OutArgs oa;
     oa.m = m;
     oa.n = n;
@@ -939,7 +946,7 @@ static cudaError_t zgemm_run(ZgemmWork* w, cudaStream_t st, int cls, bool transA
     oa.C = C + (size_t)b0 * sC;
     oa.ldc = ldc;
     oa.sC = sC;
-    k_zgemm_out<<<dim3((m + 63) / 64, nsplit >= 4 ? n : (n + 3) / 4, nb), dim3(64, 4), 0, st>>>(oa);
+    launch_dep(st, k_zgemm_out, dim3((m + 63) / 64, nsplit >= 4 ? n : (n + 3) / 4, nb), dim3(64, 4), 0, oa);
     *launches += 4;
   }
   return cudaGetLastError();
@@ -974,6 +981,7 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_zgemm_small(int transA, int m, int n, int k, double alpha, const double2* A,
                                                       int64_t lda, int64_t sA, const double2* B, int64_t ldb,
                                                       int64_t sB, double beta, double2* C, int64_t ldc, int64_t sC) {
+  griddep_entry();
   using Cr = rc_t<R>;
   __shared__ Cr As[ZS_T][ZS_KC + 1];   // op(A) rows of the tile, a chunk of the reduction
   __shared__ Cr Bs[ZS_KC][ZS_T];       // B rows (reduction index) x the tile's columns
@@ -1048,9 +1056,9 @@ cudaError_t zgemm_small(cudaStream_t st, int cls, bool transA, int m, int n, int
     return cudaErrorInvalidValue;
   const dim3 grid((m + ZS_T - 1) / ZS_T, (n + ZS_T - 1) / ZS_T, batch);
   if (cls == 0)
-    k_zgemm_small<ff><<<grid, 256, 0, st>>>(transA, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    launch_dep(st, k_zgemm_small<ff>, grid, 256, 0, transA, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
   else
-    k_zgemm_small<float><<<grid, 256, 0, st>>>(transA, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    launch_dep(st, k_zgemm_small<float>, grid, 256, 0, transA, m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
   return cudaGetLastError();
 }
 
