@@ -77,6 +77,20 @@ inline cudaError_t launch_dep(cudaStream_t st, void (*k)(KArgs...), dim3 grid, d
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
+// The same for a kernel given by address with its argument array (as cudaLaunchKernel takes).
+inline cudaError_t launch_dep_c(cudaStream_t st, const void* k, dim3 grid, dim3 block, size_t smem, void** args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, k, args);
+}
 #endif
 
 // FP64 <-> FP32 by integer bit operations.  This GPU executes the hardware conversions on its

@@ -261,6 +261,7 @@ inline size_t rad_fwd_smem(int Nr, int K, size_t tsz) {
 // row for every lane of a warp: one broadcast word), the item's coefficients 4 at a time.
 template <typename T>
 __global__ void __launch_bounds__(RAD_THREADS, sizeof(T) == 4 ? 2 : 1) k_radial_inv(RadArgs<T> A) {
+  griddep_entry();
   using V = cplx_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = blockIdx.y;
@@ -386,6 +387,7 @@ __device__ __forceinline__ void step_store(const RadArgs<T>& A, int slot, double
 // forward radial quadrature + diagonal term + scatter
 template <typename T>
 __global__ void __launch_bounds__(RAD_THREADS, sizeof(T) == 4 ? 2 : 1) k_radial_fwd(RadArgs<T> A) {
+  griddep_entry();
   using V = cplx_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = blockIdx.y;
@@ -590,6 +592,7 @@ __global__ void __launch_bounds__(RAD_THREADS, sizeof(T) == 4 ? 2 : 1) k_radial_
 // bytes per complex value as complex128), X read and Y written in FP64 with the diagonal term
 // in FP64.  Item and table layout as k_radial_inv / k_radial_fwd; one node per thread at a time.
 __global__ void __launch_bounds__(RAD_THREADS, 2) k_radial_inv_ff(RadArgs<double> A, const ff* __restrict__ tabff) {
+  griddep_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = blockIdx.y;
   const int gs = A.group_start[g], na = A.group_start[g + 1] - gs;
@@ -660,6 +663,7 @@ __global__ void __launch_bounds__(RAD_THREADS, 2) k_radial_inv_ff(RadArgs<double
 }
 
 __global__ void __launch_bounds__(RAD_THREADS, 2) k_radial_fwd_ff(RadArgs<double> A, const ff* __restrict__ tabff) {
+  griddep_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int g = blockIdx.y;
   const int gs = A.group_start[g], na = A.group_start[g + 1] - gs;
@@ -801,6 +805,7 @@ constexpr int SLAB_THREADS = 256;
 // kernel is then specialised for them); 0: taken from A.
 template <typename T, int N1 = 0, int N2 = 0>
 __global__ void __launch_bounds__(SLAB_THREADS) k_slab(SlabArgs<T> A) {
+  griddep_entry();
   using V = cplx_t<T>;
   // the specialised FP32 FFTs address their buffers through pd (16-byte FP64 elements spread
   // over the banks already; padding them measured slower)
@@ -939,6 +944,7 @@ __device__ __forceinline__ void dft16(R (&xr)[16], R (&xi)[16]) {
 // pass works in place on the inverse theta2 pass's output buffer.
 template <typename T, int N1, int N2>
 __global__ void __launch_bounds__(SLAB_THREADS) k_slab_r16(SlabArgs<T> A) {
+  griddep_entry();
   static_assert(N1 == 64 && (4 * N2) % 32 == 0 && 4 * N2 <= SLAB_THREADS, "4 lanes of 16 points per theta2 row");
   using V = cplx_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1353,8 +1359,8 @@ static cudaError_t launch_slab(const hw_ctx* ctx, dim3 grid, size_t smem, const 
     const dim3 g((grid.x + sq - 1) / sq, grid.y);
     if constexpr (sizeof(T) == sizeof(double)) {
       if (ffp) {
-        k_slab_q<double, ff><<<g, SLAB_THREADS, smem, ctx->stream>>>(sa, reinterpret_cast<const ff*>(ctx->db.vff), sq);
-        return cudaGetLastError();
+        return launch_dep(ctx->stream, k_slab_q<double, ff>, g, dim3(SLAB_THREADS), smem, sa,
+                          reinterpret_cast<const ff*>(ctx->db.vff), sq);
       }
     }
     // the FP32 slab between the tensor-core radial kernels starts while the inverse drains
@@ -1363,7 +1369,7 @@ static cudaError_t launch_slab(const hw_ctx* ctx, dim3 grid, size_t smem, const 
   }
   void* f = use_slab_r16(ctx, sizeof(cplx_t<T>)) ? (void*)k_slab_r16<T, 64, 48> : slab_kernel<T>(sa.Nth1, sa.Nth2);
   void* args[] = {(void*)&sa};
-  return cudaLaunchKernel(f, grid, dim3(SLAB_THREADS), args, smem, ctx->stream);
+  return launch_dep_c(ctx->stream, f, grid, dim3(SLAB_THREADS), smem, args);
 }
 
 static FftDev to_dev(const FftPlan& p) {
@@ -1466,9 +1472,9 @@ static cudaError_t launch_hx_bufs(hw_ctx* ctx, const Blocks& blk, int ns, int64_
         if (e != cudaSuccess) return e;
       } else if (ffp) {
         if constexpr (sizeof(T) == 8)
-          k_radial_inv_ff<<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra, reinterpret_cast<const ff*>(db.ff_rinv));
+          launch_dep(ctx->stream, k_radial_inv_ff, grid, RAD_THREADS, sm_inv, ra, reinterpret_cast<const ff*>(db.ff_rinv));
       } else {
-        k_radial_inv<T><<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra);
+        launch_dep(ctx->stream, k_radial_inv<T>, grid, RAD_THREADS, sm_inv, ra);
       }
       ctx->launches++;
     }
@@ -1511,9 +1517,9 @@ static cudaError_t launch_hx_bufs(hw_ctx* ctx, const Blocks& blk, int ns, int64_
         if (e != cudaSuccess) return e;
       } else if (ffp) {
         if constexpr (sizeof(T) == 8)
-          k_radial_fwd_ff<<<grid, RAD_THREADS, sm_fwd, ctx->stream>>>(ra, reinterpret_cast<const ff*>(db.ff_rfwd));
+          launch_dep(ctx->stream, k_radial_fwd_ff, grid, RAD_THREADS, sm_fwd, ra, reinterpret_cast<const ff*>(db.ff_rfwd));
       } else {
-        k_radial_fwd<T><<<grid, RAD_THREADS, sm_fwd, ctx->stream>>>(ra);
+        launch_dep(ctx->stream, k_radial_fwd<T>, grid, RAD_THREADS, sm_fwd, ra);
       }
       ctx->launches++;
     }
@@ -1675,7 +1681,7 @@ cudaError_t launch_density(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, c
     const size_t sm_inv = rad_inv_smem(Nr, K, sizeof(T));
     {
       ProfScope ps(ctx, HW_PH_RADIAL_INV);
-      k_radial_inv<T><<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra);
+      launch_dep(ctx->stream, k_radial_inv<T>, grid, RAD_THREADS, sm_inv, ra);
       ctx->launches++;
     }
     DensArgs<T> da;
@@ -1879,7 +1885,7 @@ cudaError_t launch_gradient(hw_ctx* ctx, const Blocks& blk, int ns, int64_t ld, 
       ra.rtab = src == 0 ? tb.rder : tb.rinv;
       ra.scale_mode = src == 0 ? 0 : (src == 1 ? 2 : 1);
       ProfScope ps(ctx, HW_PH_RADIAL_INV);
-      k_radial_inv<T><<<grid, RAD_THREADS, sm_inv, ctx->stream>>>(ra);
+      launch_dep(ctx->stream, k_radial_inv<T>, grid, RAD_THREADS, sm_inv, ra);
       ctx->launches++;
     }
     GradArgs<T> ga;
