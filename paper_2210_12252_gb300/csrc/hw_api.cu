@@ -51,6 +51,7 @@ void dfree(T*& p) {
 // V[i][j][p] (eq. wavefun_storage_real) -> Vd[p][j][i] in FP64 and FP32
 __global__ void k_v_relayout(const double* __restrict__ V, double* __restrict__ V64,
                              float* __restrict__ V32, float2* __restrict__ Vff, int n1, int n2, int nr) {
+  griddep_entry();
   const long total = (long)n1 * n2 * nr;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
     const int i = (int)(t % n1);
@@ -363,7 +364,7 @@ hw_status hw_set_potential(hw_ctx* ctx, const double* V, int on_device) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "set_potential copy");
-  k_v_relayout<<<1024, 256, 0, ctx->stream>>>(ctx->db.vscratch, ctx->db.t64.V, ctx->db.t32.V, ctx->db.vff,
+  launch_dep(ctx->stream, k_v_relayout, 1024, 256, 0, ctx->db.vscratch, ctx->db.t64.V, ctx->db.t32.V, ctx->db.vff,
                                               p.Nth1, p.Nth2, p.Nr);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "set_potential relayout");

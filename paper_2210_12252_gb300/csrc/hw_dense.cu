@@ -1857,13 +1857,6 @@ cudaError_t launch_sort_wanted(cudaStream_t st, const double* lam_in, int lstrid
   return cudaGetLastError();
 }
 
-// add the identity to E (so that Z (I + E) is one GEMM); grid (8, nprob)
-__global__ void k_add_identity(double2* E, int nw) {
-  const int b = blockIdx.y;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += gridDim.x * blockDim.x)
-    E[(size_t)b * nw * nw + i + (size_t)i * nw].x += 1.0;
-}
-
 }  // namespace hw
 
 // ===================================================================== Cholesky-QR apply

@@ -53,6 +53,7 @@ __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__floa
 // ------------------------------------------------------------------------ potential diagonal
 // sum of V over the angular grid at each radial node
 __global__ void k_vsum(const double* V, int n12, double* vsum) {
+  griddep_entry();
   __shared__ double red[8];
   const int p = blockIdx.x;
   double s = 0.0;
@@ -70,6 +71,7 @@ __global__ void k_vsum(const double* V, int n12, double* vsum) {
 // Vd_i = sum_p rfwd[n][k][p] rinv[n][p][k] vsum[p]  (rfwd carries 2 pi tau/Ncyc w_p/(N1 N2))
 __global__ void k_vdiag(const int* mnk, int64_t nmode, const double* rinv, const double* rfwd,
                         const double* vsum, int Nr, int K, double* vd) {
+  griddep_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nmode; i += (int64_t)gridDim.x * blockDim.x) {
     const int n = abs(mnk[3 * i + 1]), k = mnk[3 * i + 2];
     const double* rf = rfwd + ((size_t)n * K + k) * Nr;
@@ -146,6 +148,7 @@ __device__ __forceinline__ double tpa_of(double g) {
 
 // per column: KE_res of the residual (the TPA statistic); grid (ns, nslot)
 __global__ void k_col_keres(MlpArgs A) {
+  griddep_entry();
   __shared__ double red[2][8];
   const int slot = blockIdx.y, s = blockIdx.x;
   const double2* r = reinterpret_cast<const double2*>(A.blk.x[slot]) + (size_t)s * A.ld;
@@ -182,6 +185,7 @@ __global__ void k_col_keres(MlpArgs A) {
 // operations, since this GPU's FP64 pipe would otherwise cost as much as the network);
 // grid (row chunks, ns, nslot)
 __global__ void __launch_bounds__(128) k_mlp_apply(MlpArgs A) {
+  griddep_entry();
   extern __shared__ __align__(16) float Ps[];
   load_params_bf16(A.params, Ps);
   const int slot = blockIdx.z, s = blockIdx.y;
@@ -212,6 +216,7 @@ __global__ void __launch_bounds__(128) k_mlp_apply(MlpArgs A) {
 
 // training forward: s_i per row and column sums A = <z,e>, B = |z|^2, C = |e|^2
 __global__ void __launch_bounds__(128) k_mlp_fwd_train(MlpArgs A) {
+  griddep_entry();
   extern __shared__ __align__(16) float Ps[];
   __shared__ double red[5][4];
   load_params_bf16(A.params, Ps);
@@ -251,6 +256,7 @@ __global__ void __launch_bounds__(128) k_mlp_fwd_train(MlpArgs A) {
 
 // training backward per row: writes x, h1, da1, h2, da2, do to the row buffer
 __global__ void __launch_bounds__(128) k_mlp_bwd_rows(MlpArgs A, int ncols_total) {
+  griddep_entry();
   extern __shared__ __align__(16) float Ps[];
   load_params_bf16(A.params, Ps);
   const int slot = blockIdx.z, s = blockIdx.y;
@@ -303,6 +309,7 @@ __global__ void __launch_bounds__(128) k_mlp_bwd_rows(MlpArgs A, int ncols_total
 
 // weight gradients as sums over rows of outer products (split over row chunks, atomics)
 __global__ void __launch_bounds__(256) k_mlp_wgrad(const float* rowbuf, int64_t rows, float* grad) {
+  griddep_entry();
   constexpr int CH = 32;
   __shared__ float rv[CH][ROWVEC];
   float acc[(NPARAM + 255) / 256];
@@ -348,6 +355,7 @@ __global__ void __launch_bounds__(256) k_mlp_wgrad(const float* rowbuf, int64_t 
 }
 
 __global__ void k_loss(const double* colstat, int ncols, double* loss) {
+  griddep_entry();
   double s = 0.0;
   for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
     const double* cs = colstat + 5 * c;
@@ -367,6 +375,7 @@ __global__ void k_loss(const double* colstat, int ncols, double* loss) {
 
 __global__ void k_adam(float* p, float* m, float* v, const float* g, float lr, float b1, float b2,
                        float eps, float c1, float c2) {
+  griddep_entry();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= NPARAM) return;
   const float gi = g[i];
@@ -448,8 +457,8 @@ cudaError_t mlp_refresh_potential(hw_ctx* ctx) {
   double* vsum = nullptr;
   if (e == cudaSuccess) e = cudaMalloc((void**)&vsum, hb.prm.Nr * sizeof(double));
   if (e != cudaSuccess) return e;
-  k_vsum<<<hb.prm.Nr, 256, 0, ctx->stream>>>(ctx->db.t64.V, hb.prm.Nth1 * hb.prm.Nth2, vsum);
-  k_vdiag<<<256, 256, 0, ctx->stream>>>(st->mnk, nmode, ctx->db.t64.rinv, ctx->db.t64.rfwd, vsum, hb.prm.Nr,
+  launch_dep(ctx->stream, k_vsum, hb.prm.Nr, 256, 0, ctx->db.t64.V, hb.prm.Nth1 * hb.prm.Nth2, vsum);
+  launch_dep(ctx->stream, k_vdiag, 256, 256, 0, st->mnk, nmode, ctx->db.t64.rinv, ctx->db.t64.rfwd, vsum, hb.prm.Nr,
                                         hb.K, st->vdiag);
   ctx->launches += 2;
   e = cudaStreamSynchronize(ctx->stream);
@@ -490,9 +499,9 @@ cudaError_t launch_precond_learned(hw_ctx* ctx, const Blocks& blk, int ns, int64
   MlpArgs a;
   mlp_fill_args(ctx, blk, ns, ld, a);
   ProfScope ps(ctx, HW_PH_MLP);
-  k_col_keres<<<dim3(ns, blk.nslot), 256, 0, ctx->stream>>>(a);
+  launch_dep(ctx->stream, k_col_keres, dim3(ns, blk.nslot), 256, 0, a);
   const int rb = 128;
-  k_mlp_apply<<<dim3((unsigned)((a.Lmax + rb - 1) / rb), ns, blk.nslot), rb, NPARAM * sizeof(float), ctx->stream>>>(a);
+  launch_dep(ctx->stream, k_mlp_apply, dim3((unsigned)((a.Lmax + rb - 1) / rb), ns, blk.nslot), rb, NPARAM * sizeof(float), a);
   ctx->launches += 2;
   return cudaGetLastError();
 }
@@ -518,14 +527,14 @@ static cudaError_t mlp_grad(hw_ctx* ctx, int k, const double* R, const double* E
   }
   ProfScope ps(ctx, HW_PH_MLP);
   cudaMemsetAsync(st->grad, 0, NPARAM * sizeof(float), ctx->stream);
-  k_col_keres<<<dim3(ns, 1), 256, 0, ctx->stream>>>(a);
+  launch_dep(ctx->stream, k_col_keres, dim3(ns, 1), 256, 0, a);
   const int rb = 128;
   const dim3 g((unsigned)((L + rb - 1) / rb), ns, 1);
-  k_mlp_fwd_train<<<g, rb, NPARAM * sizeof(float), ctx->stream>>>(a);
-  k_mlp_bwd_rows<<<g, rb, NPARAM * sizeof(float), ctx->stream>>>(a, ns);
+  launch_dep(ctx->stream, k_mlp_fwd_train, g, rb, NPARAM * sizeof(float), a);
+  launch_dep(ctx->stream, k_mlp_bwd_rows, g, rb, NPARAM * sizeof(float), a, ns);
   const int64_t rows = (int64_t)ns * L;
-  k_mlp_wgrad<<<(unsigned)((rows + 1023) / 1024), 256, 0, ctx->stream>>>(st->rowbuf, rows, st->grad);
-  k_loss<<<1, 256, 0, ctx->stream>>>(st->colstat, ns, loss_dev);
+  launch_dep(ctx->stream, k_mlp_wgrad, (unsigned)((rows + 1023) / 1024), 256, 0, st->rowbuf, rows, st->grad);
+  launch_dep(ctx->stream, k_loss, 1, 256, 0, st->colstat, ns, loss_dev);
   ctx->launches += 5;
   return cudaGetLastError();
 }
@@ -619,7 +628,7 @@ hw_status hw_mlp_train_step(hw_ctx* ctx, int k, const double* R, const double* E
   const float c1 = 1.f - std::pow(b1, (float)st->adam_t), c2 = 1.f - std::pow(b2, (float)st->adam_t);
   {
     ProfScope ps(ctx, HW_PH_MLP);
-    k_adam<<<(NPARAM + 255) / 256, 256, 0, ctx->stream>>>(st->p32, st->m, st->v, st->grad, lr, b1, b2, 1e-8f, c1, c2);
+    launch_dep(ctx->stream, k_adam, (NPARAM + 255) / 256, 256, 0, st->p32, st->m, st->v, st->grad, lr, b1, b2, 1e-8f, c1, c2);
     ctx->launches++;
   }
   if (loss) e = cudaMemcpyAsync(loss, dloss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
