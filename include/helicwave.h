@@ -458,7 +458,11 @@ typedef enum {
                                programmatic stream serialisation, so that each starts its CTAs
                                while the one before it drains and waits on the device for that
                                kernel's results (the same order and results as 0); 0 plain
-                               stream-ordered launches. */
+                               stream-ordered launches.  The library's other kernels always use
+                               such launches, each waiting for the kernel before it before it
+                               reads or writes anything (again the order and results of plain
+                               launches), except the cooperative Jacobi kernels and the gradient
+                               kernel. */
 } hw_option;
 /* Set an option (HW_EINVAL for an unknown option, a read-only one or a bad value). */
 hw_status hw_set_option(hw_ctx* ctx, int option, int value);
