@@ -147,3 +147,22 @@ def test_chfsi_tube_mixed_overlap_bit_identical(hwmod):
     assert np.array_equal(res[1]["evals"][0], res[0]["evals"][0])
     assert np.array_equal(np.asarray(res[1]["iters"]), np.asarray(res[0]["iters"]))
     assert np.abs(res[1]["evals"][0] - golden("tube_eigs.txt")[: w.n_eig]).max() < 1e-6
+
+
+@pytest.mark.parametrize("block", [80, 95])
+def test_chfsi_tube_mixed_wide_block_takes_householder_route(hwmod, block):
+    """Blocks whose 3 nb Rayleigh-Ritz size (LOBPCG's [X W P]) does not fit one CTA's shared
+    memory (nb > 78) still take the Householder route for the smaller sizes (the filter's nb, the
+    end phase's [X W]); they once fell to the Jacobi solver for every step (2-3x slower).  The
+    phase profile records the reduction's launches only on the Householder route."""
+    w = inputs.tube()
+    ctx, L = make_ctx(hwmod, w, degree=28)
+    X0 = torch.from_numpy(np.ascontiguousarray(inputs.random_block(int(L[0]), block, 1234).T)).cuda()
+    ctx.profile(True)
+    r = ctx.solve_eigs([0], w.n_eig, block=block, tol=1e-6, maxit=100, prec="mixed", X0=[X0])
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    assert r["converged"]
+    assert prof["tridiag"][1] > 0
+    assert np.abs(r["evals"][0] - golden("tube_eigs.txt")[: w.n_eig]).max() < 1e-6
+    ctx.close()
