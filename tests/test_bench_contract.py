@@ -67,3 +67,16 @@ def test_profile_commands_run_committed_files_only():
         txt = open(os.path.join(pdir, name)).read()
         assert "_work/" not in txt, name
         assert "--clock-control none" in txt or "nvidia-smi" in txt, name
+
+
+def test_chosen_block_and_degree():
+    """The tube's chosen form runs at the swept block and degree unless the flags override them;
+    LOBPCG keeps the library's block rule; every start block is drawn at least as wide as the
+    block it feeds."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.chosen_block_degree(bench.parse([]), 64) == (80, 28)
+    assert bench.chosen_block_degree(bench.parse(["--block", "84", "--degree", "26"]), 64) == (84, 26)
+    assert bench.chosen_block_degree(bench.parse(["--solver", "lobpcg"]), 64) == (bench.solver_blocks(64)["lobpcg"], None)
+    nb = bench.chosen_block_degree(bench.parse([]), 64)[0]
+    assert max(max(bench.solver_blocks(64).values()), nb) >= nb > bench.solver_blocks(64)["chfsi"]
